@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the deterministic-NQS hot path on one B300 (or N independent replicas).
+
+One step = one pass of the whole path over the synthetic 16-orbital workload (8a+8b,
+|S| = 16384, backflow MLP 32-256-256-256 in the mixed BF16 form):
+  nqs_connections  (enumerate all singles/doubles of S, look up in S, build H_SS CSR)
+  nqs_energy_grad  (amplitudes, E_S, adjoint gradient)
+  nqs_pt2          (emit C, radix sort, dedup, segmented reduce, EN-PT2 sums)
+Metric: connections resolved per second over the step (H_SS lookups + PT2 emissions), with
+E_S+grad evaluations per second reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nqs|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+from paper_2601_21310_b300 import synth  # noqa: E402
+
+METRIC = "connections/s and E_S+grad evals/s at 1 B300; BF16 form vs FP64 at 1e-6 Ha"
+UNIT = "connections/s"
+WORKLOAD = "small_n16"
+L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nqs", choices=["nqs", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--buckets", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=4096, help="dets in the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region (read-only NVML queries)
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    REASONS = {
+        0x0000000000000004: "sw_power_cap",
+        0x0000000000000008: "hw_slowdown",
+        0x0000000000000020: "sw_thermal_slowdown",
+        0x0000000000000040: "hw_thermal_slowdown",
+        0x0000000000000080: "hw_power_brake_slowdown",
+    }
+
+    def __init__(self, index: int):
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self._stop = threading.Event()
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+        except Exception:
+            self.nv = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
+                r = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                for bit, name in self.REASONS.items():
+                    if r & bit:
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            time.sleep(0.05)
+
+    def __enter__(self):
+        if self.nv:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.nv:
+            self._stop.set()
+            self.t.join()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons)}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons)}
+
+
+# ------------------------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic work per launch of each instrumented kernel family
+# ------------------------------------------------------------------------------------------
+def algorithmic_work(name, wl, nS, nexc, nnz, n_emit, n_unique, net_flops):
+    """(bound, amount per launch, unit) - bytes for HBM-bound kernels, FLOP for GEMMs."""
+    if name == "rs_scatter":   # read key+value, write key+value
+        return "hbm", 32.0 * n_emit, "B"
+    if name == "rs_hist":      # read keys
+        return "hbm", 8.0 * n_emit, "B"
+    if name == "pt2_emit":     # write key+value per emission, read S and psi
+        return "hbm", 16.0 * n_emit + 24.0 * nS, "B"
+    if name == "seg_reduce":   # read values, read run starts + first keys, write one term per run
+        return "hbm", 8.0 * n_emit + 24.0 * n_unique, "B"
+    if name == "conn_fill":    # write col+val per nonzero, read S
+        return "hbm", 12.0 * nnz + 16.0 * nS, "B"
+    if name == "conn_count":
+        return "hbm", 24.0 * nS, "B"
+    if name == "spmv":
+        return "hbm", 12.0 * nnz + 8.0 * 3 * nS, "B"
+    if name == "gemm":
+        return "tensor", net_flops, "FLOP"
+    return "hbm", 0.0, "B"
+
+
+def kernel_traffic(name, wl):
+    """dram read+write bytes per launch from the committed ncu summary, if the kernel source is
+    unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{name}_{wl}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip().split()[0]
+    src = vals.get("source_file")
+    sha = vals.get("source_sha256")
+    tr = vals.get("dram_bytes_per_launch")
+    if not (src and sha and tr):
+        return None
+    with open(os.path.join(ROOT, src), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != sha:
+            return None
+    return float(tr)
+
+
+# ------------------------------------------------------------------------------------------
+# the GPU arm
+# ------------------------------------------------------------------------------------------
+def run_nqs(args, ws, rank, local):
+    import paper_2601_21310_b300.nqs as N
+    from paper_2601_21310_b300 import build as B
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synth.WORKLOADS[args.workload]
+    p = synth.make_problem(wl)
+    dtype = N.NQS_MIXED if wl.mixed else N.NQS_FP64
+    P = N.Problem(wl.norb, wl.nalpha, wl.nbeta, p.h, p.eri)
+    S_host = torch.from_numpy(p.S.view(np.int64)).view(torch.uint64).pin_memory()
+    dets = S_host.to(dev)
+    params = N.net_tensors(p.net, dtype, device=dev)
+    params_host = [t.cpu().pin_memory() for t in params]
+    net = N.Net(P, params, dtype)
+    nS = len(p.S)
+    o_conn = N.opts(precision=dtype, validate=0)
+    o_eg = N.opts(precision=dtype, validate=0)
+    o_pt = N.opts(precision=dtype, buckets=args.buckets, validate=0)
+    out = torch.empty(4, dtype=torch.float64, device=dev)
+    grad = torch.empty(net.num_params(), dtype=net.grad_dtype(), device=dev)
+    psi = torch.empty(nS, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev_eg = []
+
+    def step(record=False):
+        csr = N.connections(P, dets, o_conn)
+        if record:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        N.energy_grad(P, net, csr, dets, o=o_eg, out=out, grad=grad, psi=psi)
+        if record:
+            b.record(stream)
+            ev_eg.append((a, b))
+        E = out[0].item()
+        r = N.pt2(P, dets, psi, E, o=o_pt)
+        info = dict(n_conn=csr.n_enumerated + r["n_emitted"], n_hss=csr.n_enumerated,
+                    n_emit=r["n_emitted"], nnz=csr.nnz, n_unique=r["n_unique"], E=E,
+                    ext=r["ext"], int=r["int"])
+        csr.free()
+        return info
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    N.profile_reset()
+    N.profile_enable(True)
+    launches0 = N.launch_count()
+    times = []
+    n_conn_total = 0
+    sampler = ClockSampler(local)
+    t_wall0 = time.perf_counter()
+    with sampler:
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps (outside the events)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            info = step(record=True)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            n_conn_total += info["n_conn"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    launches = N.launch_count() - launches0
+    N.profile_enable(False)
+    prof = N.profile_read()
+    eg_ms = [x.elapsed_time(y) for x, y in ev_eg]
+    ms_step = sum(times) / len(times)
+    if ws > 1:
+        t = torch.tensor([sum(times)], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = t.item()
+    else:
+        total_ms = sum(times)
+    value = ws * n_conn_total / (total_ms / 1e3)
+
+    # roofline of the dominant instrumented kernel
+    peaks, peak_kind = load_peaks()
+    net_flops_fwd = 2.0 * nS * (wl.hidden[0] * wl.hidden[1] + wl.hidden[1] * wl.norb * wl.nelec)
+    total_gemm_flops = 3.0 * net_flops_fwd
+    shares = {k: v[0] for k, v in prof.items() if v[1] > 0}
+    dom = max(shares, key=shares.get)
+    ms_dom, n_dom = prof[dom]
+    nexc = synth_nexc(wl)
+    per_launch_flops = total_gemm_flops / max(1, n_dom / args.steps)
+    bound, amount, unit = algorithmic_work(dom, wl, nS, nexc, info["nnz"], info["n_emit"],
+                                           info["n_unique"], per_launch_flops)
+    avg_launch_s = ms_dom / n_dom / 1e3
+    if unit == "B":
+        achieved = amount / avg_launch_s / 1e9
+        peak = peaks["hbm_gbs"]
+        r_unit = "GB/s"
+    else:
+        achieved = amount / avg_launch_s / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1400.0)
+        r_unit = "TFLOP/s"
+    traffic = kernel_traffic(dom, wl.name)
+    roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 2), "peak": peak,
+                "unit": r_unit, "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_per_launch": amount, "peak_source": peak_kind}
+    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 4), "launches": v[1],
+                   "share_of_step": round(v[0] / args.steps / ms_step, 4)}
+               for k, v in prof.items() if v[1] > 0}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if wl.mixed else "f64",
+        "data": "synthetic (seeded integrals, level-major S, random-init backflow MLP)",
+        "config": {"workload": wl.name, "norb": wl.norb, "nalpha": wl.nalpha, "nbeta": wl.nbeta,
+                   "n_S": nS, "mlp": [2 * wl.norb, *wl.hidden, wl.norb * wl.nelec],
+                   "pt2_buckets": args.buckets, "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas{ws}"},
+        "evals_per_s": 1e3 / (sum(eg_ms) / len(eg_ms)),
+        "dets_evals_per_s": nS * 1e3 / (sum(eg_ms) / len(eg_ms)),
+        "connections_per_step": info["n_conn"], "hss_nnz": info["nnz"],
+        "pt2_unique": info["n_unique"], "E_S": info["E"], "dE_pt2_ext": info["ext"],
+        "dE_pt2_int": info["int"], "wall_s": wall, "gpu_launches": launches,
+        "roofline": roofline, "kernels": kernels, "clocks": sampler.summary(),
+    }
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg,
+                                o_pt, out, grad, psi, stream, ws)
+    return result, p
+
+
+def synth_nexc(wl):
+    n, m = wl.nalpha, wl.norb - wl.nalpha
+    c2 = lambda k: k * (k - 1) // 2  # noqa: E731
+    return 2 * n * m + 2 * c2(n) * c2(m) + (n * m) ** 2
+
+
+def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_pt, out, grad,
+            psi, stream, ws):
+    """Same metric through the public API with host buffers: every step copies S and the
+    parameters host->device and reads E, the gradient and the PT2 result back."""
+    grad_host = torch.empty(grad.shape, dtype=grad.dtype).pin_memory()
+    out_host = torch.empty(4, dtype=torch.float64).pin_memory()
+    h2d = S_host.numel() * 8 + sum(t.numel() * t.element_size() for t in params_host)
+    d2h = 4 * 8 + grad.numel() * grad.element_size() + 4 * 8 + 2 * 8 * o_pt.buckets
+    times, n_conn = [], 0
+    for it in range(args.warmup + args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dets.copy_(S_host, non_blocking=True)
+        for d, h in zip(params, params_host):
+            d.copy_(h, non_blocking=True)
+        csr = N.connections(P, dets, o_conn)
+        N.energy_grad(P, net, csr, dets, o=o_eg, out=out, grad=grad, psi=psi)
+        out_host.copy_(out, non_blocking=True)
+        grad_host.copy_(grad, non_blocking=True)
+        stream.synchronize()
+        r = N.pt2(P, dets, psi, float(out_host[0]), o=o_pt)
+        n = csr.n_enumerated + r["n_emitted"]
+        csr.free()
+        b.record(stream)
+        b.synchronize()
+        if it >= args.warmup:
+            times.append(a.elapsed_time(b))
+            n_conn += n
+    total = sum(times)
+    if ws > 1:
+        t = torch.tensor([total], device=dets.device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total = t.item()
+    return {"value": ws * n_conn / (total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": total / len(times)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (the reported baseline, and the reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_step(O, p, k, quant):
+    S = p.S[:k]
+    wl = p.wl
+    csr = O.hss(wl.norb, p.h, p.eri, S)
+    r = O.energy_grad(O.Net(p.net, quant=quant), S, csr)
+    pt = O.pt2(wl.norb, p.h, p.eri, S, r["psi"], r["E"])
+    return csr.n_enumerated + len(S) * O.n_excitations(wl.norb, wl.nalpha, wl.nbeta)
+
+
+def cpu_baseline(p, k):
+    from oracle import oracle as O
+    O.lib()
+    t = time.perf_counter()
+    n = oracle_step(O, p, k, p.wl.mixed)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"first {k} of {len(p.S)} dets of S: H_SS rows, E_S + gradient, PT2 over "
+                      f"their connected space ({n} connections, {dt:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    O.lib()
+    wl = synth.WORKLOADS[args.workload]
+    p = synth.make_problem(wl)
+    k = min(2048, len(p.S))
+    for _ in range(args.warmup):
+        oracle_step(O, p, k, wl.mixed)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        n += oracle_step(O, p, k, wl.mixed)
+    dt = time.perf_counter() - t0
+    v = n / dt
+    sample = f"first {k} of {len(p.S)} dets of S per step: H_SS rows, E_S + gradient, PT2"
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "norb": wl.norb, "nalpha": wl.nalpha, "n_S": len(p.S),
+                       "mlp": [2 * wl.norb, *wl.hidden, wl.norb * wl.nelec]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, ws, rank)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    if ws > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res, p = run_nqs(args, ws, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(p, min(args.cpu_sample, len(p.S)))
+        print(json.dumps(res))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

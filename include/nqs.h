@@ -1,0 +1,190 @@
+/*
+ * nqs.h -- C ABI of the B300 (sm_103a) library for the data-parallel hot path of the
+ * deterministic neural-network-quantum-state method of arXiv 2601.21310:
+ *   (1) Slater-Condon generation of all single and double excitations of the configurations
+ *       of a selected set S, with fermionic signs and FP64 matrix elements, and the projected
+ *       Hamiltonian H_SS in CSR (Sec. 3.1 "Discrete Combinatorial Kernel"; Eq. connected_set);
+ *   (2) the neural-backflow amplitude psi(x) = det Phi(x)[occ_a, 0:na] * det Phi(x)[occ_b,
+ *       na:na+nb] with Phi(x) = Phi0 + MLP(x) (Eqs. effective_orbital_matrix,
+ *       occupied_submatrix, backflow_amplitude);
+ *   (3) the subspace variational energy E_S and its parameter gradient (Eqs.
+ *       variational_energy, variational_gradient);
+ *   (4) the post-hoc Epstein-Nesbet PT2 correction over C\S (Eq. pt2_correction).
+ *
+ * Conventions shared by every entry point
+ *   - A configuration ("det") is two uint64 words {a, b}: bit p of a (b) set means alpha (beta)
+ *     spatial orbital p is occupied. Arrays of dets are [n][2] uint64, 16-byte aligned.
+ *   - Key order is (a, b) lexicographic with a in the high word. S must be sorted ascending
+ *     and unique, and every det must hold nalpha alpha and nbeta beta electrons.
+ *   - Spin-orbital order is alpha 0..norb-1 then beta 0..norb-1, and |x> is the product of
+ *     creation operators of the occupied spin-orbitals in ascending order acting on |0>. Under
+ *     this order the single-excitation sign is (-1)^(occupied orbitals of that spin strictly
+ *     between the two indices).
+ *   - ERIs are real, in chemists' notation (pq|rs), with eightfold symmetry, stored row-major
+ *     as eri[((p*norb+q)*norb+r)*norb+s].
+ *   - Canonical excitation order of one det: alpha singles (i asc, a asc), beta singles,
+ *     alpha-alpha doubles (hole pairs i<j lexicographic, then particle pairs a<b
+ *     lexicographic), beta-beta doubles, alpha-beta doubles (i_a, a_a, j_b, b_b, b fastest).
+ *   - Pointers marked "device" are CUDA device pointers of the current device; "host" are
+ *     ordinary host pointers. Unless stated, the caller owns every buffer it passes.
+ *   - All work is ordered on the given stream (NULL = legacy default stream). Calls that
+ *     return host scalars synchronise that stream before returning.
+ *   - Every function returns NQS_OK (0), a positive warning, or a negative error code; no
+ *     C++ exception crosses this boundary. On error, outputs are unspecified.
+ *   - Handles are not thread safe: use one problem handle from one host thread at a time.
+ */
+#ifndef NQS_H
+#define NQS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* nqs_stream_t; /* the same object as cudaStream_t */
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define NQS_OK 0
+#define NQS_WARN_SINGULAR 1        /* an occupied block had an exactly zero pivot: psi = 0 */
+#define NQS_ERR_ARG (-1)           /* invalid argument (null pointer, size, option) */
+#define NQS_ERR_UNSORTED (-2)      /* S is not sorted ascending or has duplicates */
+#define NQS_ERR_POPCOUNT (-3)      /* a det has the wrong number of alpha/beta electrons */
+#define NQS_ERR_NORB (-4)          /* norb outside 1..64, or key wider than supported */
+#define NQS_ERR_OOM (-5)           /* device allocation failed */
+#define NQS_ERR_CUDA (-6)          /* a CUDA runtime call or a kernel launch failed */
+#define NQS_ERR_TIMEOUT (-7)       /* a bounded device-side wait gave up */
+#define NQS_ERR_UNSUPPORTED (-8)   /* valid request outside what this build implements */
+
+/* ---- precision forms -------------------------------------------------------------------- */
+#define NQS_FP64 0   /* plain form: FP64 parameters, FP64 GEMMs, FP64 LU */
+#define NQS_MIXED 1  /* BF16 weights and activations on tensor cores with FP32 accumulation,
+                        FP32 biases/Phi0, FP32 LU with FP64 log|det|; FP64 for everything
+                        Hamiltonian-side (elements, SpMV, reductions, PT2) */
+
+typedef struct nqs_problem nqs_problem; /* opaque: device copies of the integrals */
+typedef struct nqs_net nqs_net;         /* opaque: refers to caller-owned device parameters */
+
+/* Options. Zero-initialise and set what you need; nqs_opts_default() fills the defaults. */
+typedef struct {
+    int precision;      /* NQS_FP64 or NQS_MIXED (must match the net's dtype) */
+    int buckets;        /* PT2 hash buckets, >= 1 (more buckets = less scratch memory) */
+    int64_t chunk;      /* PT2 cap on emitted (key, value) pairs held at once; 0 = automatic */
+    int validate;       /* 1: check that S is sorted, unique and has the right popcounts */
+    int internal_pt2;   /* 1: also compute the internal (x in S) PT2 term */
+    int reserved[8];
+} nqs_opts;
+
+/* Library-owned CSR of H_SS (device memory). Row r holds, in order: the diagonal element
+ * (column r), then every excitation of S[r] that lies in S, in canonical excitation order.
+ * val[k] = <S[col[k]]|H|S[r]> (H_SS is symmetric, bit for bit under this library's summation
+ * order). Free with nqs_csr_free. */
+typedef struct {
+    int64_t* row_ptr; /* device [n_rows + 1] */
+    int32_t* col;     /* device [nnz] */
+    double* val;      /* device [nnz] */
+    int64_t nnz;
+    int64_t n_rows;
+} nqs_csr;
+
+void nqs_opts_default(nqs_opts* opts);
+const char* nqs_status_string(int status);
+const char* nqs_version(void);
+/* message of the last failed CUDA call on this host thread ("" if none) */
+const char* nqs_last_error(void);
+
+/* Build the problem: copies h (host, norb*norb FP64, symmetric) and eri (host, norb^4 FP64,
+ * chemists' notation) to the current device, with derived tables (Coulomb J_pq = (pp|qq),
+ * exchange K_pq = (pq|qp)). ecore is added to nothing: energies are electronic. Requires
+ * 1 <= norb <= 64 and 0 < nalpha, nbeta < norb. Synchronous. Errors: NQS_ERR_ARG,
+ * NQS_ERR_NORB, NQS_ERR_OOM, NQS_ERR_CUDA. Sec. 3.3 (Hamiltonian integrals as input),
+ * Algorithm 1 input. */
+int nqs_problem_create(int norb, int nalpha, int nbeta, const double* h, const double* eri,
+                       double ecore, nqs_problem** out);
+int nqs_problem_destroy(nqs_problem* problem);
+
+/* Describe the backflow network of Sec. 2.2 / Sec. 3.3: input x in {0,1}^(2 norb) (alpha bits
+ * then beta bits), z1 = W1 x + b1, h1 = tanh z1, z2 = W2 h1 + b2, h2 = tanh z2,
+ * out = W3 h2 + b3, Phi = Phi0 + reshape(out, [norb][na+nb]) row-major.
+ * params: 7 device pointers {W1 [H1][2 norb], b1 [H1], W2 [H2][H1], b2 [H2],
+ * W3 [norb(na+nb)][H2], b3 [norb(na+nb)], Phi0 [norb][na+nb]}, all row-major, owned by the
+ * caller and read at every call (so optimiser updates in place are seen).
+ * dtype NQS_FP64: all FP64. dtype NQS_MIXED: W1, W2, W3 bfloat16; b1, b2, b3, Phi0 float.
+ * Phi0 is fixed (not differentiated). Errors: NQS_ERR_ARG, NQS_ERR_OOM. */
+int nqs_net_create(nqs_problem* problem, int H1, int H2, int dtype, const void* const* params,
+                   nqs_net** out);
+int nqs_net_destroy(nqs_net* net);
+/* number of trainable parameters = H1*2norb + H1 + H2*H1 + H2 + nout*H2 + nout */
+int64_t nqs_net_num_params(const nqs_net* net);
+
+/* H_xx for n dets (Slater-Condon, zero excitations; the denominators of Eq. pt2_correction).
+ * dets: device [n][2]; out: device [n] FP64. Stream-ordered, no sync. */
+int nqs_diag(nqs_problem* problem, const uint64_t* dets, int64_t n, double* out,
+             nqs_stream_t stream);
+
+/* Enumerate every single and double excitation of every det of S (Eq. connected_set), look
+ * each up in S, and build H_SS in CSR (Sec. 3.1: the combinatorial kernel exports H_VV as
+ * CSR; Algorithm 1 step 1). dets: device [nS][2], sorted and unique. On success *out holds a
+ * library-owned CSR and *n_enumerated (host, may be NULL) the number of (det, excitation)
+ * pairs resolved. Synchronises the stream (nnz must be known to allocate). Errors:
+ * NQS_ERR_ARG, NQS_ERR_UNSORTED / NQS_ERR_POPCOUNT (with validate), NQS_ERR_OOM, NQS_ERR_CUDA. */
+int nqs_connections(nqs_problem* problem, const uint64_t* dets, int64_t nS, const nqs_opts* opts,
+                    nqs_csr* out, int64_t* n_enumerated, nqs_stream_t stream);
+int nqs_csr_free(nqs_csr* csr);
+
+/* Amplitudes psi(x) of Eq. backflow_amplitude as log|psi| (device [nS] FP64) and sign (device
+ * [nS] int8: +1, -1, or 0 for an exactly singular block, reported as NQS_WARN_SINGULAR).
+ * Stream-ordered; synchronises only to report the singular warning. */
+int nqs_amplitudes(nqs_problem* problem, nqs_net* net, const uint64_t* dets, int64_t nS,
+                   double* logabs, int8_t* sign, const nqs_opts* opts, nqs_stream_t stream);
+
+/* Rayleigh quotient of a given vector on H_SS (Eq. variational_energy with psi injected):
+ * psi device [nS] FP64; out device [3] = {E, N, D}; v device [nS] (may be NULL) = H_SS psi.
+ * N and D are compensated FP64 sums. Stream-ordered, no sync. */
+int nqs_energy_from_psi(const nqs_csr* csr, const double* psi, int64_t nS, double* out,
+                        double* v, nqs_stream_t stream);
+
+/* E_S and its gradient, Eqs. variational_energy and variational_gradient:
+ *   psi~ = sign * exp(log|psi| - max log|psi|), v = H_SS psi~, N = psi~.v, D = psi~.psi~,
+ *   E = N/D, grad = (2/D) sum_x (v_x - E psi~_x) dpsi~_x/dtheta
+ * through a hand-written adjoint (Jacobi's formula with the LU inverse, then the MLP
+ * backward). out: device [4] = {E, N, D, max log|psi|}. grad: device, nqs_net_num_params
+ * entries laid out W1, b1, W2, b2, W3, b3 (FP64 for NQS_FP64, float for NQS_MIXED), or NULL
+ * for the energy only. psi_out: device [nS] FP64 psi~ (may be NULL). Stream-ordered, no sync.
+ * csr must come from nqs_connections on the same S. */
+int nqs_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr, const uint64_t* dets,
+                    int64_t nS, double* out, void* grad, double* psi_out, const nqs_opts* opts,
+                    nqs_stream_t stream);
+
+/* Epstein-Nesbet PT2, Eq. pt2_correction, with Psi_S = psi / sqrt(D), D = psi.psi:
+ *   external = sum_{x' in C\S} c(x')^2 / (D (E - H_x'x')),  c(x') = sum_{y in S} H_x'y psi_y
+ *   internal = sum_{x in S} r_x^2 / (D (E - H_xx)),         r = H_SS psi - E psi
+ * C\S is generated on the device: every excitation of every y in S is emitted as
+ * (key x', H_x'y psi_y) in canonical order, radix-sorted by key (stable), deduplicated, and
+ * each run summed in emission order; members of S feed the internal term. The work is split
+ * into hash buckets (SplitMix64 finaliser: bucket = mix(mix(a) ^ b) mod B).
+ * psi: device [nS] FP64 at any scale. out: host [4] = {external, internal, number of unique
+ * x' in C\S, number of emitted pairs}. bucket_partials: host [2*B] (external, internal per
+ * bucket) or NULL. Requires 2*norb <= 64 (single-word keys). Synchronises the stream.
+ * Errors: NQS_ERR_ARG, NQS_ERR_NORB, NQS_ERR_OOM, NQS_ERR_CUDA. */
+int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64_t nS,
+            double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
+            nqs_stream_t stream);
+
+/* Optional per-kernel timing for benchmarks (not part of the method): when enabled, the
+ * library brackets its main kernel launches with CUDA events recorded on the launching stream.
+ * nqs_profile_read synchronises those events and returns the summed milliseconds and the
+ * launch count of one kernel family: "conn_count", "conn_fill", "pt2_count", "pt2_emit",
+ * "rs_hist", "rs_scatter", "seg_reduce", "gemm", "lu", "spmv", "layer1". Process-wide state;
+ * not thread safe. */
+int nqs_profile_enable(int on);
+int nqs_profile_reset(void);
+int nqs_profile_read(const char* kernel, double* total_ms, int64_t* launches);
+/* number of kernels this library has launched in this process so far */
+int64_t nqs_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NQS_H */

@@ -1,0 +1,606 @@
+// Neural-backflow amplitude (Sec. 2.2; Eqs. effective_orbital_matrix, occupied_submatrix,
+// backflow_amplitude) and its hand-written adjoint (Eq. variational_gradient via Jacobi's
+// formula d det A / dA = det A * A^{-T}).
+//
+//   layer 1: z1 = W1 x + b1 over the 0/1 input -> a gather-sum of the occupied columns of W1
+//   layer 2: z2 = W2 h1 + b2, h2 = tanh z2        (dense GEMM)
+//   layer 3: Phi = Phi0 + (W3 h2 + b3)            (dense GEMM, epilogue adds b3 then Phi0)
+//   psi = det Phi[occ_a, 0:na] * det Phi[occ_b, na:na+nb]: warp-per-block LU with partial
+//   pivoting (FP64 form: double; mixed form: float) with log|det| summed in FP64, and the
+//   block inverse kept for the adjoint.
+#include <math.h>
+#include <string.h>
+
+#include "ansatz.cuh"
+#include "excite.cuh"
+#include "nqs_internal.cuh"
+#include "prof.cuh"
+
+template <class T>
+struct Cvt;
+template <>
+struct Cvt<double> {
+    __device__ static double to_acc(double x) { return x; }
+    __device__ static double from(double x) { return x; }
+};
+template <>
+struct Cvt<float> {
+    __device__ static float to_acc(float x) { return x; }
+    __device__ static float from(float x) { return x; }
+};
+template <>
+struct Cvt<__nv_bfloat16> {
+    __device__ static float to_acc(__nv_bfloat16 x) { return __bfloat162float(x); }
+    __device__ static __nv_bfloat16 from(float x) { return __float2bfloat16_rn(x); }
+};
+
+__device__ __forceinline__ double act_tanh(double z) { return tanh(z); }
+__device__ __forceinline__ float act_tanh(float z) { return tanhf(z); }
+
+// ------------------------------------------------------------------------------------------
+// layer 1: gather-sum over occupied inputs (alpha bit p -> column p, beta bit p -> norb + p),
+// summed in ascending column order, then + b1, tanh.
+// ------------------------------------------------------------------------------------------
+template <class TW, class TAcc, class TH>
+__global__ void k_layer1(const ulonglong2* __restrict__ dets, int64_t M, int norb, int H1,
+                         const TW* __restrict__ W1, const TAcc* __restrict__ b1,
+                         TH* __restrict__ H, TH* __restrict__ X) {
+    const int nin = 2 * norb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M * H1;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = t / H1;
+        int i = (int)(t - m * H1);
+        ulonglong2 x = dets[m];
+        const TW* w = W1 + (int64_t)i * nin;
+        TAcc z = TAcc(0);
+        for (uint64_t v = x.x; v; v &= v - 1) z += Cvt<TW>::to_acc(w[__ffsll((long long)v) - 1]);
+        for (uint64_t v = x.y; v; v &= v - 1)
+            z += Cvt<TW>::to_acc(w[norb + __ffsll((long long)v) - 1]);
+        z = z + b1[i];
+        H[t] = Cvt<TH>::from(act_tanh(z));
+        if (X && i < nin) {
+            uint64_t word = i < norb ? x.x : x.y;
+            int bit = i < norb ? i : i - norb;
+            X[m * nin + i] = Cvt<TH>::from((TAcc)((word >> bit) & 1ull));
+        }
+    }
+}
+
+// X for layers narrower than the input (H1 < 2 norb): a separate fill
+template <class TH, class TAcc>
+__global__ void k_bits(const ulonglong2* __restrict__ dets, int64_t M, int norb, TH* X) {
+    const int nin = 2 * norb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M * nin;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = t / nin;
+        int i = (int)(t - m * nin);
+        ulonglong2 x = dets[m];
+        uint64_t word = i < norb ? x.x : x.y;
+        int bit = i < norb ? i : i - norb;
+        X[t] = Cvt<TH>::from((TAcc)((word >> bit) & 1ull));
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// generic SIMT GEMM C = epi(A B^T) with arbitrary element strides: the FP64 form, and the
+// reference mixed path (BF16 inputs, FP32 accumulation). 64x64 tile, 16-deep k slices.
+// ------------------------------------------------------------------------------------------
+#define GB_M 64
+#define GB_N 64
+#define GB_K 16
+
+template <class TIn, class TAcc, class TOut>
+__global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs g) {
+    __shared__ TAcc As[GB_K][GB_M + 1];
+    __shared__ TAcc Bs[GB_K][GB_N + 1];
+    const TIn* A = (const TIn*)g.A;
+    const TIn* B = (const TIn*)g.B;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * GB_M, n0 = (int64_t)blockIdx.x * GB_N;
+    TAcc acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = TAcc(0);
+    const bool a_kfast = g.a_k == 1, b_kfast = g.b_k == 1;
+    for (int k0 = 0; k0 < g.K; k0 += GB_K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int e = tid + 256 * q;
+            int r, kk;
+            if (a_kfast) {
+                r = e / GB_K;
+                kk = e % GB_K;
+            } else {
+                kk = e / GB_M;
+                r = e % GB_M;
+            }
+            int64_t gm = m0 + r;
+            int gk = k0 + kk;
+            As[kk][r] = (gm < g.M && gk < g.K) ? Cvt<TIn>::to_acc(A[gm * g.a_m + gk * g.a_k])
+                                               : TAcc(0);
+            if (b_kfast) {
+                r = e / GB_K;
+                kk = e % GB_K;
+            } else {
+                kk = e / GB_N;
+                r = e % GB_N;
+            }
+            int64_t gn = n0 + r;
+            gk = k0 + kk;
+            Bs[kk][r] = (gn < g.N && gk < g.K) ? Cvt<TIn>::to_acc(B[gn * g.b_n + gk * g.b_k])
+                                               : TAcc(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GB_K; ++kk) {
+            TAcc a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+    TOut* C = (TOut*)g.C;
+    const TAcc* bias = (const TAcc*)g.bias;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t n = n0 + tx + 16 * j;
+            if (n >= g.N) continue;
+            TAcc v = acc[i][j];
+            if (g.epi == EPI_BIAS_TANH) {
+                TAcc z = v + bias[n];
+                v = act_tanh(z);
+            } else if (g.epi == EPI_BIAS_PHI0) {
+                TAcc z = v + bias[n];
+                v = ((const TAcc*)g.aux)[n] + z;
+            } else if (g.epi == EPI_TANH_BWD) {
+                TAcc h = Cvt<TIn>::to_acc(((const TIn*)g.aux)[m * g.ld_aux + n]);
+                v = v * (TAcc(1) - h * h);
+            }
+            C[m * g.ldc + n] = Cvt<TOut>::from(v);
+        }
+    }
+}
+
+int gemm_f64(const GemmArgs& g, cudaStream_t s) {
+    dim3 grid((g.N + GB_N - 1) / GB_N, (unsigned)((g.M + GB_M - 1) / GB_M));
+    {
+        ProfScope prof_(PROF_GEMM, s);
+        k_gemm_simt<double, double, double><<<grid, 256, 0, s>>>(g);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int gemm_bf16_simt(const GemmArgs& g, bool out_bf16, cudaStream_t s) {
+    dim3 grid((g.N + GB_N - 1) / GB_N, (unsigned)((g.M + GB_M - 1) / GB_M));
+    {
+        ProfScope prof_(PROF_GEMM, s);
+        if (out_bf16) k_gemm_simt<__nv_bfloat16, float, __nv_bfloat16><<<grid, 256, 0, s>>>(g);
+        else k_gemm_simt<__nv_bfloat16, float, float><<<grid, 256, 0, s>>>(g);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+static int gemm_mixed(const GemmArgs& g, bool out_bf16, cudaStream_t s) {
+    int st = gemm_bf16_tc(g, out_bf16, s);
+    if (st != NQS_ERR_UNSUPPORTED) return st;
+    return gemm_bf16_simt(g, out_bf16, s);
+}
+
+// ------------------------------------------------------------------------------------------
+// batched LU: one warp per (det, spin block); the block sits in shared memory. Task t covers
+// det t/2, spin t%2; it writes log|det| and the sign of its block to la2/sg2[spin*M + m] and the
+// block inverse to Ainv (if requested). Pivot: largest |a_ik|, lowest row on ties.
+// ------------------------------------------------------------------------------------------
+#define LU_WARPS 4
+
+template <class T>
+__global__ void __launch_bounds__(LU_WARPS * 32) k_lu(const ulonglong2* __restrict__ dets,
+                                                      int64_t M, int norb, int na, int nb,
+                                                      const T* __restrict__ Phi,
+                                                      double* __restrict__ la2,
+                                                      int8_t* __restrict__ sg2, T* Ainv_a,
+                                                      T* Ainv_b, int* singular) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nmax = na > nb ? na : nb, ld = nmax + 1;
+    T* A = (T*)smem_raw + (size_t)warp * 2 * nmax * ld;
+    T* Xs = A + nmax * ld;
+    __shared__ int perm_s[LU_WARPS][64];
+    __shared__ uint8_t occ_s[LU_WARPS][64];
+    const int nel = na + nb;
+    for (int64_t task = (int64_t)blockIdx.x * LU_WARPS + warp; task < 2 * M;
+         task += (int64_t)gridDim.x * LU_WARPS) {
+        const int64_t m = task >> 1;
+        const int spin = (int)(task & 1);
+        const int n = spin == 0 ? na : nb;
+        const int col0 = spin == 0 ? 0 : na;
+        ulonglong2 x = dets[m];
+        uint64_t w = spin == 0 ? x.x : x.y;
+        for (int p = lane; p < norb; p += 32) {
+            if ((w >> p) & 1ull) {
+                uint64_t below = p == 0 ? 0ull : ((1ull << p) - 1ull);
+                occ_s[warp][__popcll(w & below)] = (uint8_t)p;
+            }
+        }
+        __syncwarp();
+        const T* phi = Phi + m * (int64_t)norb * nel;
+        for (int t = lane; t < n * n; t += 32) {
+            int r = t / n, c = t - r * n;
+            A[r * ld + c] = phi[(int64_t)occ_s[warp][r] * nel + col0 + c];
+        }
+        for (int t = lane; t < n; t += 32) perm_s[warp][t] = t;
+        __syncwarp();
+        int sgn = 1;
+        double la = 0.0;
+        bool sing = false;
+        for (int k = 0; k < n; ++k) {
+            T best = T(-1);
+            int bi = n;
+            for (int i = k + lane; i < n; i += 32) {
+                T v = fabs(A[i * ld + k]);
+                if (v > best) {
+                    best = v;
+                    bi = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                T ob = __shfl_xor_sync(FULL_MASK, best, o);
+                int oi = __shfl_xor_sync(FULL_MASK, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (bi != k) {
+                for (int c = lane; c < n; c += 32) {
+                    T t = A[k * ld + c];
+                    A[k * ld + c] = A[bi * ld + c];
+                    A[bi * ld + c] = t;
+                }
+                if (lane == 0) {
+                    int t = perm_s[warp][k];
+                    perm_s[warp][k] = perm_s[warp][bi];
+                    perm_s[warp][bi] = t;
+                }
+                sgn = -sgn;
+            }
+            __syncwarp();
+            T piv = A[k * ld + k];
+            if (piv == T(0)) {
+                sing = true;
+                break;
+            }
+            if (piv < T(0)) sgn = -sgn;
+            la += log(fabs((double)piv));
+            for (int i = k + 1 + lane; i < n; i += 32) {
+                T l = A[i * ld + k] / piv;
+                A[i * ld + k] = l;
+                for (int j = k + 1; j < n; ++j) A[i * ld + j] -= l * A[k * ld + j];
+            }
+            __syncwarp();
+        }
+        T* Ainv = spin == 0 ? Ainv_a : Ainv_b;
+        if (lane == 0) {
+            la2[spin * M + m] = sing ? -INFINITY : la;
+            sg2[spin * M + m] = (int8_t)(sing ? 0 : sgn);
+            if (sing && singular) atomicOr(singular, 1);
+        }
+        if (Ainv) {
+            if (sing) {
+                for (int t = lane; t < n * n; t += 32) Ainv[m * n * n + t] = T(0);
+            } else {
+                // column c of the inverse: solve L U y = P^T e_c (lane c)
+                for (int c = lane; c < n; c += 32) {
+                    for (int i = 0; i < n; ++i) {
+                        T v = perm_s[warp][i] == c ? T(1) : T(0);
+                        for (int j = 0; j < i; ++j) v -= A[i * ld + j] * Xs[j * ld + c];
+                        Xs[i * ld + c] = v;
+                    }
+                    for (int i = n - 1; i >= 0; --i) {
+                        T v = Xs[i * ld + c];
+                        for (int j = i + 1; j < n; ++j) v -= A[i * ld + j] * Xs[j * ld + c];
+                        Xs[i * ld + c] = v / A[i * ld + i];
+                    }
+                }
+                __syncwarp();
+                for (int t = lane; t < n * n; t += 32) {
+                    int r = t / n, c = t - r * n;
+                    Ainv[m * n * n + t] = Xs[r * ld + c];
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_combine(int64_t M, const double* la2, const int8_t* sg2, double* logabs,
+                          int8_t* sign) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        int s = sg2[m] * sg2[M + m];
+        sign[m] = (int8_t)s;
+        logabs[m] = s == 0 ? -INFINITY : la2[m] + la2[M + m];
+    }
+}
+
+template <class T>
+static int launch_lu(nqs_net* net, const uint64_t* dets, int64_t M, const T* Phi, double* la2,
+                     int8_t* sg2, T* Ainv_a, T* Ainv_b, int* singular, cudaStream_t s) {
+    const ProblemDev& P = net->prob->d;
+    int nmax = P.na > P.nb ? P.na : P.nb;
+    size_t smem = (size_t)LU_WARPS * 2 * nmax * (nmax + 1) * sizeof(T);
+    if (smem > 48 * 1024)
+        NQS_CK(cudaFuncSetAttribute(k_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    unsigned grid = grid_for(2 * M, LU_WARPS, 148 * 64);
+    {
+        ProfScope prof_(PROF_LU, s);
+        k_lu<T><<<grid, LU_WARPS * 32, smem, s>>>((const ulonglong2*)dets, M, P.norb, P.na, P.nb, Phi,
+                                                  la2, sg2, Ainv_a, Ainv_b, singular);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// forward: layer 1 gather, layers 2 and 3 as GEMMs, then the two LU factorisations
+// ------------------------------------------------------------------------------------------
+int net_forward(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t M, Fwd& f,
+                bool keep, double* logabs, int8_t* sign, cudaStream_t s) {
+    const ProblemDev& P = net->prob->d;
+    const bool mixed = net->dtype == NQS_MIXED;
+    const int H1 = net->H1, H2 = net->H2, nin = net->nin, nout = net->nout;
+    const size_t esz = mixed ? 2 : 8;  // activation element size
+    const size_t psz = mixed ? 4 : 8;  // Phi / LU element size
+    memset(&f, 0, sizeof f);
+    f.M = M;
+    f.logabs = logabs;
+    f.sign = sign;
+    NQS_TRY(sc.get((uint8_t**)&f.H1, M * H1 * esz));
+    NQS_TRY(sc.get((uint8_t**)&f.H2, M * H2 * esz));
+    NQS_TRY(sc.get((uint8_t**)&f.Phi, M * nout * psz));
+    if (keep) {
+        NQS_TRY(sc.get((uint8_t**)&f.X, M * nin * esz));
+        NQS_TRY(sc.get((uint8_t**)&f.Ainv_a, M * P.na * P.na * psz));
+        NQS_TRY(sc.get((uint8_t**)&f.Ainv_b, M * P.nb * P.nb * psz));
+    }
+    NQS_TRY(sc.get(&f.singular, 1));
+    NQS_CK(cudaMemsetAsync(f.singular, 0, sizeof(int), s));
+    const ulonglong2* D2 = (const ulonglong2*)dets;
+    unsigned g1 = grid_for(M * H1, 256, 148 * 64);
+    if (mixed) {
+        k_layer1<__nv_bfloat16, float, __nv_bfloat16><<<g1, 256, 0, s>>>(
+            D2, M, P.norb, H1, (const __nv_bfloat16*)net->p[0], (const float*)net->p[1],
+            (__nv_bfloat16*)f.H1, nullptr);
+        NQS_CK_LAUNCH();
+        if (keep) {
+            k_bits<__nv_bfloat16, float><<<grid_for(M * nin, 256), 256, 0, s>>>(
+                D2, M, P.norb, (__nv_bfloat16*)f.X);
+            NQS_CK_LAUNCH();
+        }
+    } else {
+        k_layer1<double, double, double><<<g1, 256, 0, s>>>(D2, M, P.norb, H1,
+                                                            (const double*)net->p[0],
+                                                            (const double*)net->p[1],
+                                                            (double*)f.H1, nullptr);
+        NQS_CK_LAUNCH();
+        if (keep) {
+            k_bits<double, double><<<grid_for(M * nin, 256), 256, 0, s>>>(D2, M, P.norb,
+                                                                         (double*)f.X);
+            NQS_CK_LAUNCH();
+        }
+    }
+    GemmArgs g{};
+    g.M = (int)M;
+    g.N = H2;
+    g.K = H1;
+    g.A = f.H1;
+    g.a_m = H1;
+    g.a_k = 1;
+    g.B = net->p[2];
+    g.b_n = H1;
+    g.b_k = 1;
+    g.C = f.H2;
+    g.ldc = H2;
+    g.epi = EPI_BIAS_TANH;
+    g.bias = net->p[3];
+    NQS_TRY(mixed ? gemm_mixed(g, true, s) : gemm_f64(g, s));
+    g.N = nout;
+    g.K = H2;
+    g.A = f.H2;
+    g.a_m = H2;
+    g.B = net->p[4];
+    g.b_n = H2;
+    g.C = f.Phi;
+    g.ldc = nout;
+    g.epi = EPI_BIAS_PHI0;
+    g.bias = net->p[5];
+    g.aux = net->p[6];
+    NQS_TRY(mixed ? gemm_mixed(g, false, s) : gemm_f64(g, s));
+    double* la2;
+    int8_t* sg2;
+    NQS_TRY(sc.get(&la2, 2 * M));
+    NQS_TRY(sc.get(&sg2, 2 * M));
+    if (mixed)
+        NQS_TRY(launch_lu<float>(net, dets, M, (const float*)f.Phi, la2, sg2, (float*)f.Ainv_a,
+                                 (float*)f.Ainv_b, f.singular, s));
+    else
+        NQS_TRY(launch_lu<double>(net, dets, M, (const double*)f.Phi, la2, sg2,
+                                  (double*)f.Ainv_a, (double*)f.Ainv_b, f.singular, s));
+    k_combine<<<grid_for(M, 256), 256, 0, s>>>(M, la2, sg2, logabs, sign);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// backward (hand-written adjoint)
+//   dPhi(x)[occ_s[j]][col0_s + k] = w_x (A_s^{-1})[k][j]     (Jacobi's formula)
+//   dW3 = dPhi^T H2, db3 = colsum dPhi, dZ2 = (dPhi W3) * (1 - H2^2)
+//   dW2 = dZ2^T H1,  db2 = colsum dZ2,  dZ1 = (dZ2 W2) * (1 - H1^2)
+//   dW1 = dZ1^T X,   db1 = colsum dZ1
+// ------------------------------------------------------------------------------------------
+template <class TG>
+__device__ __forceinline__ TG grad_from_double(double g);
+template <>
+__device__ __forceinline__ double grad_from_double<double>(double g) { return g; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 grad_from_double<__nv_bfloat16>(double g) {
+    return __float2bfloat16_rn((float)g);
+}
+
+template <class T, class TG>
+__global__ void k_adjoint(const ulonglong2* __restrict__ dets, int64_t M, int norb, int na,
+                          int nb, const double* __restrict__ w, const T* __restrict__ Ainv_a,
+                          const T* __restrict__ Ainv_b, TG* __restrict__ dPhi) {
+    const int nel = na + nb;
+    const int per = na * na + nb * nb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M * per;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = t / per;
+        int r = (int)(t - m * per);
+        int spin = r < na * na ? 0 : 1;
+        int n = spin == 0 ? na : nb;
+        if (spin) r -= na * na;
+        int j = r / n, k = r - j * n;  // row j of the block (occupied orbital), column k
+        uint64_t word = spin == 0 ? dets[m].x : dets[m].y;
+        // j-th occupied orbital of word
+        uint64_t v = word;
+        for (int q = 0; q < j; ++q) v &= v - 1;
+        int orb = __ffsll((long long)v) - 1;
+        const T* inv = (spin == 0 ? Ainv_a + m * na * na : Ainv_b + m * nb * nb);
+        double g = w[m] * (double)inv[k * n + j];
+        dPhi[m * (int64_t)norb * nel + (int64_t)orb * nel + (spin == 0 ? 0 : na) + k] =
+            grad_from_double<TG>(g);
+    }
+}
+
+// column sums of X [M][N] into out[N], split over row chunks then combined (deterministic)
+template <class TIn, class TAcc>
+__global__ void k_colsum_part(const TIn* __restrict__ X, int64_t M, int N, int64_t rows_per,
+                              TAcc* __restrict__ part) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    int64_t r0 = (int64_t)blockIdx.y * rows_per, r1 = r0 + rows_per < M ? r0 + rows_per : M;
+    TAcc s = TAcc(0);
+    for (int64_t r = r0; r < r1; ++r) s += Cvt<TIn>::to_acc(X[r * N + n]);
+    part[(int64_t)blockIdx.y * N + n] = s;
+}
+template <class TAcc>
+__global__ void k_colsum_final(const TAcc* __restrict__ part, int splits, int N,
+                               TAcc* __restrict__ out) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    TAcc s = TAcc(0);
+    for (int k = 0; k < splits; ++k) s += part[(int64_t)k * N + n];
+    out[n] = s;
+}
+
+template <class TIn, class TAcc>
+static int colsum(Scratch& sc, const void* X, int64_t M, int N, void* out, cudaStream_t s) {
+    int splits = (int)((M + 1023) / 1024);
+    if (splits > 256) splits = 256;
+    if (splits < 1) splits = 1;
+    int64_t rows_per = (M + splits - 1) / splits;
+    TAcc* part;
+    NQS_TRY(sc.get(&part, (size_t)splits * N));
+    dim3 grid((N + 127) / 128, splits);
+    k_colsum_part<TIn, TAcc><<<grid, 128, 0, s>>>((const TIn*)X, M, N, rows_per, part);
+    NQS_CK_LAUNCH();
+    k_colsum_final<TAcc><<<(N + 127) / 128, 128, 0, s>>>(part, splits, N, (TAcc*)out);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int net_backward(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f, const double* w,
+                 void* grad, cudaStream_t s) {
+    const ProblemDev& P = net->prob->d;
+    const bool mixed = net->dtype == NQS_MIXED;
+    const int64_t M = f.M;
+    const int H1 = net->H1, H2 = net->H2, nin = net->nin, nout = net->nout;
+    const size_t esz = mixed ? 2 : 8, gsz = mixed ? 4 : 8;
+    uint8_t* G = (uint8_t*)grad;
+    uint8_t* gW1 = G;
+    uint8_t* gb1 = gW1 + (size_t)H1 * nin * gsz;
+    uint8_t* gW2 = gb1 + (size_t)H1 * gsz;
+    uint8_t* gb2 = gW2 + (size_t)H2 * H1 * gsz;
+    uint8_t* gW3 = gb2 + (size_t)H2 * gsz;
+    uint8_t* gb3 = gW3 + (size_t)nout * H2 * gsz;
+    void *dPhi, *dZ2, *dZ1;
+    NQS_TRY(sc.get((uint8_t**)&dPhi, M * nout * esz));
+    NQS_TRY(sc.get((uint8_t**)&dZ2, M * H2 * esz));
+    NQS_TRY(sc.get((uint8_t**)&dZ1, M * H1 * esz));
+    NQS_CK(cudaMemsetAsync(dPhi, 0, M * nout * esz, s));
+    int64_t per = (int64_t)P.na * P.na + (int64_t)P.nb * P.nb;
+    const ulonglong2* D2 = (const ulonglong2*)dets;
+    if (mixed)
+        k_adjoint<float, __nv_bfloat16><<<grid_for(M * per, 256, 148 * 64), 256, 0, s>>>(
+            D2, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a, (const float*)f.Ainv_b,
+            (__nv_bfloat16*)dPhi);
+    else
+        k_adjoint<double, double><<<grid_for(M * per, 256, 148 * 64), 256, 0, s>>>(
+            D2, M, P.norb, P.na, P.nb, w, (const double*)f.Ainv_a, (const double*)f.Ainv_b,
+            (double*)dPhi);
+    NQS_CK_LAUNCH();
+    auto gemm = [&](const GemmArgs& g, bool out_act) -> int {
+        return mixed ? gemm_mixed(g, out_act, s) : gemm_f64(g, s);
+    };
+    GemmArgs g{};
+    // dW3[o][k] = sum_m dPhi[m][o] H2[m][k]
+    g.M = nout; g.N = H2; g.K = (int)M;
+    g.A = dPhi; g.a_m = 1; g.a_k = nout;
+    g.B = f.H2; g.b_n = 1; g.b_k = H2;
+    g.C = gW3; g.ldc = H2; g.epi = EPI_STORE;
+    NQS_TRY(gemm(g, false));
+    // dZ2[m][k] = (sum_o dPhi[m][o] W3[o][k]) (1 - H2^2)
+    g = GemmArgs{};
+    g.M = (int)M; g.N = H2; g.K = nout;
+    g.A = dPhi; g.a_m = nout; g.a_k = 1;
+    g.B = net->p[4]; g.b_n = 1; g.b_k = H2;
+    g.C = dZ2; g.ldc = H2; g.epi = EPI_TANH_BWD; g.aux = f.H2; g.ld_aux = H2;
+    NQS_TRY(gemm(g, true));
+    // dW2[i][k] = sum_m dZ2[m][i] H1[m][k]
+    g = GemmArgs{};
+    g.M = H2; g.N = H1; g.K = (int)M;
+    g.A = dZ2; g.a_m = 1; g.a_k = H2;
+    g.B = f.H1; g.b_n = 1; g.b_k = H1;
+    g.C = gW2; g.ldc = H1; g.epi = EPI_STORE;
+    NQS_TRY(gemm(g, false));
+    // dZ1[m][k] = (sum_i dZ2[m][i] W2[i][k]) (1 - H1^2)
+    g = GemmArgs{};
+    g.M = (int)M; g.N = H1; g.K = H2;
+    g.A = dZ2; g.a_m = H2; g.a_k = 1;
+    g.B = net->p[2]; g.b_n = 1; g.b_k = H1;
+    g.C = dZ1; g.ldc = H1; g.epi = EPI_TANH_BWD; g.aux = f.H1; g.ld_aux = H1;
+    NQS_TRY(gemm(g, true));
+    // dW1[i][k] = sum_m dZ1[m][i] X[m][k]
+    g = GemmArgs{};
+    g.M = H1; g.N = nin; g.K = (int)M;
+    g.A = dZ1; g.a_m = 1; g.a_k = H1;
+    g.B = f.X; g.b_n = 1; g.b_k = nin;
+    g.C = gW1; g.ldc = nin; g.epi = EPI_STORE;
+    NQS_TRY(gemm(g, false));
+    if (mixed) {
+        NQS_TRY((colsum<__nv_bfloat16, float>(sc, dPhi, M, nout, gb3, s)));
+        NQS_TRY((colsum<__nv_bfloat16, float>(sc, dZ2, M, H2, gb2, s)));
+        NQS_TRY((colsum<__nv_bfloat16, float>(sc, dZ1, M, H1, gb1, s)));
+    } else {
+        NQS_TRY((colsum<double, double>(sc, dPhi, M, nout, gb3, s)));
+        NQS_TRY((colsum<double, double>(sc, dZ2, M, H2, gb2, s)));
+        NQS_TRY((colsum<double, double>(sc, dZ1, M, H1, gb1, s)));
+    }
+    return NQS_OK;
+}

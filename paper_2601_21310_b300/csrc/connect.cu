@@ -1,0 +1,177 @@
+// H_SS construction (Sec. 3.1 combinatorial kernel, Eq. connected_set, Algorithm 1 step 1):
+// every single and double excitation of every det of S is enumerated in canonical order,
+// looked up in S through an open-addressing hash table, and the hits become CSR entries.
+//
+// One warp per det. Pass 1 counts the hits of each row; an exclusive scan gives row_ptr;
+// pass 2 re-enumerates in rounds of 32 canonical indices and compacts the hits with a warp
+// ballot, so each row is written in canonical order without any sort. The matrix element is
+// computed only for hits.
+#include <stdlib.h>
+#include <string.h>
+
+#include "excite.cuh"
+#include "nqs_internal.cuh"
+#include "prof.cuh"
+
+#define CONN_THREADS 256
+#define CONN_WARPS (CONN_THREADS / 32)
+
+__global__ void __launch_bounds__(CONN_THREADS) k_conn_count(ProblemDev P, HashS H,
+                                                              const ulonglong2* __restrict__ S,
+                                                              int64_t nS, int64_t* rowcnt) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nexc = (uint32_t)P.nexc;
+    for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * CONN_WARPS) {
+        ulonglong2 x = S[det];
+        fill_ctx(P, x.x, x.y, ctx, lane);
+        int cnt = 0;
+        for (uint32_t e = lane; e < nexc; e += 32) {
+            uint64_t a2, b2;
+            decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+            cnt += hash_lookup(H, a2, b2) >= 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
+        if (lane == 0) rowcnt[det] = cnt + 1;  // + diagonal
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(CONN_THREADS) k_conn_fill(ProblemDev P, HashS H,
+                                                             const ulonglong2* __restrict__ S,
+                                                             int64_t nS,
+                                                             const int64_t* __restrict__ row_ptr,
+                                                             int32_t* __restrict__ col,
+                                                             double* __restrict__ val) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const uint32_t nexc = (uint32_t)P.nexc;
+    for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * CONN_WARPS) {
+        ulonglong2 x = S[det];
+        fill_ctx(P, x.x, x.y, ctx, lane);
+        const int64_t base = row_ptr[det];
+        if (lane == 0) {
+            col[base] = (int32_t)det;
+            val[base] = diag_element_impl(P, x.x, x.y);
+        }
+        int64_t run = base + 1;
+        for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
+            uint32_t e = r0 + lane;
+            int32_t hit = -1;
+            Exc ex;
+            if (e < nexc) {
+                decode_exc(P, T, *ctx, x.x, x.y, e, ex);
+                hit = hash_lookup(H, ex.a2, ex.b2);
+            }
+            unsigned m = __ballot_sync(FULL_MASK, hit >= 0);
+            if (hit >= 0) {
+                int64_t pos = run + __popc(m & lt);
+                col[pos] = hit;
+                val[pos] = exc_element(P, *ctx, ex);
+            }
+            run += __popc(m);
+        }
+        __syncwarp();
+    }
+}
+
+static size_t conn_smem(const ProblemDev& P) {
+    return pair_table_bytes(P) + CONN_WARPS * sizeof(DetCtx);
+}
+
+static unsigned conn_grid(int64_t nS) {
+    int64_t g = (nS + CONN_WARPS - 1) / CONN_WARPS;
+    if (g > 148 * 16) g = 148 * 16;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
+                               const nqs_opts* opts, nqs_csr* out, int64_t* n_enumerated,
+                               nqs_stream_t stream) {
+    if (!p || !out || nS <= 0 || !dets) return NQS_ERR_ARG;
+    if (nS >= ((int64_t)1 << 31)) return NQS_ERR_UNSUPPORTED;
+    if (((uintptr_t)dets) & 15) return NQS_ERR_ARG;
+    memset(out, 0, sizeof *out);
+    cudaStream_t s = (cudaStream_t)stream;
+    nqs_opts def;
+    if (!opts) {
+        nqs_opts_default(&def);
+        opts = &def;
+    }
+    Scratch sc(p, s);
+    if (opts->validate) NQS_TRY(validate_dets(p, sc, dets, nS, true, s));
+    HashS H;
+    NQS_TRY(hash_build(p, sc, dets, nS, &H, s));
+    size_t smem = conn_smem(p->d);
+    if (smem > 48 * 1024) {
+        NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_conn_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    }
+    int64_t* rowcnt;
+    NQS_TRY(sc.get(&rowcnt, nS));
+    int64_t* row_ptr = nullptr;
+    NQS_CK(cudaMalloc(&row_ptr, (nS + 1) * sizeof(int64_t)));
+    auto fail = [&](int code) {
+        cudaFree(row_ptr);
+        return code;
+    };
+    {
+        ProfScope prof_(PROF_CONN_COUNT, s);
+        k_conn_count<<<conn_grid(nS), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)dets, nS,
+                                                               rowcnt);
+    }
+    nqs_note_launch();
+    if (cudaGetLastError() != cudaSuccess) return fail(NQS_ERR_CUDA);
+    int st = scan_exclusive_i64(p, sc, rowcnt, row_ptr, nS, row_ptr + nS, s);
+    if (st < 0) return fail(st);
+    int64_t nnz = 0;
+    if (cudaMemcpyAsync(&nnz, row_ptr + nS, sizeof nnz, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(NQS_ERR_CUDA);
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    if (cudaMalloc(&col, nnz * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&val, nnz * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(col);
+        return fail(NQS_ERR_OOM);
+    }
+    {
+        ProfScope prof_(PROF_CONN_FILL, s);
+        k_conn_fill<<<conn_grid(nS), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)dets, nS,
+                                                              row_ptr, col, val);
+    }
+    nqs_note_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+        cudaFree(col);
+        cudaFree(val);
+        return fail(NQS_ERR_CUDA);
+    }
+    out->row_ptr = row_ptr;
+    out->col = col;
+    out->val = val;
+    out->nnz = nnz;
+    out->n_rows = nS;
+    if (n_enumerated) *n_enumerated = nS * p->d.nexc;
+    return NQS_OK;
+}
+
+extern "C" int nqs_csr_free(nqs_csr* csr) {
+    if (!csr) return NQS_ERR_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(csr->row_ptr);
+    cudaFree(csr->col);
+    cudaFree(csr->val);
+    memset(csr, 0, sizeof *csr);
+    return NQS_OK;
+}

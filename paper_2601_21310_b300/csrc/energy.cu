@@ -1,0 +1,171 @@
+// E_S and its gradient (Eqs. variational_energy, variational_gradient; Algorithm 1 step 2),
+// the device SpMV v = H_SS psi (the paper's host-resident SciPy SpMV, moved on-device), the
+// amplitude entry point and the network handle.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "ansatz.cuh"
+#include "excite.cuh"
+#include "nqs_internal.cuh"
+#include "prof.cuh"
+
+// one warp per row, FP64 (lanes stride the row, then a shuffle tree)
+__global__ void k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, const double* __restrict__ x, int64_t n,
+                       double* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        double s = 0.0;
+        for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s = fma(val[k], x[col[k]], s);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+        if (lane == 0) y[r] = s;
+    }
+}
+
+// psi~ = sign * exp(log|psi| - max log|psi|)
+__global__ void k_scaled_psi(const double* __restrict__ logabs, const int8_t* __restrict__ sign,
+                             const double* __restrict__ maxlog, int64_t n,
+                             double* __restrict__ psi) {
+    const double M = *maxlog;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        psi[i] = sign[i] == 0 ? 0.0 : (double)sign[i] * exp(logabs[i] - M);
+}
+
+__global__ void k_energy(double* out) { out[0] = out[1] / out[2]; }
+
+// w_x = (2/D) (v_x - E psi~_x) psi~_x
+__global__ void k_adjoint_weight(const double* __restrict__ v, const double* __restrict__ psi,
+                                 const double* __restrict__ ev, int64_t n, double* __restrict__ w) {
+    const double E = ev[0], D = ev[2];
+    const double c = __ddiv_rn(2.0, D);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = __dmul_rn(__dmul_rn(c, __dsub_rn(v[i], __dmul_rn(E, psi[i]))), psi[i]);
+}
+
+static int spmv(const nqs_csr* csr, const double* x, double* y, cudaStream_t s) {
+    int64_t n = csr->n_rows;
+    {
+        ProfScope prof_(PROF_SPMV, s);
+        k_spmv<<<grid_for(n * 32, 256, 148 * 64), 256, 0, s>>>(csr->row_ptr, csr->col, csr->val, x, n,
+                                                               y);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+extern "C" int nqs_energy_from_psi(const nqs_csr* csr, const double* psi, int64_t nS, double* out,
+                                   double* v, nqs_stream_t stream) {
+    if (!csr || !psi || !out || nS <= 0 || csr->n_rows != nS) return NQS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // no problem handle here: scratch comes from the device's default stream-ordered pool
+    nqs_problem host;
+    memset(&host, 0, sizeof host);
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    NQS_CK(cudaDeviceGetDefaultMemPool(&host.pool, dev));
+    Scratch sc(&host, s);
+    double* vv = v;
+    if (!vv) NQS_TRY(sc.get(&vv, nS));
+    NQS_TRY(spmv(csr, psi, vv, s));
+    NQS_TRY(kdot2_f64(&host, sc, vv, psi, nS, out + 1, s));
+    k_energy<<<1, 1, 0, s>>>(out);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// network handle
+// ------------------------------------------------------------------------------------------
+extern "C" int nqs_net_create(nqs_problem* p, int H1, int H2, int dtype,
+                              const void* const* params, nqs_net** out) {
+    if (!p || !params || !out || H1 <= 0 || H2 <= 0) return NQS_ERR_ARG;
+    if (dtype != NQS_FP64 && dtype != NQS_MIXED) return NQS_ERR_ARG;
+    for (int i = 0; i < 7; ++i)
+        if (!params[i]) return NQS_ERR_ARG;
+    nqs_net* n = (nqs_net*)calloc(1, sizeof(nqs_net));
+    if (!n) return NQS_ERR_OOM;
+    n->prob = p;
+    n->H1 = H1;
+    n->H2 = H2;
+    n->nin = 2 * p->d.norb;
+    n->nout = p->d.norb * (p->d.na + p->d.nb);
+    n->dtype = dtype;
+    for (int i = 0; i < 7; ++i) n->p[i] = params[i];
+    *out = n;
+    return NQS_OK;
+}
+
+extern "C" int nqs_net_destroy(nqs_net* n) {
+    free(n);
+    return NQS_OK;
+}
+
+extern "C" int64_t nqs_net_num_params(const nqs_net* n) {
+    if (!n) return 0;
+    return (int64_t)n->H1 * n->nin + n->H1 + (int64_t)n->H2 * n->H1 + n->H2 +
+           (int64_t)n->nout * n->H2 + n->nout;
+}
+
+static int check_common(nqs_problem* p, nqs_net* net, const uint64_t* dets, int64_t nS,
+                        const nqs_opts* opts) {
+    if (!p || !net || !dets || nS <= 0 || net->prob != p) return NQS_ERR_ARG;
+    if (((uintptr_t)dets) & 15) return NQS_ERR_ARG;
+    if (nS >= ((int64_t)1 << 31)) return NQS_ERR_UNSUPPORTED;
+    if (opts && opts->precision != net->dtype) return NQS_ERR_ARG;
+    return NQS_OK;
+}
+
+extern "C" int nqs_amplitudes(nqs_problem* p, nqs_net* net, const uint64_t* dets, int64_t nS,
+                              double* logabs, int8_t* sign, const nqs_opts* opts,
+                              nqs_stream_t stream) {
+    NQS_TRY(check_common(p, net, dets, nS, opts));
+    if (!logabs || !sign) return NQS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(p, s);
+    if (opts && opts->validate) NQS_TRY(validate_dets(p, sc, dets, nS, false, s));
+    Fwd f;
+    NQS_TRY(net_forward(net, sc, dets, nS, f, false, logabs, sign, s));
+    int sing = 0;
+    NQS_CK(cudaMemcpyAsync(&sing, f.singular, sizeof sing, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    return sing ? NQS_WARN_SINGULAR : NQS_OK;
+}
+
+extern "C" int nqs_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr* csr,
+                               const uint64_t* dets, int64_t nS, double* out, void* grad,
+                               double* psi_out, const nqs_opts* opts, nqs_stream_t stream) {
+    NQS_TRY(check_common(p, net, dets, nS, opts));
+    if (!csr || !out || csr->n_rows != nS) return NQS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(p, s);
+    if (opts && opts->validate) NQS_TRY(validate_dets(p, sc, dets, nS, true, s));
+    double *logabs, *psi, *v;
+    int8_t* sign;
+    NQS_TRY(sc.get(&logabs, nS));
+    NQS_TRY(sc.get(&sign, nS));
+    NQS_TRY(sc.get(&v, nS));
+    psi = psi_out;
+    if (!psi) NQS_TRY(sc.get(&psi, nS));
+    Fwd f;
+    NQS_TRY(net_forward(net, sc, dets, nS, f, grad != nullptr, logabs, sign, s));
+    NQS_TRY(max_f64_masked(p, sc, logabs, sign, nS, out + 3, s));
+    k_scaled_psi<<<grid_for(nS, 256), 256, 0, s>>>(logabs, sign, out + 3, nS, psi);
+    NQS_CK_LAUNCH();
+    NQS_TRY(spmv(csr, psi, v, s));
+    NQS_TRY(kdot2_f64(p, sc, v, psi, nS, out + 1, s));
+    k_energy<<<1, 1, 0, s>>>(out);
+    NQS_CK_LAUNCH();
+    if (grad) {
+        double* w;
+        NQS_TRY(sc.get(&w, nS));
+        k_adjoint_weight<<<grid_for(nS, 256), 256, 0, s>>>(v, psi, out, nS, w);
+        NQS_CK_LAUNCH();
+        NQS_TRY(net_backward(net, sc, dets, f, w, grad, s));
+    }
+    return NQS_OK;
+}

@@ -1,0 +1,284 @@
+// Device-side Slater-Condon machinery: per-det occupation lists, decoding of the canonical
+// excitation index, excitation signs, matrix elements and the diagonal element.
+//
+// Canonical excitation order of one det (class offsets in ProblemDev):
+//   class 0  alpha singles       i in occ_a asc, a in vir_a asc
+//   class 1  beta singles        same for beta
+//   class 2  alpha-alpha doubles hole pair (i<j) lexicographic, then particle pair (a<b)
+//   class 3  beta-beta doubles
+//   class 4  alpha-beta doubles  (i_a, a_a) single index major, (j_b, b_b) minor, b fastest
+// The matrix-element summation order below is the library's canonical order; it makes H_SS
+// symmetric bit for bit (the same terms are added in the same order from either side).
+#pragma once
+#include "nqs_internal.cuh"
+
+#define FULL_MASK 0xffffffffu
+
+// per-warp occupation lists of the det being processed
+struct DetCtx {
+    uint8_t occA[64];
+    uint8_t virA[64];
+    uint8_t occB[64];
+    uint8_t virB[64];
+};
+
+// pair tables (shared by all warps of a CTA): entry = lo | hi << 8, lo < hi, lexicographic
+struct PairTables {
+    const uint16_t* occA;
+    const uint16_t* virA;
+    const uint16_t* occB;
+    const uint16_t* virB;
+};
+
+__host__ __device__ __forceinline__ int64_t choose2(int64_t n) { return n * (n - 1) / 2; }
+
+// shared-memory bytes needed for the pair tables of a problem (16-byte rounded)
+__host__ __device__ __forceinline__ size_t pair_table_bytes(const ProblemDev& P) {
+    size_t n = choose2(P.na) + choose2(P.ma) + choose2(P.nb) + choose2(P.mb);
+    return (n * sizeof(uint16_t) + 15) & ~(size_t)15;
+}
+
+// fill the pair tables cooperatively (whole CTA), then __syncthreads()
+__device__ __forceinline__ PairTables setup_pair_tables(const ProblemDev& P, uint16_t* base) {
+    PairTables T;
+    T.occA = base;
+    T.virA = T.occA + choose2(P.na);
+    T.occB = T.virA + choose2(P.ma);
+    T.virB = T.occB + choose2(P.nb);
+    int sizes[4] = {P.na, P.ma, P.nb, P.mb};
+    uint16_t* outs[4] = {(uint16_t*)T.occA, (uint16_t*)T.virA, (uint16_t*)T.occB,
+                         (uint16_t*)T.virB};
+    for (int t = 0; t < 4; ++t) {
+        int n = sizes[t];
+        int total = (int)choose2(n);
+        for (int k = threadIdx.x; k < total; k += blockDim.x) {
+            // invert k = lo*(2n-lo-1)/2 + (hi-lo-1) by walking rows (n <= 64)
+            int lo = 0, rem = k;
+            while (rem >= n - 1 - lo) {
+                rem -= n - 1 - lo;
+                ++lo;
+            }
+            int hi = lo + 1 + rem;
+            outs[t][k] = (uint16_t)(lo | (hi << 8));
+        }
+    }
+    __syncthreads();
+    return T;
+}
+
+// lane-parallel construction of the occupation lists of det (A, B); ends with __syncwarp
+__device__ __forceinline__ void fill_ctx(const ProblemDev& P, uint64_t A, uint64_t B, DetCtx* c,
+                                         int lane) {
+    for (int p = lane; p < P.norb; p += 32) {
+        uint64_t below = (p == 0) ? 0ull : ((1ull << p) - 1ull);
+        int ka = __popcll(A & below), kb = __popcll(B & below);
+        if ((A >> p) & 1ull) c->occA[ka] = (uint8_t)p;
+        else c->virA[p - ka] = (uint8_t)p;
+        if ((B >> p) & 1ull) c->occB[kb] = (uint8_t)p;
+        else c->virB[p - kb] = (uint8_t)p;
+    }
+    __syncwarp();
+}
+
+struct Exc {
+    uint64_t a2, b2;  // the excited det
+    int cls;          // 0..4
+    int i, a, j, b;   // holes i(, j) and particles a(, b); j, b unused for singles
+    int sign;         // +1 / -1
+};
+
+// decode canonical index e (< P.nexc) of det (A, B)
+__device__ __forceinline__ void decode_exc(const ProblemDev& P, const PairTables& T,
+                                           const DetCtx& c, uint64_t A, uint64_t B, uint32_t e,
+                                           Exc& x) {
+    const uint32_t o1 = (uint32_t)P.sA, o2 = o1 + (uint32_t)P.sB, o3 = o2 + (uint32_t)P.dAA,
+                   o4 = o3 + (uint32_t)P.dBB;
+    if (e < o2) {
+        bool alpha = e < o1;
+        uint32_t l = alpha ? e : e - o1;
+        uint32_t m = alpha ? P.ma : P.mb;
+        uint32_t xo = l / m, yv = l - xo * m;
+        int i = alpha ? c.occA[xo] : c.occB[xo];
+        int a = alpha ? c.virA[yv] : c.virB[yv];
+        uint64_t w = alpha ? A : B;
+        uint64_t w2 = w ^ (1ull << i) ^ (1ull << a);
+        x.cls = alpha ? 0 : 1;
+        x.i = i;
+        x.a = a;
+        x.j = -1;
+        x.b = -1;
+        x.sign = exc_sign(w, i, a);
+        x.a2 = alpha ? w2 : A;
+        x.b2 = alpha ? B : w2;
+    } else if (e < o4) {
+        bool alpha = e < o3;
+        uint32_t l = alpha ? e - o2 : e - o3;
+        uint32_t Q = (uint32_t)(alpha ? choose2(P.ma) : choose2(P.mb));
+        uint32_t pi = l / Q, qi = l - pi * Q;
+        uint16_t po = alpha ? T.occA[pi] : T.occB[pi];
+        uint16_t pv = alpha ? T.virA[qi] : T.virB[qi];
+        const uint8_t* occ = alpha ? c.occA : c.occB;
+        const uint8_t* vir = alpha ? c.virA : c.virB;
+        int i = occ[po & 0xff], j = occ[po >> 8];
+        int a = vir[pv & 0xff], b = vir[pv >> 8];
+        uint64_t w = alpha ? A : B;
+        int s1 = exc_sign(w, i, a);
+        uint64_t w1 = w ^ (1ull << i) ^ (1ull << a);
+        int s2 = exc_sign(w1, j, b);
+        uint64_t w2 = w1 ^ (1ull << j) ^ (1ull << b);
+        x.cls = alpha ? 2 : 3;
+        x.i = i;
+        x.j = j;
+        x.a = a;
+        x.b = b;
+        x.sign = s1 * s2;
+        x.a2 = alpha ? w2 : A;
+        x.b2 = alpha ? B : w2;
+    } else {
+        uint32_t l = e - o4;
+        uint32_t sB = (uint32_t)P.sB;
+        uint32_t la = l / sB, lb = l - la * sB;
+        uint32_t xa = la / P.ma, ya = la - xa * P.ma;
+        uint32_t xb = lb / P.mb, yb = lb - xb * P.mb;
+        int i = c.occA[xa], a = c.virA[ya], j = c.occB[xb], b = c.virB[yb];
+        x.cls = 4;
+        x.i = i;
+        x.a = a;
+        x.j = j;
+        x.b = b;
+        x.sign = exc_sign(A, i, a) * exc_sign(B, j, b);
+        x.a2 = A ^ (1ull << i) ^ (1ull << a);
+        x.b2 = B ^ (1ull << j) ^ (1ull << b);
+    }
+}
+
+// only the excited det (cheaper than decode_exc when the element is not needed)
+__device__ __forceinline__ void decode_key(const ProblemDev& P, const PairTables& T,
+                                           const DetCtx& c, uint64_t A, uint64_t B, uint32_t e,
+                                           uint64_t& a2, uint64_t& b2) {
+    const uint32_t o1 = (uint32_t)P.sA, o2 = o1 + (uint32_t)P.sB, o3 = o2 + (uint32_t)P.dAA,
+                   o4 = o3 + (uint32_t)P.dBB;
+    if (e < o2) {
+        bool alpha = e < o1;
+        uint32_t l = alpha ? e : e - o1;
+        uint32_t m = alpha ? P.ma : P.mb;
+        uint32_t xo = l / m, yv = l - xo * m;
+        int i = alpha ? c.occA[xo] : c.occB[xo];
+        int a = alpha ? c.virA[yv] : c.virB[yv];
+        uint64_t f = (1ull << i) ^ (1ull << a);
+        a2 = alpha ? A ^ f : A;
+        b2 = alpha ? B : B ^ f;
+    } else if (e < o4) {
+        bool alpha = e < o3;
+        uint32_t l = alpha ? e - o2 : e - o3;
+        uint32_t Q = (uint32_t)(alpha ? choose2(P.ma) : choose2(P.mb));
+        uint32_t pi = l / Q, qi = l - pi * Q;
+        uint16_t po = alpha ? T.occA[pi] : T.occB[pi];
+        uint16_t pv = alpha ? T.virA[qi] : T.virB[qi];
+        const uint8_t* occ = alpha ? c.occA : c.occB;
+        const uint8_t* vir = alpha ? c.virA : c.virB;
+        uint64_t f = (1ull << occ[po & 0xff]) ^ (1ull << occ[po >> 8]) ^ (1ull << vir[pv & 0xff]) ^
+                     (1ull << vir[pv >> 8]);
+        a2 = alpha ? A ^ f : A;
+        b2 = alpha ? B : B ^ f;
+    } else {
+        uint32_t l = e - o4;
+        uint32_t sB = (uint32_t)P.sB;
+        uint32_t la = l / sB, lb = l - la * sB;
+        uint32_t xa = la / P.ma, ya = la - xa * P.ma;
+        uint32_t xb = lb / P.mb, yb = lb - xb * P.mb;
+        a2 = A ^ (1ull << c.occA[xa]) ^ (1ull << c.virA[ya]);
+        b2 = B ^ (1ull << c.occB[xb]) ^ (1ull << c.virB[yb]);
+    }
+}
+
+__device__ __forceinline__ double eri_at(const ProblemDev& P, int p, int q, int r, int s) {
+    const int n = P.norb;
+    return __ldg(&P.eri[(((size_t)p * n + q) * n + r) * n + s]);
+}
+
+// <x'|H|x> for the decoded excitation x of det with occupation lists c.
+//   single i->a of spin s: h_ia + sum_{j in occ_a, j != i (if s=a)} t_a(j)
+//                               + sum_{j in occ_b, j != i (if s=b)} t_b(j),
+//     t(j) = (ia|jj) - (ij|ja) for j of spin s, (ia|jj) otherwise (ascending j, alpha first);
+//   same-spin double: (ia|jb) - (ib|ja); alpha-beta double: (ia|jb); times the sign.
+__device__ __forceinline__ double exc_element(const ProblemDev& P, const DetCtx& c, const Exc& x) {
+    double v;
+    const int n = P.norb;
+    if (x.cls <= 1) {
+        const size_t base = ((size_t)x.i * n + x.a) * n;
+        v = __ldg(&P.h[x.i * n + x.a]);
+        const bool alpha = x.cls == 0;
+        for (int k = 0; k < P.na; ++k) {
+            int j = c.occA[k];
+            if (alpha) {
+                if (j == x.i) continue;
+                double t = __ldg(&P.TJ[base + j]) - __ldg(&P.TK[base + j]);
+                v = v + t;
+            } else {
+                v = v + __ldg(&P.TJ[base + j]);
+            }
+        }
+        for (int k = 0; k < P.nb; ++k) {
+            int j = c.occB[k];
+            if (!alpha) {
+                if (j == x.i) continue;
+                double t = __ldg(&P.TJ[base + j]) - __ldg(&P.TK[base + j]);
+                v = v + t;
+            } else {
+                v = v + __ldg(&P.TJ[base + j]);
+            }
+        }
+    } else if (x.cls <= 3) {
+        // (ib|ja) read as (ja|ib): equal bit for bit under the eightfold symmetry
+        v = eri_at(P, x.i, x.a, x.j, x.b) - eri_at(P, x.j, x.a, x.i, x.b);
+    } else {
+        v = eri_at(P, x.i, x.a, x.j, x.b);
+    }
+    return x.sign < 0 ? -v : v;
+}
+
+// H_xx: sum_{occ} h_ii + sum_{i<j same spin} [J_ij - K_ij] + sum_{i alpha, j beta} J_ij, in the
+// order alpha h, beta h, alpha pairs, beta pairs, alpha-beta pairs (one running sum).
+__device__ __forceinline__ double diag_element_impl(const ProblemDev& P, uint64_t a, uint64_t b) {
+    const int n = P.norb;
+    double e = 0.0;
+    for (uint64_t w = a; w; w &= w - 1) {
+        int i = __ffsll((long long)w) - 1;
+        e = e + __ldg(&P.h[i * n + i]);
+    }
+    for (uint64_t w = b; w; w &= w - 1) {
+        int i = __ffsll((long long)w) - 1;
+        e = e + __ldg(&P.h[i * n + i]);
+    }
+    for (uint64_t wi = a; wi; wi &= wi - 1) {
+        int i = __ffsll((long long)wi) - 1;
+        for (uint64_t wj = wi & (wi - 1); wj; wj &= wj - 1) {
+            int j = __ffsll((long long)wj) - 1;
+            double t = __ldg(&P.J[i * n + j]) - __ldg(&P.K[i * n + j]);
+            e = e + t;
+        }
+    }
+    for (uint64_t wi = b; wi; wi &= wi - 1) {
+        int i = __ffsll((long long)wi) - 1;
+        for (uint64_t wj = wi & (wi - 1); wj; wj &= wj - 1) {
+            int j = __ffsll((long long)wj) - 1;
+            double t = __ldg(&P.J[i * n + j]) - __ldg(&P.K[i * n + j]);
+            e = e + t;
+        }
+    }
+    for (uint64_t wi = a; wi; wi &= wi - 1) {
+        int i = __ffsll((long long)wi) - 1;
+        for (uint64_t wj = b; wj; wj &= wj - 1) {
+            int j = __ffsll((long long)wj) - 1;
+            e = e + __ldg(&P.J[i * n + j]);
+        }
+    }
+    return e;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}

@@ -1,0 +1,175 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/nqs.h"
+
+#define NQS_MAX_NORB 64
+
+// ------------------------------------------------------------------------------------------
+// error plumbing: every CUDA call is checked; a failure records a message and returns a code
+// ------------------------------------------------------------------------------------------
+void nqs_record_error(const char* what, cudaError_t e, const char* file, int line);
+
+#define NQS_CK(call)                                                            \
+    do {                                                                        \
+        cudaError_t e_ = (call);                                                \
+        if (e_ != cudaSuccess) {                                                \
+            nqs_record_error(#call, e_, __FILE__, __LINE__);                    \
+            return (e_ == cudaErrorMemoryAllocation) ? NQS_ERR_OOM : NQS_ERR_CUDA; \
+        }                                                                       \
+    } while (0)
+
+// every kernel launch is followed by NQS_CK_LAUNCH, which also counts it (nqs_launch_count)
+void nqs_note_launch();
+#define NQS_CK_LAUNCH()              \
+    do {                             \
+        nqs_note_launch();           \
+        NQS_CK(cudaGetLastError());  \
+    } while (0)
+
+#define NQS_TRY(expr)            \
+    do {                         \
+        int s_ = (expr);         \
+        if (s_ < 0) return s_;   \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+// problem handle
+// ------------------------------------------------------------------------------------------
+struct ProblemDev {
+    int norb, na, nb, ma, mb;
+    int64_t sA, sB, dAA, dBB, dAB;  // class sizes of the canonical excitation list
+    int64_t nexc;                   // excitations per det
+    const double* h;                // [norb][norb]
+    const double* eri;              // [norb]^4
+    const double* J;                // J[p][q] = (pp|qq)
+    const double* K;                // K[p][q] = (pq|qp)
+    const double* TJ;               // TJ[(i*norb+a)*norb+j] = (ia|jj)
+    const double* TK;               // TK[(i*norb+a)*norb+j] = (ij|ja)
+};
+
+struct nqs_problem {
+    ProblemDev d;
+    int device;
+    double ecore;
+    double *h, *eri, *J, *K, *TJ, *TK;
+    cudaMemPool_t pool;  // library-owned stream-ordered pool for per-call scratch
+};
+
+struct nqs_net {
+    nqs_problem* prob;
+    int H1, H2, nin, nout, dtype;
+    const void* p[7];    // W1, b1, W2, b2, W3, b3, Phi0 (caller-owned device pointers)
+};
+
+// stream-ordered scratch from the problem's pool
+int nqs_scratch_alloc(nqs_problem* p, void** ptr, size_t bytes, cudaStream_t s);
+void nqs_scratch_free(nqs_problem* p, void* ptr, cudaStream_t s);
+
+// RAII holder for scratch so that every early return frees what it took
+struct Scratch {
+    nqs_problem* p;
+    cudaStream_t s;
+    void* ptrs[64];
+    int n = 0;
+    Scratch(nqs_problem* p_, cudaStream_t s_) : p(p_), s(s_) {}
+    ~Scratch() {
+        for (int i = n - 1; i >= 0; --i) nqs_scratch_free(p, ptrs[i], s);
+    }
+    template <class T>
+    int get(T** out, size_t count) {
+        void* v = nullptr;
+        if (count == 0) count = 1;
+        int st = nqs_scratch_alloc(p, &v, count * sizeof(T), s);
+        if (st != NQS_OK) return st;
+        if (n == 64) { nqs_scratch_free(p, v, s); return NQS_ERR_OOM; }
+        ptrs[n++] = v;
+        *out = (T*)v;
+        return NQS_OK;
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+// device helpers: bit strings
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t bits_between(int p, int q) {
+    int lo = min(p, q), hi = max(p, q);
+    uint64_t below_hi = (hi >= 64) ? ~0ull : ((1ull << hi) - 1ull);
+    uint64_t upto_lo = (lo + 1 >= 64) ? ~0ull : ((1ull << (lo + 1)) - 1ull);
+    return below_hi & ~upto_lo;
+}
+// (-1)^(occupied orbitals of w strictly between i and a), as +1 / -1
+__device__ __forceinline__ int exc_sign(uint64_t w, int i, int a) {
+    return (__popcll(w & bits_between(i, a)) & 1) ? -1 : 1;
+}
+
+// SplitMix64 output finaliser (Steele, Lea, Flood, OOPSLA 2014); bucket and hash function
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t det_hash(uint64_t a, uint64_t b) {
+    return mix64(mix64(a) ^ b);
+}
+
+// ------------------------------------------------------------------------------------------
+// hash table of S: open addressing, linear probing, capacity a power of two >= 2|S|
+// ------------------------------------------------------------------------------------------
+#define NQS_EMPTY_WORD 0xffffffffffffffffull
+struct HashS {
+    const ulonglong2* keys;  // [cap] {a, b}; a == NQS_EMPTY_WORD marks an empty slot
+    const int32_t* idx;      // [cap] position in S
+    uint64_t mask;           // cap - 1
+};
+
+__device__ __forceinline__ int32_t hash_lookup(const HashS& H, uint64_t a, uint64_t b) {
+    uint64_t slot = det_hash(a, b) & H.mask;
+    for (uint64_t it = 0; it <= H.mask; ++it) {
+        ulonglong2 k = __ldg(&H.keys[slot]);
+        if (k.x == a && k.y == b) return __ldg(&H.idx[slot]);
+        if (k.x == NQS_EMPTY_WORD) return -1;
+        slot = (slot + 1) & H.mask;
+    }
+    return -1;
+}
+
+int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, HashS* out,
+               cudaStream_t s);
+int validate_dets(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, bool sorted,
+                  cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// primitives (primitives.cu)
+// ------------------------------------------------------------------------------------------
+// exclusive prefix sum of n values; total (device, may be null) receives the sum
+int scan_exclusive_i64(nqs_problem* p, Scratch& sc, const int64_t* in, int64_t* out, int64_t n,
+                       int64_t* total, cudaStream_t s);
+int scan_exclusive_u32(nqs_problem* p, Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n,
+                       cudaStream_t s);
+// compensated (Neumaier) sum of n FP64 values into *out (device); deterministic
+int ksum_f64(nqs_problem* p, Scratch& sc, const double* x, int64_t n, double* out,
+             cudaStream_t s);
+// compensated dot products: out[0] = sum x*y, out[1] = sum y*y
+int kdot2_f64(nqs_problem* p, Scratch& sc, const double* x, const double* y, int64_t n,
+              double* out, cudaStream_t s);
+// max of n FP64 values (ignoring entries whose mask byte is 0)
+int max_f64_masked(nqs_problem* p, Scratch& sc, const double* x, const int8_t* mask, int64_t n,
+                   double* out, cudaStream_t s);
+// stable LSD radix sort of (u64 key, f64 value) pairs on the low `bits` key bits.
+// Result ends in (keys, vals); (keys_alt, vals_alt) are scratch of the same size.
+// The pointers are swapped in place so that (keys, vals) name the sorted result on return.
+int radix_sort_pairs(nqs_problem* p, Scratch& sc, uint64_t*& keys, double*& vals,
+                     uint64_t*& keys_alt, double*& vals_alt, int64_t n, int bits, cudaStream_t s);
+
+inline unsigned grid_for(int64_t n, int block, int cap = 148 * 32) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}

@@ -1,0 +1,345 @@
+// Device primitives: exclusive scans, compensated FP64 reductions, masked max and a stable
+// LSD radix sort of (u64 key, f64 value) pairs. All are deterministic for a given input size.
+#include "excite.cuh"
+#include "nqs_internal.cuh"
+#include "prof.cuh"
+
+// ------------------------------------------------------------------------------------------
+// exclusive scan: tiles of 256 threads x 8 items, three phases (tile sums, scan of the sums,
+// tile scans plus offsets), recursive on the tile sums.
+// ------------------------------------------------------------------------------------------
+#define SC_THREADS 256
+#define SC_ITEMS 8
+#define SC_TILE (SC_THREADS * SC_ITEMS)
+
+template <class T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* warp_tot, T* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < (SC_THREADS / 32) ? warp_tot[lane] : T(0);
+        T wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(FULL_MASK, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < (SC_THREADS / 32)) warp_tot[lane] = wi - w;
+        if (lane == (SC_THREADS / 32) - 1) *total = wi;
+    }
+    __syncthreads();
+    T r = warp_tot[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+template <class T>
+__global__ void __launch_bounds__(SC_THREADS) k_tile_sum(const T* in, int64_t n, T* sums) {
+    __shared__ T warp_tot[SC_THREADS / 32];
+    __shared__ T total;
+    int64_t base = (int64_t)blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k)
+        if (base + k < n) s += in[base + k];
+    block_exclusive_scan<T>(s, warp_tot, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+template <class T>
+__global__ void __launch_bounds__(SC_THREADS) k_tile_scan(const T* in, T* out, int64_t n,
+                                                          const T* offs, T* grand) {
+    __shared__ T warp_tot[SC_THREADS / 32];
+    __shared__ T total;
+    int64_t base = (int64_t)blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+    T v[SC_ITEMS];
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : T(0);
+        s += v[k];
+    }
+    T ex = block_exclusive_scan<T>(s, warp_tot, &total);
+    T off = offs ? offs[blockIdx.x] : T(0);
+    T run = off + ex;
+#pragma unroll
+    for (int k = 0; k < SC_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (grand && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *grand = off + total;
+}
+
+template <class T>
+static int scan_exclusive(nqs_problem* p, Scratch& sc, const T* in, T* out, int64_t n, T* total,
+                          cudaStream_t s) {
+    if (n <= 0) {
+        if (total) NQS_CK(cudaMemsetAsync(total, 0, sizeof(T), s));
+        return NQS_OK;
+    }
+    int64_t tiles = (n + SC_TILE - 1) / SC_TILE;
+    if (tiles == 1) {
+        k_tile_scan<T><<<1, SC_THREADS, 0, s>>>(in, out, n, nullptr, total);
+        NQS_CK_LAUNCH();
+        return NQS_OK;
+    }
+    T* sums;
+    NQS_TRY(sc.get(&sums, tiles));
+    k_tile_sum<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, n, sums);
+    NQS_CK_LAUNCH();
+    NQS_TRY(scan_exclusive<T>(p, sc, sums, sums, tiles, (T*)nullptr, s));
+    k_tile_scan<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, sums, total);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int scan_exclusive_i64(nqs_problem* p, Scratch& sc, const int64_t* in, int64_t* out, int64_t n,
+                       int64_t* total, cudaStream_t s) {
+    return scan_exclusive<int64_t>(p, sc, in, out, n, total, s);
+}
+int scan_exclusive_u32(nqs_problem* p, Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n,
+                       cudaStream_t s) {
+    return scan_exclusive<uint32_t>(p, sc, in, out, n, (uint32_t*)nullptr, s);
+}
+
+// ------------------------------------------------------------------------------------------
+// compensated (Neumaier) reductions: fixed grid, fixed tree -> deterministic
+// ------------------------------------------------------------------------------------------
+struct KS {
+    double s, c;
+};
+__device__ __forceinline__ KS ks_add(KS k, double x) {
+    double t = __dadd_rn(k.s, x);
+    if (fabs(k.s) >= fabs(x)) k.c = __dadd_rn(k.c, __dadd_rn(__dsub_rn(k.s, t), x));
+    else k.c = __dadd_rn(k.c, __dadd_rn(__dsub_rn(x, t), k.s));
+    k.s = t;
+    return k;
+}
+__device__ __forceinline__ KS ks_merge(KS a, KS b) {
+    KS r = ks_add(a, b.s);
+    r.c = __dadd_rn(r.c, b.c);
+    return r;
+}
+
+#define KR_THREADS 256
+#define KR_BLOCKS 256
+
+__device__ __forceinline__ KS block_ks(KS v) {
+    __shared__ double ss[KR_THREADS], cc[KR_THREADS];
+    ss[threadIdx.x] = v.s;
+    cc[threadIdx.x] = v.c;
+    __syncthreads();
+    for (int o = KR_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            KS a{ss[threadIdx.x], cc[threadIdx.x]}, b{ss[threadIdx.x + o], cc[threadIdx.x + o]};
+            KS r = ks_merge(a, b);
+            ss[threadIdx.x] = r.s;
+            cc[threadIdx.x] = r.c;
+        }
+        __syncthreads();
+    }
+    KS r{ss[0], cc[0]};
+    __syncthreads();
+    return r;
+}
+
+// mode 0: sum x; mode 1: sum x*y; mode 2: sum y*y
+template <int MODE>
+__global__ void __launch_bounds__(KR_THREADS) k_ksum(const double* x, const double* y, int64_t n,
+                                                      double2* part) {
+    KS k{0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * KR_THREADS + threadIdx.x; i < n;
+         i += (int64_t)KR_BLOCKS * KR_THREADS) {
+        double v = MODE == 0 ? x[i] : (MODE == 1 ? __dmul_rn(x[i], y[i]) : __dmul_rn(y[i], y[i]));
+        k = ks_add(k, v);
+    }
+    KS r = block_ks(k);
+    if (threadIdx.x == 0) part[blockIdx.x] = make_double2(r.s, r.c);
+}
+
+__global__ void __launch_bounds__(KR_THREADS) k_ksum_final(const double2* part, int nparts,
+                                                            double* out) {
+    KS k{0.0, 0.0};
+    for (int i = threadIdx.x; i < nparts; i += KR_THREADS) k = ks_merge(k, KS{part[i].x, part[i].y});
+    KS r = block_ks(k);
+    if (threadIdx.x == 0) *out = r.s + r.c;
+}
+
+int ksum_f64(nqs_problem* p, Scratch& sc, const double* x, int64_t n, double* out,
+             cudaStream_t s) {
+    double2* part;
+    NQS_TRY(sc.get(&part, KR_BLOCKS));
+    k_ksum<0><<<KR_BLOCKS, KR_THREADS, 0, s>>>(x, nullptr, n, part);
+    NQS_CK_LAUNCH();
+    k_ksum_final<<<1, KR_THREADS, 0, s>>>(part, KR_BLOCKS, out);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int kdot2_f64(nqs_problem* p, Scratch& sc, const double* x, const double* y, int64_t n,
+              double* out, cudaStream_t s) {
+    double2* part;
+    NQS_TRY(sc.get(&part, 2 * KR_BLOCKS));
+    k_ksum<1><<<KR_BLOCKS, KR_THREADS, 0, s>>>(x, y, n, part);
+    NQS_CK_LAUNCH();
+    k_ksum<2><<<KR_BLOCKS, KR_THREADS, 0, s>>>(x, y, n, part + KR_BLOCKS);
+    NQS_CK_LAUNCH();
+    k_ksum_final<<<1, KR_THREADS, 0, s>>>(part, KR_BLOCKS, out);
+    NQS_CK_LAUNCH();
+    k_ksum_final<<<1, KR_THREADS, 0, s>>>(part + KR_BLOCKS, KR_BLOCKS, out + 1);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+__global__ void __launch_bounds__(KR_THREADS) k_max_masked(const double* x, const int8_t* mask,
+                                                            int64_t n, double* part, int final_) {
+    __shared__ double sm[KR_THREADS];
+    double m = -INFINITY;
+    for (int64_t i = (int64_t)blockIdx.x * KR_THREADS + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * KR_THREADS)
+        if (!mask || mask[i] != 0) m = fmax(m, x[i]);
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = KR_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+int max_f64_masked(nqs_problem* p, Scratch& sc, const double* x, const int8_t* mask, int64_t n,
+                   double* out, cudaStream_t s) {
+    double* part;
+    NQS_TRY(sc.get(&part, KR_BLOCKS));
+    k_max_masked<<<KR_BLOCKS, KR_THREADS, 0, s>>>(x, mask, n, part, 0);
+    NQS_CK_LAUNCH();
+    k_max_masked<<<1, KR_THREADS, 0, s>>>(part, nullptr, KR_BLOCKS, out, 1);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits. Per pass: per-tile digit histograms, one exclusive
+// scan over (digit-major, tile-minor) counts, then a scatter in which each warp ranks its
+// elements with __match_any_sync (elements in ascending index order: warp, item, lane), so
+// equal digits keep their input order. No inter-block waiting of any kind.
+// ------------------------------------------------------------------------------------------
+#define RS_THREADS 256
+#define RS_ITEMS 16
+#define RS_TILE (RS_THREADS * RS_ITEMS)
+#define RS_WARPS (RS_THREADS / 32)
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restrict__ keys,
+                                                         int64_t n, int shift,
+                                                         uint32_t* __restrict__ counts,
+                                                         int64_t T) {
+    __shared__ uint32_t hist[256];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        int64_t i = base + k * RS_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&hist[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * T + blockIdx.x] = hist[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __restrict__ kin,
+                                                            const double* __restrict__ vin,
+                                                            uint64_t* __restrict__ kout,
+                                                            double* __restrict__ vout, int64_t n,
+                                                            int shift,
+                                                            const uint32_t* __restrict__ offs,
+                                                            int64_t T) {
+    __shared__ uint32_t whist[RS_WARPS][256];
+    __shared__ uint32_t toff[256];
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&whist[0][0])[i] = 0;
+    toff[threadIdx.x] = offs[(int64_t)threadIdx.x * T + blockIdx.x];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + warp * (RS_ITEMS * 32);
+    uint64_t key[RS_ITEMS];
+    double val[RS_ITEMS];
+    uint32_t rank[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        int64_t i = wbase + k * 32 + lane;
+        bool v = i < n;
+        key[k] = v ? kin[i] : 0ull;
+        val[k] = v ? vin[i] : 0.0;
+    }
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        int64_t i = wbase + k * 32 + lane;
+        bool v = i < n;
+        uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
+        unsigned peers = __match_any_sync(FULL_MASK, v ? d : 256u);
+        uint32_t old = v ? whist[warp][d] : 0u;
+        __syncwarp();
+        int leader = __ffs(peers) - 1;
+        if (v && lane == leader) whist[warp][d] = old + __popc(peers);
+        __syncwarp();
+        rank[k] = old + __popc(peers & lt);
+    }
+    __syncthreads();
+    {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            uint32_t c = whist[w][threadIdx.x];
+            whist[w][threadIdx.x] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        int64_t i = wbase + k * 32 + lane;
+        if (i < n) {
+            uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
+            uint32_t pos = toff[d] + whist[warp][d] + rank[k];
+            kout[pos] = key[k];
+            vout[pos] = val[k];
+        }
+    }
+}
+
+int radix_sort_pairs(nqs_problem* p, Scratch& sc, uint64_t*& keys, double*& vals,
+                     uint64_t*& keys_alt, double*& vals_alt, int64_t n, int bits, cudaStream_t s) {
+    if (n <= 1) return NQS_OK;
+    if (n >= (int64_t)1 << 32) return NQS_ERR_UNSUPPORTED;
+    int64_t T = (n + RS_TILE - 1) / RS_TILE;
+    uint32_t* counts;
+    NQS_TRY(sc.get(&counts, 256 * T));
+    for (int shift = 0; shift < bits; shift += 8) {
+        {
+            ProfScope prof_(PROF_RS_HIST, s);
+            k_rs_hist<<<(unsigned)T, RS_THREADS, 0, s>>>(keys, n, shift, counts, T);
+        }
+        NQS_CK_LAUNCH();
+        NQS_TRY(scan_exclusive_u32(p, sc, counts, counts, 256 * T, s));
+        {
+            ProfScope prof_(PROF_RS_SCATTER, s);
+            k_rs_scatter<<<(unsigned)T, RS_THREADS, 0, s>>>(keys, vals, keys_alt, vals_alt, n, shift,
+                                                            counts, T);
+        }
+        NQS_CK_LAUNCH();
+        uint64_t* tk = keys;
+        keys = keys_alt;
+        keys_alt = tk;
+        double* tv = vals;
+        vals = vals_alt;
+        vals_alt = tv;
+    }
+    return NQS_OK;
+}

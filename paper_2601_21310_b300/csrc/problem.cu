@@ -1,0 +1,269 @@
+// Problem handle (integrals on the device), scratch pool, validation of S, the hash table of S
+// and the diagonal element H_xx.
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "excite.cuh"
+#include "nqs_internal.cuh"
+
+static thread_local char g_last_error[512];
+
+void nqs_record_error(const char* what, cudaError_t e, const char* file, int line) {
+    snprintf(g_last_error, sizeof g_last_error, "%s failed: %s (%s:%d)", what,
+             cudaGetErrorString(e), file, line);
+}
+
+extern "C" const char* nqs_last_error(void) { return g_last_error; }
+
+extern "C" const char* nqs_status_string(int status) {
+    switch (status) {
+        case NQS_OK: return "ok";
+        case NQS_WARN_SINGULAR: return "warning: an occupied block is exactly singular";
+        case NQS_ERR_ARG: return "invalid argument";
+        case NQS_ERR_UNSORTED: return "determinants not sorted ascending / not unique";
+        case NQS_ERR_POPCOUNT: return "determinant with the wrong electron count";
+        case NQS_ERR_NORB: return "orbital count unsupported";
+        case NQS_ERR_OOM: return "device allocation failed";
+        case NQS_ERR_CUDA: return "CUDA error";
+        case NQS_ERR_TIMEOUT: return "device wait timed out";
+        case NQS_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* nqs_version(void) { return "nqs-b300 0.1 (sm_103a)"; }
+
+extern "C" void nqs_opts_default(nqs_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->precision = NQS_FP64;
+    o->buckets = 1;
+    o->chunk = 0;
+    o->validate = 1;
+    o->internal_pt2 = 1;
+}
+
+// ------------------------------------------------------------------------------------------
+// scratch: a library-owned memory pool, so repeated calls reuse memory without cudaMalloc
+// ------------------------------------------------------------------------------------------
+int nqs_scratch_alloc(nqs_problem* p, void** ptr, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, p->pool, s);
+    if (e != cudaSuccess) {
+        nqs_record_error("cudaMallocFromPoolAsync", e, __FILE__, __LINE__);
+        cudaGetLastError();
+        return NQS_ERR_OOM;
+    }
+    return NQS_OK;
+}
+
+void nqs_scratch_free(nqs_problem* p, void* ptr, cudaStream_t s) {
+    if (ptr) cudaFreeAsync(ptr, s);
+}
+
+// ------------------------------------------------------------------------------------------
+// problem create / destroy
+// ------------------------------------------------------------------------------------------
+__global__ void k_tables(int n, const double* eri, double* J, double* K, double* TJ, double* TK) {
+    int64_t total = (int64_t)n * n * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int j = (int)(t % n), a = (int)((t / n) % n), i = (int)(t / ((int64_t)n * n));
+        TJ[t] = eri[(((size_t)i * n + a) * n + j) * n + j];   // (ia|jj)
+        TK[t] = eri[(((size_t)i * n + j) * n + j) * n + a];   // (ij|ja)
+        if (a == 0) {
+            J[i * n + j] = eri[(((size_t)i * n + i) * n + j) * n + j];  // (ii|jj)
+            K[i * n + j] = eri[(((size_t)i * n + j) * n + j) * n + i];  // (ij|ji)
+        }
+    }
+}
+
+extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double* h,
+                                  const double* eri, double ecore, nqs_problem** out) {
+    if (!out || !h || !eri) return NQS_ERR_ARG;
+    *out = nullptr;
+    if (norb < 1 || norb > NQS_MAX_NORB) return NQS_ERR_NORB;
+    if (nalpha <= 0 || nbeta <= 0 || nalpha >= norb || nbeta >= norb) return NQS_ERR_ARG;
+    nqs_problem* p = (nqs_problem*)calloc(1, sizeof(nqs_problem));
+    if (!p) return NQS_ERR_OOM;
+    p->ecore = ecore;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        free(p);
+        return NQS_ERR_CUDA;
+    }
+    size_t n2 = (size_t)norb * norb, n3 = n2 * norb, n4 = n3 * norb;
+    auto fail = [&](int code) {
+        nqs_problem_destroy(p);
+        return code;
+    };
+    if (cudaMalloc(&p->h, n2 * 8) != cudaSuccess || cudaMalloc(&p->eri, n4 * 8) != cudaSuccess ||
+        cudaMalloc(&p->J, n2 * 8) != cudaSuccess || cudaMalloc(&p->K, n2 * 8) != cudaSuccess ||
+        cudaMalloc(&p->TJ, n3 * 8) != cudaSuccess || cudaMalloc(&p->TK, n3 * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NQS_ERR_OOM);
+    }
+    if (cudaMemcpy(p->h, h, n2 * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->eri, eri, n4 * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(NQS_ERR_CUDA);
+    k_tables<<<grid_for((int64_t)n3, 256), 256>>>(norb, p->eri, p->J, p->K, p->TJ, p->TK);
+    nqs_note_launch();
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return fail(NQS_ERR_CUDA);
+
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = p->device;
+    if (cudaMemPoolCreate(&p->pool, &props) != cudaSuccess) {
+        p->pool = nullptr;
+        return fail(NQS_ERR_CUDA);
+    }
+    uint64_t thresh = ~0ull;  // keep freed scratch in the pool between calls
+    cudaMemPoolSetAttribute(p->pool, cudaMemPoolAttrReleaseThreshold, &thresh);
+
+    ProblemDev& d = p->d;
+    d.norb = norb;
+    d.na = nalpha;
+    d.nb = nbeta;
+    d.ma = norb - nalpha;
+    d.mb = norb - nbeta;
+    d.sA = (int64_t)d.na * d.ma;
+    d.sB = (int64_t)d.nb * d.mb;
+    d.dAA = choose2(d.na) * choose2(d.ma);
+    d.dBB = choose2(d.nb) * choose2(d.mb);
+    d.dAB = d.sA * d.sB;
+    d.nexc = d.sA + d.sB + d.dAA + d.dBB + d.dAB;
+    d.h = p->h;
+    d.eri = p->eri;
+    d.J = p->J;
+    d.K = p->K;
+    d.TJ = p->TJ;
+    d.TK = p->TK;
+    if (d.nexc >= ((int64_t)1 << 31)) return fail(NQS_ERR_NORB);
+    *out = p;
+    return NQS_OK;
+}
+
+extern "C" int nqs_problem_destroy(nqs_problem* p) {
+    if (!p) return NQS_OK;
+    cudaDeviceSynchronize();
+    cudaFree(p->h);
+    cudaFree(p->eri);
+    cudaFree(p->J);
+    cudaFree(p->K);
+    cudaFree(p->TJ);
+    cudaFree(p->TK);
+    if (p->pool) cudaMemPoolDestroy(p->pool);
+    free(p);
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// validation: sorted strictly ascending (optional) and right popcounts
+// ------------------------------------------------------------------------------------------
+__global__ void k_validate(const ulonglong2* S, int64_t n, int na, int nb, int check_sorted,
+                           uint64_t norb_mask, int* flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ulonglong2 x = S[i];
+        if (__popcll(x.x) != na || __popcll(x.y) != nb || (x.x & ~norb_mask) || (x.y & ~norb_mask))
+            atomicOr(&flags[0], 1);
+        if (check_sorted && i > 0) {
+            ulonglong2 y = S[i - 1];
+            bool ok = (y.x < x.x) || (y.x == x.x && y.y < x.y);
+            if (!ok) atomicOr(&flags[1], 1);
+        }
+    }
+}
+
+int validate_dets(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, bool sorted,
+                  cudaStream_t s) {
+    int* flags;
+    NQS_TRY(sc.get(&flags, 2));
+    NQS_CK(cudaMemsetAsync(flags, 0, 2 * sizeof(int), s));
+    uint64_t mask = p->d.norb == 64 ? ~0ull : ((1ull << p->d.norb) - 1ull);
+    k_validate<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, p->d.na, p->d.nb,
+                                                 sorted ? 1 : 0, mask, flags);
+    NQS_CK_LAUNCH();
+    int h[2];
+    NQS_CK(cudaMemcpyAsync(h, flags, sizeof h, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    if (h[0]) return NQS_ERR_POPCOUNT;
+    if (h[1]) return NQS_ERR_UNSORTED;
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// hash table of S
+// ------------------------------------------------------------------------------------------
+__global__ void k_hash_clear(ulonglong2* keys, int32_t* idx, uint64_t cap) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        keys[i] = make_ulonglong2(NQS_EMPTY_WORD, NQS_EMPTY_WORD);
+        idx[i] = -1;
+    }
+}
+
+__global__ void k_hash_insert(const ulonglong2* S, int64_t n, int32_t* idx, uint64_t mask) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ulonglong2 x = S[i];
+        uint64_t slot = det_hash(x.x, x.y) & mask;
+        for (uint64_t it = 0; it <= mask; ++it) {  // capacity > n: an empty slot exists
+            if (atomicCAS(&idx[slot], -1, (int32_t)i) == -1) break;
+            slot = (slot + 1) & mask;
+        }
+    }
+}
+
+__global__ void k_hash_keys(const ulonglong2* S, const int32_t* idx, ulonglong2* keys,
+                            uint64_t cap) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        int32_t k = idx[i];
+        if (k >= 0) keys[i] = S[k];
+    }
+}
+
+int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, HashS* out,
+               cudaStream_t s) {
+    uint64_t cap = 1024;
+    while (cap < 2 * (uint64_t)nS) cap <<= 1;
+    ulonglong2* keys;
+    int32_t* idx;
+    NQS_TRY(sc.get(&keys, cap));
+    NQS_TRY(sc.get(&idx, cap));
+    k_hash_clear<<<grid_for(cap, 256), 256, 0, s>>>(keys, idx, cap);
+    NQS_CK_LAUNCH();
+    k_hash_insert<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, idx, cap - 1);
+    NQS_CK_LAUNCH();
+    k_hash_keys<<<grid_for(cap, 256), 256, 0, s>>>((const ulonglong2*)dets, idx, keys, cap);
+    NQS_CK_LAUNCH();
+    out->keys = keys;
+    out->idx = idx;
+    out->mask = cap - 1;
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// diagonal elements
+// ------------------------------------------------------------------------------------------
+__global__ void k_diag(ProblemDev P, const ulonglong2* dets, int64_t n, double* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ulonglong2 x = dets[i];
+        out[i] = diag_element_impl(P, x.x, x.y);
+    }
+}
+
+extern "C" int nqs_diag(nqs_problem* p, const uint64_t* dets, int64_t n, double* out,
+                        nqs_stream_t stream) {
+    if (!p || (n > 0 && (!dets || !out)) || n < 0) return NQS_ERR_ARG;
+    if (n == 0) return NQS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_diag<<<grid_for(n, 128), 128, 0, s>>>(p->d, (const ulonglong2*)dets, n, out);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}

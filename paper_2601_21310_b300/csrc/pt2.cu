@@ -1,0 +1,323 @@
+// Epstein-Nesbet PT2 over the connected space (Eq. pt2_correction; Algorithm 1 step 4).
+//
+// For each hash bucket b (SplitMix64 finaliser of the det, mod B):
+//   1. emit (key x', H_x'y psi_y) for every excitation x' of every y in S with bucket(x') = b,
+//      in canonical order (y ascending, then canonical excitation index) - with B = 1 the
+//      position of every emission is fixed, otherwise a count pass and a scan give them;
+//   2. stable LSD radix sort by key (2 norb bits), so equal keys stay in emission order;
+//   3. mark run heads, scan them, sum each run in order -> c(x'); runs whose x' is in S feed
+//      the internal term (c(x) is the off-diagonal part of (H_SS psi)_x), the others give
+//      c^2 / (D (E - H_x'x')) with H_x'x' from the Slater-Condon diagonal;
+//   4. compensated sums of the external terms, and of the internal terms of the dets of S in
+//      bucket b: r_x = H_xx psi_x + c(x) - E psi_x, r_x^2 / (D (E - H_xx)).
+// D = psi.psi, compensated. Keys are (a << norb) | b in one uint64, so 2 norb <= 64.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "excite.cuh"
+#include "nqs_internal.cuh"
+#include "prof.cuh"
+
+#define PT_THREADS 256
+#define PT_WARPS (PT_THREADS / 32)
+
+__device__ __forceinline__ bool in_bucket(uint64_t a, uint64_t b, uint64_t B, uint64_t bucket) {
+    return B == 1 || (det_hash(a, b) % B) == bucket;
+}
+
+__global__ void __launch_bounds__(PT_THREADS) k_pt2_count(ProblemDev P,
+                                                           const ulonglong2* __restrict__ S,
+                                                           int64_t nS, uint64_t B,
+                                                           uint64_t bucket, int64_t* cnt) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nexc = (uint32_t)P.nexc;
+    for (int64_t det = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * PT_WARPS) {
+        ulonglong2 x = S[det];
+        fill_ctx(P, x.x, x.y, ctx, lane);
+        int c = 0;
+        for (uint32_t e = lane; e < nexc; e += 32) {
+            uint64_t a2, b2;
+            decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+            c += in_bucket(a2, b2, B, bucket);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL_MASK, c, o);
+        if (lane == 0) cnt[det] = c;
+        __syncwarp();
+    }
+}
+
+// offs == nullptr: every excitation is emitted at det * nexc + e (B = 1)
+__global__ void __launch_bounds__(PT_THREADS) k_pt2_emit(ProblemDev P,
+                                                          const ulonglong2* __restrict__ S,
+                                                          const double* __restrict__ psi,
+                                                          int64_t nS, uint64_t B, uint64_t bucket,
+                                                          const int64_t* __restrict__ offs,
+                                                          uint64_t* __restrict__ keys,
+                                                          double* __restrict__ vals) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const uint32_t nexc = (uint32_t)P.nexc;
+    const int norb = P.norb;
+    for (int64_t det = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * PT_WARPS) {
+        ulonglong2 x = S[det];
+        fill_ctx(P, x.x, x.y, ctx, lane);
+        const double py = psi[det];
+        int64_t run = offs ? offs[det] : det * (int64_t)nexc;
+        for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
+            uint32_t e = r0 + lane;
+            bool take = false;
+            Exc ex;
+            if (e < nexc) {
+                decode_exc(P, T, *ctx, x.x, x.y, e, ex);
+                take = in_bucket(ex.a2, ex.b2, B, bucket);
+            }
+            unsigned m = __ballot_sync(FULL_MASK, take);
+            if (take) {
+                int64_t pos = run + __popc(m & lt);
+                keys[pos] = (ex.a2 << norb) | ex.b2;
+                vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
+            }
+            run += __popc(m);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_heads(const uint64_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ f) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_starts(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ pos,
+                         int64_t n, int64_t* __restrict__ starts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (i == 0 || keys[i] != keys[i - 1]) starts[pos[i]] = i;
+}
+
+__global__ void k_seg_reduce(ProblemDev P, HashS H, const uint64_t* __restrict__ keys,
+                             const double* __restrict__ vals, const int64_t* __restrict__ starts,
+                             int64_t nuniq, int64_t n, const double* __restrict__ Dp, double E,
+                             double* __restrict__ cS, double* __restrict__ eterm,
+                             unsigned long long* __restrict__ next) {
+    const double D = *Dp;
+    const int norb = P.norb;
+    const uint64_t bmask = norb == 64 ? ~0ull : ((1ull << norb) - 1ull);
+    unsigned long long local = 0;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nuniq;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i0 = starts[u], i1 = (u + 1 < nuniq) ? starts[u + 1] : n;
+        double c = 0.0;
+        for (int64_t i = i0; i < i1; ++i) c = __dadd_rn(c, vals[i]);
+        uint64_t k = keys[i0];
+        uint64_t a = norb == 64 ? 0 : (k >> norb), b = k & bmask;
+        int32_t s = hash_lookup(H, a, b);
+        if (s >= 0) {
+            cS[s] = c;
+            eterm[u] = 0.0;
+        } else {
+            double hxx = diag_element_impl(P, a, b);
+            eterm[u] = __ddiv_rn(__dmul_rn(c, c), __dmul_rn(D, __dsub_rn(E, hxx)));
+            ++local;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(FULL_MASK, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(next, local);
+}
+
+__global__ void k_pt2_internal(ProblemDev P, const ulonglong2* __restrict__ S,
+                               const double* __restrict__ psi, const double* __restrict__ cS,
+                               int64_t nS, const double* __restrict__ Dp, double E, uint64_t B,
+                               uint64_t bucket, double* __restrict__ eterm) {
+    const double D = *Dp;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nS;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        ulonglong2 x = S[i];
+        if (!in_bucket(x.x, x.y, B, bucket)) {
+            eterm[i] = 0.0;
+            continue;
+        }
+        double hxx = diag_element_impl(P, x.x, x.y);
+        double vx = __dadd_rn(__dmul_rn(hxx, psi[i]), cS[i]);
+        double r = __dsub_rn(vx, __dmul_rn(E, psi[i]));
+        eterm[i] = __ddiv_rn(__dmul_rn(r, r), __dmul_rn(D, __dsub_rn(E, hxx)));
+    }
+}
+
+static size_t pt_smem(const ProblemDev& P) {
+    return pair_table_bytes(P) + PT_WARPS * sizeof(DetCtx);
+}
+static unsigned pt_grid(int64_t nS) {
+    int64_t g = (nS + PT_WARPS - 1) / PT_WARPS;
+    if (g > 148 * 16) g = 148 * 16;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+// host-side compensated sum (bucket partials)
+static double host_ksum(const std::vector<double>& v) {
+    double s = 0, c = 0;
+    for (double x : v) {
+        double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    return s + c;
+}
+
+extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                       double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
+                       nqs_stream_t stream) {
+    if (!p || !dets || !psi || !out || nS <= 0) return NQS_ERR_ARG;
+    if (((uintptr_t)dets) & 15) return NQS_ERR_ARG;
+    if (2 * p->d.norb > 64) return NQS_ERR_NORB;
+    if (nS >= ((int64_t)1 << 31)) return NQS_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    nqs_opts def;
+    if (!opts) {
+        nqs_opts_default(&def);
+        opts = &def;
+    }
+    const int64_t B = opts->buckets < 1 ? 1 : opts->buckets;
+    Scratch sc(p, s);
+    if (opts->validate) NQS_TRY(validate_dets(p, sc, dets, nS, true, s));
+    HashS H;
+    NQS_TRY(hash_build(p, sc, dets, nS, &H, s));
+    const ProblemDev& P = p->d;
+    size_t smem = pt_smem(P);
+    if (smem > 48 * 1024) {
+        NQS_CK(cudaFuncSetAttribute(k_pt2_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_pt2_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    }
+    double* dev_scalars;  // [0] = D, then per bucket (ext, int)
+    NQS_TRY(sc.get(&dev_scalars, 1 + 2 * B));
+    unsigned long long* next_dev;
+    NQS_TRY(sc.get(&next_dev, B));
+    NQS_CK(cudaMemsetAsync(next_dev, 0, B * sizeof(unsigned long long), s));
+    NQS_TRY(kdot2_f64(p, sc, psi, psi, nS, dev_scalars, s));  // dev_scalars[0] = psi.psi
+    double* cS;
+    NQS_TRY(sc.get(&cS, nS));
+    NQS_CK(cudaMemsetAsync(cS, 0, nS * sizeof(double), s));
+    double* eint;
+    NQS_TRY(sc.get(&eint, nS));
+    int64_t* cnt = nullptr;
+    int64_t* offs = nullptr;
+    int64_t* total_dev = nullptr;
+    if (B > 1) {
+        NQS_TRY(sc.get(&cnt, nS));
+        NQS_TRY(sc.get(&offs, nS));
+        NQS_TRY(sc.get(&total_dev, 1));
+    }
+    const int64_t cap = opts->chunk > 0 ? opts->chunk : ((int64_t)1 << 32) - 1;
+    const int keybits = 2 * P.norb;
+    int64_t total_emitted = 0;
+    // per-bucket buffers are allocated per bucket and released at the end of the bucket
+    for (int64_t b = 0; b < B; ++b) {
+        Scratch bs(p, s);
+        int64_t n;
+        if (B == 1) {
+            n = nS * P.nexc;
+        } else {
+            {
+                ProfScope prof_(PROF_PT2_COUNT, s);
+                k_pt2_count<<<pt_grid(nS), PT_THREADS, smem, s>>>(P, (const ulonglong2*)dets, nS,
+                                                                  (uint64_t)B, (uint64_t)b, cnt);
+            }
+            NQS_CK_LAUNCH();
+            NQS_TRY(scan_exclusive_i64(p, bs, cnt, offs, nS, total_dev, s));
+            NQS_CK(cudaMemcpyAsync(&n, total_dev, sizeof n, cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaStreamSynchronize(s));
+        }
+        if (n > cap) return NQS_ERR_OOM;  // more buckets needed
+        total_emitted += n;
+        uint64_t *keys, *keys2;
+        double *vals, *vals2;
+        NQS_TRY(bs.get(&keys, n));
+        NQS_TRY(bs.get(&vals, n));
+        NQS_TRY(bs.get(&keys2, n));
+        NQS_TRY(bs.get(&vals2, n));
+        {
+            ProfScope prof_(PROF_PT2_EMIT, s);
+            k_pt2_emit<<<pt_grid(nS), PT_THREADS, smem, s>>>(P, (const ulonglong2*)dets, psi, nS,
+                                                             (uint64_t)B, (uint64_t)b,
+                                                             B == 1 ? nullptr : offs, keys, vals);
+        }
+        NQS_CK_LAUNCH();
+        NQS_TRY(radix_sort_pairs(p, bs, keys, vals, keys2, vals2, n, keybits, s));
+        // unique + segmented reduction (reuse the alternate buffers as scratch)
+        uint32_t* flags = (uint32_t*)keys2;  // n u32 fit in n u64
+        uint32_t* pos = flags + n;           // second half of keys2 (n u32)
+        k_heads<<<grid_for(n, 256), 256, 0, s>>>(keys, n, flags);
+        NQS_CK_LAUNCH();
+        NQS_TRY(scan_exclusive_u32(p, bs, flags, pos, n, s));
+        uint32_t last_pos = 0, last_flag = 0;
+        if (n > 0) {
+            NQS_CK(cudaMemcpyAsync(&last_pos, pos + n - 1, 4, cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaMemcpyAsync(&last_flag, flags + n - 1, 4, cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaStreamSynchronize(s));
+        }
+        int64_t nuniq = n > 0 ? (int64_t)last_pos + last_flag : 0;
+        int64_t* starts = (int64_t*)vals2;    // nuniq <= n int64
+        double* eterm;
+        NQS_TRY(bs.get(&eterm, nuniq));
+        if (nuniq > 0) {
+            k_starts<<<grid_for(n, 256), 256, 0, s>>>(keys, pos, n, starts);
+            NQS_CK_LAUNCH();
+            {
+                ProfScope prof_(PROF_SEG_REDUCE, s);
+                k_seg_reduce<<<grid_for(nuniq, 256), 256, 0, s>>>(P, H, keys, vals, starts, nuniq, n,
+                                                                  dev_scalars, E_var, cS, eterm,
+                                                                  next_dev + b);
+            }
+            NQS_CK_LAUNCH();
+        }
+        NQS_TRY(ksum_f64(p, bs, eterm, nuniq, dev_scalars + 1 + 2 * b, s));
+        if (opts->internal_pt2) {
+            k_pt2_internal<<<grid_for(nS, 256), 256, 0, s>>>(P, (const ulonglong2*)dets, psi, cS,
+                                                             nS, dev_scalars, E_var, (uint64_t)B,
+                                                             (uint64_t)b, eint);
+            NQS_CK_LAUNCH();
+            NQS_TRY(ksum_f64(p, bs, eint, nS, dev_scalars + 2 + 2 * b, s));
+        } else {
+            NQS_CK(cudaMemsetAsync(dev_scalars + 2 + 2 * b, 0, sizeof(double), s));
+        }
+    }
+    std::vector<double> hs(1 + 2 * B);
+    std::vector<unsigned long long> hn(B);
+    NQS_CK(cudaMemcpyAsync(hs.data(), dev_scalars, hs.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaMemcpyAsync(hn.data(), next_dev, B * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    std::vector<double> ext(B), in(B);
+    double nu = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        ext[b] = hs[1 + 2 * b];
+        in[b] = hs[2 + 2 * b];
+        nu += (double)hn[b];
+        if (bucket_partials) {
+            bucket_partials[2 * b] = ext[b];
+            bucket_partials[2 * b + 1] = in[b];
+        }
+    }
+    out[0] = host_ksum(ext);
+    out[1] = host_ksum(in);
+    out[2] = nu;
+    out[3] = (double)total_emitted;
+    return NQS_OK;
+}

@@ -1,0 +1,373 @@
+"""Python binding of the C ABI in include/nqs.h (argument marshalling only).
+
+Every computation runs in libnqs.so on the GPU; this module converts torch tensors to device
+pointers, fills the option struct and turns status codes into exceptions. There is no CPU
+path: if the library or a CUDA device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnqs.so")
+
+NQS_FP64 = 0
+NQS_MIXED = 1
+NQS_WARN_SINGULAR = 1
+
+_lib = None
+
+
+class NQSError(RuntimeError):
+    pass
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("buckets", C.c_int), ("chunk", C.c_int64),
+                ("validate", C.c_int), ("internal_pt2", C.c_int), ("reserved", C.c_int * 8)]
+
+
+class CSRStruct(C.Structure):
+    _fields_ = [("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p),
+                ("nnz", C.c_int64), ("n_rows", C.c_int64)]
+
+
+EXPORTS = {
+    # name: (restype, argtypes)
+    "nqs_opts_default": (None, [C.c_void_p]),
+    "nqs_status_string": (C.c_char_p, [C.c_int]),
+    "nqs_version": (C.c_char_p, []),
+    "nqs_last_error": (C.c_char_p, []),
+    "nqs_problem_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                     C.c_double, C.c_void_p]),
+    "nqs_problem_destroy": (C.c_int, [C.c_void_p]),
+    "nqs_net_create": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "nqs_net_destroy": (C.c_int, [C.c_void_p]),
+    "nqs_net_num_params": (C.c_int64, [C.c_void_p]),
+    "nqs_diag": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "nqs_connections": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+    "nqs_csr_free": (C.c_int, [C.c_void_p]),
+    "nqs_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_energy_from_psi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
+    "nqs_energy_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_pt2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
+                          C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_profile_enable": (C.c_int, [C.c_int]),
+    "nqs_profile_reset": (C.c_int, []),
+    "nqs_profile_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p]),
+    "nqs_launch_count": (C.c_int64, []),
+}
+
+PROFILED = ["conn_count", "conn_fill", "pt2_count", "pt2_emit", "rs_hist", "rs_scatter",
+            "seg_reduce", "gemm", "lu", "spmv", "layer1"]
+
+
+def lib():
+    """Load libnqs.so (in-tree build). Raises if it is missing: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise NQSError(f"{LIB_PATH} is missing: build it with paper_2601_21310_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+_cudart_lib = None
+
+
+def _cudart():
+    """The CUDA runtime already loaded by torch (same soname), for raw device-to-host copies."""
+    global _cudart_lib
+    if _cudart_lib is None:
+        torch.cuda.init()
+        _cudart_lib = C.CDLL("libcudart.so.13")
+        _cudart_lib.cudaMemcpy.restype = C.c_int
+        _cudart_lib.cudaMemcpy.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+    return _cudart_lib
+
+
+def _check(status: int, what: str):
+    if status < 0:
+        L = lib()
+        msg = L.nqs_status_string(status).decode()
+        detail = L.nqs_last_error().decode()
+        raise NQSError(f"{what}: {msg} ({status}) {detail}")
+    return status
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dets(d: torch.Tensor) -> torch.Tensor:
+    if not (d.is_cuda and d.dtype == torch.uint64 and d.dim() == 2 and d.shape[1] == 2):
+        raise NQSError("dets must be a CUDA uint64 tensor of shape [n, 2]")
+    return d.contiguous()
+
+
+def opts(precision=NQS_FP64, buckets=1, chunk=0, validate=1, internal_pt2=1) -> Opts:
+    o = Opts()
+    lib().nqs_opts_default(C.byref(o))
+    o.precision, o.buckets, o.chunk = precision, buckets, chunk
+    o.validate, o.internal_pt2 = validate, internal_pt2
+    return o
+
+
+class Problem:
+    """nqs_problem: device copies of h and the ERIs (Sec. 3.3 Hamiltonian input)."""
+
+    def __init__(self, norb: int, nalpha: int, nbeta: int, h, eri, ecore: float = 0.0):
+        import numpy as np
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        eri = np.ascontiguousarray(eri, dtype=np.float64)
+        self.norb, self.nalpha, self.nbeta = norb, nalpha, nbeta
+        handle = C.c_void_p()
+        _check(lib().nqs_problem_create(norb, nalpha, nbeta, h.ctypes.data_as(C.c_void_p),
+                                        eri.ctypes.data_as(C.c_void_p), ecore, C.byref(handle)),
+               "nqs_problem_create")
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().nqs_problem_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """nqs_net over caller-owned device parameters [W1, b1, W2, b2, W3, b3, Phi0]."""
+
+    def __init__(self, problem: Problem, params: list, dtype: int):
+        self.problem = problem
+        self.params = [p.contiguous() for p in params]
+        self.dtype = dtype
+        H1, H2 = self.params[0].shape[0], self.params[2].shape[0]
+        arr = (C.c_void_p * 7)(*[p.data_ptr() for p in self.params])
+        handle = C.c_void_p()
+        _check(lib().nqs_net_create(problem.handle, H1, H2, dtype, arr, C.byref(handle)),
+               "nqs_net_create")
+        self.handle = handle
+
+    def num_params(self) -> int:
+        return lib().nqs_net_num_params(self.handle)
+
+    def grad_dtype(self):
+        return torch.float64 if self.dtype == NQS_FP64 else torch.float32
+
+    def split(self, flat: torch.Tensor):
+        out, k = [], 0
+        for p in self.params[:6]:
+            out.append(flat[k:k + p.numel()].view(p.shape))
+            k += p.numel()
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().nqs_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def net_tensors(params, dtype: int, device="cuda") -> list:
+    """Device tensors for a synth.NetParams in the requested precision form. The mixed form
+    rounds weights to bfloat16 (through float32) and biases / Phi0 to float32."""
+    ts = [torch.from_numpy(x.copy()) for x in params.as_list()]
+    if dtype == NQS_FP64:
+        return [t.to(device=device, dtype=torch.float64).contiguous() for t in ts]
+    out = []
+    for i, t in enumerate(ts):
+        t32 = t.to(torch.float32)
+        out.append((t32.to(torch.bfloat16) if i in (0, 2, 4) else t32).to(device).contiguous())
+    return out
+
+
+class CSR:
+    """Library-owned H_SS in CSR (freed with nqs_csr_free)."""
+
+    def __init__(self, st: CSRStruct, n_enumerated: int):
+        self.s = st
+        self.n_enumerated = n_enumerated
+
+    @property
+    def nnz(self) -> int:
+        return self.s.nnz
+
+    @property
+    def n_rows(self) -> int:
+        return self.s.n_rows
+
+    def host(self):
+        """(row_ptr, col, val) copied to host numpy arrays."""
+        import numpy as np
+        torch.cuda.synchronize()
+        rp = np.zeros(self.n_rows + 1, np.int64)
+        col = np.zeros(max(self.nnz, 1), np.int32)
+        val = np.zeros(max(self.nnz, 1), np.float64)
+        cudart = _cudart()
+        for dst, src, nb in ((rp, self.s.row_ptr, rp.nbytes), (col, self.s.col, self.nnz * 4),
+                             (val, self.s.val, self.nnz * 8)):
+            if nb:
+                st = cudart.cudaMemcpy(C.c_void_p(dst.ctypes.data), C.c_void_p(src),
+                                       C.c_size_t(nb), 2)
+                if st != 0:
+                    raise NQSError(f"cudaMemcpy failed ({st})")
+        return rp, col[:self.nnz], val[:self.nnz]
+
+    def free(self):
+        if self.s is not None and self.s.row_ptr:
+            lib().nqs_csr_free(C.byref(self.s))
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def diag(problem: Problem, dets: torch.Tensor, stream=None) -> torch.Tensor:
+    dets = _dets(dets)
+    out = torch.empty(dets.shape[0], dtype=torch.float64, device=dets.device)
+    _check(lib().nqs_diag(problem.handle, _ptr(dets), dets.shape[0], _ptr(out), _stream(stream)),
+           "nqs_diag")
+    return out
+
+
+def connections(problem: Problem, dets: torch.Tensor, o: Opts | None = None, stream=None) -> CSR:
+    dets = _dets(dets)
+    st = CSRStruct()
+    nen = C.c_int64(0)
+    _check(lib().nqs_connections(problem.handle, _ptr(dets), dets.shape[0],
+                                 C.byref(o) if o else None, C.byref(st), C.byref(nen),
+                                 _stream(stream)), "nqs_connections")
+    return CSR(st, nen.value)
+
+
+def amplitudes(problem: Problem, net: Net, dets: torch.Tensor, o: Opts | None = None,
+               stream=None):
+    dets = _dets(dets)
+    n = dets.shape[0]
+    la = torch.empty(n, dtype=torch.float64, device=dets.device)
+    sg = torch.empty(n, dtype=torch.int8, device=dets.device)
+    o = o or opts(precision=net.dtype)
+    st = _check(lib().nqs_amplitudes(problem.handle, net.handle, _ptr(dets), n, _ptr(la), _ptr(sg),
+                                     C.byref(o), _stream(stream)), "nqs_amplitudes")
+    return la, sg, st
+
+
+def energy_from_psi(csr: CSR, psi: torch.Tensor, stream=None):
+    psi = psi.contiguous()
+    out = torch.empty(3, dtype=torch.float64, device=psi.device)
+    v = torch.empty_like(psi)
+    _check(lib().nqs_energy_from_psi(C.byref(csr.s), _ptr(psi), psi.shape[0], _ptr(out), _ptr(v),
+                                     _stream(stream)), "nqs_energy_from_psi")
+    return out, v
+
+
+def energy_grad(problem: Problem, net: Net, csr: CSR, dets: torch.Tensor, with_grad=True,
+                o: Opts | None = None, stream=None, out=None, grad=None, psi=None):
+    """Returns (out[4] = E, N, D, max log|psi|, grad or None, psi~), all device tensors."""
+    dets = _dets(dets)
+    n = dets.shape[0]
+    dev = dets.device
+    out = out if out is not None else torch.empty(4, dtype=torch.float64, device=dev)
+    if with_grad and grad is None:
+        grad = torch.empty(net.num_params(), dtype=net.grad_dtype(), device=dev)
+    psi = psi if psi is not None else torch.empty(n, dtype=torch.float64, device=dev)
+    o = o or opts(precision=net.dtype, validate=0)
+    _check(lib().nqs_energy_grad(problem.handle, net.handle, C.byref(csr.s), _ptr(dets), n,
+                                 _ptr(out), _ptr(grad) if with_grad else None, _ptr(psi),
+                                 C.byref(o), _stream(stream)), "nqs_energy_grad")
+    return out, (grad if with_grad else None), psi
+
+
+def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, buckets: int = 1,
+        o: Opts | None = None, stream=None):
+    """Epstein-Nesbet PT2. Returns dict(ext, int, n_unique, n_emitted, partials[B,2])."""
+    import numpy as np
+    dets = _dets(dets)
+    psi = psi.contiguous()
+    o = o or opts(buckets=buckets)
+    out = np.zeros(4)
+    parts = np.zeros(2 * o.buckets)
+    _check(lib().nqs_pt2(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0], float(E), C.byref(o),
+                         out.ctypes.data_as(C.c_void_p), parts.ctypes.data_as(C.c_void_p),
+                         _stream(stream)), "nqs_pt2")
+    return dict(ext=out[0], int=out[1], n_unique=int(out[2]), n_emitted=int(out[3]),
+                partials=parts.reshape(-1, 2))
+
+
+def profile_enable(on: bool = True):
+    lib().nqs_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    lib().nqs_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kernel family: (total ms, launches)} for the instrumented launches since the reset."""
+    out = {}
+    for name in PROFILED:
+        ms = C.c_double(0)
+        n = C.c_int64(0)
+        _check(lib().nqs_profile_read(name.encode(), C.byref(ms), C.byref(n)), "nqs_profile_read")
+        out[name] = (ms.value, n.value)
+    return out
+
+
+def launch_count() -> int:
+    return lib().nqs_launch_count()
+
+
+class EnergyFunction(torch.autograd.Function):
+    """E_S as a differentiable function of the six trainable parameter tensors; the backward
+    returns the gradient computed by the hand-written adjoint in nqs_energy_grad."""
+
+    @staticmethod
+    def forward(ctx, problem, net, csr, dets, *params):
+        out, grad, _ = energy_grad(problem, net, csr, dets, with_grad=True)
+        ctx.net = net
+        ctx.save_for_backward(grad)
+        return out[0].clone()
+
+    @staticmethod
+    def backward(ctx, gE):
+        (grad,) = ctx.saved_tensors
+        parts = ctx.net.split(grad)
+        grads = [(g * gE).to(p.dtype) for g, p in zip(parts, ctx.net.params[:6])]
+        return (None, None, None, None, *grads)
+
+
+def energy(problem: Problem, net: Net, csr: CSR, dets: torch.Tensor) -> torch.Tensor:
+    """Differentiable E_S (autograd through the adjoint kernel)."""
+    return EnergyFunction.apply(problem, net, csr, dets, *net.params[:6])

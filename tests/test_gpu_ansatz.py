@@ -1,0 +1,148 @@
+"""GPU parity of amplitudes, E_S and its gradient against the oracle (FP64 form: 1e-8 Ha and
+tight gradient agreement; mixed form: 1e-6 Ha against the quantisation-matched oracle), and the
+adjoint against central finite differences, through the C ABI and the autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import need_gpu, nqs, problem_for, small_problem, to_dev
+from oracle import oracle as O
+from paper_2601_21310_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(name, mixed):
+    N = nqs()
+    p = synth.make_problem(name)
+    P = problem_for(N, p)
+    dt = N.NQS_MIXED if mixed else N.NQS_FP64
+    net = N.Net(P, N.net_tensors(p.net, dt), dt)
+    return N, p, P, net
+
+
+def test_amplitudes_fp64():
+    need_gpu()
+    N, p, P, net = _setup("tiny_n10", False)
+    la, sg, st = N.amplitudes(P, net, to_dev(p.S))
+    rla, rsg = O.amplitudes(O.Net(p.net), p.S)
+    assert st == 0
+    assert np.array_equal(sg.cpu().numpy(), rsg)
+    assert np.abs(la.cpu().numpy() - rla).max() < 1e-11
+
+
+def test_amplitudes_mixed_vs_quantised_oracle():
+    need_gpu()
+    N, p, P, net = _setup("small_n16", True)
+    la, sg, _ = N.amplitudes(P, net, to_dev(p.S))
+    rla, rsg = O.amplitudes(O.Net(p.net, quant=True), p.S)
+    assert np.array_equal(sg.cpu().numpy(), rsg)
+    # FP32 accumulation / FP32 LU against FP64: log|psi| agrees to ~1e-4 absolute
+    assert np.abs(la.cpu().numpy() - rla).max() < 5e-4
+
+
+@pytest.mark.parametrize("name", ["tiny_n10"])
+def test_energy_grad_fp64(name):
+    need_gpu()
+    N, p, P, net = _setup(name, False)
+    dets = to_dev(p.S)
+    csr = N.connections(P, dets)
+    out, grad, psi = N.energy_grad(P, net, csr, dets)
+    ref_csr = O.hss(p.wl.norb, p.h, p.eri, p.S)
+    ref = O.energy_grad(O.Net(p.net), p.S, ref_csr)
+    out = out.cpu().numpy()
+    assert abs(out[0] - ref["E"]) < 1e-8
+    assert abs(out[2] - ref["D"]) < 1e-10 * ref["D"]
+    assert out[3] == pytest.approx(ref["maxlog"], abs=1e-11)
+    assert np.abs(psi.cpu().numpy() - ref["psi"]).max() < 1e-10
+    g = grad.cpu().numpy()
+    rel = np.linalg.norm(g - ref["grad"]) / np.linalg.norm(ref["grad"])
+    assert rel < 1e-9, rel
+
+
+def test_energy_grad_mixed_vs_quantised_oracle():
+    need_gpu()
+    N, p, P, net = _setup("small_n16", True)
+    dets = to_dev(p.S)
+    csr = N.connections(P, dets)
+    out, grad, psi = N.energy_grad(P, net, csr, dets)
+    ref_csr = O.hss(16, p.h, p.eri, p.S)
+    refq = O.energy_grad(O.Net(p.net, quant=True), p.S, ref_csr)
+    out = out.cpu().numpy()
+    assert abs(out[0] - refq["E"]) < 1e-6, out[0] - refq["E"]
+    g = grad.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(g - refq["grad"]) / np.linalg.norm(refq["grad"])
+    assert rel < 1e-2, rel
+
+
+def test_energy_from_psi_eigenvector():
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("tiny_n10")
+    P = problem_for(N, p)
+    csr = N.connections(P, to_dev(p.S))
+    ref = O.hss(10, p.h, p.eri, p.S)
+    w, V = np.linalg.eigh(ref.to_scipy().toarray())
+    out, v = N.energy_from_psi(csr, torch.from_numpy(V[:, 0] * 2.5).cuda())
+    out = out.cpu().numpy()
+    assert abs(out[0] - w[0]) < 1e-10
+    ref_out, ref_v = O.energy_from_psi(ref, V[:, 0] * 2.5)
+    assert np.abs(v.cpu().numpy() - ref_v).max() < 1e-12
+
+
+def test_gradient_central_differences_gpu():
+    """GPU adjoint against central differences of the GPU energy (FP64 form, h = 1e-5, 64
+    parameters chosen with seed 7)."""
+    need_gpu()
+    N, p, P, net = _setup("tiny_n10", False)
+    dets = to_dev(p.S)
+    csr = N.connections(P, dets)
+    _, grad, _ = N.energy_grad(P, net, csr, dets)
+    g = grad.cpu().numpy()
+    flat_views = [t.view(-1) for t in net.params[:6]]
+    sizes = [t.numel() for t in flat_views]
+    offs = np.cumsum([0] + sizes)
+    rng = np.random.default_rng(7)
+    pick = rng.choice(offs[-1], size=64, replace=False)
+    fd = []
+    for k in pick:
+        li = int(np.searchsorted(offs, k, side="right") - 1)
+        j = int(k - offs[li])
+        t = flat_views[li]
+        orig = t[j].item()
+        t[j] = orig + 1e-5
+        ep = N.energy_grad(P, net, csr, dets, with_grad=False)[0][0].item()
+        t[j] = orig - 1e-5
+        em = N.energy_grad(P, net, csr, dets, with_grad=False)[0][0].item()
+        t[j] = orig
+        fd.append((ep - em) / 2e-5)
+    fd = np.array(fd)
+    rel = np.linalg.norm(fd - g[pick]) / np.linalg.norm(g[pick])
+    assert rel < 1e-6, rel
+
+
+def test_autograd_function():
+    need_gpu()
+    N, p, P, net = _setup("tiny_n10", False)
+    dets = to_dev(p.S)
+    csr = N.connections(P, dets)
+    for t in net.params[:6]:
+        t.requires_grad_(True)
+    E = N.energy(P, net, csr, dets)
+    E.backward()
+    _, grad, _ = N.energy_grad(P, net, csr, dets)
+    got = torch.cat([t.grad.reshape(-1) for t in net.params[:6]])
+    assert torch.equal(got, grad)
+
+
+def test_amplitudes_other_shapes():
+    need_gpu()
+    N = nqs()
+    for norb, na, nb, nS in [(12, 5, 4, 300), (20, 7, 7, 513)]:
+        p, nb = small_problem(norb, na, nS, 50 + norb, hidden=(48, 40), nb=nb)
+        P = N.Problem(norb, na, nb, p.h, p.eri)
+        net = N.Net(P, N.net_tensors(p.net, N.NQS_FP64), N.NQS_FP64)
+        la, sg, _ = N.amplitudes(P, net, to_dev(p.S))
+        rla, rsg = O.amplitudes(O.Net(p.net), p.S)
+        assert np.array_equal(sg.cpu().numpy(), rsg)
+        assert np.abs(la.cpu().numpy() - rla).max() < 1e-10
