@@ -70,54 +70,62 @@ def load_peaks():
 # clocks sampled during the timed region (read-only NVML queries)
 # ------------------------------------------------------------------------------------------
 class ClockSampler:
-    REASONS = {
-        0x0000000000000004: "sw_power_cap",
-        0x0000000000000008: "hw_slowdown",
-        0x0000000000000020: "sw_thermal_slowdown",
-        0x0000000000000040: "hw_thermal_slowdown",
-        0x0000000000000080: "hw_power_brake_slowdown",
-    }
+    """nvidia-smi sampled every 200 ms during the timed region (read-only queries), filtered to
+    this process's GPU by PCI bus id."""
+    FIELDS = ["pci.bus_id", "clocks.sm", "clocks.max.sm", "power.draw",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, index: int):
-        self.samples, self.reasons, self.max_mhz = [], set(), None
-        self._stop = threading.Event()
+    def __init__(self, device_index: int):
+        self.rows, self.err = [], None
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.bus = int(torch.cuda.get_device_properties(device_index).pci_bus_id)
         except Exception:
-            self.nv = None
-
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
-                r = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-                for bit, name in self.REASONS.items():
-                    if r & bit:
-                        self.reasons.add(name)
-            except Exception:
-                pass
-            time.sleep(0.05)
+            self.bus = None
 
     def __enter__(self):
-        if self.nv:
-            self.t = threading.Thread(target=self._run, daemon=True)
-            self.t.start()
+        import subprocess
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:  # no nvidia-smi: report no clocks
+            self.proc, self.err = None, str(e)
         return self
 
     def __exit__(self, *a):
-        if self.nv:
-            self._stop.set()
-            self.t.join()
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [[x.strip() for x in line.split(",")] for line in out.splitlines()]
+        rows = [r for r in rows if len(r) == len(self.FIELDS)]
+        buses = {r[0] for r in rows}
+        for r in rows:
+            try:
+                mine = self.bus is None or int(r[0].split(":")[1], 16) == self.bus
+            except (IndexError, ValueError):
+                mine = False
+            if mine or len(buses) == 1:
+                self.rows.append(r)
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons)}
-        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
-                "reasons": sorted(self.reasons)}
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "error": self.err}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = sorted({self.REASONS[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
 
 
 # ------------------------------------------------------------------------------------------

