@@ -172,6 +172,23 @@ int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64
             double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
             nqs_stream_t stream);
 
+/* H_SS build without any device allocation (the paper has no counterpart: this exists for
+ * callers that cannot allocate device memory, such as a host framework that owns every
+ * allocation or code that must not call the allocator while work is being recorded).
+ * Same result as nqs_connections, written into caller-owned device buffers: row_ptr
+ * [nS + 1] int64, col [capacity] int32, val [capacity] FP64. The library's scratch (hash table
+ * of S, row counts, scan partials) lives in one static device array of 4 MiB, which limits
+ * nS to 65536 (larger nS returns NQS_ERR_ARG with a message in nqs_last_error()). Every GPU
+ * that loads the library holds the array until process exit. The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current; make it
+ * before any stream capture. *nnz (host) receives the number of nonzeros; if it exceeds
+ * capacity the call returns NQS_ERR_ARG without writing col/val, so the caller can size the
+ * buffers and call again. All calls share the static array: calls that overlap on the GPU
+ * race and must be serialised. validate as in nqs_opts. Synchronises the stream. */
+int nqs_connections_noalloc(nqs_problem* problem, const uint64_t* dets, int64_t nS, int validate,
+                            int64_t* row_ptr, int32_t* col, double* val, int64_t capacity,
+                            int64_t* nnz, int64_t* n_enumerated, nqs_stream_t stream);
+
 /* Optional per-kernel timing for benchmarks (not part of the method): when enabled, the
  * library brackets its main kernel launches with CUDA events recorded on the launching stream.
  * nqs_profile_read synchronises those events and returns the summed milliseconds and the

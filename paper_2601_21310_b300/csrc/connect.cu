@@ -13,9 +13,6 @@
 #include "nqs_internal.cuh"
 #include "prof.cuh"
 
-#define CONN_THREADS 256
-#define CONN_WARPS (CONN_THREADS / 32)
-
 __global__ void __launch_bounds__(CONN_THREADS) k_conn_count(ProblemDev P, HashS H,
                                                               const ulonglong2* __restrict__ S,
                                                               int64_t nS, int64_t* rowcnt) {
@@ -92,6 +89,9 @@ static unsigned conn_grid(int64_t nS) {
     if (g > 148 * 16) g = 148 * 16;
     return (unsigned)(g < 1 ? 1 : g);
 }
+
+size_t conn_smem_bytes(const ProblemDev& P) { return conn_smem(P); }
+unsigned conn_grid_size(int64_t nS) { return conn_grid(nS); }
 
 extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
                                const nqs_opts* opts, nqs_csr* out, int64_t* n_enumerated,

@@ -14,6 +14,7 @@
 // error plumbing: every CUDA call is checked; a failure records a message and returns a code
 // ------------------------------------------------------------------------------------------
 void nqs_record_error(const char* what, cudaError_t e, const char* file, int line);
+void nqs_record_message(const char* msg);
 
 #define NQS_CK(call)                                                            \
     do {                                                                        \
@@ -71,13 +72,19 @@ struct nqs_net {
 int nqs_scratch_alloc(nqs_problem* p, void** ptr, size_t bytes, cudaStream_t s);
 void nqs_scratch_free(nqs_problem* p, void* ptr, cudaStream_t s);
 
-// RAII holder for scratch so that every early return frees what it took
+// RAII holder for scratch so that every early return frees what it took. With an arena (a
+// caller-supplied device region), get() hands out 256-byte aligned slices of it instead and
+// nothing is allocated or freed.
 struct Scratch {
     nqs_problem* p;
     cudaStream_t s;
     void* ptrs[64];
     int n = 0;
+    uint8_t* arena = nullptr;
+    size_t arena_size = 0, arena_used = 0;
     Scratch(nqs_problem* p_, cudaStream_t s_) : p(p_), s(s_) {}
+    Scratch(void* arena_, size_t size_, cudaStream_t s_)
+        : p(nullptr), s(s_), arena((uint8_t*)arena_), arena_size(size_) {}
     ~Scratch() {
         for (int i = n - 1; i >= 0; --i) nqs_scratch_free(p, ptrs[i], s);
     }
@@ -85,6 +92,13 @@ struct Scratch {
     int get(T** out, size_t count) {
         void* v = nullptr;
         if (count == 0) count = 1;
+        if (arena) {
+            size_t off = (arena_used + 255) & ~(size_t)255;
+            if (off + count * sizeof(T) > arena_size) return NQS_ERR_OOM;
+            arena_used = off + count * sizeof(T);
+            *out = (T*)(arena + off);
+            return NQS_OK;
+        }
         int st = nqs_scratch_alloc(p, &v, count * sizeof(T), s);
         if (st != NQS_OK) return st;
         if (n == 64) { nqs_scratch_free(p, v, s); return NQS_ERR_OOM; }
@@ -138,6 +152,17 @@ __device__ __forceinline__ int32_t hash_lookup(const HashS& H, uint64_t a, uint6
     }
     return -1;
 }
+
+// the H_SS enumeration kernels (connect.cu) and their launch shape
+#define CONN_THREADS 256
+#define CONN_WARPS (CONN_THREADS / 32)
+__global__ void k_conn_count(ProblemDev P, HashS H, const ulonglong2* __restrict__ S, int64_t nS,
+                             int64_t* rowcnt);
+__global__ void k_conn_fill(ProblemDev P, HashS H, const ulonglong2* __restrict__ S, int64_t nS,
+                            const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+                            double* __restrict__ val);
+size_t conn_smem_bytes(const ProblemDev& P);
+unsigned conn_grid_size(int64_t nS);
 
 int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, HashS* out,
                cudaStream_t s);

@@ -15,6 +15,8 @@ void nqs_record_error(const char* what, cudaError_t e, const char* file, int lin
              cudaGetErrorString(e), file, line);
 }
 
+void nqs_record_message(const char* msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
 extern "C" const char* nqs_last_error(void) { return g_last_error; }
 
 extern "C" const char* nqs_status_string(int status) {

@@ -63,6 +63,9 @@ EXPORTS = {
     "nqs_profile_reset": (C.c_int, []),
     "nqs_profile_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p]),
     "nqs_launch_count": (C.c_int64, []),
+    "nqs_connections_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
 }
 
 PROFILED = ["conn_count", "conn_fill", "pt2_count", "pt2_emit", "rs_hist", "rs_scatter",
@@ -270,6 +273,20 @@ def connections(problem: Problem, dets: torch.Tensor, o: Opts | None = None, str
                                  C.byref(o) if o else None, C.byref(st), C.byref(nen),
                                  _stream(stream)), "nqs_connections")
     return CSR(st, nen.value)
+
+
+def connections_noalloc(problem: Problem, dets: torch.Tensor, row_ptr: torch.Tensor,
+                        col: torch.Tensor, val: torch.Tensor, validate: bool = True, stream=None):
+    """H_SS into caller-owned buffers with the library's static scratch (no device
+    allocation). Returns (status, nnz, n_enumerated); a negative status is returned, not
+    raised, so that a caller can read the nnz it needs."""
+    dets = _dets(dets)
+    nnz = C.c_int64(0)
+    nen = C.c_int64(0)
+    st = lib().nqs_connections_noalloc(problem.handle, _ptr(dets), dets.shape[0], int(validate),
+                                       _ptr(row_ptr), _ptr(col), _ptr(val), col.numel(),
+                                       C.byref(nnz), C.byref(nen), _stream(stream))
+    return st, nnz.value, nen.value
 
 
 def amplitudes(problem: Problem, net: Net, dets: torch.Tensor, o: Opts | None = None,
