@@ -189,6 +189,15 @@ int nqs_connections_noalloc(nqs_problem* problem, const uint64_t* dets, int64_t 
                             int64_t* row_ptr, int32_t* col, double* val, int64_t capacity,
                             int64_t* nnz, int64_t* n_enumerated, nqs_stream_t stream);
 
+/* Plain library GEMM on the tensor cores used by the backflow network (not a step of the
+ * paper's method; exposed for testing and reuse): C[m][n] = sum_k A[m][k] B[n][k] with A
+ * [M][lda] and B [N][ldb] bfloat16, k contiguous (lda, ldb multiples of 8, 16-byte aligned
+ * bases), C [M][ldc] float, FP32 accumulation. err_flag (device int, may be NULL) is set to 1
+ * if a bounded pipeline wait timed out. Stream-ordered, no sync. Returns NQS_ERR_UNSUPPORTED
+ * for strides the tensor-memory-access unit cannot take. */
+int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
+                  float* C, int64_t ldc, int* err_flag, nqs_stream_t stream);
+
 /* Optional per-kernel timing for benchmarks (not part of the method): when enabled, the
  * library brackets its main kernel launches with CUDA events recorded on the launching stream.
  * nqs_profile_read synchronises those events and returns the summed milliseconds and the

@@ -359,8 +359,17 @@ static int launch_lu(nqs_net* net, const uint64_t* dets, int64_t M, const T* Phi
 // ------------------------------------------------------------------------------------------
 // forward: layer 1 gather, layers 2 and 3 as GEMMs, then the two LU factorisations
 // ------------------------------------------------------------------------------------------
+static bool tc_shapes_ok(const nqs_net* net) {
+    return net->dtype == NQS_MIXED && net->H1 % 8 == 0 && net->H2 % 8 == 0;
+}
+static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t M, Fwd& f,
+                            bool keep, double* logabs, int8_t* sign, cudaStream_t s);
+static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f,
+                             const double* w, void* grad, cudaStream_t s);
+
 int net_forward(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t M, Fwd& f,
                 bool keep, double* logabs, int8_t* sign, cudaStream_t s) {
+    if (tc_shapes_ok(net)) return forward_mixed_tc(net, sc, dets, M, f, keep, logabs, sign, s);
     const ProblemDev& P = net->prob->d;
     const bool mixed = net->dtype == NQS_MIXED;
     const int H1 = net->H1, H2 = net->H2, nin = net->nin, nout = net->nout;
@@ -465,7 +474,8 @@ __device__ __forceinline__ __nv_bfloat16 grad_from_double<__nv_bfloat16>(double 
 template <class T, class TG>
 __global__ void k_adjoint(const ulonglong2* __restrict__ dets, int64_t M, int norb, int na,
                           int nb, const double* __restrict__ w, const T* __restrict__ Ainv_a,
-                          const T* __restrict__ Ainv_b, TG* __restrict__ dPhi) {
+                          const T* __restrict__ Ainv_b, TG* __restrict__ dPhi, int64_t ldp,
+                          TG* __restrict__ dPhiT, int64_t ldt) {
     const int nel = na + nb;
     const int per = na * na + nb * nb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M * per;
@@ -483,8 +493,10 @@ __global__ void k_adjoint(const ulonglong2* __restrict__ dets, int64_t M, int no
         int orb = __ffsll((long long)v) - 1;
         const T* inv = (spin == 0 ? Ainv_a + m * na * na : Ainv_b + m * nb * nb);
         double g = w[m] * (double)inv[k * n + j];
-        dPhi[m * (int64_t)norb * nel + (int64_t)orb * nel + (spin == 0 ? 0 : na) + k] =
-            grad_from_double<TG>(g);
+        const int64_t o = (int64_t)orb * nel + (spin == 0 ? 0 : na) + k;
+        const TG gv = grad_from_double<TG>(g);
+        dPhi[m * ldp + o] = gv;
+        if (dPhiT) dPhiT[o * ldt + m] = gv;
     }
 }
 
@@ -527,6 +539,7 @@ static int colsum(Scratch& sc, const void* X, int64_t M, int N, void* out, cudaS
 
 int net_backward(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f, const double* w,
                  void* grad, cudaStream_t s) {
+    if (f.tc) return backward_mixed_tc(net, sc, dets, f, w, grad, s);
     const ProblemDev& P = net->prob->d;
     const bool mixed = net->dtype == NQS_MIXED;
     const int64_t M = f.M;
@@ -549,11 +562,11 @@ int net_backward(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f, 
     if (mixed)
         k_adjoint<float, __nv_bfloat16><<<grid_for(M * per, 256, 148 * 64), 256, 0, s>>>(
             D2, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a, (const float*)f.Ainv_b,
-            (__nv_bfloat16*)dPhi);
+            (__nv_bfloat16*)dPhi, nout, nullptr, 0);
     else
         k_adjoint<double, double><<<grid_for(M * per, 256, 148 * 64), 256, 0, s>>>(
             D2, M, P.norb, P.na, P.nb, w, (const double*)f.Ainv_a, (const double*)f.Ainv_b,
-            (double*)dPhi);
+            (double*)dPhi, nout, nullptr, 0);
     NQS_CK_LAUNCH();
     auto gemm = [&](const GemmArgs& g, bool out_act) -> int {
         return mixed ? gemm_mixed(g, out_act, s) : gemm_f64(g, s);
@@ -602,5 +615,246 @@ int net_backward(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f, 
         NQS_TRY((colsum<double, double>(sc, dZ2, M, H2, gb2, s)));
         NQS_TRY((colsum<double, double>(sc, dZ1, M, H1, gb1, s)));
     }
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// mixed form on tensor cores (tcgen05): every GEMM operand is K-major, so the activations
+// that later act as the reduction operand of a weight gradient (K = |S|) are also kept
+// transposed ([H][ldM], ldM = |S| rounded up to 8 for 16-byte TMA strides).
+// ------------------------------------------------------------------------------------------
+// dst[c][r] = src[r][c] for a bf16 matrix, 32x32 tiles through shared memory
+__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ src, int64_t R, int64_t Cn,
+                                 int64_t lds, __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+    __shared__ unsigned short tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const unsigned short* S = (const unsigned short*)src;
+    unsigned short* D = (unsigned short*)dst;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        int64_t r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < R && c < Cn) ? S[r * lds + c] : (unsigned short)0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < Cn && r < R) D[c * ldd + r] = tile[threadIdx.x][i];
+    }
+}
+
+static int transpose_bf16(const void* src, int64_t R, int64_t Cn, int64_t lds, void* dst,
+                          int64_t ldd, cudaStream_t s) {
+    dim3 grid((unsigned)((Cn + 31) / 32), (unsigned)((R + 31) / 32));
+    k_transpose_bf16<<<grid, dim3(32, 8), 0, s>>>((const __nv_bfloat16*)src, R, Cn, lds,
+                                                  (__nv_bfloat16*)dst, ldd);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// X^T[i][m]: input bit i of det m (alpha bits 0..norb-1, then beta)
+__global__ void k_bitsT(const ulonglong2* __restrict__ dets, int64_t M, int norb,
+                        __nv_bfloat16* __restrict__ XT, int64_t ldM) {
+    const int nin = 2 * norb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M * nin;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(t / M);
+        int64_t m = t - (int64_t)i * M;
+        ulonglong2 x = dets[m];
+        uint64_t word = i < norb ? x.x : x.y;
+        int bit = i < norb ? i : i - norb;
+        XT[(int64_t)i * ldM + m] = __float2bfloat16_rn((float)((word >> bit) & 1ull));
+    }
+}
+
+// out[r] = sum over the first M entries of row r of X [R][ld] (bf16), FP32, fixed order
+__global__ void k_rowsum_bf16(const __nv_bfloat16* __restrict__ X, int R, int64_t M, int64_t ld,
+                              float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < R;
+         r += (gridDim.x * blockDim.x) >> 5) {
+        const __nv_bfloat16* row = X + (int64_t)r * ld;
+        float acc = 0.f;
+        for (int64_t m = lane; m < M; m += 32) acc += __bfloat162float(row[m]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+        if (lane == 0) out[r] = acc;
+    }
+}
+
+static int rowsum_bf16(const void* X, int R, int64_t M, int64_t ld, float* out, cudaStream_t s) {
+    k_rowsum_bf16<<<grid_for((int64_t)R * 32, 256), 256, 0, s>>>((const __nv_bfloat16*)X, R, M, ld,
+                                                                 out);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t M, Fwd& f,
+                            bool keep, double* logabs, int8_t* sign, cudaStream_t s) {
+    const ProblemDev& P = net->prob->d;
+    const int H1 = net->H1, H2 = net->H2, nin = net->nin, nout = net->nout;
+    memset(&f, 0, sizeof f);
+    f.M = M;
+    f.tc = true;
+    f.ldM = (M + 7) & ~(int64_t)7;
+    f.logabs = logabs;
+    f.sign = sign;
+    f.err = net->prob->err_word;
+    NQS_TRY(sc.get((__nv_bfloat16**)&f.H1, M * H1));
+    NQS_TRY(sc.get((__nv_bfloat16**)&f.H2, M * H2));
+    NQS_TRY(sc.get((float**)&f.Phi, M * nout));
+    if (keep) {
+        NQS_TRY(sc.get((__nv_bfloat16**)&f.H1T, (size_t)H1 * f.ldM));
+        NQS_TRY(sc.get((__nv_bfloat16**)&f.H2T, (size_t)H2 * f.ldM));
+        NQS_TRY(sc.get((__nv_bfloat16**)&f.XT, (size_t)nin * f.ldM));
+        NQS_TRY(sc.get((float**)&f.Ainv_a, M * P.na * P.na));
+        NQS_TRY(sc.get((float**)&f.Ainv_b, M * P.nb * P.nb));
+    }
+    NQS_TRY(sc.get(&f.singular, 1));
+    NQS_CK(cudaMemsetAsync(f.singular, 0, sizeof(int), s));
+    const ulonglong2* D2 = (const ulonglong2*)dets;
+    k_layer1<__nv_bfloat16, float, __nv_bfloat16><<<grid_for(M * H1, 256, 148 * 64), 256, 0, s>>>(
+        D2, M, P.norb, H1, (const __nv_bfloat16*)net->p[0], (const float*)net->p[1],
+        (__nv_bfloat16*)f.H1, nullptr);
+    NQS_CK_LAUNCH();
+    if (keep) {
+        NQS_TRY(transpose_bf16(f.H1, M, H1, H1, f.H1T, f.ldM, s));
+        k_bitsT<<<grid_for(M * nin, 256), 256, 0, s>>>(D2, M, P.norb, (__nv_bfloat16*)f.XT, f.ldM);
+        NQS_CK_LAUNCH();
+    }
+    TcGemm g;
+    memset(&g, 0, sizeof g);
+    g.err = f.err;
+    // layer 2: H2 = tanh(H1 W2^T + b2), with the transposed copy for dW3
+    g.A = (const __nv_bfloat16*)f.H1;
+    g.lda = H1;
+    g.B = (const __nv_bfloat16*)net->p[2];
+    g.ldb = H1;
+    g.M = (int)M;
+    g.N = H2;
+    g.K = H1;
+    g.epi = EPI_BIAS_TANH;
+    g.bias = (const float*)net->p[3];
+    g.C = f.H2;
+    g.ldc = H2;
+    g.c_bf16 = 1;
+    g.CT = keep ? (__nv_bfloat16*)f.H2T : nullptr;
+    g.ldct = f.ldM;
+    NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
+    // layer 3: Phi = Phi0 + (H2 W3^T + b3)
+    memset(&g, 0, sizeof g);
+    g.err = f.err;
+    g.A = (const __nv_bfloat16*)f.H2;
+    g.lda = H2;
+    g.B = (const __nv_bfloat16*)net->p[4];
+    g.ldb = H2;
+    g.M = (int)M;
+    g.N = nout;
+    g.K = H2;
+    g.epi = EPI_BIAS_PHI0;
+    g.bias = (const float*)net->p[5];
+    g.phi0 = (const float*)net->p[6];
+    g.C = f.Phi;
+    g.ldc = nout;
+    NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
+    double* la2;
+    int8_t* sg2;
+    NQS_TRY(sc.get(&la2, 2 * M));
+    NQS_TRY(sc.get(&sg2, 2 * M));
+    NQS_TRY(launch_lu<float>(net, dets, M, (const float*)f.Phi, la2, sg2, (float*)f.Ainv_a,
+                             (float*)f.Ainv_b, f.singular, s));
+    k_combine<<<grid_for(M, 256), 256, 0, s>>>(M, la2, sg2, logabs, sign);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f,
+                             const double* w, void* grad, cudaStream_t s) {
+    const ProblemDev& P = net->prob->d;
+    const int64_t M = f.M, ldM = f.ldM;
+    const int H1 = net->H1, H2 = net->H2, nin = net->nin, nout = net->nout;
+    const int64_t ldP = (nout + 7) & ~7;
+    float* G = (float*)grad;
+    float* gW1 = G;
+    float* gb1 = gW1 + (size_t)H1 * nin;
+    float* gW2 = gb1 + H1;
+    float* gb2 = gW2 + (size_t)H2 * H1;
+    float* gW3 = gb2 + H2;
+    float* gb3 = gW3 + (size_t)nout * H2;
+    __nv_bfloat16 *dPhi, *dPhiT, *W3T, *W2T, *dZ2, *dZ2T, *dZ1T;
+    NQS_TRY(sc.get(&dPhi, M * ldP));
+    NQS_TRY(sc.get(&dPhiT, (size_t)nout * ldM));
+    NQS_TRY(sc.get(&W3T, (size_t)H2 * ldP));
+    NQS_TRY(sc.get(&W2T, (size_t)H1 * H2));
+    NQS_TRY(sc.get(&dZ2, M * H2));
+    NQS_TRY(sc.get(&dZ2T, (size_t)H2 * ldM));
+    NQS_TRY(sc.get(&dZ1T, (size_t)H1 * ldM));
+    NQS_CK(cudaMemsetAsync(dPhi, 0, M * ldP * 2, s));
+    NQS_CK(cudaMemsetAsync(dPhiT, 0, (size_t)nout * ldM * 2, s));
+    const int64_t per = (int64_t)P.na * P.na + (int64_t)P.nb * P.nb;
+    k_adjoint<float, __nv_bfloat16><<<grid_for(M * per, 256, 148 * 64), 256, 0, s>>>(
+        (const ulonglong2*)dets, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a,
+        (const float*)f.Ainv_b, dPhi, ldP, dPhiT, ldM);
+    NQS_CK_LAUNCH();
+    NQS_TRY(transpose_bf16(net->p[4], nout, H2, H2, W3T, ldP, s));  // W3 [nout][H2] -> [H2][nout]
+    NQS_TRY(transpose_bf16(net->p[2], H2, H1, H1, W2T, H2, s));     // W2 [H2][H1] -> [H1][H2]
+    TcGemm g;
+    // dZ2 = (dPhi W3) * (1 - H2^2), row-major and transposed
+    memset(&g, 0, sizeof g);
+    g.err = f.err;
+    g.A = dPhi;
+    g.lda = ldP;
+    g.B = W3T;
+    g.ldb = ldP;
+    g.M = (int)M;
+    g.N = H2;
+    g.K = nout;
+    g.epi = EPI_TANH_BWD;
+    g.aux = (const __nv_bfloat16*)f.H2;
+    g.ld_aux = H2;
+    g.C = dZ2;
+    g.ldc = H2;
+    g.c_bf16 = 1;
+    g.CT = dZ2T;
+    g.ldct = ldM;
+    NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
+    // dZ1^T = ((dZ2 W2) * (1 - H1^2))^T
+    memset(&g, 0, sizeof g);
+    g.err = f.err;
+    g.A = dZ2;
+    g.lda = H2;
+    g.B = W2T;
+    g.ldb = H2;
+    g.M = (int)M;
+    g.N = H1;
+    g.K = H2;
+    g.epi = EPI_TANH_BWD;
+    g.aux = (const __nv_bfloat16*)f.H1;
+    g.ld_aux = H1;
+    g.CT = dZ1T;
+    g.ldct = ldM;
+    NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
+    // weight gradients: reductions over |S| (K = M), split across CTAs
+    auto wgrad = [&](const __nv_bfloat16* At, int rows, const __nv_bfloat16* Bt, int cols,
+                     float* out) -> int {
+        TcGemm q;
+        memset(&q, 0, sizeof q);
+        q.err = f.err;
+        q.A = At;
+        q.lda = ldM;
+        q.B = Bt;
+        q.ldb = ldM;
+        q.M = rows;
+        q.N = cols;
+        q.K = (int)M;
+        q.epi = EPI_STORE;
+        q.C = out;
+        q.ldc = cols;
+        return gemm_bf16_tcgen05(q, sc, s);
+    };
+    NQS_TRY(wgrad(dPhiT, nout, (const __nv_bfloat16*)f.H2T, H2, gW3));
+    NQS_TRY(wgrad(dZ2T, H2, (const __nv_bfloat16*)f.H1T, H1, gW2));
+    NQS_TRY(wgrad(dZ1T, H1, (const __nv_bfloat16*)f.XT, nin, gW1));
+    NQS_TRY(rowsum_bf16(dPhiT, nout, M, ldM, gb3, s));
+    NQS_TRY(rowsum_bf16(dZ2T, H2, M, ldM, gb2, s));
+    NQS_TRY(rowsum_bf16(dZ1T, H1, M, ldM, gb1, s));
     return NQS_OK;
 }

@@ -27,6 +27,29 @@ int gemm_bf16_simt(const GemmArgs& g, bool out_bf16, cudaStream_t s);
 // tcgen05 tensor-core path (gemm_tc.cu): returns NQS_ERR_UNSUPPORTED for shapes it does not take
 int gemm_bf16_tc(const GemmArgs& g, bool out_bf16, cudaStream_t s);
 
+// tcgen05 path (gemm_tc.cu): C[m][n] = epi(sum_k A[m][k] B[n][k]), A [M][lda] and B [N][ldb]
+// bfloat16 with k contiguous (lda, ldb multiples of 8). Optional row-major C (bf16 or float)
+// and transposed bf16 copy CT[n][m]. EPI_STORE with float C may split K across CTAs.
+struct TcGemm {
+    const __nv_bfloat16* A;
+    int64_t lda;
+    const __nv_bfloat16* B;
+    int64_t ldb;
+    int M, N, K;
+    int epi;
+    void* C;
+    int64_t ldc;
+    int c_bf16;
+    __nv_bfloat16* CT;
+    int64_t ldct;
+    const float* bias;
+    const float* phi0;
+    const __nv_bfloat16* aux;
+    int64_t ld_aux;
+    int* err;
+};
+int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s);
+
 // forward intermediates kept for the backward
 struct Fwd {
     int64_t M;
@@ -39,6 +62,13 @@ struct Fwd {
     double* logabs; // [M]
     int8_t* sign;   // [M]
     int* singular;  // device flag
+    // mixed form on tensor cores: transposed copies ([H][ldM], ldM = M rounded up to 8)
+    bool tc;
+    int64_t ldM;
+    void* H1T;
+    void* H2T;
+    void* XT;       // [nin][ldM]
+    int* err;       // tensor-core pipeline error word
 };
 
 int net_forward(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t M, Fwd& f,

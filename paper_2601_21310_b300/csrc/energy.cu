@@ -132,7 +132,7 @@ extern "C" int nqs_amplitudes(nqs_problem* p, nqs_net* net, const uint64_t* dets
     NQS_TRY(net_forward(net, sc, dets, nS, f, false, logabs, sign, s));
     int sing = 0;
     NQS_CK(cudaMemcpyAsync(&sing, f.singular, sizeof sing, cudaMemcpyDeviceToHost, s));
-    NQS_CK(cudaStreamSynchronize(s));
+    NQS_TRY(check_err_word(p, s));
     return sing ? NQS_WARN_SINGULAR : NQS_OK;
 }
 
@@ -167,5 +167,7 @@ extern "C" int nqs_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr* csr,
         NQS_CK_LAUNCH();
         NQS_TRY(net_backward(net, sc, dets, f, w, grad, s));
     }
+    // with validation on, synchronise and report a timed-out tensor-core wait
+    if (opts && opts->validate) NQS_TRY(check_err_word(p, s));
     return NQS_OK;
 }

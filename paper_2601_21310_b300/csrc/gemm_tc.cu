@@ -1,10 +1,457 @@
-// tcgen05 BF16 GEMM for the dense backflow layers (placeholder until the tensor-core kernel
-// lands: every shape is declined and the SIMT kernel runs).
+// BF16 tensor-core GEMM for the dense backflow layers on sm_103a (5th-generation tensor cores):
+//   C[m][n] = epilogue( sum_k A[m][k] * B[n][k] ),  A, B bfloat16, K-major (k contiguous),
+//   FP32 accumulation in tensor memory.
+//
+// One CTA computes a 128 x BN output tile with 4 warps:
+//   warp 0 / lane 0  TMA producer: 128x64 (A) and BNx64 (B) tiles, 128-byte swizzle, into a
+//                    3-stage shared-memory ring guarded by mbarriers (full / empty);
+//   warp 1 / lane 0  MMA issuer: tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN, K=16) x 4 per
+//                    stage, accumulating in TMEM; tcgen05.commit frees the stage;
+//   all 4 warps      epilogue: tcgen05.ld (32 lanes x 32 columns per load, warp w owns TMEM
+//                    lanes 32w..32w+31 = tile rows), fused bias / tanh / Phi0 / tanh'
+//                    epilogues, row-major and (optionally) transposed stores.
+// Split-K (grid.z) writes FP32 partials that a second kernel sums in a fixed order.
+// Every mbarrier wait is bounded (about 2 s of clock); a timeout sets the error word, skips the
+// remaining work and still releases the tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
+#include <mutex>
+
 #include "ansatz.cuh"
+#include "nqs_internal.cuh"
+#include "prof.cuh"
+
+#define TC_THREADS 128
+#define TC_STAGES 3
+#define TC_BK 64  // bf16 elements per 128-byte swizzle row
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait on the given phase parity; false after ~2 s of SM clock
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > 4000000000ll) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused when swizzled)
+    d |= (uint64_t)(1024u >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // swizzle: 128 B
+    return d;
+}
+
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both operands K-major
+template <int BN>
+__device__ __forceinline__ uint32_t idesc_bf16() {
+    return (1u << 4)            // D format: F32
+           | (1u << 7)          // A format: BF16
+           | (1u << 10)         // B format: BF16
+           | ((uint32_t)(BN >> 3) << 17)   // N / 8
+           | ((uint32_t)(128 >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+    int M, N, K;
+    int epi;                 // EPI_* (ansatz.cuh)
+    void* C;                 // [M][ldc] (bf16 if c_bf16 else float), may be null
+    int64_t ldc;
+    int c_bf16;
+    __nv_bfloat16* CT;       // [N][ldct] transposed bf16 copy, may be null
+    int64_t ldct;
+    const float* bias;       // [N]
+    const float* phi0;       // [N]
+    const __nv_bfloat16* aux;  // [M][ld_aux] activation for tanh'
+    int64_t ld_aux;
+    float* partial;          // split-K partials [gridDim.z][M][N]
+    int* err;
+};
+
+template <int BN>
+struct TcSmem {
+    static constexpr int A_BYTES = 128 * TC_BK * 2;
+    static constexpr int B_BYTES = BN * TC_BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int BYTES = TC_STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              TcArgs a) {
+    using L = TcSmem<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + TC_STAGES * L::STAGE);
+    uint64_t* empty = full + TC_STAGES;
+    uint64_t* done = empty + TC_STAGES;
+    uint32_t* tslot = (uint32_t*)(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * 128;
+    const int nkb = (a.K + TC_BK - 1) / TC_BK;
+    const int per = (nkb + gridDim.z - 1) / gridDim.z;
+    const int kb0 = blockIdx.z * per;
+    const int nk = max(0, min(nkb, kb0 + per) - kb0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(tslot)),
+            "r"((uint32_t)BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+
+    if (nk > 0 && warp == 0 && lane == 0) {
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TC_STAGES;
+            const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+            if (i >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+                ok = false;
+                break;
+            }
+            uint8_t* st = smem + s * L::STAGE;
+            mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
+            tma_load_2d(st, &tmA, &full[s], (kb0 + i) * TC_BK, m0);
+            tma_load_2d(st + L::A_BYTES, &tmB, &full[s], (kb0 + i) * TC_BK, n0);
+        }
+    } else if (nk > 0 && warp == 1 && lane == 0) {
+        const uint32_t idesc = idesc_bf16<BN>();
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % TC_STAGES;
+            const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint8_t* st = smem + s * L::STAGE;
+            const uint64_t da = sdesc_sw128(smem_u32(st));
+            const uint64_t db = sdesc_sw128(smem_u32(st + L::A_BYTES));
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)  // +32 bytes per K=16 step inside the atom
+                umma(tmem, da + 2 * kk, db + 2 * kk, idesc, (i | kk) != 0 ? 1u : 0u);
+            umma_commit(&empty[s]);
+        }
+        umma_commit(done);
+    }
+    __syncwarp();
+    if (nk > 0 && !mbar_wait(done, 0)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok && a.err) atomicExch(a.err, 1);
+
+    // ---------------- epilogue: thread owns tile row m0 + 32 warp + lane ----------------
+    const int row = m0 + warp * 32 + lane;
+    const bool row_ok = row < a.M;
+    const bool split = gridDim.z > 1;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        if (nk > 0 && ok) {
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) r[j] = 0u;
+        }
+        const int nb = n0 + c;
+        if (split) {
+            float* P = a.partial + (size_t)blockIdx.z * a.M * a.N;
+            if (row_ok)
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (nb + j < a.N) P[(size_t)row * a.N + nb + j] = __uint_as_float(r[j]);
+            continue;
+        }
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int n = nb + j;
+            float x = __uint_as_float(r[j]);
+            if (n < a.N && row_ok) {
+                if (a.epi == EPI_BIAS_TANH) {
+                    x = tanhf(x + a.bias[n]);
+                } else if (a.epi == EPI_BIAS_PHI0) {
+                    float z = x + a.bias[n];
+                    x = a.phi0[n] + z;
+                } else if (a.epi == EPI_TANH_BWD) {
+                    float h = __bfloat162float(a.aux[(size_t)row * a.ld_aux + n]);
+                    x = x * (1.0f - h * h);
+                }
+            }
+            v[j] = x;
+        }
+        if (row_ok && a.C) {
+            if (a.c_bf16) {
+                __nv_bfloat16* C = (__nv_bfloat16*)a.C + (size_t)row * a.ldc;
+                if (nb + 32 <= a.N && (a.ldc % 8) == 0) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint4 pk;
+                        uint32_t* w = (uint32_t*)&pk;
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[q * 8 + 2 * t],
+                                                                      v[q * 8 + 2 * t + 1]);
+                            w[t] = *(uint32_t*)&h2;
+                        }
+                        *(uint4*)(C + nb + q * 8) = pk;
+                    }
+                } else {
+                    for (int j = 0; j < 32; ++j)
+                        if (nb + j < a.N) C[nb + j] = __float2bfloat16_rn(v[j]);
+                }
+            } else {
+                float* C = (float*)a.C + (size_t)row * a.ldc;
+                if (nb + 32 <= a.N && (a.ldc % 4) == 0) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        *(float4*)(C + nb + q * 4) =
+                            make_float4(v[q * 4], v[q * 4 + 1], v[q * 4 + 2], v[q * 4 + 3]);
+                } else {
+                    for (int j = 0; j < 32; ++j)
+                        if (nb + j < a.N) C[nb + j] = v[j];
+                }
+            }
+        }
+        if (row_ok && a.CT) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (nb + j < a.N) a.CT[(size_t)(nb + j) * a.ldct + row] = __float2bfloat16_rn(v[j]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)BN));
+}
+
+// C[m][n] = sum over splits of P[z][m][n] (fixed order)
+__global__ void k_splitk_reduce(const float* __restrict__ P, int splits, int M, int N,
+                                float* __restrict__ C, int64_t ldc) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += P[(size_t)z * total + t];
+        const int64_t m = t / N, n = t - m * N;
+        C[m * ldc + n] = s;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+int get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_encode ? NQS_OK : NQS_ERR_CUDA;
+}
+
+// 2-D bf16 tensor map over [rows][ld] (k contiguous) with a box of box_rows x 64
+int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld,
+             int box_rows) {
+    NQS_TRY(get_encoder());
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box,
+                          es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        nqs_record_message("cuTensorMapEncodeTiled rejected a GEMM operand");
+        return NQS_ERR_CUDA;
+    }
+    return NQS_OK;
+}
+
+template <int BN>
+int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int splits,
+              cudaStream_t s) {
+    const int smem = TcSmem<BN>::BYTES;
+    NQS_CK(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid((a.N + BN - 1) / BN, (a.M + 127) / 128, splits);
+    {
+        ProfScope prof_(PROF_GEMM, s);
+        k_gemm_tc<BN><<<grid, TC_THREADS, smem, s>>>(ta, tb, a);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+}  // namespace
+
+// Tensor-core GEMM for row-major K-major operands: see gemm_bf16_tcgen05 in ansatz.cuh.
+int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0) return NQS_ERR_ARG;
+    if ((g.lda * 2) % 16 || (g.ldb * 2) % 16 || ((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15))
+        return NQS_ERR_UNSUPPORTED;
+    const int BN = g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256);
+    CUtensorMap ta, tb;
+    NQS_TRY(make_map(&ta, g.A, g.M, g.K, g.lda, 128));
+    NQS_TRY(make_map(&tb, g.B, g.N, g.K, g.ldb, BN));
+    TcArgs a;
+    memset(&a, 0, sizeof a);
+    a.M = g.M;
+    a.N = g.N;
+    a.K = g.K;
+    a.epi = g.epi;
+    a.C = g.C;
+    a.ldc = g.ldc;
+    a.c_bf16 = g.c_bf16;
+    a.CT = g.CT;
+    a.ldct = g.ldct;
+    a.bias = g.bias;
+    a.phi0 = g.phi0;
+    a.aux = g.aux;
+    a.ld_aux = g.ld_aux;
+    a.err = g.err;
+    // split K when the output has too few tiles to fill the GPU
+    const int tiles = ((g.N + BN - 1) / BN) * ((g.M + 127) / 128);
+    const int nkb = (g.K + TC_BK - 1) / TC_BK;
+    int splits = 1;
+    if (g.epi == EPI_STORE && !g.CT && !g.c_bf16) {
+        while (tiles * splits < 148 && splits * 2 <= nkb && splits < 64) splits *= 2;
+    }
+    if (splits > 1) {
+        NQS_TRY(sc.get(&a.partial, (size_t)splits * g.M * g.N));
+        // ceil split so that no split is empty
+        const int per = (nkb + splits - 1) / splits;
+        splits = (nkb + per - 1) / per;
+    }
+    int st = BN == 64 ? launch_tc<64>(ta, tb, a, splits, s)
+                      : (BN == 128 ? launch_tc<128>(ta, tb, a, splits, s)
+                                   : launch_tc<256>(ta, tb, a, splits, s));
+    NQS_TRY(st);
+    if (splits > 1) {
+        k_splitk_reduce<<<grid_for((int64_t)g.M * g.N, 256), 256, 0, s>>>(
+            a.partial, splits, g.M, g.N, (float*)g.C, g.ldc);
+        NQS_CK_LAUNCH();
+    }
+    return NQS_OK;
+}
 
 int gemm_bf16_tc(const GemmArgs& g, bool out_bf16, cudaStream_t s) {
     (void)g;
     (void)out_bf16;
     (void)s;
-    return NQS_ERR_UNSUPPORTED;
+    return NQS_ERR_UNSUPPORTED;  // the mixed path calls gemm_bf16_tcgen05 directly
+}
+
+// ------------------------------------------------------------------------------------------
+// C ABI: plain library GEMM C = A B^T (bf16 in, FP32 out), the same kernel the network uses
+// ------------------------------------------------------------------------------------------
+extern "C" int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N,
+                             int K, float* C, int64_t ldc, int* err_flag, nqs_stream_t stream) {
+    if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0) return NQS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    nqs_problem host;
+    memset(&host, 0, sizeof host);
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    NQS_CK(cudaDeviceGetDefaultMemPool(&host.pool, dev));
+    Scratch sc(&host, s);
+    TcGemm g;
+    memset(&g, 0, sizeof g);
+    g.A = (const __nv_bfloat16*)A;
+    g.lda = lda;
+    g.B = (const __nv_bfloat16*)B;
+    g.ldb = ldb;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.epi = EPI_STORE;
+    g.C = C;
+    g.ldc = ldc;
+    g.err = err_flag;
+    return gemm_bf16_tcgen05(g, sc, s);
 }

@@ -60,7 +60,11 @@ struct nqs_problem {
     double ecore;
     double *h, *eri, *J, *K, *TJ, *TK;
     cudaMemPool_t pool;  // library-owned stream-ordered pool for per-call scratch
+    int* err_word;       // device: set by a kernel whose bounded wait timed out
 };
+
+// read and clear the problem's device error word (synchronises the stream)
+int check_err_word(nqs_problem* p, cudaStream_t s);
 
 struct nqs_net {
     nqs_problem* prob;

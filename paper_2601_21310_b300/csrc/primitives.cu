@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restri
     counts[(int64_t)threadIdx.x * T + blockIdx.x] = hist[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __restrict__ kin,
+__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const uint64_t* __restrict__ kin,
                                                             const double* __restrict__ vin,
                                                             uint64_t* __restrict__ kout,
                                                             double* __restrict__ vout, int64_t n,
@@ -267,15 +267,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + warp * (RS_ITEMS * 32);
+    // keys stay in registers; each value is read once, at scatter time (same coalesced pattern)
     uint64_t key[RS_ITEMS];
-    double val[RS_ITEMS];
     uint32_t rank[RS_ITEMS];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         int64_t i = wbase + k * 32 + lane;
-        bool v = i < n;
-        key[k] = v ? kin[i] : 0ull;
-        val[k] = v ? vin[i] : 0.0;
+        key[k] = i < n ? kin[i] : 0ull;
     }
     const unsigned lt = lanemask_lt();
 #pragma unroll
@@ -309,7 +307,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
             uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
             uint32_t pos = toff[d] + whist[warp][d] + rank[k];
             kout[pos] = key[k];
-            vout[pos] = val[k];
+            vout[pos] = vin[i];
         }
     }
 }

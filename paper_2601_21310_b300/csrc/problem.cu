@@ -124,6 +124,11 @@ extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double*
     }
     uint64_t thresh = ~0ull;  // keep freed scratch in the pool between calls
     cudaMemPoolSetAttribute(p->pool, cudaMemPoolAttrReleaseThreshold, &thresh);
+    if (cudaMalloc(&p->err_word, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->err_word, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NQS_ERR_OOM);
+    }
 
     ProblemDev& d = p->d;
     d.norb = norb;
@@ -157,8 +162,21 @@ extern "C" int nqs_problem_destroy(nqs_problem* p) {
     cudaFree(p->K);
     cudaFree(p->TJ);
     cudaFree(p->TK);
+    cudaFree(p->err_word);
     if (p->pool) cudaMemPoolDestroy(p->pool);
     free(p);
+    return NQS_OK;
+}
+
+int check_err_word(nqs_problem* p, cudaStream_t s) {
+    int h = 0;
+    NQS_CK(cudaMemcpyAsync(&h, p->err_word, sizeof h, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    if (h) {
+        NQS_CK(cudaMemsetAsync(p->err_word, 0, sizeof(int), s));
+        nqs_record_message("a tensor-core pipeline wait timed out; results are invalid");
+        return NQS_ERR_TIMEOUT;
+    }
     return NQS_OK;
 }
 

@@ -63,6 +63,8 @@ EXPORTS = {
     "nqs_profile_reset": (C.c_int, []),
     "nqs_profile_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p]),
     "nqs_launch_count": (C.c_int64, []),
+    "nqs_gemm_bf16": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_int,
+                                C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "nqs_connections_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                           C.c_void_p, C.c_void_p]),
@@ -341,6 +343,20 @@ def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, bucke
                          _stream(stream)), "nqs_pt2")
     return dict(ext=out[0], int=out[1], n_unique=int(out[2]), n_emitted=int(out[3]),
                 partials=parts.reshape(-1, 2))
+
+
+def gemm_bf16(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
+    """C = A B^T on the tcgen05 tensor-core kernel (A [M][K], B [N][K] bfloat16, C float)."""
+    A, B = A.contiguous(), B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C_ = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().nqs_gemm_bf16(_ptr(A), K, _ptr(B), K, M, N, K, _ptr(C_), N, _ptr(err),
+                               _stream(stream)), "nqs_gemm_bf16")
+    if int(err.item()) != 0:
+        raise NQSError("nqs_gemm_bf16: a pipeline wait timed out")
+    return C_
 
 
 def profile_enable(on: bool = True):
