@@ -133,14 +133,15 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 def algorithmic_work(name, wl, nS, nexc, nnz, n_emit, n_unique, net_flops):
     """(bound, amount per launch, unit) - bytes for HBM-bound kernels, FLOP for GEMMs."""
+    kb = 4.0 if 2 * wl.norb <= 32 else 8.0  # PT2 key width
     if name == "rs_scatter":   # read key+value, write key+value
-        return "hbm", 32.0 * n_emit, "B"
+        return "hbm", 2.0 * (kb + 8.0) * n_emit, "B"
     if name == "rs_hist":      # read keys
-        return "hbm", 8.0 * n_emit, "B"
+        return "hbm", kb * n_emit, "B"
     if name == "pt2_emit":     # write key+value per emission, read S and psi
-        return "hbm", 16.0 * n_emit + 24.0 * nS, "B"
-    if name == "seg_reduce":   # read values, read run starts + first keys, write one term per run
-        return "hbm", 8.0 * n_emit + 24.0 * n_unique, "B"
+        return "hbm", (kb + 8.0) * n_emit + 24.0 * nS, "B"
+    if name == "seg_reduce":   # read keys + values, write (sum, key) per run, read its run index
+        return "hbm", (kb + 8.0) * n_emit + (kb + 12.0) * n_unique, "B"
     if name == "conn_fill":    # write col+val per nonzero, read S
         return "hbm", 12.0 * nnz + 16.0 * nS, "B"
     if name == "conn_count":

@@ -177,7 +177,7 @@ int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64
  * allocation or code that must not call the allocator while work is being recorded).
  * Same result as nqs_connections, written into caller-owned device buffers: row_ptr
  * [nS + 1] int64, col [capacity] int32, val [capacity] FP64. The library's scratch (hash table
- * of S, row counts, scan partials) lives in one static device array of 4 MiB, which limits
+ * of S, row counts, scan partials) lives in one static device array of 8 MiB, which limits
  * nS to 65536 (larger nS returns NQS_ERR_ARG with a message in nqs_last_error()). Every GPU
  * that loads the library holds the array until process exit. The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device current; make it

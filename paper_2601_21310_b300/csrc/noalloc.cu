@@ -23,7 +23,7 @@
 #include "nqs_internal.cuh"
 
 #define NQS_NOALLOC_MAX_DETS 65536
-#define NQS_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define NQS_NOALLOC_SCRATCH_BYTES (8u << 20)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NQS_NOALLOC_SCRATCH_BYTES];
 

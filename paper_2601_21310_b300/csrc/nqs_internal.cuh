@@ -137,7 +137,7 @@ __host__ __device__ __forceinline__ uint64_t det_hash(uint64_t a, uint64_t b) {
 }
 
 // ------------------------------------------------------------------------------------------
-// hash table of S: open addressing, linear probing, capacity a power of two >= 2|S|
+// hash table of S: open addressing, linear probing, capacity a power of two >= 4|S|
 // ------------------------------------------------------------------------------------------
 #define NQS_EMPTY_WORD 0xffffffffffffffffull
 struct HashS {
@@ -195,6 +195,9 @@ int max_f64_masked(nqs_problem* p, Scratch& sc, const double* x, const int8_t* m
 // The pointers are swapped in place so that (keys, vals) name the sorted result on return.
 int radix_sort_pairs(nqs_problem* p, Scratch& sc, uint64_t*& keys, double*& vals,
                      uint64_t*& keys_alt, double*& vals_alt, int64_t n, int bits, cudaStream_t s);
+int radix_sort_pairs32(nqs_problem* p, Scratch& sc, uint32_t*& keys, double*& vals,
+                       uint32_t*& keys_alt, double*& vals_alt, int64_t n, int bits,
+                       cudaStream_t s);
 
 inline unsigned grid_for(int64_t n, int block, int cap = 148 * 32) {
     int64_t g = (n + block - 1) / block;

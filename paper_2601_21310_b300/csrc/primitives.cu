@@ -226,19 +226,23 @@ int max_f64_masked(nqs_problem* p, Scratch& sc, const double* x, const int8_t* m
 }
 
 // ------------------------------------------------------------------------------------------
-// stable LSD radix sort, 8-bit digits. Per pass: per-tile digit histograms, one exclusive
-// scan over (digit-major, tile-minor) counts, then a scatter in which each warp ranks its
-// elements with __match_any_sync (elements in ascending index order: warp, item, lane), so
-// equal digits keep their input order. No inter-block waiting of any kind.
+// stable LSD radix sort, 8-bit digits, keys of 32 or 64 bits with FP64 values. Per pass:
+//   k_rs_hist     per-tile digit histograms (digit-major, tile-minor counts);
+//   one exclusive scan over the counts -> global offset of (digit, tile);
+//   k_rs_scatter  each warp ranks its keys with __match_any_sync (elements in ascending index
+//                 order: warp, item, lane), the tile is staged in shared memory in digit order
+//                 (values loaded straight into place), then written out so that consecutive
+//                 threads store consecutive elements of each digit run (coalesced writes).
+// Equal digits keep their input order (stable). No inter-block waiting of any kind.
 // ------------------------------------------------------------------------------------------
 #define RS_THREADS 256
 #define RS_ITEMS 16
 #define RS_TILE (RS_THREADS * RS_ITEMS)
 #define RS_WARPS (RS_THREADS / 32)
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restrict__ keys,
-                                                         int64_t n, int shift,
-                                                         uint32_t* __restrict__ counts,
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ keys, int64_t n,
+                                                         int shift, uint32_t* __restrict__ counts,
                                                          int64_t T) {
     __shared__ uint32_t hist[256];
     hist[threadIdx.x] = 0;
@@ -247,33 +251,40 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restri
 #pragma unroll 4
     for (int k = 0; k < RS_ITEMS; ++k) {
         int64_t i = base + k * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&hist[(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&hist[(uint32_t)(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
     counts[(int64_t)threadIdx.x * T + blockIdx.x] = hist[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const uint64_t* __restrict__ kin,
-                                                            const double* __restrict__ vin,
-                                                            uint64_t* __restrict__ kout,
-                                                            double* __restrict__ vout, int64_t n,
-                                                            int shift,
-                                                            const uint32_t* __restrict__ offs,
-                                                            int64_t T) {
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const K* __restrict__ kin,
+                                                               const double* __restrict__ vin,
+                                                               K* __restrict__ kout,
+                                                               double* __restrict__ vout,
+                                                               int64_t n, int shift,
+                                                               const uint32_t* __restrict__ offs,
+                                                               int64_t T) {
+    extern __shared__ __align__(16) uint8_t rs_smem[];
+    double* svals = (double*)rs_smem;               // [RS_TILE]
+    K* skeys = (K*)(svals + RS_TILE);               // [RS_TILE]
     __shared__ uint32_t whist[RS_WARPS][256];
-    __shared__ uint32_t toff[256];
+    __shared__ uint32_t dstart[256];
+    __shared__ uint32_t goff[256];
+    __shared__ uint32_t warp_tot[RS_THREADS / 32];
+    __shared__ uint32_t total;
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&whist[0][0])[i] = 0;
-    toff[threadIdx.x] = offs[(int64_t)threadIdx.x * T + blockIdx.x];
+    goff[threadIdx.x] = offs[(int64_t)threadIdx.x * T + blockIdx.x];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + warp * (RS_ITEMS * 32);
-    // keys stay in registers; each value is read once, at scatter time (same coalesced pattern)
-    uint64_t key[RS_ITEMS];
+    const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t wbase = tbase + warp * (RS_ITEMS * 32);
+    K key[RS_ITEMS];
     uint32_t rank[RS_ITEMS];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         int64_t i = wbase + k * 32 + lane;
-        key[k] = i < n ? kin[i] : 0ull;
+        key[k] = i < n ? kin[i] : (K)0;
     }
     const unsigned lt = lanemask_lt();
 #pragma unroll
@@ -290,49 +301,63 @@ __global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const uint64_t* __
         rank[k] = old + __popc(peers & lt);
     }
     __syncthreads();
-    {
-        uint32_t run = 0;
+    // per digit (thread = digit): exclusive prefix over warps, then over digits inside the tile
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) {
-            uint32_t c = whist[w][threadIdx.x];
-            whist[w][threadIdx.x] = run;
-            run += c;
-        }
+    for (int w = 0; w < RS_WARPS; ++w) {
+        uint32_t c = whist[w][threadIdx.x];
+        whist[w][threadIdx.x] = cnt;
+        cnt += c;
     }
+    uint32_t ds = block_exclusive_scan<uint32_t>(cnt, warp_tot, &total);
+    dstart[threadIdx.x] = ds;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         int64_t i = wbase + k * 32 + lane;
         if (i < n) {
             uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
-            uint32_t pos = toff[d] + whist[warp][d] + rank[k];
-            kout[pos] = key[k];
-            vout[pos] = vin[i];
+            uint32_t lp = dstart[d] + whist[warp][d] + rank[k];
+            skeys[lp] = key[k];
+            svals[lp] = vin[i];
         }
+    }
+    __syncthreads();
+    const int tn = (int)((n - tbase) < RS_TILE ? (n - tbase) : RS_TILE);
+    for (int i = threadIdx.x; i < tn; i += RS_THREADS) {
+        K kk = skeys[i];
+        uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        uint32_t gp = goff[d] + (uint32_t)i - dstart[d];
+        kout[gp] = kk;
+        vout[gp] = svals[i];
     }
 }
 
-int radix_sort_pairs(nqs_problem* p, Scratch& sc, uint64_t*& keys, double*& vals,
-                     uint64_t*& keys_alt, double*& vals_alt, int64_t n, int bits, cudaStream_t s) {
+template <class K>
+static int radix_sort_impl(nqs_problem* p, Scratch& sc, K*& keys, double*& vals, K*& keys_alt,
+                           double*& vals_alt, int64_t n, int bits, cudaStream_t s) {
     if (n <= 1) return NQS_OK;
     if (n >= (int64_t)1 << 32) return NQS_ERR_UNSUPPORTED;
     int64_t T = (n + RS_TILE - 1) / RS_TILE;
     uint32_t* counts;
     NQS_TRY(sc.get(&counts, 256 * T));
+    const int smem = RS_TILE * (int)(sizeof(double) + sizeof(K));
+    NQS_CK(cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem));
     for (int shift = 0; shift < bits; shift += 8) {
         {
             ProfScope prof_(PROF_RS_HIST, s);
-            k_rs_hist<<<(unsigned)T, RS_THREADS, 0, s>>>(keys, n, shift, counts, T);
+            k_rs_hist<K><<<(unsigned)T, RS_THREADS, 0, s>>>(keys, n, shift, counts, T);
         }
         NQS_CK_LAUNCH();
         NQS_TRY(scan_exclusive_u32(p, sc, counts, counts, 256 * T, s));
         {
             ProfScope prof_(PROF_RS_SCATTER, s);
-            k_rs_scatter<<<(unsigned)T, RS_THREADS, 0, s>>>(keys, vals, keys_alt, vals_alt, n, shift,
-                                                            counts, T);
+            k_rs_scatter<K><<<(unsigned)T, RS_THREADS, smem, s>>>(keys, vals, keys_alt, vals_alt, n,
+                                                                  shift, counts, T);
         }
         NQS_CK_LAUNCH();
-        uint64_t* tk = keys;
+        K* tk = keys;
         keys = keys_alt;
         keys_alt = tk;
         double* tv = vals;
@@ -340,4 +365,15 @@ int radix_sort_pairs(nqs_problem* p, Scratch& sc, uint64_t*& keys, double*& vals
         vals_alt = tv;
     }
     return NQS_OK;
+}
+
+int radix_sort_pairs(nqs_problem* p, Scratch& sc, uint64_t*& keys, double*& vals,
+                     uint64_t*& keys_alt, double*& vals_alt, int64_t n, int bits, cudaStream_t s) {
+    return radix_sort_impl<uint64_t>(p, sc, keys, vals, keys_alt, vals_alt, n, bits, s);
+}
+
+int radix_sort_pairs32(nqs_problem* p, Scratch& sc, uint32_t*& keys, double*& vals,
+                       uint32_t*& keys_alt, double*& vals_alt, int64_t n, int bits,
+                       cudaStream_t s) {
+    return radix_sort_impl<uint32_t>(p, sc, keys, vals, keys_alt, vals_alt, n, bits, s);
 }

@@ -250,7 +250,7 @@ __global__ void k_hash_keys(const ulonglong2* S, const int32_t* idx, ulonglong2*
 int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, HashS* out,
                cudaStream_t s) {
     uint64_t cap = 1024;
-    while (cap < 2 * (uint64_t)nS) cap <<= 1;
+    while (cap < 4 * (uint64_t)nS) cap <<= 1;  // load factor <= 1/4: short probe sequences
     ulonglong2* keys;
     int32_t* idx;
     NQS_TRY(sc.get(&keys, cap));

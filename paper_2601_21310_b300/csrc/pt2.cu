@@ -5,12 +5,15 @@
 //      in canonical order (y ascending, then canonical excitation index) - with B = 1 the
 //      position of every emission is fixed, otherwise a count pass and a scan give them;
 //   2. stable LSD radix sort by key (2 norb bits), so equal keys stay in emission order;
-//   3. mark run heads, scan them, sum each run in order -> c(x'); runs whose x' is in S feed
-//      the internal term (c(x) is the off-diagonal part of (H_SS psi)_x), the others give
+//   3. mark run heads and scan them (run index of every element); each warp then sums the
+//      runs that start in its chunk with a segmented warp scan (carrying the open run across
+//      iterations) -> c(x') for every unique x'; a per-unique pass sends members of S to the
+//      internal term (c(x) is the off-diagonal part of (H_SS psi)_x) and turns the others into
 //      c^2 / (D (E - H_x'x')) with H_x'x' from the Slater-Condon diagonal;
 //   4. compensated sums of the external terms, and of the internal terms of the dets of S in
 //      bucket b: r_x = H_xx psi_x + c(x) - E psi_x, r_x^2 / (D (E - H_xx)).
-// D = psi.psi, compensated. Keys are (a << norb) | b in one uint64, so 2 norb <= 64.
+// D = psi.psi, compensated. Keys are (a << norb) | b: uint32 when 2 norb <= 32, else uint64
+// (so 2 norb <= 64).
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -55,12 +58,13 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_count(ProblemDev P,
 }
 
 // offs == nullptr: every excitation is emitted at det * nexc + e (B = 1)
+template <class K>
 __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit(ProblemDev P,
                                                           const ulonglong2* __restrict__ S,
                                                           const double* __restrict__ psi,
                                                           int64_t nS, uint64_t B, uint64_t bucket,
                                                           const int64_t* __restrict__ offs,
-                                                          uint64_t* __restrict__ keys,
+                                                          K* __restrict__ keys,
                                                           double* __restrict__ vals) {
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit(ProblemDev P,
             unsigned m = __ballot_sync(FULL_MASK, take);
             if (take) {
                 int64_t pos = run + __popc(m & lt);
-                keys[pos] = (ex.a2 << norb) | ex.b2;
+                keys[pos] = (K)((ex.a2 << norb) | ex.b2);
                 vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
             }
             run += __popc(m);
@@ -95,41 +99,99 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit(ProblemDev P,
     }
 }
 
-__global__ void k_heads(const uint64_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ f) {
+template <class K>
+__global__ void k_heads(const K* __restrict__ keys, int64_t n, uint32_t* __restrict__ f) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         f[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
 }
 
-__global__ void k_starts(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ pos,
-                         int64_t n, int64_t* __restrict__ starts) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        if (i == 0 || keys[i] != keys[i - 1]) starts[pos[i]] = i;
+// Segmented sums of the sorted values. Warp chunk [c0, c1) owns the runs whose head lies in
+// it: it skips the tail of the previous chunk's last run and finishes its own last run past c1.
+// Within 32 consecutive elements a shuffle scan adds along runs (earlier elements first); the
+// open run is carried to the next 32. The last element of a run writes c and the run's key at
+// the run index (exclusive head count pos[] plus its own head flag, minus one).
+#define SEG_CHUNK 1024
+template <class K>
+__global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
+                                                 const double* __restrict__ vals,
+                                                 const uint32_t* __restrict__ pos, int64_t n,
+                                                 double* __restrict__ cU, K* __restrict__ keyU) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (n + SEG_CHUNK - 1) / SEG_CHUNK;
+    for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
+         ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t c0 = ch * SEG_CHUNK, c1 = min(n, c0 + SEG_CHUNK);
+        // first head inside [c0, c1)
+        int64_t s0 = -1;
+        for (int64_t b = c0; b < c1 && s0 < 0; b += 32) {
+            const int64_t i = b + lane;
+            const bool h = i < c1 && (i == 0 || keys[i] != keys[i - 1]);
+            const unsigned m = __ballot_sync(FULL_MASK, h);
+            if (m) s0 = b + __ffs(m) - 1;
+        }
+        if (s0 < 0) continue;  // every element continues a run owned by an earlier chunk
+        double carry = 0.0;
+        for (int64_t b = s0; b < n; b += 32) {
+            const int64_t i = b + lane;
+            const bool in = i < n;
+            const K k = in ? keys[i] : (K)0;
+            const K kprev = __shfl_up_sync(FULL_MASK, k, 1);
+            const bool h = in && (i == 0 || (lane == 0 ? keys[i - 1] != k : kprev != k));
+            // a head at or beyond c1 starts a run owned by the next chunk: stop before it
+            const unsigned stopm = __ballot_sync(FULL_MASK, !in || (h && i >= c1));
+            const int nact = stopm ? __ffs(stopm) - 1 : 32;
+            const bool act = lane < nact;
+            double v = act ? vals[i] : 0.0;
+            int f = (act && h) ? 1 : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double yv = __shfl_up_sync(FULL_MASK, v, o);
+                const int yf = __shfl_up_sync(FULL_MASK, f, o);
+                if (lane >= o) {
+                    if (!f) v = yv + v;
+                    f |= yf;
+                }
+            }
+            if (act && !f) v = carry + v;
+            const unsigned hm = __ballot_sync(FULL_MASK, act && h);
+            bool tail = false;
+            if (act) {
+                if (lane < nact - 1) tail = (hm >> (lane + 1)) & 1u;
+                else if (nact < 32) tail = true;
+                else tail = (i == n - 1) || (keys[i + 1] != k);
+            }
+            if (tail) {
+                const uint32_t ridx = pos[i] + (h ? 1u : 0u) - 1u;
+                cU[ridx] = v;
+                keyU[ridx] = k;
+            }
+            carry = __shfl_sync(FULL_MASK, v, 31);
+            if (nact < 32) break;
+        }
+    }
 }
 
-__global__ void k_seg_reduce(ProblemDev P, HashS H, const uint64_t* __restrict__ keys,
-                             const double* __restrict__ vals, const int64_t* __restrict__ starts,
-                             int64_t nuniq, int64_t n, const double* __restrict__ Dp, double E,
-                             double* __restrict__ cS, double* __restrict__ eterm,
-                             unsigned long long* __restrict__ next) {
+template <class K>
+__global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU,
+                               const double* __restrict__ cU, int64_t nuniq,
+                               const double* __restrict__ Dp, double E, double* __restrict__ cS,
+                               double* __restrict__ eterm, unsigned long long* __restrict__ next) {
     const double D = *Dp;
     const int norb = P.norb;
-    const uint64_t bmask = norb == 64 ? ~0ull : ((1ull << norb) - 1ull);
+    const uint64_t bmask = (1ull << norb) - 1ull;
     unsigned long long local = 0;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nuniq;
          u += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i0 = starts[u], i1 = (u + 1 < nuniq) ? starts[u + 1] : n;
-        double c = 0.0;
-        for (int64_t i = i0; i < i1; ++i) c = __dadd_rn(c, vals[i]);
-        uint64_t k = keys[i0];
-        uint64_t a = norb == 64 ? 0 : (k >> norb), b = k & bmask;
-        int32_t s = hash_lookup(H, a, b);
+        const uint64_t k = (uint64_t)keyU[u];
+        const uint64_t a = k >> norb, b = k & bmask;
+        const double c = cU[u];
+        const int32_t s = hash_lookup(H, a, b);
         if (s >= 0) {
             cS[s] = c;
             eterm[u] = 0.0;
         } else {
-            double hxx = diag_element_impl(P, a, b);
+            const double hxx = diag_element_impl(P, a, b);
             eterm[u] = __ddiv_rn(__dmul_rn(c, c), __dmul_rn(D, __dsub_rn(E, hxx)));
             ++local;
         }
@@ -178,6 +240,66 @@ static double host_ksum(const std::vector<double>& v) {
     return s + c;
 }
 
+// one bucket of the pipeline with key type K; adds the bucket's partial sums on the device
+template <class K>
+static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                      double E_var, int64_t B, int64_t b, const int64_t* offs, int64_t n,
+                      const HashS& H, double* cS, double* D_dev, double* ext_dev,
+                      unsigned long long* nuniq_dev, size_t smem, cudaStream_t s) {
+    const ProblemDev& P = p->d;
+    Scratch bs(p, s);
+    K *keys, *keys2;
+    double *vals, *vals2;
+    NQS_TRY(bs.get(&keys, n));
+    NQS_TRY(bs.get(&vals, n));
+    NQS_TRY(bs.get(&keys2, n));
+    NQS_TRY(bs.get(&vals2, n));
+    {
+        ProfScope prof_(PROF_PT2_EMIT, s);
+        k_pt2_emit<K><<<pt_grid(nS), PT_THREADS, smem, s>>>(P, (const ulonglong2*)dets, psi, nS,
+                                                            (uint64_t)B, (uint64_t)b, offs, keys,
+                                                            vals);
+    }
+    NQS_CK_LAUNCH();
+    if (sizeof(K) == 4)
+        NQS_TRY(radix_sort_pairs32(p, bs, (uint32_t*&)keys, vals, (uint32_t*&)keys2, vals2, n,
+                                   2 * P.norb, s));
+    else
+        NQS_TRY(radix_sort_pairs(p, bs, (uint64_t*&)keys, vals, (uint64_t*&)keys2, vals2, n,
+                                 2 * P.norb, s));
+    // run heads and their exclusive scan, in the free value buffer (8 bytes per element)
+    uint32_t* flags = (uint32_t*)vals2;
+    uint32_t* pos = flags + n;
+    k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(keys, n, flags);
+    NQS_CK_LAUNCH();
+    NQS_TRY(scan_exclusive_u32(p, bs, flags, pos, n, s));
+    uint32_t last_pos = 0, last_flag = 0;
+    if (n > 0) {
+        NQS_CK(cudaMemcpyAsync(&last_pos, pos + n - 1, 4, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaMemcpyAsync(&last_flag, flags + n - 1, 4, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+    }
+    const int64_t nuniq = n > 0 ? (int64_t)last_pos + last_flag : 0;
+    double *cU, *eterm;
+    K* keyU;
+    NQS_TRY(bs.get(&cU, nuniq));
+    NQS_TRY(bs.get(&keyU, nuniq));
+    NQS_TRY(bs.get(&eterm, nuniq));
+    if (nuniq > 0) {
+        {
+            ProfScope prof_(PROF_SEG_REDUCE, s);
+            k_seg_sum<K><<<grid_for((n + SEG_CHUNK - 1) / SEG_CHUNK * 32, 256, 148 * 16), 256, 0,
+                           s>>>(keys, vals, pos, n, cU, keyU);
+        }
+        NQS_CK_LAUNCH();
+        k_unique_terms<K><<<grid_for(nuniq, 256), 256, 0, s>>>(P, H, keyU, cU, nuniq, D_dev,
+                                                               E_var, cS, eterm, nuniq_dev);
+        NQS_CK_LAUNCH();
+    }
+    NQS_TRY(ksum_f64(p, bs, eterm, nuniq, ext_dev, s));
+    return NQS_OK;
+}
+
 extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
                        double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
                        nqs_stream_t stream) {
@@ -201,8 +323,10 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     if (smem > 48 * 1024) {
         NQS_CK(cudaFuncSetAttribute(k_pt2_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-        NQS_CK(cudaFuncSetAttribute(k_pt2_emit, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_pt2_emit<uint32_t>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_pt2_emit<uint64_t>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     double* dev_scalars;  // [0] = D, then per bucket (ext, int)
     NQS_TRY(sc.get(&dev_scalars, 1 + 2 * B));
@@ -224,75 +348,39 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
         NQS_TRY(sc.get(&total_dev, 1));
     }
     const int64_t cap = opts->chunk > 0 ? opts->chunk : ((int64_t)1 << 32) - 1;
-    const int keybits = 2 * P.norb;
+    const bool k32 = 2 * P.norb <= 32;
     int64_t total_emitted = 0;
-    // per-bucket buffers are allocated per bucket and released at the end of the bucket
     for (int64_t b = 0; b < B; ++b) {
-        Scratch bs(p, s);
         int64_t n;
         if (B == 1) {
             n = nS * P.nexc;
         } else {
+            Scratch cs(p, s);
             {
                 ProfScope prof_(PROF_PT2_COUNT, s);
                 k_pt2_count<<<pt_grid(nS), PT_THREADS, smem, s>>>(P, (const ulonglong2*)dets, nS,
                                                                   (uint64_t)B, (uint64_t)b, cnt);
             }
             NQS_CK_LAUNCH();
-            NQS_TRY(scan_exclusive_i64(p, bs, cnt, offs, nS, total_dev, s));
+            NQS_TRY(scan_exclusive_i64(p, cs, cnt, offs, nS, total_dev, s));
             NQS_CK(cudaMemcpyAsync(&n, total_dev, sizeof n, cudaMemcpyDeviceToHost, s));
             NQS_CK(cudaStreamSynchronize(s));
         }
         if (n > cap) return NQS_ERR_OOM;  // more buckets needed
         total_emitted += n;
-        uint64_t *keys, *keys2;
-        double *vals, *vals2;
-        NQS_TRY(bs.get(&keys, n));
-        NQS_TRY(bs.get(&vals, n));
-        NQS_TRY(bs.get(&keys2, n));
-        NQS_TRY(bs.get(&vals2, n));
-        {
-            ProfScope prof_(PROF_PT2_EMIT, s);
-            k_pt2_emit<<<pt_grid(nS), PT_THREADS, smem, s>>>(P, (const ulonglong2*)dets, psi, nS,
-                                                             (uint64_t)B, (uint64_t)b,
-                                                             B == 1 ? nullptr : offs, keys, vals);
-        }
-        NQS_CK_LAUNCH();
-        NQS_TRY(radix_sort_pairs(p, bs, keys, vals, keys2, vals2, n, keybits, s));
-        // unique + segmented reduction (reuse the alternate buffers as scratch)
-        uint32_t* flags = (uint32_t*)keys2;  // n u32 fit in n u64
-        uint32_t* pos = flags + n;           // second half of keys2 (n u32)
-        k_heads<<<grid_for(n, 256), 256, 0, s>>>(keys, n, flags);
-        NQS_CK_LAUNCH();
-        NQS_TRY(scan_exclusive_u32(p, bs, flags, pos, n, s));
-        uint32_t last_pos = 0, last_flag = 0;
-        if (n > 0) {
-            NQS_CK(cudaMemcpyAsync(&last_pos, pos + n - 1, 4, cudaMemcpyDeviceToHost, s));
-            NQS_CK(cudaMemcpyAsync(&last_flag, flags + n - 1, 4, cudaMemcpyDeviceToHost, s));
-            NQS_CK(cudaStreamSynchronize(s));
-        }
-        int64_t nuniq = n > 0 ? (int64_t)last_pos + last_flag : 0;
-        int64_t* starts = (int64_t*)vals2;    // nuniq <= n int64
-        double* eterm;
-        NQS_TRY(bs.get(&eterm, nuniq));
-        if (nuniq > 0) {
-            k_starts<<<grid_for(n, 256), 256, 0, s>>>(keys, pos, n, starts);
-            NQS_CK_LAUNCH();
-            {
-                ProfScope prof_(PROF_SEG_REDUCE, s);
-                k_seg_reduce<<<grid_for(nuniq, 256), 256, 0, s>>>(P, H, keys, vals, starts, nuniq, n,
-                                                                  dev_scalars, E_var, cS, eterm,
-                                                                  next_dev + b);
-            }
-            NQS_CK_LAUNCH();
-        }
-        NQS_TRY(ksum_f64(p, bs, eterm, nuniq, dev_scalars + 1 + 2 * b, s));
+        int st = k32 ? pt2_bucket<uint32_t>(p, dets, psi, nS, E_var, B, b, B == 1 ? nullptr : offs,
+                                            n, H, cS, dev_scalars, dev_scalars + 1 + 2 * b,
+                                            next_dev + b, smem, s)
+                     : pt2_bucket<uint64_t>(p, dets, psi, nS, E_var, B, b, B == 1 ? nullptr : offs,
+                                            n, H, cS, dev_scalars, dev_scalars + 1 + 2 * b,
+                                            next_dev + b, smem, s);
+        NQS_TRY(st);
         if (opts->internal_pt2) {
             k_pt2_internal<<<grid_for(nS, 256), 256, 0, s>>>(P, (const ulonglong2*)dets, psi, cS,
                                                              nS, dev_scalars, E_var, (uint64_t)B,
                                                              (uint64_t)b, eint);
             NQS_CK_LAUNCH();
-            NQS_TRY(ksum_f64(p, bs, eint, nS, dev_scalars + 2 + 2 * b, s));
+            NQS_TRY(ksum_f64(p, sc, eint, nS, dev_scalars + 2 + 2 * b, s));
         } else {
             NQS_CK(cudaMemsetAsync(dev_scalars + 2 + 2 * b, 0, sizeof(double), s));
         }

@@ -46,6 +46,21 @@ def test_noalloc_matches_connections_two_calls_in_a_row():
         assert np.abs(val - val_ref).max() <= 1e-12
 
 
+def test_noalloc_at_the_maximum_size():
+    """65536 determinants, the largest input the static scratch accepts."""
+    need_gpu()
+    N = nqs()
+    h, eri, _ = synth.integrals(16, 32, 1, 3.0)
+    S = synth.select_S(16, 8, 65536)
+    P = N.Problem(16, 8, 8, h, eri)
+    dets = to_dev(S)
+    rp_ref, col_ref, val_ref = N.connections(P, dets).host()
+    st, nnz, _, rp, col, val = _noalloc(N, P, dets, len(col_ref))
+    assert st == 0, N.lib().nqs_last_error()
+    assert np.array_equal(rp, rp_ref) and np.array_equal(col, col_ref)
+    assert np.abs(val - val_ref).max() <= 1e-12
+
+
 def test_noalloc_reports_size_limits():
     need_gpu()
     N = nqs()
