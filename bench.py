@@ -206,24 +206,32 @@ def run_nqs(args, ws, rank, local):
     psi = torch.empty(nS, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    ev_eg = []
+    ev_phase = {"connections": [], "energy_grad": [], "pt2": [], "csr_free": []}
+
+    def mark(record):
+        if not record:
+            return None
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
 
     def step(record=False):
+        e0 = mark(record)
         csr = N.connections(P, dets, o_conn)
-        if record:
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+        e1 = mark(record)
         N.energy_grad(P, net, csr, dets, o=o_eg, out=out, grad=grad, psi=psi)
-        if record:
-            b.record(stream)
-            ev_eg.append((a, b))
+        e2 = mark(record)
         E = out[0].item()
         r = N.pt2(P, dets, psi, E, o=o_pt)
+        e3 = mark(record)
         info = dict(n_conn=csr.n_enumerated + r["n_emitted"], n_hss=csr.n_enumerated,
                     n_emit=r["n_emitted"], nnz=csr.nnz, n_unique=r["n_unique"], E=E,
                     ext=r["ext"], int=r["int"])
         csr.free()
+        e4 = mark(record)
+        if record:
+            for k, (x, y) in zip(ev_phase, [(e0, e1), (e1, e2), (e2, e3), (e3, e4)]):
+                ev_phase[k].append((x, y))
         return info
 
     for _ in range(args.warmup):
@@ -255,7 +263,8 @@ def run_nqs(args, ws, rank, local):
     launches = N.launch_count() - launches0
     N.profile_enable(False)
     prof = N.profile_read()
-    eg_ms = [x.elapsed_time(y) for x, y in ev_eg]
+    phase_ms = {k: sum(x.elapsed_time(y) for x, y in v) / len(v) for k, v in ev_phase.items()}
+    eg_ms = [x.elapsed_time(y) for x, y in ev_phase["energy_grad"]]
     ms_step = sum(times) / len(times)
     if ws > 1:
         t = torch.tensor([sum(times)], device=dev)
@@ -307,7 +316,8 @@ def run_nqs(args, ws, rank, local):
         "connections_per_step": info["n_conn"], "hss_nnz": info["nnz"],
         "pt2_unique": info["n_unique"], "E_S": info["E"], "dE_pt2_ext": info["ext"],
         "dE_pt2_int": info["int"], "wall_s": wall, "gpu_launches": launches,
-        "roofline": roofline, "kernels": kernels, "clocks": sampler.summary(),
+        "roofline": roofline, "kernels": kernels, "phase_ms": phase_ms,
+        "clocks": sampler.summary(),
     }
     if not args.no_e2e:
         result["e2e"] = run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg,

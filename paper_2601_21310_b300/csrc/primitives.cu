@@ -247,89 +247,154 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ ke
     __shared__ uint32_t hist[256];
     hist[threadIdx.x] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
-#pragma unroll 4
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    // issue every load of the tile before the first atomic
+    K key[RS_ITEMS];
+#pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-        int64_t i = base + k * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&hist[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        const int64_t i = base + k * RS_THREADS + threadIdx.x;
+        key[k] = i < n ? keys[i] : (K)0;
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const int64_t i = base + k * RS_THREADS + threadIdx.x;
+        const bool v = i < n;
+        const uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
+        // one shared atomic per distinct digit of the warp (digits are highly skewed)
+        const unsigned peers = __match_any_sync(FULL_MASK, v ? d : 256u);
+        if (v && lane == __ffs(peers) - 1) atomicAdd(&hist[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     counts[(int64_t)threadIdx.x * T + blockIdx.x] = hist[threadIdx.x];
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Tile staging: one thread issues bulk asynchronous copies (global -> shared, completion
+// counted in bytes on an mbarrier) for the tile's keys and values, so the whole tile is in
+// flight at once; ranks are then computed from shared memory, a permutation is built in digit
+// order, and the tile is written out digit run by digit run (coalesced). The wait on the
+// mbarrier is bounded; on timeout the error word is set and the tile is left unwritten.
 template <class K>
-__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const K* __restrict__ kin,
-                                                               const double* __restrict__ vin,
-                                                               K* __restrict__ kout,
-                                                               double* __restrict__ vout,
-                                                               int64_t n, int shift,
-                                                               const uint32_t* __restrict__ offs,
-                                                               int64_t T) {
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__ kin,
+                                                            const double* __restrict__ vin,
+                                                            K* __restrict__ kout,
+                                                            double* __restrict__ vout, int64_t n,
+                                                            int shift,
+                                                            const uint32_t* __restrict__ offs,
+                                                            int64_t T, int* err) {
     extern __shared__ __align__(16) uint8_t rs_smem[];
-    double* svals = (double*)rs_smem;               // [RS_TILE]
-    K* skeys = (K*)(svals + RS_TILE);               // [RS_TILE]
+    double* sv = (double*)rs_smem;             // [RS_TILE] values, input order
+    K* sk = (K*)(sv + RS_TILE);                // [RS_TILE] keys, input order
+    uint16_t* perm = (uint16_t*)(sk + RS_TILE);  // [RS_TILE] input index at each sorted slot
     __shared__ uint32_t whist[RS_WARPS][256];
     __shared__ uint32_t dstart[256];
     __shared__ uint32_t goff[256];
     __shared__ uint32_t warp_tot[RS_THREADS / 32];
     __shared__ uint32_t total;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int ok_s;
+    const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+    const int tn = (int)((n - tbase) < RS_TILE ? (n - tbase) : RS_TILE);
+    const bool bulk = tn == RS_TILE;  // full tiles are 16-byte aligned multiples of 16 bytes
+    if (threadIdx.x == 0) {
+        ok_s = 1;
+        if (bulk) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            const uint32_t kb = RS_TILE * sizeof(K), vb = RS_TILE * sizeof(double);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                             smem_addr(&bar)),
+                         "r"(kb + vb)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                "[%3];" ::"r"(smem_addr(sk)),
+                "l"(kin + tbase), "r"(kb), "r"(smem_addr(&bar))
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                "[%3];" ::"r"(smem_addr(sv)),
+                "l"(vin + tbase), "r"(vb), "r"(smem_addr(&bar))
+                : "memory");
+        }
+    }
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&whist[0][0])[i] = 0;
     goff[threadIdx.x] = offs[(int64_t)threadIdx.x * T + blockIdx.x];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
-    const int64_t wbase = tbase + warp * (RS_ITEMS * 32);
-    K key[RS_ITEMS];
-    uint32_t rank[RS_ITEMS];
-#pragma unroll
-    for (int k = 0; k < RS_ITEMS; ++k) {
-        int64_t i = wbase + k * 32 + lane;
-        key[k] = i < n ? kin[i] : (K)0;
+    if (!bulk) {
+        for (int i = threadIdx.x; i < tn; i += RS_THREADS) {
+            sk[i] = kin[tbase + i];
+            sv[i] = vin[tbase + i];
+        }
     }
+    __syncthreads();
+    if (bulk) {
+        const long long t0 = clock64();
+        while (true) {
+            uint32_t done;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(smem_addr(&bar))
+                : "memory");
+            if (done) break;
+            if (clock64() - t0 > 4000000000ll) {
+                ok_s = 0;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    if (!ok_s) {
+        if (threadIdx.x == 0 && err) atomicExch(err, 1);
+        return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wb = warp * (RS_ITEMS * 32);
+    uint32_t rank[RS_ITEMS];
     const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-        int64_t i = wbase + k * 32 + lane;
-        bool v = i < n;
-        uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
-        unsigned peers = __match_any_sync(FULL_MASK, v ? d : 256u);
-        uint32_t old = v ? whist[warp][d] : 0u;
+        const int li = wb + k * 32 + lane;
+        const bool v = li < tn;
+        const uint32_t d = v ? ((uint32_t)(sk[li] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(FULL_MASK, d);
+        const uint32_t old = v ? whist[warp][d] : 0u;
         __syncwarp();
-        int leader = __ffs(peers) - 1;
-        if (v && lane == leader) whist[warp][d] = old + __popc(peers);
+        if (v && lane == __ffs(peers) - 1) whist[warp][d] = old + __popc(peers);
         __syncwarp();
         rank[k] = old + __popc(peers & lt);
     }
     __syncthreads();
-    // per digit (thread = digit): exclusive prefix over warps, then over digits inside the tile
     uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) {
-        uint32_t c = whist[w][threadIdx.x];
+        const uint32_t c = whist[w][threadIdx.x];
         whist[w][threadIdx.x] = cnt;
         cnt += c;
     }
-    uint32_t ds = block_exclusive_scan<uint32_t>(cnt, warp_tot, &total);
-    dstart[threadIdx.x] = ds;
+    dstart[threadIdx.x] = block_exclusive_scan<uint32_t>(cnt, warp_tot, &total);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-        int64_t i = wbase + k * 32 + lane;
-        if (i < n) {
-            uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
-            uint32_t lp = dstart[d] + whist[warp][d] + rank[k];
-            skeys[lp] = key[k];
-            svals[lp] = vin[i];
+        const int li = wb + k * 32 + lane;
+        if (li < tn) {
+            const uint32_t d = (uint32_t)(sk[li] >> shift) & 255u;
+            perm[dstart[d] + whist[warp][d] + rank[k]] = (uint16_t)li;
         }
     }
     __syncthreads();
-    const int tn = (int)((n - tbase) < RS_TILE ? (n - tbase) : RS_TILE);
     for (int i = threadIdx.x; i < tn; i += RS_THREADS) {
-        K kk = skeys[i];
-        uint32_t d = (uint32_t)(kk >> shift) & 255u;
-        uint32_t gp = goff[d] + (uint32_t)i - dstart[d];
+        const int j = perm[i];
+        const K kk = sk[j];
+        const uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        const uint32_t gp = goff[d] + (uint32_t)i - dstart[d];
         kout[gp] = kk;
-        vout[gp] = svals[i];
+        vout[gp] = sv[j];
     }
 }
 
@@ -341,7 +406,7 @@ static int radix_sort_impl(nqs_problem* p, Scratch& sc, K*& keys, double*& vals,
     int64_t T = (n + RS_TILE - 1) / RS_TILE;
     uint32_t* counts;
     NQS_TRY(sc.get(&counts, 256 * T));
-    const int smem = RS_TILE * (int)(sizeof(double) + sizeof(K));
+    const int smem = RS_TILE * (int)(sizeof(double) + sizeof(K) + sizeof(uint16_t));
     NQS_CK(cudaFuncSetAttribute(k_rs_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smem));
     for (int shift = 0; shift < bits; shift += 8) {
@@ -354,7 +419,7 @@ static int radix_sort_impl(nqs_problem* p, Scratch& sc, K*& keys, double*& vals,
         {
             ProfScope prof_(PROF_RS_SCATTER, s);
             k_rs_scatter<K><<<(unsigned)T, RS_THREADS, smem, s>>>(keys, vals, keys_alt, vals_alt, n,
-                                                                  shift, counts, T);
+                                                                  shift, counts, T, p->err_word);
         }
         NQS_CK_LAUNCH();
         K* tk = keys;

@@ -131,18 +131,27 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
             if (m) s0 = b + __ffs(m) - 1;
         }
         if (s0 < 0) continue;  // every element continues a run owned by an earlier chunk
+        // software pipeline: the next 32 keys and values are loaded before this 32 is reduced,
+        // and the boundary keys (element before lane 0, element after lane 31) come from
+        // registers instead of extra dependent loads
         double carry = 0.0;
+        K kbefore = s0 > 0 ? keys[s0 - 1] : (K)0;
+        K k = (s0 + lane < n) ? keys[s0 + lane] : (K)0;
+        double vv = (s0 + lane < n) ? vals[s0 + lane] : 0.0;
         for (int64_t b = s0; b < n; b += 32) {
             const int64_t i = b + lane;
             const bool in = i < n;
-            const K k = in ? keys[i] : (K)0;
+            const int64_t inext = i + 32;
+            const K knext = inext < n ? keys[inext] : (K)0;
+            const double vnext = inext < n ? vals[inext] : 0.0;
             const K kprev = __shfl_up_sync(FULL_MASK, k, 1);
-            const bool h = in && (i == 0 || (lane == 0 ? keys[i - 1] != k : kprev != k));
+            const K kfirst_next = __shfl_sync(FULL_MASK, knext, 0);
+            const bool h = in && (i == 0 || (lane == 0 ? kbefore != k : kprev != k));
             // a head at or beyond c1 starts a run owned by the next chunk: stop before it
             const unsigned stopm = __ballot_sync(FULL_MASK, !in || (h && i >= c1));
             const int nact = stopm ? __ffs(stopm) - 1 : 32;
             const bool act = lane < nact;
-            double v = act ? vals[i] : 0.0;
+            double v = act ? vv : 0.0;
             int f = (act && h) ? 1 : 0;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -159,7 +168,7 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
             if (act) {
                 if (lane < nact - 1) tail = (hm >> (lane + 1)) & 1u;
                 else if (nact < 32) tail = true;
-                else tail = (i == n - 1) || (keys[i + 1] != k);
+                else tail = (i == n - 1) || (kfirst_next != k);
             }
             if (tail) {
                 const uint32_t ridx = pos[i] + (h ? 1u : 0u) - 1u;
@@ -167,7 +176,10 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
                 keyU[ridx] = k;
             }
             carry = __shfl_sync(FULL_MASK, v, 31);
+            kbefore = __shfl_sync(FULL_MASK, k, 31);
             if (nact < 32) break;
+            k = knext;
+            vv = vnext;
         }
     }
 }

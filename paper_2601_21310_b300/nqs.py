@@ -217,11 +217,13 @@ def net_tensors(params, dtype: int, device="cuda") -> list:
 
 
 class CSR:
-    """Library-owned H_SS in CSR (freed with nqs_csr_free)."""
+    """Library-owned H_SS in CSR (freed with nqs_csr_free). Holds a reference to its problem so
+    that the problem is never destroyed before the matrix."""
 
-    def __init__(self, st: CSRStruct, n_enumerated: int):
+    def __init__(self, st: CSRStruct, n_enumerated: int, problem=None):
         self.s = st
         self.n_enumerated = n_enumerated
+        self.problem = problem
 
     @property
     def nnz(self) -> int:
@@ -274,7 +276,7 @@ def connections(problem: Problem, dets: torch.Tensor, o: Opts | None = None, str
     _check(lib().nqs_connections(problem.handle, _ptr(dets), dets.shape[0],
                                  C.byref(o) if o else None, C.byref(st), C.byref(nen),
                                  _stream(stream)), "nqs_connections")
-    return CSR(st, nen.value)
+    return CSR(st, nen.value, problem)
 
 
 def connections_noalloc(problem: Problem, dets: torch.Tensor, row_ptr: torch.Tensor,
