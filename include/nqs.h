@@ -202,7 +202,8 @@ int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M,
  * library brackets its main kernel launches with CUDA events recorded on the launching stream.
  * nqs_profile_read synchronises those events and returns the summed milliseconds and the
  * launch count of one kernel family: "conn_count", "conn_fill", "pt2_count", "pt2_emit",
- * "rs_hist", "rs_scatter", "seg_reduce", "gemm", "lu", "spmv", "layer1". Process-wide state;
+ * "rs_hist", "rs_scatter", "seg_reduce", "gemm", "lu", "spmv", "layer1", "unique_terms",
+ * "heads", "scan". Process-wide state;
  * not thread safe. */
 int nqs_profile_enable(int on);
 int nqs_profile_reset(void);

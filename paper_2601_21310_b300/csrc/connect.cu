@@ -13,43 +13,60 @@
 #include "nqs_internal.cuh"
 #include "prof.cuh"
 
+// Pass 1: count the hits of each row. With bits != nullptr the hit pattern is also stored, one
+// 32-bit ballot word per 32 canonical indices ([nS][ceil(nexc/32)]), so that pass 2 only
+// revisits hits.
 __global__ void __launch_bounds__(CONN_THREADS) k_conn_count(ProblemDev P, HashS H,
                                                               const ulonglong2* __restrict__ S,
-                                                              int64_t nS, int64_t* rowcnt) {
+                                                              int64_t nS, int64_t* rowcnt,
+                                                              uint32_t* __restrict__ bits) {
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const uint32_t nexc = (uint32_t)P.nexc;
+    const uint32_t nwords = (nexc + 31) / 32;
     for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * CONN_WARPS) {
         ulonglong2 x = S[det];
         fill_ctx(P, x.x, x.y, ctx, lane);
         int cnt = 0;
-        for (uint32_t e = lane; e < nexc; e += 32) {
-            uint64_t a2, b2;
-            decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
-            cnt += hash_lookup(H, a2, b2) >= 0;
+        for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
+            const uint32_t e = r0 + lane;
+            bool hit = false;
+            if (e < nexc) {
+                uint64_t a2, b2;
+                decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+                hit = hash_lookup(H, a2, b2) >= 0;
+            }
+            const unsigned m = __ballot_sync(FULL_MASK, hit);
+            if (lane == 0) {
+                cnt += __popc(m);
+                if (bits) bits[det * nwords + r0 / 32] = m;
+            }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(FULL_MASK, cnt, o);
         if (lane == 0) rowcnt[det] = cnt + 1;  // + diagonal
         __syncwarp();
     }
 }
 
+// Pass 2: write each row in canonical order: the diagonal, then the hits. With bits the warp
+// walks the stored ballot words (skipping empty ones) and decodes, probes and evaluates only
+// the hits; without bits it re-enumerates every excitation.
 __global__ void __launch_bounds__(CONN_THREADS) k_conn_fill(ProblemDev P, HashS H,
                                                              const ulonglong2* __restrict__ S,
                                                              int64_t nS,
                                                              const int64_t* __restrict__ row_ptr,
                                                              int32_t* __restrict__ col,
-                                                             double* __restrict__ val) {
+                                                             double* __restrict__ val,
+                                                             const uint32_t* __restrict__ bits) {
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     const uint32_t nexc = (uint32_t)P.nexc;
+    const uint32_t nwords = (nexc + 31) / 32;
     for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * CONN_WARPS) {
         ulonglong2 x = S[det];
@@ -60,21 +77,44 @@ __global__ void __launch_bounds__(CONN_THREADS) k_conn_fill(ProblemDev P, HashS 
             val[base] = diag_element_impl(P, x.x, x.y);
         }
         int64_t run = base + 1;
-        for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
-            uint32_t e = r0 + lane;
-            int32_t hit = -1;
-            Exc ex;
-            if (e < nexc) {
-                decode_exc(P, T, *ctx, x.x, x.y, e, ex);
-                hit = hash_lookup(H, ex.a2, ex.b2);
+        if (bits) {
+            const uint32_t* wb = bits + det * nwords;
+            for (uint32_t w0 = 0; w0 < nwords; w0 += 32) {
+                // 32 ballot words at a time; lanes then take the set bits of each word in turn
+                const uint32_t my = (w0 + lane < nwords) ? wb[w0 + lane] : 0u;
+                unsigned nz = __ballot_sync(FULL_MASK, my != 0u);
+                while (nz) {
+                    const int src = __ffs(nz) - 1;
+                    nz &= nz - 1;
+                    const uint32_t m = __shfl_sync(FULL_MASK, my, src);
+                    const bool hit = (m >> lane) & 1u;
+                    if (hit) {
+                        Exc ex;
+                        decode_exc(P, T, *ctx, x.x, x.y, (w0 + src) * 32 + lane, ex);
+                        const int64_t pos = run + __popc(m & lt);
+                        col[pos] = hash_lookup(H, ex.a2, ex.b2);
+                        val[pos] = exc_element(P, *ctx, ex);
+                    }
+                    run += __popc(m);
+                }
             }
-            unsigned m = __ballot_sync(FULL_MASK, hit >= 0);
-            if (hit >= 0) {
-                int64_t pos = run + __popc(m & lt);
-                col[pos] = hit;
-                val[pos] = exc_element(P, *ctx, ex);
+        } else {
+            for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
+                uint32_t e = r0 + lane;
+                int32_t hit = -1;
+                Exc ex;
+                if (e < nexc) {
+                    decode_exc(P, T, *ctx, x.x, x.y, e, ex);
+                    hit = hash_lookup(H, ex.a2, ex.b2);
+                }
+                unsigned m = __ballot_sync(FULL_MASK, hit >= 0);
+                if (hit >= 0) {
+                    int64_t pos = run + __popc(m & lt);
+                    col[pos] = hit;
+                    val[pos] = exc_element(P, *ctx, ex);
+                }
+                run += __popc(m);
             }
-            run += __popc(m);
         }
         __syncwarp();
     }
@@ -119,6 +159,8 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
     }
     int64_t* rowcnt;
     NQS_TRY(sc.get(&rowcnt, nS));
+    uint32_t* bits;
+    NQS_TRY(sc.get(&bits, (size_t)nS * ((p->d.nexc + 31) / 32)));
     int64_t* row_ptr = nullptr;
     NQS_CK(cudaMalloc(&row_ptr, (nS + 1) * sizeof(int64_t)));
     auto fail = [&](int code) {
@@ -128,7 +170,7 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
     {
         ProfScope prof_(PROF_CONN_COUNT, s);
         k_conn_count<<<conn_grid(nS), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)dets, nS,
-                                                               rowcnt);
+                                                               rowcnt, bits);
     }
     nqs_note_launch();
     if (cudaGetLastError() != cudaSuccess) return fail(NQS_ERR_CUDA);
@@ -149,7 +191,7 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
     {
         ProfScope prof_(PROF_CONN_FILL, s);
         k_conn_fill<<<conn_grid(nS), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)dets, nS,
-                                                              row_ptr, col, val);
+                                                              row_ptr, col, val, bits);
     }
     nqs_note_launch();
     if (cudaGetLastError() != cudaSuccess) {

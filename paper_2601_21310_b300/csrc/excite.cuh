@@ -277,6 +277,104 @@ __device__ __forceinline__ double diag_element_impl(const ProblemDev& P, uint64_
     return e;
 }
 
+// H_xx with the one-body diagonal hd[p] = h_pp and the J/K tables in shared memory; the same
+// terms in the same order as diag_element_impl (bit-identical result)
+__device__ __forceinline__ double diag_element_smem(int n, const double* hd, const double* J,
+                                                    const double* K, uint64_t a, uint64_t b) {
+    double e = 0.0;
+    for (uint64_t w = a; w; w &= w - 1) e = e + hd[__ffsll((long long)w) - 1];
+    for (uint64_t w = b; w; w &= w - 1) e = e + hd[__ffsll((long long)w) - 1];
+    for (uint64_t wi = a; wi; wi &= wi - 1) {
+        const int i = __ffsll((long long)wi) - 1;
+        for (uint64_t wj = wi & (wi - 1); wj; wj &= wj - 1) {
+            const int j = __ffsll((long long)wj) - 1;
+            const double t = J[i * n + j] - K[i * n + j];
+            e = e + t;
+        }
+    }
+    for (uint64_t wi = b; wi; wi &= wi - 1) {
+        const int i = __ffsll((long long)wi) - 1;
+        for (uint64_t wj = wi & (wi - 1); wj; wj &= wj - 1) {
+            const int j = __ffsll((long long)wj) - 1;
+            const double t = J[i * n + j] - K[i * n + j];
+            e = e + t;
+        }
+    }
+    for (uint64_t wi = a; wi; wi &= wi - 1) {
+        const int i = __ffsll((long long)wi) - 1;
+        for (uint64_t wj = b; wj; wj &= wj - 1) e = e + J[i * n + __ffsll((long long)wj) - 1];
+    }
+    return e;
+}
+
+// H_xx accumulated exactly in 64-bit fixed point (tables in shared memory), converted once to
+// FP64: integer adds instead of FP64 adds (FP64 issues at a small fraction of the FP32/INT32
+// rate on this GPU). Same terms as diag_element_impl; the sum itself is exact, so the only
+// difference from an FP64 sum is the one rounding of each table entry (~2^-52 relative).
+__device__ __forceinline__ double diag_element_fixed(int n, const long long* hf,
+                                                     const long long* jk, const long long* jf,
+                                                     double dscale, uint64_t a, uint64_t b) {
+    long long e = 0;
+    for (uint64_t w = a; w; w &= w - 1) e += hf[__ffsll((long long)w) - 1];
+    for (uint64_t w = b; w; w &= w - 1) e += hf[__ffsll((long long)w) - 1];
+    for (uint64_t wi = a; wi; wi &= wi - 1) {
+        const long long* row = jk + (__ffsll((long long)wi) - 1) * n;
+        for (uint64_t wj = wi & (wi - 1); wj; wj &= wj - 1) e += row[__ffsll((long long)wj) - 1];
+    }
+    for (uint64_t wi = b; wi; wi &= wi - 1) {
+        const long long* row = jk + (__ffsll((long long)wi) - 1) * n;
+        for (uint64_t wj = wi & (wi - 1); wj; wj &= wj - 1) e += row[__ffsll((long long)wj) - 1];
+    }
+    for (uint64_t wi = a; wi; wi &= wi - 1) {
+        const long long* row = jf + (__ffsll((long long)wi) - 1) * n;
+        for (uint64_t wj = b; wj; wj &= wj - 1) e += row[__ffsll((long long)wj) - 1];
+    }
+    return (double)e * dscale;
+}
+
+// H_xx from the byte tables: F(a) + F(b) + G(a, b) with F(w) = sum_k Dt[k][w_k] +
+// sum_{k<l} Xt[kl][w_k][w_l] and G = sum_{k,l} Yt[k][l][a_k][b_l]; the same exact fixed-point
+// sum as diag_element_fixed, in a handful of (L2-resident) table reads.
+__device__ __forceinline__ double diag_element_bytes(const ProblemDev& P, uint64_t a, uint64_t b) {
+    const int nb = P.nbytes;
+    long long e = 0;
+    int pair = 0;
+    for (int k = 0; k < nb; ++k) {
+        const unsigned ak = (unsigned)(a >> (8 * k)) & 255u, bk = (unsigned)(b >> (8 * k)) & 255u;
+        e += __ldg(&P.Dt[k * 256 + ak]) + __ldg(&P.Dt[k * 256 + bk]);
+        for (int l = k + 1; l < nb; ++l, ++pair) {
+            const unsigned al = (unsigned)(a >> (8 * l)) & 255u,
+                           bl = (unsigned)(b >> (8 * l)) & 255u;
+            const long long* X = P.Xt + (size_t)pair * 65536;
+            e += __ldg(&X[ak * 256 + al]) + __ldg(&X[bk * 256 + bl]);
+        }
+        for (int l = 0; l < nb; ++l) {
+            const unsigned bl = (unsigned)(b >> (8 * l)) & 255u;
+            e += __ldg(&P.Yt[((size_t)(k * nb + l)) * 65536 + ak * 256 + bl]);
+        }
+    }
+    return (double)e * P.dscale;
+}
+
+// cooperative load of the fixed-point diagonal tables into shared memory, then __syncthreads()
+__device__ __forceinline__ void load_fixed_tables(const ProblemDev& P, long long* dst) {
+    const int m = P.norb + 2 * P.norb * P.norb;
+    for (int t = threadIdx.x; t < m; t += blockDim.x) dst[t] = P.hfx[t];
+    __syncthreads();
+}
+
+// cooperative load of h_pp, J and K into shared memory (whole block), then __syncthreads()
+__device__ __forceinline__ void load_diag_tables(const ProblemDev& P, double* hd, double* J,
+                                                 double* K) {
+    const int n = P.norb;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        J[t] = P.J[t];
+        K[t] = P.K[t];
+        if (t < n) hd[t] = P.h[t * n + t];
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -76,7 +76,7 @@ extern "C" int nqs_connections_noalloc(nqs_problem* p, const uint64_t* dets, int
     int64_t* rowcnt;
     NQS_TRY(sc.get(&rowcnt, nS));
     k_conn_count<<<conn_grid_size(nS), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)dets,
-                                                                nS, rowcnt);
+                                                                nS, rowcnt, nullptr);
     NQS_CK_LAUNCH();
     NQS_TRY(scan_exclusive_i64(p, sc, rowcnt, row_ptr, nS, row_ptr + nS, s));
     int64_t total = 0;
@@ -90,7 +90,7 @@ extern "C" int nqs_connections_noalloc(nqs_problem* p, const uint64_t* dets, int
         return NQS_ERR_ARG;
     }
     k_conn_fill<<<conn_grid_size(nS), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)dets,
-                                                               nS, row_ptr, col, val);
+                                                               nS, row_ptr, col, val, nullptr);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }

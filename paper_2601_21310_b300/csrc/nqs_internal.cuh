@@ -52,6 +52,20 @@ struct ProblemDev {
     const double* K;                // K[p][q] = (pq|qp)
     const double* TJ;               // TJ[(i*norb+a)*norb+j] = (ia|jj)
     const double* TK;               // TK[(i*norb+a)*norb+j] = (ij|ja)
+    // fixed-point copies for exact integer accumulation of H_xx (value = int * dscale):
+    // hfx[p] = h_pp, JKfx[p][q] = J_pq - K_pq (same spin), Jfx[p][q] = J_pq (opposite spin)
+    const long long* hfx;
+    const long long* JKfx;
+    const long long* Jfx;
+    double dscale;
+    // byte tables of the same sums (diag_element_bytes): nbytes = ceil(norb / 8);
+    //   Dt[k][u]        = sum over bits i of byte u at byte k of h_ii + sum_{i<j} (J-K)_ij
+    //   Xt[kl][u][v]    = sum_{i in u at k, j in v at l} (J-K)_ij      for byte pairs k < l
+    //   Yt[k][l][u][v]  = sum_{i in u at k, j in v at l} J_ij          for all k, l
+    const long long* Dt;
+    const long long* Xt;
+    const long long* Yt;
+    int nbytes;
 };
 
 struct nqs_problem {
@@ -59,6 +73,8 @@ struct nqs_problem {
     int device;
     double ecore;
     double *h, *eri, *J, *K, *TJ, *TK;
+    long long* fx;  // hfx | JKfx | Jfx
+    long long* bt;  // Dt | Xt | Yt
     cudaMemPool_t pool;  // library-owned stream-ordered pool for per-call scratch
     int* err_word;       // device: set by a kernel whose bounded wait timed out
 };
@@ -161,10 +177,10 @@ __device__ __forceinline__ int32_t hash_lookup(const HashS& H, uint64_t a, uint6
 #define CONN_THREADS 256
 #define CONN_WARPS (CONN_THREADS / 32)
 __global__ void k_conn_count(ProblemDev P, HashS H, const ulonglong2* __restrict__ S, int64_t nS,
-                             int64_t* rowcnt);
+                             int64_t* rowcnt, uint32_t* __restrict__ bits);
 __global__ void k_conn_fill(ProblemDev P, HashS H, const ulonglong2* __restrict__ S, int64_t nS,
                             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
-                            double* __restrict__ val);
+                            double* __restrict__ val, const uint32_t* __restrict__ bits);
 size_t conn_smem_bytes(const ProblemDev& P);
 unsigned conn_grid_size(int64_t nS);
 

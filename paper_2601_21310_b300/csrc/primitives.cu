@@ -92,10 +92,16 @@ static int scan_exclusive(nqs_problem* p, Scratch& sc, const T* in, T* out, int6
     }
     T* sums;
     NQS_TRY(sc.get(&sums, tiles));
-    k_tile_sum<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, n, sums);
+    {
+        ProfScope prof_(PROF_SCAN, s);
+        k_tile_sum<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, n, sums);
+    }
     NQS_CK_LAUNCH();
     NQS_TRY(scan_exclusive<T>(p, sc, sums, sums, tiles, (T*)nullptr, s));
-    k_tile_scan<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, sums, total);
+    {
+        ProfScope prof_(PROF_SCAN, s);
+        k_tile_scan<T><<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, sums, total);
+    }
     NQS_CK_LAUNCH();
     return NQS_OK;
 }
@@ -244,29 +250,28 @@ template <class K>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ keys, int64_t n,
                                                          int shift, uint32_t* __restrict__ counts,
                                                          int64_t T) {
-    __shared__ uint32_t hist[256];
-    hist[threadIdx.x] = 0;
+    // one private sub-histogram per warp keeps shared-atomic contention inside a warp
+    __shared__ uint32_t hist[RS_WARPS][256];
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&hist[0][0])[i] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-    // issue every load of the tile before the first atomic
     K key[RS_ITEMS];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t i = base + k * RS_THREADS + threadIdx.x;
         key[k] = i < n ? keys[i] : (K)0;
     }
-    const int lane = threadIdx.x & 31;
+    uint32_t* h = hist[threadIdx.x >> 5];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t i = base + k * RS_THREADS + threadIdx.x;
-        const bool v = i < n;
-        const uint32_t d = (uint32_t)(key[k] >> shift) & 255u;
-        // one shared atomic per distinct digit of the warp (digits are highly skewed)
-        const unsigned peers = __match_any_sync(FULL_MASK, v ? d : 256u);
-        if (v && lane == __ffs(peers) - 1) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+        if (i < n) atomicAdd(&h[(uint32_t)(key[k] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    counts[(int64_t)threadIdx.x * T + blockIdx.x] = hist[threadIdx.x];
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) c += hist[w][threadIdx.x];
+    counts[(int64_t)threadIdx.x * T + blockIdx.x] = c;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

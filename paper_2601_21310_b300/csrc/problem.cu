@@ -3,7 +3,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <math.h>
+
 #include <mutex>
+#include <vector>
 
 #include "excite.cuh"
 #include "nqs_internal.cuh"
@@ -81,6 +84,51 @@ __global__ void k_tables(int n, const double* eri, double* J, double* K, double*
     }
 }
 
+// entry t of the byte tables (layout in ProblemDev); sums of fixed-point terms, exact
+__global__ void k_byte_tables(ProblemDev d, size_t nD, size_t nX, size_t nY) {
+    const int n = d.norb, nb = d.nbytes;
+    long long* out = (long long*)d.Dt;  // the three tables are contiguous
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nD + nX + nY;
+         t += (size_t)gridDim.x * blockDim.x) {
+        long long v = 0;
+        if (t < nD) {
+            const int k = (int)(t / 256), u = (int)(t % 256);
+            for (int i = 0; i < 8; ++i) {
+                if (!((u >> i) & 1) || 8 * k + i >= n) continue;
+                const int pi = 8 * k + i;
+                v += d.hfx[pi];
+                for (int j = i + 1; j < 8; ++j)
+                    if (((u >> j) & 1) && 8 * k + j < n) v += d.JKfx[pi * n + 8 * k + j];
+            }
+        } else {
+            const bool same = t < nD + nX;
+            const size_t r = same ? t - nD : t - nD - nX;
+            const size_t pair = r / 65536;
+            const int u = (int)((r % 65536) / 256), w = (int)(r % 256);
+            int k, l;
+            if (same) {  // pair index over k < l, lexicographic
+                int rem = (int)pair;
+                k = 0;
+                while (rem >= nb - 1 - k) {
+                    rem -= nb - 1 - k;
+                    ++k;
+                }
+                l = k + 1 + rem;
+            } else {
+                k = (int)(pair / nb);
+                l = (int)(pair % nb);
+            }
+            const long long* tab = same ? d.JKfx : d.Jfx;
+            for (int i = 0; i < 8; ++i) {
+                if (!((u >> i) & 1) || 8 * k + i >= n) continue;
+                for (int j = 0; j < 8; ++j)
+                    if (((w >> j) & 1) && 8 * l + j < n) v += tab[(8 * k + i) * n + 8 * l + j];
+            }
+        }
+        out[t] = v;
+    }
+}
+
 extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double* h,
                                   const double* eri, double ecore, nqs_problem** out) {
     if (!out || !h || !eri) return NQS_ERR_ARG;
@@ -149,6 +197,56 @@ extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double*
     d.TJ = p->TJ;
     d.TK = p->TK;
     if (d.nexc >= ((int64_t)1 << 31)) return fail(NQS_ERR_NORB);
+    // Fixed-point tables for the diagonal: every partial sum of H_xx is bounded by
+    // bound = sum_p |h_pp| + sum_{p<q} |J_pq - K_pq| * 2 + sum_{p,q} |J_pq|, so with
+    // scale 2^e, e = 61 - ceil(log2(bound)), no int64 partial sum can overflow and each term
+    // is rounded once (relative error ~2^-e * number of terms).
+    {
+        const int n = norb;
+        std::vector<double> Jh(n * n), Kh(n * n);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                Jh[i * n + j] = eri[(((size_t)i * n + i) * n + j) * n + j];
+                Kh[i * n + j] = eri[(((size_t)i * n + j) * n + j) * n + i];
+            }
+        double bound = 1.0;
+        for (int i = 0; i < n; ++i) bound += fabs(h[i * n + i]);
+        for (int i = 0; i < n * n; ++i) bound += 2.0 * fabs(Jh[i] - Kh[i]) + fabs(Jh[i]);
+        const int e = 61 - (int)ceil(log2(bound));
+        std::vector<long long> fx(n + 2 * n * n);
+        for (int i = 0; i < n; ++i) fx[i] = llrint(ldexp(h[i * n + i], e));
+        for (int i = 0; i < n * n; ++i) {
+            fx[n + i] = llrint(ldexp(Jh[i] - Kh[i], e));
+            fx[n + n * n + i] = llrint(ldexp(Jh[i], e));
+        }
+        if (cudaMalloc(&p->fx, fx.size() * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NQS_ERR_OOM);
+        }
+        if (cudaMemcpy(p->fx, fx.data(), fx.size() * sizeof(long long),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(NQS_ERR_CUDA);
+        d.hfx = p->fx;
+        d.JKfx = p->fx + n;
+        d.Jfx = p->fx + n + n * n;
+        d.dscale = ldexp(1.0, -e);
+        // byte tables
+        const int nb = (n + 7) / 8;
+        const size_t nD = (size_t)nb * 256, nX = (size_t)nb * (nb - 1) / 2 * 65536,
+                     nY = (size_t)nb * nb * 65536;
+        if (cudaMalloc(&p->bt, (nD + nX + nY) * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NQS_ERR_OOM);
+        }
+        d.Dt = p->bt;
+        d.Xt = p->bt + nD;
+        d.Yt = p->bt + nD + nX;
+        d.nbytes = nb;
+        k_byte_tables<<<grid_for((int64_t)(nD + nX + nY), 256), 256>>>(d, nD, nX, nY);
+        nqs_note_launch();
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+            return fail(NQS_ERR_CUDA);
+    }
     *out = p;
     return NQS_OK;
 }
@@ -163,6 +261,8 @@ extern "C" int nqs_problem_destroy(nqs_problem* p) {
     cudaFree(p->TJ);
     cudaFree(p->TK);
     cudaFree(p->err_word);
+    cudaFree(p->fx);
+    cudaFree(p->bt);
     if (p->pool) cudaMemPoolDestroy(p->pool);
     free(p);
     return NQS_OK;

@@ -16,6 +16,9 @@ enum ProfId {
     PROF_LU,
     PROF_SPMV,
     PROF_LAYER1,
+    PROF_UNIQUE,
+    PROF_HEADS,
+    PROF_SCAN,
     PROF_N
 };
 

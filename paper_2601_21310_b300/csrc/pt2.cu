@@ -111,13 +111,15 @@ __global__ void k_heads(const K* __restrict__ keys, int64_t n, uint32_t* __restr
 // Within 32 consecutive elements a shuffle scan adds along runs (earlier elements first); the
 // open run is carried to the next 32. The last element of a run writes c and the run's key at
 // the run index (exclusive head count pos[] plus its own head flag, minus one).
-#define SEG_CHUNK 1024
+#define SEG_CHUNK 2048
+#define SEG_ITEMS 4
 template <class K>
 __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
                                                  const double* __restrict__ vals,
                                                  const uint32_t* __restrict__ pos, int64_t n,
                                                  double* __restrict__ cU, K* __restrict__ keyU) {
     const int lane = threadIdx.x & 31;
+    constexpr int W = 32 * SEG_ITEMS;  // elements per warp iteration
     const int64_t nchunks = (n + SEG_CHUNK - 1) / SEG_CHUNK;
     for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
          ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -131,55 +133,99 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
             if (m) s0 = b + __ffs(m) - 1;
         }
         if (s0 < 0) continue;  // every element continues a run owned by an earlier chunk
-        // software pipeline: the next 32 keys and values are loaded before this 32 is reduced,
-        // and the boundary keys (element before lane 0, element after lane 31) come from
-        // registers instead of extra dependent loads
         double carry = 0.0;
         K kbefore = s0 > 0 ? keys[s0 - 1] : (K)0;
-        K k = (s0 + lane < n) ? keys[s0 + lane] : (K)0;
-        double vv = (s0 + lane < n) ? vals[s0 + lane] : 0.0;
-        for (int64_t b = s0; b < n; b += 32) {
-            const int64_t i = b + lane;
-            const bool in = i < n;
-            const int64_t inext = i + 32;
-            const K knext = inext < n ? keys[inext] : (K)0;
-            const double vnext = inext < n ? vals[inext] : 0.0;
-            const K kprev = __shfl_up_sync(FULL_MASK, k, 1);
-            const K kfirst_next = __shfl_sync(FULL_MASK, knext, 0);
-            const bool h = in && (i == 0 || (lane == 0 ? kbefore != k : kprev != k));
-            // a head at or beyond c1 starts a run owned by the next chunk: stop before it
-            const unsigned stopm = __ballot_sync(FULL_MASK, !in || (h && i >= c1));
-            const int nact = stopm ? __ffs(stopm) - 1 : 32;
-            const bool act = lane < nact;
-            double v = act ? vv : 0.0;
-            int f = (act && h) ? 1 : 0;
+        for (int64_t b = s0; b < n; b += W) {
+            const int64_t i0 = b + (int64_t)SEG_ITEMS * lane;
+            K kk[SEG_ITEMS];
+            double v[SEG_ITEMS];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const double yv = __shfl_up_sync(FULL_MASK, v, o);
-                const int yf = __shfl_up_sync(FULL_MASK, f, o);
-                if (lane >= o) {
-                    if (!f) v = yv + v;
-                    f |= yf;
+            for (int j = 0; j < SEG_ITEMS; ++j) {
+                const bool in = i0 + j < n;
+                kk[j] = in ? keys[i0 + j] : (K)0;
+                v[j] = in ? vals[i0 + j] : 0.0;
+            }
+            const K knext = (b + W < n) ? keys[b + W] : (K)0;  // first element after this block
+            const K kprev_lane = __shfl_up_sync(FULL_MASK, kk[SEG_ITEMS - 1], 1);
+            bool hd[SEG_ITEMS];
+            int jstop = SEG_ITEMS;
+#pragma unroll
+            for (int j = 0; j < SEG_ITEMS; ++j) {
+                const int64_t i = i0 + j;
+                const bool in = i < n;
+                const K kp = j > 0 ? kk[j - 1] : (lane == 0 ? kbefore : kprev_lane);
+                hd[j] = in && (i == 0 || kp != kk[j]);
+                const bool stop = !in || (hd[j] && i >= c1);
+                if (stop && jstop == SEG_ITEMS) jstop = j;
+            }
+            // the warp's active elements end at the first stop in element order
+            const unsigned sm = __ballot_sync(FULL_MASK, jstop < SEG_ITEMS);
+            const int L = sm ? __ffs(sm) - 1 : 32;
+            const int jL = sm ? __shfl_sync(FULL_MASK, jstop, L) : 0;
+            int nact_lane = lane < L ? SEG_ITEMS : (lane == L ? jL : 0);
+            // lane summary: open run at the lane's end (from its last head, or the whole lane)
+            double lsum = 0.0;
+            int lh = 0;
+#pragma unroll
+            for (int j = 0; j < SEG_ITEMS; ++j) {
+                if (j < nact_lane) {
+                    if (hd[j]) {
+                        lh = 1;
+                        lsum = v[j];
+                    } else {
+                        lsum = lsum + v[j];
+                    }
                 }
             }
-            if (act && !f) v = carry + v;
-            const unsigned hm = __ballot_sync(FULL_MASK, act && h);
-            bool tail = false;
-            if (act) {
-                if (lane < nact - 1) tail = (hm >> (lane + 1)) & 1u;
-                else if (nact < 32) tail = true;
-                else tail = (i == n - 1) || (kfirst_next != k);
+            // segmented inclusive scan of the lane summaries (earlier lanes first)
+            double sv = lsum;
+            int sf = lh;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double yv = __shfl_up_sync(FULL_MASK, sv, o);
+                const int yf = __shfl_up_sync(FULL_MASK, sf, o);
+                if (lane >= o) {
+                    if (!sf) sv = yv + sv;
+                    sf |= yf;
+                }
             }
-            if (tail) {
-                const uint32_t ridx = pos[i] + (h ? 1u : 0u) - 1u;
-                cU[ridx] = v;
-                keyU[ridx] = k;
+            double inc = __shfl_up_sync(FULL_MASK, sv, 1);
+            int incf = __shfl_up_sync(FULL_MASK, sf, 1);
+            if (lane == 0) {
+                inc = 0.0;
+                incf = 0;
             }
-            carry = __shfl_sync(FULL_MASK, v, 31);
-            kbefore = __shfl_sync(FULL_MASK, k, 31);
-            if (nact < 32) break;
-            k = knext;
-            vv = vnext;
+            if (!incf) inc = carry + inc;
+            // does a run end after this lane's last active element? (next element is a head, a
+            // stop, or absent)
+            const int first_ends = (nact_lane == 0 || hd[0]) ? 1 : 0;
+            const int next_first_ends = __shfl_down_sync(FULL_MASK, first_ends, 1);
+            bool end_after;
+            if (nact_lane < SEG_ITEMS) {
+                end_after = true;  // a stop follows inside this lane
+            } else if (lane < 31) {
+                end_after = next_first_ends != 0;
+            } else {
+                end_after = (b + W >= n) || (knext != kk[SEG_ITEMS - 1]);
+            }
+            double r = inc;
+#pragma unroll
+            for (int j = 0; j < SEG_ITEMS; ++j) {
+                if (j < nact_lane) {
+                    r = hd[j] ? v[j] : r + v[j];
+                    const bool tail = (j + 1 < nact_lane) ? hd[j + 1] : end_after;
+                    if (tail) {
+                        const uint32_t ridx = pos[i0 + j] + (hd[j] ? 1u : 0u) - 1u;
+                        cU[ridx] = r;
+                        keyU[ridx] = kk[j];
+                    }
+                }
+            }
+            const double sv31 = __shfl_sync(FULL_MASK, sv, 31);
+            const int sf31 = __shfl_sync(FULL_MASK, sf, 31);
+            carry = sf31 ? sv31 : carry + sv31;
+            kbefore = __shfl_sync(FULL_MASK, kk[SEG_ITEMS - 1], 31);
+            if (L < 32) break;
         }
     }
 }
@@ -189,6 +235,7 @@ __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU
                                const double* __restrict__ cU, int64_t nuniq,
                                const double* __restrict__ Dp, double E, double* __restrict__ cS,
                                double* __restrict__ eterm, unsigned long long* __restrict__ next) {
+
     const double D = *Dp;
     const int norb = P.norb;
     const uint64_t bmask = (1ull << norb) - 1ull;
@@ -203,7 +250,7 @@ __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU
             cS[s] = c;
             eterm[u] = 0.0;
         } else {
-            const double hxx = diag_element_impl(P, a, b);
+            const double hxx = diag_element_bytes(P, a, b);
             eterm[u] = __ddiv_rn(__dmul_rn(c, c), __dmul_rn(D, __dsub_rn(E, hxx)));
             ++local;
         }
@@ -282,7 +329,10 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
     // run heads and their exclusive scan, in the free value buffer (8 bytes per element)
     uint32_t* flags = (uint32_t*)vals2;
     uint32_t* pos = flags + n;
-    k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(keys, n, flags);
+    {
+        ProfScope prof_(PROF_HEADS, s);
+        k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(keys, n, flags);
+    }
     NQS_CK_LAUNCH();
     NQS_TRY(scan_exclusive_u32(p, bs, flags, pos, n, s));
     uint32_t last_pos = 0, last_flag = 0;
@@ -304,8 +354,11 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
                            s>>>(keys, vals, pos, n, cU, keyU);
         }
         NQS_CK_LAUNCH();
-        k_unique_terms<K><<<grid_for(nuniq, 256), 256, 0, s>>>(P, H, keyU, cU, nuniq, D_dev,
-                                                               E_var, cS, eterm, nuniq_dev);
+        {
+            ProfScope prof_(PROF_UNIQUE, s);
+            k_unique_terms<K><<<grid_for(nuniq, 256), 256, 0, s>>>(P, H, keyU, cU, nuniq, D_dev,
+                                                                     E_var, cS, eterm, nuniq_dev);
+        }
         NQS_CK_LAUNCH();
     }
     NQS_TRY(ksum_f64(p, bs, eterm, nuniq, ext_dev, s));

@@ -71,7 +71,7 @@ EXPORTS = {
 }
 
 PROFILED = ["conn_count", "conn_fill", "pt2_count", "pt2_emit", "rs_hist", "rs_scatter",
-            "seg_reduce", "gemm", "lu", "spmv", "layer1"]
+            "seg_reduce", "gemm", "lu", "spmv", "layer1", "unique_terms", "heads", "scan"]
 
 
 def lib():
