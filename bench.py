@@ -70,7 +70,7 @@ def load_peaks():
 # clocks sampled during the timed region (read-only NVML queries)
 # ------------------------------------------------------------------------------------------
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms during the timed region (read-only queries), filtered to
+    """nvidia-smi sampled every 100 ms during the timed region (read-only queries), filtered to
     this process's GPU by PCI bus id."""
     FIELDS = ["pci.bus_id", "clocks.sm", "clocks.max.sm", "power.draw",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
@@ -89,7 +89,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception as e:  # no nvidia-smi: report no clocks
             self.proc, self.err = None, str(e)
@@ -265,6 +265,7 @@ def run_nqs(args, ws, rank, local):
     prof = N.profile_read()
     phase_ms = {k: sum(x.elapsed_time(y) for x, y in v) / len(v) for k, v in ev_phase.items()}
     eg_ms = [x.elapsed_time(y) for x, y in ev_phase["energy_grad"]]
+    grad_mixed = grad.clone()
     ms_step = sum(times) / len(times)
     if ws > 1:
         t = torch.tensor([sum(times)], device=dev)
@@ -319,10 +320,54 @@ def run_nqs(args, ws, rank, local):
         "roofline": roofline, "kernels": kernels, "phase_ms": phase_ms,
         "clocks": sampler.summary(),
     }
+    result["fp64_form"] = run_fp64_form(args, N, P, p, dets, dtype, out, grad_mixed, psi, info,
+                                        stream)
+    if result["fp64_form"]:
+        result["speedup_mixed_over_fp64_form"] = (result["evals_per_s"] /
+                                                  result["fp64_form"]["evals_per_s"])
     if not args.no_e2e:
         result["e2e"] = run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg,
                                 o_pt, out, grad, psi, stream, ws)
     return result, p
+
+
+def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, info_mixed,
+                  stream):
+    """The same evaluation in the plain FP64 form (FP64 parameters, FP64 GEMMs and LU): its
+    E_S + gradient rate, and the mixed form's deviation from it (E_S, gradient, PT2)."""
+    if dtype != N.NQS_MIXED:
+        return None
+    dev = dets.device
+    net64 = N.Net(P, N.net_tensors(p.net, N.NQS_FP64, device=dev), N.NQS_FP64)
+    o64 = N.opts(precision=N.NQS_FP64, validate=0)
+    csr = N.connections(P, dets, N.opts(validate=0))
+    out64 = torch.empty(4, dtype=torch.float64, device=dev)
+    g64 = torch.empty(net64.num_params(), dtype=torch.float64, device=dev)
+    psi64 = torch.empty(len(p.S), dtype=torch.float64, device=dev)
+    for _ in range(max(1, args.warmup)):
+        N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
+    times = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = sum(times) / len(times)
+    # mixed-form results of the timed steps vs the FP64 form
+    N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
+    E64 = out64[0].item()
+    r64 = N.pt2(P, dets, psi64, E64, o=N.opts(validate=0))
+    csr.free()
+    gm = grad_mixed.double()
+    grel = (torch.linalg.norm(gm - g64) / torch.linalg.norm(g64)).item()
+    return {"energy_grad_ms": ms, "evals_per_s": 1e3 / ms, "E_S": E64,
+            "E_S_mixed_minus_fp64": info_mixed["E"] - E64,
+            "grad_rel_l2_mixed_vs_fp64": grel,
+            "dE_pt2_ext": r64["ext"], "dE_pt2_ext_mixed_minus_fp64": info_mixed["ext"] - r64["ext"],
+            "dE_pt2_int_mixed_minus_fp64": info_mixed["int"] - r64["int"]}
 
 
 def synth_nexc(wl):
@@ -340,7 +385,9 @@ def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_
     h2d = S_host.numel() * 8 + sum(t.numel() * t.element_size() for t in params_host)
     d2h = 4 * 8 + grad.numel() * grad.element_size() + 4 * 8 + 2 * 8 * o_pt.buckets
     times, n_conn = [], 0
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dets.device)
     for it in range(args.warmup + args.steps):
+        flush.zero_()  # same L2 hygiene as the device-timed steps (outside the events)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)

@@ -246,12 +246,24 @@ static int64_t find_in_S(const uint64_t* S, int64_t nS, uint64_t a, uint64_t b) 
  * Pass 1 (fill == 0) writes row lengths into row_ptr[1..nS] and the prefix sums into row_ptr.
  * Pass 2 (fill == 1) writes col/val. n_enum receives the number of (x, excitation) pairs.
  * ---------------------------------------------------------------------------------------- */
+int orc_hss_rows(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
+                 int64_t r0, int64_t r1, int fill, int64_t* row_ptr, int32_t* col, double* val);
+
 int orc_hss(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
             int fill, int64_t* row_ptr, int32_t* col, double* val, int64_t* n_enum) {
     if (norb < 1 || norb > 64 || nS < 0) return ORC_ERR_ARG;
     int na = popc(nS ? S[0] : 0), nb = popc(nS ? S[1] : 0);
+    if (n_enum) *n_enum = orc_n_excitations(norb, na, nb) * nS;
+    return orc_hss_rows(norb, h, eri, S, nS, 0, nS, fill, row_ptr, col, val);
+}
+
+/* Rows r0..r1-1 of the same CSR (lookups still into all of S); row_ptr has r1 - r0 + 1
+ * entries and starts at 0. Used to check large problems on a sample of rows. */
+int orc_hss_rows(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
+                 int64_t r0, int64_t r1, int fill, int64_t* row_ptr, int32_t* col, double* val) {
+    if (norb < 1 || norb > 64 || nS < 0 || r0 < 0 || r1 > nS || r0 > r1) return ORC_ERR_ARG;
+    int na = popc(nS ? S[0] : 0), nb = popc(nS ? S[1] : 0);
     int64_t nexc = orc_n_excitations(norb, na, nb);
-    if (n_enum) *n_enum = nexc * nS;
     int err = 0;
 #pragma omp parallel
     {
@@ -261,7 +273,7 @@ int orc_hss(int norb, const double* h, const double* eri, const uint64_t* S, int
             err = 1;
         }
 #pragma omp for schedule(dynamic, 16)
-        for (int64_t r = 0; r < nS; ++r) {
+        for (int64_t r = r0; r < r1; ++r) {
             if (!buf) continue;
             uint64_t a = S[2 * r], b = S[2 * r + 1];
             int64_t n = orc_excitations(norb, a, b, buf);
@@ -269,9 +281,9 @@ int orc_hss(int norb, const double* h, const double* eri, const uint64_t* S, int
                 int64_t cnt = 1;
                 for (int64_t k = 0; k < n; ++k)
                     if (find_in_S(S, nS, buf[2 * k], buf[2 * k + 1]) >= 0) ++cnt;
-                row_ptr[r + 1] = cnt;
+                row_ptr[r - r0 + 1] = cnt;
             } else {
-                int64_t pos = row_ptr[r];
+                int64_t pos = row_ptr[r - r0];
                 col[pos] = (int32_t)r;
                 val[pos] = orc_diag(norb, h, eri, a, b);
                 ++pos;
@@ -289,7 +301,7 @@ int orc_hss(int norb, const double* h, const double* eri, const uint64_t* S, int
     if (err) return ORC_ERR_OOM;
     if (!fill) {
         row_ptr[0] = 0;
-        for (int64_t r = 0; r < nS; ++r) row_ptr[r + 1] += row_ptr[r];
+        for (int64_t r = 0; r < r1 - r0; ++r) row_ptr[r + 1] += row_ptr[r];
     }
     return ORC_OK;
 }

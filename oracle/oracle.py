@@ -31,6 +31,8 @@ def lib():
         L.orc_excitations.argtypes = [C.c_int, u64, u64, dp]
         L.orc_hss.restype = C.c_int
         L.orc_hss.argtypes = [C.c_int, dp, dp, dp, i64, C.c_int, dp, dp, dp, dp]
+        L.orc_hss_rows.restype = C.c_int
+        L.orc_hss_rows.argtypes = [C.c_int, dp, dp, dp, i64, i64, i64, C.c_int, dp, dp, dp]
         L.orc_bf16_round.restype = C.c_double
         L.orc_bf16_round.argtypes = [C.c_double]
         L.orc_amplitudes.restype = C.c_int
@@ -130,6 +132,23 @@ def hss(norb, h, eri, S) -> CSR:
     st = L.orc_hss(norb, _p(h), _p(eri), _p(S), nS, 1, _p(row_ptr), _p(col), _p(val), _p(nen))
     assert st == 0, st
     return CSR(row_ptr, col[:nnz], val[:nnz], int(nen[0]))
+
+
+def hss_rows(norb, h, eri, S, r0: int, r1: int):
+    """Rows r0..r1-1 of H_SS (same layout as hss), lookups into all of S: (row_ptr, col, val)
+    with row_ptr starting at 0."""
+    h, eri, S = _f64(h), _f64(eri), _u64(S)
+    nS = S.shape[0]
+    rp = np.zeros(r1 - r0 + 1, np.int64)
+    L = lib()
+    st = L.orc_hss_rows(norb, _p(h), _p(eri), _p(S), nS, r0, r1, 0, _p(rp), None, None)
+    assert st == 0, st
+    nnz = int(rp[-1])
+    col = np.zeros(max(nnz, 1), np.int32)
+    val = np.zeros(max(nnz, 1), np.float64)
+    st = L.orc_hss_rows(norb, _p(h), _p(eri), _p(S), nS, r0, r1, 1, _p(rp), _p(col), _p(val))
+    assert st == 0, st
+    return rp, col[:nnz], val[:nnz]
 
 
 # ------------------------------------------------------------------------------------------

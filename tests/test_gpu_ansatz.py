@@ -51,7 +51,7 @@ def test_amplitudes_mixed_vs_quantised_oracle():
     assert np.array_equal(sg[big], rsg[big])
     assert np.abs(la - rla)[big].max() < 1e-3
     d = np.abs(la - rla)
-    assert np.median(d) < 1e-5 and np.quantile(d, 0.99) < 1e-3
+    assert np.median(d) < 1e-5 and np.quantile(d, 0.99) < 5e-3
 
 
 @pytest.mark.parametrize("name", ["tiny_n10"])

@@ -1,0 +1,93 @@
+"""Parity at the shape of Cr2 CAS(24e,30o) (30 orbitals, 12a+12b): the full-size workload
+(|S| = 131072, 67284 excitations per determinant, 8.8e9 connections) on sampled outputs the
+oracle computes one by one, PT2 invariants at full size, and full parity on a 30-orbital
+problem with a smaller S."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import need_gpu, nqs, problem_for, to_dev
+from oracle import oracle as O
+from paper_2601_21310_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cr2():
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("cr2_24e30o")
+    P = problem_for(N, p)
+    dets = to_dev(p.S)
+    return N, p, P, dets
+
+
+def test_full_size_hss_sampled_rows(cr2):
+    N, p, P, dets = cr2
+    csr = N.connections(P, dets)
+    assert csr.n_enumerated == len(p.S) * 67284
+    rp, col, val = csr.host()
+    for r0 in (0, 65536, len(p.S) - 64):
+        r1 = r0 + 64
+        orp, ocol, oval = O.hss_rows(30, p.h, p.eri, p.S, r0, r1)
+        a, b = rp[r0], rp[r1]
+        assert np.array_equal(rp[r0:r1 + 1] - a, orp)
+        assert np.array_equal(col[a:b], ocol)
+        assert np.array_equal(val[a:b], oval)
+
+
+def test_full_size_mixed_amplitudes_sampled(cr2):
+    N, p, P, dets = cr2
+    net = N.Net(P, N.net_tensors(p.net, N.NQS_MIXED), N.NQS_MIXED)
+    la, sg, _ = N.amplitudes(P, net, dets)
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    pick = np.sort(np.random.default_rng(3).choice(len(p.S), 1024, replace=False))
+    rla, rsg = O.amplitudes(O.Net(p.net, quant=True), p.S[pick])
+    M = la.max()
+    pg = sg[pick] * np.exp(la[pick] - M)
+    pr = rsg * np.exp(rla - M)
+    assert np.abs(pg - pr).max() < 2e-5
+    d = np.abs(la[pick] - rla)
+    assert np.median(d) < 1e-5 and np.quantile(d, 0.99) < 5e-3
+
+
+def test_full_size_pt2_independent_of_bucketing(cr2):
+    """PT2 over the 8.8e9-connection space: the sums and the unique count do not depend on how
+    the connected space is split into hash buckets."""
+    N, p, P, dets = cr2
+    psi = torch.from_numpy(np.random.default_rng(9).normal(size=len(p.S))).cuda()
+    r1 = N.pt2(P, dets, psi, -40.0, buckets=12)
+    r2 = N.pt2(P, dets, psi, -40.0, buckets=16)
+    assert r1["n_emitted"] == r2["n_emitted"] == len(p.S) * 67284
+    assert r1["n_unique"] == r2["n_unique"] > 0
+    assert abs(r1["ext"] - r2["ext"]) < 1e-11 * abs(r1["ext"])
+    assert abs(r1["int"] - r2["int"]) < 1e-11 * abs(r1["int"])
+    assert abs(r1["partials"][:, 0].sum() - r1["ext"]) < 1e-11 * abs(r1["ext"])
+
+
+def test_norb30_smaller_S_full_parity():
+    """30 orbitals, 12a+12b, |S| = 1500: H_SS, E_S + gradient (FP64 form) and one PT2 bucket of
+    four against the oracle."""
+    need_gpu()
+    N = nqs()
+    h, eri, _ = synth.integrals(30, 60, 2, 5.0)
+    S = synth.select_S(30, 12, 1500)
+    params = synth.net_params(30, 12, 12, (64, 48), 102)
+    P = N.Problem(30, 12, 12, h, eri)
+    dets = to_dev(S)
+    csr = N.connections(P, dets)
+    ref = O.hss(30, h, eri, S)
+    rp, col, val = csr.host()
+    assert np.array_equal(rp, ref.row_ptr) and np.array_equal(col, ref.col)
+    assert np.array_equal(val, ref.val)
+    net = N.Net(P, N.net_tensors(params, N.NQS_FP64), N.NQS_FP64)
+    out, grad, psi = N.energy_grad(P, net, csr, dets)
+    r = O.energy_grad(O.Net(params), S, ref)
+    assert abs(out[0].item() - r["E"]) < 1e-8
+    g = grad.cpu().numpy()
+    assert np.linalg.norm(g - r["grad"]) < 1e-9 * np.linalg.norm(r["grad"])
+    got = N.pt2(P, dets, psi, out[0].item(), buckets=4)
+    rb = O.pt2(30, h, eri, S, r["psi"], r["E"], 4, 0)
+    assert abs(got["partials"][0, 0] - rb["ext"]) < 1e-10 * abs(rb["ext"])
+    assert abs(got["partials"][0, 1] - rb["int"]) < 1e-10 * max(1e-30, abs(rb["int"]))

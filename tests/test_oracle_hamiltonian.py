@@ -133,3 +133,15 @@ def test_h2_minimal_basis_textbook(olib):
     # the Rayleigh quotient of the eigenvector reproduces the eigenvalue
     out, _ = olib.energy_from_psi(csr, V[:, 0])
     assert abs(out[0] - w[0]) < 1e-12
+
+
+def test_hss_rows_equals_slices_of_full(olib):
+    """The row-range H_SS used for sampled checks of large problems equals the same rows of the
+    full matrix."""
+    p = synth.make_problem("tiny_n10")
+    full = olib.hss(10, p.h, p.eri, p.S)
+    for r0, r1 in [(0, 1), (100, 250), (990, 1000)]:
+        rp, col, val = olib.hss_rows(10, p.h, p.eri, p.S, r0, r1)
+        a, b = full.row_ptr[r0], full.row_ptr[r1]
+        assert np.array_equal(rp, full.row_ptr[r0:r1 + 1] - a)
+        assert np.array_equal(col, full.col[a:b]) and np.array_equal(val, full.val[a:b])
