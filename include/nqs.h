@@ -172,6 +172,35 @@ int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64
             double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
             nqs_stream_t stream);
 
+/* ---- batched evaluation of many independent problems ------------------------------------ */
+typedef struct nqs_batch nqs_batch; /* opaque */
+
+/* A batch of n independent E_S + gradient evaluations (nqs_energy_grad per problem; problems
+ * may differ in norb, electron counts, |S| and network width). All arrays have n entries and
+ * refer to caller-owned objects that must outlive the batch: problems[i], nets[i] (with
+ * nets[i] created on problems[i]), csrs[i] (from nqs_connections on dets[i]), dets[i] (device
+ * [nS[i]][2]), outs[i] (device [4]) and grads[i] (device, or NULL for energy only).
+ * nstreams side streams run the problems concurrently (largest |S| first). */
+int nqs_batch_create(int n, nqs_problem* const* problems, nqs_net* const* nets,
+                     const nqs_csr* csrs, const uint64_t* const* dets, const int64_t* nS,
+                     double* const* outs, void* const* grads, int nstreams, nqs_batch** out);
+/* Run the batch eagerly: fork from `stream`, one pipeline per problem on the side streams,
+ * join back; stream-ordered, no host sync. */
+int nqs_batch_run(nqs_batch* batch, nqs_stream_t stream);
+/* Record nqs_batch_run once into a CUDA graph (stream must not be the legacy NULL stream) and
+ * instantiate it; nqs_batch_launch then replays the whole batch with one graph launch. Run
+ * the batch eagerly (with autotuning on, if wanted) before capturing. */
+int nqs_batch_capture(nqs_batch* batch, nqs_stream_t stream);
+int nqs_batch_launch(nqs_batch* batch, nqs_stream_t stream);
+int nqs_batch_destroy(nqs_batch* batch);
+
+/* GEMM tile-width autotuner (project-written): when on, the first tensor-core GEMM of each
+ * shape times tile widths 64/128/256 on its stream and keeps the fastest for the process
+ * (never inside stream capture). nqs_autotune_entries copies up to capacity tuned shapes
+ * (M, N, K, chosen width) and returns how many there are. */
+int nqs_set_autotune(int on);
+int nqs_autotune_entries(int* M, int* N, int* K, int* width, int capacity);
+
 /* H_SS build without any device allocation (the paper has no counterpart: this exists for
  * callers that cannot allocate device memory, such as a host framework that owns every
  * allocation or code that must not call the allocator while work is being recorded).

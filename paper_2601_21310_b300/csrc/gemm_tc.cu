@@ -17,6 +17,7 @@
 #include <cudaTypedefs.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 
 #include "ansatz.cuh"
@@ -370,12 +371,8 @@ int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int
 
 }  // namespace
 
-// Tensor-core GEMM for row-major K-major operands: see gemm_bf16_tcgen05 in ansatz.cuh.
-int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s) {
-    if (g.M <= 0 || g.N <= 0 || g.K <= 0) return NQS_ERR_ARG;
-    if ((g.lda * 2) % 16 || (g.ldb * 2) % 16 || ((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15))
-        return NQS_ERR_UNSUPPORTED;
-    const int BN = g.N <= 64 ? 64 : (g.N <= 128 ? 128 : 256);
+// launch with a given tile width
+static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
     CUtensorMap ta, tb;
     NQS_TRY(make_map(&ta, g.A, g.M, g.K, g.lda, 128));
     NQS_TRY(make_map(&tb, g.B, g.N, g.K, g.ldb, BN));
@@ -418,6 +415,92 @@ int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s) {
         NQS_CK_LAUNCH();
     }
     return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// tile-width autotuner: when enabled, the first GEMM of each (M, N, K, epilogue, output kind)
+// shape is timed with BN = 64, 128 and 256 (CUDA events on the launching stream, one warm-up
+// and two timed runs each) and the fastest width is remembered for the process. Tuning never
+// runs inside stream capture; untuned shapes use the heuristic below.
+// ------------------------------------------------------------------------------------------
+namespace {
+struct TuneKey {
+    int M, N, K, epi, kind;
+    bool operator<(const TuneKey& o) const {
+        if (M != o.M) return M < o.M;
+        if (N != o.N) return N < o.N;
+        if (K != o.K) return K < o.K;
+        if (epi != o.epi) return epi < o.epi;
+        return kind < o.kind;
+    }
+};
+std::map<TuneKey, int> g_tuned;
+std::mutex g_tune_mu;
+bool g_autotune = false;
+
+int heuristic_bn(int N) { return N <= 64 ? 64 : (N <= 128 ? 128 : 256); }
+}  // namespace
+
+extern "C" int nqs_set_autotune(int on) {
+    g_autotune = on != 0;
+    return NQS_OK;
+}
+
+extern "C" int nqs_autotune_entries(int* M, int* N, int* K, int* bn, int capacity) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int i = 0;
+    for (const auto& kv : g_tuned) {
+        if (i < capacity && M && N && K && bn) {
+            M[i] = kv.first.M;
+            N[i] = kv.first.N;
+            K[i] = kv.first.K;
+            bn[i] = kv.second;
+        }
+        ++i;
+    }
+    return i;
+}
+
+int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0) return NQS_ERR_ARG;
+    if ((g.lda * 2) % 16 || (g.ldb * 2) % 16 || ((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15))
+        return NQS_ERR_UNSUPPORTED;
+    const TuneKey key{g.M, g.N, g.K, g.epi, (g.c_bf16 ? 1 : 0) | (g.CT ? 2 : 0)};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return gemm_tc_run(g, sc, s, it->second);
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NQS_CK(cudaStreamIsCapturing(s, &cap));
+    if (!g_autotune || cap != cudaStreamCaptureStatusNone)
+        return gemm_tc_run(g, sc, s, heuristic_bn(g.N));
+    cudaEvent_t e0, e1;
+    NQS_CK(cudaEventCreate(&e0));
+    NQS_CK(cudaEventCreate(&e1));
+    int best = heuristic_bn(g.N);
+    float best_ms = 1e30f;
+    for (int bn : {64, 128, 256}) {
+        if (bn >= 2 * ((g.N + 63) / 64 * 64)) continue;  // tile at least twice as wide as N
+        NQS_TRY(gemm_tc_run(g, sc, s, bn));
+        NQS_CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 2; ++r) NQS_TRY(gemm_tc_run(g, sc, s, bn));
+        NQS_CK(cudaEventRecord(e1, s));
+        NQS_CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        NQS_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = bn;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = best;
+    }
+    return gemm_tc_run(g, sc, s, best);
 }
 
 int gemm_bf16_tc(const GemmArgs& g, bool out_bf16, cudaStream_t s) {

@@ -63,6 +63,14 @@ EXPORTS = {
     "nqs_profile_reset": (C.c_int, []),
     "nqs_profile_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p]),
     "nqs_launch_count": (C.c_int64, []),
+    "nqs_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "nqs_batch_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nqs_batch_capture": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nqs_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nqs_batch_destroy": (C.c_int, [C.c_void_p]),
+    "nqs_set_autotune": (C.c_int, [C.c_int]),
+    "nqs_autotune_entries": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "nqs_gemm_bf16": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_int,
                                 C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "nqs_connections_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
@@ -359,6 +367,57 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
     if int(err.item()) != 0:
         raise NQSError("nqs_gemm_bf16: a pipeline wait timed out")
     return C_
+
+
+class Batch:
+    """nqs_batch: many independent E_S + gradient evaluations run concurrently, optionally as
+    one CUDA graph. items: list of (problem, net, csr, dets, out[4], grad) tuples."""
+
+    def __init__(self, items, nstreams: int = 16):
+        self.items = items  # keeps every referenced object alive
+        n = len(items)
+        P = (C.c_void_p * n)(*[it[0].handle.value for it in items])
+        Nt = (C.c_void_p * n)(*[it[1].handle.value for it in items])
+        csrs = (CSRStruct * n)(*[it[2].s for it in items])
+        D = (C.c_void_p * n)(*[it[3].data_ptr() for it in items])
+        nS = (C.c_int64 * n)(*[it[3].shape[0] for it in items])
+        O = (C.c_void_p * n)(*[it[4].data_ptr() for it in items])
+        G = (C.c_void_p * n)(*[(it[5].data_ptr() if it[5] is not None else 0) for it in items])
+        h = C.c_void_p()
+        _check(lib().nqs_batch_create(n, P, Nt, csrs, D, nS, O, G, nstreams, C.byref(h)),
+               "nqs_batch_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(lib().nqs_batch_run(self.handle, _stream(stream)), "nqs_batch_run")
+
+    def capture(self, stream):
+        _check(lib().nqs_batch_capture(self.handle, _stream(stream)), "nqs_batch_capture")
+
+    def launch(self, stream):
+        _check(lib().nqs_batch_launch(self.handle, _stream(stream)), "nqs_batch_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().nqs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def set_autotune(on: bool):
+    lib().nqs_set_autotune(1 if on else 0)
+
+
+def autotune_entries():
+    n = lib().nqs_autotune_entries(None, None, None, None, 0)
+    arrs = [(C.c_int * max(n, 1))() for _ in range(4)]
+    lib().nqs_autotune_entries(*arrs, n)
+    return [(arrs[0][i], arrs[1][i], arrs[2][i], arrs[3][i]) for i in range(n)]
 
 
 def profile_enable(on: bool = True):
