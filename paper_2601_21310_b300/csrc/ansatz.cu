@@ -337,10 +337,148 @@ __global__ void k_combine(int64_t M, const double* la2, const int8_t* sg2, doubl
     }
 }
 
+// Small blocks: one thread per (det, spin block), the block in registers (N known at compile
+// time, so every register index is static; the pivot row is swapped with predicated moves).
+// Same partial pivoting as the warp kernel (largest |a_ik|, lowest row on ties), log|det| in
+// FP64, and the inverse solved column by column from the factors.
+template <class T, int N>
+__global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ dets, int64_t M,
+                                                int norb, int nel, int spin,
+                                                const T* __restrict__ Phi,
+                                                double* __restrict__ la_out,
+                                                int8_t* __restrict__ sg_out, T* __restrict__ Ainv,
+                                                int* singular) {
+    const int col0 = spin == 0 ? 0 : nel - N;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const ulonglong2 x = dets[m];
+        uint64_t w = spin == 0 ? x.x : x.y;
+        const T* phi = Phi + m * (int64_t)norb * nel + col0;
+        T A[N][N];
+        int perm[N];
+#pragma unroll
+        for (int r = 0; r < N; ++r) {
+            const int p = __ffsll((long long)w) - 1;
+            w &= w - 1;
+#pragma unroll
+            for (int c = 0; c < N; ++c) A[r][c] = phi[(int64_t)p * nel + c];
+            perm[r] = r;
+        }
+        int sgn = 1;
+        double la = 0.0;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            T best = fabs(A[k][k]);
+            int pv = k;
+#pragma unroll
+            for (int i = k + 1; i < N; ++i)
+                if (fabs(A[i][k]) > best) {
+                    best = fabs(A[i][k]);
+                    pv = i;
+                }
+            if (pv != k) {
+                sgn = -sgn;
+#pragma unroll
+                for (int i = k + 1; i < N; ++i)
+                    if (i == pv) {
+#pragma unroll
+                        for (int c = 0; c < N; ++c) {
+                            const T t = A[k][c];
+                            A[k][c] = A[i][c];
+                            A[i][c] = t;
+                        }
+                        const int t = perm[k];
+                        perm[k] = perm[i];
+                        perm[i] = t;
+                    }
+            }
+            const T piv = A[k][k];
+            if (piv == T(0)) ok = false;
+            if (ok) {
+                if (piv < T(0)) sgn = -sgn;
+                la += log(fabs((double)piv));
+#pragma unroll
+                for (int i = k + 1; i < N; ++i) {
+                    const T l = A[i][k] / piv;
+                    A[i][k] = l;
+#pragma unroll
+                    for (int j = k + 1; j < N; ++j) A[i][j] -= l * A[k][j];
+                }
+            }
+        }
+        la_out[m] = ok ? la : -INFINITY;
+        sg_out[m] = (int8_t)(ok ? sgn : 0);
+        if (!ok && singular) atomicOr(singular, 1);
+        if (Ainv) {
+            T* out = Ainv + m * (int64_t)N * N;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                T y[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    T v = perm[i] == c ? T(1) : T(0);
+#pragma unroll
+                    for (int j = 0; j < i; ++j) v -= A[i][j] * y[j];
+                    y[i] = v;
+                }
+#pragma unroll
+                for (int i = N - 1; i >= 0; --i) {
+                    T v = y[i];
+#pragma unroll
+                    for (int j = i + 1; j < N; ++j) v -= A[i][j] * y[j];
+                    y[i] = ok ? v / A[i][i] : T(0);
+                }
+#pragma unroll
+                for (int i = 0; i < N; ++i) out[i * N + c] = y[i];
+            }
+        }
+    }
+}
+
+template <class T, int N>
+static int launch_lu_reg_n(const uint64_t* dets, int64_t M, int norb, int nel, int spin,
+                           const T* Phi, double* la, int8_t* sg, T* Ainv, int* singular,
+                           cudaStream_t s) {
+    k_lu_reg<T, N><<<grid_for(M, 128, 148 * 32), 128, 0, s>>>((const ulonglong2*)dets, M, norb, nel,
+                                                              spin, Phi, la, sg, Ainv, singular);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// dispatch on the block size; returns NQS_ERR_UNSUPPORTED above the register limit
+template <class T>
+static int launch_lu_reg(const uint64_t* dets, int64_t M, int norb, int nel, int spin, int n,
+                         const T* Phi, double* la, int8_t* sg, T* Ainv, int* singular,
+                         cudaStream_t s) {
+    const int nmax = sizeof(T) == 8 ? 7 : 12;
+    if (n > nmax) return NQS_ERR_UNSUPPORTED;
+    switch (n) {
+#define NQS_LU_CASE(K)                                                                     \
+    case K:                                                                                \
+        return launch_lu_reg_n<T, (K <= (sizeof(T) == 8 ? 7 : 12) ? K : 1)>(               \
+            dets, M, norb, nel, spin, Phi, la, sg, Ainv, singular, s);
+        NQS_LU_CASE(1) NQS_LU_CASE(2) NQS_LU_CASE(3) NQS_LU_CASE(4) NQS_LU_CASE(5)
+        NQS_LU_CASE(6) NQS_LU_CASE(7) NQS_LU_CASE(8) NQS_LU_CASE(9) NQS_LU_CASE(10)
+        NQS_LU_CASE(11) NQS_LU_CASE(12)
+#undef NQS_LU_CASE
+        default: return NQS_ERR_UNSUPPORTED;
+    }
+}
+
 template <class T>
 static int launch_lu(nqs_net* net, const uint64_t* dets, int64_t M, const T* Phi, double* la2,
                      int8_t* sg2, T* Ainv_a, T* Ainv_b, int* singular, cudaStream_t s) {
     const ProblemDev& P = net->prob->d;
+    if (P.na <= (sizeof(T) == 8 ? 7 : 12) && P.nb <= (sizeof(T) == 8 ? 7 : 12)) {
+        const int nel = P.na + P.nb;
+        ProfScope prof_(PROF_LU, s);
+        NQS_TRY(launch_lu_reg<T>(dets, M, P.norb, nel, 0, P.na, Phi, la2, sg2, Ainv_a, singular,
+                                 s));
+        NQS_TRY(launch_lu_reg<T>(dets, M, P.norb, nel, 1, P.nb, Phi, la2 + M, sg2 + M, Ainv_b,
+                                 singular, s));
+        return NQS_OK;
+    }
     int nmax = P.na > P.nb ? P.na : P.nb;
     size_t smem = (size_t)LU_WARPS * 2 * nmax * (nmax + 1) * sizeof(T);
     if (smem > 48 * 1024)
