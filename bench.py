@@ -57,6 +57,21 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max_over_ranks(x: float, device=None) -> float:
+    """Max of a per-rank value over all ranks (identity on one process)."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.item()
+
+
+def whole_job_rate(units_per_rank: float, max_ms: float, world_size: int) -> float:
+    """Weak scaling: every rank processes the same units; the job rate is all ranks' units over
+    the slowest rank's time."""
+    return world_size * units_per_rank / (max_ms / 1e3)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -267,13 +282,8 @@ def run_nqs(args, ws, rank, local):
     eg_ms = [x.elapsed_time(y) for x, y in ev_phase["energy_grad"]]
     grad_mixed = grad.clone()
     ms_step = sum(times) / len(times)
-    if ws > 1:
-        t = torch.tensor([sum(times)], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = t.item()
-    else:
-        total_ms = sum(times)
-    value = ws * n_conn_total / (total_ms / 1e3)
+    total_ms = reduce_max_over_ranks(sum(times), dev)
+    value = whole_job_rate(n_conn_total, total_ms, ws)
 
     # roofline of the dominant instrumented kernel
     peaks, peak_kind = load_peaks()
@@ -407,12 +417,8 @@ def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_
         if it >= args.warmup:
             times.append(a.elapsed_time(b))
             n_conn += n
-    total = sum(times)
-    if ws > 1:
-        t = torch.tensor([total], device=dets.device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = t.item()
-    return {"value": ws * n_conn / (total / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    total = reduce_max_over_ranks(sum(times), dets.device)
+    return {"value": whole_job_rate(n_conn, total, ws), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": total / len(times)}
 
 
