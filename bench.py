@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--buckets", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the plain-FP64 comparison run (e.g. for a launch list of the step)")
     ap.add_argument("--cpu-sample", type=int, default=4096, help="dets in the CPU-baseline sample")
     return ap.parse_args()
 
@@ -255,8 +257,7 @@ def run_nqs(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    N.profile_reset()
-    N.profile_enable(True)
+    # timed region 1: the step as a user runs it (no per-kernel instrumentation)
     launches0 = N.launch_count()
     times = []
     n_conn_total = 0
@@ -276,14 +277,31 @@ def run_nqs(args, ws, rank, local):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall0
     launches = N.launch_count() - launches0
-    N.profile_enable(False)
-    prof = N.profile_read()
     phase_ms = {k: sum(x.elapsed_time(y) for x, y in v) / len(v) for k, v in ev_phase.items()}
     eg_ms = [x.elapsed_time(y) for x, y in ev_phase["energy_grad"]]
     grad_mixed = grad.clone()
     ms_step = sum(times) / len(times)
     total_ms = reduce_max_over_ranks(sum(times), dev)
     value = whole_job_rate(n_conn_total, total_ms, ws)
+
+    # timed region 2: the same steps with every main kernel bracketed by CUDA events on its
+    # launching stream (per-kernel times for the roofline; slightly slower steps)
+    N.profile_reset()
+    N.profile_enable(True)
+    prof_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        prof_times.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    N.profile_enable(False)
+    prof = N.profile_read()
+    ms_step_prof = sum(prof_times) / len(prof_times)
 
     # roofline of the dominant instrumented kernel
     peaks, peak_kind = load_peaks()
@@ -310,7 +328,7 @@ def run_nqs(args, ws, rank, local):
                 "unit": r_unit, "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_per_launch": amount, "peak_source": peak_kind}
     kernels = {k: {"ms_per_step": round(v[0] / args.steps, 4), "launches": v[1],
-                   "share_of_step": round(v[0] / args.steps / ms_step, 4)}
+                   "share_of_step": round(v[0] / args.steps / ms_step_prof, 4)}
                for k, v in prof.items() if v[1] > 0}
 
     result = {
@@ -327,11 +345,12 @@ def run_nqs(args, ws, rank, local):
         "connections_per_step": info["n_conn"], "hss_nnz": info["nnz"],
         "pt2_unique": info["n_unique"], "E_S": info["E"], "dE_pt2_ext": info["ext"],
         "dE_pt2_int": info["int"], "wall_s": wall, "gpu_launches": launches,
-        "roofline": roofline, "kernels": kernels, "phase_ms": phase_ms,
+        "roofline": roofline, "kernels": kernels, "ms_per_step_instrumented": ms_step_prof,
+        "phase_ms": phase_ms,
         "clocks": sampler.summary(),
     }
-    result["fp64_form"] = run_fp64_form(args, N, P, p, dets, dtype, out, grad_mixed, psi, info,
-                                        stream)
+    result["fp64_form"] = None if args.no_fp64_form else run_fp64_form(
+        args, N, P, p, dets, dtype, out, grad_mixed, psi, info, stream)
     if result["fp64_form"]:
         result["speedup_mixed_over_fp64_form"] = (result["evals_per_s"] /
                                                   result["fp64_form"]["evals_per_s"])
