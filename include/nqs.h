@@ -166,8 +166,9 @@ int nqs_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr, cons
  * into hash buckets (SplitMix64 finaliser: bucket = mix(mix(a) ^ b) mod B).
  * psi: device [nS] FP64 at any scale. out: host [4] = {external, internal, number of unique
  * x' in C\S, number of emitted pairs}. bucket_partials: host [2*B] (external, internal per
- * bucket) or NULL. Requires 2*norb <= 64 (single-word keys). Synchronises the stream.
- * Errors: NQS_ERR_ARG, NQS_ERR_NORB, NQS_ERR_OOM, NQS_ERR_CUDA. */
+ * bucket) or NULL. Sort keys are 32-bit, 64-bit or two-word by 2*norb. Each bucket's emissions
+ * must stay below 2^32 (and fit in memory): use more buckets for larger problems. Synchronises
+ * the stream. Errors: NQS_ERR_ARG, NQS_ERR_OOM (a bucket too large), NQS_ERR_CUDA. */
 int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64_t nS,
             double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
             nqs_stream_t stream);

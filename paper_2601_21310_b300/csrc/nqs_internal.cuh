@@ -190,6 +190,62 @@ int validate_dets(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS,
                   cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
+// PT2 sort keys: the determinant (a, b) packed as the 2 norb-bit number (a << norb) | b, in a
+// uint32 (2 norb <= 32), a uint64 (<= 64) or two words (<= 128); numeric order = (a, b) order.
+// ------------------------------------------------------------------------------------------
+struct Key128 {
+    uint64_t lo, hi;
+};
+__host__ __device__ __forceinline__ bool operator!=(const Key128& x, const Key128& y) {
+    return x.lo != y.lo || x.hi != y.hi;
+}
+template <class K>
+__device__ __forceinline__ K key_zero() { return (K)0; }
+template <>
+__device__ __forceinline__ Key128 key_zero<Key128>() { return Key128{0ull, 0ull}; }
+template <class K>
+__device__ __forceinline__ uint32_t key_digit(const K& k, int s) { return (uint32_t)(k >> s) & 255u; }
+__device__ __forceinline__ uint32_t key_digit(const Key128& k, int s) {
+    return (uint32_t)(s < 64 ? (k.lo >> s) : (k.hi >> (s - 64))) & 255u;
+}
+template <class K>
+__device__ __forceinline__ K key_make(uint64_t a, uint64_t b, int norb) {
+    return (K)((a << norb) | b);
+}
+template <>
+__device__ __forceinline__ Key128 key_make<Key128>(uint64_t a, uint64_t b, int norb) {
+    Key128 k;
+    k.lo = b | (norb < 64 ? (a << norb) : 0ull);
+    k.hi = norb == 0 ? 0ull : (a >> (64 - norb));
+    return k;
+}
+template <class K>
+__device__ __forceinline__ void key_split(const K& k, int norb, uint64_t& a, uint64_t& b) {
+    const uint64_t v = (uint64_t)k;
+    a = v >> norb;
+    b = v & ((1ull << norb) - 1ull);
+}
+__device__ __forceinline__ void key_split(const Key128& k, int norb, uint64_t& a, uint64_t& b) {
+    const uint64_t m = norb >= 64 ? ~0ull : ((1ull << norb) - 1ull);
+    b = k.lo & m;
+    a = ((k.lo >> norb) | (k.hi << (64 - norb))) & m;
+}
+template <class K>
+__device__ __forceinline__ K key_shfl_up(const K& k, int d) {
+    return __shfl_up_sync(0xffffffffu, k, d);
+}
+__device__ __forceinline__ Key128 key_shfl_up(const Key128& k, int d) {
+    return Key128{__shfl_up_sync(0xffffffffu, k.lo, d), __shfl_up_sync(0xffffffffu, k.hi, d)};
+}
+template <class K>
+__device__ __forceinline__ K key_shfl(const K& k, int src) {
+    return __shfl_sync(0xffffffffu, k, src);
+}
+__device__ __forceinline__ Key128 key_shfl(const Key128& k, int src) {
+    return Key128{__shfl_sync(0xffffffffu, k.lo, src), __shfl_sync(0xffffffffu, k.hi, src)};
+}
+
+// ------------------------------------------------------------------------------------------
 // primitives (primitives.cu)
 // ------------------------------------------------------------------------------------------
 // exclusive prefix sum of n values; total (device, may be null) receives the sum
@@ -214,6 +270,9 @@ int radix_sort_pairs(nqs_problem* p, Scratch& sc, uint64_t*& keys, double*& vals
 int radix_sort_pairs32(nqs_problem* p, Scratch& sc, uint32_t*& keys, double*& vals,
                        uint32_t*& keys_alt, double*& vals_alt, int64_t n, int bits,
                        cudaStream_t s);
+int radix_sort_pairs128(nqs_problem* p, Scratch& sc, Key128*& keys, double*& vals,
+                        Key128*& keys_alt, double*& vals_alt, int64_t n, int bits,
+                        cudaStream_t s);
 
 inline unsigned grid_for(int64_t n, int block, int cap = 148 * 32) {
     int64_t g = (n + block - 1) / block;

@@ -242,14 +242,20 @@ int max_f64_masked(nqs_problem* p, Scratch& sc, const double* x, const int8_t* m
 // Equal digits keep their input order (stable). No inter-block waiting of any kind.
 // ------------------------------------------------------------------------------------------
 #define RS_THREADS 256
-#define RS_ITEMS 16
-#define RS_TILE (RS_THREADS * RS_ITEMS)
 #define RS_WARPS (RS_THREADS / 32)
+// items per thread: 16 for 4/8-byte keys, 8 for 16-byte keys (tile staging must fit in smem)
+template <class K>
+struct RsCfg {
+    static constexpr int ITEMS = sizeof(K) > 8 ? 8 : 16;
+    static constexpr int TILE = RS_THREADS * ITEMS;
+};
 
 template <class K>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ keys, int64_t n,
                                                          int shift, uint32_t* __restrict__ counts,
                                                          int64_t T) {
+    constexpr int RS_ITEMS = RsCfg<K>::ITEMS;
+    constexpr int RS_TILE = RsCfg<K>::TILE;
     // one private sub-histogram per warp keeps shared-atomic contention inside a warp
     __shared__ uint32_t hist[RS_WARPS][256];
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&hist[0][0])[i] = 0;
@@ -259,13 +265,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const K* __restrict__ ke
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t i = base + k * RS_THREADS + threadIdx.x;
-        key[k] = i < n ? keys[i] : (K)0;
+        key[k] = i < n ? keys[i] : key_zero<K>();
     }
     uint32_t* h = hist[threadIdx.x >> 5];
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int64_t i = base + k * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(uint32_t)(key[k] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&h[key_digit(key[k], shift)], 1u);
     }
     __syncthreads();
     uint32_t c = 0;
@@ -291,6 +297,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
                                                             int shift,
                                                             const uint32_t* __restrict__ offs,
                                                             int64_t T, int* err) {
+    constexpr int RS_ITEMS = RsCfg<K>::ITEMS;
+    constexpr int RS_TILE = RsCfg<K>::TILE;
     extern __shared__ __align__(16) uint8_t rs_smem[];
     double* sv = (double*)rs_smem;             // [RS_TILE] values, input order
     K* sk = (K*)(sv + RS_TILE);                // [RS_TILE] keys, input order
@@ -366,7 +374,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int li = wb + k * 32 + lane;
         const bool v = li < tn;
-        const uint32_t d = v ? ((uint32_t)(sk[li] >> shift) & 255u) : 256u;
+        const uint32_t d = v ? key_digit(sk[li], shift) : 256u;
         const unsigned peers = __match_any_sync(FULL_MASK, d);
         const uint32_t old = v ? whist[warp][d] : 0u;
         __syncwarp();
@@ -388,7 +396,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     for (int k = 0; k < RS_ITEMS; ++k) {
         const int li = wb + k * 32 + lane;
         if (li < tn) {
-            const uint32_t d = (uint32_t)(sk[li] >> shift) & 255u;
+            const uint32_t d = key_digit(sk[li], shift);
             perm[dstart[d] + whist[warp][d] + rank[k]] = (uint16_t)li;
         }
     }
@@ -396,7 +404,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     for (int i = threadIdx.x; i < tn; i += RS_THREADS) {
         const int j = perm[i];
         const K kk = sk[j];
-        const uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        const uint32_t d = key_digit(kk, shift);
         const uint32_t gp = goff[d] + (uint32_t)i - dstart[d];
         kout[gp] = kk;
         vout[gp] = sv[j];
@@ -408,6 +416,7 @@ static int radix_sort_impl(nqs_problem* p, Scratch& sc, K*& keys, double*& vals,
                            double*& vals_alt, int64_t n, int bits, cudaStream_t s) {
     if (n <= 1) return NQS_OK;
     if (n >= (int64_t)1 << 32) return NQS_ERR_UNSUPPORTED;
+    constexpr int RS_TILE = RsCfg<K>::TILE;
     int64_t T = (n + RS_TILE - 1) / RS_TILE;
     uint32_t* counts;
     NQS_TRY(sc.get(&counts, 256 * T));
@@ -446,4 +455,10 @@ int radix_sort_pairs32(nqs_problem* p, Scratch& sc, uint32_t*& keys, double*& va
                        uint32_t*& keys_alt, double*& vals_alt, int64_t n, int bits,
                        cudaStream_t s) {
     return radix_sort_impl<uint32_t>(p, sc, keys, vals, keys_alt, vals_alt, n, bits, s);
+}
+
+int radix_sort_pairs128(nqs_problem* p, Scratch& sc, Key128*& keys, double*& vals,
+                        Key128*& keys_alt, double*& vals_alt, int64_t n, int bits,
+                        cudaStream_t s) {
+    return radix_sort_impl<Key128>(p, sc, keys, vals, keys_alt, vals_alt, n, bits, s);
 }

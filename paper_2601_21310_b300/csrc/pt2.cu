@@ -12,8 +12,8 @@
 //      c^2 / (D (E - H_x'x')) with H_x'x' from the Slater-Condon diagonal;
 //   4. compensated sums of the external terms, and of the internal terms of the dets of S in
 //      bucket b: r_x = H_xx psi_x + c(x) - E psi_x, r_x^2 / (D (E - H_xx)).
-// D = psi.psi, compensated. Keys are (a << norb) | b: uint32 when 2 norb <= 32, else uint64
-// (so 2 norb <= 64).
+// D = psi.psi, compensated. Keys are the 2 norb-bit number (a << norb) | b: uint32 when
+// 2 norb <= 32, uint64 when <= 64, two words above.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit(ProblemDev P,
             unsigned m = __ballot_sync(FULL_MASK, take);
             if (take) {
                 int64_t pos = run + __popc(m & lt);
-                keys[pos] = (K)((ex.a2 << norb) | ex.b2);
+                keys[pos] = key_make<K>(ex.a2, ex.b2, norb);
                 vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
             }
             run += __popc(m);
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
         }
         if (s0 < 0) continue;  // every element continues a run owned by an earlier chunk
         double carry = 0.0;
-        K kbefore = s0 > 0 ? keys[s0 - 1] : (K)0;
+        K kbefore = s0 > 0 ? keys[s0 - 1] : key_zero<K>();
         for (int64_t b = s0; b < n; b += W) {
             const int64_t i0 = b + (int64_t)SEG_ITEMS * lane;
             K kk[SEG_ITEMS];
@@ -142,11 +142,11 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
 #pragma unroll
             for (int j = 0; j < SEG_ITEMS; ++j) {
                 const bool in = i0 + j < n;
-                kk[j] = in ? keys[i0 + j] : (K)0;
+                kk[j] = in ? keys[i0 + j] : key_zero<K>();
                 v[j] = in ? vals[i0 + j] : 0.0;
             }
-            const K knext = (b + W < n) ? keys[b + W] : (K)0;  // first element after this block
-            const K kprev_lane = __shfl_up_sync(FULL_MASK, kk[SEG_ITEMS - 1], 1);
+            const K knext = (b + W < n) ? keys[b + W] : key_zero<K>();  // first element after this block
+            const K kprev_lane = key_shfl_up(kk[SEG_ITEMS - 1], 1);
             bool hd[SEG_ITEMS];
             int jstop = SEG_ITEMS;
 #pragma unroll
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
             const double sv31 = __shfl_sync(FULL_MASK, sv, 31);
             const int sf31 = __shfl_sync(FULL_MASK, sf, 31);
             carry = sf31 ? sv31 : carry + sv31;
-            kbefore = __shfl_sync(FULL_MASK, kk[SEG_ITEMS - 1], 31);
+            kbefore = key_shfl(kk[SEG_ITEMS - 1], 31);
             if (L < 32) break;
         }
     }
@@ -238,12 +238,11 @@ __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU
 
     const double D = *Dp;
     const int norb = P.norb;
-    const uint64_t bmask = (1ull << norb) - 1ull;
     unsigned long long local = 0;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nuniq;
          u += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = (uint64_t)keyU[u];
-        const uint64_t a = k >> norb, b = k & bmask;
+        uint64_t a, b;
+        key_split(keyU[u], norb, a, b);
         const double c = cU[u];
         const int32_t s = hash_lookup(H, a, b);
         if (s >= 0) {
@@ -323,9 +322,12 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
     if (sizeof(K) == 4)
         NQS_TRY(radix_sort_pairs32(p, bs, (uint32_t*&)keys, vals, (uint32_t*&)keys2, vals2, n,
                                    2 * P.norb, s));
-    else
+    else if (sizeof(K) == 8)
         NQS_TRY(radix_sort_pairs(p, bs, (uint64_t*&)keys, vals, (uint64_t*&)keys2, vals2, n,
                                  2 * P.norb, s));
+    else
+        NQS_TRY(radix_sort_pairs128(p, bs, (Key128*&)keys, vals, (Key128*&)keys2, vals2, n,
+                                    2 * P.norb, s));
     // run heads and their exclusive scan, in the free value buffer (8 bytes per element)
     uint32_t* flags = (uint32_t*)vals2;
     uint32_t* pos = flags + n;
@@ -370,7 +372,6 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
                        nqs_stream_t stream) {
     if (!p || !dets || !psi || !out || nS <= 0) return NQS_ERR_ARG;
     if (((uintptr_t)dets) & 15) return NQS_ERR_ARG;
-    if (2 * p->d.norb > 64) return NQS_ERR_NORB;
     if (nS >= ((int64_t)1 << 31)) return NQS_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     nqs_opts def;
@@ -391,6 +392,8 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit<uint32_t>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit<uint64_t>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_pt2_emit<Key128>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     double* dev_scalars;  // [0] = D, then per bucket (ext, int)
@@ -413,7 +416,7 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
         NQS_TRY(sc.get(&total_dev, 1));
     }
     const int64_t cap = opts->chunk > 0 ? opts->chunk : ((int64_t)1 << 32) - 1;
-    const bool k32 = 2 * P.norb <= 32;
+    const int kbits = 2 * P.norb;  // 32-bit, 64-bit or two-word keys
     int64_t total_emitted = 0;
     for (int64_t b = 0; b < B; ++b) {
         int64_t n;
@@ -433,12 +436,17 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
         }
         if (n > cap) return NQS_ERR_OOM;  // more buckets needed
         total_emitted += n;
-        int st = k32 ? pt2_bucket<uint32_t>(p, dets, psi, nS, E_var, B, b, B == 1 ? nullptr : offs,
-                                            n, H, cS, dev_scalars, dev_scalars + 1 + 2 * b,
-                                            next_dev + b, smem, s)
-                     : pt2_bucket<uint64_t>(p, dets, psi, nS, E_var, B, b, B == 1 ? nullptr : offs,
-                                            n, H, cS, dev_scalars, dev_scalars + 1 + 2 * b,
-                                            next_dev + b, smem, s);
+        const int64_t* o = B == 1 ? nullptr : offs;
+        int st = kbits <= 32
+                     ? pt2_bucket<uint32_t>(p, dets, psi, nS, E_var, B, b, o, n, H, cS,
+                                            dev_scalars, dev_scalars + 1 + 2 * b, next_dev + b,
+                                            smem, s)
+                 : kbits <= 64
+                     ? pt2_bucket<uint64_t>(p, dets, psi, nS, E_var, B, b, o, n, H, cS,
+                                            dev_scalars, dev_scalars + 1 + 2 * b, next_dev + b,
+                                            smem, s)
+                     : pt2_bucket<Key128>(p, dets, psi, nS, E_var, B, b, o, n, H, cS, dev_scalars,
+                                          dev_scalars + 1 + 2 * b, next_dev + b, smem, s);
         NQS_TRY(st);
         if (opts->internal_pt2) {
             k_pt2_internal<<<grid_for(nS, 256), 256, 0, s>>>(P, (const ulonglong2*)dets, psi, cS,

@@ -258,6 +258,26 @@ class CSR:
                     raise NQSError(f"cudaMemcpy failed ({st})")
         return rp, col[:self.nnz], val[:self.nnz]
 
+    def host_rows(self, r0: int, r1: int):
+        """Rows r0..r1-1 copied to host: (row_ptr starting at 0, col, val)."""
+        import numpy as np
+        torch.cuda.synchronize()
+        cudart = _cudart()
+        rp = np.zeros(r1 - r0 + 1, np.int64)
+        st = cudart.cudaMemcpy(C.c_void_p(rp.ctypes.data), C.c_void_p(self.s.row_ptr + 8 * r0),
+                               C.c_size_t(rp.nbytes), 2)
+        if st != 0:
+            raise NQSError(f"cudaMemcpy failed ({st})")
+        a, b = int(rp[0]), int(rp[-1])
+        col = np.zeros(max(b - a, 1), np.int32)
+        val = np.zeros(max(b - a, 1), np.float64)
+        for dst, src, nb in ((col, self.s.col + 4 * a, (b - a) * 4),
+                             (val, self.s.val + 8 * a, (b - a) * 8)):
+            if nb and cudart.cudaMemcpy(C.c_void_p(dst.ctypes.data), C.c_void_p(src),
+                                        C.c_size_t(nb), 2) != 0:
+                raise NQSError("cudaMemcpy failed")
+        return rp - a, col[:b - a], val[:b - a]
+
     def free(self):
         if self.s is not None and self.s.row_ptr:
             lib().nqs_csr_free(C.byref(self.s))

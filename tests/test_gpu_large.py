@@ -91,3 +91,54 @@ def test_norb30_smaller_S_full_parity():
     rb = O.pt2(30, h, eri, S, r["psi"], r["E"], 4, 0)
     assert abs(got["partials"][0, 0] - rb["ext"]) < 1e-10 * abs(rb["ext"])
     assert abs(got["partials"][0, 1] - rb["int"]) < 1e-10 * max(1e-30, abs(rb["int"]))
+
+
+@pytest.fixture(scope="module")
+def cr2_48():
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("cr2_48e42o")
+    P = problem_for(N, p)
+    dets = to_dev(p.S)
+    return N, p, P, dets
+
+
+def test_cr2_48e42o_full_size_hss_amplitudes_energy(cr2_48):
+    """42 orbitals, 24a+24b, |S| = 2^20 (2.85e11 connections): H_SS on sampled rows bit-exactly,
+    mixed-form amplitudes on sampled determinants, and E_S consistent with the matrix."""
+    N, p, P, dets = cr2_48
+    csr = N.connections(P, dets)
+    assert csr.n_enumerated == len(p.S) * 271944
+    for r0 in (0, 500000, len(p.S) - 8):
+        rp, col, val = csr.host_rows(r0, r0 + 8)
+        orp, ocol, oval = O.hss_rows(42, p.h, p.eri, p.S, r0, r0 + 8)
+        assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+        assert np.array_equal(val, oval)
+    net = N.Net(P, N.net_tensors(p.net, N.NQS_MIXED), N.NQS_MIXED)
+    out, grad, psi = N.energy_grad(P, net, csr, dets)
+    la, sg, _ = N.amplitudes(P, net, dets)
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    pick = np.sort(np.random.default_rng(5).choice(len(p.S), 128, replace=False))
+    rla, rsg = O.amplitudes(O.Net(p.net, quant=True), p.S[pick])
+    M = la.max()
+    assert np.abs(sg[pick] * np.exp(la[pick] - M) - rsg * np.exp(rla - M)).max() < 2e-5
+    e2, _ = N.energy_from_psi(csr, psi)
+    assert abs(e2[0].item() - out[0].item()) < 1e-12 * abs(out[0].item())
+    assert bool(torch.isfinite(grad).all())
+    csr.free()
+
+
+def test_norb42_pt2_two_word_keys():
+    """42 orbitals, 24a+24b (84-bit PT2 keys), |S| = 150: one PT2 bucket of four against the
+    oracle, and the unique count over all buckets."""
+    need_gpu()
+    N = nqs()
+    h, eri, _ = synth.integrals(42, 84, 3, 3.0)
+    S = synth.select_S(42, 24, 150)
+    P = N.Problem(42, 24, 24, h, eri)
+    psi = np.random.default_rng(2).normal(size=len(S))
+    got = N.pt2(P, to_dev(S), torch.from_numpy(psi).cuda(), -60.0, buckets=4)
+    ref = O.pt2(42, h, eri, S, psi, -60.0, 4, 1)
+    assert abs(got["partials"][1, 0] - ref["ext"]) < 1e-10 * abs(ref["ext"])
+    assert abs(got["partials"][1, 1] - ref["int"]) < 1e-10 * max(1e-300, abs(ref["int"]))
+    assert got["n_emitted"] == len(S) * 271944
