@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nqs", choices=["nqs", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--buckets", type=int, default=1)
+    ap.add_argument("--buckets", type=int, default=0,
+                    help="PT2 hash buckets (0: enough to keep each bucket under 2^30 emissions)")
+    ap.add_argument("--no-pt2", action="store_true",
+                    help="step without PT2 (for shapes whose PT2 takes minutes); labelled in config")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true",
@@ -217,7 +220,9 @@ def run_nqs(args, ws, rank, local):
     nS = len(p.S)
     o_conn = N.opts(precision=dtype, validate=0)
     o_eg = N.opts(precision=dtype, validate=0)
-    o_pt = N.opts(precision=dtype, buckets=args.buckets, validate=0)
+    nexc_total = nS * synth_nexc(wl)
+    buckets = args.buckets if args.buckets > 0 else max(1, -(-nexc_total // (1 << 30)))
+    o_pt = N.opts(precision=dtype, buckets=buckets, validate=0)
     out = torch.empty(4, dtype=torch.float64, device=dev)
     grad = torch.empty(net.num_params(), dtype=net.grad_dtype(), device=dev)
     psi = torch.empty(nS, dtype=torch.float64, device=dev)
@@ -239,7 +244,10 @@ def run_nqs(args, ws, rank, local):
         N.energy_grad(P, net, csr, dets, o=o_eg, out=out, grad=grad, psi=psi)
         e2 = mark(record)
         E = out[0].item()
-        r = N.pt2(P, dets, psi, E, o=o_pt)
+        if args.no_pt2:
+            r = dict(n_emitted=0, n_unique=0, ext=float("nan"), int=float("nan"))
+        else:
+            r = N.pt2(P, dets, psi, E, o=o_pt)
         e3 = mark(record)
         info = dict(n_conn=csr.n_enumerated + r["n_emitted"], n_hss=csr.n_enumerated,
                     n_emit=r["n_emitted"], nnz=csr.nnz, n_unique=r["n_unique"], E=E,
@@ -338,7 +346,10 @@ def run_nqs(args, ws, rank, local):
         "data": "synthetic (seeded integrals, level-major S, random-init backflow MLP)",
         "config": {"workload": wl.name, "norb": wl.norb, "nalpha": wl.nalpha, "nbeta": wl.nbeta,
                    "n_S": nS, "mlp": [2 * wl.norb, *wl.hidden, wl.norb * wl.nelec],
-                   "pt2_buckets": args.buckets, "l2": "flushed between timed steps (512 MB write)",
+                   "pt2_buckets": 0 if args.no_pt2 else buckets,
+                   "step": "connections + energy_grad" if args.no_pt2 else
+                           "connections + energy_grad + pt2",
+                   "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas{ws}"},
         "evals_per_s": 1e3 / (sum(eg_ms) / len(eg_ms)),
         "dets_evals_per_s": nS * 1e3 / (sum(eg_ms) / len(eg_ms)),
@@ -388,7 +399,8 @@ def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, 
     # mixed-form results of the timed steps vs the FP64 form
     N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
     E64 = out64[0].item()
-    r64 = N.pt2(P, dets, psi64, E64, o=N.opts(validate=0))
+    r64 = (dict(ext=float("nan"), int=float("nan")) if args.no_pt2 else
+           N.pt2(P, dets, psi64, E64, o=N.opts(validate=0, buckets=o_pt_buckets(args, p))))
     csr.free()
     gm = grad_mixed.double()
     grel = (torch.linalg.norm(gm - g64) / torch.linalg.norm(g64)).item()
@@ -397,6 +409,11 @@ def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, 
             "grad_rel_l2_mixed_vs_fp64": grel,
             "dE_pt2_ext": r64["ext"], "dE_pt2_ext_mixed_minus_fp64": info_mixed["ext"] - r64["ext"],
             "dE_pt2_int_mixed_minus_fp64": info_mixed["int"] - r64["int"]}
+
+
+def o_pt_buckets(args, p):
+    n = len(p.S) * synth_nexc(p.wl)
+    return args.buckets if args.buckets > 0 else max(1, -(-n // (1 << 30)))
 
 
 def synth_nexc(wl):
@@ -428,7 +445,8 @@ def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_
         out_host.copy_(out, non_blocking=True)
         grad_host.copy_(grad, non_blocking=True)
         stream.synchronize()
-        r = N.pt2(P, dets, psi, float(out_host[0]), o=o_pt)
+        r = (dict(n_emitted=0) if args.no_pt2 else
+             N.pt2(P, dets, psi, float(out_host[0]), o=o_pt))
         n = csr.n_enumerated + r["n_emitted"]
         csr.free()
         b.record(stream)
@@ -444,24 +462,32 @@ def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_
 # ------------------------------------------------------------------------------------------
 # CPU oracle (the reported baseline, and the reference arm)
 # ------------------------------------------------------------------------------------------
-def oracle_step(O, p, k, quant):
+def oracle_step(O, p, k, quant, with_pt2=True):
     S = p.S[:k]
     wl = p.wl
     csr = O.hss(wl.norb, p.h, p.eri, S)
     r = O.energy_grad(O.Net(p.net, quant=quant), S, csr)
-    pt = O.pt2(wl.norb, p.h, p.eri, S, r["psi"], r["E"])
-    return csr.n_enumerated + len(S) * O.n_excitations(wl.norb, wl.nalpha, wl.nbeta)
+    n = csr.n_enumerated
+    if with_pt2:
+        O.pt2(wl.norb, p.h, p.eri, S, r["psi"], r["E"])
+        n += len(S) * O.n_excitations(wl.norb, wl.nalpha, wl.nbeta)
+    return n
 
 
-def cpu_baseline(p, k):
+def cpu_sample_size(args, p) -> int:
+    """Dets in the CPU-baseline sample: about 5e7 excitations (10-30 s of oracle work)."""
+    return int(max(64, min(args.cpu_sample, len(p.S), 5e7 // synth_nexc(p.wl))))
+
+
+def cpu_baseline(p, k, with_pt2=True):
     from oracle import oracle as O
     O.lib()
     t = time.perf_counter()
-    n = oracle_step(O, p, k, p.wl.mixed)
+    n = oracle_step(O, p, k, p.wl.mixed, with_pt2)
     dt = time.perf_counter() - t
+    what = "H_SS rows, E_S + gradient" + (", PT2 over their connected space" if with_pt2 else "")
     return {"value": n / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"first {k} of {len(p.S)} dets of S: H_SS rows, E_S + gradient, PT2 over "
-                      f"their connected space ({n} connections, {dt:.1f} s)"}
+            "sample": f"first {k} of {len(p.S)} dets of S: {what} ({n} connections, {dt:.1f} s)"}
 
 
 def run_reference(args, ws, rank):
@@ -590,7 +616,7 @@ def main():
     res, p = run_nqs(args, ws, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(p, min(args.cpu_sample, len(p.S)))
+            res["cpu_baseline"] = cpu_baseline(p, cpu_sample_size(args, p), not args.no_pt2)
         print(json.dumps(res))
     if ws > 1:
         torch.distributed.destroy_process_group()
