@@ -13,7 +13,8 @@
  *   - the ansatz is Eqs. (effective_orbital_matrix), (occupied_submatrix), (backflow_amplitude)
  *     in the spin-blocked form psi = det Phi[occ_a, 0:na] * det Phi[occ_b, na:na+nb];
  *   - the objective and its gradient are Eqs. (variational_energy), (variational_gradient);
- *   - the perturbative correction is Eq. (pt2_correction).
+ *   - the perturbative correction is Eq. (pt2_correction);
+ *   - the heat-bath screened perturbative set is Eq. (hb_screen).
  *
  * Conventions fixed here (the paper is silent on them):
  *   - spin-orbital order alpha 0..norb-1, then beta 0..norb-1; |x> = prod over occupied
@@ -779,6 +780,94 @@ int orc_pt2(int norb, const double* h, const double* eri, const uint64_t* S, int
     free(em);
     free(cnt);
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Heat-bath screened perturbative set, Eq. (hb_screen) of Sec. 3.3:
+ *   P = { x' not in S : max over x in S of |H_x'x psi(x)| >= eps }.
+ * Written as that definition: every excitation x' of every x in S gets its Slater-Condon
+ * element; the pair is kept when |H_x'x| * |psi_x| >= eps (one FP64 product) and x' is not in
+ * S; the kept pairs are sorted by key and each run reduced to its maximum. (The sorted-table
+ * early exit of Sec. 3.3 is an acceleration of the same test and is not used here.)
+ * Writes keys[n][2] (ascending) and mx[n] = max_x |H_x'x| |psi_x| when cap >= n.
+ * Returns n, or a negative status.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    uint64_t a, b;
+    double m;
+} hb_t;
+
+static int hb_cmp(const void* p, const void* q) {
+    const hb_t* x = (const hb_t*)p;
+    const hb_t* y = (const hb_t*)q;
+    if (x->a != y->a) return x->a < y->a ? -1 : 1;
+    if (x->b != y->b) return x->b < y->b ? -1 : 1;
+    return 0;
+}
+
+int64_t orc_hb_select(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
+                      const double* psi, double eps, int64_t cap, uint64_t* keys, double* mx) {
+    if (nS <= 0 || !(eps >= 0.0)) return ORC_ERR_ARG;
+    int na = popc(S[0]), nb = popc(S[1]);
+    int64_t nexc = orc_n_excitations(norb, na, nb);
+    int64_t* cnt = (int64_t*)calloc(nS + 1, sizeof(int64_t));
+    if (!cnt) return ORC_ERR_OOM;
+    /* pass 1 counts the kept pairs of each x, pass 2 writes them at the prefix offsets */
+    hb_t* kept = NULL;
+    for (int pass = 0; pass < 2; ++pass) {
+#pragma omp parallel
+        {
+            uint64_t* buf = (uint64_t*)malloc(sizeof(uint64_t) * 2 * nexc);
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t r = 0; r < nS; ++r) {
+                uint64_t a = S[2 * r], b = S[2 * r + 1];
+                int64_t n = orc_excitations(norb, a, b, buf), c = 0;
+                for (int64_t k = 0; k < n; ++k) {
+                    uint64_t xa = buf[2 * k], xb = buf[2 * k + 1];
+                    double hv = orc_element(norb, h, eri, a, b, xa, xb, NULL);
+                    double m = fabs(hv) * fabs(psi[r]);
+                    if (!(m >= eps) || find_in_S(S, nS, xa, xb) >= 0) continue;
+                    if (pass == 1) {
+                        kept[cnt[r] + c].a = xa;
+                        kept[cnt[r] + c].b = xb;
+                        kept[cnt[r] + c].m = m;
+                    }
+                    ++c;
+                }
+                if (pass == 0) cnt[r + 1] = c;
+            }
+            free(buf);
+        }
+        if (pass == 0) {
+            for (int64_t r = 0; r < nS; ++r) cnt[r + 1] += cnt[r];
+            kept = (hb_t*)malloc(sizeof(hb_t) * (cnt[nS] > 0 ? cnt[nS] : 1));
+            if (!kept) {
+                free(cnt);
+                return ORC_ERR_OOM;
+            }
+        }
+    }
+    int64_t total = cnt[nS];
+    qsort(kept, total, sizeof(hb_t), hb_cmp);
+    int64_t n = 0;
+    for (int64_t k = 0; k < total;) {
+        int64_t e = k;
+        double m = kept[k].m;
+        while (e < total && kept[e].a == kept[k].a && kept[e].b == kept[k].b) {
+            if (kept[e].m > m) m = kept[e].m;
+            ++e;
+        }
+        if (keys && mx && n < cap) {
+            keys[2 * n] = kept[k].a;
+            keys[2 * n + 1] = kept[k].b;
+            mx[n] = m;
+        }
+        ++n;
+        k = e;
+    }
+    free(kept);
+    free(cnt);
+    return n;
 }
 
 int orc_num_threads(void) {

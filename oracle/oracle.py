@@ -47,6 +47,8 @@ def lib():
         L.orc_bucket.argtypes = [u64, u64, u64]
         L.orc_pt2.restype = C.c_int
         L.orc_pt2.argtypes = [C.c_int, dp, dp, dp, i64, dp, C.c_double, i64, i64, dp]
+        L.orc_hb_select.restype = i64
+        L.orc_hb_select.argtypes = [C.c_int, dp, dp, dp, i64, dp, C.c_double, i64, dp, dp]
         L.orc_num_threads.restype = C.c_int
         L.orc_num_threads.argtypes = []
     return _lib
@@ -244,3 +246,22 @@ def pt2(norb, h, eri, S, psi, E, nbuckets: int = 1, bucket_id: int = -1):
                        int(bucket_id), _p(out))
     assert st == 0, st
     return dict(ext=out[0], int=out[1], n_unique=int(out[2]), D=out[3])
+
+
+# ------------------------------------------------------------------------------------------
+# heat-bath screened perturbative set (Eq. hb_screen, Sec. 3.3)
+# ------------------------------------------------------------------------------------------
+def hb_select(norb, h, eri, S, psi, eps):
+    """P = {x' not in S : max_x |H_x'x psi_x| >= eps}: (keys uint64 [n, 2] ascending,
+    max coupling [n])."""
+    h, eri, S, psi = _f64(h), _f64(eri), _u64(S), _f64(psi)
+    L = lib()
+    n = L.orc_hb_select(norb, _p(h), _p(eri), _p(S), S.shape[0], _p(psi), float(eps), 0, None,
+                        None)
+    assert n >= 0, n
+    keys = np.zeros((max(n, 1), 2), np.uint64)
+    mx = np.zeros(max(n, 1))
+    n2 = L.orc_hb_select(norb, _p(h), _p(eri), _p(S), S.shape[0], _p(psi), float(eps), n,
+                         _p(keys), _p(mx))
+    assert n2 == n
+    return keys[:n], mx[:n]
