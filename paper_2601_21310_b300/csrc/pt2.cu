@@ -57,9 +57,40 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_count(ProblemDev P,
     }
 }
 
-// offs == nullptr: every excitation is emitted at det * nexc + e (B = 1)
+// All buckets in one pass: cnt[b * nS + det] = number of excitations of det in bucket b, from a
+// per-warp shared-memory histogram over the B buckets (B <= PT_HIST_MAX).
+#define PT_HIST_MAX 1024
+__global__ void __launch_bounds__(PT_THREADS) k_pt2_count_all(ProblemDev P,
+                                                               const ulonglong2* __restrict__ S,
+                                                               int64_t nS, uint32_t B,
+                                                               int64_t* __restrict__ cnt) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    uint32_t* hist = (uint32_t*)(smem + pair_table_bytes(P) + PT_WARPS * sizeof(DetCtx)) +
+                     (threadIdx.x >> 5) * B;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nexc = (uint32_t)P.nexc;
+    for (int64_t det = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * PT_WARPS) {
+        ulonglong2 x = S[det];
+        for (uint32_t k = lane; k < B; k += 32) hist[k] = 0;
+        fill_ctx(P, x.x, x.y, ctx, lane);  // ends with __syncwarp
+        for (uint32_t e = lane; e < nexc; e += 32) {
+            uint64_t a2, b2;
+            decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+            atomicAdd(&hist[det_hash(a2, b2) % B], 1u);
+        }
+        __syncwarp();
+        for (uint32_t k = lane; k < B; k += 32) cnt[(int64_t)k * nS + det] = hist[k];
+        __syncwarp();
+    }
+}
+
+// offs == nullptr: every excitation is emitted at det * nexc + e (B = 1). With B > 1 only the
+// key is decoded first; the full decode and the element are computed for in-bucket ones.
 template <class K>
-__global__ void __launch_bounds__(PT_THREADS) k_pt2_emit(ProblemDev P,
+__global__ void __launch_bounds__(PT_THREADS, 6) k_pt2_emit(ProblemDev P,
                                                           const ulonglong2* __restrict__ S,
                                                           const double* __restrict__ psi,
                                                           int64_t nS, uint64_t B, uint64_t bucket,
@@ -69,6 +100,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit(ProblemDev P,
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    __shared__ uint32_t queue[PT_WARPS * 64];
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     const uint32_t nexc = (uint32_t)P.nexc;
@@ -79,21 +111,65 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit(ProblemDev P,
         fill_ctx(P, x.x, x.y, ctx, lane);
         const double py = psi[det];
         int64_t run = offs ? offs[det] : det * (int64_t)nexc;
-        for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
-            uint32_t e = r0 + lane;
-            bool take = false;
-            Exc ex;
-            if (e < nexc) {
-                decode_exc(P, T, *ctx, x.x, x.y, e, ex);
-                take = in_bucket(ex.a2, ex.b2, B, bucket);
+        if (B == 1) {
+            for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
+                const uint32_t e = r0 + lane;
+                const bool take = e < nexc;
+                const unsigned m = __ballot_sync(FULL_MASK, take);
+                if (take) {
+                    Exc ex;
+                    decode_exc(P, T, *ctx, x.x, x.y, e, ex);
+                    const int64_t pos = run + __popc(m & lt);
+                    keys[pos] = key_make<K>(ex.a2, ex.b2, norb);
+                    vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
+                }
+                run += __popc(m);
             }
-            unsigned m = __ballot_sync(FULL_MASK, take);
-            if (take) {
-                int64_t pos = run + __popc(m & lt);
-                keys[pos] = key_make<K>(ex.a2, ex.b2, norb);
-                vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
+        } else {
+            // Only the key is decoded for every excitation. In-bucket indices are appended, in
+            // canonical order, to a per-warp queue; each time it holds 32 the whole warp decodes
+            // and evaluates them together, so the expensive part runs without divergence.
+            uint32_t* q = queue + (threadIdx.x >> 5) * 64;
+            uint32_t qn = 0;
+            for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
+                const uint32_t e = r0 + lane;
+                bool take = false;
+                if (e < nexc) {
+                    uint64_t a2, b2;
+                    decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+                    take = in_bucket(a2, b2, B, bucket);
+                }
+                const unsigned m = __ballot_sync(FULL_MASK, take);
+                if (take) q[qn + __popc(m & lt)] = e;
+                qn += __popc(m);
+                __syncwarp();
+                if (qn >= 32 || (r0 + 32 >= nexc && qn > 0)) {
+                    const uint32_t nt = qn < 32 ? qn : 32;
+                    if ((uint32_t)lane < nt) {
+                        Exc ex;
+                        decode_exc(P, T, *ctx, x.x, x.y, q[lane], ex);
+                        keys[run + lane] = key_make<K>(ex.a2, ex.b2, norb);
+                        vals[run + lane] = __dmul_rn(exc_element(P, *ctx, ex), py);
+                    }
+                    run += nt;
+                    const uint32_t rest = qn - nt;  // < 32
+                    const uint32_t moved = (uint32_t)lane < rest ? q[32 + lane] : 0u;
+                    __syncwarp();
+                    if ((uint32_t)lane < rest) q[lane] = moved;
+                    qn = rest;
+                    __syncwarp();
+                }
             }
-            run += __popc(m);
+            // a last partial batch can remain only if the final flush took exactly 32
+            if (qn > 0) {
+                if ((uint32_t)lane < qn) {
+                    Exc ex;
+                    decode_exc(P, T, *ctx, x.x, x.y, q[lane], ex);
+                    keys[run + lane] = key_make<K>(ex.a2, ex.b2, norb);
+                    vals[run + lane] = __dmul_rn(exc_element(P, *ctx, ex), py);
+                }
+                __syncwarp();
+            }
         }
         __syncwarp();
     }
@@ -410,10 +486,26 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     int64_t* cnt = nullptr;
     int64_t* offs = nullptr;
     int64_t* total_dev = nullptr;
+    // one counting pass for every bucket when the B x nS count table stays below 2 GiB
+    const bool count_all =
+        B > 1 && B <= PT_HIST_MAX && (double)nS * (double)B * sizeof(int64_t) <= 2147483648.0;
     if (B > 1) {
-        NQS_TRY(sc.get(&cnt, nS));
+        NQS_TRY(sc.get(&cnt, count_all ? (size_t)nS * B : (size_t)nS));
         NQS_TRY(sc.get(&offs, nS));
         NQS_TRY(sc.get(&total_dev, 1));
+    }
+    if (count_all) {
+        const size_t smem_all = smem + (size_t)PT_WARPS * B * sizeof(uint32_t);
+        if (smem_all > 48 * 1024)
+            NQS_CK(cudaFuncSetAttribute(k_pt2_count_all,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_all));
+        {
+            ProfScope prof_(PROF_PT2_COUNT, s);
+            k_pt2_count_all<<<pt_grid(nS), PT_THREADS, smem_all, s>>>(
+                P, (const ulonglong2*)dets, nS, (uint32_t)B, cnt);
+        }
+        NQS_CK_LAUNCH();
     }
     const int64_t cap = opts->chunk > 0 ? opts->chunk : ((int64_t)1 << 32) - 1;
     const int kbits = 2 * P.norb;  // 32-bit, 64-bit or two-word keys
@@ -424,13 +516,16 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
             n = nS * P.nexc;
         } else {
             Scratch cs(p, s);
-            {
-                ProfScope prof_(PROF_PT2_COUNT, s);
-                k_pt2_count<<<pt_grid(nS), PT_THREADS, smem, s>>>(P, (const ulonglong2*)dets, nS,
-                                                                  (uint64_t)B, (uint64_t)b, cnt);
+            if (!count_all) {
+                {
+                    ProfScope prof_(PROF_PT2_COUNT, s);
+                    k_pt2_count<<<pt_grid(nS), PT_THREADS, smem, s>>>(
+                        P, (const ulonglong2*)dets, nS, (uint64_t)B, (uint64_t)b, cnt);
+                }
+                NQS_CK_LAUNCH();
             }
-            NQS_CK_LAUNCH();
-            NQS_TRY(scan_exclusive_i64(p, cs, cnt, offs, nS, total_dev, s));
+            NQS_TRY(scan_exclusive_i64(p, cs, count_all ? cnt + (size_t)b * nS : cnt, offs, nS,
+                                       total_dev, s));
             NQS_CK(cudaMemcpyAsync(&n, total_dev, sizeof n, cudaMemcpyDeviceToHost, s));
             NQS_CK(cudaStreamSynchronize(s));
         }
