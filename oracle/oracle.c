@@ -14,7 +14,9 @@
  *     in the spin-blocked form psi = det Phi[occ_a, 0:na] * det Phi[occ_b, na:na+nb];
  *   - the objective and its gradient are Eqs. (variational_energy), (variational_gradient);
  *   - the perturbative correction is Eq. (pt2_correction);
- *   - the heat-bath screened perturbative set is Eq. (hb_screen).
+ *   - the heat-bath screened perturbative set is Eq. (hb_screen);
+ *   - the subspace selector of the outer loop is Sec. 2.4.2 (Top-K, cumulative mass,
+ *     absolute threshold).
  *
  * Conventions fixed here (the paper is silent on them):
  *   - spin-orbital order alpha 0..norb-1, then beta 0..norb-1; |x> = prod over occupied
@@ -805,9 +807,20 @@ static int hb_cmp(const void* p, const void* q) {
     return 0;
 }
 
+int64_t orc_hb_select_rows(int norb, const double* h, const double* eri, const uint64_t* S,
+                           int64_t nS, int64_t r0, int64_t r1, const double* psi, double eps,
+                           int64_t cap, uint64_t* keys, double* mx);
 int64_t orc_hb_select(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
                       const double* psi, double eps, int64_t cap, uint64_t* keys, double* mx) {
-    if (nS <= 0 || !(eps >= 0.0)) return ORC_ERR_ARG;
+    return orc_hb_select_rows(norb, h, eri, S, nS, 0, nS, psi, eps, cap, keys, mx);
+}
+
+/* The same with the maximum taken over the parents x = S[r0..r1-1] only (membership is still
+ * tested against all of S): a subset of P whose couplings are lower bounds of P's. */
+int64_t orc_hb_select_rows(int norb, const double* h, const double* eri, const uint64_t* S,
+                           int64_t nS, int64_t r0, int64_t r1, const double* psi, double eps,
+                           int64_t cap, uint64_t* keys, double* mx) {
+    if (nS <= 0 || !(eps >= 0.0) || r0 < 0 || r1 > nS || r0 > r1) return ORC_ERR_ARG;
     int na = popc(S[0]), nb = popc(S[1]);
     int64_t nexc = orc_n_excitations(norb, na, nb);
     int64_t* cnt = (int64_t*)calloc(nS + 1, sizeof(int64_t));
@@ -819,7 +832,7 @@ int64_t orc_hb_select(int norb, const double* h, const double* eri, const uint64
         {
             uint64_t* buf = (uint64_t*)malloc(sizeof(uint64_t) * 2 * nexc);
 #pragma omp for schedule(dynamic, 16)
-            for (int64_t r = 0; r < nS; ++r) {
+            for (int64_t r = r0; r < r1; ++r) {
                 uint64_t a = S[2 * r], b = S[2 * r + 1];
                 int64_t n = orc_excitations(norb, a, b, buf), c = 0;
                 for (int64_t k = 0; k < n; ++k) {
@@ -839,7 +852,7 @@ int64_t orc_hb_select(int norb, const double* h, const double* eri, const uint64
             free(buf);
         }
         if (pass == 0) {
-            for (int64_t r = 0; r < nS; ++r) cnt[r + 1] += cnt[r];
+            for (int64_t r = 0; r < nS; ++r) cnt[r + 1] += cnt[r];  /* rows outside stay 0 */
             kept = (hb_t*)malloc(sizeof(hb_t) * (cnt[nS] > 0 ? cnt[nS] : 1));
             if (!kept) {
                 free(cnt);
@@ -868,6 +881,78 @@ int64_t orc_hb_select(int norb, const double* h, const double* eri, const uint64
     free(kept);
     free(cnt);
     return n;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Subspace selection of the outer loop (Sec. 2.4.2; Algorithm 1 step 3, Selector(T, K,
+ * key = |psi|)): the configurations of T ranked by |psi| descending, ties by ascending key,
+ * and a prefix of that ranking kept:
+ *   mode 0  Top-K:            the first min(K, n);
+ *   mode 1  cumulative mass:  the shortest prefix whose sum of psi^2 (added in rank order)
+ *                             reaches gamma * D, D = sum over T of psi^2 (compensated, T order);
+ *                             all of T if rounding keeps the sum below;
+ *   mode 2  absolute threshold: every x with psi_x^2 / D > eps (a prefix of the ranking).
+ * Writes the positions in T of the kept configurations, ascending by key, and returns their
+ * number (or a negative status).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    uint64_t a, b;
+    double m;
+    int64_t pos;
+} rank_t;
+
+static int rank_cmp(const void* p, const void* q) {
+    const rank_t* x = (const rank_t*)p;
+    const rank_t* y = (const rank_t*)q;
+    if (x->m != y->m) return x->m > y->m ? -1 : 1;
+    if (x->a != y->a) return x->a < y->a ? -1 : 1;
+    if (x->b != y->b) return x->b < y->b ? -1 : 1;
+    return 0;
+}
+
+static int key_cmp(const void* p, const void* q) {
+    const rank_t* x = (const rank_t*)p;
+    const rank_t* y = (const rank_t*)q;
+    if (x->a != y->a) return x->a < y->a ? -1 : 1;
+    if (x->b != y->b) return x->b < y->b ? -1 : 1;
+    return 0;
+}
+
+int64_t orc_select(const uint64_t* T, const double* psi, int64_t n, int mode, int64_t K,
+                   double param, int64_t* out_pos) {
+    if (n <= 0 || mode < 0 || mode > 2) return ORC_ERR_ARG;
+    rank_t* r = (rank_t*)malloc(sizeof(rank_t) * n);
+    if (!r) return ORC_ERR_OOM;
+    ksum Dk = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        r[i].a = T[2 * i];
+        r[i].b = T[2 * i + 1];
+        r[i].m = fabs(psi[i]);
+        r[i].pos = i;
+        kadd(&Dk, psi[i] * psi[i]);
+    }
+    double D = kval(&Dk);
+    qsort(r, n, sizeof(rank_t), rank_cmp);
+    int64_t c = 0;
+    if (mode == 0) {
+        c = K < n ? (K > 0 ? K : 0) : n;
+    } else if (mode == 1) {
+        double target = param * D, acc = 0.0;
+        c = n;
+        for (int64_t i = 0; i < n; ++i) {
+            acc = acc + r[i].m * r[i].m;
+            if (acc >= target) {
+                c = i + 1;
+                break;
+            }
+        }
+    } else {
+        while (c < n && (r[c].m * r[c].m) / D > param) ++c;
+    }
+    qsort(r, c, sizeof(rank_t), key_cmp);
+    for (int64_t i = 0; i < c; ++i) out_pos[i] = r[i].pos;
+    free(r);
+    return c;
 }
 
 int orc_num_threads(void) {

@@ -49,6 +49,11 @@ def lib():
         L.orc_pt2.argtypes = [C.c_int, dp, dp, dp, i64, dp, C.c_double, i64, i64, dp]
         L.orc_hb_select.restype = i64
         L.orc_hb_select.argtypes = [C.c_int, dp, dp, dp, i64, dp, C.c_double, i64, dp, dp]
+        L.orc_hb_select_rows.restype = i64
+        L.orc_hb_select_rows.argtypes = [C.c_int, dp, dp, dp, i64, i64, i64, dp, C.c_double, i64,
+                                         dp, dp]
+        L.orc_select.restype = i64
+        L.orc_select.argtypes = [dp, dp, i64, C.c_int, i64, C.c_double, dp]
         L.orc_num_threads.restype = C.c_int
         L.orc_num_threads.argtypes = []
     return _lib
@@ -251,17 +256,33 @@ def pt2(norb, h, eri, S, psi, E, nbuckets: int = 1, bucket_id: int = -1):
 # ------------------------------------------------------------------------------------------
 # heat-bath screened perturbative set (Eq. hb_screen, Sec. 3.3)
 # ------------------------------------------------------------------------------------------
-def hb_select(norb, h, eri, S, psi, eps):
+def hb_select(norb, h, eri, S, psi, eps, rows=None):
     """P = {x' not in S : max_x |H_x'x psi_x| >= eps}: (keys uint64 [n, 2] ascending,
-    max coupling [n])."""
+    max coupling [n]). rows=(r0, r1) takes the maximum over the parents S[r0:r1] only."""
     h, eri, S, psi = _f64(h), _f64(eri), _u64(S), _f64(psi)
+    nS = S.shape[0]
+    r0, r1 = rows if rows is not None else (0, nS)
     L = lib()
-    n = L.orc_hb_select(norb, _p(h), _p(eri), _p(S), S.shape[0], _p(psi), float(eps), 0, None,
-                        None)
+    args = (norb, _p(h), _p(eri), _p(S), nS, r0, r1, _p(psi), float(eps))
+    n = L.orc_hb_select_rows(*args, 0, None, None)
     assert n >= 0, n
     keys = np.zeros((max(n, 1), 2), np.uint64)
     mx = np.zeros(max(n, 1))
-    n2 = L.orc_hb_select(norb, _p(h), _p(eri), _p(S), S.shape[0], _p(psi), float(eps), n,
-                         _p(keys), _p(mx))
+    n2 = L.orc_hb_select_rows(*args, n, _p(keys), _p(mx))
     assert n2 == n
     return keys[:n], mx[:n]
+
+
+# ------------------------------------------------------------------------------------------
+# subspace selection of the outer loop (Sec. 2.4.2, Algorithm 1 step 3)
+# ------------------------------------------------------------------------------------------
+SELECT_TOPK, SELECT_MASS, SELECT_THRESHOLD = 0, 1, 2
+
+
+def select(T, psi, mode, K=0, param=0.0):
+    """Positions in T of the kept configurations, ascending by key."""
+    T, psi = _u64(T), _f64(psi)
+    out = np.zeros(max(T.shape[0], 1), np.int64)
+    c = lib().orc_select(_p(T), _p(psi), T.shape[0], int(mode), int(K), float(param), _p(out))
+    assert c >= 0, c
+    return out[:c]

@@ -166,3 +166,19 @@ def test_hb_select_limits_and_nesting(olib):
         if prev is not None:
             assert set(cur) <= set(prev)
         prev = cur
+
+
+def test_hb_select_row_blocks_combine_to_the_whole(olib):
+    """Parents split into row blocks: the union of the blocks' sets, with the maximum of their
+    couplings, is the set of all parents (what the sampled full-size GPU checks rely on)."""
+    norb, na, nb = 6, 3, 3
+    h, eri, dets, H, pick, psi = _case(norb, na, nb, 60, 11)
+    S = dets[pick]
+    eps = 3e-3
+    whole = _as_dict(*O.hb_select(norb, h, eri, S, psi, eps))
+    merged = {}
+    for r0, r1 in [(0, 7), (7, 30), (30, 31), (31, 60)]:
+        for k, v in _as_dict(*O.hb_select(norb, h, eri, S, psi, eps, rows=(r0, r1))).items():
+            merged[k] = max(merged.get(k, 0.0), v)
+    assert merged == whole
+    assert len(O.hb_select(norb, h, eri, S, psi, eps, rows=(5, 5))[0]) == 0
