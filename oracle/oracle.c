@@ -885,13 +885,14 @@ int64_t orc_hb_select_rows(int norb, const double* h, const double* eri, const u
 
 /* ------------------------------------------------------------------------------------------
  * Subspace selection of the outer loop (Sec. 2.4.2; Algorithm 1 step 3, Selector(T, K,
- * key = |psi|)): the configurations of T ranked by |psi| descending, ties by ascending key,
- * and a prefix of that ranking kept:
- *   mode 0  Top-K:            the first min(K, n);
- *   mode 1  cumulative mass:  the shortest prefix whose sum of psi^2 (added in rank order)
- *                             reaches gamma * D, D = sum over T of psi^2 (compensated, T order);
- *                             all of T if rounding keeps the sum below;
- *   mode 2  absolute threshold: every x with psi_x^2 / D > eps (a prefix of the ranking).
+ * key = |psi|)). Input: the amplitudes on T as log|psi| (-inf for psi = 0). The configurations
+ * are ranked by log|psi| descending, ties by ascending key, and a prefix of the ranking is kept.
+ * With w_x = exp(2 (log|psi_x| - max log|psi|)) (psi^2 up to one common factor) and
+ * D = sum over T of w (compensated, in T order):
+ *   mode 0  Top-K:              the first min(K, n);
+ *   mode 1  cumulative mass:    the shortest prefix whose sum of w (added in rank order)
+ *                               reaches gamma * D; all of T if rounding keeps it below;
+ *   mode 2  absolute threshold: every x with p(x) = w_x / D > eps (a prefix of the ranking).
  * Writes the positions in T of the kept configurations, ascending by key, and returns their
  * number (or a negative status).
  * ---------------------------------------------------------------------------------------- */
@@ -918,19 +919,21 @@ static int key_cmp(const void* p, const void* q) {
     return 0;
 }
 
-int64_t orc_select(const uint64_t* T, const double* psi, int64_t n, int mode, int64_t K,
+int64_t orc_select(const uint64_t* T, const double* logabs, int64_t n, int mode, int64_t K,
                    double param, int64_t* out_pos) {
     if (n <= 0 || mode < 0 || mode > 2) return ORC_ERR_ARG;
     rank_t* r = (rank_t*)malloc(sizeof(rank_t) * n);
     if (!r) return ORC_ERR_OOM;
-    ksum Dk = {0, 0};
+    double lmax = -INFINITY;
     for (int64_t i = 0; i < n; ++i) {
         r[i].a = T[2 * i];
         r[i].b = T[2 * i + 1];
-        r[i].m = fabs(psi[i]);
+        r[i].m = logabs[i];
         r[i].pos = i;
-        kadd(&Dk, psi[i] * psi[i]);
+        if (logabs[i] > lmax) lmax = logabs[i];
     }
+    ksum Dk = {0, 0};
+    for (int64_t i = 0; i < n; ++i) kadd(&Dk, exp(2.0 * (logabs[i] - lmax)));
     double D = kval(&Dk);
     qsort(r, n, sizeof(rank_t), rank_cmp);
     int64_t c = 0;
@@ -940,14 +943,14 @@ int64_t orc_select(const uint64_t* T, const double* psi, int64_t n, int mode, in
         double target = param * D, acc = 0.0;
         c = n;
         for (int64_t i = 0; i < n; ++i) {
-            acc = acc + r[i].m * r[i].m;
+            acc = acc + exp(2.0 * (r[i].m - lmax));
             if (acc >= target) {
                 c = i + 1;
                 break;
             }
         }
     } else {
-        while (c < n && (r[c].m * r[c].m) / D > param) ++c;
+        while (c < n && exp(2.0 * (r[c].m - lmax)) / D > param) ++c;
     }
     qsort(r, c, sizeof(rank_t), key_cmp);
     for (int64_t i = 0; i < c; ++i) out_pos[i] = r[i].pos;

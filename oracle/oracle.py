@@ -279,10 +279,10 @@ def hb_select(norb, h, eri, S, psi, eps, rows=None):
 SELECT_TOPK, SELECT_MASS, SELECT_THRESHOLD = 0, 1, 2
 
 
-def select(T, psi, mode, K=0, param=0.0):
-    """Positions in T of the kept configurations, ascending by key."""
-    T, psi = _u64(T), _f64(psi)
+def select(T, logabs, mode, K=0, param=0.0):
+    """Positions in T of the kept configurations, ascending by key (amplitudes as log|psi|)."""
+    T, logabs = _u64(T), _f64(logabs)
     out = np.zeros(max(T.shape[0], 1), np.int64)
-    c = lib().orc_select(_p(T), _p(psi), T.shape[0], int(mode), int(K), float(param), _p(out))
+    c = lib().orc_select(_p(T), _p(logabs), T.shape[0], int(mode), int(K), float(param), _p(out))
     assert c >= 0, c
     return out[:c]
