@@ -219,6 +219,57 @@ int nqs_connections_noalloc(nqs_problem* problem, const uint64_t* dets, int64_t 
                             int64_t* row_ptr, int32_t* col, double* val, int64_t capacity,
                             int64_t* nnz, int64_t* n_enumerated, nqs_stream_t stream);
 
+/* Library-owned set of configurations (device memory), ascending by (a, b). Free with
+ * nqs_detset_free. */
+typedef struct {
+    uint64_t* dets;     /* device [n][2] */
+    double* value;      /* device [n]: nqs_hb_select: max over x in S of |H_x'x| |psi_x|;
+                           nqs_select: log|psi| of the kept configuration */
+    int64_t* index;     /* device [n]: nqs_select: position in T; NULL for nqs_hb_select */
+    int64_t n;
+    int64_t n_emitted;  /* nqs_hb_select: (x, x') pairs that passed, before removing duplicates */
+    int64_t n_examined; /* nqs_hb_select: candidates whose coupling was tested */
+} nqs_detset;
+
+/* Heat-bath screened perturbative set, Eq. (hb_screen) of Sec. 3.3 (Algorithm 1 step 1):
+ * P = { x' not in S : max over x in S of |H_x'x psi_x| >= eps_hb }, with the product taken in
+ * FP64. dets: device [nS][2], sorted and unique (checked with opts->validate); psi: device [nS]
+ * FP64, the amplitudes the cutoff refers to (the caller chooses their normalisation, e.g.
+ * psi / ||psi||). eps_hb >= 0 (0 keeps the whole connected set outside S). Doubles are found by
+ * the sorted-integral walk with early exit of Sec. 3.3 (exact: nothing the definition keeps is
+ * skipped); singles are all evaluated. The sorted integral tables are built on the first call
+ * for a problem and kept until nqs_problem_destroy: 10 bytes per entry, C(norb,2) C(norb-2,2) +
+ * norb^2 (norb-1)^2 entries (37 MB at norb 42, 200 MB at 64). On success *out holds a
+ * library-owned set; on failure it is empty. Synchronises the stream. Errors: NQS_ERR_ARG
+ * (null pointer, nS <= 0, eps_hb < 0 or NaN, misaligned dets), NQS_ERR_UNSORTED /
+ * NQS_ERR_POPCOUNT (with validate), NQS_ERR_UNSUPPORTED (2^32 or more kept pairs), NQS_ERR_OOM,
+ * NQS_ERR_CUDA. */
+int nqs_hb_select(nqs_problem* problem, const uint64_t* dets, const double* psi, int64_t nS,
+                  double eps_hb, const nqs_opts* opts, nqs_detset* out, nqs_stream_t stream);
+int nqs_detset_free(nqs_detset* set);
+
+/* Subspace selection of the outer loop, Sec. 2.4.2 (Algorithm 1 step 3: V <- Selector(T, K,
+ * key = |psi|)). T: device [n][2] configurations (any order, no repeats: checked with
+ * opts->validate); logabs: device [n] log|psi| (as nqs_amplitudes returns it; -inf for psi = 0;
+ * NaN or +inf is an error). Ranking: log|psi| descending, ties by ascending (a, b). With
+ * w = exp(2 (log|psi| - max log|psi|)) and D = sum of w over T, the kept prefix is
+ *   NQS_SELECT_TOPK       the first min(K, n) (param unused);
+ *   NQS_SELECT_MASS       the shortest prefix whose sum of w reaches param * D
+ *                         (0 <= param <= 1; all of T if rounding keeps it below);
+ *   NQS_SELECT_THRESHOLD  every x with w_x / D > param (param >= 0; K unused).
+ * *out receives the kept configurations ascending by key (the next S), their log|psi| and their
+ * positions in T. Sums are FP64 in a fixed device order: at the boundary of the mass and
+ * threshold protocols the count can differ from a serial sum by the configurations whose
+ * running mass or weight lies within rounding of the cutoff. Synchronises the stream. Errors:
+ * NQS_ERR_ARG, NQS_ERR_UNSORTED (repeated configuration, with validate), NQS_ERR_OOM,
+ * NQS_ERR_CUDA. */
+#define NQS_SELECT_TOPK 0
+#define NQS_SELECT_MASS 1
+#define NQS_SELECT_THRESHOLD 2
+int nqs_select(nqs_problem* problem, const uint64_t* T, const double* logabs, int64_t n, int mode,
+               int64_t K, double param, const nqs_opts* opts, nqs_detset* out,
+               nqs_stream_t stream);
+
 /* Plain library GEMM on the tensor cores used by the backflow network (not a step of the
  * paper's method; exposed for testing and reuse): C[m][n] = sum_k A[m][k] B[n][k] with A
  * [M][lda] and B [N][ldb] bfloat16, k contiguous (lda, ldb multiples of 8, 16-byte aligned
@@ -233,7 +284,7 @@ int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M,
  * nqs_profile_read synchronises those events and returns the summed milliseconds and the
  * launch count of one kernel family: "conn_count", "conn_fill", "pt2_count", "pt2_emit",
  * "rs_hist", "rs_scatter", "seg_reduce", "gemm", "lu", "spmv", "layer1", "unique_terms",
- * "heads", "scan". Process-wide state;
+ * "heads", "scan", "hb_select", "select". Process-wide state;
  * not thread safe. */
 int nqs_profile_enable(int on);
 int nqs_profile_reset(void);

@@ -1,0 +1,471 @@
+// Heat-bath screened perturbative set, Eq. (hb_screen) of Sec. 3.3:
+//   P = { x' not in S : max over x in S of |H_x'x psi(x)| >= eps }.
+//
+// Sec. 3.3 accelerates the test with integral tables: for every pair of occupied orbitals the
+// particle pairs are sorted by descending |<ij||ab>|, and the walk over them stops at the first
+// entry below the cutoff. Doubles are exactly those entries (|H_x'x| = |<ij||ab>|), so with the
+// cutoff tested as the product |<ij||ab>| * |psi_x| >= eps (FP64, monotone in the table value)
+// the early exit drops nothing that the definition keeps. Singles have an element that depends
+// on x; they are few (n (norb - n) per spin) and are all evaluated exactly.
+//
+// Tables (built once per problem, on first use):
+//   same spin     one list per orbital pair i<j: particle pairs a<b with {a,b} and {i,j}
+//                 disjoint, value |(ia|jb) - (ib|ja)|, length C(norb-2, 2);
+//   opposite spin one list per (i alpha, j beta): (a alpha, b beta) with a != i, b != j,
+//                 value |(ia|jb)|, length (norb-1)^2.
+// Each list is sorted descending in shared memory by one CTA (bitonic network).
+//
+// Selection: one warp per x of S. A count pass and an emit pass run the same traversal
+// (singles, same-spin pairs, opposite-spin pairs; lists whose head fails the cutoff are skipped
+// from a ballot over 32 hole pairs). Kept configurations are probed in the hash table of S and
+// dropped when present. The emitted (key, |H psi|) pairs are radix-sorted by key; each run
+// becomes one output configuration with the maximum of its couplings.
+#include <math.h>
+
+#include "excite.cuh"
+#include "nqs_internal.cuh"
+#include "prof.cuh"
+
+#define HB_THREADS 256
+#define HB_WARPS (HB_THREADS / 32)
+#define HB_SORT_THREADS 512
+
+struct HbTab {
+    const double* val;    // [lists][len] descending
+    const uint16_t* code; // a | b << 8
+    int Lss, Los;         // list lengths
+    int64_t os_base;      // index of the first opposite-spin entry
+};
+
+// index of the orbital pair i < j among all C(norb, 2) pairs, lexicographic
+__device__ __forceinline__ int pair_index(int i, int j, int n) {
+    return i * (2 * n - i - 1) / 2 + (j - i - 1);
+}
+
+// x comes before y in a descending list (ties by ascending code)
+__device__ __forceinline__ bool hb_before(double vx, uint16_t cx, double vy, uint16_t cy) {
+    return vx > vy || (vx == vy && cx < cy);
+}
+
+// One CTA per list. Slots cover every candidate particle pair; those that share an orbital with
+// the hole pair get the value -1 and sort behind every real entry (all >= 0).
+__global__ void __launch_bounds__(HB_SORT_THREADS) k_hb_tables(int n, const double* __restrict__ eri,
+                                                               int n_ss_lists, int Lss, int Los,
+                                                               int Np, double* __restrict__ val,
+                                                               uint16_t* __restrict__ code) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    double* sv = (double*)smem;
+    uint16_t* sc = (uint16_t*)(sv + Np);
+    const int list = blockIdx.x;
+    const bool same = list < n_ss_lists;
+    int i, j, nslots;
+    if (same) {
+        int lo = 0, rem = list;
+        while (rem >= n - 1 - lo) {
+            rem -= n - 1 - lo;
+            ++lo;
+        }
+        i = lo;
+        j = lo + 1 + rem;
+        nslots = n * (n - 1) / 2;
+    } else {
+        const int q = list - n_ss_lists;
+        i = q / n;
+        j = q - i * n;
+        nslots = n * n;
+    }
+    for (int t = threadIdx.x; t < Np; t += blockDim.x) {
+        double v = -1.0;
+        int a = 0, b = 0;
+        if (t < nslots) {
+            if (same) {
+                int lo = 0, rem = t;
+                while (rem >= n - 1 - lo) {
+                    rem -= n - 1 - lo;
+                    ++lo;
+                }
+                a = lo;
+                b = lo + 1 + rem;
+                if (a != i && a != j && b != i && b != j) {
+                    const double t1 = eri[(((size_t)i * n + a) * n + j) * n + b];
+                    const double t2 = eri[(((size_t)i * n + b) * n + j) * n + a];
+                    v = fabs(t1 - t2);
+                }
+            } else {
+                a = t / n;
+                b = t - a * n;
+                if (a != i && b != j) v = fabs(eri[(((size_t)i * n + a) * n + j) * n + b]);
+            }
+        }
+        sv[t] = v;
+        sc[t] = (uint16_t)(a | (b << 8));
+    }
+    __syncthreads();
+    for (int k = 2; k <= Np; k <<= 1) {
+        for (int s = k >> 1; s > 0; s >>= 1) {
+            for (int t = threadIdx.x; t < Np; t += blockDim.x) {
+                const int u = t ^ s;
+                if (u > t) {
+                    const bool first_half = (t & k) == 0;
+                    const bool out_of_order = first_half ? hb_before(sv[u], sc[u], sv[t], sc[t])
+                                                         : hb_before(sv[t], sc[t], sv[u], sc[u]);
+                    if (out_of_order) {
+                        const double tv = sv[t];
+                        sv[t] = sv[u];
+                        sv[u] = tv;
+                        const uint16_t tc = sc[t];
+                        sc[t] = sc[u];
+                        sc[u] = tc;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int L = same ? Lss : Los;
+    const int64_t base = same ? (int64_t)list * Lss
+                              : (int64_t)n_ss_lists * Lss + (int64_t)(list - n_ss_lists) * Los;
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        val[base + t] = sv[t];
+        code[base + t] = sc[t];
+    }
+}
+
+static int hb_tables(nqs_problem* p, HbTab* out) {
+    const int n = p->d.norb;
+    const int n_ss = n * (n - 1) / 2, n_os = n * n;
+    const int Lss = (n - 2) * (n - 3) / 2 > 0 ? (n - 2) * (n - 3) / 2 : 0;
+    const int Los = (n - 1) * (n - 1);
+    if (!p->hb_val) {
+        const int64_t total = (int64_t)n_ss * Lss + (int64_t)n_os * Los;
+        int Np = 1;
+        while (Np < n * n) Np <<= 1;
+        const size_t smem = (size_t)Np * (sizeof(double) + sizeof(uint16_t));
+        if (smem > 48 * 1024)
+            NQS_CK(cudaFuncSetAttribute(k_hb_tables, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+        double* val = nullptr;
+        uint16_t* code = nullptr;
+        if (cudaMalloc(&val, (total > 0 ? total : 1) * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&code, (total > 0 ? total : 1) * sizeof(uint16_t)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(val);
+            return NQS_ERR_OOM;
+        }
+        k_hb_tables<<<n_ss + n_os, HB_SORT_THREADS, smem>>>(n, p->d.eri, n_ss, Lss, Los, Np, val,
+                                                             code);
+        nqs_note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            cudaFree(val);
+            cudaFree(code);
+            nqs_record_error("k_hb_tables", e, __FILE__, __LINE__);
+            return NQS_ERR_CUDA;
+        }
+        p->hb_val = val;
+        p->hb_code = code;
+    }
+    out->val = p->hb_val;
+    out->code = p->hb_code;
+    out->Lss = Lss;
+    out->Los = Los;
+    out->os_base = (int64_t)n_ss * Lss;
+    return NQS_OK;
+}
+
+// The screened traversal of one x per warp. EMIT = false: cnt[det] = number of kept pairs.
+// EMIT = true: the pairs are written from offs[det] on. examined (may be null) accumulates the
+// number of candidates whose coupling was tested.
+template <bool EMIT, class K>
+__global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS H, HbTab T,
+                                                          const ulonglong2* __restrict__ S,
+                                                          const double* __restrict__ psi,
+                                                          int64_t nS, double eps,
+                                                          int64_t* __restrict__ cnt,
+                                                          const int64_t* __restrict__ offs,
+                                                          K* __restrict__ keys,
+                                                          double* __restrict__ vals,
+                                                          unsigned long long* examined) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables PT = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const int n = P.norb;
+    const uint32_t nsing = (uint32_t)(P.sA + P.sB);
+    for (int64_t det = (int64_t)blockIdx.x * HB_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * HB_WARPS) {
+        const ulonglong2 x = S[det];
+        const double ap = fabs(psi[det]);
+        int64_t run = EMIT ? offs[det] : 0;
+        unsigned long long tested = 0;
+        // m = |H| |psi| >= eps fails for every coupling when |psi| = 0 < eps, and when psi is
+        // not a number: nothing to do for this x
+        if (!(ap >= 0.0) || (ap == 0.0 && eps > 0.0)) {
+            if (!EMIT && lane == 0) cnt[det] = 0;
+            continue;
+        }
+        fill_ctx(P, x.x, x.y, ctx, lane);
+        auto keep = [&](bool take, uint64_t a2, uint64_t b2, double m) {
+            const unsigned bal = __ballot_sync(FULL_MASK, take);
+            if (EMIT && take) {
+                const int64_t pos = run + __popc(bal & lt);
+                keys[pos] = key_make<K>(a2, b2, n);
+                vals[pos] = m;
+            }
+            run += __popc(bal);
+        };
+        // singles: every one, with its exact element
+        for (uint32_t r0 = 0; r0 < nsing; r0 += 32) {
+            const uint32_t e = r0 + lane;
+            bool take = false;
+            Exc ex;
+            ex.a2 = ex.b2 = 0;
+            double m = 0.0;
+            if (e < nsing) {
+                decode_exc(P, PT, *ctx, x.x, x.y, e, ex);
+                m = __dmul_rn(fabs(exc_element(P, *ctx, ex)), ap);
+                take = m >= eps && hash_lookup(H, ex.a2, ex.b2) < 0;
+            }
+            keep(take, ex.a2, ex.b2, m);
+        }
+        tested += nsing;
+        // doubles: three groups of hole pairs; each lane tests the head of one list
+        for (int grp = 0; grp < 3; ++grp) {
+            const int npairs = grp == 0 ? (int)choose2(P.na)
+                             : grp == 1 ? (int)choose2(P.nb) : P.na * P.nb;
+            const int L = grp < 2 ? T.Lss : T.Los;
+            if (L == 0) continue;
+            const uint64_t wA = x.x, wB = x.y;
+            for (int p0 = 0; p0 < npairs; p0 += 32) {
+                const int pi = p0 + lane;
+                int i = 0, j = 0;
+                int64_t base = 0;
+                bool head = false;
+                if (pi < npairs) {
+                    if (grp < 2) {
+                        const uint16_t pr = grp == 0 ? PT.occA[pi] : PT.occB[pi];
+                        const uint8_t* occ = grp == 0 ? ctx->occA : ctx->occB;
+                        i = occ[pr & 0xff];
+                        j = occ[pr >> 8];
+                        base = (int64_t)pair_index(i, j, n) * L;
+                    } else {
+                        const int xa = pi / P.nb, xb = pi - xa * P.nb;
+                        i = ctx->occA[xa];
+                        j = ctx->occB[xb];
+                        base = T.os_base + (int64_t)(i * n + j) * L;
+                    }
+                    head = __dmul_rn(__ldg(&T.val[base]), ap) >= eps;
+                }
+                unsigned hm = __ballot_sync(FULL_MASK, head);
+                while (hm) {
+                    const int src = __ffs(hm) - 1;
+                    hm &= hm - 1;
+                    const int hi = __shfl_sync(FULL_MASK, i, src);
+                    const int hj = __shfl_sync(FULL_MASK, j, src);
+                    const int64_t hb = __shfl_sync(FULL_MASK, base, src);
+                    for (int c0 = 0; c0 < L; c0 += 32) {
+                        const int t = c0 + lane;
+                        bool pass = false, take = false;
+                        uint64_t a2 = 0, b2 = 0;
+                        double m = 0.0;
+                        if (t < L) {
+                            m = __dmul_rn(__ldg(&T.val[hb + t]), ap);
+                            pass = m >= eps;
+                            const uint16_t cd = __ldg(&T.code[hb + t]);
+                            const int a = cd & 0xff, b = cd >> 8;
+                            if (pass) {
+                                if (grp < 2) {
+                                    const uint64_t w = grp == 0 ? wA : wB;
+                                    if (!((w >> a) & 1ull) && !((w >> b) & 1ull)) {
+                                        const uint64_t w2 =
+                                            w ^ (1ull << hi) ^ (1ull << hj) ^ (1ull << a) ^ (1ull << b);
+                                        a2 = grp == 0 ? w2 : wA;
+                                        b2 = grp == 0 ? wB : w2;
+                                        take = hash_lookup(H, a2, b2) < 0;
+                                    }
+                                } else if (!((wA >> a) & 1ull) && !((wB >> b) & 1ull)) {
+                                    a2 = wA ^ (1ull << hi) ^ (1ull << a);
+                                    b2 = wB ^ (1ull << hj) ^ (1ull << b);
+                                    take = hash_lookup(H, a2, b2) < 0;
+                                }
+                            }
+                        }
+                        keep(take, a2, b2, m);
+                        const unsigned stop = __ballot_sync(FULL_MASK, !pass);
+                        tested += stop ? (unsigned)(__ffs(stop) - 1) : 32u;
+                        if (stop) break;  // sorted: every later entry fails too
+                    }
+                }
+            }
+        }
+        if (!EMIT && lane == 0) cnt[det] = run;
+        if (examined && lane == 0) atomicAdd(examined, tested);
+        __syncwarp();
+    }
+}
+
+// output: one configuration per run of equal keys, with the maximum coupling of the run
+// (non-negative doubles order like their bit patterns, so an integer atomicMax is exact)
+template <class K>
+__global__ void k_hb_out(const K* __restrict__ keys, const double* __restrict__ vals,
+                         const uint32_t* __restrict__ flags, const uint32_t* __restrict__ pos,
+                         int64_t n, int norb, ulonglong2* __restrict__ out,
+                         unsigned long long* __restrict__ mx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = (int64_t)pos[i] + flags[i] - 1;
+        if (flags[i]) {
+            uint64_t a, b;
+            key_split(keys[i], norb, a, b);
+            out[u] = make_ulonglong2(a, b);
+        }
+        atomicMax(&mx[u], (unsigned long long)__double_as_longlong(vals[i]));
+    }
+}
+
+template <class K>
+__global__ void k_hb_heads(const K* __restrict__ keys, int64_t n, uint32_t* __restrict__ f) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        f[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+static unsigned hb_grid(int64_t nS) {
+    int64_t g = (nS + HB_WARPS - 1) / HB_WARPS;
+    if (g > 148 * 16) g = 148 * 16;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <class K>
+static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
+                  const uint64_t* dets, const double* psi, int64_t nS, double eps,
+                  nqs_detset* out, cudaStream_t s) {
+    const ProblemDev& P = p->d;
+    const size_t smem = pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx);
+    if (smem > 48 * 1024) {
+        NQS_CK(cudaFuncSetAttribute(k_hb_select<false, K>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_hb_select<true, K>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    int64_t *cnt, *offs, *total_dev;
+    unsigned long long* examined;
+    NQS_TRY(sc.get(&cnt, nS));
+    NQS_TRY(sc.get(&offs, nS));
+    NQS_TRY(sc.get(&total_dev, 1));
+    NQS_TRY(sc.get(&examined, 1));
+    NQS_CK(cudaMemsetAsync(examined, 0, sizeof(unsigned long long), s));
+    {
+        ProfScope prof_(PROF_HB_SELECT, s);
+        k_hb_select<false, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
+            P, H, T, (const ulonglong2*)dets, psi, nS, eps, cnt, nullptr, nullptr, nullptr,
+            examined);
+    }
+    NQS_CK_LAUNCH();
+    NQS_TRY(scan_exclusive_i64(p, sc, cnt, offs, nS, total_dev, s));
+    int64_t n = 0;
+    unsigned long long nexam = 0;
+    NQS_CK(cudaMemcpyAsync(&n, total_dev, sizeof n, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaMemcpyAsync(&nexam, examined, sizeof nexam, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    out->n_emitted = n;
+    out->n_examined = (int64_t)nexam;
+    if (n == 0) return NQS_OK;
+    if (n >= ((int64_t)1 << 32)) {
+        nqs_record_message("nqs_hb_select: more than 2^32 kept pairs; raise eps_hb");
+        return NQS_ERR_UNSUPPORTED;
+    }
+    K *keys, *keys2;
+    double *vals, *vals2;
+    NQS_TRY(sc.get(&keys, n));
+    NQS_TRY(sc.get(&vals, n));
+    NQS_TRY(sc.get(&keys2, n));
+    NQS_TRY(sc.get(&vals2, n));
+    {
+        ProfScope prof_(PROF_HB_SELECT, s);
+        k_hb_select<true, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
+            P, H, T, (const ulonglong2*)dets, psi, nS, eps, nullptr, offs, keys, vals, nullptr);
+    }
+    NQS_CK_LAUNCH();
+    if (sizeof(K) == 4)
+        NQS_TRY(radix_sort_pairs32(p, sc, (uint32_t*&)keys, vals, (uint32_t*&)keys2, vals2, n,
+                                   2 * P.norb, s));
+    else if (sizeof(K) == 8)
+        NQS_TRY(radix_sort_pairs(p, sc, (uint64_t*&)keys, vals, (uint64_t*&)keys2, vals2, n,
+                                 2 * P.norb, s));
+    else
+        NQS_TRY(radix_sort_pairs128(p, sc, (Key128*&)keys, vals, (Key128*&)keys2, vals2, n,
+                                    2 * P.norb, s));
+    uint32_t* flags = (uint32_t*)vals2;
+    uint32_t* pos = flags + n;
+    k_hb_heads<K><<<grid_for(n, 256), 256, 0, s>>>(keys, n, flags);
+    NQS_CK_LAUNCH();
+    NQS_TRY(scan_exclusive_u32(p, sc, flags, pos, n, s));
+    uint32_t last_pos = 0, last_flag = 0;
+    NQS_CK(cudaMemcpyAsync(&last_pos, pos + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaMemcpyAsync(&last_flag, flags + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    const int64_t nu = (int64_t)last_pos + last_flag;
+    uint64_t* od = nullptr;
+    double* om = nullptr;
+    if (cudaMalloc(&od, nu * 2 * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&om, nu * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(od);
+        return NQS_ERR_OOM;
+    }
+    out->dets = od;
+    out->value = om;
+    out->n = nu;
+    NQS_CK(cudaMemsetAsync(om, 0, nu * sizeof(double), s));
+    k_hb_out<K><<<grid_for(n, 256), 256, 0, s>>>(keys, vals, flags, pos, n, P.norb,
+                                                 (ulonglong2*)od, (unsigned long long*)om);
+    NQS_CK_LAUNCH();
+    NQS_CK(cudaStreamSynchronize(s));
+    return NQS_OK;
+}
+
+extern "C" int nqs_hb_select(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                             double eps_hb, const nqs_opts* opts, nqs_detset* out,
+                             nqs_stream_t stream) {
+    if (!p || !dets || !psi || !out || nS <= 0 || !(eps_hb >= 0.0)) return NQS_ERR_ARG;
+    if (((uintptr_t)dets) & 15) return NQS_ERR_ARG;
+    if (nS >= ((int64_t)1 << 31)) return NQS_ERR_UNSUPPORTED;
+    out->dets = nullptr;
+    out->value = nullptr;
+    out->index = nullptr;
+    out->n = out->n_emitted = out->n_examined = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    nqs_opts def;
+    if (!opts) {
+        nqs_opts_default(&def);
+        opts = &def;
+    }
+    HbTab T;
+    NQS_TRY(hb_tables(p, &T));
+    Scratch sc(p, s);
+    if (opts->validate) NQS_TRY(validate_dets(p, sc, dets, nS, true, s));
+    HashS H;
+    NQS_TRY(hash_build(p, sc, dets, nS, &H, s));
+    int st;
+    const int kbits = 2 * p->d.norb;
+    if (kbits <= 32) st = hb_run<uint32_t>(p, sc, H, T, dets, psi, nS, eps_hb, out, s);
+    else if (kbits <= 64) st = hb_run<uint64_t>(p, sc, H, T, dets, psi, nS, eps_hb, out, s);
+    else st = hb_run<Key128>(p, sc, H, T, dets, psi, nS, eps_hb, out, s);
+    if (st < 0) nqs_detset_free(out);
+    return st;
+}
+
+extern "C" int nqs_detset_free(nqs_detset* d) {
+    if (!d) return NQS_OK;
+    cudaFree(d->dets);
+    cudaFree(d->value);
+    cudaFree(d->index);
+    d->dets = nullptr;
+    d->value = nullptr;
+    d->index = nullptr;
+    d->n = 0;
+    return NQS_OK;
+}

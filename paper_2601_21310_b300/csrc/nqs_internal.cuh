@@ -77,6 +77,8 @@ struct nqs_problem {
     long long* bt;  // Dt | Xt | Yt
     cudaMemPool_t pool;  // library-owned stream-ordered pool for per-call scratch
     int* err_word;       // device: set by a kernel whose bounded wait timed out
+    double* hb_val;      // heat-bath integral tables (hb.cu), built on first use
+    uint16_t* hb_code;
 };
 
 // read and clear the problem's device error word (synchronises the stream)
@@ -253,6 +255,9 @@ int scan_exclusive_i64(nqs_problem* p, Scratch& sc, const int64_t* in, int64_t* 
                        int64_t* total, cudaStream_t s);
 int scan_exclusive_u32(nqs_problem* p, Scratch& sc, const uint32_t* in, uint32_t* out, int64_t n,
                        cudaStream_t s);
+// the same for FP64 in a fixed tile order (deterministic; rounding differs from a serial sum)
+int scan_exclusive_f64(nqs_problem* p, Scratch& sc, const double* in, double* out, int64_t n,
+                       double* total, cudaStream_t s);
 // compensated (Neumaier) sum of n FP64 values into *out (device); deterministic
 int ksum_f64(nqs_problem* p, Scratch& sc, const double* x, int64_t n, double* out,
              cudaStream_t s);

@@ -114,6 +114,10 @@ int scan_exclusive_u32(nqs_problem* p, Scratch& sc, const uint32_t* in, uint32_t
                        cudaStream_t s) {
     return scan_exclusive<uint32_t>(p, sc, in, out, n, (uint32_t*)nullptr, s);
 }
+int scan_exclusive_f64(nqs_problem* p, Scratch& sc, const double* in, double* out, int64_t n,
+                       double* total, cudaStream_t s) {
+    return scan_exclusive<double>(p, sc, in, out, n, total, s);
+}
 
 // ------------------------------------------------------------------------------------------
 // compensated (Neumaier) reductions: fixed grid, fixed tree -> deterministic

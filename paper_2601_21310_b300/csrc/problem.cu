@@ -263,6 +263,8 @@ extern "C" int nqs_problem_destroy(nqs_problem* p) {
     cudaFree(p->err_word);
     cudaFree(p->fx);
     cudaFree(p->bt);
+    cudaFree(p->hb_val);
+    cudaFree(p->hb_code);
     if (p->pool) cudaMemPoolDestroy(p->pool);
     free(p);
     return NQS_OK;

@@ -18,7 +18,8 @@ extern "C" int64_t nqs_launch_count(void) { return (int64_t)g_launches.load(); }
 static const char* kNames[PROF_N] = {"conn_count", "conn_fill", "pt2_count", "pt2_emit",
                                      "rs_hist",    "rs_scatter", "seg_reduce", "gemm",
                                      "lu",         "spmv",      "layer1",    "unique_terms",
-                                     "heads",      "scan"};
+                                     "heads",      "scan",      "hb_select",
+                                     "select"};
 
 struct EvPair {
     cudaEvent_t a, b;

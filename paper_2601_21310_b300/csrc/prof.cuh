@@ -19,6 +19,8 @@ enum ProfId {
     PROF_UNIQUE,
     PROF_HEADS,
     PROF_SCAN,
+    PROF_HB_SELECT,
+    PROF_SELECT,
     PROF_N
 };
 

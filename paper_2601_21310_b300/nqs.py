@@ -35,6 +35,11 @@ class CSRStruct(C.Structure):
                 ("nnz", C.c_int64), ("n_rows", C.c_int64)]
 
 
+class DetSetStruct(C.Structure):
+    _fields_ = [("dets", C.c_void_p), ("value", C.c_void_p), ("index", C.c_void_p),
+                ("n", C.c_int64), ("n_emitted", C.c_int64), ("n_examined", C.c_int64)]
+
+
 EXPORTS = {
     # name: (restype, argtypes)
     "nqs_opts_default": (None, [C.c_void_p]),
@@ -59,6 +64,11 @@ EXPORTS = {
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_pt2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                           C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_hb_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                                C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_detset_free": (C.c_int, [C.c_void_p]),
+    "nqs_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int64,
+                             C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_profile_enable": (C.c_int, [C.c_int]),
     "nqs_profile_reset": (C.c_int, []),
     "nqs_profile_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p]),
@@ -79,7 +89,8 @@ EXPORTS = {
 }
 
 PROFILED = ["conn_count", "conn_fill", "pt2_count", "pt2_emit", "rs_hist", "rs_scatter",
-            "seg_reduce", "gemm", "lu", "spmv", "layer1", "unique_terms", "heads", "scan"]
+            "seg_reduce", "gemm", "lu", "spmv", "layer1", "unique_terms", "heads", "scan",
+            "hb_select", "select"]
 
 
 def lib():
@@ -373,6 +384,56 @@ def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, bucke
                          _stream(stream)), "nqs_pt2")
     return dict(ext=out[0], int=out[1], n_unique=int(out[2]), n_emitted=int(out[3]),
                 partials=parts.reshape(-1, 2))
+
+
+def hb_select(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, eps: float,
+              o: Opts | None = None, stream=None):
+    """Heat-bath screened perturbative set (Eq. hb_screen). Returns dict(dets uint64 [n, 2]
+    ascending, coupling float64 [n] = max_x |H_x'x psi_x|, n_emitted, n_examined); the library's
+    buffers are copied into torch tensors on the same stream and freed."""
+    dets = _dets(dets)
+    psi = psi.contiguous()
+    st = DetSetStruct()
+    _check(lib().nqs_hb_select(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0], float(eps),
+                               C.byref(o) if o else None, C.byref(st), _stream(stream)),
+           "nqs_hb_select")
+    out_d, out_c, _ = _take_detset(st, dets.device)
+    return dict(dets=out_d, coupling=out_c, n_emitted=st.n_emitted, n_examined=st.n_examined)
+
+
+SELECT_TOPK, SELECT_MASS, SELECT_THRESHOLD = 0, 1, 2
+
+
+def _take_detset(st: DetSetStruct, device, with_index=False):
+    """Copy a library-owned set into torch tensors and free it."""
+    try:
+        n = st.n
+        d = torch.empty((n, 2), dtype=torch.uint64, device=device)
+        v = torch.empty(n, dtype=torch.float64, device=device)
+        ix = torch.empty(n, dtype=torch.int64, device=device) if with_index else None
+        cudart = _cudart()
+        for dst, src, nb in ((d, st.dets, 16 * n), (v, st.value, 8 * n),
+                             (ix, st.index, 8 * n)):
+            if dst is not None and nb and cudart.cudaMemcpy(
+                    C.c_void_p(dst.data_ptr()), C.c_void_p(src), C.c_size_t(nb), 3) != 0:
+                raise NQSError("cudaMemcpy failed")
+    finally:
+        lib().nqs_detset_free(C.byref(st))
+    return d, v, ix
+
+
+def select(problem: Problem, T: torch.Tensor, logabs: torch.Tensor, mode: int, K: int = 0,
+           param: float = 0.0, o: Opts | None = None, stream=None):
+    """Outer-loop selector (Sec. 2.4.2). Returns dict(dets uint64 [c, 2] ascending by key,
+    logabs [c], index [c] = positions in T)."""
+    T = _dets(T)
+    logabs = logabs.contiguous()
+    st = DetSetStruct()
+    _check(lib().nqs_select(problem.handle, _ptr(T), _ptr(logabs), T.shape[0], int(mode), int(K),
+                            float(param), C.byref(o) if o else None, C.byref(st),
+                            _stream(stream)), "nqs_select")
+    d, v, ix = _take_detset(st, T.device, with_index=True)
+    return dict(dets=d, logabs=v, index=ix)
 
 
 def gemm_bf16(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
