@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nqs", choices=["nqs", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-outer", action="store_true",
+                    help="skip the outer-loop measurement (heat-bath set, amplitudes on T, Top-K)")
     ap.add_argument("--buckets", type=int, default=0,
                     help="PT2 hash buckets (0: enough to keep each bucket under 2^30 emissions)")
     ap.add_argument("--no-pt2", action="store_true",
@@ -378,6 +380,8 @@ def run_nqs(args, ws, rank, local):
     if result["fp64_form"]:
         result["speedup_mixed_over_fp64_form"] = (result["evals_per_s"] /
                                                   result["fp64_form"]["evals_per_s"])
+    if not args.no_outer:
+        result["outer_loop"] = run_outer_loop(args, N, P, net, dets, psi, dtype, stream)
     if not args.no_e2e:
         result["e2e"] = run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg,
                                 o_pt, out, grad, psi, stream, ws)
@@ -422,6 +426,43 @@ def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, 
             "grad_rel_l2_mixed_vs_fp64": grel,
             "dE_pt2_ext": r64["ext"], "dE_pt2_ext_mixed_minus_fp64": info_mixed["ext"] - r64["ext"],
             "dE_pt2_int_mixed_minus_fp64": info_mixed["int"] - r64["int"]}
+
+
+def run_outer_loop(args, N, P, net, dets, psi, dtype, stream, eps_hb=1e-6):
+    """Algorithm 1 steps 1 and 3 after the inner step: the heat-bath screened set P (Eq.
+    hb_screen, eps_hb = 1e-6 as in Sec. 3.3, on psi normalised over S), amplitudes on
+    T = S + P, and the Top-K selector back to |S| configurations. Each timed with CUDA events
+    on the launching stream (median of the timed repetitions after one untimed run)."""
+    nS = dets.shape[0]
+    psi_n = psi / torch.linalg.norm(psi)
+    o = N.opts(precision=dtype, validate=0)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts, r = [], None
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return sorted(ts)[len(ts) // 2], r
+
+    reps = max(3, min(args.steps, 10))
+    hb_ms, hb = timed(lambda: N.hb_select(P, dets, psi_n, eps_hb, o=o), reps)
+    T = torch.cat([dets.view(torch.int64), hb["dets"].view(torch.int64)]).view(torch.uint64)
+    amp_ms, (laT, _, _) = timed(lambda: N.amplitudes(P, net, T, o=o), reps)
+    sel_ms, sel = timed(lambda: N.select(P, T, laT, N.SELECT_TOPK, K=nS, o=o), reps)
+    kept_from_P = int((sel["index"] >= nS).sum().item())
+    return {"eps_hb": eps_hb, "n_P": int(hb["dets"].shape[0]), "n_T": int(T.shape[0]),
+            "hb_pairs_kept": int(hb["n_emitted"]), "hb_candidates_tested": int(hb["n_examined"]),
+            "hb_select_ms": hb_ms,
+            "hb_candidates_per_s": hb["n_examined"] / (hb_ms * 1e-3),
+            "amplitudes_T_ms": amp_ms, "amplitudes_T_dets_per_s": T.shape[0] / (amp_ms * 1e-3),
+            "select_topk_ms": sel_ms, "select_K": nS, "kept_from_P": kept_from_P}
 
 
 def o_pt_buckets(args, p):

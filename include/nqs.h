@@ -135,7 +135,8 @@ int nqs_csr_free(nqs_csr* csr);
 
 /* Amplitudes psi(x) of Eq. backflow_amplitude as log|psi| (device [nS] FP64) and sign (device
  * [nS] int8: +1, -1, or 0 for an exactly singular block, reported as NQS_WARN_SINGULAR).
- * Stream-ordered; synchronises only to report the singular warning. */
+ * Large sets are evaluated in micro-batches of 2^20 configurations (Sec. 3.3) so that the
+ * activation memory stays bounded; dets need not be sorted. Synchronises the stream. */
 int nqs_amplitudes(nqs_problem* problem, nqs_net* net, const uint64_t* dets, int64_t nS,
                    double* logabs, int8_t* sign, const nqs_opts* opts, nqs_stream_t stream);
 

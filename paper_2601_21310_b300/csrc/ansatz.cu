@@ -788,18 +788,41 @@ static int transpose_bf16(const void* src, int64_t R, int64_t Cn, int64_t lds, v
     return NQS_OK;
 }
 
-// X^T[i][m]: input bit i of det m (alpha bits 0..norb-1, then beta)
-__global__ void k_bitsT(const ulonglong2* __restrict__ dets, int64_t M, int norb,
-                        __nv_bfloat16* __restrict__ XT, int64_t ldM) {
-    const int nin = 2 * norb;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M * nin;
+// X[m][c] = input bit c of det m as bf16 0/1 (alpha bits 0..norb-1, then beta), zero for
+// nin <= c < ldX; one thread per 8 columns (one 16-byte store)
+__global__ void k_bits_rows(const ulonglong2* __restrict__ dets, int64_t M, int norb, int ldX,
+                            __nv_bfloat16* __restrict__ X) {
+    const int nin = 2 * norb, per = ldX / 8;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M * per;
          t += (int64_t)gridDim.x * blockDim.x) {
-        int i = (int)(t / M);
-        int64_t m = t - (int64_t)i * M;
-        ulonglong2 x = dets[m];
-        uint64_t word = i < norb ? x.x : x.y;
-        int bit = i < norb ? i : i - norb;
-        XT[(int64_t)i * ldM + m] = __float2bfloat16_rn((float)((word >> bit) & 1ull));
+        const int64_t m = t / per;
+        const int c0 = (int)(t - m * per) * 8;
+        const ulonglong2 x = dets[m];
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = c0 + 2 * k + h;
+                uint32_t bit = 0;
+                if (c < norb) bit = (uint32_t)(x.x >> c) & 1u;
+                else if (c < nin) bit = (uint32_t)(x.y >> (c - norb)) & 1u;
+                v |= (bit ? 0x3F80u : 0u) << (16 * h);  // bf16 1.0 = 0x3F80
+            }
+            w[k] = v;
+        }
+        *(uint4*)(X + m * ldX + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// W1 [H1][nin] -> [H1][ldX] with zero columns nin..ldX-1 (16-byte row pitch for TMA)
+__global__ void k_pad_cols_bf16(const __nv_bfloat16* __restrict__ W, int R, int nin, int ldX,
+                                __nv_bfloat16* __restrict__ Wp) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)R * ldX;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / ldX), c = (int)(t - (int64_t)r * ldX);
+        Wp[t] = c < nin ? W[(int64_t)r * nin + c] : __float2bfloat16_rn(0.f);
     }
 }
 
@@ -849,16 +872,39 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
     NQS_TRY(sc.get(&f.singular, 1));
     NQS_CK(cudaMemsetAsync(f.singular, 0, sizeof(int), s));
     const ulonglong2* D2 = (const ulonglong2*)dets;
-    k_layer1<__nv_bfloat16, float, __nv_bfloat16><<<grid_for(M * H1, 256, 148 * 64), 256, 0, s>>>(
-        D2, M, P.norb, H1, (const __nv_bfloat16*)net->p[0], (const float*)net->p[1],
-        (__nv_bfloat16*)f.H1, nullptr);
-    NQS_CK_LAUNCH();
-    if (keep) {
-        NQS_TRY(transpose_bf16(f.H1, M, H1, H1, f.H1T, f.ldM, s));
-        k_bitsT<<<grid_for(M * nin, 256), 256, 0, s>>>(D2, M, P.norb, (__nv_bfloat16*)f.XT, f.ldM);
-        NQS_CK_LAUNCH();
+    // layer 1 on the tensor cores: H1 = tanh(X W1^T + b1) with X the 0/1 input matrix (exact
+    // in bf16), K = nin padded to a 16-byte row pitch with zero columns on both operands
+    const int ldX = (nin + 7) & ~7;
+    __nv_bfloat16 *X, *W1p;
+    NQS_TRY(sc.get(&X, (size_t)M * ldX));
+    NQS_TRY(sc.get(&W1p, (size_t)H1 * ldX));
+    {
+        ProfScope prof_(PROF_LAYER1, s);
+        k_bits_rows<<<grid_for(M * (ldX / 8), 256), 256, 0, s>>>(D2, M, P.norb, ldX, X);
     }
+    NQS_CK_LAUNCH();
+    k_pad_cols_bf16<<<grid_for((int64_t)H1 * ldX, 256), 256, 0, s>>>(
+        (const __nv_bfloat16*)net->p[0], H1, nin, ldX, W1p);
+    NQS_CK_LAUNCH();
+    if (keep) NQS_TRY(transpose_bf16(X, M, nin, ldX, f.XT, f.ldM, s));
     TcGemm g;
+    memset(&g, 0, sizeof g);
+    g.err = f.err;
+    g.A = X;
+    g.lda = ldX;
+    g.B = W1p;
+    g.ldb = ldX;
+    g.M = (int)M;
+    g.N = H1;
+    g.K = ldX;
+    g.epi = EPI_BIAS_TANH;
+    g.bias = (const float*)net->p[1];
+    g.C = f.H1;
+    g.ldc = H1;
+    g.c_bf16 = 1;
+    g.CT = keep ? (__nv_bfloat16*)f.H1T : nullptr;
+    g.ldct = f.ldM;
+    NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
     memset(&g, 0, sizeof g);
     g.err = f.err;
     // layer 2: H2 = tanh(H1 W2^T + b2), with the transposed copy for dW3

@@ -120,20 +120,33 @@ static int check_common(nqs_problem* p, nqs_net* net, const uint64_t* dets, int6
     return NQS_OK;
 }
 
+#define NQS_AMP_BATCH ((int64_t)1 << 20)
+
 extern "C" int nqs_amplitudes(nqs_problem* p, nqs_net* net, const uint64_t* dets, int64_t nS,
                               double* logabs, int8_t* sign, const nqs_opts* opts,
                               nqs_stream_t stream) {
     NQS_TRY(check_common(p, net, dets, nS, opts));
     if (!logabs || !sign) return NQS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    Scratch sc(p, s);
-    if (opts && opts->validate) NQS_TRY(validate_dets(p, sc, dets, nS, false, s));
-    Fwd f;
-    NQS_TRY(net_forward(net, sc, dets, nS, f, false, logabs, sign, s));
-    int sing = 0;
-    NQS_CK(cudaMemcpyAsync(&sing, f.singular, sizeof sing, cudaMemcpyDeviceToHost, s));
+    if (opts && opts->validate) {
+        Scratch sv(p, s);
+        NQS_TRY(validate_dets(p, sv, dets, nS, false, s));
+    }
+    // micro-batches bound the activation memory for large target sets (Sec. 3.3); each
+    // configuration's amplitude is independent of the others, so the batching is invisible
+    int sing_any = 0;
+    for (int64_t c0 = 0; c0 < nS; c0 += NQS_AMP_BATCH) {
+        const int64_t m = nS - c0 < NQS_AMP_BATCH ? nS - c0 : NQS_AMP_BATCH;
+        Scratch sc(p, s);
+        Fwd f;
+        NQS_TRY(net_forward(net, sc, dets + 2 * c0, m, f, false, logabs + c0, sign + c0, s));
+        int sing = 0;
+        NQS_CK(cudaMemcpyAsync(&sing, f.singular, sizeof sing, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+        sing_any |= sing;
+    }
     NQS_TRY(check_err_word(p, s));
-    return sing ? NQS_WARN_SINGULAR : NQS_OK;
+    return sing_any ? NQS_WARN_SINGULAR : NQS_OK;
 }
 
 extern "C" int nqs_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr* csr,

@@ -2,17 +2,22 @@
 //   C[m][n] = epilogue( sum_k A[m][k] * B[n][k] ),  A, B bfloat16, K-major (k contiguous),
 //   FP32 accumulation in tensor memory.
 //
-// One CTA computes a 128 x BN output tile with 4 warps:
+// Persistent kernel, one CTA per SM, work units (128 x BN output tiles, times the K splits)
+// dealt round-robin; ten warps:
 //   warp 0 / lane 0  TMA producer: 128x64 (A) and BNx64 (B) tiles, 128-byte swizzle, into a
-//                    3-stage shared-memory ring guarded by mbarriers (full / empty);
+//                    shared-memory ring of up to 8 stages guarded by mbarriers (full / empty);
 //   warp 1 / lane 0  MMA issuer: tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN, K=16) x 4 per
-//                    stage, accumulating in TMEM; tcgen05.commit frees the stage;
-//   all 4 warps      epilogue: tcgen05.ld (32 lanes x 32 columns per load, warp w owns TMEM
-//                    lanes 32w..32w+31 = tile rows), fused bias / tanh / Phi0 / tanh'
-//                    epilogues, row-major and (optionally) transposed stores.
-// Split-K (grid.z) writes FP32 partials that a second kernel sums in a fixed order.
-// Every mbarrier wait is bounded (about 2 s of clock); a timeout sets the error word, skips the
-// remaining work and still releases the tensor memory.
+//                    stage into one of two TMEM accumulators; tcgen05.commit frees the stage
+//                    and, after the last stage of a tile, hands the accumulator over;
+//   warps 2..9       epilogue: tcgen05.ld (32 lanes x 32 columns per load; warp w reads TMEM
+//                    lanes 32 (w % 4).. = tile rows, and one half of the columns), fused bias /
+//                    tanh / Phi0 / tanh' epilogues, row-major and (optionally) transposed
+//                    stores, then frees the accumulator. The epilogue of one tile overlaps the
+//                    main loop of the next.
+// Split-K writes FP32 partials that a second kernel sums in a fixed order.
+// Every mbarrier wait is bounded (about 2 s of clock); a timeout raises a CTA-wide abort flag
+// that ends every role's loop, the producer still waits for its copies in flight, the error
+// word is set and the tensor memory is released.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <string.h>
@@ -24,8 +29,8 @@
 #include "nqs_internal.cuh"
 #include "prof.cuh"
 
-#define TC_THREADS 128
-#define TC_STAGES 3
+#define TC_EPI_WARPS 8
+#define TC_THREADS (32 * (2 + TC_EPI_WARPS))
 #define TC_BK 64  // bf16 elements per 128-byte swizzle row
 
 namespace {
@@ -42,24 +47,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
-}
-
-// bounded wait on the given phase parity; false after ~2 s of SM clock
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t addr = smem_u32(bar);
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > 4000000000ll) return false;
-    }
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
@@ -134,179 +121,266 @@ struct TcArgs {
     const float* phi0;       // [N]
     const __nv_bfloat16* aux;  // [M][ld_aux] activation for tanh'
     int64_t ld_aux;
-    float* partial;          // split-K partials [gridDim.z][M][N]
+    float* partial;          // split-K partials [splits][M][N]
+    int splits;
     int* err;
 };
+
+// The epilogue of 32 accumulator columns [nb, nb + 32) of one tile row: fused bias / tanh /
+// Phi0 / tanh' and row-major (optionally transposed) stores, or the FP32 split-K partial.
+template <class U>
+__device__ __forceinline__ void epilogue32(const TcArgs& a, const U& w, int row, bool row_ok,
+                                           int nb, const uint32_t (&r)[32]) {
+    if (a.splits > 1) {
+        float* P = a.partial + (size_t)w.z * a.M * a.N;
+        if (row_ok)
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (nb + j < a.N) P[(size_t)row * a.N + nb + j] = __uint_as_float(r[j]);
+        return;
+    }
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int n = nb + j;
+        float x = __uint_as_float(r[j]);
+        if (n < a.N && row_ok) {
+            if (a.epi == EPI_BIAS_TANH) {
+                x = tanhf(x + a.bias[n]);
+            } else if (a.epi == EPI_BIAS_PHI0) {
+                float z = x + a.bias[n];
+                x = a.phi0[n] + z;
+            } else if (a.epi == EPI_TANH_BWD) {
+                float h = __bfloat162float(a.aux[(size_t)row * a.ld_aux + n]);
+                x = x * (1.0f - h * h);
+            }
+        }
+        v[j] = x;
+    }
+    if (row_ok && a.C) {
+        if (a.c_bf16) {
+            __nv_bfloat16* C = (__nv_bfloat16*)a.C + (size_t)row * a.ldc;
+            if (nb + 32 <= a.N && (a.ldc % 8) == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 pk;
+                    uint32_t* wd = (uint32_t*)&pk;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[q * 8 + 2 * t],
+                                                                  v[q * 8 + 2 * t + 1]);
+                        wd[t] = *(uint32_t*)&h2;
+                    }
+                    *(uint4*)(C + nb + q * 8) = pk;
+                }
+            } else {
+                for (int j = 0; j < 32; ++j)
+                    if (nb + j < a.N) C[nb + j] = __float2bfloat16_rn(v[j]);
+            }
+        } else {
+            float* C = (float*)a.C + (size_t)row * a.ldc;
+            if (nb + 32 <= a.N && (a.ldc % 4) == 0) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    *(float4*)(C + nb + q * 4) =
+                        make_float4(v[q * 4], v[q * 4 + 1], v[q * 4 + 2], v[q * 4 + 3]);
+            } else {
+                for (int j = 0; j < 32; ++j)
+                    if (nb + j < a.N) C[nb + j] = v[j];
+            }
+        }
+    }
+    if (row_ok && a.CT) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (nb + j < a.N) a.CT[(size_t)(nb + j) * a.ldct + row] = __float2bfloat16_rn(v[j]);
+    }
+}
 
 template <int BN>
 struct TcSmem {
     static constexpr int A_BYTES = 128 * TC_BK * 2;
     static constexpr int B_BYTES = BN * TC_BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int BYTES = TC_STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int STAGES = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;
+    static constexpr int BYTES = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait that also gives up as soon as another role of the CTA has aborted
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    const uint32_t addr = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > 4000000000ll) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// One work unit = (split z, row tile, column tile); units are dealt round-robin to the
+// persistent CTAs, column tile fastest so that CTAs running together share the A rows in L2.
+struct Unit {
+    int m0, n0, kb0, nk, z;
+};
+__device__ __forceinline__ Unit unit_of(int u, const TcArgs& a, int BN) {
+    const int ntn = (a.N + BN - 1) / BN, ntm = (a.M + 127) / 128;
+    const int tiles = ntn * ntm;
+    const int z = u / tiles, t = u - z * tiles;
+    const int nkb = (a.K + TC_BK - 1) / TC_BK;
+    const int per = (nkb + a.splits - 1) / a.splits;
+    Unit r;
+    r.z = z;
+    r.m0 = (t / ntn) * 128;
+    r.n0 = (t % ntn) * BN;
+    r.kb0 = z * per;
+    r.nk = max(0, min(nkb, r.kb0 + per) - r.kb0);
+    return r;
+}
+
+// Persistent, warp-specialised: warp 0 lane 0 issues TMA, warp 1 lane 0 issues tcgen05.mma into
+// one of two TMEM accumulators (2 x BN columns), warps 2..9 drain the other accumulator
+// through the epilogue meanwhile (warp w reads TMEM lanes 32 (w % 4).., half (w - 2) / 4 of the
+// columns). Barriers: full/empty per shared-memory stage, tfull/tempty per accumulator.
 template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               TcArgs a) {
     using L = TcSmem<BN>;
+    constexpr int ST = L::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + TC_STAGES * L::STAGE);
-    uint64_t* empty = full + TC_STAGES;
-    uint64_t* done = empty + TC_STAGES;
-    uint32_t* tslot = (uint32_t*)(done + 1);
+    uint64_t* full = (uint64_t*)(smem + ST * L::STAGE);
+    uint64_t* empty = full + ST;
+    uint64_t* tfull = empty + ST;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tslot = (uint32_t*)(tempty + 2);
+    volatile int* abort = (volatile int*)(tslot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * 128;
-    const int nkb = (a.K + TC_BK - 1) / TC_BK;
-    const int per = (nkb + gridDim.z - 1) / gridDim.z;
-    const int kb0 = blockIdx.z * per;
-    const int nk = max(0, min(nkb, kb0 + per) - kb0);
+    const int units = ((a.N + BN - 1) / BN) * ((a.M + 127) / 128) * a.splits;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], TC_EPI_WARPS);
+        }
+        *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile(
             "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                 smem_u32(tslot)),
-            "r"((uint32_t)BN));
+            "r"((uint32_t)(2 * BN)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    bool ok = true;
 
-    if (nk > 0 && warp == 0 && lane == 0) {
-        for (int i = 0; i < nk; ++i) {
-            const int s = i % TC_STAGES;
-            const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
-            if (i >= TC_STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
-                ok = false;
-                break;
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        uint32_t it = 0;
+        for (int u = blockIdx.x; u < units && !*abort; u += gridDim.x) {
+            const Unit w = unit_of(u, a, BN);
+            for (int i = 0; i < w.nk; ++i, ++it) {
+                const int s = it % ST;
+                const uint32_t ph = (it / ST) & 1u;
+                if (it >= (uint32_t)ST && !mbar_wait_ab(&empty[s], ph ^ 1u, abort)) break;
+                uint8_t* st = smem + s * L::STAGE;
+                mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
+                tma_load_2d(st, &tmA, &full[s], (w.kb0 + i) * TC_BK, w.m0);
+                tma_load_2d(st + L::A_BYTES, &tmB, &full[s], (w.kb0 + i) * TC_BK, w.n0);
             }
-            uint8_t* st = smem + s * L::STAGE;
-            mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
-            tma_load_2d(st, &tmA, &full[s], (kb0 + i) * TC_BK, m0);
-            tma_load_2d(st + L::A_BYTES, &tmB, &full[s], (kb0 + i) * TC_BK, n0);
         }
-    } else if (nk > 0 && warp == 1 && lane == 0) {
+        // never leave with copies in flight: wait (bounded) for the last load of each stage
+        const uint32_t last = it;
+        for (uint32_t j = last > (uint32_t)ST ? last - ST : 0; j < last; ++j) {
+            volatile int no_abort = 0;
+            mbar_wait_ab(&full[j % ST], (j / ST) & 1u, &no_abort);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
         const uint32_t idesc = idesc_bf16<BN>();
-        for (int i = 0; i < nk; ++i) {
-            const int s = i % TC_STAGES;
-            const uint32_t ph = (uint32_t)(i / TC_STAGES) & 1u;
-            if (!mbar_wait(&full[s], ph)) {
-                ok = false;
-                break;
-            }
+        uint32_t it = 0, j = 0;
+        for (int u = blockIdx.x; u < units && !*abort; u += gridDim.x, ++j) {
+            const Unit w = unit_of(u, a, BN);
+            const uint32_t b = j & 1u, use = j >> 1;
+            if (use > 0 && !mbar_wait_ab(&tempty[b], (use - 1) & 1u, abort)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint8_t* st = smem + s * L::STAGE;
-            const uint64_t da = sdesc_sw128(smem_u32(st));
-            const uint64_t db = sdesc_sw128(smem_u32(st + L::A_BYTES));
+            const uint32_t acc = tmem + b * BN;
+            bool ok = true;
+            for (int i = 0; i < w.nk; ++i, ++it) {
+                const int s = it % ST;
+                if (!mbar_wait_ab(&full[s], (it / ST) & 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint8_t* st = smem + s * L::STAGE;
+                const uint64_t da = sdesc_sw128(smem_u32(st));
+                const uint64_t db = sdesc_sw128(smem_u32(st + L::A_BYTES));
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk)  // +32 bytes per K=16 step inside the atom
-                umma(tmem, da + 2 * kk, db + 2 * kk, idesc, (i | kk) != 0 ? 1u : 0u);
-            umma_commit(&empty[s]);
+                for (int kk = 0; kk < TC_BK / 16; ++kk)  // +32 bytes per K=16 step in the atom
+                    umma(acc, da + 2 * kk, db + 2 * kk, idesc, (i | kk) != 0 ? 1u : 0u);
+                umma_commit(&empty[s]);
+            }
+            if (!ok) break;
+            umma_commit(&tfull[b]);
         }
-        umma_commit(done);
-    }
-    __syncwarp();
-    if (nk > 0 && !mbar_wait(done, 0)) ok = false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok && a.err) atomicExch(a.err, 1);
-
-    // ---------------- epilogue: thread owns tile row m0 + 32 warp + lane ----------------
-    const int row = m0 + warp * 32 + lane;
-    const bool row_ok = row < a.M;
-    const bool split = gridDim.z > 1;
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int c_lo = half * (BN / 2), c_hi = c_lo + BN / 2;
+        uint32_t j = 0;
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++j) {
+            const Unit w = unit_of(u, a, BN);
+            const uint32_t b = j & 1u, use = j >> 1;
+            if (!mbar_wait_ab(&tfull[b], use & 1u, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = w.m0 + q * 32 + lane;
+            const bool row_ok = row < a.M;
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        if (nk > 0 && ok) {
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) r[j] = 0u;
-        }
-        const int nb = n0 + c;
-        if (split) {
-            float* P = a.partial + (size_t)blockIdx.z * a.M * a.N;
-            if (row_ok)
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (nb + j < a.N) P[(size_t)row * a.N + nb + j] = __uint_as_float(r[j]);
-            continue;
-        }
-        float v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int n = nb + j;
-            float x = __uint_as_float(r[j]);
-            if (n < a.N && row_ok) {
-                if (a.epi == EPI_BIAS_TANH) {
-                    x = tanhf(x + a.bias[n]);
-                } else if (a.epi == EPI_BIAS_PHI0) {
-                    float z = x + a.bias[n];
-                    x = a.phi0[n] + z;
-                } else if (a.epi == EPI_TANH_BWD) {
-                    float h = __bfloat162float(a.aux[(size_t)row * a.ld_aux + n]);
-                    x = x * (1.0f - h * h);
-                }
-            }
-            v[j] = x;
-        }
-        if (row_ok && a.C) {
-            if (a.c_bf16) {
-                __nv_bfloat16* C = (__nv_bfloat16*)a.C + (size_t)row * a.ldc;
-                if (nb + 32 <= a.N && (a.ldc % 8) == 0) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint4 pk;
-                        uint32_t* w = (uint32_t*)&pk;
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[q * 8 + 2 * t],
-                                                                      v[q * 8 + 2 * t + 1]);
-                            w[t] = *(uint32_t*)&h2;
-                        }
-                        *(uint4*)(C + nb + q * 8) = pk;
-                    }
+            for (int c = c_lo; c < c_hi; c += 32) {
+                uint32_t r[32];
+                if (w.nk > 0) {
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)c, r);
                 } else {
-                    for (int j = 0; j < 32; ++j)
-                        if (nb + j < a.N) C[nb + j] = __float2bfloat16_rn(v[j]);
-                }
-            } else {
-                float* C = (float*)a.C + (size_t)row * a.ldc;
-                if (nb + 32 <= a.N && (a.ldc % 4) == 0) {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        *(float4*)(C + nb + q * 4) =
-                            make_float4(v[q * 4], v[q * 4 + 1], v[q * 4 + 2], v[q * 4 + 3]);
-                } else {
-                    for (int j = 0; j < 32; ++j)
-                        if (nb + j < a.N) C[nb + j] = v[j];
+                    for (int t = 0; t < 32; ++t) r[t] = 0u;
                 }
+                epilogue32(a, w, row, row_ok, w.n0 + c, r);
             }
-        }
-        if (row_ok && a.CT) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (nb + j < a.N) a.CT[(size_t)(nb + j) * a.ldct + row] = __float2bfloat16_rn(v[j]);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
         }
     }
+    if (*abort && a.err) atomicExch(a.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"((uint32_t)BN));
+                     "r"((uint32_t)(2 * BN)));
 }
 
 // C[m][n] = sum over splits of P[z][m][n] (fixed order)
@@ -355,12 +429,25 @@ int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64
     return NQS_OK;
 }
 
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 148;
+    }
+    return n;
+}
+
 template <int BN>
-int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int splits,
-              cudaStream_t s) {
+int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, cudaStream_t s) {
     const int smem = TcSmem<BN>::BYTES;
     NQS_CK(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    dim3 grid((a.N + BN - 1) / BN, (a.M + 127) / 128, splits);
+    const int units = ((a.N + BN - 1) / BN) * ((a.M + 127) / 128) * a.splits;
+    const int grid = units < num_sms() ? units : num_sms();
     {
         ProfScope prof_(PROF_GEMM, s);
         k_gemm_tc<BN><<<grid, TC_THREADS, smem, s>>>(ta, tb, a);
@@ -405,9 +492,9 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
         const int per = (nkb + splits - 1) / splits;
         splits = (nkb + per - 1) / per;
     }
-    int st = BN == 64 ? launch_tc<64>(ta, tb, a, splits, s)
-                      : (BN == 128 ? launch_tc<128>(ta, tb, a, splits, s)
-                                   : launch_tc<256>(ta, tb, a, splits, s));
+    a.splits = splits;
+    int st = BN == 64 ? launch_tc<64>(ta, tb, a, s)
+                      : (BN == 128 ? launch_tc<128>(ta, tb, a, s) : launch_tc<256>(ta, tb, a, s));
     NQS_TRY(st);
     if (splits > 1) {
         k_splitk_reduce<<<grid_for((int64_t)g.M * g.N, 256), 256, 0, s>>>(

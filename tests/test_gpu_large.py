@@ -142,3 +142,24 @@ def test_norb42_pt2_two_word_keys():
     assert abs(got["partials"][1, 0] - ref["ext"]) < 1e-10 * abs(ref["ext"])
     assert abs(got["partials"][1, 1] - ref["int"]) < 1e-10 * max(1e-300, abs(ref["int"]))
     assert got["n_emitted"] == len(S) * 271944
+
+
+def test_amplitudes_beyond_one_micro_batch():
+    """nqs_amplitudes on 1.2 million configurations (two micro-batches of 2^20): sampled rows on
+    both sides of the batch boundary equal the oracle's FP64 amplitudes."""
+    need_gpu()
+    N = nqs()
+    norb, n = 16, 8
+    h, eri, _ = synth.integrals(norb, 2 * norb, 1, 3.0)
+    T = synth.select_S(norb, n, 1_200_000)
+    T = T[np.random.default_rng(0).permutation(len(T))]  # amplitudes need no ordering
+    net = synth.net_params(norb, n, n, (64, 64), 21)
+    P = N.Problem(norb, n, n, h, eri)
+    gnet = N.Net(P, N.net_tensors(net, N.NQS_FP64), N.NQS_FP64)
+    la, sg, _ = N.amplitudes(P, gnet, to_dev(T), o=N.opts(validate=0))
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    B = 1 << 20
+    rows = np.r_[0:500, B - 500:B + 500, len(T) - 500:len(T)]
+    rla, rsg = O.amplitudes(O.Net(net), T[rows])
+    assert np.array_equal(sg[rows], rsg)
+    assert np.abs(la[rows] - rla).max() < 1e-9
