@@ -694,9 +694,31 @@ static int emit_cmp(const void* p, const void* q) {
     return 0;
 }
 
+int orc_pt2_eps(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
+                const double* psi, double E, double eps, int64_t nbuckets, int64_t bucket,
+                double* out);
 int orc_pt2(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
             const double* psi, double E, int64_t nbuckets, int64_t bucket, double* out) {
-    if (nS <= 0 || nbuckets < 1) return ORC_ERR_ARG;
+    return orc_pt2_eps(norb, h, eri, S, nS, psi, E, 0.0, nbuckets, bucket, out);
+}
+
+/* emission test of the screened form: targets inside S always (the internal term is exact);
+ * targets outside S when |H_x'y| |psi_y| >= eps (every one when eps = 0) */
+static int pt2_keep(const uint64_t* S, int64_t nS, uint64_t xa, uint64_t xb, double hv,
+                    double py, double eps) {
+    if (eps == 0.0) return 1;
+    if (fabs(hv) * fabs(py) >= eps) return 1;
+    return find_in_S(S, nS, xa, xb) >= 0;
+}
+
+/* The same correction with the external sum screened as in Sec. 3.3 (Eq. hb_screen applied to
+ * each contribution): c(x') keeps only the terms H_x'y psi_y with |H_x'y psi_y| >= eps, and the
+ * external sum runs over the x' outside S that receive at least one such term (the screened
+ * perturbative set P). The internal term stays exact. eps = 0 is orc_pt2. */
+int orc_pt2_eps(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
+                const double* psi, double E, double eps, int64_t nbuckets, int64_t bucket,
+                double* out) {
+    if (nS <= 0 || nbuckets < 1 || !(eps >= 0.0)) return ORC_ERR_ARG;
     int na = popc(S[0]), nb = popc(S[1]);
     int64_t nexc = orc_n_excitations(norb, na, nb);
     ksum Dk = {0, 0};
@@ -711,9 +733,14 @@ int orc_pt2(int norb, const double* h, const double* eri, const uint64_t* S, int
 #pragma omp for schedule(dynamic, 16)
         for (int64_t r = 0; r < nS; ++r) {
             int64_t n = orc_excitations(norb, S[2 * r], S[2 * r + 1], buf), c = 0;
-            for (int64_t k = 0; k < n; ++k)
-                if (bucket < 0 || (int64_t)orc_bucket(buf[2 * k], buf[2 * k + 1], nbuckets) == bucket)
-                    ++c;
+            for (int64_t k = 0; k < n; ++k) {
+                uint64_t xa = buf[2 * k], xb = buf[2 * k + 1];
+                if (bucket >= 0 && (int64_t)orc_bucket(xa, xb, nbuckets) != bucket) continue;
+                double hv = eps == 0.0 ? 0.0
+                                       : orc_element(norb, h, eri, S[2 * r], S[2 * r + 1], xa, xb,
+                                                     NULL);
+                if (pt2_keep(S, nS, xa, xb, hv, psi[r], eps)) ++c;
+            }
             cnt[r + 1] = c;
         }
         free(buf);
@@ -735,9 +762,11 @@ int orc_pt2(int norb, const double* h, const double* eri, const uint64_t* S, int
             for (int64_t k = 0; k < n; ++k) {
                 uint64_t xa = buf[2 * k], xb = buf[2 * k + 1];
                 if (bucket >= 0 && (int64_t)orc_bucket(xa, xb, nbuckets) != bucket) continue;
+                double hv = orc_element(norb, h, eri, a, b, xa, xb, NULL);
+                if (!pt2_keep(S, nS, xa, xb, hv, psi[r], eps)) continue;
                 em[pos].a = xa;
                 em[pos].b = xb;
-                em[pos].v = orc_element(norb, h, eri, a, b, xa, xb, NULL) * psi[r];
+                em[pos].v = hv * psi[r];
                 em[pos].seq = pos;
                 ++pos;
             }

@@ -54,6 +54,9 @@ def lib():
                                          dp, dp]
         L.orc_select.restype = i64
         L.orc_select.argtypes = [dp, dp, i64, C.c_int, i64, C.c_double, dp]
+        L.orc_pt2_eps.restype = C.c_int
+        L.orc_pt2_eps.argtypes = [C.c_int, dp, dp, dp, i64, dp, C.c_double, C.c_double, i64, i64,
+                                  dp]
         L.orc_num_threads.restype = C.c_int
         L.orc_num_threads.argtypes = []
     return _lib
@@ -242,13 +245,14 @@ def bucket(a, b, nbuckets) -> int:
     return int(lib().orc_bucket(int(a), int(b), int(nbuckets)))
 
 
-def pt2(norb, h, eri, S, psi, E, nbuckets: int = 1, bucket_id: int = -1):
+def pt2(norb, h, eri, S, psi, E, nbuckets: int = 1, bucket_id: int = -1, eps: float = 0.0):
     """Returns dict(ext, int, n_unique, D). bucket_id >= 0 restricts both terms to the
-    configurations of that hash bucket."""
+    configurations of that hash bucket. eps > 0 screens the external contributions
+    (|H_x'y psi_y| >= eps, Sec. 3.3); the internal term stays exact."""
     h, eri, S, psi = _f64(h), _f64(eri), _u64(S), _f64(psi)
     out = np.zeros(4)
-    st = lib().orc_pt2(norb, _p(h), _p(eri), _p(S), S.shape[0], _p(psi), float(E), int(nbuckets),
-                       int(bucket_id), _p(out))
+    st = lib().orc_pt2_eps(norb, _p(h), _p(eri), _p(S), S.shape[0], _p(psi), float(E),
+                           float(eps), int(nbuckets), int(bucket_id), _p(out))
     assert st == 0, st
     return dict(ext=out[0], int=out[1], n_unique=int(out[2]), D=out[3])
 

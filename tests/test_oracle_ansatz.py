@@ -224,3 +224,41 @@ def test_pt2_internal_vanishes_at_eigenvector(olib, tiny):
     w, V = np.linalg.eigh(csr.to_scipy().toarray())
     r = olib.pt2(p.wl.norb, p.h, p.eri, p.S, V[:, 0], w[0])
     assert abs(r["int"]) < 1e-18
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-2, 5e-2])
+def test_screened_pt2_matches_dense_bruteforce(olib, eps):
+    """Screened external term (Sec. 3.3 applied to each contribution): c(x') keeps the terms
+    H_x'y psi_y with |H_x'y psi_y| >= eps; x' outside S with at least one kept term form P.
+    Against the dense brute-force H; the internal term stays exact."""
+    norb, n = 6, 3
+    h, eri, _ = synth.integrals(norb, 12, 23, 3.0)
+    dets, H = BF.dense_hamiltonian(norb, n, n, h, eri)
+    rng = np.random.default_rng(6)
+    pick = np.sort(rng.choice(len(dets), size=70, replace=False))
+    S = dets[pick]
+    psi = rng.normal(size=70) * np.exp(-3 * rng.random(70))
+    csr = olib.hss(norb, h, eri, S)
+    out, _ = olib.energy_from_psi(csr, psi)
+    E, D = out[0], out[2]
+    inS = np.zeros(len(dets), bool)
+    inS[pick] = True
+    dH = np.diag(H)
+    Hc = H[:, pick] * psi[None, :]          # contributions H_x'y psi_y
+    Hc[np.arange(len(dets))[:, None] == pick[None, :]] = 0.0  # no diagonal contribution
+    keep = np.abs(Hc) >= eps
+    c = np.where(keep, Hc, 0.0).sum(axis=1)
+    in_P = (~inS) & keep.any(axis=1)
+    ext = np.sum(c[in_P] ** 2 / (D * (E - dH[in_P])))
+    full = np.zeros(len(dets))
+    full[pick] = psi
+    r = (H @ full)[pick] - E * psi
+    intl = np.sum(r ** 2 / (D * (E - dH[pick])))
+    got = olib.pt2(norb, h, eri, S, psi, E, eps=eps)
+    assert got["n_unique"] == int(in_P.sum())
+    assert abs(got["ext"] - ext) <= 1e-12 * abs(ext)
+    assert abs(got["int"] - intl) <= 1e-12 * abs(intl)
+    # eps = 0 is the unscreened correction
+    z = olib.pt2(norb, h, eri, S, psi, E, eps=0.0)
+    u = olib.pt2(norb, h, eri, S, psi, E)
+    assert z == u
