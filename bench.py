@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nqs", choices=["nqs", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--eps-pt2", type=float, default=0.0,
+                    help="PT2 screening threshold on psi normalised over S (0: the full "
+                         "connected space; the paper's heat-bath value is 1e-6)")
     ap.add_argument("--no-outer", action="store_true",
                     help="skip the outer-loop measurement (heat-bath set, amplitudes on T, Top-K)")
     ap.add_argument("--buckets", type=int, default=0,
@@ -226,7 +229,9 @@ def run_nqs(args, ws, rank, local):
     o_eg = N.opts(precision=dtype, validate=0)
     nexc_total = nS * synth_nexc(wl)
     buckets = args.buckets if args.buckets > 0 else max(1, -(-nexc_total // (1 << 30)))
-    o_pt = N.opts(precision=dtype, buckets=buckets, validate=0)
+    if args.eps_pt2 > 0 and args.buckets == 0:
+        buckets = 0  # screened: the library sizes the buckets from the counted emissions
+    o_pt = N.opts(precision=dtype, buckets=buckets, validate=0, eps_pt2=args.eps_pt2)
     out = torch.empty(4, dtype=torch.float64, device=dev)
     grad = torch.empty(net.num_params(), dtype=net.grad_dtype(), device=dev)
     psi = torch.empty(nS, dtype=torch.float64, device=dev)
@@ -250,10 +255,14 @@ def run_nqs(args, ws, rank, local):
         E = out[0].item()
         if args.no_pt2:
             r = dict(n_emitted=0, n_unique=0, ext=float("nan"), int=float("nan"))
+        elif args.eps_pt2 > 0:
+            # the screening threshold refers to psi normalised over S
+            r = N.pt2(P, dets, psi / torch.linalg.norm(psi), E, o=o_pt)
         else:
             r = N.pt2(P, dets, psi, E, o=o_pt)
         e3 = mark(record)
         info = dict(n_conn=csr.n_enumerated + r["n_emitted"], n_hss=csr.n_enumerated,
+                    buckets=r.get("buckets", 0),
                     n_emit=r["n_emitted"], nnz=csr.nnz, n_unique=r["n_unique"], E=E,
                     ext=r["ext"], int=r["int"])
         csr.free()
@@ -325,7 +334,7 @@ def run_nqs(args, ws, rank, local):
     def work(k):
         per_launch_flops = total_gemm_flops / max(1, prof[k][1] / args.steps)
         return algorithmic_work(k, wl, nS, nexc, info["nnz"], info["n_emit"], info["n_unique"],
-                                per_launch_flops, max(1, buckets))
+                                per_launch_flops, max(1, info["buckets"]))
 
     # the roofline is reported for the largest kernel with a byte or FLOP bound; the largest
     # kernel overall is named beside it when it is an issue-bound one
@@ -361,7 +370,8 @@ def run_nqs(args, ws, rank, local):
         "data": "synthetic (seeded integrals, level-major S, random-init backflow MLP)",
         "config": {"workload": wl.name, "norb": wl.norb, "nalpha": wl.nalpha, "nbeta": wl.nbeta,
                    "n_S": nS, "mlp": [2 * wl.norb, *wl.hidden, wl.norb * wl.nelec],
-                   "pt2_buckets": 0 if args.no_pt2 else buckets,
+                   "pt2_buckets": 0 if args.no_pt2 else info["buckets"],
+                   "pt2_eps": args.eps_pt2,
                    "step": "connections + energy_grad" if args.no_pt2 else
                            "connections + energy_grad + pt2",
                    "l2": "flushed between timed steps (512 MB write)",
@@ -417,6 +427,8 @@ def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, 
     N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
     E64 = out64[0].item()
     r64 = (dict(ext=float("nan"), int=float("nan")) if args.no_pt2 else
+           N.pt2(P, dets, psi64 / torch.linalg.norm(psi64), E64,
+                 o=N.opts(validate=0, buckets=0, eps_pt2=args.eps_pt2)) if args.eps_pt2 > 0 else
            N.pt2(P, dets, psi64, E64, o=N.opts(validate=0, buckets=o_pt_buckets(args, p))))
     csr.free()
     gm = grad_mixed.double()

@@ -73,7 +73,12 @@ typedef struct {
     int64_t chunk;      /* PT2 cap on emitted (key, value) pairs held at once; 0 = automatic */
     int validate;       /* 1: check that S is sorted, unique and has the right popcounts */
     int internal_pt2;   /* 1: also compute the internal (x in S) PT2 term */
-    int reserved[8];
+    double eps_pt2;     /* PT2 screening (Sec. 3.3 criterion per contribution): 0 = the full
+                           connected space; > 0 keeps only the external contributions
+                           |H_x'y psi_y| >= eps_pt2 (psi as passed to nqs_pt2), so the external
+                           sum runs over the screened perturbative set; the internal term stays
+                           exact */
+    int reserved[6];
 } nqs_opts;
 
 /* Library-owned CSR of H_SS (device memory). Row r holds, in order: the diagonal element
@@ -165,11 +170,17 @@ int nqs_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr, cons
  * (key x', H_x'y psi_y) in canonical order, radix-sorted by key (stable), deduplicated, and
  * each run summed in emission order; members of S feed the internal term. The work is split
  * into hash buckets (SplitMix64 finaliser: bucket = mix(mix(a) ^ b) mod B).
- * psi: device [nS] FP64 at any scale. out: host [4] = {external, internal, number of unique
- * x' in C\S, number of emitted pairs}. bucket_partials: host [2*B] (external, internal per
- * bucket) or NULL. Sort keys are 32-bit, 64-bit or two-word by 2*norb. Each bucket's emissions
- * must stay below 2^32 (and fit in memory): use more buckets for larger problems. Synchronises
- * the stream. Errors: NQS_ERR_ARG, NQS_ERR_OOM (a bucket too large), NQS_ERR_CUDA. */
+ * psi: device [nS] FP64 at any scale. out: host [5] = {external, internal, number of unique
+ * x' in C\S, number of emitted pairs, number of buckets used}. opts->buckets = 0 chooses the
+ * bucket count: one bucket's pairs use at most half of the free device memory. bucket_partials:
+ * host [2*B] (external, internal per bucket) or NULL (required with opts->buckets = 0). Sort keys are 32-bit, 64-bit or two-word by 2*norb. Each bucket's emissions
+ * must stay below 2^32 (and fit in memory): use more buckets for larger problems.
+ * With opts->eps_pt2 > 0 (Sec. 3.3: the external sum of Eq. pt2_correction runs over the
+ * screened perturbative set P) only the contributions with |H_x'y psi_y| >= eps_pt2 to x' outside
+ * S are emitted, found by the sorted-integral walk of nqs_hb_select; c(x') sums those, P is the
+ * x' that receive at least one, and the internal term takes H_SS psi exactly from the connected
+ * sets of S. Synchronises the stream. Errors: NQS_ERR_ARG (also eps_pt2 < 0 or NaN),
+ * NQS_ERR_OOM (a bucket too large), NQS_ERR_CUDA. */
 int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64_t nS,
             double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
             nqs_stream_t stream);

@@ -174,19 +174,48 @@ static int hb_tables(nqs_problem* p, HbTab* out) {
     return NQS_OK;
 }
 
-// The screened traversal of one x per warp. EMIT = false: cnt[det] = number of kept pairs.
-// EMIT = true: the pairs are written from offs[det] on. examined (may be null) accumulates the
-// number of candidates whose coupling was tested.
-template <bool EMIT, class K>
+__device__ __forceinline__ bool in_bucket_of(uint64_t a, uint64_t b, uint64_t B, uint64_t bucket) {
+    return B == 1 || (det_hash(a, b) % B) == bucket;
+}
+
+// signed <x'|H|x> of a double read from its orbitals, with the same terms and signs as
+// exc_element: same spin (grp 0 alpha, 1 beta) holes i<j -> particles a<b, sign of i->a then
+// j->b; opposite spin i->a (alpha), j->b (beta)
+__device__ __forceinline__ double double_element(const ProblemDev& P, int grp, uint64_t wA,
+                                                 uint64_t wB, int i, int j, int a, int b) {
+    if (grp < 2) {
+        const uint64_t w = grp == 0 ? wA : wB;
+        const int s1 = exc_sign(w, i, a);
+        const uint64_t w1 = w ^ (1ull << i) ^ (1ull << a);
+        const int s2 = exc_sign(w1, j, b);
+        const double v = eri_at(P, i, a, j, b) - eri_at(P, j, a, i, b);
+        return s1 * s2 < 0 ? -v : v;
+    }
+    const double v = eri_at(P, i, a, j, b);
+    return exc_sign(wA, i, a) * exc_sign(wB, j, b) < 0 ? -v : v;
+}
+
+// The screened traversal of one x per warp, in four modes:
+//   HB_COUNT / HB_EMIT  heat-bath set: cnt[det] = number of kept pairs, or the pairs
+//                       (key, |H_x'x psi_x|) written from offs[det] on;
+//   PT_COUNT / PT_EMIT  screened PT2 emissions of one hash bucket: the same test plus
+//                       bucket(x') == bucket, emitting the signed H_x'x psi_x.
+// examined (may be null) accumulates the number of candidates whose coupling was tested.
+enum { HB_COUNT = 0, HB_EMIT = 1, PT_COUNT = 2, PT_EMIT = 3 };
+
+template <int MODE, class K>
 __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS H, HbTab T,
                                                           const ulonglong2* __restrict__ S,
                                                           const double* __restrict__ psi,
-                                                          int64_t nS, double eps,
+                                                          int64_t nS, double eps, uint64_t B,
+                                                          uint64_t bucket,
                                                           int64_t* __restrict__ cnt,
                                                           const int64_t* __restrict__ offs,
                                                           K* __restrict__ keys,
                                                           double* __restrict__ vals,
                                                           unsigned long long* examined) {
+    constexpr bool EMIT = (MODE & 1) != 0;
+    constexpr bool PTM = MODE >= PT_COUNT;
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables PT = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
@@ -197,7 +226,8 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
     for (int64_t det = (int64_t)blockIdx.x * HB_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * HB_WARPS) {
         const ulonglong2 x = S[det];
-        const double ap = fabs(psi[det]);
+        const double py = psi[det];
+        const double ap = fabs(py);
         int64_t run = EMIT ? offs[det] : 0;
         unsigned long long tested = 0;
         // m = |H| |psi| >= eps fails for every coupling when |psi| = 0 < eps, and when psi is
@@ -225,8 +255,15 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             double m = 0.0;
             if (e < nsing) {
                 decode_exc(P, PT, *ctx, x.x, x.y, e, ex);
-                m = __dmul_rn(fabs(exc_element(P, *ctx, ex)), ap);
-                take = m >= eps && hash_lookup(H, ex.a2, ex.b2) < 0;
+                const double hv = exc_element(P, *ctx, ex);
+                m = __dmul_rn(fabs(hv), ap);
+                if (PTM) {
+                    take = m >= eps && in_bucket_of(ex.a2, ex.b2, B, bucket) &&
+                           hash_lookup(H, ex.a2, ex.b2) < 0;
+                    m = __dmul_rn(hv, py);
+                } else {
+                    take = m >= eps && hash_lookup(H, ex.a2, ex.b2) < 0;
+                }
             }
             keep(take, ex.a2, ex.b2, m);
         }
@@ -276,6 +313,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                             const uint16_t cd = __ldg(&T.code[hb + t]);
                             const int a = cd & 0xff, b = cd >> 8;
                             if (pass) {
+                                bool valid = false;
                                 if (grp < 2) {
                                     const uint64_t w = grp == 0 ? wA : wB;
                                     if (!((w >> a) & 1ull) && !((w >> b) & 1ull)) {
@@ -283,13 +321,17 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                                             w ^ (1ull << hi) ^ (1ull << hj) ^ (1ull << a) ^ (1ull << b);
                                         a2 = grp == 0 ? w2 : wA;
                                         b2 = grp == 0 ? wB : w2;
-                                        take = hash_lookup(H, a2, b2) < 0;
+                                        valid = true;
                                     }
                                 } else if (!((wA >> a) & 1ull) && !((wB >> b) & 1ull)) {
                                     a2 = wA ^ (1ull << hi) ^ (1ull << a);
                                     b2 = wB ^ (1ull << hj) ^ (1ull << b);
-                                    take = hash_lookup(H, a2, b2) < 0;
+                                    valid = true;
                                 }
+                                if (PTM) valid = valid && in_bucket_of(a2, b2, B, bucket);
+                                take = valid && hash_lookup(H, a2, b2) < 0;
+                                if (PTM && EMIT && take)
+                                    m = __dmul_rn(double_element(P, grp, wA, wB, hi, hj, a, b), py);
                             }
                         }
                         keep(take, a2, b2, m);
@@ -345,9 +387,9 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
     const ProblemDev& P = p->d;
     const size_t smem = pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx);
     if (smem > 48 * 1024) {
-        NQS_CK(cudaFuncSetAttribute(k_hb_select<false, K>,
+        NQS_CK(cudaFuncSetAttribute(k_hb_select<HB_COUNT, K>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        NQS_CK(cudaFuncSetAttribute(k_hb_select<true, K>,
+        NQS_CK(cudaFuncSetAttribute(k_hb_select<HB_EMIT, K>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     int64_t *cnt, *offs, *total_dev;
@@ -359,8 +401,8 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
     NQS_CK(cudaMemsetAsync(examined, 0, sizeof(unsigned long long), s));
     {
         ProfScope prof_(PROF_HB_SELECT, s);
-        k_hb_select<false, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
-            P, H, T, (const ulonglong2*)dets, psi, nS, eps, cnt, nullptr, nullptr, nullptr,
+        k_hb_select<HB_COUNT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
+            P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, cnt, nullptr, nullptr, nullptr,
             examined);
     }
     NQS_CK_LAUNCH();
@@ -385,8 +427,9 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
     NQS_TRY(sc.get(&vals2, n));
     {
         ProfScope prof_(PROF_HB_SELECT, s);
-        k_hb_select<true, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
-            P, H, T, (const ulonglong2*)dets, psi, nS, eps, nullptr, offs, keys, vals, nullptr);
+        k_hb_select<HB_EMIT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
+            P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, nullptr, offs, keys, vals,
+            nullptr);
     }
     NQS_CK_LAUNCH();
     if (sizeof(K) == 4)
@@ -425,6 +468,52 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
     NQS_CK_LAUNCH();
     NQS_CK(cudaStreamSynchronize(s));
     return NQS_OK;
+}
+
+// One pass of the screened PT2 emission for bucket `bucket` of B: with cnt, the per-x counts;
+// otherwise the (key, H_x'x psi_x) pairs written at offs (keys of the width 2 norb needs).
+template <class K>
+static int hb_pt2_pass_k(nqs_problem* p, const HbTab& T, const HashS& H, const uint64_t* dets,
+                         const double* psi, int64_t nS, double eps, uint64_t B, uint64_t bucket,
+                         int64_t* cnt, const int64_t* offs, void* keys, double* vals,
+                         cudaStream_t s) {
+    const ProblemDev& P = p->d;
+    const size_t smem = pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx);
+    if (smem > 48 * 1024) {
+        NQS_CK(cudaFuncSetAttribute(k_hb_select<PT_COUNT, K>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_hb_select<PT_EMIT, K>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    if (cnt) {
+        ProfScope prof_(PROF_PT2_COUNT, s);
+        k_hb_select<PT_COUNT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
+            P, H, T, (const ulonglong2*)dets, psi, nS, eps, B, bucket, cnt, nullptr, nullptr,
+            nullptr, nullptr);
+    } else {
+        ProfScope prof_(PROF_PT2_EMIT, s);
+        k_hb_select<PT_EMIT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
+            P, H, T, (const ulonglong2*)dets, psi, nS, eps, B, bucket, nullptr, offs, (K*)keys,
+            vals, nullptr);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int hb_pt2_pass(nqs_problem* p, const HashS& H, const uint64_t* dets, const double* psi,
+                int64_t nS, double eps, uint64_t B, uint64_t bucket, int64_t* cnt,
+                const int64_t* offs, void* keys, double* vals, cudaStream_t s) {
+    HbTab T;
+    NQS_TRY(hb_tables(p, &T));
+    const int kbits = 2 * p->d.norb;
+    if (kbits <= 32)
+        return hb_pt2_pass_k<uint32_t>(p, T, H, dets, psi, nS, eps, B, bucket, cnt, offs, keys,
+                                       vals, s);
+    if (kbits <= 64)
+        return hb_pt2_pass_k<uint64_t>(p, T, H, dets, psi, nS, eps, B, bucket, cnt, offs, keys,
+                                       vals, s);
+    return hb_pt2_pass_k<Key128>(p, T, H, dets, psi, nS, eps, B, bucket, cnt, offs, keys, vals,
+                                 s);
 }
 
 extern "C" int nqs_hb_select(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,

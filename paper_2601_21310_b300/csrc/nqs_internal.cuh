@@ -188,6 +188,11 @@ unsigned conn_grid_size(int64_t nS);
 
 int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, HashS* out,
                cudaStream_t s);
+// screened PT2 emission pass (hb.cu): counts per det when cnt != null, else the (key, H psi)
+// pairs at offs; keys are uint32 / uint64 / Key128 by 2 norb
+int hb_pt2_pass(nqs_problem* p, const HashS& H, const uint64_t* dets, const double* psi,
+                int64_t nS, double eps, uint64_t B, uint64_t bucket, int64_t* cnt,
+                const int64_t* offs, void* keys, double* vals, cudaStream_t s);
 int validate_dets(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, bool sorted,
                   cudaStream_t s);
 

@@ -334,6 +334,41 @@ __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(next, local);
 }
 
+// cS[x] = sum over the excitations y of x that lie in S of <x|H|y> psi_y (the off-diagonal part
+// of (H_SS psi)_x), by enumerating x's own connected set; one warp per x, lanes keep partial
+// sums in canonical order, then a fixed shuffle tree. Used by the screened form, whose
+// emissions leave out the configurations of S.
+__global__ void __launch_bounds__(PT_THREADS) k_pt2_hss_psi(ProblemDev P, HashS H,
+                                                             const ulonglong2* __restrict__ S,
+                                                             const double* __restrict__ psi,
+                                                             int64_t nS, double* __restrict__ cS) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nexc = (uint32_t)P.nexc;
+    for (int64_t det = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * PT_WARPS) {
+        const ulonglong2 x = S[det];
+        fill_ctx(P, x.x, x.y, ctx, lane);
+        double acc = 0.0;
+        for (uint32_t e = lane; e < nexc; e += 32) {
+            uint64_t a2, b2;
+            decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+            const int32_t hit = hash_lookup(H, a2, b2);
+            if (hit >= 0) {
+                Exc ex;
+                decode_exc(P, T, *ctx, x.x, x.y, e, ex);
+                acc = __dadd_rn(acc, __dmul_rn(exc_element(P, *ctx, ex), psi[hit]));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(FULL_MASK, acc, o));
+        if (lane == 0) cS[det] = acc;
+        __syncwarp();
+    }
+}
+
 __global__ void k_pt2_internal(ProblemDev P, const ulonglong2* __restrict__ S,
                                const double* __restrict__ psi, const double* __restrict__ cS,
                                int64_t nS, const double* __restrict__ Dp, double E, uint64_t B,
@@ -379,7 +414,7 @@ template <class K>
 static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
                       double E_var, int64_t B, int64_t b, const int64_t* offs, int64_t n,
                       const HashS& H, double* cS, double* D_dev, double* ext_dev,
-                      unsigned long long* nuniq_dev, size_t smem, cudaStream_t s) {
+                      unsigned long long* nuniq_dev, size_t smem, double eps, cudaStream_t s) {
     const ProblemDev& P = p->d;
     Scratch bs(p, s);
     K *keys, *keys2;
@@ -388,13 +423,17 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
     NQS_TRY(bs.get(&vals, n));
     NQS_TRY(bs.get(&keys2, n));
     NQS_TRY(bs.get(&vals2, n));
-    {
-        ProfScope prof_(PROF_PT2_EMIT, s);
-        k_pt2_emit<K><<<pt_grid(nS), PT_THREADS, smem, s>>>(P, (const ulonglong2*)dets, psi, nS,
-                                                            (uint64_t)B, (uint64_t)b, offs, keys,
-                                                            vals);
+    if (eps > 0.0) {
+        NQS_TRY(hb_pt2_pass(p, H, dets, psi, nS, eps, (uint64_t)B, (uint64_t)b, nullptr, offs,
+                            keys, vals, s));
+    } else {
+        {
+            ProfScope prof_(PROF_PT2_EMIT, s);
+            k_pt2_emit<K><<<pt_grid(nS), PT_THREADS, smem, s>>>(
+                P, (const ulonglong2*)dets, psi, nS, (uint64_t)B, (uint64_t)b, offs, keys, vals);
+        }
+        NQS_CK_LAUNCH();
     }
-    NQS_CK_LAUNCH();
     if (sizeof(K) == 4)
         NQS_TRY(radix_sort_pairs32(p, bs, (uint32_t*&)keys, vals, (uint32_t*&)keys2, vals2, n,
                                    2 * P.norb, s));
@@ -450,12 +489,16 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     if (((uintptr_t)dets) & 15) return NQS_ERR_ARG;
     if (nS >= ((int64_t)1 << 31)) return NQS_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
+    if (opts && opts->buckets <= 0 && bucket_partials) return NQS_ERR_ARG;
     nqs_opts def;
     if (!opts) {
         nqs_opts_default(&def);
         opts = &def;
     }
-    const int64_t B = opts->buckets < 1 ? 1 : opts->buckets;
+    const double eps = opts->eps_pt2;
+    if (!(eps >= 0.0)) return NQS_ERR_ARG;
+    const bool screened = eps > 0.0;
+    int64_t B = opts->buckets;
     Scratch sc(p, s);
     if (opts->validate) NQS_TRY(validate_dets(p, sc, dets, nS, true, s));
     HashS H;
@@ -472,6 +515,38 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit<Key128>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
+    int64_t* pre_offs = nullptr;  // offsets of a screened single-bucket count, when one ran
+    int64_t pre_total = 0;
+    if (B <= 0) {
+        // automatic: enough buckets that one bucket's pairs (keys and values twice, flags and
+        // positions) use at most half of the free device memory, and stay below 2^31
+        const int kbits_ = 2 * P.norb;
+        const double kb = kbits_ <= 32 ? 4.0 : (kbits_ <= 64 ? 8.0 : 16.0);
+        size_t fr = 0, tot = 0;
+        NQS_CK(cudaMemGetInfo(&fr, &tot));
+        // memory the library's pool holds but does not use is available too
+        uint64_t reserved = 0, used = 0;
+        NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+        NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        const double avail = (double)fr + (double)(reserved > used ? reserved - used : 0);
+        double cap = 0.5 * avail / (2.0 * (kb + 8.0) + 8.0);
+        if (cap > 2147483647.0) cap = 2147483647.0;
+        double total = (double)nS * (double)P.nexc;
+        if (screened) {
+            NQS_TRY(sc.get(&pre_offs, nS));
+            int64_t *c1, *t1;
+            NQS_TRY(sc.get(&c1, nS));
+            NQS_TRY(sc.get(&t1, 1));
+            NQS_TRY(hb_pt2_pass(p, H, dets, psi, nS, eps, 1, 0, c1, nullptr, nullptr, nullptr, s));
+            NQS_TRY(scan_exclusive_i64(p, sc, c1, pre_offs, nS, t1, s));
+            NQS_CK(cudaMemcpyAsync(&pre_total, t1, sizeof pre_total, cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaStreamSynchronize(s));
+            total = (double)pre_total;
+        }
+        B = (int64_t)ceil(total / cap);
+        if (B < 1) B = 1;
+        if (B > 1) pre_offs = nullptr;  // the counts of one bucket serve only B = 1
+    }
     double* dev_scalars;  // [0] = D, then per bucket (ext, int)
     NQS_TRY(sc.get(&dev_scalars, 1 + 2 * B));
     unsigned long long* next_dev;
@@ -487,9 +562,18 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     int64_t* offs = nullptr;
     int64_t* total_dev = nullptr;
     // one counting pass for every bucket when the B x nS count table stays below 2 GiB
-    const bool count_all =
-        B > 1 && B <= PT_HIST_MAX && (double)nS * (double)B * sizeof(int64_t) <= 2147483648.0;
-    if (B > 1) {
+    const bool count_all = !screened && B > 1 && B <= PT_HIST_MAX &&
+                           (double)nS * (double)B * sizeof(int64_t) <= 2147483648.0;
+    if (screened && opts->internal_pt2) {
+        // the screened emissions leave S out: the internal term takes H_SS psi from S itself
+        if (smem > 48 * 1024)
+            NQS_CK(cudaFuncSetAttribute(k_pt2_hss_psi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+        k_pt2_hss_psi<<<pt_grid(nS), PT_THREADS, smem, s>>>(P, H, (const ulonglong2*)dets, psi,
+                                                             nS, cS);
+        NQS_CK_LAUNCH();
+    }
+    if (B > 1 || screened) {
         NQS_TRY(sc.get(&cnt, count_all ? (size_t)nS * B : (size_t)nS));
         NQS_TRY(sc.get(&offs, nS));
         NQS_TRY(sc.get(&total_dev, 1));
@@ -512,11 +596,16 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     int64_t total_emitted = 0;
     for (int64_t b = 0; b < B; ++b) {
         int64_t n;
-        if (B == 1) {
+        if (B == 1 && !screened) {
             n = nS * P.nexc;
+        } else if (pre_offs) {
+            n = pre_total;
         } else {
             Scratch cs(p, s);
-            if (!count_all) {
+            if (screened) {
+                NQS_TRY(hb_pt2_pass(p, H, dets, psi, nS, eps, (uint64_t)B, (uint64_t)b, cnt,
+                                    nullptr, nullptr, nullptr, s));
+            } else if (!count_all) {
                 {
                     ProfScope prof_(PROF_PT2_COUNT, s);
                     k_pt2_count<<<pt_grid(nS), PT_THREADS, smem, s>>>(
@@ -531,17 +620,17 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
         }
         if (n > cap) return NQS_ERR_OOM;  // more buckets needed
         total_emitted += n;
-        const int64_t* o = B == 1 ? nullptr : offs;
+        const int64_t* o = (B == 1 && !screened) ? nullptr : (pre_offs ? pre_offs : offs);
         int st = kbits <= 32
                      ? pt2_bucket<uint32_t>(p, dets, psi, nS, E_var, B, b, o, n, H, cS,
                                             dev_scalars, dev_scalars + 1 + 2 * b, next_dev + b,
-                                            smem, s)
+                                            smem, eps, s)
                  : kbits <= 64
                      ? pt2_bucket<uint64_t>(p, dets, psi, nS, E_var, B, b, o, n, H, cS,
                                             dev_scalars, dev_scalars + 1 + 2 * b, next_dev + b,
-                                            smem, s)
+                                            smem, eps, s)
                      : pt2_bucket<Key128>(p, dets, psi, nS, E_var, B, b, o, n, H, cS, dev_scalars,
-                                          dev_scalars + 1 + 2 * b, next_dev + b, smem, s);
+                                          dev_scalars + 1 + 2 * b, next_dev + b, smem, eps, s);
         NQS_TRY(st);
         if (opts->internal_pt2) {
             k_pt2_internal<<<grid_for(nS, 256), 256, 0, s>>>(P, (const ulonglong2*)dets, psi, cS,
@@ -575,5 +664,6 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     out[1] = host_ksum(in);
     out[2] = nu;
     out[3] = (double)total_emitted;
+    out[4] = (double)B;
     return NQS_OK;
 }

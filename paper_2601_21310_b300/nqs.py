@@ -27,7 +27,8 @@ class NQSError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("buckets", C.c_int), ("chunk", C.c_int64),
-                ("validate", C.c_int), ("internal_pt2", C.c_int), ("reserved", C.c_int * 8)]
+                ("validate", C.c_int), ("internal_pt2", C.c_int), ("eps_pt2", C.c_double),
+                ("reserved", C.c_int * 6)]
 
 
 class CSRStruct(C.Structure):
@@ -149,11 +150,12 @@ def _dets(d: torch.Tensor) -> torch.Tensor:
     return d.contiguous()
 
 
-def opts(precision=NQS_FP64, buckets=1, chunk=0, validate=1, internal_pt2=1) -> Opts:
+def opts(precision=NQS_FP64, buckets=1, chunk=0, validate=1, internal_pt2=1,
+         eps_pt2=0.0) -> Opts:
     o = Opts()
     lib().nqs_opts_default(C.byref(o))
     o.precision, o.buckets, o.chunk = precision, buckets, chunk
-    o.validate, o.internal_pt2 = validate, internal_pt2
+    o.validate, o.internal_pt2, o.eps_pt2 = validate, internal_pt2, eps_pt2
     return o
 
 
@@ -377,13 +379,14 @@ def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, bucke
     dets = _dets(dets)
     psi = psi.contiguous()
     o = o or opts(buckets=buckets)
-    out = np.zeros(4)
-    parts = np.zeros(2 * o.buckets)
+    out = np.zeros(5)
+    parts = np.zeros(2 * max(o.buckets, 1))
     _check(lib().nqs_pt2(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0], float(E), C.byref(o),
-                         out.ctypes.data_as(C.c_void_p), parts.ctypes.data_as(C.c_void_p),
+                         out.ctypes.data_as(C.c_void_p),
+                         parts.ctypes.data_as(C.c_void_p) if o.buckets > 0 else None,
                          _stream(stream)), "nqs_pt2")
     return dict(ext=out[0], int=out[1], n_unique=int(out[2]), n_emitted=int(out[3]),
-                partials=parts.reshape(-1, 2))
+                buckets=int(out[4]), partials=parts.reshape(-1, 2) if o.buckets > 0 else None)
 
 
 def hb_select(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, eps: float,

@@ -92,3 +92,86 @@ def test_pt2_ragged_shapes():
         assert got["n_unique"] == ref["n_unique"]
         assert abs(got["ext"] - ref["ext"]) < 1e-11 * max(1, abs(ref["ext"]))
         assert abs(got["int"] - ref["int"]) < 1e-11 * max(1, abs(ref["int"]))
+
+
+def _norm_psi_E(p):
+    psi, E = _psi_E(p)
+    return psi / np.linalg.norm(psi), E
+
+
+@pytest.mark.parametrize("eps", [1e-5, 1e-4, 1e-3])
+def test_screened_pt2_tiny_matches_oracle(eps):
+    """External sum over the screened perturbative set (contributions |H_x'y psi_y| >= eps):
+    the set (its size) exactly, energies within 1e-12 Ha; the internal term stays exact."""
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("tiny_n10")
+    P = problem_for(N, p)
+    psi, E = _norm_psi_E(p)
+    ref = O.pt2(10, p.h, p.eri, p.S, psi, E, eps=eps)
+    full = O.pt2(10, p.h, p.eri, p.S, psi, E)
+    got = N.pt2(P, to_dev(p.S), torch.from_numpy(psi).cuda(), E, o=N.opts(eps_pt2=eps))
+    assert got["n_unique"] == ref["n_unique"] < full["n_unique"]
+    assert abs(got["ext"] - ref["ext"]) < 1e-12
+    assert abs(got["int"] - ref["int"]) < 1e-12
+    assert abs(got["int"] - full["int"]) < 1e-12
+    for B in (3, 8):
+        gb = N.pt2(P, to_dev(p.S), torch.from_numpy(psi).cuda(), E,
+                   o=N.opts(eps_pt2=eps, buckets=B))
+        assert gb["n_unique"] == ref["n_unique"]
+        assert abs(gb["ext"] - ref["ext"]) < 1e-12 and abs(gb["int"] - ref["int"]) < 1e-12
+
+
+@pytest.mark.parametrize("norb,n,nS,eps", [(16, 8, 2000, 1e-5), (30, 12, 400, 1e-5),
+                                           (42, 24, 80, 1e-5)])
+def test_screened_pt2_key_widths_match_oracle(norb, n, nS, eps):
+    need_gpu()
+    N = nqs()
+    h, eri, _ = synth.integrals(norb, 2 * norb, norb, 3.0)
+    S = synth.select_S(norb, n, nS)
+    rng = np.random.default_rng(norb)
+    psi = rng.standard_normal(len(S)) * np.exp(-rng.uniform(0, 6, len(S)))
+    psi /= np.linalg.norm(psi)
+    E = -30.0  # below every H_xx of these integrals: every denominator has the same sign
+    P = N.Problem(norb, n, n, h, eri)
+    ref = O.pt2(norb, h, eri, S, psi, E, eps=eps)
+    got = N.pt2(P, to_dev(S), torch.from_numpy(psi).cuda(), E, o=N.opts(eps_pt2=eps))
+    assert got["n_unique"] == ref["n_unique"]
+    assert abs(got["ext"] - ref["ext"]) <= 1e-10 * abs(ref["ext"])
+    assert abs(got["int"] - ref["int"]) <= 1e-10 * abs(ref["int"])
+
+
+def test_screened_pt2_full_size_bucket_invariance():
+    """cr2_24e30o, all 131072 configurations, eps = 1e-6 on the normalised amplitudes: one
+    bucket and five buckets give the same screened set and the same energies."""
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("cr2_24e30o")
+    P = problem_for(N, p)
+    la, sg = O.amplitudes(O.Net(p.net), p.S)
+    psi = sg * np.exp(la - la.max())
+    psi /= np.linalg.norm(psi)
+    E = -60.0
+    d, ps = to_dev(p.S), torch.from_numpy(psi).cuda()
+    a = N.pt2(P, d, ps, E, o=N.opts(eps_pt2=1e-6, validate=0))
+    b = N.pt2(P, d, ps, E, o=N.opts(eps_pt2=1e-6, buckets=5, validate=0))
+    assert a["n_unique"] == b["n_unique"] > 0
+    assert abs(a["ext"] - b["ext"]) <= 1e-10 * abs(a["ext"])
+    assert abs(a["int"] - b["int"]) <= 1e-10 * abs(a["int"])
+
+
+def test_automatic_bucket_count():
+    """opts.buckets = 0: the library picks the bucket count (here one: the tiny case fits) and
+    reports it; partials are not available then."""
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("tiny_n10")
+    P = problem_for(N, p)
+    psi, E = _norm_psi_E(p)
+    d, ps = to_dev(p.S), torch.from_numpy(psi).cuda()
+    for eps in (0.0, 1e-4):
+        one = N.pt2(P, d, ps, E, o=N.opts(eps_pt2=eps, buckets=1))
+        auto = N.pt2(P, d, ps, E, o=N.opts(eps_pt2=eps, buckets=0))
+        assert auto["buckets"] == 1 and auto["partials"] is None
+        assert auto["n_unique"] == one["n_unique"]
+        assert auto["ext"] == one["ext"] and auto["int"] == one["int"]
