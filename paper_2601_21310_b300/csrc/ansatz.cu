@@ -199,6 +199,27 @@ static int gemm_mixed(const GemmArgs& g, bool out_bf16, cudaStream_t s) {
     return gemm_bf16_simt(g, out_bf16, s);
 }
 
+// |det| accumulated as m * 2^e with m in [0.5, 1): one FP64 multiply per pivot and a single
+// log at the end, instead of one FP64 log per pivot (FP64 issues slowly on this part). The
+// split of a positive normal double into mantissa and exponent is done on its bit pattern.
+struct LogDet {
+    double m = 1.0;
+    int e = 0;
+    __device__ __forceinline__ void mul(double v) {  // v > 0, finite
+        const double x = m * v;
+        if (!(x >= 2.2250738585072014e-308)) {  // subnormal product: the library split
+            int k;
+            m = frexp(x, &k);
+            e += k;
+            return;
+        }
+        const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+        e += (int)((b >> 52) & 0x7ffull) - 1022;
+        m = __longlong_as_double((long long)((b & ~(0x7ffull << 52)) | (1022ull << 52)));
+    }
+    __device__ __forceinline__ double log_abs() const { return log(m) + (double)e * M_LN2; }
+};
+
 // ------------------------------------------------------------------------------------------
 // batched LU: one warp per (det, spin block); the block sits in shared memory. Task t covers
 // det t/2, spin t%2; it writes log|det| and the sign of its block to la2/sg2[spin*M + m] and the
@@ -244,7 +265,7 @@ __global__ void __launch_bounds__(LU_WARPS * 32) k_lu(const ulonglong2* __restri
         for (int t = lane; t < n; t += 32) perm_s[warp][t] = t;
         __syncwarp();
         int sgn = 1;
-        double la = 0.0;
+        LogDet det_acc;
         bool sing = false;
         for (int k = 0; k < n; ++k) {
             T best = T(-1);
@@ -285,7 +306,7 @@ __global__ void __launch_bounds__(LU_WARPS * 32) k_lu(const ulonglong2* __restri
                 break;
             }
             if (piv < T(0)) sgn = -sgn;
-            la += log(fabs((double)piv));
+            det_acc.mul(fabs((double)piv));
             for (int i = k + 1 + lane; i < n; i += 32) {
                 T l = A[i * ld + k] / piv;
                 A[i * ld + k] = l;
@@ -295,7 +316,7 @@ __global__ void __launch_bounds__(LU_WARPS * 32) k_lu(const ulonglong2* __restri
         }
         T* Ainv = spin == 0 ? Ainv_a : Ainv_b;
         if (lane == 0) {
-            la2[spin * M + m] = sing ? -INFINITY : la;
+            la2[spin * M + m] = sing ? -INFINITY : det_acc.log_abs();
             sg2[spin * M + m] = (int8_t)(sing ? 0 : sgn);
             if (sing && singular) atomicOr(singular, 1);
         }
@@ -365,7 +386,7 @@ __global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ d
             perm[r] = r;
         }
         int sgn = 1;
-        double la = 0.0;
+        LogDet det_acc;
         bool ok = true;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
@@ -397,7 +418,7 @@ __global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ d
             if (piv == T(0)) ok = false;
             if (ok) {
                 if (piv < T(0)) sgn = -sgn;
-                la += log(fabs((double)piv));
+                det_acc.mul(fabs((double)piv));
 #pragma unroll
                 for (int i = k + 1; i < N; ++i) {
                     const T l = A[i][k] / piv;
@@ -407,7 +428,7 @@ __global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ d
                 }
             }
         }
-        la_out[m] = ok ? la : -INFINITY;
+        la_out[m] = ok ? det_acc.log_abs() : -INFINITY;
         sg_out[m] = (int8_t)(ok ? sgn : 0);
         if (!ok && singular) atomicOr(singular, 1);
         if (Ainv) {
