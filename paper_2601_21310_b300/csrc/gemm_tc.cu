@@ -123,8 +123,126 @@ struct TcArgs {
     int64_t ld_aux;
     float* partial;          // split-K partials [splits][M][N]
     int splits;
+    int tma_c, tma_ct, tma_p;  // stores go through the tensor maps below (else direct)
     int* err;
 };
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+            (uint64_t)map),
+        "r"(smem_u32(src)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y,
+                                             int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            (uint64_t)map),
+        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read0() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait0() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// The epilogue of 32 accumulator columns [nb, nb + 32) of the 32 tile rows of one warp, staged
+// in the warp's 4 KB shared-memory buffer and written by TMA stores (the hardware clips rows
+// >= M and columns >= N): the row-major output (bf16 or FP32), the transposed bf16 copy, or the
+// FP32 split-K partial. Row-contiguous operands of the epilogue (tanh' activations) are read
+// with 16-byte loads.
+template <class U>
+__device__ __forceinline__ void epilogue32_tma(const TcArgs& a, const U& w, int row, bool row_ok,
+                                               int nb, int rowbase, const uint32_t (&r)[32],
+                                               uint8_t* stage, const CUtensorMap* mapC,
+                                               const CUtensorMap* mapCT, const CUtensorMap* mapP) {
+    const int lane = threadIdx.x & 31;
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    if (a.splits <= 1 && row_ok) {
+        if (a.epi == EPI_BIAS_TANH) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (nb + j < a.N) v[j] = tanhf(v[j] + a.bias[nb + j]);
+        } else if (a.epi == EPI_BIAS_PHI0) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (nb + j < a.N) {
+                    const float z = v[j] + a.bias[nb + j];
+                    v[j] = a.phi0[nb + j] + z;
+                }
+        } else if (a.epi == EPI_TANH_BWD) {
+            const __nv_bfloat16* hrow = a.aux + (size_t)row * a.ld_aux + nb;
+            if (nb + 32 <= a.N && (a.ld_aux % 8) == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 pk = *(const uint4*)(hrow + 8 * q);
+                    const __nv_bfloat162* h2 = (const __nv_bfloat162*)&pk;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float2 hf = __bfloat1622float2(h2[t]);
+                        v[8 * q + 2 * t] *= 1.0f - hf.x * hf.x;
+                        v[8 * q + 2 * t + 1] *= 1.0f - hf.y * hf.y;
+                    }
+                }
+            } else {
+                for (int j = 0; j < 32; ++j)
+                    if (nb + j < a.N) {
+                        const float h = __bfloat162float(hrow[j]);
+                        v[j] *= 1.0f - h * h;
+                    }
+            }
+        }
+    }
+    const bool f32 = a.splits > 1 || !a.c_bf16;
+    const bool do_c = a.splits > 1 || a.C;
+    if (do_c) {
+        if (f32) {
+            float4* dst = (float4*)(stage + lane * 128);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+            uint4* dst = (uint4*)(stage + lane * 64);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint4 pk;
+                uint32_t* wd = (uint32_t*)&pk;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[q * 8 + 2 * t], v[q * 8 + 2 * t + 1]);
+                    wd[t] = *(uint32_t*)&h2;
+                }
+                dst[q] = pk;
+            }
+        }
+    }
+    uint16_t* stT = (uint16_t*)(stage + 2048);
+    if (a.CT) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            __nv_bfloat16 hv = __float2bfloat16_rn(v[j]);
+            stT[j * 32 + lane] = *(uint16_t*)&hv;
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) {
+        if (a.splits > 1) tma_store_3d(mapP, stage, nb, rowbase, w.z);
+        else if (a.C) tma_store_2d(mapC, stage, nb, rowbase);
+        if (a.CT) tma_store_2d(mapCT, stT, rowbase, nb);
+        bulk_commit();
+        bulk_wait_read0();  // the buffer is rewritten by the next chunk
+    }
+    __syncwarp();
+}
 
 // The epilogue of 32 accumulator columns [nb, nb + 32) of one tile row: fused bias / tanh /
 // Phi0 / tanh' and row-major (optionally transposed) stores, or the FP32 split-K partial.
@@ -203,7 +321,8 @@ struct TcSmem {
     static constexpr int B_BYTES = BN * TC_BK * 2;
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int STAGES = (200 * 1024) / STAGE < 8 ? (200 * 1024) / STAGE : 8;
-    static constexpr int BYTES = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+    static constexpr int EPI = TC_EPI_WARPS * 4096;  // per-warp epilogue staging
+    static constexpr int BYTES = STAGES * STAGE + EPI + 1024 /*align*/ + 256 /*barriers*/;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -259,12 +378,14 @@ __device__ __forceinline__ Unit unit_of(int u, const TcArgs& a, int BN) {
 template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              TcArgs a) {
+              const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmCT,
+              const __grid_constant__ CUtensorMap tmP, TcArgs a) {
     using L = TcSmem<BN>;
     constexpr int ST = L::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + ST * L::STAGE);
+    uint8_t* epi_stage = smem + ST * L::STAGE;
+    uint64_t* full = (uint64_t*)(smem + ST * L::STAGE + L::EPI);
     uint64_t* empty = full + ST;
     uint64_t* tfull = empty + ST;
     uint64_t* tempty = tfull + 2;
@@ -368,12 +489,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int t = 0; t < 32; ++t) r[t] = 0u;
                 }
-                epilogue32(a, w, row, row_ok, w.n0 + c, r);
+                if (a.tma_c)
+                    epilogue32_tma(a, w, row, row_ok, w.n0 + c, w.m0 + q * 32, r,
+                                   epi_stage + (warp - 2) * 4096, &tmC, &tmCT, &tmP);
+                else
+                    epilogue32(a, w, row, row_ok, w.n0 + c, r);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
         }
+        if (a.tma_c && lane == 0) bulk_wait0();  // every store of this warp has landed
     }
     if (*abort && a.err) atomicExch(a.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -429,6 +555,23 @@ int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64
     return NQS_OK;
 }
 
+// plain (unswizzled) store map with a 32 x 32 box: dims innermost first, strides in bytes of
+// the outer dims; false when the layout cannot take TMA (alignment) — the caller then stores
+// directly
+bool make_store_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int esize, int rank,
+                    const cuuint64_t* dims, const cuuint64_t* strides) {
+    if (get_encoder() != NQS_OK || ((uintptr_t)base & 15)) return false;
+    for (int i = 0; i < rank - 1; ++i)
+        if (strides[i] % 16) return false;
+    cuuint32_t box[3] = {32, 32, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    (void)esize;
+    CUresult r = g_encode(m, dt, rank, (void*)base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 int num_sms() {
     static int n = 0;
     if (n == 0) {
@@ -443,14 +586,15 @@ int num_sms() {
 }
 
 template <int BN>
-int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, cudaStream_t s) {
+int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
+              const CUtensorMap& tct, const CUtensorMap& tp, const TcArgs& a, cudaStream_t s) {
     const int smem = TcSmem<BN>::BYTES;
     NQS_CK(cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int units = ((a.N + BN - 1) / BN) * ((a.M + 127) / 128) * a.splits;
     const int grid = units < num_sms() ? units : num_sms();
     {
         ProfScope prof_(PROF_GEMM, s);
-        k_gemm_tc<BN><<<grid, TC_THREADS, smem, s>>>(ta, tb, a);
+        k_gemm_tc<BN><<<grid, TC_THREADS, smem, s>>>(ta, tb, tc, tct, tp, a);
     }
     NQS_CK_LAUNCH();
     return NQS_OK;
@@ -493,8 +637,37 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
         splits = (nkb + per - 1) / per;
     }
     a.splits = splits;
-    int st = BN == 64 ? launch_tc<64>(ta, tb, a, s)
-                      : (BN == 128 ? launch_tc<128>(ta, tb, a, s) : launch_tc<256>(ta, tb, a, s));
+    // epilogue stores through TMA when every output the GEMM writes has a TMA-able layout
+    CUtensorMap tc, tct, tp;
+    memset(&tc, 0, sizeof tc);
+    memset(&tct, 0, sizeof tct);
+    memset(&tp, 0, sizeof tp);
+    bool tma = true;
+    if (splits > 1) {
+        const cuuint64_t dims[3] = {(cuuint64_t)g.N, (cuuint64_t)g.M, (cuuint64_t)splits};
+        const cuuint64_t str[2] = {(cuuint64_t)g.N * 4, (cuuint64_t)g.M * g.N * 4};
+        tma = make_store_map(&tp, a.partial, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 3, dims, str);
+    } else {
+        if (g.C) {
+            const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
+            const cuuint64_t str[1] = {(cuuint64_t)g.ldc * (g.c_bf16 ? 2 : 4)};
+            tma = make_store_map(&tc, g.C,
+                                 g.c_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                 g.c_bf16 ? 2 : 4, 2, dims, str);
+        }
+        if (tma && g.CT) {
+            tma = g.C == nullptr || g.c_bf16;  // one 4 KB staging buffer: bf16 C + bf16 CT
+            const cuuint64_t dims[2] = {(cuuint64_t)g.M, (cuuint64_t)g.N};
+            const cuuint64_t str[1] = {(cuuint64_t)g.ldct * 2};
+            tma = tma && make_store_map(&tct, g.CT, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2, dims,
+                                        str);
+        }
+    }
+    a.tma_c = tma ? 1 : 0;
+    int st = BN == 64 ? launch_tc<64>(ta, tb, tc, tct, tp, a, s)
+                      : (BN == 128 ? launch_tc<128>(ta, tb, tc, tct, tp, a, s)
+                                   : launch_tc<256>(ta, tb, tc, tct, tp, a, s));
     NQS_TRY(st);
     if (splits > 1) {
         k_splitk_reduce<<<grid_for((int64_t)g.M * g.N, 256), 256, 0, s>>>(
