@@ -16,7 +16,8 @@
  *   - the perturbative correction is Eq. (pt2_correction);
  *   - the heat-bath screened perturbative set is Eq. (hb_screen);
  *   - the subspace selector of the outer loop is Sec. 2.4.2 (Top-K, cumulative mass,
- *     absolute threshold).
+ *     absolute threshold);
+ *   - the Proxy-mode Hamiltonian is Eq. (proxy_hamiltonian).
  *
  * Conventions fixed here (the paper is silent on them):
  *   - spin-orbital order alpha 0..norb-1, then beta 0..norb-1; |x> = prod over occupied
@@ -810,6 +811,88 @@ int orc_pt2_eps(int norb, const double* h, const double* eri, const uint64_t* S,
     free(cS);
     free(em);
     free(cnt);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Proxy Hamiltonian of Eq. (proxy_hamiltonian) (Sec. 2.4.1, Proxy mode) on T = V + P as a CSR
+ * over T, with T[0..nV) = V and T[nV..nT) = P, each sorted by key:
+ *   (H~)_xy = H_xy when x or y is in V;  H_xx on the diagonal;  0 for x != y both in P.
+ * Row x in V: [diagonal, then every excitation of x found in T, canonical order]; row x in P:
+ * [diagonal, then every excitation of x found in V, ascending V index]. Column = index in T.
+ * With this matrix E_proxy (Eq. proxy_energy) and its gradient (Eq. proxy_gradient) are the
+ * Rayleigh quotient and gradient of orc_energy_grad over T. Two passes like orc_hss.
+ * ---------------------------------------------------------------------------------------- */
+static int64_t find_in_T(const uint64_t* T, int64_t nV, int64_t nT, uint64_t a, uint64_t b) {
+    int64_t v = find_in_S(T, nV, a, b);
+    if (v >= 0) return v;
+    int64_t q = find_in_S(T + 2 * nV, nT - nV, a, b);
+    return q >= 0 ? nV + q : -1;
+}
+
+typedef struct {
+    int64_t c;
+    double v;
+} colval_t;
+
+static int colval_cmp(const void* p, const void* q) {
+    int64_t a = ((const colval_t*)p)->c, b = ((const colval_t*)q)->c;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+int orc_proxy_csr(int norb, const double* h, const double* eri, const uint64_t* T, int64_t nV,
+                  int64_t nT, int fill, int64_t* row_ptr, int32_t* col, double* val) {
+    if (norb < 1 || norb > 64 || nV < 0 || nT < nV) return ORC_ERR_ARG;
+    if (nT == 0) {
+        row_ptr[0] = 0;
+        return ORC_OK;
+    }
+    int na = popc(T[0]), nb = popc(T[1]);
+    int64_t nexc = orc_n_excitations(norb, na, nb);
+    int err = 0;
+#pragma omp parallel
+    {
+        uint64_t* buf = (uint64_t*)malloc(sizeof(uint64_t) * 2 * (size_t)(nexc > 0 ? nexc : 1));
+        colval_t* cv = (colval_t*)malloc(sizeof(colval_t) * (size_t)(nexc > 0 ? nexc : 1));
+        if (!buf || !cv) {
+#pragma omp atomic write
+            err = 1;
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t r = 0; r < nT; ++r) {
+            if (!buf || !cv) continue;
+            uint64_t a = T[2 * r], b = T[2 * r + 1];
+            int64_t n = orc_excitations(norb, a, b, buf), m = 0;
+            for (int64_t k = 0; k < n; ++k) {
+                int64_t c = r < nV ? find_in_T(T, nV, nT, buf[2 * k], buf[2 * k + 1])
+                                   : find_in_S(T, nV, buf[2 * k], buf[2 * k + 1]);
+                if (c < 0) continue;
+                cv[m].c = c;
+                cv[m].v = fill ? orc_element(norb, h, eri, a, b, buf[2 * k], buf[2 * k + 1], NULL)
+                               : 0.0;
+                ++m;
+            }
+            if (!fill) {
+                row_ptr[r + 1] = m + 1;
+                continue;
+            }
+            if (r >= nV) qsort(cv, m, sizeof(colval_t), colval_cmp);
+            int64_t pos = row_ptr[r];
+            col[pos] = (int32_t)r;
+            val[pos] = orc_diag(norb, h, eri, a, b);
+            for (int64_t k = 0; k < m; ++k) {
+                col[pos + 1 + k] = (int32_t)cv[k].c;
+                val[pos + 1 + k] = cv[k].v;
+            }
+        }
+        free(buf);
+        free(cv);
+    }
+    if (err) return ORC_ERR_OOM;
+    if (!fill) {
+        row_ptr[0] = 0;
+        for (int64_t r = 0; r < nT; ++r) row_ptr[r + 1] += row_ptr[r];
+    }
     return ORC_OK;
 }
 

@@ -57,6 +57,8 @@ def lib():
         L.orc_pt2_eps.restype = C.c_int
         L.orc_pt2_eps.argtypes = [C.c_int, dp, dp, dp, i64, dp, C.c_double, C.c_double, i64, i64,
                                   dp]
+        L.orc_proxy_csr.restype = C.c_int
+        L.orc_proxy_csr.argtypes = [C.c_int, dp, dp, dp, i64, i64, C.c_int, dp, dp, dp]
         L.orc_num_threads.restype = C.c_int
         L.orc_num_threads.argtypes = []
     return _lib
@@ -290,3 +292,25 @@ def select(T, logabs, mode, K=0, param=0.0):
     c = lib().orc_select(_p(T), _p(logabs), T.shape[0], int(mode), int(K), float(param), _p(out))
     assert c >= 0, c
     return out[:c]
+
+
+# ------------------------------------------------------------------------------------------
+# Proxy mode (Sec. 2.4.1): the proxy Hamiltonian of Eq. (proxy_hamiltonian) on T = V + P
+# ------------------------------------------------------------------------------------------
+def proxy_csr(norb, h, eri, V, P) -> CSR:
+    """CSR of H~ over T = [V; P] (V and P each sorted): rows of V hold every connection inside T,
+    rows of P the diagonal and their connections to V only. E_proxy and its gradient are
+    energy_grad(net, T, proxy_csr(...))."""
+    h, eri = _f64(h), _f64(eri)
+    T = _u64(np.concatenate([_u64(V).reshape(-1, 2), _u64(P).reshape(-1, 2)]))
+    nV, nT = len(V), T.shape[0]
+    row_ptr = np.zeros(nT + 1, np.int64)
+    L = lib()
+    st = L.orc_proxy_csr(norb, _p(h), _p(eri), _p(T), nV, nT, 0, _p(row_ptr), None, None)
+    assert st == 0, st
+    nnz = int(row_ptr[-1])
+    col = np.zeros(max(nnz, 1), np.int32)
+    val = np.zeros(max(nnz, 1), np.float64)
+    st = L.orc_proxy_csr(norb, _p(h), _p(eri), _p(T), nV, nT, 1, _p(row_ptr), _p(col), _p(val))
+    assert st == 0, st
+    return CSR(row_ptr, col[:nnz], val[:nnz], 0)
