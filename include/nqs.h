@@ -138,6 +138,19 @@ int nqs_connections(nqs_problem* problem, const uint64_t* dets, int64_t nS, cons
                     nqs_csr* out, int64_t* n_enumerated, nqs_stream_t stream);
 int nqs_csr_free(nqs_csr* csr);
 
+/* Proxy-mode Hamiltonian, Eq. (proxy_hamiltonian) of Sec. 2.4.1, on the target set T = V + P:
+ * (H~)_xy = H_xy when x or y lies in V, H_xx on the diagonal, 0 between distinct members of P.
+ * T: device [nT][2] with T[0..nV) = V and T[nV..nT) = P, each sorted by key (checked with
+ * opts->validate) and disjoint. On success *out holds a library-owned CSR over T (free with
+ * nqs_csr_free): row x of V = [diagonal, then every excitation of x found in T, canonical order];
+ * row x of P = [diagonal, then the members of V connected to x, ascending]; columns are positions
+ * in T; symmetric bit for bit. nqs_energy_grad over T with this matrix gives E_proxy
+ * (Eq. proxy_energy) and its gradient (Eq. proxy_gradient). Synchronises the stream. Errors:
+ * NQS_ERR_ARG, NQS_ERR_UNSORTED / NQS_ERR_POPCOUNT (with validate), NQS_ERR_UNSUPPORTED
+ * (nT >= 2^31), NQS_ERR_OOM, NQS_ERR_CUDA. */
+int nqs_proxy_hamiltonian(nqs_problem* problem, const uint64_t* T, int64_t nV, int64_t nT,
+                          const nqs_opts* opts, nqs_csr* out, nqs_stream_t stream);
+
 /* Amplitudes psi(x) of Eq. backflow_amplitude as log|psi| (device [nS] FP64) and sign (device
  * [nS] int8: +1, -1, or 0 for an exactly singular block, reported as NQS_WARN_SINGULAR).
  * Large sets are evaluated in micro-batches of 2^20 configurations (Sec. 3.3) so that the

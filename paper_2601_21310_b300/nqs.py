@@ -57,6 +57,8 @@ EXPORTS = {
     "nqs_connections": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "nqs_csr_free": (C.c_int, [C.c_void_p]),
+    "nqs_proxy_hamiltonian": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]),
     "nqs_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_energy_from_psi": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
@@ -318,6 +320,17 @@ def connections(problem: Problem, dets: torch.Tensor, o: Opts | None = None, str
                                  C.byref(o) if o else None, C.byref(st), C.byref(nen),
                                  _stream(stream)), "nqs_connections")
     return CSR(st, nen.value, problem)
+
+
+def proxy_hamiltonian(problem: Problem, T: torch.Tensor, nV: int, o: Opts | None = None,
+                      stream=None) -> CSR:
+    """H~ of the Proxy mode (Eq. proxy_hamiltonian) over T = [V; P] as a library-owned CSR."""
+    T = _dets(T)
+    st = CSRStruct()
+    _check(lib().nqs_proxy_hamiltonian(problem.handle, _ptr(T), int(nV), T.shape[0],
+                                       C.byref(o) if o else None, C.byref(st), _stream(stream)),
+           "nqs_proxy_hamiltonian")
+    return CSR(st, 0, problem)
 
 
 def connections_noalloc(problem: Problem, dets: torch.Tensor, row_ptr: torch.Tensor,
