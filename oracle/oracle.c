@@ -17,7 +17,8 @@
  *   - the heat-bath screened perturbative set is Eq. (hb_screen);
  *   - the subspace selector of the outer loop is Sec. 2.4.2 (Top-K, cumulative mass,
  *     absolute threshold);
- *   - the Proxy-mode Hamiltonian is Eq. (proxy_hamiltonian).
+ *   - the Proxy-mode Hamiltonian is Eq. (proxy_hamiltonian); the Asymmetric mode is
+ *     Eqs. (asymmetric_energy), (asymmetric_gradient) with its exact gradient derived here.
  *
  * Conventions fixed here (the paper is silent on them):
  *   - spin-orbital order alpha 0..norb-1, then beta 0..norb-1; |x> = prod over occupied
@@ -534,6 +535,104 @@ int64_t orc_n_params(const orc_net* n) {
            nout;
 }
 
+/* sum over r of coef_r * (d psi_r / d theta), with d psi / d Phi = psi A^{-T} per spin block
+ * (Jacobi's formula through the LU inverse) pushed back through the MLP; written as
+ * coef_r psi_r d log|psi_r| / d theta. Configurations with a singular block are skipped. */
+static int grad_core(const orc_net* n, const uint64_t* S, int64_t nS, const int8_t* sg,
+                     const double* psi, const double* coef, double* grad) {
+    int norb = n->norb, nin = 2 * norb, nel = n->na + n->nb, nout = norb * nel;
+    int64_t np = orc_n_params(n);
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    double* acc = (double*)calloc((size_t)np * nthr, sizeof(double));
+    if (!acc) return ORC_ERR_OOM;
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* g = acc + (size_t)np * tid;
+        double *gW1 = g, *gb1 = gW1 + (size_t)n->H1 * nin, *gW2 = gb1 + n->H1;
+        double *gb2 = gW2 + (size_t)n->H2 * n->H1, *gW3 = gb2 + n->H2;
+        double* gb3 = gW3 + (size_t)nout * n->H2;
+        double* x = (double*)malloc(sizeof(double) * nin);
+        double* h1 = (double*)malloc(sizeof(double) * n->H1);
+        double* h2 = (double*)malloc(sizeof(double) * n->H2);
+        double* phi = (double*)malloc(sizeof(double) * nout);
+        double* dphi = (double*)malloc(sizeof(double) * nout);
+        double* dh2 = (double*)malloc(sizeof(double) * n->H2);
+        double* dh1 = (double*)malloc(sizeof(double) * n->H1);
+        double A[64 * 64], inv[64 * 64];
+        int perm[64], oa[64], ob[64];
+#pragma omp for schedule(static)
+        for (int64_t r = 0; r < nS; ++r) {
+            if (sg[r] == 0) continue; /* singular block: contribution dropped */
+            double w = coef[r] * psi[r];
+            net_forward(n, S[2 * r], S[2 * r + 1], x, h1, h2, phi);
+            occ_list(S[2 * r], norb, oa);
+            occ_list(S[2 * r + 1], norb, ob);
+            memset(dphi, 0, sizeof(double) * nout);
+            double la;
+            gather_block(phi, nel, oa, n->na, 0, A);
+            lu_factor(A, n->na, perm, &la);
+            lu_inverse(A, perm, n->na, inv);
+            for (int j = 0; j < n->na; ++j)
+                for (int k = 0; k < n->na; ++k)
+                    dphi[(size_t)oa[j] * nel + k] += w * inv[k * n->na + j];
+            gather_block(phi, nel, ob, n->nb, n->na, A);
+            lu_factor(A, n->nb, perm, &la);
+            lu_inverse(A, perm, n->nb, inv);
+            for (int j = 0; j < n->nb; ++j)
+                for (int k = 0; k < n->nb; ++k)
+                    dphi[(size_t)ob[j] * nel + n->na + k] += w * inv[k * n->nb + j];
+            /* output layer */
+            for (int i = 0; i < n->H2; ++i) dh2[i] = 0.0;
+            for (int o = 0; o < nout; ++o) {
+                double d = dphi[o];
+                if (d == 0.0) continue;
+                gb3[o] += d;
+                for (int k = 0; k < n->H2; ++k) {
+                    gW3[(size_t)o * n->H2 + k] += d * h2[k];
+                    dh2[k] += wq(n, n->W3[(size_t)o * n->H2 + k]) * d;
+                }
+            }
+            /* hidden layer 2: tanh' = 1 - h^2 */
+            for (int i = 0; i < n->H1; ++i) dh1[i] = 0.0;
+            for (int i = 0; i < n->H2; ++i) {
+                double dz = dh2[i] * (1.0 - h2[i] * h2[i]);
+                gb2[i] += dz;
+                for (int k = 0; k < n->H1; ++k) {
+                    gW2[(size_t)i * n->H1 + k] += dz * h1[k];
+                    dh1[k] += wq(n, n->W2[(size_t)i * n->H1 + k]) * dz;
+                }
+            }
+            /* hidden layer 1 */
+            for (int i = 0; i < n->H1; ++i) {
+                double dz = dh1[i] * (1.0 - h1[i] * h1[i]);
+                gb1[i] += dz;
+                for (int k = 0; k < nin; ++k) gW1[(size_t)i * nin + k] += dz * x[k];
+            }
+        }
+        free(x);
+        free(h1);
+        free(h2);
+        free(phi);
+        free(dphi);
+        free(dh2);
+        free(dh1);
+    }
+    for (int64_t p = 0; p < np; ++p) {
+        double s = 0.0;
+        for (int t = 0; t < nthr; ++t) s += acc[(size_t)np * t + p];
+        grad[p] = s;
+    }
+    free(acc);
+    return ORC_OK;
+}
+
 int orc_energy_grad(const orc_net* n, const uint64_t* S, int64_t nS, const int64_t* row_ptr,
                     const int32_t* col, const double* val, double* out, double* grad,
                     double* psi_out, double* v_out) {
@@ -556,96 +655,12 @@ int orc_energy_grad(const orc_net* n, const uint64_t* S, int64_t nS, const int64
     out[3] = M;
     double E = ev[0], D = ev[2];
     if (grad) {
-        int norb = n->norb, nin = 2 * norb, nel = n->na + n->nb, nout = norb * nel;
-        int64_t np = orc_n_params(n);
-        int nthr = 1;
-#ifdef _OPENMP
-        nthr = omp_get_max_threads();
-#endif
-        double* acc = (double*)calloc((size_t)np * nthr, sizeof(double));
-        if (!acc) return ORC_ERR_OOM;
-#pragma omp parallel
-        {
-            int tid = 0;
-#ifdef _OPENMP
-            tid = omp_get_thread_num();
-#endif
-            double* g = acc + (size_t)np * tid;
-            double *gW1 = g, *gb1 = gW1 + (size_t)n->H1 * nin, *gW2 = gb1 + n->H1;
-            double *gb2 = gW2 + (size_t)n->H2 * n->H1, *gW3 = gb2 + n->H2;
-            double* gb3 = gW3 + (size_t)nout * n->H2;
-            double* x = (double*)malloc(sizeof(double) * nin);
-            double* h1 = (double*)malloc(sizeof(double) * n->H1);
-            double* h2 = (double*)malloc(sizeof(double) * n->H2);
-            double* phi = (double*)malloc(sizeof(double) * nout);
-            double* dphi = (double*)malloc(sizeof(double) * nout);
-            double* dh2 = (double*)malloc(sizeof(double) * n->H2);
-            double* dh1 = (double*)malloc(sizeof(double) * n->H1);
-            double A[64 * 64], inv[64 * 64];
-            int perm[64], oa[64], ob[64];
-#pragma omp for schedule(static)
-            for (int64_t r = 0; r < nS; ++r) {
-                if (sg[r] == 0) continue; /* singular block: contribution dropped */
-                double w = (2.0 / D) * (v[r] - E * psi[r]) * psi[r];
-                net_forward(n, S[2 * r], S[2 * r + 1], x, h1, h2, phi);
-                occ_list(S[2 * r], norb, oa);
-                occ_list(S[2 * r + 1], norb, ob);
-                memset(dphi, 0, sizeof(double) * nout);
-                double la;
-                gather_block(phi, nel, oa, n->na, 0, A);
-                lu_factor(A, n->na, perm, &la);
-                lu_inverse(A, perm, n->na, inv);
-                for (int j = 0; j < n->na; ++j)
-                    for (int k = 0; k < n->na; ++k)
-                        dphi[(size_t)oa[j] * nel + k] += w * inv[k * n->na + j];
-                gather_block(phi, nel, ob, n->nb, n->na, A);
-                lu_factor(A, n->nb, perm, &la);
-                lu_inverse(A, perm, n->nb, inv);
-                for (int j = 0; j < n->nb; ++j)
-                    for (int k = 0; k < n->nb; ++k)
-                        dphi[(size_t)ob[j] * nel + n->na + k] += w * inv[k * n->nb + j];
-                /* output layer */
-                for (int i = 0; i < n->H2; ++i) dh2[i] = 0.0;
-                for (int o = 0; o < nout; ++o) {
-                    double d = dphi[o];
-                    if (d == 0.0) continue;
-                    gb3[o] += d;
-                    for (int k = 0; k < n->H2; ++k) {
-                        gW3[(size_t)o * n->H2 + k] += d * h2[k];
-                        dh2[k] += wq(n, n->W3[(size_t)o * n->H2 + k]) * d;
-                    }
-                }
-                /* hidden layer 2: tanh' = 1 - h^2 */
-                for (int i = 0; i < n->H1; ++i) dh1[i] = 0.0;
-                for (int i = 0; i < n->H2; ++i) {
-                    double dz = dh2[i] * (1.0 - h2[i] * h2[i]);
-                    gb2[i] += dz;
-                    for (int k = 0; k < n->H1; ++k) {
-                        gW2[(size_t)i * n->H1 + k] += dz * h1[k];
-                        dh1[k] += wq(n, n->W2[(size_t)i * n->H1 + k]) * dz;
-                    }
-                }
-                /* hidden layer 1 */
-                for (int i = 0; i < n->H1; ++i) {
-                    double dz = dh1[i] * (1.0 - h1[i] * h1[i]);
-                    gb1[i] += dz;
-                    for (int k = 0; k < nin; ++k) gW1[(size_t)i * nin + k] += dz * x[k];
-                }
-            }
-            free(x);
-            free(h1);
-            free(h2);
-            free(phi);
-            free(dphi);
-            free(dh2);
-            free(dh1);
-        }
-        for (int64_t p = 0; p < np; ++p) {
-            double s = 0.0;
-            for (int t = 0; t < nthr; ++t) s += acc[(size_t)np * t + p];
-            grad[p] = s;
-        }
-        free(acc);
+        double* coef = (double*)malloc(sizeof(double) * nS);
+        if (!coef) return ORC_ERR_OOM;
+        for (int64_t r = 0; r < nS; ++r) coef[r] = (2.0 / D) * (v[r] - E * psi[r]);
+        int st = grad_core(n, S, nS, sg, psi, coef, grad);
+        free(coef);
+        if (st != ORC_OK) return st;
     }
     if (psi_out) memcpy(psi_out, psi, sizeof(double) * nS);
     if (v_out) memcpy(v_out, v, sizeof(double) * nS);
@@ -653,6 +668,79 @@ int orc_energy_grad(const orc_net* n, const uint64_t* S, int64_t nS, const int64
     free(sg);
     free(psi);
     free(v);
+    return status;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Asymmetric mode (Sec. 2.4.1, Eqs. asymmetric_energy, asymmetric_gradient) on T = V + P with
+ * the proxy CSR over T (its V rows hold every connection inside T; its P rows the connections to
+ * V after their diagonal):
+ *   E_asym = N / D,  N = sum_{x in V} psi_x (H_VT psi_T)_x,  D = sum_{x in V} psi_x^2
+ *     (= sum_V p_V(x) E_loc(x) with E_loc(x) = (H_VT psi_T)_x / psi_x).
+ * Gradient, as sum over z in T of c_z d psi_z / d theta:
+ *   exact = 0:  the log-derivative estimator of Eq. (asymmetric_gradient):
+ *               c_z = 2 ((H_VT psi)_z - E psi_z) / D for z in V, 0 for z in P;
+ *   exact = 1:  the derivative of E_asym itself (dependence through psi_P included):
+ *               c_z = ((H_VT psi)_z + (H_VV psi_V)_z - 2 E psi_z) / D  for z in V,
+ *               c_z = (H_PV psi_V)_z / D                              for z in P.
+ * psi is scaled by exp(-max over T of log|psi|). out = [E, N, D, max log|psi|].
+ * ---------------------------------------------------------------------------------------- */
+int orc_asym_energy_grad(const orc_net* n, const uint64_t* T, int64_t nT, int64_t nV,
+                         const int64_t* row_ptr, const int32_t* col, const double* val,
+                         int exact, double* out, double* grad) {
+    if (nV <= 0 || nT < nV) return ORC_ERR_ARG;
+    double* logabs = (double*)malloc(sizeof(double) * nT);
+    int8_t* sg = (int8_t*)malloc(nT);
+    double* psi = (double*)malloc(sizeof(double) * nT);
+    double* c = (double*)malloc(sizeof(double) * nT);
+    if (!logabs || !sg || !psi || !c) return ORC_ERR_OOM;
+    int status = orc_amplitudes(n, T, nT, logabs, sg);
+    double M = -INFINITY;
+    for (int64_t r = 0; r < nT; ++r)
+        if (sg[r] != 0 && logabs[r] > M) M = logabs[r];
+    for (int64_t r = 0; r < nT; ++r) psi[r] = sg[r] == 0 ? 0.0 : sg[r] * exp(logabs[r] - M);
+    /* row sums: all of row x (H_VT psi), its V columns (H_VV psi_V), P rows without diagonal */
+    double* v_all = (double*)malloc(sizeof(double) * nT);
+    double* v_in = (double*)malloc(sizeof(double) * nT);
+    if (!v_all || !v_in) return ORC_ERR_OOM;
+    for (int64_t r = 0; r < nT; ++r) {
+        double sa = 0.0, si = 0.0;
+        for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+            double t = val[k] * psi[col[k]];
+            if (r >= nV && k == row_ptr[r]) continue; /* the diagonal of a P row */
+            sa += t;
+            if (col[k] < nV) si += t;
+        }
+        v_all[r] = sa;
+        v_in[r] = si;
+    }
+    ksum Nk = {0, 0}, Dk = {0, 0};
+    for (int64_t r = 0; r < nV; ++r) {
+        kadd(&Nk, psi[r] * v_all[r]);
+        kadd(&Dk, psi[r] * psi[r]);
+    }
+    double N = kval(&Nk), D = kval(&Dk), E = N / D;
+    out[0] = E;
+    out[1] = N;
+    out[2] = D;
+    out[3] = M;
+    if (grad) {
+        for (int64_t r = 0; r < nT; ++r) {
+            if (r < nV)
+                c[r] = exact ? (v_all[r] + v_in[r] - 2.0 * E * psi[r]) / D
+                             : 2.0 * (v_all[r] - E * psi[r]) / D;
+            else
+                c[r] = exact ? v_all[r] / D : 0.0;
+        }
+        int st = grad_core(n, T, nT, sg, psi, c, grad);
+        if (st != ORC_OK) return st;
+    }
+    free(logabs);
+    free(sg);
+    free(psi);
+    free(c);
+    free(v_all);
+    free(v_in);
     return status;
 }
 

@@ -59,6 +59,8 @@ def lib():
                                   dp]
         L.orc_proxy_csr.restype = C.c_int
         L.orc_proxy_csr.argtypes = [C.c_int, dp, dp, dp, i64, i64, C.c_int, dp, dp, dp]
+        L.orc_asym_energy_grad.restype = C.c_int
+        L.orc_asym_energy_grad.argtypes = [dp, dp, i64, i64, dp, dp, dp, C.c_int, dp, dp]
         L.orc_num_threads.restype = C.c_int
         L.orc_num_threads.argtypes = []
     return _lib
@@ -314,3 +316,17 @@ def proxy_csr(norb, h, eri, V, P) -> CSR:
     st = L.orc_proxy_csr(norb, _p(h), _p(eri), _p(T), nV, nT, 1, _p(row_ptr), _p(col), _p(val))
     assert st == 0, st
     return CSR(row_ptr, col[:nnz], val[:nnz], 0)
+
+
+def asym_energy_grad(net: Net, V, P, csr: CSR, exact: bool, with_grad: bool = True):
+    """Asymmetric mode on T = [V; P] with the proxy CSR over T: dict(E, N, D, maxlog, grad).
+    exact=False: the log-derivative estimator (Eq. asymmetric_gradient); exact=True: the
+    derivative of E_asym."""
+    T = _u64(np.concatenate([_u64(V).reshape(-1, 2), _u64(P).reshape(-1, 2)]))
+    out = np.zeros(4)
+    grad = np.zeros(net.n_params()) if with_grad else None
+    st = lib().orc_asym_energy_grad(net.ref, _p(T), T.shape[0], len(V), _p(csr.row_ptr),
+                                    _p(csr.col), _p(csr.val), int(exact), _p(out),
+                                    _p(grad) if with_grad else None)
+    assert st >= 0, st
+    return dict(E=out[0], N=out[1], D=out[2], maxlog=out[3], grad=grad)
