@@ -151,6 +151,19 @@ int nqs_csr_free(nqs_csr* csr);
 int nqs_proxy_hamiltonian(nqs_problem* problem, const uint64_t* T, int64_t nV, int64_t nT,
                           const nqs_opts* opts, nqs_csr* out, nqs_stream_t stream);
 
+/* Asymmetric mode, Sec. 2.4.1 (Eqs. asymmetric_energy, asymmetric_gradient), on T = V + P with
+ * csr = nqs_proxy_hamiltonian(T, nV): E_asym = sum_{x in V} p_V(x) E_loc(x) with
+ * E_loc(x) = sum_{y in T} H_xy psi_y / psi_x, i.e. sum_V psi (H_VT psi) / sum_V psi^2.
+ * exact = 0: the log-derivative estimator 2 sum_V p_V(x) (E_loc(x) - E) grad ln|psi(x)| (not
+ * the gradient of E_asym); exact = 1: the gradient of E_asym, which also reaches the amplitudes
+ * of P: sum_{z in T} c_z grad psi_z with c_z = ((H_VT psi)_z + (H_VV psi_V)_z - 2 E psi_z) / D on
+ * V and c_z = (H_PV psi_V)_z / D on P. out: device [4] = {E, N, D, max log|psi| over T}; grad
+ * and psi_out as in nqs_energy_grad (over T). T need not be sorted. Stream-ordered. Errors as
+ * nqs_energy_grad. */
+int nqs_asym_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr,
+                         const uint64_t* T, int64_t nT, int64_t nV, int exact, double* out,
+                         void* grad, double* psi_out, const nqs_opts* opts, nqs_stream_t stream);
+
 /* Amplitudes psi(x) of Eq. backflow_amplitude as log|psi| (device [nS] FP64) and sign (device
  * [nS] int8: +1, -1, or 0 for an exactly singular block, reported as NQS_WARN_SINGULAR).
  * Large sets are evaluated in micro-batches of 2^20 configurations (Sec. 3.3) so that the

@@ -47,6 +47,54 @@ __global__ void k_adjoint_weight(const double* __restrict__ v, const double* __r
         w[i] = __dmul_rn(__dmul_rn(c, __dsub_rn(v[i], __dmul_rn(E, psi[i]))), psi[i]);
 }
 
+// Asymmetric mode on the proxy CSR over T = V + P: per row, the sum over every entry (H_VT psi
+// for rows of V; H_PV psi_V for rows of P, whose leading diagonal is skipped) and the sum over
+// the columns inside V. One warp per row, lanes stride the row, then a shuffle tree.
+__global__ void k_asym_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, const double* __restrict__ x,
+                            int64_t n, int64_t nV, double* __restrict__ v_all,
+                            double* __restrict__ v_in) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        double sa = 0.0, si = 0.0;
+        const int64_t k0 = rp[r] + (r >= nV ? 1 : 0);
+        for (int64_t k = k0 + lane; k < rp[r + 1]; k += 32) {
+            const double t = __dmul_rn(val[k], x[col[k]]);
+            sa = __dadd_rn(sa, t);
+            if (col[k] < nV) si = __dadd_rn(si, t);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(FULL_MASK, sa, o);
+            si += __shfl_xor_sync(FULL_MASK, si, o);
+        }
+        if (lane == 0) {
+            v_all[r] = sa;
+            v_in[r] = si;
+        }
+    }
+}
+
+// w_z = c_z psi~_z with the coefficients of the estimator (exact = 0) or of the exact gradient
+__global__ void k_asym_weight(const double* __restrict__ v_all, const double* __restrict__ v_in,
+                              const double* __restrict__ psi, const double* __restrict__ ev,
+                              int64_t n, int64_t nV, int exact, double* __restrict__ w) {
+    const double E = ev[0], D = ev[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double c;
+        if (i < nV)
+            c = exact ? __ddiv_rn(__dsub_rn(__dadd_rn(v_all[i], v_in[i]),
+                                            __dmul_rn(__dmul_rn(2.0, E), psi[i])),
+                                  D)
+                      : __ddiv_rn(__dmul_rn(2.0, __dsub_rn(v_all[i], __dmul_rn(E, psi[i]))), D);
+        else
+            c = exact ? __ddiv_rn(v_all[i], D) : 0.0;
+        w[i] = __dmul_rn(c, psi[i]);
+    }
+}
+
 static int spmv(const nqs_csr* csr, const double* x, double* y, cudaStream_t s) {
     int64_t n = csr->n_rows;
     {
@@ -181,6 +229,51 @@ extern "C" int nqs_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr* csr,
         NQS_TRY(net_backward(net, sc, dets, f, w, grad, s));
     }
     // with validation on, synchronise and report a timed-out tensor-core wait
+    if (opts && opts->validate) NQS_TRY(check_err_word(p, s));
+    return NQS_OK;
+}
+
+// Asymmetric mode (Sec. 2.4.1, Eqs. asymmetric_energy, asymmetric_gradient) on T = V + P with
+// the proxy CSR over T: E_asym = sum_V psi (H_VT psi) / sum_V psi^2, and the gradient as the
+// log-derivative estimator (exact = 0) or the derivative of E_asym (exact = 1).
+extern "C" int nqs_asym_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr* csr,
+                                    const uint64_t* T, int64_t nT, int64_t nV, int exact,
+                                    double* out, void* grad, double* psi_out,
+                                    const nqs_opts* opts, nqs_stream_t stream) {
+    NQS_TRY(check_common(p, net, T, nT, opts));
+    if (!csr || !out || csr->n_rows != nT || nV <= 0 || nV > nT) return NQS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(p, s);
+    double *logabs, *psi, *v_all, *v_in;
+    int8_t* sign;
+    NQS_TRY(sc.get(&logabs, nT));
+    NQS_TRY(sc.get(&sign, nT));
+    NQS_TRY(sc.get(&v_all, nT));
+    NQS_TRY(sc.get(&v_in, nT));
+    psi = psi_out;
+    if (!psi) NQS_TRY(sc.get(&psi, nT));
+    Fwd f;
+    NQS_TRY(net_forward(net, sc, T, nT, f, grad != nullptr, logabs, sign, s));
+    NQS_TRY(max_f64_masked(p, sc, logabs, sign, nT, out + 3, s));
+    k_scaled_psi<<<grid_for(nT, 256), 256, 0, s>>>(logabs, sign, out + 3, nT, psi);
+    NQS_CK_LAUNCH();
+    {
+        ProfScope prof_(PROF_SPMV, s);
+        k_asym_spmv<<<grid_for(nT * 32, 256, 148 * 64), 256, 0, s>>>(
+            csr->row_ptr, csr->col, csr->val, psi, nT, nV, v_all, v_in);
+    }
+    NQS_CK_LAUNCH();
+    NQS_TRY(kdot2_f64(p, sc, v_all, psi, nV, out + 1, s));  // N and D over V
+    k_energy<<<1, 1, 0, s>>>(out);
+    NQS_CK_LAUNCH();
+    if (grad) {
+        double* w;
+        NQS_TRY(sc.get(&w, nT));
+        k_asym_weight<<<grid_for(nT, 256), 256, 0, s>>>(v_all, v_in, psi, out, nT, nV,
+                                                        exact ? 1 : 0, w);
+        NQS_CK_LAUNCH();
+        NQS_TRY(net_backward(net, sc, T, f, w, grad, s));
+    }
     if (opts && opts->validate) NQS_TRY(check_err_word(p, s));
     return NQS_OK;
 }

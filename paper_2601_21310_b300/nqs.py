@@ -65,6 +65,9 @@ EXPORTS = {
                                       C.c_void_p]),
     "nqs_energy_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_asym_energy_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                       C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]),
     "nqs_pt2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_hb_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
@@ -383,6 +386,23 @@ def energy_grad(problem: Problem, net: Net, csr: CSR, dets: torch.Tensor, with_g
                                  _ptr(out), _ptr(grad) if with_grad else None, _ptr(psi),
                                  C.byref(o), _stream(stream)), "nqs_energy_grad")
     return out, (grad if with_grad else None), psi
+
+
+def asym_energy_grad(problem: Problem, net: Net, csr: CSR, T: torch.Tensor, nV: int,
+                     exact: bool, with_grad=True, o: Opts | None = None, stream=None):
+    """Asymmetric mode over T = [V; P] with the proxy CSR: (out[4] = E, N, D, max log|psi|,
+    grad or None, psi~ over T)."""
+    T = _dets(T)
+    n = T.shape[0]
+    out = torch.empty(4, dtype=torch.float64, device=T.device)
+    grad = torch.empty(net.num_params(), dtype=net.grad_dtype(), device=T.device) \
+        if with_grad else None
+    psi = torch.empty(n, dtype=torch.float64, device=T.device)
+    o = o or opts(precision=net.dtype, validate=0)
+    _check(lib().nqs_asym_energy_grad(problem.handle, net.handle, C.byref(csr.s), _ptr(T), n,
+                                      int(nV), int(exact), _ptr(out), _ptr(grad), _ptr(psi),
+                                      C.byref(o), _stream(stream)), "nqs_asym_energy_grad")
+    return out, grad, psi
 
 
 def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, buckets: int = 1,
