@@ -164,6 +164,18 @@ int nqs_asym_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr,
                          const uint64_t* T, int64_t nT, int64_t nV, int exact, double* out,
                          void* grad, double* psi_out, const nqs_opts* opts, nqs_stream_t stream);
 
+/* Post-hoc diagonalisation diagnostic E_diag = lambda_min(H_VV) (Sec. 3.5 and the Supporting
+ * Information's subspace diagonalisation; Delta_opt = E_var - E_diag): Lanczos on csr (any
+ * symmetric CSR, e.g. from nqs_connections) with full reorthogonalisation on the device, the
+ * lowest eigenvalue of the tridiagonal by bisection. start: device [n] start vector or NULL
+ * (a fixed pseudo-random vector). Stops when the lowest Ritz value changes by at most
+ * tol * max(1, |lambda|) between steps, on an invariant subspace, or after max_iters steps.
+ * *eigval (host) receives the value, *iters_done (host, may be NULL) the steps taken. Holds
+ * (max_iters + 1) * n FP64 of scratch. Synchronises the stream every step. Errors: NQS_ERR_ARG,
+ * NQS_ERR_OOM, NQS_ERR_CUDA. */
+int nqs_lanczos_min(const nqs_csr* csr, int max_iters, double tol, const double* start,
+                    double* eigval, int* iters_done, nqs_stream_t stream);
+
 /* Amplitudes psi(x) of Eq. backflow_amplitude as log|psi| (device [nS] FP64) and sign (device
  * [nS] int8: +1, -1, or 0 for an exactly singular block, reported as NQS_WARN_SINGULAR).
  * Large sets are evaluated in micro-batches of 2^20 configurations (Sec. 3.3) so that the

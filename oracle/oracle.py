@@ -330,3 +330,16 @@ def asym_energy_grad(net: Net, V, P, csr: CSR, exact: bool, with_grad: bool = Tr
                                     _p(grad) if with_grad else None)
     assert st >= 0, st
     return dict(E=out[0], N=out[1], D=out[2], maxlog=out[3], grad=grad)
+
+
+# ------------------------------------------------------------------------------------------
+# post-hoc diagonalisation diagnostic E_diag = lambda_min(H_VV) (Sec. 3.5)
+# ------------------------------------------------------------------------------------------
+def e_diag(csr: CSR) -> float:
+    """Lowest eigenvalue of the CSR matrix: dense eigvalsh up to 4000 rows, else SciPy's
+    implicitly restarted Lanczos (eigsh, smallest algebraic) to 1e-13."""
+    A = csr.to_scipy()
+    if A.shape[0] <= 4000:
+        return float(np.linalg.eigvalsh(A.toarray())[0])
+    import scipy.sparse.linalg as sla
+    return float(sla.eigsh(A, k=1, which="SA", tol=1e-13, return_eigenvectors=False)[0])

@@ -68,6 +68,8 @@ EXPORTS = {
     "nqs_asym_energy_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                                        C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_void_p]),
+    "nqs_lanczos_min": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
     "nqs_pt2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_hb_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
@@ -403,6 +405,17 @@ def asym_energy_grad(problem: Problem, net: Net, csr: CSR, T: torch.Tensor, nV: 
                                       int(nV), int(exact), _ptr(out), _ptr(grad), _ptr(psi),
                                       C.byref(o), _stream(stream)), "nqs_asym_energy_grad")
     return out, grad, psi
+
+
+def lanczos_min(csr: CSR, max_iters: int = 300, tol: float = 1e-13,
+                start: torch.Tensor | None = None, stream=None):
+    """E_diag = lambda_min of the CSR matrix: (eigenvalue, iterations)."""
+    ev = C.c_double(0)
+    it = C.c_int(0)
+    _check(lib().nqs_lanczos_min(C.byref(csr.s), int(max_iters), float(tol),
+                                 _ptr(start.contiguous()) if start is not None else None,
+                                 C.byref(ev), C.byref(it), _stream(stream)), "nqs_lanczos_min")
+    return ev.value, it.value
 
 
 def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, buckets: int = 1,
