@@ -469,12 +469,38 @@ def run_outer_loop(args, N, P, net, dets, psi, dtype, stream, eps_hb=1e-6):
     amp_ms, (laT, _, _) = timed(lambda: N.amplitudes(P, net, T, o=o), reps)
     sel_ms, sel = timed(lambda: N.select(P, T, laT, N.SELECT_TOPK, K=nS, o=o), reps)
     kept_from_P = int((sel["index"] >= nS).sum().item())
+    modes = run_modes(N, P, net, dets, T, nS, o, timed) if T.shape[0] <= MODES_MAX_T else {
+        "skipped": f"|T| = {int(T.shape[0])} > {MODES_MAX_T}: the Proxy/Asymmetric modes hold "
+                   "activations of all of T for the backward"}
     return {"eps_hb": eps_hb, "n_P": int(hb["dets"].shape[0]), "n_T": int(T.shape[0]),
             "hb_pairs_kept": int(hb["n_emitted"]), "hb_candidates_tested": int(hb["n_examined"]),
             "hb_select_ms": hb_ms,
             "hb_candidates_per_s": hb["n_examined"] / (hb_ms * 1e-3),
             "amplitudes_T_ms": amp_ms, "amplitudes_T_dets_per_s": T.shape[0] / (amp_ms * 1e-3),
-            "select_topk_ms": sel_ms, "select_K": nS, "kept_from_P": kept_from_P}
+            "select_topk_ms": sel_ms, "select_K": nS, "kept_from_P": kept_from_P,
+            "modes": modes}
+
+
+MODES_MAX_T = 4 << 20
+
+
+def run_modes(N, P, net, dets, T, nS, o, timed):
+    """The target-set modes of Sec. 2.4.1 on T = S + P and the E_diag diagnostic on S: proxy
+    Hamiltonian build, E_proxy + gradient, E_asym + exact gradient, Lanczos lambda_min(H_SS)."""
+    ph_ms, H = timed(lambda: N.proxy_hamiltonian(P, T, nS, o=o), 3)
+    px_ms, (opx, _, _) = timed(lambda: N.energy_grad(P, net, H, T, o=o), 3)
+    as_ms, (oas, _, _) = timed(lambda: N.asym_energy_grad(P, net, H, T, nS, True, o=o), 3)
+    csr = N.connections(P, dets, o)
+    lz_ms, (lam, iters) = timed(lambda: N.lanczos_min(csr, max_iters=300, tol=1e-12), 1)
+    out, _, _ = N.energy_grad(P, net, csr, dets, o=o, with_grad=False)
+    res = {"proxy_hamiltonian_ms": ph_ms, "proxy_nnz": int(H.nnz),
+           "E_proxy": float(opx[0].item()), "proxy_energy_grad_ms": px_ms,
+           "E_asym": float(oas[0].item()), "asym_exact_grad_ms": as_ms,
+           "E_diag": lam, "lanczos_iters": iters, "lanczos_ms": lz_ms,
+           "delta_opt": float(out[0].item()) - lam}
+    csr.free()
+    H.free()
+    return res
 
 
 def o_pt_buckets(args, p):
