@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--eps-pt2", type=float, default=0.0,
                     help="PT2 screening threshold on psi normalised over S (0: the full "
                          "connected space; the paper's heat-bath value is 1e-6)")
+    ap.add_argument("--no-tensor-probe", action="store_true",
+                    help="skip the tensor-core GEMM probe on the 42-orbital output-layer shape")
     ap.add_argument("--no-outer", action="store_true",
                     help="skip the outer-loop measurement (heat-bath set, amplitudes on T, Top-K)")
     ap.add_argument("--buckets", type=int, default=0,
@@ -392,6 +394,8 @@ def run_nqs(args, ws, rank, local):
                                                   result["fp64_form"]["evals_per_s"])
     if not args.no_outer:
         result["outer_loop"] = run_outer_loop(args, N, P, net, dets, psi, dtype, stream)
+    if not args.no_tensor_probe:
+        result["tensor_roofline"] = run_tensor_probe(N, stream)
     if not args.no_e2e:
         result["e2e"] = run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg,
                                 o_pt, out, grad, psi, stream, ws)
@@ -479,6 +483,33 @@ def run_outer_loop(args, N, P, net, dets, psi, dtype, stream, eps_hb=1e-6):
             "amplitudes_T_ms": amp_ms, "amplitudes_T_dets_per_s": T.shape[0] / (amp_ms * 1e-3),
             "select_topk_ms": sel_ms, "select_K": nS, "kept_from_P": kept_from_P,
             "modes": modes}
+
+
+def run_tensor_probe(N, stream, M=1 << 20, Nn=2016, K=1024, reps=10):
+    """The library's tcgen05 GEMM (nqs_gemm_bf16: bf16 in, FP32 out) on the output-layer shape
+    of the 42-orbital network (|S| = 2^20 rows, 2016 outputs, width 1024), timed with CUDA events
+    on the launching stream after warm-up, against the measured bf16 peaks."""
+    A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+    B = torch.randn(Nn, K, device="cuda").to(torch.bfloat16)
+    for _ in range(3):
+        N.gemm_bf16(A, B)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        N.gemm_bf16(A, B)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    tf = 2.0 * M * Nn * K / (ms * 1e-3) / 1e12
+    peaks, kind = load_peaks()
+    peak = peaks.get("bf16_tflops", 1800.0)
+    del A, B
+    torch.cuda.empty_cache()
+    return {"kernel": "k_gemm_tc", "shape": [M, Nn, K], "bound": "tensor", "ms": ms,
+            "achieved": round(tf, 1), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(tf / peak, 4), "peak_source": kind + " bf16 burst"}
 
 
 MODES_MAX_T = 4 << 20
