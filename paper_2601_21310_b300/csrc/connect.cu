@@ -14,8 +14,58 @@
 #include "prof.cuh"
 
 // Pass 1: count the hits of each row. With bits != nullptr the hit pattern is also stored, one
-// 32-bit ballot word per 32 canonical indices ([nS][ceil(nexc/32)]), so that pass 2 only
-// revisits hits.
+// 32-bit ballot word per 32 canonical indices ([nS][ceil(nexc/32)], written with streaming
+// stores so that it does not push the hash table of S out of L2), so that pass 2 only revisits
+// hits.
+//
+// The probes into the hash table are the bound (random L2/DRAM reads), so each lane handles two
+// indices per round (e and e + 32) and issues both first probes before resolving either. The
+// alpha-beta doubles (most of the connected set) are decoded incrementally: a lane keeps the
+// positions (x_a, y_a, x_b, y_b) of its current index in the occupied/virtual lists and steps
+// them by 32 without dividing.
+struct AbPos {
+    int xa, ya, xb, yb;
+    bool init;
+};
+
+__device__ __forceinline__ void ab_locate(const ProblemDev& P, uint32_t l, AbPos& q) {
+    const uint32_t sB = (uint32_t)P.sB;
+    const uint32_t la = l / sB, lb = l - la * sB;
+    q.xa = (int)(la / (uint32_t)P.ma);
+    q.ya = (int)(la - (uint32_t)q.xa * (uint32_t)P.ma);
+    q.xb = (int)(lb / (uint32_t)P.mb);
+    q.yb = (int)(lb - (uint32_t)q.xb * (uint32_t)P.mb);
+    q.init = true;
+}
+
+__device__ __forceinline__ void ab_advance32(const ProblemDev& P, AbPos& q) {
+    q.yb += 32;
+    while (q.yb >= P.mb) {
+        q.yb -= P.mb;
+        if (++q.xb == P.nb) {
+            q.xb = 0;
+            if (++q.ya == P.ma) {
+                q.ya = 0;
+                ++q.xa;
+            }
+        }
+    }
+}
+
+// the excited det of canonical index e (this lane's next index: e grows by 32 between calls)
+__device__ __forceinline__ void count_key(const ProblemDev& P, const PairTables& T,
+                                          const DetCtx& c, uint64_t A, uint64_t B, uint32_t e,
+                                          uint32_t o4, AbPos& q, uint64_t& a2, uint64_t& b2) {
+    if (e < o4) {
+        decode_key(P, T, c, A, B, e, a2, b2);
+        return;
+    }
+    if (!q.init) ab_locate(P, e - o4, q);
+    else ab_advance32(P, q);
+    a2 = A ^ (1ull << c.occA[q.xa]) ^ (1ull << c.virA[q.ya]);
+    b2 = B ^ (1ull << c.occB[q.xb]) ^ (1ull << c.virB[q.yb]);
+}
+
 __global__ void __launch_bounds__(CONN_THREADS) k_conn_count(ProblemDev P, HashS H,
                                                               const ulonglong2* __restrict__ S,
                                                               int64_t nS, int64_t* rowcnt,
@@ -26,23 +76,56 @@ __global__ void __launch_bounds__(CONN_THREADS) k_conn_count(ProblemDev P, HashS
     const int lane = threadIdx.x & 31;
     const uint32_t nexc = (uint32_t)P.nexc;
     const uint32_t nwords = (nexc + 31) / 32;
+    const uint32_t o4 = (uint32_t)(P.sA + P.sB + P.dAA + P.dBB);
     for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * CONN_WARPS) {
         ulonglong2 x = S[det];
         fill_ctx(P, x.x, x.y, ctx, lane);
         int cnt = 0;
-        for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
-            const uint32_t e = r0 + lane;
-            bool hit = false;
-            if (e < nexc) {
-                uint64_t a2, b2;
-                decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
-                hit = hash_lookup(H, a2, b2) >= 0;
+        AbPos q;
+        q.init = false;
+        for (uint32_t r0 = 0; r0 < nexc; r0 += 64) {
+            const uint32_t e0 = r0 + lane, e1 = e0 + 32;
+            const bool v0 = e0 < nexc, v1 = e1 < nexc;
+            uint64_t a0 = 0, b0 = 0, a1 = 0, b1 = 0, s0 = 0, s1 = 0;
+            ulonglong2 k0 = make_ulonglong2(NQS_EMPTY_WORD, 0), k1 = k0;
+            if (v0) {
+                count_key(P, T, *ctx, x.x, x.y, e0, o4, q, a0, b0);
+                s0 = det_hash(a0, b0) & H.mask;
+                k0 = __ldg(&H.keys[s0]);
             }
-            const unsigned m = __ballot_sync(FULL_MASK, hit);
+            if (v1) {
+                count_key(P, T, *ctx, x.x, x.y, e1, o4, q, a1, b1);
+                s1 = det_hash(a1, b1) & H.mask;
+                k1 = __ldg(&H.keys[s1]);
+            }
+            bool h0 = false, h1 = false;
+            for (uint64_t it = 0; v0 && it <= H.mask; ++it) {
+                if (k0.x == a0 && k0.y == b0) {
+                    h0 = true;
+                    break;
+                }
+                if (k0.x == NQS_EMPTY_WORD) break;
+                s0 = (s0 + 1) & H.mask;
+                k0 = __ldg(&H.keys[s0]);
+            }
+            for (uint64_t it = 0; v1 && it <= H.mask; ++it) {
+                if (k1.x == a1 && k1.y == b1) {
+                    h1 = true;
+                    break;
+                }
+                if (k1.x == NQS_EMPTY_WORD) break;
+                s1 = (s1 + 1) & H.mask;
+                k1 = __ldg(&H.keys[s1]);
+            }
+            const unsigned m0 = __ballot_sync(FULL_MASK, h0);
+            const unsigned m1 = __ballot_sync(FULL_MASK, h1);
             if (lane == 0) {
-                cnt += __popc(m);
-                if (bits) bits[det * nwords + r0 / 32] = m;
+                cnt += __popc(m0) + __popc(m1);
+                if (bits) {
+                    __stcs(&bits[det * nwords + r0 / 32], m0);
+                    if (r0 / 32 + 1 < nwords) __stcs(&bits[det * nwords + r0 / 32 + 1], m1);
+                }
             }
         }
         if (lane == 0) rowcnt[det] = cnt + 1;  // + diagonal
