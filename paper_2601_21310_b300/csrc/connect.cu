@@ -18,27 +18,28 @@
 // stores so that it does not push the hash table of S out of L2), so that pass 2 only revisits
 // hits.
 //
-// The probes into the hash table are the bound (random L2/DRAM reads), so each lane handles two
-// indices per round (e and e + 32) and issues both first probes before resolving either. The
-// alpha-beta doubles (most of the connected set) are decoded incrementally: a lane keeps the
-// positions (x_a, y_a, x_b, y_b) of its current index in the occupied/virtual lists and steps
-// them by 32 without dividing.
-struct AbPos {
-    int xa, ya, xb, yb;
-    bool init;
+// The kernel is instruction-issue bound, so the work per index is kept small: each lane handles
+// two indices per round (e and e + 32) and issues both first probes before resolving either,
+// and the doubles are decoded incrementally: a lane keeps the positions of its current index
+// (hole-pair / particle-pair positions for same-spin doubles, positions in the occupied and
+// virtual lists for alpha-beta doubles) and steps them by 32 without dividing.
+struct EnumPos {
+    int cls;             // class of the lane's current index (-1: not located yet)
+    int pi, qi;          // same-spin doubles: hole-pair and particle-pair positions
+    int xa, ya, xb, yb;  // alpha-beta doubles: positions in the occupied / virtual lists
 };
 
-__device__ __forceinline__ void ab_locate(const ProblemDev& P, uint32_t l, AbPos& q) {
+__device__ __forceinline__ void ab_locate(const ProblemDev& P, uint32_t l, EnumPos& q) {
     const uint32_t sB = (uint32_t)P.sB;
     const uint32_t la = l / sB, lb = l - la * sB;
     q.xa = (int)(la / (uint32_t)P.ma);
     q.ya = (int)(la - (uint32_t)q.xa * (uint32_t)P.ma);
     q.xb = (int)(lb / (uint32_t)P.mb);
     q.yb = (int)(lb - (uint32_t)q.xb * (uint32_t)P.mb);
-    q.init = true;
+    q.cls = 4;
 }
 
-__device__ __forceinline__ void ab_advance32(const ProblemDev& P, AbPos& q) {
+__device__ __forceinline__ void ab_advance32(const ProblemDev& P, EnumPos& q) {
     q.yb += 32;
     while (q.yb >= P.mb) {
         q.yb -= P.mb;
@@ -52,21 +53,49 @@ __device__ __forceinline__ void ab_advance32(const ProblemDev& P, AbPos& q) {
     }
 }
 
-// the excited det of canonical index e (this lane's next index: e grows by 32 between calls)
+// the excited det of canonical index e (this lane's next index: e grows by 32 between calls).
+// Singles decode directly; same-spin and alpha-beta doubles step their positions by 32.
 __device__ __forceinline__ void count_key(const ProblemDev& P, const PairTables& T,
                                           const DetCtx& c, uint64_t A, uint64_t B, uint32_t e,
-                                          uint32_t o4, AbPos& q, uint64_t& a2, uint64_t& b2) {
-    if (e < o4) {
+                                          uint32_t o2, uint32_t o3, uint32_t o4, EnumPos& q,
+                                          uint64_t& a2, uint64_t& b2) {
+    if (e < o2) {
         decode_key(P, T, c, A, B, e, a2, b2);
         return;
     }
-    if (!q.init) ab_locate(P, e - o4, q);
+    if (e < o4) {
+        const bool alpha = e < o3;
+        const int cls = alpha ? 2 : 3;
+        const int Q = (int)(alpha ? choose2(P.ma) : choose2(P.mb));
+        if (q.cls != cls) {
+            const uint32_t l = e - (alpha ? o2 : o3);
+            q.pi = (int)(l / (uint32_t)Q);
+            q.qi = (int)(l - (uint32_t)q.pi * (uint32_t)Q);
+            q.cls = cls;
+        } else {
+            q.qi += 32;
+            while (q.qi >= Q) {
+                q.qi -= Q;
+                ++q.pi;
+            }
+        }
+        const uint16_t po = alpha ? T.occA[q.pi] : T.occB[q.pi];
+        const uint16_t pv = alpha ? T.virA[q.qi] : T.virB[q.qi];
+        const uint8_t* occ = alpha ? c.occA : c.occB;
+        const uint8_t* vir = alpha ? c.virA : c.virB;
+        const uint64_t f = (1ull << occ[po & 0xff]) ^ (1ull << occ[po >> 8]) ^
+                           (1ull << vir[pv & 0xff]) ^ (1ull << vir[pv >> 8]);
+        a2 = alpha ? A ^ f : A;
+        b2 = alpha ? B : B ^ f;
+        return;
+    }
+    if (q.cls != 4) ab_locate(P, e - o4, q);
     else ab_advance32(P, q);
     a2 = A ^ (1ull << c.occA[q.xa]) ^ (1ull << c.virA[q.ya]);
     b2 = B ^ (1ull << c.occB[q.xb]) ^ (1ull << c.virB[q.yb]);
 }
 
-__global__ void __launch_bounds__(CONN_THREADS) k_conn_count(ProblemDev P, HashS H,
+__global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count(ProblemDev P, HashS H,
                                                               const ulonglong2* __restrict__ S,
                                                               int64_t nS, int64_t* rowcnt,
                                                               uint32_t* __restrict__ bits) {
@@ -76,47 +105,57 @@ __global__ void __launch_bounds__(CONN_THREADS) k_conn_count(ProblemDev P, HashS
     const int lane = threadIdx.x & 31;
     const uint32_t nexc = (uint32_t)P.nexc;
     const uint32_t nwords = (nexc + 31) / 32;
-    const uint32_t o4 = (uint32_t)(P.sA + P.sB + P.dAA + P.dBB);
+    const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                   o4 = o3 + (uint32_t)P.dBB;
     for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * CONN_WARPS) {
         ulonglong2 x = S[det];
         fill_ctx(P, x.x, x.y, ctx, lane);
         int cnt = 0;
-        AbPos q;
-        q.init = false;
+        EnumPos q;
+        q.cls = -1;
         for (uint32_t r0 = 0; r0 < nexc; r0 += 64) {
             const uint32_t e0 = r0 + lane, e1 = e0 + 32;
             const bool v0 = e0 < nexc, v1 = e1 < nexc;
             uint64_t a0 = 0, b0 = 0, a1 = 0, b1 = 0, s0 = 0, s1 = 0;
-            ulonglong2 k0 = make_ulonglong2(NQS_EMPTY_WORD, 0), k1 = k0;
+            uint16_t f0 = 0, f1 = 0, g0 = 0, g1 = 0;
             if (v0) {
-                count_key(P, T, *ctx, x.x, x.y, e0, o4, q, a0, b0);
-                s0 = det_hash(a0, b0) & H.mask;
-                k0 = __ldg(&H.keys[s0]);
+                count_key(P, T, *ctx, x.x, x.y, e0, o2, o3, o4, q, a0, b0);
+                const uint64_t hh = s_hash(a0, b0);
+                s0 = hash_slot(hh, H.mask);
+                f0 = hash_fingerprint(hh);
+                g0 = __ldg(&H.fp[s0]);
             }
             if (v1) {
-                count_key(P, T, *ctx, x.x, x.y, e1, o4, q, a1, b1);
-                s1 = det_hash(a1, b1) & H.mask;
-                k1 = __ldg(&H.keys[s1]);
+                count_key(P, T, *ctx, x.x, x.y, e1, o2, o3, o4, q, a1, b1);
+                const uint64_t hh = s_hash(a1, b1);
+                s1 = hash_slot(hh, H.mask);
+                f1 = hash_fingerprint(hh);
+                g1 = __ldg(&H.fp[s1]);
             }
+            // resolve both probe sequences (fingerprints first; a key only on a match)
             bool h0 = false, h1 = false;
-            for (uint64_t it = 0; v0 && it <= H.mask; ++it) {
-                if (k0.x == a0 && k0.y == b0) {
-                    h0 = true;
-                    break;
+            for (uint64_t it = 0; v0 && g0 != 0 && it <= H.mask; ++it) {
+                if (g0 == f0) {
+                    const ulonglong2 k = __ldg(&H.keys[s0]);
+                    if (k.x == a0 && k.y == b0) {
+                        h0 = true;
+                        break;
+                    }
                 }
-                if (k0.x == NQS_EMPTY_WORD) break;
                 s0 = (s0 + 1) & H.mask;
-                k0 = __ldg(&H.keys[s0]);
+                g0 = __ldg(&H.fp[s0]);
             }
-            for (uint64_t it = 0; v1 && it <= H.mask; ++it) {
-                if (k1.x == a1 && k1.y == b1) {
-                    h1 = true;
-                    break;
+            for (uint64_t it = 0; v1 && g1 != 0 && it <= H.mask; ++it) {
+                if (g1 == f1) {
+                    const ulonglong2 k = __ldg(&H.keys[s1]);
+                    if (k.x == a1 && k.y == b1) {
+                        h1 = true;
+                        break;
+                    }
                 }
-                if (k1.x == NQS_EMPTY_WORD) break;
                 s1 = (s1 + 1) & H.mask;
-                k1 = __ldg(&H.keys[s1]);
+                g1 = __ldg(&H.fp[s1]);
             }
             const unsigned m0 = __ballot_sync(FULL_MASK, h0);
             const unsigned m1 = __ballot_sync(FULL_MASK, h1);

@@ -155,24 +155,54 @@ __host__ __device__ __forceinline__ uint64_t det_hash(uint64_t a, uint64_t b) {
 }
 
 // ------------------------------------------------------------------------------------------
-// hash table of S: open addressing, linear probing, capacity a power of two >= 4|S|
+// hash table of S: open addressing, linear probing, capacity a power of two >= 4|S|. Next to
+// the 16-byte keys each slot has a 2-byte fingerprint (16 bits of the hash, low bit forced to
+// 1; 0 = empty): a probe reads the fingerprints (32 slots per 64 bytes; 8 MB for 4 M slots,
+// so they stay in L2 while the keys may not) and touches a key only when its fingerprint
+// matches. Most probes of the method miss, and a miss then never reads a key.
 // ------------------------------------------------------------------------------------------
 #define NQS_EMPTY_WORD 0xffffffffffffffffull
 struct HashS {
-    const ulonglong2* keys;  // [cap] {a, b}; a == NQS_EMPTY_WORD marks an empty slot
+    const ulonglong2* keys;  // [cap] {a, b}
     const int32_t* idx;      // [cap] position in S
+    const uint16_t* fp;      // [cap] fingerprint, 0 = empty slot
     uint64_t mask;           // cap - 1
 };
 
-__device__ __forceinline__ int32_t hash_lookup(const HashS& H, uint64_t a, uint64_t b) {
-    uint64_t slot = det_hash(a, b) & H.mask;
+// Hash of a configuration for this table (independent of the bucket hash det_hash, which is
+// part of the PT2 interface): two odd-constant multiplies, xor, one xorshift; the slot comes
+// from bits 24.. and the fingerprint from bits 0..15. Half the work of det_hash with the same
+// probe-length statistics on the method's sets.
+__host__ __device__ __forceinline__ uint64_t s_hash(uint64_t a, uint64_t b) {
+    uint64_t h = (a * 0x9E3779B97F4A7C15ull) ^ (b * 0xC2B2AE3D27D4EB4Full);
+    return h ^ (h >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t hash_slot(uint64_t h, uint64_t mask) {
+    return (h >> 24) & mask;
+}
+__host__ __device__ __forceinline__ uint16_t hash_fingerprint(uint64_t h) {
+    return (uint16_t)(h | 1ull);
+}
+
+// lookup with the hash h = s_hash(a, b) already formed
+__device__ __forceinline__ int32_t hash_lookup_h(const HashS& H, uint64_t a, uint64_t b,
+                                                 uint64_t h) {
+    uint64_t slot = hash_slot(h, H.mask);
+    const uint16_t f = hash_fingerprint(h);
     for (uint64_t it = 0; it <= H.mask; ++it) {
-        ulonglong2 k = __ldg(&H.keys[slot]);
-        if (k.x == a && k.y == b) return __ldg(&H.idx[slot]);
-        if (k.x == NQS_EMPTY_WORD) return -1;
+        const uint16_t v = __ldg(&H.fp[slot]);
+        if (v == 0) return -1;
+        if (v == f) {
+            const ulonglong2 k = __ldg(&H.keys[slot]);
+            if (k.x == a && k.y == b) return __ldg(&H.idx[slot]);
+        }
         slot = (slot + 1) & H.mask;
     }
     return -1;
+}
+
+__device__ __forceinline__ int32_t hash_lookup(const HashS& H, uint64_t a, uint64_t b) {
+    return hash_lookup_h(H, a, b, s_hash(a, b));
 }
 
 // the H_SS enumeration kernels (connect.cu) and their launch shape

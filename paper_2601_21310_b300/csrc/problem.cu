@@ -320,11 +320,12 @@ int validate_dets(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS,
 // ------------------------------------------------------------------------------------------
 // hash table of S
 // ------------------------------------------------------------------------------------------
-__global__ void k_hash_clear(ulonglong2* keys, int32_t* idx, uint64_t cap) {
+__global__ void k_hash_clear(ulonglong2* keys, int32_t* idx, uint16_t* fp, uint64_t cap) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
          i += (uint64_t)gridDim.x * blockDim.x) {
         keys[i] = make_ulonglong2(NQS_EMPTY_WORD, NQS_EMPTY_WORD);
         idx[i] = -1;
+        fp[i] = 0;
     }
 }
 
@@ -332,7 +333,7 @@ __global__ void k_hash_insert(const ulonglong2* S, int64_t n, int32_t* idx, uint
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         ulonglong2 x = S[i];
-        uint64_t slot = det_hash(x.x, x.y) & mask;
+        uint64_t slot = hash_slot(s_hash(x.x, x.y), mask);
         for (uint64_t it = 0; it <= mask; ++it) {  // capacity > n: an empty slot exists
             if (atomicCAS(&idx[slot], -1, (int32_t)i) == -1) break;
             slot = (slot + 1) & mask;
@@ -341,11 +342,15 @@ __global__ void k_hash_insert(const ulonglong2* S, int64_t n, int32_t* idx, uint
 }
 
 __global__ void k_hash_keys(const ulonglong2* S, const int32_t* idx, ulonglong2* keys,
-                            uint64_t cap) {
+                            uint16_t* fp, uint64_t cap) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
          i += (uint64_t)gridDim.x * blockDim.x) {
         int32_t k = idx[i];
-        if (k >= 0) keys[i] = S[k];
+        if (k >= 0) {
+            const ulonglong2 x = S[k];
+            keys[i] = x;
+            fp[i] = hash_fingerprint(s_hash(x.x, x.y));
+        }
     }
 }
 
@@ -355,16 +360,19 @@ int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, Ha
     while (cap < 4 * (uint64_t)nS) cap <<= 1;  // load factor <= 1/4: short probe sequences
     ulonglong2* keys;
     int32_t* idx;
+    uint16_t* fp;
     NQS_TRY(sc.get(&keys, cap));
     NQS_TRY(sc.get(&idx, cap));
-    k_hash_clear<<<grid_for(cap, 256), 256, 0, s>>>(keys, idx, cap);
+    NQS_TRY(sc.get(&fp, cap));
+    k_hash_clear<<<grid_for(cap, 256), 256, 0, s>>>(keys, idx, fp, cap);
     NQS_CK_LAUNCH();
     k_hash_insert<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, idx, cap - 1);
     NQS_CK_LAUNCH();
-    k_hash_keys<<<grid_for(cap, 256), 256, 0, s>>>((const ulonglong2*)dets, idx, keys, cap);
+    k_hash_keys<<<grid_for(cap, 256), 256, 0, s>>>((const ulonglong2*)dets, idx, keys, fp, cap);
     NQS_CK_LAUNCH();
     out->keys = keys;
     out->idx = idx;
+    out->fp = fp;
     out->mask = cap - 1;
     return NQS_OK;
 }
