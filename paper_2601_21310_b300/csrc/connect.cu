@@ -23,78 +23,6 @@
 // and the doubles are decoded incrementally: a lane keeps the positions of its current index
 // (hole-pair / particle-pair positions for same-spin doubles, positions in the occupied and
 // virtual lists for alpha-beta doubles) and steps them by 32 without dividing.
-struct EnumPos {
-    int cls;             // class of the lane's current index (-1: not located yet)
-    int pi, qi;          // same-spin doubles: hole-pair and particle-pair positions
-    int xa, ya, xb, yb;  // alpha-beta doubles: positions in the occupied / virtual lists
-};
-
-__device__ __forceinline__ void ab_locate(const ProblemDev& P, uint32_t l, EnumPos& q) {
-    const uint32_t sB = (uint32_t)P.sB;
-    const uint32_t la = l / sB, lb = l - la * sB;
-    q.xa = (int)(la / (uint32_t)P.ma);
-    q.ya = (int)(la - (uint32_t)q.xa * (uint32_t)P.ma);
-    q.xb = (int)(lb / (uint32_t)P.mb);
-    q.yb = (int)(lb - (uint32_t)q.xb * (uint32_t)P.mb);
-    q.cls = 4;
-}
-
-__device__ __forceinline__ void ab_advance32(const ProblemDev& P, EnumPos& q) {
-    q.yb += 32;
-    while (q.yb >= P.mb) {
-        q.yb -= P.mb;
-        if (++q.xb == P.nb) {
-            q.xb = 0;
-            if (++q.ya == P.ma) {
-                q.ya = 0;
-                ++q.xa;
-            }
-        }
-    }
-}
-
-// the excited det of canonical index e (this lane's next index: e grows by 32 between calls).
-// Singles decode directly; same-spin and alpha-beta doubles step their positions by 32.
-__device__ __forceinline__ void count_key(const ProblemDev& P, const PairTables& T,
-                                          const DetCtx& c, uint64_t A, uint64_t B, uint32_t e,
-                                          uint32_t o2, uint32_t o3, uint32_t o4, EnumPos& q,
-                                          uint64_t& a2, uint64_t& b2) {
-    if (e < o2) {
-        decode_key(P, T, c, A, B, e, a2, b2);
-        return;
-    }
-    if (e < o4) {
-        const bool alpha = e < o3;
-        const int cls = alpha ? 2 : 3;
-        const int Q = (int)(alpha ? choose2(P.ma) : choose2(P.mb));
-        if (q.cls != cls) {
-            const uint32_t l = e - (alpha ? o2 : o3);
-            q.pi = (int)(l / (uint32_t)Q);
-            q.qi = (int)(l - (uint32_t)q.pi * (uint32_t)Q);
-            q.cls = cls;
-        } else {
-            q.qi += 32;
-            while (q.qi >= Q) {
-                q.qi -= Q;
-                ++q.pi;
-            }
-        }
-        const uint16_t po = alpha ? T.occA[q.pi] : T.occB[q.pi];
-        const uint16_t pv = alpha ? T.virA[q.qi] : T.virB[q.qi];
-        const uint8_t* occ = alpha ? c.occA : c.occB;
-        const uint8_t* vir = alpha ? c.virA : c.virB;
-        const uint64_t f = (1ull << occ[po & 0xff]) ^ (1ull << occ[po >> 8]) ^
-                           (1ull << vir[pv & 0xff]) ^ (1ull << vir[pv >> 8]);
-        a2 = alpha ? A ^ f : A;
-        b2 = alpha ? B : B ^ f;
-        return;
-    }
-    if (q.cls != 4) ab_locate(P, e - o4, q);
-    else ab_advance32(P, q);
-    a2 = A ^ (1ull << c.occA[q.xa]) ^ (1ull << c.virA[q.ya]);
-    b2 = B ^ (1ull << c.occB[q.xb]) ^ (1ull << c.virB[q.yb]);
-}
-
 __global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count(ProblemDev P, HashS H,
                                                               const ulonglong2* __restrict__ S,
                                                               int64_t nS, int64_t* rowcnt,
@@ -120,14 +48,14 @@ __global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count(ProblemDev P, Ha
             uint64_t a0 = 0, b0 = 0, a1 = 0, b1 = 0, s0 = 0, s1 = 0;
             uint16_t f0 = 0, f1 = 0, g0 = 0, g1 = 0;
             if (v0) {
-                count_key(P, T, *ctx, x.x, x.y, e0, o2, o3, o4, q, a0, b0);
+                step_key(P, T, *ctx, x.x, x.y, e0, o2, o3, o4, q, a0, b0);
                 const uint64_t hh = s_hash(a0, b0);
                 s0 = hash_slot(hh, H.mask);
                 f0 = hash_fingerprint(hh);
                 g0 = __ldg(&H.fp[s0]);
             }
             if (v1) {
-                count_key(P, T, *ctx, x.x, x.y, e1, o2, o3, o4, q, a1, b1);
+                step_key(P, T, *ctx, x.x, x.y, e1, o2, o3, o4, q, a1, b1);
                 const uint64_t hh = s_hash(a1, b1);
                 s1 = hash_slot(hh, H.mask);
                 f1 = hash_fingerprint(hh);

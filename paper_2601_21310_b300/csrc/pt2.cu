@@ -45,9 +45,13 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_count(ProblemDev P,
         ulonglong2 x = S[det];
         fill_ctx(P, x.x, x.y, ctx, lane);
         int c = 0;
+        EnumPos q;
+        q.cls = -1;
+        const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                       o4 = o3 + (uint32_t)P.dBB;
         for (uint32_t e = lane; e < nexc; e += 32) {
             uint64_t a2, b2;
-            decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+            step_key(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, a2, b2);
             c += in_bucket(a2, b2, B, bucket);
         }
 #pragma unroll
@@ -71,14 +75,18 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_count_all(ProblemDev P,
                      (threadIdx.x >> 5) * B;
     const int lane = threadIdx.x & 31;
     const uint32_t nexc = (uint32_t)P.nexc;
+    const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                   o4 = o3 + (uint32_t)P.dBB;
     for (int64_t det = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * PT_WARPS) {
         ulonglong2 x = S[det];
         for (uint32_t k = lane; k < B; k += 32) hist[k] = 0;
         fill_ctx(P, x.x, x.y, ctx, lane);  // ends with __syncwarp
+        EnumPos q;
+        q.cls = -1;
         for (uint32_t e = lane; e < nexc; e += 32) {
             uint64_t a2, b2;
-            decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+            step_key(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, a2, b2);
             atomicAdd(&hist[det_hash(a2, b2) % B], 1u);
         }
         __syncwarp();
@@ -131,12 +139,16 @@ __global__ void __launch_bounds__(PT_THREADS, 6) k_pt2_emit(ProblemDev P,
             // and evaluates them together, so the expensive part runs without divergence.
             uint32_t* q = queue + (threadIdx.x >> 5) * 64;
             uint32_t qn = 0;
+            EnumPos pos;
+            pos.cls = -1;
+            const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                           o4 = o3 + (uint32_t)P.dBB;
             for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
                 const uint32_t e = r0 + lane;
                 bool take = false;
                 if (e < nexc) {
                     uint64_t a2, b2;
-                    decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+                    step_key(P, T, *ctx, x.x, x.y, e, o2, o3, o4, pos, a2, b2);
                     take = in_bucket(a2, b2, B, bucket);
                 }
                 const unsigned m = __ballot_sync(FULL_MASK, take);
@@ -352,9 +364,13 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_hss_psi(ProblemDev P, HashS 
         const ulonglong2 x = S[det];
         fill_ctx(P, x.x, x.y, ctx, lane);
         double acc = 0.0;
+        EnumPos q;
+        q.cls = -1;
+        const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                       o4 = o3 + (uint32_t)P.dBB;
         for (uint32_t e = lane; e < nexc; e += 32) {
             uint64_t a2, b2;
-            decode_key(P, T, *ctx, x.x, x.y, e, a2, b2);
+            step_key(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, a2, b2);
             const int32_t hit = hash_lookup(H, a2, b2);
             if (hit >= 0) {
                 Exc ex;
