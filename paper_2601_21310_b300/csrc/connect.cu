@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(CONN_THREADS) k_conn_fill(ProblemDev P, HashS 
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    __shared__ uint32_t queue[CONN_WARPS * 64];
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     const uint32_t nexc = (uint32_t)P.nexc;
@@ -128,26 +129,42 @@ __global__ void __launch_bounds__(CONN_THREADS) k_conn_fill(ProblemDev P, HashS 
         }
         int64_t run = base + 1;
         if (bits) {
+            // The hits of the stored ballot words are appended, in canonical order, to a per-warp
+            // queue; each time it holds 32 the whole warp decodes, probes and evaluates them
+            // together (hits are ~10% of the excitations: one word at a time would leave most
+            // lanes idle).
             const uint32_t* wb = bits + det * nwords;
+            uint32_t* qu = queue + (threadIdx.x >> 5) * 64;
+            uint32_t qn = 0;
+            auto flush = [&](uint32_t nt) {
+                if ((uint32_t)lane < nt) {
+                    Exc ex;
+                    decode_exc(P, T, *ctx, x.x, x.y, qu[lane], ex);
+                    col[run + lane] = hash_lookup(H, ex.a2, ex.b2);
+                    val[run + lane] = exc_element(P, *ctx, ex);
+                }
+                run += nt;
+                const uint32_t rest = qn - nt;
+                const uint32_t moved = (uint32_t)lane < rest ? qu[nt + lane] : 0u;
+                __syncwarp();
+                if ((uint32_t)lane < rest) qu[lane] = moved;
+                qn = rest;
+                __syncwarp();
+            };
             for (uint32_t w0 = 0; w0 < nwords; w0 += 32) {
-                // 32 ballot words at a time; lanes then take the set bits of each word in turn
                 const uint32_t my = (w0 + lane < nwords) ? wb[w0 + lane] : 0u;
                 unsigned nz = __ballot_sync(FULL_MASK, my != 0u);
                 while (nz) {
                     const int src = __ffs(nz) - 1;
                     nz &= nz - 1;
                     const uint32_t m = __shfl_sync(FULL_MASK, my, src);
-                    const bool hit = (m >> lane) & 1u;
-                    if (hit) {
-                        Exc ex;
-                        decode_exc(P, T, *ctx, x.x, x.y, (w0 + src) * 32 + lane, ex);
-                        const int64_t pos = run + __popc(m & lt);
-                        col[pos] = hash_lookup(H, ex.a2, ex.b2);
-                        val[pos] = exc_element(P, *ctx, ex);
-                    }
-                    run += __popc(m);
+                    if ((m >> lane) & 1u) qu[qn + __popc(m & lt)] = (w0 + src) * 32 + lane;
+                    qn += __popc(m);
+                    __syncwarp();
+                    if (qn >= 32) flush(32);
                 }
             }
+            if (qn > 0) flush(qn);
         } else {
             for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
                 uint32_t e = r0 + lane;
