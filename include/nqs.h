@@ -78,7 +78,12 @@ typedef struct {
                            |H_x'y psi_y| >= eps_pt2 (psi as passed to nqs_pt2), so the external
                            sum runs over the screened perturbative set; the internal term stays
                            exact */
-    int reserved[6];
+    int batch_log2;     /* micro-batch of the amplitude and energy paths, 2^batch_log2
+                           configurations (0 = 2^20). Larger sets are evaluated batch by batch,
+                           and their gradient recomputes each batch's activations (Sec. 3.2:
+                           gradients accumulated over fixed-size micro-batches), so activation
+                           memory is bounded by the batch. */
+    int reserved[5];
 } nqs_opts;
 
 /* Library-owned CSR of H_SS (device memory). Row r holds, in order: the diagonal element
@@ -178,7 +183,7 @@ int nqs_lanczos_min(const nqs_csr* csr, int max_iters, double tol, const double*
 
 /* Amplitudes psi(x) of Eq. backflow_amplitude as log|psi| (device [nS] FP64) and sign (device
  * [nS] int8: +1, -1, or 0 for an exactly singular block, reported as NQS_WARN_SINGULAR).
- * Large sets are evaluated in micro-batches of 2^20 configurations (Sec. 3.3) so that the
+ * Large sets are evaluated in micro-batches (opts->batch_log2, default 2^20; Sec. 3.2) so that the
  * activation memory stays bounded; dets need not be sorted. Synchronises the stream. */
 int nqs_amplitudes(nqs_problem* problem, nqs_net* net, const uint64_t* dets, int64_t nS,
                    double* logabs, int8_t* sign, const nqs_opts* opts, nqs_stream_t stream);
@@ -195,8 +200,11 @@ int nqs_energy_from_psi(const nqs_csr* csr, const double* psi, int64_t nS, doubl
  * through a hand-written adjoint (Jacobi's formula with the LU inverse, then the MLP
  * backward). out: device [4] = {E, N, D, max log|psi|}. grad: device, nqs_net_num_params
  * entries laid out W1, b1, W2, b2, W3, b3 (FP64 for NQS_FP64, float for NQS_MIXED), or NULL
- * for the energy only. psi_out: device [nS] FP64 psi~ (may be NULL). Stream-ordered, no sync.
- * csr must come from nqs_connections on the same S. */
+ * for the energy only. psi_out: device [nS] FP64 psi~ (may be NULL). Sets larger than the
+ * micro-batch (opts->batch_log2) are evaluated batch by batch; the gradient then recomputes
+ * each batch's activations and accumulates the batches' gradients (Sec. 3.2), so memory stays
+ * bounded by the batch. Stream-ordered, no sync. csr must come from nqs_connections on the same
+ * S (or nqs_proxy_hamiltonian on a target set). */
 int nqs_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr, const uint64_t* dets,
                     int64_t nS, double* out, void* grad, double* psi_out, const nqs_opts* opts,
                     nqs_stream_t stream);

@@ -168,7 +168,70 @@ static int check_common(nqs_problem* p, nqs_net* net, const uint64_t* dets, int6
     return NQS_OK;
 }
 
-#define NQS_AMP_BATCH ((int64_t)1 << 20)
+__global__ void k_add_f32(float* __restrict__ a, const float* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
+}
+__global__ void k_add_f64(double* __restrict__ a, const double* __restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
+}
+
+// micro-batch size of the amplitude and energy paths: 2^opts->batch_log2 (0: 2^20)
+static int64_t micro_batch(const nqs_opts* opts) {
+    const int lg = (opts && opts->batch_log2 > 0 && opts->batch_log2 < 31) ? opts->batch_log2 : 20;
+    return (int64_t)1 << lg;
+}
+
+// Forward over n configurations. One micro-batch: activations are kept in f for the backward
+// (when keep). More: amplitudes only, batch by batch (the backward recomputes them).
+static int forward_batched(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t n,
+                           int64_t mb, bool keep, Fwd& f, double* logabs, int8_t* sign,
+                           cudaStream_t s) {
+    if (n <= mb) return net_forward(net, sc, dets, n, f, keep, logabs, sign, s);
+    for (int64_t c0 = 0; c0 < n; c0 += mb) {
+        const int64_t m = n - c0 < mb ? n - c0 : mb;
+        Scratch bs(net->prob, s);
+        Fwd fb;
+        NQS_TRY(net_forward(net, bs, dets + 2 * c0, m, fb, false, logabs + c0, sign + c0, s));
+    }
+    return NQS_OK;
+}
+
+// grad = sum over the n configurations of w_x d log|psi_x| / d theta (weights as in
+// net_backward). One micro-batch: from the activations in f. More: per batch, the forward is
+// recomputed with activations kept, the batch's gradient formed and added (Sec. 3.2:
+// gradients accumulated over fixed-size micro-batches, so memory is bounded by the batch).
+static int backward_batched(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t n,
+                            int64_t mb, const Fwd& f, const double* w, void* grad,
+                            cudaStream_t s) {
+    if (n <= mb) return net_backward(net, sc, dets, f, w, grad, s);
+    const int64_t np = nqs_net_num_params(net);
+    const bool mixed = net->dtype == NQS_MIXED;
+    void* part = nullptr;
+    if (mixed) NQS_TRY(sc.get((float**)&part, np));
+    else NQS_TRY(sc.get((double**)&part, np));
+    double* la;
+    int8_t* sg;
+    NQS_TRY(sc.get(&la, mb));
+    NQS_TRY(sc.get(&sg, mb));
+    for (int64_t c0 = 0; c0 < n; c0 += mb) {
+        const int64_t m = n - c0 < mb ? n - c0 : mb;
+        Scratch bs(net->prob, s);
+        Fwd fb;
+        NQS_TRY(net_forward(net, bs, dets + 2 * c0, m, fb, true, la, sg, s));
+        NQS_TRY(net_backward(net, bs, dets + 2 * c0, fb, w + c0, c0 == 0 ? grad : part, s));
+        if (c0 > 0) {
+            if (mixed) k_add_f32<<<grid_for(np, 256), 256, 0, s>>>((float*)grad, (const float*)part, np);
+            else k_add_f64<<<grid_for(np, 256), 256, 0, s>>>((double*)grad, (const double*)part, np);
+            NQS_CK_LAUNCH();
+        }
+    }
+    return NQS_OK;
+}
+
 
 extern "C" int nqs_amplitudes(nqs_problem* p, nqs_net* net, const uint64_t* dets, int64_t nS,
                               double* logabs, int8_t* sign, const nqs_opts* opts,
@@ -183,8 +246,9 @@ extern "C" int nqs_amplitudes(nqs_problem* p, nqs_net* net, const uint64_t* dets
     // micro-batches bound the activation memory for large target sets (Sec. 3.3); each
     // configuration's amplitude is independent of the others, so the batching is invisible
     int sing_any = 0;
-    for (int64_t c0 = 0; c0 < nS; c0 += NQS_AMP_BATCH) {
-        const int64_t m = nS - c0 < NQS_AMP_BATCH ? nS - c0 : NQS_AMP_BATCH;
+    const int64_t mb = micro_batch(opts);
+    for (int64_t c0 = 0; c0 < nS; c0 += mb) {
+        const int64_t m = nS - c0 < mb ? nS - c0 : mb;
         Scratch sc(p, s);
         Fwd f;
         NQS_TRY(net_forward(net, sc, dets + 2 * c0, m, f, false, logabs + c0, sign + c0, s));
@@ -213,7 +277,8 @@ extern "C" int nqs_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr* csr,
     psi = psi_out;
     if (!psi) NQS_TRY(sc.get(&psi, nS));
     Fwd f;
-    NQS_TRY(net_forward(net, sc, dets, nS, f, grad != nullptr, logabs, sign, s));
+    const int64_t mb = micro_batch(opts);
+    NQS_TRY(forward_batched(net, sc, dets, nS, mb, grad != nullptr, f, logabs, sign, s));
     NQS_TRY(max_f64_masked(p, sc, logabs, sign, nS, out + 3, s));
     k_scaled_psi<<<grid_for(nS, 256), 256, 0, s>>>(logabs, sign, out + 3, nS, psi);
     NQS_CK_LAUNCH();
@@ -226,7 +291,7 @@ extern "C" int nqs_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr* csr,
         NQS_TRY(sc.get(&w, nS));
         k_adjoint_weight<<<grid_for(nS, 256), 256, 0, s>>>(v, psi, out, nS, w);
         NQS_CK_LAUNCH();
-        NQS_TRY(net_backward(net, sc, dets, f, w, grad, s));
+        NQS_TRY(backward_batched(net, sc, dets, nS, mb, f, w, grad, s));
     }
     // with validation on, synchronise and report a timed-out tensor-core wait
     if (opts && opts->validate) NQS_TRY(check_err_word(p, s));
@@ -253,7 +318,8 @@ extern "C" int nqs_asym_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr*
     psi = psi_out;
     if (!psi) NQS_TRY(sc.get(&psi, nT));
     Fwd f;
-    NQS_TRY(net_forward(net, sc, T, nT, f, grad != nullptr, logabs, sign, s));
+    const int64_t mb = micro_batch(opts);
+    NQS_TRY(forward_batched(net, sc, T, nT, mb, grad != nullptr, f, logabs, sign, s));
     NQS_TRY(max_f64_masked(p, sc, logabs, sign, nT, out + 3, s));
     k_scaled_psi<<<grid_for(nT, 256), 256, 0, s>>>(logabs, sign, out + 3, nT, psi);
     NQS_CK_LAUNCH();
@@ -272,7 +338,7 @@ extern "C" int nqs_asym_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr*
         k_asym_weight<<<grid_for(nT, 256), 256, 0, s>>>(v_all, v_in, psi, out, nT, nV,
                                                         exact ? 1 : 0, w);
         NQS_CK_LAUNCH();
-        NQS_TRY(net_backward(net, sc, T, f, w, grad, s));
+        NQS_TRY(backward_batched(net, sc, T, nT, mb, f, w, grad, s));
     }
     if (opts && opts->validate) NQS_TRY(check_err_word(p, s));
     return NQS_OK;

@@ -28,7 +28,7 @@ class NQSError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("buckets", C.c_int), ("chunk", C.c_int64),
                 ("validate", C.c_int), ("internal_pt2", C.c_int), ("eps_pt2", C.c_double),
-                ("reserved", C.c_int * 6)]
+                ("batch_log2", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class CSRStruct(C.Structure):
@@ -158,11 +158,12 @@ def _dets(d: torch.Tensor) -> torch.Tensor:
 
 
 def opts(precision=NQS_FP64, buckets=1, chunk=0, validate=1, internal_pt2=1,
-         eps_pt2=0.0) -> Opts:
+         eps_pt2=0.0, batch_log2=0) -> Opts:
     o = Opts()
     lib().nqs_opts_default(C.byref(o))
     o.precision, o.buckets, o.chunk = precision, buckets, chunk
     o.validate, o.internal_pt2, o.eps_pt2 = validate, internal_pt2, eps_pt2
+    o.batch_log2 = batch_log2
     return o
 
 
