@@ -152,7 +152,7 @@ int nqs_csr_free(nqs_csr* csr);
  * in T; symmetric bit for bit. nqs_energy_grad over T with this matrix gives E_proxy
  * (Eq. proxy_energy) and its gradient (Eq. proxy_gradient). Synchronises the stream. Errors:
  * NQS_ERR_ARG, NQS_ERR_UNSORTED / NQS_ERR_POPCOUNT (with validate), NQS_ERR_UNSUPPORTED
- * (nT >= 2^31), NQS_ERR_OOM, NQS_ERR_CUDA. */
+ * (nT >= 2^31, or 2^32 or more nonzeros in the rows of V), NQS_ERR_OOM, NQS_ERR_CUDA. */
 int nqs_proxy_hamiltonian(nqs_problem* problem, const uint64_t* T, int64_t nV, int64_t nT,
                           const nqs_opts* opts, nqs_csr* out, nqs_stream_t stream);
 

@@ -138,6 +138,10 @@ extern "C" int nqs_proxy_hamiltonian(nqs_problem* p, const uint64_t* T, int64_t 
     int64_t nnzV = 0;
     NQS_CK(cudaMemcpyAsync(&nnzV, rpV + nV, sizeof nnzV, cudaMemcpyDeviceToHost, s));
     NQS_CK(cudaStreamSynchronize(s));
+    if (nnzV >= ((int64_t)1 << 32)) {
+        nqs_record_message("nqs_proxy_hamiltonian: 2^32 or more nonzeros in the rows of V");
+        return NQS_ERR_UNSUPPORTED;
+    }
     int32_t* colV;
     double* valV;
     NQS_TRY(sc.get(&colV, nnzV));
