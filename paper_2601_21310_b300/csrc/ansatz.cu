@@ -193,9 +193,9 @@ int gemm_bf16_simt(const GemmArgs& g, bool out_bf16, cudaStream_t s) {
     return NQS_OK;
 }
 
+// mixed-form GEMMs with strided operands (widths that are not multiples of 8, which the
+// tensor-memory-access unit cannot address): BF16 inputs, FP32 accumulation on the CUDA cores
 static int gemm_mixed(const GemmArgs& g, bool out_bf16, cudaStream_t s) {
-    int st = gemm_bf16_tc(g, out_bf16, s);
-    if (st != NQS_ERR_UNSUPPORTED) return st;
     return gemm_bf16_simt(g, out_bf16, s);
 }
 

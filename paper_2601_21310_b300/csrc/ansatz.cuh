@@ -24,8 +24,6 @@ struct GemmArgs {
 // FP32 accumulation, bias/Phi0 float, output bf16 (activations) or float (Phi, gradients).
 int gemm_f64(const GemmArgs& g, cudaStream_t s);
 int gemm_bf16_simt(const GemmArgs& g, bool out_bf16, cudaStream_t s);
-// tcgen05 tensor-core path (gemm_tc.cu): returns NQS_ERR_UNSUPPORTED for shapes it does not take
-int gemm_bf16_tc(const GemmArgs& g, bool out_bf16, cudaStream_t s);
 
 // tcgen05 path (gemm_tc.cu): C[m][n] = epi(sum_k A[m][k] B[n][k]), A [M][lda] and B [N][ldb]
 // bfloat16 with k contiguous (lda, ldb multiples of 8). Optional row-major C (bf16 or float)

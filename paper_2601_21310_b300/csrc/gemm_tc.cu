@@ -763,12 +763,6 @@ int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s) {
     return gemm_tc_run(g, sc, s, best);
 }
 
-int gemm_bf16_tc(const GemmArgs& g, bool out_bf16, cudaStream_t s) {
-    (void)g;
-    (void)out_bf16;
-    (void)s;
-    return NQS_ERR_UNSUPPORTED;  // the mixed path calls gemm_bf16_tcgen05 directly
-}
 
 // ------------------------------------------------------------------------------------------
 // C ABI: plain library GEMM C = A B^T (bf16 in, FP32 out), the same kernel the network uses
