@@ -474,8 +474,8 @@ def run_outer_loop(args, N, P, net, dets, psi, dtype, stream, eps_hb=1e-6):
     sel_ms, sel = timed(lambda: N.select(P, T, laT, N.SELECT_TOPK, K=nS, o=o), reps)
     kept_from_P = int((sel["index"] >= nS).sum().item())
     modes = run_modes(N, P, net, dets, T, nS, o, timed) if T.shape[0] <= MODES_MAX_T else {
-        "skipped": f"|T| = {int(T.shape[0])} > {MODES_MAX_T}: the Proxy/Asymmetric modes hold "
-                   "activations of all of T for the backward"}
+        "skipped": f"|T| = {int(T.shape[0])} > {MODES_MAX_T}: the proxy Hamiltonian over T "
+                   "(rows of S reach most of T) would hold billions of nonzeros"}
     return {"eps_hb": eps_hb, "n_P": int(hb["dets"].shape[0]), "n_T": int(T.shape[0]),
             "hb_pairs_kept": int(hb["n_emitted"]), "hb_candidates_tested": int(hb["n_examined"]),
             "hb_select_ms": hb_ms,
