@@ -145,8 +145,8 @@ int nqs_csr_free(nqs_csr* csr);
 
 /* Proxy-mode Hamiltonian, Eq. (proxy_hamiltonian) of Sec. 2.4.1, on the target set T = V + P:
  * (H~)_xy = H_xy when x or y lies in V, H_xx on the diagonal, 0 between distinct members of P.
- * T: device [nT][2] with T[0..nV) = V and T[nV..nT) = P, each sorted by key (checked with
- * opts->validate) and disjoint. On success *out holds a library-owned CSR over T (free with
+ * T: device [nT][2] with T[0..nV) = V and T[nV..nT) = P, each sorted by key and disjoint
+ * (both checked with opts->validate). On success *out holds a library-owned CSR over T (free with
  * nqs_csr_free): row x of V = [diagonal, then every excitation of x found in T, canonical order];
  * row x of P = [diagonal, then the members of V connected to x, ascending]; columns are positions
  * in T; symmetric bit for bit. nqs_energy_grad over T with this matrix gives E_proxy

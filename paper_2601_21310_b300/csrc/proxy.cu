@@ -44,6 +44,16 @@ __global__ void k_proxy_rowlen(const int64_t* __restrict__ rpV, int64_t nV, cons
         len[r] = r < nV ? rpV[r + 1] - rpV[r] : 1 + (int64_t)cntP[r - nV];
 }
 
+// flag[0] = 1 when a configuration of T does not find itself in the hash table (it occurs twice)
+__global__ void k_proxy_unique(HashS H, const ulonglong2* __restrict__ T, int64_t nT,
+                               int* __restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nT;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const ulonglong2 x = T[i];
+        if (hash_lookup(H, x.x, x.y) != (int32_t)i) atomicOr(flag, 1);
+    }
+}
+
 __global__ void k_i32_to_i64(const int* __restrict__ a, int64_t n, int64_t* __restrict__ b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -115,6 +125,20 @@ extern "C" int nqs_proxy_hamiltonian(nqs_problem* p, const uint64_t* T, int64_t 
     }
     HashS H;
     NQS_TRY(hash_build(p, sc, T, nT, &H, s));
+    if (opts->validate) {  // V and P disjoint: every configuration finds its own position
+        int* flag;
+        NQS_TRY(sc.get(&flag, 1));
+        NQS_CK(cudaMemsetAsync(flag, 0, sizeof(int), s));
+        k_proxy_unique<<<grid_for(nT, 256), 256, 0, s>>>(H, (const ulonglong2*)T, nT, flag);
+        NQS_CK_LAUNCH();
+        int hf = 0;
+        NQS_CK(cudaMemcpyAsync(&hf, flag, sizeof hf, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+        if (hf) {
+            nqs_record_message("nqs_proxy_hamiltonian: a configuration occurs in both V and P");
+            return NQS_ERR_UNSORTED;
+        }
+    }
     const size_t smem = conn_smem_bytes(p->d);
     if (smem > 48 * 1024) {
         NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -101,3 +101,14 @@ def test_proxy_energy_grad_mixed_vs_quantised_oracle():
     assert abs(out[0].item() - ref["E"]) < 1e-6
     g = grad.double().cpu().numpy()
     assert np.linalg.norm(g - ref["grad"]) / np.linalg.norm(ref["grad"]) < 1e-2
+
+
+def test_proxy_rejects_overlapping_sets():
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("tiny_n10")
+    P = problem_for(N, p)
+    V = p.S[:100]
+    Pk = p.S[50:150]  # shares 50 configurations with V
+    with pytest.raises(N.NQSError):
+        N.proxy_hamiltonian(P, to_dev(np.concatenate([V, Pk])), len(V), o=N.opts(validate=1))
