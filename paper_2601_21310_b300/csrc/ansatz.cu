@@ -631,31 +631,40 @@ __device__ __forceinline__ __nv_bfloat16 grad_from_double<__nv_bfloat16>(double 
 }
 
 template <class T, class TG>
-__global__ void k_adjoint(const ulonglong2* __restrict__ dets, int64_t M, int norb, int na,
-                          int nb, const double* __restrict__ w, const T* __restrict__ Ainv_a,
-                          const T* __restrict__ Ainv_b, TG* __restrict__ dPhi, int64_t ldp,
-                          TG* __restrict__ dPhiT, int64_t ldt) {
+__global__ void __launch_bounds__(256) k_adjoint(const ulonglong2* __restrict__ dets, int64_t M,
+                                                 int norb, int na, int nb,
+                                                 const double* __restrict__ w,
+                                                 const T* __restrict__ Ainv_a,
+                                                 const T* __restrict__ Ainv_b,
+                                                 TG* __restrict__ dPhi, int64_t ldp) {
+    // One warp per configuration: its occupied orbitals are listed in shared memory, then the
+    // lanes write dPhi[occ_j][col0 + k] = w * (A^-1)_kj of each spin block, a block row (k
+    // contiguous) per group of lanes. dPhi is zero elsewhere (cleared by the caller). The
+    // product is formed in T (FP32 in the mixed form, whose dPhi is bf16; FP64 otherwise).
+    __shared__ uint8_t occ_s[8][2][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nel = na + nb;
-    const int per = na * na + nb * nb;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < M * per;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t m = t / per;
-        int r = (int)(t - m * per);
-        int spin = r < na * na ? 0 : 1;
-        int n = spin == 0 ? na : nb;
-        if (spin) r -= na * na;
-        int j = r / n, k = r - j * n;  // row j of the block (occupied orbital), column k
-        uint64_t word = spin == 0 ? dets[m].x : dets[m].y;
-        // j-th occupied orbital of word
-        uint64_t v = word;
-        for (int q = 0; q < j; ++q) v &= v - 1;
-        int orb = __ffsll((long long)v) - 1;
-        const T* inv = (spin == 0 ? Ainv_a + m * na * na : Ainv_b + m * nb * nb);
-        double g = w[m] * (double)inv[k * n + j];
-        const int64_t o = (int64_t)orb * nel + (spin == 0 ? 0 : na) + k;
-        const TG gv = grad_from_double<TG>(g);
-        dPhi[m * ldp + o] = gv;
-        if (dPhiT) dPhiT[o * ldt + m] = gv;
+    for (int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; m < M;
+         m += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const ulonglong2 x = dets[m];
+        for (int p = lane; p < norb; p += 32) {
+            const uint64_t below = p == 0 ? 0ull : ((1ull << p) - 1ull);
+            if ((x.x >> p) & 1ull) occ_s[warp][0][__popcll(x.x & below)] = (uint8_t)p;
+            if ((x.y >> p) & 1ull) occ_s[warp][1][__popcll(x.y & below)] = (uint8_t)p;
+        }
+        __syncwarp();
+        const T wm = (T)w[m];
+        for (int spin = 0; spin < 2; ++spin) {
+            const int n = spin == 0 ? na : nb, col0 = spin == 0 ? 0 : na;
+            const T* inv = spin == 0 ? Ainv_a + m * na * na : Ainv_b + m * nb * nb;
+            for (int r = lane; r < n * n; r += 32) {
+                const int j = r / n, k = r - j * n;
+                const T g = wm * inv[k * n + j];
+                dPhi[m * ldp + (int64_t)occ_s[warp][spin][j] * nel + col0 + k] =
+                    grad_from_double<TG>((double)g);
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -716,16 +725,15 @@ int net_backward(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f, 
     NQS_TRY(sc.get((uint8_t**)&dZ2, M * H2 * esz));
     NQS_TRY(sc.get((uint8_t**)&dZ1, M * H1 * esz));
     NQS_CK(cudaMemsetAsync(dPhi, 0, M * nout * esz, s));
-    int64_t per = (int64_t)P.na * P.na + (int64_t)P.nb * P.nb;
     const ulonglong2* D2 = (const ulonglong2*)dets;
     if (mixed)
-        k_adjoint<float, __nv_bfloat16><<<grid_for(M * per, 256, 148 * 64), 256, 0, s>>>(
+        k_adjoint<float, __nv_bfloat16><<<grid_for(M * 32, 256, 148 * 64), 256, 0, s>>>(
             D2, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a, (const float*)f.Ainv_b,
-            (__nv_bfloat16*)dPhi, nout, nullptr, 0);
+            (__nv_bfloat16*)dPhi, nout);
     else
-        k_adjoint<double, double><<<grid_for(M * per, 256, 148 * 64), 256, 0, s>>>(
+        k_adjoint<double, double><<<grid_for(M * 32, 256, 148 * 64), 256, 0, s>>>(
             D2, M, P.norb, P.na, P.nb, w, (const double*)f.Ainv_a, (const double*)f.Ainv_b,
-            (double*)dPhi, nout, nullptr, 0);
+            (double*)dPhi, nout);
     NQS_CK_LAUNCH();
     auto gemm = [&](const GemmArgs& g, bool out_act) -> int {
         return mixed ? gemm_mixed(g, out_act, s) : gemm_f64(g, s);
@@ -847,24 +855,63 @@ __global__ void k_pad_cols_bf16(const __nv_bfloat16* __restrict__ W, int R, int 
     }
 }
 
-// out[r] = sum over the first M entries of row r of X [R][ld] (bf16), FP32, fixed order
-__global__ void k_rowsum_bf16(const __nv_bfloat16* __restrict__ X, int R, int64_t M, int64_t ld,
-                              float* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < R;
-         r += (gridDim.x * blockDim.x) >> 5) {
-        const __nv_bfloat16* row = X + (int64_t)r * ld;
-        float acc = 0.f;
-        for (int64_t m = lane; m < M; m += 32) acc += __bfloat162float(row[m]);
+// out[r] = sum over the first M entries of row r of X [R][ld] (bf16), FP32, fixed order: each
+// block sums one chunk of ROWSUM_CHUNK entries of one row (16-byte loads, a fixed tree), then
+// one thread per row adds the chunk partials in order
+#define ROWSUM_CHUNK 16384
+__global__ void __launch_bounds__(256) k_rowsum_part(const __nv_bfloat16* __restrict__ X, int64_t M,
+                                                     int64_t ld, float* __restrict__ part,
+                                                     int nchunks) {
+    __shared__ float red[8];
+    const int r = blockIdx.y, c = blockIdx.x;
+    const __nv_bfloat16* row = X + (int64_t)r * ld;
+    const int64_t c0 = (int64_t)c * ROWSUM_CHUNK;
+    const int64_t c1 = c0 + ROWSUM_CHUNK < M ? c0 + ROWSUM_CHUNK : M;
+    float acc = 0.f;
+    if ((ld % 8) == 0) {
+        const int64_t v1 = c0 + ((c1 - c0) & ~(int64_t)7);
+        for (int64_t i = c0 + 8 * threadIdx.x; i < v1; i += 8 * 256) {
+            const uint4 pk = *(const uint4*)(row + i);
+            const __nv_bfloat162* h2 = (const __nv_bfloat162*)&pk;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
-        if (lane == 0) out[r] = acc;
+            for (int t = 0; t < 4; ++t) {
+                const float2 f = __bfloat1622float2(h2[t]);
+                acc += f.x + f.y;
+            }
+        }
+        for (int64_t i = v1 + threadIdx.x; i < c1; i += 256) acc += __bfloat162float(row[i]);
+    } else {
+        for (int64_t i = c0 + threadIdx.x; i < c1; i += 256) acc += __bfloat162float(row[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int k = 0; k < 8; ++k) t += red[k];
+        part[(int64_t)r * nchunks + c] = t;
     }
 }
 
-static int rowsum_bf16(const void* X, int R, int64_t M, int64_t ld, float* out, cudaStream_t s) {
-    k_rowsum_bf16<<<grid_for((int64_t)R * 32, 256), 256, 0, s>>>((const __nv_bfloat16*)X, R, M, ld,
-                                                                 out);
+__global__ void k_rowsum_final(const float* __restrict__ part, int R, int nchunks,
+                               float* __restrict__ out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    float t = 0.f;
+    for (int c = 0; c < nchunks; ++c) t += part[(int64_t)r * nchunks + c];
+    out[r] = t;
+}
+
+static int rowsum_bf16(Scratch& sc, const void* X, int R, int64_t M, int64_t ld, float* out,
+                       cudaStream_t s) {
+    const int nchunks = (int)((M + ROWSUM_CHUNK - 1) / ROWSUM_CHUNK);
+    float* part;
+    NQS_TRY(sc.get(&part, (size_t)R * nchunks));
+    k_rowsum_part<<<dim3((unsigned)nchunks, (unsigned)R), 256, 0, s>>>(
+        (const __nv_bfloat16*)X, M, ld, part, nchunks);
+    NQS_CK_LAUNCH();
+    k_rowsum_final<<<(R + 255) / 256, 256, 0, s>>>(part, R, nchunks, out);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }
@@ -993,12 +1040,11 @@ static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, co
     NQS_TRY(sc.get(&dZ2T, (size_t)H2 * ldM));
     NQS_TRY(sc.get(&dZ1T, (size_t)H1 * ldM));
     NQS_CK(cudaMemsetAsync(dPhi, 0, M * ldP * 2, s));
-    NQS_CK(cudaMemsetAsync(dPhiT, 0, (size_t)nout * ldM * 2, s));
-    const int64_t per = (int64_t)P.na * P.na + (int64_t)P.nb * P.nb;
-    k_adjoint<float, __nv_bfloat16><<<grid_for(M * per, 256, 148 * 64), 256, 0, s>>>(
+    k_adjoint<float, __nv_bfloat16><<<grid_for(M * 32, 256, 148 * 64), 256, 0, s>>>(
         (const ulonglong2*)dets, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a,
-        (const float*)f.Ainv_b, dPhi, ldP, dPhiT, ldM);
+        (const float*)f.Ainv_b, dPhi, ldP);
     NQS_CK_LAUNCH();
+    NQS_TRY(transpose_bf16(dPhi, M, nout, ldP, dPhiT, ldM, s));  // [M][nout] -> [nout][ldM]
     NQS_TRY(transpose_bf16(net->p[4], nout, H2, H2, W3T, ldP, s));  // W3 [nout][H2] -> [H2][nout]
     NQS_TRY(transpose_bf16(net->p[2], H2, H1, H1, W2T, H2, s));     // W2 [H2][H1] -> [H1][H2]
     TcGemm g;
@@ -1058,8 +1104,8 @@ static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, co
     NQS_TRY(wgrad(dPhiT, nout, (const __nv_bfloat16*)f.H2T, H2, gW3));
     NQS_TRY(wgrad(dZ2T, H2, (const __nv_bfloat16*)f.H1T, H1, gW2));
     NQS_TRY(wgrad(dZ1T, H1, (const __nv_bfloat16*)f.XT, nin, gW1));
-    NQS_TRY(rowsum_bf16(dPhiT, nout, M, ldM, gb3, s));
-    NQS_TRY(rowsum_bf16(dZ2T, H2, M, ldM, gb2, s));
-    NQS_TRY(rowsum_bf16(dZ1T, H1, M, ldM, gb1, s));
+    NQS_TRY(rowsum_bf16(sc, dPhiT, nout, M, ldM, gb3, s));
+    NQS_TRY(rowsum_bf16(sc, dZ2T, H2, M, ldM, gb2, s));
+    NQS_TRY(rowsum_bf16(sc, dZ1T, H1, M, ldM, gb1, s));
     return NQS_OK;
 }
