@@ -199,9 +199,10 @@ static int gemm_mixed(const GemmArgs& g, bool out_bf16, cudaStream_t s) {
     return gemm_bf16_simt(g, out_bf16, s);
 }
 
-// |det| accumulated as m * 2^e with m in [0.5, 1): one FP64 multiply per pivot and a single
-// log at the end, instead of one FP64 log per pivot (FP64 issues slowly on this part). The
-// split of a positive normal double into mantissa and exponent is done on its bit pattern.
+// |det| accumulated as m * 2^e with m in [0.5, 1): one FP64 multiply per pivot and no log in
+// the factorisation kernels (FP64 issues slowly on this part): they store (m, e) per block and
+// k_combine takes one log per configuration, log(m_a m_b) + (e_a + e_b) ln 2. The split of a
+// positive normal double into mantissa and exponent is done on its bit pattern.
 struct LogDet {
     double m = 1.0;
     int e = 0;
@@ -217,13 +218,12 @@ struct LogDet {
         e += (int)((b >> 52) & 0x7ffull) - 1022;
         m = __longlong_as_double((long long)((b & ~(0x7ffull << 52)) | (1022ull << 52)));
     }
-    __device__ __forceinline__ double log_abs() const { return log(m) + (double)e * M_LN2; }
 };
 
 // ------------------------------------------------------------------------------------------
 // batched LU: one warp per (det, spin block); the block sits in shared memory. Task t covers
-// det t/2, spin t%2; it writes log|det| and the sign of its block to la2/sg2[spin*M + m] and the
-// block inverse to Ainv (if requested). Pivot: largest |a_ik|, lowest row on ties.
+// det t/2, spin t%2; it writes |det| of its block as (mantissa, exponent) to la2/ex2[spin*M + m],
+// the sign to sg2[spin*M + m] and the block inverse to Ainv (if requested). Pivot: largest |a_ik|, lowest row on ties.
 // ------------------------------------------------------------------------------------------
 #define LU_WARPS 4
 
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(LU_WARPS * 32) k_lu(const ulonglong2* __restri
                                                       int64_t M, int norb, int na, int nb,
                                                       const T* __restrict__ Phi,
                                                       double* __restrict__ la2,
+                                                      int* __restrict__ ex2,
                                                       int8_t* __restrict__ sg2, T* Ainv_a,
                                                       T* Ainv_b, int* singular) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -316,7 +317,8 @@ __global__ void __launch_bounds__(LU_WARPS * 32) k_lu(const ulonglong2* __restri
         }
         T* Ainv = spin == 0 ? Ainv_a : Ainv_b;
         if (lane == 0) {
-            la2[spin * M + m] = sing ? -INFINITY : det_acc.log_abs();
+            la2[spin * M + m] = sing ? 0.0 : det_acc.m;
+            ex2[spin * M + m] = sing ? 0 : det_acc.e;
             sg2[spin * M + m] = (int8_t)(sing ? 0 : sgn);
             if (sing && singular) atomicOr(singular, 1);
         }
@@ -348,25 +350,29 @@ __global__ void __launch_bounds__(LU_WARPS * 32) k_lu(const ulonglong2* __restri
     }
 }
 
-__global__ void k_combine(int64_t M, const double* la2, const int8_t* sg2, double* logabs,
-                          int8_t* sign) {
+// log|psi| = log(m_a m_b) + (e_a + e_b) ln 2 from the two blocks' (mantissa, exponent) pairs
+__global__ void k_combine(int64_t M, const double* __restrict__ la2, const int* __restrict__ ex2,
+                          const int8_t* __restrict__ sg2, double* __restrict__ logabs,
+                          int8_t* __restrict__ sign) {
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x) {
         int s = sg2[m] * sg2[M + m];
         sign[m] = (int8_t)s;
-        logabs[m] = s == 0 ? -INFINITY : la2[m] + la2[M + m];
+        logabs[m] = s == 0 ? -INFINITY
+                           : log(la2[m] * la2[M + m]) + (double)(ex2[m] + ex2[M + m]) * M_LN2;
     }
 }
 
 // Small blocks: one thread per (det, spin block), the block in registers (N known at compile
 // time, so every register index is static; the pivot row is swapped with predicated moves).
-// Same partial pivoting as the warp kernel (largest |a_ik|, lowest row on ties), log|det| in
-// FP64, and the inverse solved column by column from the factors.
+// Same partial pivoting as the warp kernel (largest |a_ik|, lowest row on ties), |det| in FP64
+// as (mantissa, exponent), and the inverse solved column by column from the factors.
 template <class T, int N>
 __global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ dets, int64_t M,
                                                 int norb, int nel, int spin,
                                                 const T* __restrict__ Phi,
                                                 double* __restrict__ la_out,
+                                                int* __restrict__ ex_out,
                                                 int8_t* __restrict__ sg_out, T* __restrict__ Ainv,
                                                 int* singular) {
     const int col0 = spin == 0 ? 0 : nel - N;
@@ -428,7 +434,8 @@ __global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ d
                 }
             }
         }
-        la_out[m] = ok ? det_acc.log_abs() : -INFINITY;
+        la_out[m] = ok ? det_acc.m : 0.0;
+        ex_out[m] = ok ? det_acc.e : 0;
         sg_out[m] = (int8_t)(ok ? sgn : 0);
         if (!ok && singular) atomicOr(singular, 1);
         if (Ainv) {
@@ -459,10 +466,10 @@ __global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ d
 
 template <class T, int N>
 static int launch_lu_reg_n(const uint64_t* dets, int64_t M, int norb, int nel, int spin,
-                           const T* Phi, double* la, int8_t* sg, T* Ainv, int* singular,
+                           const T* Phi, double* la, int* ex, int8_t* sg, T* Ainv, int* singular,
                            cudaStream_t s) {
-    k_lu_reg<T, N><<<grid_for(M, 128, 148 * 32), 128, 0, s>>>((const ulonglong2*)dets, M, norb, nel,
-                                                              spin, Phi, la, sg, Ainv, singular);
+    k_lu_reg<T, N><<<grid_for(M, 128, 148 * 32), 128, 0, s>>>(
+        (const ulonglong2*)dets, M, norb, nel, spin, Phi, la, ex, sg, Ainv, singular);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }
@@ -470,7 +477,7 @@ static int launch_lu_reg_n(const uint64_t* dets, int64_t M, int norb, int nel, i
 // dispatch on the block size; returns NQS_ERR_UNSUPPORTED above the register limit
 template <class T>
 static int launch_lu_reg(const uint64_t* dets, int64_t M, int norb, int nel, int spin, int n,
-                         const T* Phi, double* la, int8_t* sg, T* Ainv, int* singular,
+                         const T* Phi, double* la, int* ex, int8_t* sg, T* Ainv, int* singular,
                          cudaStream_t s) {
     const int nmax = sizeof(T) == 8 ? 7 : 12;
     if (n > nmax) return NQS_ERR_UNSUPPORTED;
@@ -478,7 +485,7 @@ static int launch_lu_reg(const uint64_t* dets, int64_t M, int norb, int nel, int
 #define NQS_LU_CASE(K)                                                                     \
     case K:                                                                                \
         return launch_lu_reg_n<T, (K <= (sizeof(T) == 8 ? 7 : 12) ? K : 1)>(               \
-            dets, M, norb, nel, spin, Phi, la, sg, Ainv, singular, s);
+            dets, M, norb, nel, spin, Phi, la, ex, sg, Ainv, singular, s);
         NQS_LU_CASE(1) NQS_LU_CASE(2) NQS_LU_CASE(3) NQS_LU_CASE(4) NQS_LU_CASE(5)
         NQS_LU_CASE(6) NQS_LU_CASE(7) NQS_LU_CASE(8) NQS_LU_CASE(9) NQS_LU_CASE(10)
         NQS_LU_CASE(11) NQS_LU_CASE(12)
@@ -487,18 +494,223 @@ static int launch_lu_reg(const uint64_t* dets, int64_t M, int norb, int nel, int
     }
 }
 
+// Mixed-form blocks of 13..32 rows: one warp per (configuration, spin block), lane i holds row i
+// of the block in registers (N is a template parameter, so every register index is static).
+// Partial pivoting as in the other kernels (largest |a_ik|; on ties the row that would sit
+// lowest after the row exchanges so far, tracked per lane as its current position): a warp
+// max-reduction over |a_ik| of the rows not yet used, then a min-reduction over the positions
+// of the maxima. Rows are not moved; the lane that pivots step k holds row k of U and row k of
+// the multipliers of L. The pivot row reaches the other lanes by shuffles. The factors are then
+// stored in pivot order in shared memory and lane c solves L U x = P e_c for column c of the
+// inverse, reading the factors as 16-byte broadcasts. |det| = product of the pivots, reduced
+// over the lanes in FP64 as mantissa x 2^exponent.
+#define LU_LANE_WARPS 4
+template <int N>
+__global__ void __launch_bounds__(LU_LANE_WARPS * 32) k_lu_lane(
+    const ulonglong2* __restrict__ dets, int64_t M, int norb, int nel, int spin,
+    const float* __restrict__ Phi, double* __restrict__ la_out, int* __restrict__ ex_out,
+    int8_t* __restrict__ sg_out, float* __restrict__ Ainv, int* singular) {
+    constexpr int LD = (N + 3) & ~3;  // factor rows padded to 16 bytes
+    __shared__ __align__(16) float lu_s[LU_LANE_WARPS][N][LD];
+    __shared__ float dinv_s[LU_LANE_WARPS][N];
+    __shared__ uint8_t occ_s[LU_LANE_WARPS][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int col0 = spin == 0 ? 0 : nel - N;
+    const bool vec = ((nel | col0) & 3) == 0 && (N & 3) == 0;
+    float(*LU)[LD] = lu_s[warp];
+    for (int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; m < M;
+         m += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const ulonglong2 x = dets[m];
+        const uint64_t w = spin == 0 ? x.x : x.y;
+        for (int p = lane; p < norb; p += 32) {
+            const uint64_t below = p == 0 ? 0ull : ((1ull << p) - 1ull);
+            if ((w >> p) & 1ull) occ_s[warp][__popcll(w & below)] = (uint8_t)p;
+        }
+        __syncwarp();
+        float r[N];
+        if (lane < N) {
+            const float* row = Phi + m * (int64_t)norb * nel + (int64_t)occ_s[warp][lane] * nel + col0;
+            if (vec) {
+#pragma unroll
+                for (int c = 0; c < N; c += 4) {
+                    const float4 v = *(const float4*)(row + c);
+                    r[c] = v.x;
+                    r[c + 1] = v.y;
+                    r[c + 2] = v.z;
+                    r[c + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < N; ++c) r[c] = row[c];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < N; ++c) r[c] = 0.f;
+        }
+        bool used = lane >= N;
+        int pos = lane, step = 0, sgn = 1;
+        float piv_own = 1.f, dinv_own = 1.f;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            if (!ok) continue;  // warp-uniform
+            const unsigned key = used ? 0u : __float_as_uint(fabsf(r[k]));
+            const unsigned mx = __reduce_max_sync(FULL_MASK, key);
+            if (mx == 0u) {  // no nonzero pivot left: singular block
+                ok = false;
+                continue;
+            }
+            const unsigned cand = key == mx ? (unsigned)pos : 0xffffffffu;
+            const unsigned pmin = __reduce_min_sync(FULL_MASK, cand);
+            const int p = __ffs(__ballot_sync(FULL_MASK, cand == pmin)) - 1;
+            const float piv = __shfl_sync(FULL_MASK, r[k], p);
+            if ((int)pmin != k) {  // the equivalent row exchange of positions k and pmin
+                sgn = -sgn;
+                if (pos == k) pos = (int)pmin;
+            }
+            if (piv < 0.f) sgn = -sgn;
+            const float rp = 1.0f / piv;
+            if (lane == p) {
+                used = true;
+                pos = k;
+                step = k;
+                piv_own = fabsf(piv);
+                dinv_own = rp;
+            }
+#pragma unroll
+            for (int j = 0; j < N; ++j) {  // full range: the guard is static once unrolled
+                if (j > k) {
+                    const float u = __shfl_sync(FULL_MASK, r[j], p);
+                    if (!used) r[j] = fmaf(-(r[k] * rp), u, r[j]);
+                }
+            }
+            if (!used) r[k] *= rp;
+        }
+        // |det| over the lanes: mantissa in [0.5, 1) and exponent of each pivot, a product tree
+        int e_own = 0;
+        const double m_own = lane < N && ok ? (double)frexpf(piv_own, &e_own) : 1.0;
+        double mt = m_own;
+        int et = lane < N && ok ? e_own : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mt *= __shfl_xor_sync(FULL_MASK, mt, o);
+            et += __shfl_xor_sync(FULL_MASK, et, o);
+        }
+        if (lane == 0) {
+            la_out[m] = ok ? mt : 0.0;
+            ex_out[m] = ok ? et : 0;
+            sg_out[m] = (int8_t)(ok ? sgn : 0);
+            if (!ok && singular) atomicOr(singular, 1);
+        }
+        if (Ainv) {
+            float* out = Ainv + m * (int64_t)N * N;
+            if (!ok) {
+                for (int t = lane; t < N * N; t += 32) out[t] = 0.f;
+            } else {
+                if (lane < N) {
+#pragma unroll
+                    for (int c = 0; c < LD; c += 4)
+                        *(float4*)&LU[step][c] = make_float4(r[c], c + 1 < N ? r[c + 1] : 0.f,
+                                                             c + 2 < N ? r[c + 2] : 0.f,
+                                                             c + 3 < N ? r[c + 3] : 0.f);
+                    dinv_s[warp][step] = dinv_own;
+                }
+                __syncwarp();
+                if (lane < N) {
+                    // forward: y = L^{-1} e_step, L unit lower triangular
+                    float y[N];
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                        float v = i == step ? 1.f : 0.f;
+#pragma unroll
+                        for (int c = 0; c < ((i + 3) & ~3); c += 4) {
+                            const float4 l4 = *(const float4*)&LU[i][c];
+                            if (c < i) v = fmaf(-l4.x, y[c], v);
+                            if (c + 1 < i) v = fmaf(-l4.y, y[c + 1], v);
+                            if (c + 2 < i) v = fmaf(-l4.z, y[c + 2], v);
+                            if (c + 3 < i) v = fmaf(-l4.w, y[c + 3], v);
+                        }
+                        y[i] = v;
+                    }
+                    // backward: x = U^{-1} y
+#pragma unroll
+                    for (int i = N - 1; i >= 0; --i) {
+                        float v = y[i];
+#pragma unroll
+                        for (int c = (i + 1) & ~3; c < N; c += 4) {
+                            const float4 u4 = *(const float4*)&LU[i][c];
+                            if (c > i) v = fmaf(-u4.x, y[c], v);
+                            if (c + 1 > i && c + 1 < N) v = fmaf(-u4.y, y[c + 1], v);
+                            if (c + 2 > i && c + 2 < N) v = fmaf(-u4.z, y[c + 2], v);
+                            if (c + 3 > i && c + 3 < N) v = fmaf(-u4.w, y[c + 3], v);
+                        }
+                        y[i] = v * dinv_s[warp][i];
+                    }
+#pragma unroll
+                    for (int i = 0; i < N; ++i) out[i * N + lane] = y[i];
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int N>
+static int launch_lu_lane_n(const uint64_t* dets, int64_t M, int norb, int nel, int spin,
+                            const float* Phi, double* la, int* ex, int8_t* sg, float* Ainv,
+                            int* singular, cudaStream_t s) {
+    k_lu_lane<N><<<grid_for(M * 32, LU_LANE_WARPS * 32, 148 * 32), LU_LANE_WARPS * 32, 0, s>>>(
+        (const ulonglong2*)dets, M, norb, nel, spin, Phi, la, ex, sg, Ainv, singular);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+static int launch_lu_lane(const uint64_t* dets, int64_t M, int norb, int nel, int spin, int n,
+                          const float* Phi, double* la, int* ex, int8_t* sg, float* Ainv,
+                          int* singular, cudaStream_t s) {
+    switch (n) {
+#define NQS_LANE_CASE(K)                                                                      \
+    case K:                                                                                   \
+        return launch_lu_lane_n<K>(dets, M, norb, nel, spin, Phi, la, ex, sg, Ainv, singular, s);
+        NQS_LANE_CASE(13) NQS_LANE_CASE(14) NQS_LANE_CASE(15) NQS_LANE_CASE(16)
+        NQS_LANE_CASE(17) NQS_LANE_CASE(18) NQS_LANE_CASE(19) NQS_LANE_CASE(20)
+        NQS_LANE_CASE(21) NQS_LANE_CASE(22) NQS_LANE_CASE(23) NQS_LANE_CASE(24)
+        NQS_LANE_CASE(25) NQS_LANE_CASE(26) NQS_LANE_CASE(27) NQS_LANE_CASE(28)
+        NQS_LANE_CASE(29) NQS_LANE_CASE(30) NQS_LANE_CASE(31) NQS_LANE_CASE(32)
+#undef NQS_LANE_CASE
+        default: return NQS_ERR_UNSUPPORTED;
+    }
+}
+
 template <class T>
 static int launch_lu(nqs_net* net, const uint64_t* dets, int64_t M, const T* Phi, double* la2,
-                     int8_t* sg2, T* Ainv_a, T* Ainv_b, int* singular, cudaStream_t s) {
+                     int* ex2, int8_t* sg2, T* Ainv_a, T* Ainv_b, int* singular,
+                     cudaStream_t s) {
     const ProblemDev& P = net->prob->d;
+    const int nel = P.na + P.nb;
     if (P.na <= (sizeof(T) == 8 ? 7 : 12) && P.nb <= (sizeof(T) == 8 ? 7 : 12)) {
-        const int nel = P.na + P.nb;
         ProfScope prof_(PROF_LU, s);
-        NQS_TRY(launch_lu_reg<T>(dets, M, P.norb, nel, 0, P.na, Phi, la2, sg2, Ainv_a, singular,
-                                 s));
-        NQS_TRY(launch_lu_reg<T>(dets, M, P.norb, nel, 1, P.nb, Phi, la2 + M, sg2 + M, Ainv_b,
+        NQS_TRY(launch_lu_reg<T>(dets, M, P.norb, nel, 0, P.na, Phi, la2, ex2, sg2, Ainv_a,
                                  singular, s));
+        NQS_TRY(launch_lu_reg<T>(dets, M, P.norb, nel, 1, P.nb, Phi, la2 + M, ex2 + M, sg2 + M,
+                                 Ainv_b, singular, s));
         return NQS_OK;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (P.na <= 32 && P.nb <= 32) {  // FP32: register kernels per block
+            ProfScope prof_(PROF_LU, s);
+            for (int spin = 0; spin < 2; ++spin) {
+                const int n = spin == 0 ? P.na : P.nb;
+                T* inv = spin == 0 ? Ainv_a : Ainv_b;
+                if (n <= 12)
+                    NQS_TRY(launch_lu_reg<T>(dets, M, P.norb, nel, spin, n, Phi, la2 + spin * M,
+                                             ex2 + spin * M, sg2 + spin * M, inv, singular, s));
+                else
+                    NQS_TRY(launch_lu_lane(dets, M, P.norb, nel, spin, n, Phi, la2 + spin * M,
+                                           ex2 + spin * M, sg2 + spin * M, inv, singular, s));
+            }
+            return NQS_OK;
+        }
     }
     int nmax = P.na > P.nb ? P.na : P.nb;
     size_t smem = (size_t)LU_WARPS * 2 * nmax * (nmax + 1) * sizeof(T);
@@ -509,7 +721,7 @@ static int launch_lu(nqs_net* net, const uint64_t* dets, int64_t M, const T* Phi
     {
         ProfScope prof_(PROF_LU, s);
         k_lu<T><<<grid, LU_WARPS * 32, smem, s>>>((const ulonglong2*)dets, M, P.norb, P.na, P.nb, Phi,
-                                                  la2, sg2, Ainv_a, Ainv_b, singular);
+                                                  la2, ex2, sg2, Ainv_a, Ainv_b, singular);
     }
     NQS_CK_LAUNCH();
     return NQS_OK;
@@ -600,16 +812,18 @@ int net_forward(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t M, Fwd&
     g.aux = net->p[6];
     NQS_TRY(mixed ? gemm_mixed(g, false, s) : gemm_f64(g, s));
     double* la2;
+    int* ex2;
     int8_t* sg2;
     NQS_TRY(sc.get(&la2, 2 * M));
+    NQS_TRY(sc.get(&ex2, 2 * M));
     NQS_TRY(sc.get(&sg2, 2 * M));
     if (mixed)
-        NQS_TRY(launch_lu<float>(net, dets, M, (const float*)f.Phi, la2, sg2, (float*)f.Ainv_a,
-                                 (float*)f.Ainv_b, f.singular, s));
+        NQS_TRY(launch_lu<float>(net, dets, M, (const float*)f.Phi, la2, ex2, sg2,
+                                 (float*)f.Ainv_a, (float*)f.Ainv_b, f.singular, s));
     else
-        NQS_TRY(launch_lu<double>(net, dets, M, (const double*)f.Phi, la2, sg2,
+        NQS_TRY(launch_lu<double>(net, dets, M, (const double*)f.Phi, la2, ex2, sg2,
                                   (double*)f.Ainv_a, (double*)f.Ainv_b, f.singular, s));
-    k_combine<<<grid_for(M, 256), 256, 0, s>>>(M, la2, sg2, logabs, sign);
+    k_combine<<<grid_for(M, 256), 256, 0, s>>>(M, la2, ex2, sg2, logabs, sign);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }
@@ -1008,12 +1222,14 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
     g.ldc = nout;
     NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
     double* la2;
+    int* ex2;
     int8_t* sg2;
     NQS_TRY(sc.get(&la2, 2 * M));
+    NQS_TRY(sc.get(&ex2, 2 * M));
     NQS_TRY(sc.get(&sg2, 2 * M));
-    NQS_TRY(launch_lu<float>(net, dets, M, (const float*)f.Phi, la2, sg2, (float*)f.Ainv_a,
-                             (float*)f.Ainv_b, f.singular, s));
-    k_combine<<<grid_for(M, 256), 256, 0, s>>>(M, la2, sg2, logabs, sign);
+    NQS_TRY(launch_lu<float>(net, dets, M, (const float*)f.Phi, la2, ex2, sg2,
+                             (float*)f.Ainv_a, (float*)f.Ainv_b, f.singular, s));
+    k_combine<<<grid_for(M, 256), 256, 0, s>>>(M, la2, ex2, sg2, logabs, sign);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }

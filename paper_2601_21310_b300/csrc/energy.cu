@@ -10,15 +10,32 @@
 #include "nqs_internal.cuh"
 #include "prof.cuh"
 
-// one warp per row, FP64 (lanes stride the row, then a shuffle tree)
-__global__ void k_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                       const double* __restrict__ val, const double* __restrict__ x, int64_t n,
-                       double* __restrict__ y) {
+// y = H x, one warp per row, FP64. Lanes stride the row with four independent partial sums
+// (the loads of four strides in flight per lane: the gathers x[col] are dependent loads), which
+// are added in a fixed order and then reduced by a shuffle tree: the result is deterministic.
+__global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rp,
+                                              const int32_t* __restrict__ col,
+                                              const double* __restrict__ val,
+                                              const double* __restrict__ x, int64_t n,
+                                              double* __restrict__ y) {
     const int lane = threadIdx.x & 31;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        double s = 0.0;
-        for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s = fma(val[k], x[col[k]], s);
+        const int64_t k1 = rp[r + 1];
+        int64_t k = rp[r] + lane;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (; k + 96 < k1; k += 128) {
+            const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + 32), c2 = __ldg(col + k + 64),
+                          c3 = __ldg(col + k + 96);
+            const double v0 = __ldg(val + k), v1 = __ldg(val + k + 32), v2 = __ldg(val + k + 64),
+                         v3 = __ldg(val + k + 96);
+            s0 = fma(v0, __ldg(x + c0), s0);
+            s1 = fma(v1, __ldg(x + c1), s1);
+            s2 = fma(v2, __ldg(x + c2), s2);
+            s3 = fma(v3, __ldg(x + c3), s3);
+        }
+        for (; k < k1; k += 32) s0 = fma(__ldg(val + k), __ldg(x + __ldg(col + k)), s0);
+        double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
         if (lane == 0) y[r] = s;
@@ -95,7 +112,7 @@ __global__ void k_asym_weight(const double* __restrict__ v_all, const double* __
     }
 }
 
-static int spmv(const nqs_csr* csr, const double* x, double* y, cudaStream_t s) {
+int csr_spmv(const nqs_csr* csr, const double* x, double* y, cudaStream_t s) {
     int64_t n = csr->n_rows;
     {
         ProfScope prof_(PROF_SPMV, s);
@@ -119,7 +136,7 @@ extern "C" int nqs_energy_from_psi(const nqs_csr* csr, const double* psi, int64_
     Scratch sc(&host, s);
     double* vv = v;
     if (!vv) NQS_TRY(sc.get(&vv, nS));
-    NQS_TRY(spmv(csr, psi, vv, s));
+    NQS_TRY(csr_spmv(csr, psi, vv, s));
     NQS_TRY(kdot2_f64(&host, sc, vv, psi, nS, out + 1, s));
     k_energy<<<1, 1, 0, s>>>(out);
     NQS_CK_LAUNCH();
@@ -282,7 +299,7 @@ extern "C" int nqs_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr* csr,
     NQS_TRY(max_f64_masked(p, sc, logabs, sign, nS, out + 3, s));
     k_scaled_psi<<<grid_for(nS, 256), 256, 0, s>>>(logabs, sign, out + 3, nS, psi);
     NQS_CK_LAUNCH();
-    NQS_TRY(spmv(csr, psi, v, s));
+    NQS_TRY(csr_spmv(csr, psi, v, s));
     NQS_TRY(kdot2_f64(p, sc, v, psi, nS, out + 1, s));
     k_energy<<<1, 1, 0, s>>>(out);
     NQS_CK_LAUNCH();

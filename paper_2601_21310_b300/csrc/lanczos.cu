@@ -3,7 +3,7 @@
 // reorthogonalisation (classical Gram-Schmidt, applied twice per step) on the device, and the
 // lowest eigenvalue of the Lanczos tridiagonal matrix by Sturm-sequence bisection on the host.
 //
-// Per step: w = H q_j (warp-per-row SpMV); alpha_j = q_j . w; w -= Q^T (Q w) twice over all
+// Per step: w = H q_j (the library's warp-per-row SpMV); alpha_j = q_j . w; w -= Q^T (Q w) twice over all
 // basis vectors so far (the first pass also removes alpha_j q_j and beta_{j-1} q_{j-1});
 // beta_j = |w|; q_{j+1} = w / beta_j. Dot products use the library's fixed-order compensated
 // reductions, so a run is deterministic. The basis is kept: iters x n FP64.
@@ -15,20 +15,6 @@
 #include "excite.cuh"
 #include "nqs_internal.cuh"
 #include "prof.cuh"
-
-__global__ void k_lz_spmv(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                          const double* __restrict__ val, const double* __restrict__ x, int64_t n,
-                          double* __restrict__ y) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n;
-         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        double s = 0.0;
-        for (int64_t k = rp[r] + lane; k < rp[r + 1]; k += 32) s = fma(val[k], x[col[k]], s);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
-        if (lane == 0) y[r] = s;
-    }
-}
 
 // h[i] = Q[i] . w for i < m: one CTA per basis vector, fixed-order block reduction
 __global__ void __launch_bounds__(256) k_lz_proj(const double* __restrict__ Q, int64_t n, int m,
@@ -136,12 +122,7 @@ extern "C" int nqs_lanczos_min(const nqs_csr* csr, int max_iters, double tol, co
     int m = 0;
     for (m = 0; m < m_max; ++m) {
         double* q = Q + (size_t)m * n;
-        {
-            ProfScope prof_(PROF_SPMV, s);
-            k_lz_spmv<<<grid_for(n * 32, 256, 148 * 64), 256, 0, s>>>(csr->row_ptr, csr->col,
-                                                                      csr->val, q, n, w);
-        }
-        NQS_CK_LAUNCH();
+        NQS_TRY(csr_spmv(csr, q, w, s));
         Scratch st(&host, s);  // per-step reduction scratch
         NQS_TRY(kdot2_f64(&host, st, q, w, n, dots, s));  // dots[0] = alpha_m
         double hd[2];

@@ -293,6 +293,8 @@ int scan_exclusive_u32(nqs_problem* p, Scratch& sc, const uint32_t* in, uint32_t
 // the same for FP64 in a fixed tile order (deterministic; rounding differs from a serial sum)
 int scan_exclusive_f64(nqs_problem* p, Scratch& sc, const double* in, double* out, int64_t n,
                        double* total, cudaStream_t s);
+// y = H x for a device CSR (one warp per row, fixed summation order)
+int csr_spmv(const nqs_csr* csr, const double* x, double* y, cudaStream_t s);
 // compensated (Neumaier) sum of n FP64 values into *out (device); deterministic
 int ksum_f64(nqs_problem* p, Scratch& sc, const double* x, int64_t n, double* out,
              cudaStream_t s);

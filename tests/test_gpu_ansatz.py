@@ -177,3 +177,54 @@ def test_micro_batched_gradient_recomputation(mixed):
     assert ob[0].item() == o1[0].item()
     rel = (torch.linalg.norm(gb.double() - g1.double()) / torch.linalg.norm(g1.double())).item()
     assert rel < (1e-5 if mixed else 1e-12), rel
+
+
+@pytest.mark.parametrize("norb,n", [(18, 13), (20, 16), (26, 24)])
+def test_mixed_blocks_of_13_to_32_rows_vs_quantised_oracle(norb, n):
+    """Spin blocks of 13..32 rows in the mixed form (the FP32 LU with one lane per row, scalar
+    loads at 13 rows, 16-byte loads at 16 and 24): amplitudes, E_S and the gradient, which goes
+    through the block inverses, against the quantisation-matched oracle."""
+    need_gpu()
+    N = nqs()
+    p, _ = small_problem(norb, n, 400, 70 + norb, hidden=(64, 64))
+    P = N.Problem(norb, n, n, p.h, p.eri)
+    net = N.Net(P, N.net_tensors(p.net, N.NQS_MIXED), N.NQS_MIXED)
+    dets = to_dev(p.S)
+    la, sg, _ = N.amplitudes(P, net, dets)
+    onet = O.Net(p.net, quant=True)
+    rla, rsg = O.amplitudes(onet, p.S)
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    M = rla.max()
+    assert np.abs(sg * np.exp(la - M) - rsg * np.exp(rla - M)).max() < 2e-5
+    csr = N.connections(P, dets)
+    out, grad, _ = N.energy_grad(P, net, csr, dets)
+    ref = O.energy_grad(onet, p.S, O.hss(norb, p.h, p.eri, p.S))
+    assert abs(out[0].item() - ref["E"]) < 1e-6
+    g = grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - ref["grad"]) / np.linalg.norm(ref["grad"]) < 1e-2
+
+
+def test_mixed_singular_blocks_of_24_rows():
+    """Output layer zero: Phi = Phi0 (identity columns), so every configuration other than the
+    reference has a singular block. Those get sign 0 and log|psi| = -inf, the reference gets
+    psi = 1, E_S = H_00 and the gradient stays finite."""
+    need_gpu()
+    N = nqs()
+    norb, n = 30, 24
+    h, eri, _ = synth.integrals(norb, 2 * norb, 9, 3.0)
+    S = synth.select_S(norb, n, 300)
+    netp = synth.net_params(norb, n, n, (64, 64), 9, out_scale=0.0)
+    P = N.Problem(norb, n, n, h, eri)
+    net = N.Net(P, N.net_tensors(netp, N.NQS_MIXED), N.NQS_MIXED)
+    dets = to_dev(S)
+    la, sg, _ = N.amplitudes(P, net, dets)
+    la, sg = la.cpu().numpy(), sg.cpu().numpy()
+    hf = (S[:, 0] == (1 << n) - 1) & (S[:, 1] == (1 << n) - 1)
+    assert hf.sum() == 1
+    assert sg[hf][0] == 1 and abs(la[hf][0]) < 1e-12
+    assert np.all(sg[~hf] == 0) and np.all(np.isneginf(la[~hf]))
+    csr = N.connections(P, dets)
+    out, grad, _ = N.energy_grad(P, net, csr, dets)
+    H00 = O.hss_rows(norb, h, eri, S, int(np.argmax(hf)), int(np.argmax(hf)) + 1)[2][0]
+    assert abs(out[0].item() - H00) < 1e-10 * abs(H00)
+    assert bool(torch.isfinite(grad).all())
