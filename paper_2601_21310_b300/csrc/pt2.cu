@@ -5,9 +5,10 @@
 //      in canonical order (y ascending, then canonical excitation index) - with B = 1 the
 //      position of every emission is fixed, otherwise a count pass and a scan give them;
 //   2. stable LSD radix sort by key (2 norb bits), so equal keys stay in emission order;
-//   3. mark run heads and scan them (run index of every element); each warp then sums the
-//      runs that start in its chunk with a segmented warp scan (carrying the open run across
-//      iterations) -> c(x') for every unique x'; a per-unique pass sends members of S to the
+//   3. count the run heads per chunk and scan the counts (each chunk's first run index); each
+//      warp then sums the runs that start in its chunk, lane by lane along runs, carrying the
+//      open run across lanes and steps -> c(x') for every unique x'; a per-unique pass sends
+//      members of S to the
 //      internal term (c(x) is the off-diagonal part of (H_SS psi)_x) and turns the others into
 //      c^2 / (D (E - H_x'x')) with H_x'x' from the Slater-Condon diagonal;
 //   4. compensated sums of the external terms, and of the internal terms of the dets of S in
@@ -187,27 +188,92 @@ __global__ void __launch_bounds__(PT_THREADS, 6) k_pt2_emit(ProblemDev P,
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Run reduction over the sorted (key, value) pairs. The pairs are cut into chunks of SEG_CHUNK;
+// a chunk owns the runs of equal keys whose first element (head) lies in it.
+//   k_seg_heads  number of heads per chunk (an exclusive scan gives each chunk's first run
+//                index and the total number of unique keys);
+//   k_seg_sum    one warp per chunk: from the chunk's first head to the first head at or past
+//                the chunk's end, 32 x SEG_ITEMS elements per step (16-byte loads, SEG_ITEMS
+//                consecutive elements per lane). Each lane adds its elements along runs (one FP64
+//                add per element); the open run at each lane's end is passed to the next lane (a
+//                segmented shuffle scan only when some lane holds no head) and, across steps, to
+//                lane 0. The last element of a run writes the run's sum and key at the run index.
+// Sums go in element order within a lane and lane order across lanes: deterministic.
+// ------------------------------------------------------------------------------------------
+#define SEG_CHUNK 2048
+#define SEG_ITEMS 8
+
+// SEG_ITEMS consecutive keys from i0 (a multiple of SEG_ITEMS); past `end` reads key zero
 template <class K>
-__global__ void k_heads(const K* __restrict__ keys, int64_t n, uint32_t* __restrict__ f) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        f[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+__device__ __forceinline__ void seg_load_keys(const K* __restrict__ keys, int64_t i0, int64_t end,
+                                              K (&kk)[SEG_ITEMS]) {
+    if (i0 + SEG_ITEMS <= end) {  // SEG_ITEMS * sizeof(K) is a multiple of 16 bytes
+        constexpr int NV = SEG_ITEMS * (int)sizeof(K) / 16;
+        uint4 t[NV];
+        const uint4* src = reinterpret_cast<const uint4*>(keys + i0);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) t[q] = __ldg(src + q);
+        memcpy(kk, t, sizeof(t));
+    } else {
+#pragma unroll
+        for (int j = 0; j < SEG_ITEMS; ++j) kk[j] = i0 + j < end ? keys[i0 + j] : key_zero<K>();
+    }
 }
 
-// Segmented sums of the sorted values. Warp chunk [c0, c1) owns the runs whose head lies in
-// it: it skips the tail of the previous chunk's last run and finishes its own last run past c1.
-// Within 32 consecutive elements a shuffle scan adds along runs (earlier elements first); the
-// open run is carried to the next 32. The last element of a run writes c and the run's key at
-// the run index (exclusive head count pos[] plus its own head flag, minus one).
-#define SEG_CHUNK 2048
-#define SEG_ITEMS 4
+__device__ __forceinline__ void seg_load_vals(const double* __restrict__ vals, int64_t i0,
+                                              int64_t end, double (&v)[SEG_ITEMS]) {
+    if (i0 + SEG_ITEMS <= end) {
+        const double2* src = reinterpret_cast<const double2*>(vals + i0);
+#pragma unroll
+        for (int q = 0; q < SEG_ITEMS / 2; ++q) {
+            const double2 t = __ldg(src + q);
+            v[2 * q] = t.x;
+            v[2 * q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < SEG_ITEMS; ++j) v[j] = i0 + j < end ? vals[i0 + j] : 0.0;
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(256) k_seg_heads(const K* __restrict__ keys, int64_t n,
+                                                   uint32_t* __restrict__ hc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (n + SEG_CHUNK - 1) / SEG_CHUNK;
+    for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
+         ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t c0 = ch * SEG_CHUNK, c1 = min(n, c0 + SEG_CHUNK);
+        K last = c0 > 0 ? keys[c0 - 1] : key_zero<K>();
+        uint32_t cnt = 0;
+        for (int64_t b = c0; b < c1; b += 32 * SEG_ITEMS) {
+            const int64_t i0 = b + (int64_t)SEG_ITEMS * lane;
+            K kk[SEG_ITEMS];
+            seg_load_keys(keys, i0, c1, kk);
+            const K up = key_shfl_up(kk[SEG_ITEMS - 1], 1);
+            K kp = lane == 0 ? last : up;
+#pragma unroll
+            for (int j = 0; j < SEG_ITEMS; ++j) {
+                const int64_t i = i0 + j;
+                cnt += (i < c1 && (i == 0 || kk[j] != kp)) ? 1u : 0u;
+                kp = kk[j];
+            }
+            last = key_shfl(kk[SEG_ITEMS - 1], 31);
+        }
+        cnt = __reduce_add_sync(FULL_MASK, cnt);
+        if (lane == 0) hc[ch] = cnt;
+    }
+}
+
 template <class K>
 __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
                                                  const double* __restrict__ vals,
-                                                 const uint32_t* __restrict__ pos, int64_t n,
+                                                 const uint32_t* __restrict__ rbase, int64_t n,
                                                  double* __restrict__ cU, K* __restrict__ keyU) {
     const int lane = threadIdx.x & 31;
-    constexpr int W = 32 * SEG_ITEMS;  // elements per warp iteration
+    constexpr int W = 32 * SEG_ITEMS;  // elements per warp step
+    const unsigned lt = lanemask_lt();
     const int64_t nchunks = (n + SEG_CHUNK - 1) / SEG_CHUNK;
     for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
          ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -221,97 +287,108 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
             if (m) s0 = b + __ffs(m) - 1;
         }
         if (s0 < 0) continue;  // every element continues a run owned by an earlier chunk
-        double carry = 0.0;
-        K kbefore = s0 > 0 ? keys[s0 - 1] : key_zero<K>();
-        for (int64_t b = s0; b < n; b += W) {
+        const int64_t b0 = s0 & ~(int64_t)(SEG_ITEMS - 1);
+        K kbefore = b0 > 0 ? keys[b0 - 1] : key_zero<K>();
+        uint32_t ridx0 = rbase[ch];  // run index of the next head
+        double carry = 0.0;          // the open run entering lane 0
+        for (int64_t b = b0; b < n; b += W) {
             const int64_t i0 = b + (int64_t)SEG_ITEMS * lane;
             K kk[SEG_ITEMS];
             double v[SEG_ITEMS];
-#pragma unroll
-            for (int j = 0; j < SEG_ITEMS; ++j) {
-                const bool in = i0 + j < n;
-                kk[j] = in ? keys[i0 + j] : key_zero<K>();
-                v[j] = in ? vals[i0 + j] : 0.0;
-            }
-            const K knext = (b + W < n) ? keys[b + W] : key_zero<K>();  // first element after this block
-            const K kprev_lane = key_shfl_up(kk[SEG_ITEMS - 1], 1);
-            bool hd[SEG_ITEMS];
+            seg_load_keys(keys, i0, n, kk);
+            seg_load_vals(vals, i0, n, v);
+            const K knext = b + W < n ? keys[b + W] : key_zero<K>();
+            const K up = key_shfl_up(kk[SEG_ITEMS - 1], 1);
+            // heads, and the first element that ends the walk (a head at or past c1, or past n)
+            const int ja = (b == b0 && lane == 0) ? (int)(s0 - b0) : 0;
+            unsigned hm = 0;
             int jstop = SEG_ITEMS;
+            K kp = lane == 0 ? kbefore : up;
 #pragma unroll
             for (int j = 0; j < SEG_ITEMS; ++j) {
                 const int64_t i = i0 + j;
                 const bool in = i < n;
-                const K kp = j > 0 ? kk[j - 1] : (lane == 0 ? kbefore : kprev_lane);
-                hd[j] = in && (i == 0 || kp != kk[j]);
-                const bool stop = !in || (hd[j] && i >= c1);
-                if (stop && jstop == SEG_ITEMS) jstop = j;
+                const bool h = in && (i == 0 || kk[j] != kp);
+                if (h) hm |= 1u << j;
+                if ((!in || (h && i >= c1)) && jstop == SEG_ITEMS) jstop = j;
+                kp = kk[j];
             }
-            // the warp's active elements end at the first stop in element order
             const unsigned sm = __ballot_sync(FULL_MASK, jstop < SEG_ITEMS);
             const int L = sm ? __ffs(sm) - 1 : 32;
             const int jL = sm ? __shfl_sync(FULL_MASK, jstop, L) : 0;
-            int nact_lane = lane < L ? SEG_ITEMS : (lane == L ? jL : 0);
-            // lane summary: open run at the lane's end (from its last head, or the whole lane)
-            double lsum = 0.0;
-            int lh = 0;
+            const int je = lane < L ? SEG_ITEMS : (lane == L ? jL : 0);  // active: [ja, je)
+            const unsigned am = (je >= SEG_ITEMS ? 0xffu : ((1u << je) - 1u)) & ~((1u << ja) - 1u);
+            hm &= am;
+            // lane pass: running sums along runs, one FP64 add per element
+            double run = 0.0, tv[SEG_ITEMS];
 #pragma unroll
             for (int j = 0; j < SEG_ITEMS; ++j) {
-                if (j < nact_lane) {
-                    if (hd[j]) {
-                        lh = 1;
-                        lsum = v[j];
-                    } else {
-                        lsum = lsum + v[j];
-                    }
-                }
+                if ((am >> j) & 1u) run = ((hm >> j) & 1u) ? v[j] : run + v[j];
+                tv[j] = run;
             }
-            // segmented inclusive scan of the lane summaries (earlier lanes first)
-            double sv = lsum;
-            int sf = lh;
+            const bool act = am != 0;
+            const bool lh = hm != 0;
+            const double lsum = act ? run : 0.0;
+            // the open run entering this lane: from the previous lane, or a segmented scan when
+            // some active lane holds no head (a run crosses whole lanes)
+            double inc;
+            double nextcarry;
+            if (!__any_sync(FULL_MASK, act && !lh)) {
+                const double prev = __shfl_up_sync(FULL_MASK, lsum, 1);
+                inc = lane == 0 ? carry : prev;
+                nextcarry = __shfl_sync(FULL_MASK, lsum, 31);
+            } else {
+                double sv = lsum;
+                int sf = lh ? 1 : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double yv = __shfl_up_sync(FULL_MASK, sv, o);
+                    const int yf = __shfl_up_sync(FULL_MASK, sf, o);
+                    if (lane >= o && !sf) sv = yv + sv;
+                    if (lane >= o) sf |= yf;
+                }
+                double ex = __shfl_up_sync(FULL_MASK, sv, 1);
+                int exf = __shfl_up_sync(FULL_MASK, sf, 1);
+                if (lane == 0) {
+                    ex = 0.0;
+                    exf = 0;
+                }
+                inc = exf ? ex : carry + ex;
+                const double sv31 = __shfl_sync(FULL_MASK, sv, 31);
+                const int sf31 = __shfl_sync(FULL_MASK, sf, 31);
+                nextcarry = sf31 ? sv31 : carry + sv31;
+            }
+            // run index of each tail: heads before this lane (warp prefix) + heads up to it
+            const uint32_t nh = (uint32_t)__popc(hm);
+            uint32_t hpre = nh;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const double yv = __shfl_up_sync(FULL_MASK, sv, o);
-                const int yf = __shfl_up_sync(FULL_MASK, sf, o);
-                if (lane >= o) {
-                    if (!sf) sv = yv + sv;
-                    sf |= yf;
-                }
+                const uint32_t y = __shfl_up_sync(FULL_MASK, hpre, o);
+                if (lane >= o) hpre += y;
             }
-            double inc = __shfl_up_sync(FULL_MASK, sv, 1);
-            int incf = __shfl_up_sync(FULL_MASK, sf, 1);
-            if (lane == 0) {
-                inc = 0.0;
-                incf = 0;
-            }
-            if (!incf) inc = carry + inc;
-            // does a run end after this lane's last active element? (next element is a head, a
-            // stop, or absent)
-            const int first_ends = (nact_lane == 0 || hd[0]) ? 1 : 0;
+            const uint32_t htot = __shfl_sync(FULL_MASK, hpre, 31);
+            hpre -= nh;
+            // does the run at the lane's last active element end there?
+            const int first_ends = (!act || (hm & 1u)) ? 1 : 0;
             const int next_first_ends = __shfl_down_sync(FULL_MASK, first_ends, 1);
             bool end_after;
-            if (nact_lane < SEG_ITEMS) {
-                end_after = true;  // a stop follows inside this lane
-            } else if (lane < 31) {
-                end_after = next_first_ends != 0;
-            } else {
-                end_after = (b + W >= n) || (knext != kk[SEG_ITEMS - 1]);
-            }
-            double r = inc;
+            if (je < SEG_ITEMS) end_after = true;
+            else if (lane < 31) end_after = next_first_ends != 0;
+            else end_after = (b + W >= n) || (knext != kk[SEG_ITEMS - 1]);
 #pragma unroll
             for (int j = 0; j < SEG_ITEMS; ++j) {
-                if (j < nact_lane) {
-                    r = hd[j] ? v[j] : r + v[j];
-                    const bool tail = (j + 1 < nact_lane) ? hd[j + 1] : end_after;
+                if ((am >> j) & 1u) {
+                    const bool tail = (j + 1 < je) ? ((hm >> (j + 1)) & 1u) != 0 : end_after;
                     if (tail) {
-                        const uint32_t ridx = pos[i0 + j] + (hd[j] ? 1u : 0u) - 1u;
-                        cU[ridx] = r;
-                        keyU[ridx] = kk[j];
+                        const unsigned upto = hm & ((2u << j) - 1u);  // heads at or before j
+                        const uint32_t r = ridx0 + hpre + (uint32_t)__popc(upto) - 1u;
+                        cU[r] = upto ? tv[j] : inc + tv[j];
+                        keyU[r] = kk[j];
                     }
                 }
             }
-            const double sv31 = __shfl_sync(FULL_MASK, sv, 31);
-            const int sf31 = __shfl_sync(FULL_MASK, sf, 31);
-            carry = sf31 ? sv31 : carry + sv31;
+            ridx0 += htot;
+            carry = nextcarry;
             kbefore = key_shfl(kk[SEG_ITEMS - 1], 31);
             if (L < 32) break;
         }
@@ -459,22 +536,25 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
     else
         NQS_TRY(radix_sort_pairs128(p, bs, (Key128*&)keys, vals, (Key128*&)keys2, vals2, n,
                                     2 * P.norb, s));
-    // run heads and their exclusive scan, in the free value buffer (8 bytes per element)
-    uint32_t* flags = (uint32_t*)vals2;
-    uint32_t* pos = flags + n;
-    {
-        ProfScope prof_(PROF_HEADS, s);
-        k_heads<K><<<grid_for(n, 256), 256, 0, s>>>(keys, n, flags);
-    }
-    NQS_CK_LAUNCH();
-    NQS_TRY(scan_exclusive_u32(p, bs, flags, pos, n, s));
-    uint32_t last_pos = 0, last_flag = 0;
+    // heads per chunk and their exclusive scan (the chunks' first run indices)
+    const int64_t nchunks = (n + SEG_CHUNK - 1) / SEG_CHUNK;
+    uint32_t *hc, *rbase;
+    NQS_TRY(bs.get(&hc, nchunks > 0 ? nchunks : 1));
+    NQS_TRY(bs.get(&rbase, nchunks > 0 ? nchunks : 1));
+    int64_t nuniq = 0;
     if (n > 0) {
-        NQS_CK(cudaMemcpyAsync(&last_pos, pos + n - 1, 4, cudaMemcpyDeviceToHost, s));
-        NQS_CK(cudaMemcpyAsync(&last_flag, flags + n - 1, 4, cudaMemcpyDeviceToHost, s));
+        {
+            ProfScope prof_(PROF_HEADS, s);
+            k_seg_heads<K><<<grid_for(nchunks * 32, 256, 148 * 16), 256, 0, s>>>(keys, n, hc);
+        }
+        NQS_CK_LAUNCH();
+        NQS_TRY(scan_exclusive_u32(p, bs, hc, rbase, nchunks, s));
+        uint32_t last_base = 0, last_count = 0;
+        NQS_CK(cudaMemcpyAsync(&last_base, rbase + nchunks - 1, 4, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaMemcpyAsync(&last_count, hc + nchunks - 1, 4, cudaMemcpyDeviceToHost, s));
         NQS_CK(cudaStreamSynchronize(s));
+        nuniq = (int64_t)last_base + last_count;
     }
-    const int64_t nuniq = n > 0 ? (int64_t)last_pos + last_flag : 0;
     double *cU, *eterm;
     K* keyU;
     NQS_TRY(bs.get(&cU, nuniq));
@@ -483,8 +563,8 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
     if (nuniq > 0) {
         {
             ProfScope prof_(PROF_SEG_REDUCE, s);
-            k_seg_sum<K><<<grid_for((n + SEG_CHUNK - 1) / SEG_CHUNK * 32, 256, 148 * 16), 256, 0,
-                           s>>>(keys, vals, pos, n, cU, keyU);
+            k_seg_sum<K><<<grid_for(nchunks * 32, 256, 148 * 16), 256, 0, s>>>(keys, vals, rbase, n,
+                                                                             cU, keyU);
         }
         NQS_CK_LAUNCH();
         {
@@ -534,8 +614,9 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     int64_t* pre_offs = nullptr;  // offsets of a screened single-bucket count, when one ran
     int64_t pre_total = 0;
     if (B <= 0) {
-        // automatic: enough buckets that one bucket's pairs (keys and values twice, flags and
-        // positions) use at most half of the free device memory, and stay below 2^31
+        // automatic: enough buckets that one bucket's pairs (keys and values twice, plus 8 bytes
+        // per pair toward the per-unique arrays) use at most half of the free device memory,
+        // and stay below 2^31
         const int kbits_ = 2 * P.norb;
         const double kb = kbits_ <= 32 ? 4.0 : (kbits_ <= 64 ? 8.0 : 16.0);
         size_t fr = 0, tot = 0;
