@@ -267,7 +267,7 @@ def run_nqs(args, ws, rank, local):
                     buckets=r.get("buckets", 0),
                     n_emit=r["n_emitted"], nnz=csr.nnz, n_unique=r["n_unique"], E=E,
                     ext=r["ext"], int=r["int"])
-        csr.free()
+        csr.free_async()
         e4 = mark(record)
         if record:
             for k, (x, y) in zip(ev_phase, [(e0, e1), (e1, e2), (e2, e3), (e3, e4)]):
@@ -571,7 +571,7 @@ def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_
         r = (dict(n_emitted=0) if args.no_pt2 else
              N.pt2(P, dets, psi, float(out_host[0]), o=o_pt))
         n = csr.n_enumerated + r["n_emitted"]
-        csr.free()
+        csr.free_async()
         b.record(stream)
         b.synchronize()
         if it >= args.warmup:

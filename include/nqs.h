@@ -89,7 +89,7 @@ typedef struct {
 /* Library-owned CSR of H_SS (device memory). Row r holds, in order: the diagonal element
  * (column r), then every excitation of S[r] that lies in S, in canonical excitation order.
  * val[k] = <S[col[k]]|H|S[r]> (H_SS is symmetric, bit for bit under this library's summation
- * order). Free with nqs_csr_free. */
+ * order). Free with nqs_csr_free or nqs_csr_free_async. */
 typedef struct {
     int64_t* row_ptr; /* device [n_rows + 1] */
     int32_t* col;     /* device [nnz] */
@@ -141,7 +141,14 @@ int nqs_diag(nqs_problem* problem, const uint64_t* dets, int64_t n, double* out,
  * NQS_ERR_ARG, NQS_ERR_UNSORTED / NQS_ERR_POPCOUNT (with validate), NQS_ERR_OOM, NQS_ERR_CUDA. */
 int nqs_connections(nqs_problem* problem, const uint64_t* dets, int64_t nS, const nqs_opts* opts,
                     nqs_csr* out, int64_t* n_enumerated, nqs_stream_t stream);
+/* Release a library-owned CSR (from nqs_connections or nqs_proxy_hamiltonian; its arrays come
+ * from the problem's stream-ordered pool, which outlives the problem handle while they exist).
+ * nqs_csr_free waits for the whole device first. nqs_csr_free_async releases the arrays in the
+ * order of `stream`: work already queued on that stream may still read them, and work on other
+ * streams must be ordered before it by the caller. Both zero *csr. Errors: NQS_ERR_ARG,
+ * NQS_ERR_CUDA. */
 int nqs_csr_free(nqs_csr* csr);
+int nqs_csr_free_async(nqs_csr* csr, nqs_stream_t stream);
 
 /* Proxy-mode Hamiltonian, Eq. (proxy_hamiltonian) of Sec. 2.4.1, on the target set T = V + P:
  * (H~)_xy = H_xy when x or y lies in V, H_xx on the diagonal, 0 between distinct members of P.

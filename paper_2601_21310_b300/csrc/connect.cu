@@ -228,10 +228,12 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
     NQS_TRY(sc.get(&rowcnt, nS));
     uint32_t* bits;
     NQS_TRY(sc.get(&bits, (size_t)nS * ((p->d.nexc + 31) / 32)));
+    // the matrix comes from the problem's stream-ordered pool: no device-wide synchronisation
+    // to allocate it, and nqs_csr_free_async returns it in stream order
     int64_t* row_ptr = nullptr;
-    NQS_CK(cudaMalloc(&row_ptr, (nS + 1) * sizeof(int64_t)));
+    NQS_TRY(nqs_scratch_alloc(p, (void**)&row_ptr, (nS + 1) * sizeof(int64_t), s));
     auto fail = [&](int code) {
-        cudaFree(row_ptr);
+        nqs_scratch_free(p, row_ptr, s);
         return code;
     };
     {
@@ -249,10 +251,9 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
         return fail(NQS_ERR_CUDA);
     int32_t* col = nullptr;
     double* val = nullptr;
-    if (cudaMalloc(&col, nnz * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&val, nnz * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(col);
+    if (nqs_scratch_alloc(p, (void**)&col, (nnz > 0 ? nnz : 1) * sizeof(int32_t), s) != NQS_OK ||
+        nqs_scratch_alloc(p, (void**)&val, (nnz > 0 ? nnz : 1) * sizeof(double), s) != NQS_OK) {
+        nqs_scratch_free(p, col, s);
         return fail(NQS_ERR_OOM);
     }
     {
@@ -262,8 +263,8 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
     }
     nqs_note_launch();
     if (cudaGetLastError() != cudaSuccess) {
-        cudaFree(col);
-        cudaFree(val);
+        nqs_scratch_free(p, col, s);
+        nqs_scratch_free(p, val, s);
         return fail(NQS_ERR_CUDA);
     }
     out->row_ptr = row_ptr;
@@ -277,10 +278,31 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
 
 extern "C" int nqs_csr_free(nqs_csr* csr) {
     if (!csr) return NQS_ERR_ARG;
-    cudaDeviceSynchronize();
-    cudaFree(csr->row_ptr);
-    cudaFree(csr->col);
-    cudaFree(csr->val);
+    // after every stream of the device is idle, a free in any stream order is safe
+    cudaError_t e = cudaDeviceSynchronize();
+    if (csr->row_ptr) cudaFreeAsync(csr->row_ptr, 0);
+    if (csr->col) cudaFreeAsync(csr->col, 0);
+    if (csr->val) cudaFreeAsync(csr->val, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     memset(csr, 0, sizeof *csr);
+    if (e != cudaSuccess) {
+        nqs_record_error("nqs_csr_free", e, __FILE__, __LINE__);
+        return NQS_ERR_CUDA;
+    }
+    return NQS_OK;
+}
+
+extern "C" int nqs_csr_free_async(nqs_csr* csr, nqs_stream_t stream) {
+    if (!csr) return NQS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (csr->row_ptr) cudaFreeAsync(csr->row_ptr, s);
+    if (csr->col) cudaFreeAsync(csr->col, s);
+    if (csr->val) cudaFreeAsync(csr->val, s);
+    memset(csr, 0, sizeof *csr);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        nqs_record_error("nqs_csr_free_async", e, __FILE__, __LINE__);
+        return NQS_ERR_CUDA;
+    }
     return NQS_OK;
 }

@@ -212,10 +212,12 @@ extern "C" int nqs_proxy_hamiltonian(nqs_problem* p, const uint64_t* T, int64_t 
     NQS_TRY(sc.get(&len, nT));
     k_proxy_rowlen<<<grid_for(nT, 256), 256, 0, s>>>(rpV, nV, cntP, nP, len);
     NQS_CK_LAUNCH();
+    // the matrix comes from the problem's stream-ordered pool: no device-wide synchronisation
+    // to allocate it, and nqs_csr_free_async returns it in stream order
     int64_t* row_ptr = nullptr;
-    NQS_CK(cudaMalloc(&row_ptr, (nT + 1) * sizeof(int64_t)));
+    NQS_TRY(nqs_scratch_alloc(p, (void**)&row_ptr, (nT + 1) * sizeof(int64_t), s));
     auto fail = [&](int code) {
-        cudaFree(row_ptr);
+        nqs_scratch_free(p, row_ptr, s);
         return code;
     };
     int st = scan_exclusive_i64(p, sc, len, row_ptr, nT, row_ptr + nT, s);
@@ -236,10 +238,9 @@ extern "C" int nqs_proxy_hamiltonian(nqs_problem* p, const uint64_t* T, int64_t 
         return fail(NQS_ERR_CUDA);
     int32_t* col = nullptr;
     double* val = nullptr;
-    if (cudaMalloc(&col, nnz * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&val, nnz * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(col);
+    if (nqs_scratch_alloc(p, (void**)&col, (nnz > 0 ? nnz : 1) * sizeof(int32_t), s) != NQS_OK ||
+        nqs_scratch_alloc(p, (void**)&val, (nnz > 0 ? nnz : 1) * sizeof(double), s) != NQS_OK) {
+        nqs_scratch_free(p, col, s);
         return fail(NQS_ERR_OOM);
     }
     k_proxy_copy_v<<<grid_for(nnzV, 256), 256, 0, s>>>(colV, valV, nnzV, col, val);
@@ -257,8 +258,8 @@ extern "C" int nqs_proxy_hamiltonian(nqs_problem* p, const uint64_t* T, int64_t 
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        cudaFree(col);
-        cudaFree(val);
+        nqs_scratch_free(p, col, s);
+        nqs_scratch_free(p, val, s);
         nqs_record_error("nqs_proxy_hamiltonian", e, __FILE__, __LINE__);
         return fail(NQS_ERR_CUDA);
     }

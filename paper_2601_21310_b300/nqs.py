@@ -57,6 +57,7 @@ EXPORTS = {
     "nqs_connections": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
     "nqs_csr_free": (C.c_int, [C.c_void_p]),
+    "nqs_csr_free_async": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nqs_proxy_hamiltonian": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_void_p]),
     "nqs_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
@@ -300,8 +301,16 @@ class CSR:
         return rp - a, col[:b - a], val[:b - a]
 
     def free(self):
+        """Release the matrix after the whole device is idle."""
         if self.s is not None and self.s.row_ptr:
             lib().nqs_csr_free(C.byref(self.s))
+
+    def free_async(self, stream=None):
+        """Release the matrix in the order of `stream` (default: torch's current stream); work on
+        other streams that reads it must be ordered before this call."""
+        if self.s is not None and self.s.row_ptr:
+            _check(lib().nqs_csr_free_async(C.byref(self.s), _stream(stream)),
+                   "nqs_csr_free_async")
 
     def __del__(self):
         try:
