@@ -200,6 +200,7 @@ struct EnumPos {
     int cls;             // class of the lane's current index (-1: not located yet)
     int pi, qi;          // same-spin doubles: hole-pair and particle-pair positions
     int xa, ya, xb, yb;  // alpha-beta doubles: positions in the occupied / virtual lists
+    int d_hi, d_lo;      // a step of 32 in the current class: 32 = d_hi * (inner size) + d_lo
 };
 
 __device__ __forceinline__ void ab_locate(const ProblemDev& P, uint32_t l, EnumPos& q) {
@@ -209,19 +210,43 @@ __device__ __forceinline__ void ab_locate(const ProblemDev& P, uint32_t l, EnumP
     q.ya = (int)(la - (uint32_t)q.xa * (uint32_t)P.ma);
     q.xb = (int)(lb / (uint32_t)P.mb);
     q.yb = (int)(lb - (uint32_t)q.xb * (uint32_t)P.mb);
+    q.d_hi = 32 / P.mb;
+    q.d_lo = 32 - q.d_hi * P.mb;
     q.cls = 4;
 }
 
+// (xa, ya, xb, yb) of the index 32 further on: add 32 = d_hi * mb + d_lo to (xb, yb), then
+// carry whole beta-hole rounds into the alpha positions
 __device__ __forceinline__ void ab_advance32(const ProblemDev& P, EnumPos& q) {
-    q.yb += 32;
-    while (q.yb >= P.mb) {
+    q.yb += q.d_lo;
+    q.xb += q.d_hi;
+    if (q.yb >= P.mb) {
         q.yb -= P.mb;
-        if (++q.xb == P.nb) {
-            q.xb = 0;
-            if (++q.ya == P.ma) {
-                q.ya = 0;
-                ++q.xa;
-            }
+        ++q.xb;
+    }
+    while (q.xb >= P.nb) {
+        q.xb -= P.nb;
+        if (++q.ya == P.ma) {
+            q.ya = 0;
+            ++q.xa;
+        }
+    }
+}
+
+// same-spin doubles: position of canonical offset l (first call in the class), or 32 further on
+__device__ __forceinline__ void ss_step(uint32_t l, int cls, int Q, EnumPos& q) {
+    if (q.cls != cls) {
+        q.pi = (int)(l / (uint32_t)Q);
+        q.qi = (int)(l - (uint32_t)q.pi * (uint32_t)Q);
+        q.d_hi = 32 / Q;
+        q.d_lo = 32 - q.d_hi * Q;
+        q.cls = cls;
+    } else {
+        q.qi += q.d_lo;
+        q.pi += q.d_hi;
+        if (q.qi >= Q) {
+            q.qi -= Q;
+            ++q.pi;
         }
     }
 }
@@ -238,20 +263,8 @@ __device__ __forceinline__ void step_key(const ProblemDev& P, const PairTables& 
     }
     if (e < o4) {
         const bool alpha = e < o3;
-        const int cls = alpha ? 2 : 3;
         const int Q = (int)(alpha ? choose2(P.ma) : choose2(P.mb));
-        if (q.cls != cls) {
-            const uint32_t l = e - (alpha ? o2 : o3);
-            q.pi = (int)(l / (uint32_t)Q);
-            q.qi = (int)(l - (uint32_t)q.pi * (uint32_t)Q);
-            q.cls = cls;
-        } else {
-            q.qi += 32;
-            while (q.qi >= Q) {
-                q.qi -= Q;
-                ++q.pi;
-            }
-        }
+        ss_step(e - (alpha ? o2 : o3), alpha ? 2 : 3, Q, q);
         const uint16_t po = alpha ? T.occA[q.pi] : T.occB[q.pi];
         const uint16_t pv = alpha ? T.virA[q.qi] : T.virB[q.qi];
         const uint8_t* occ = alpha ? c.occA : c.occB;
@@ -266,6 +279,54 @@ __device__ __forceinline__ void step_key(const ProblemDev& P, const PairTables& 
     else ab_advance32(P, q);
     a2 = A ^ (1ull << c.occA[q.xa]) ^ (1ull << c.virA[q.ya]);
     b2 = B ^ (1ull << c.occB[q.xb]) ^ (1ull << c.virB[q.yb]);
+}
+
+// the full excitation of canonical index e, with the same incremental positions as step_key
+// (the same values as decode_exc)
+__device__ __forceinline__ void step_exc(const ProblemDev& P, const PairTables& T,
+                                         const DetCtx& c, uint64_t A, uint64_t B, uint32_t e,
+                                         uint32_t o2, uint32_t o3, uint32_t o4, EnumPos& q,
+                                         Exc& x) {
+    if (e < o2) {
+        decode_exc(P, T, c, A, B, e, x);
+        return;
+    }
+    if (e < o4) {
+        const bool alpha = e < o3;
+        const int Q = (int)(alpha ? choose2(P.ma) : choose2(P.mb));
+        ss_step(e - (alpha ? o2 : o3), alpha ? 2 : 3, Q, q);
+        const uint16_t po = alpha ? T.occA[q.pi] : T.occB[q.pi];
+        const uint16_t pv = alpha ? T.virA[q.qi] : T.virB[q.qi];
+        const uint8_t* occ = alpha ? c.occA : c.occB;
+        const uint8_t* vir = alpha ? c.virA : c.virB;
+        const int i = occ[po & 0xff], j = occ[po >> 8];
+        const int a = vir[pv & 0xff], b = vir[pv >> 8];
+        const uint64_t w = alpha ? A : B;
+        const int s1 = exc_sign(w, i, a);
+        const uint64_t w1 = w ^ (1ull << i) ^ (1ull << a);
+        const int s2 = exc_sign(w1, j, b);
+        const uint64_t w2 = w1 ^ (1ull << j) ^ (1ull << b);
+        x.cls = alpha ? 2 : 3;
+        x.i = i;
+        x.j = j;
+        x.a = a;
+        x.b = b;
+        x.sign = s1 * s2;
+        x.a2 = alpha ? w2 : A;
+        x.b2 = alpha ? B : w2;
+        return;
+    }
+    if (q.cls != 4) ab_locate(P, e - o4, q);
+    else ab_advance32(P, q);
+    const int i = c.occA[q.xa], a = c.virA[q.ya], j = c.occB[q.xb], b = c.virB[q.yb];
+    x.cls = 4;
+    x.i = i;
+    x.a = a;
+    x.j = j;
+    x.b = b;
+    x.sign = exc_sign(A, i, a) * exc_sign(B, j, b);
+    x.a2 = A ^ (1ull << i) ^ (1ull << a);
+    x.b2 = B ^ (1ull << j) ^ (1ull << b);
 }
 
 __device__ __forceinline__ double eri_at(const ProblemDev& P, int p, int q, int r, int s) {

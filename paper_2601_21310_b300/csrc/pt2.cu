@@ -121,13 +121,17 @@ __global__ void __launch_bounds__(PT_THREADS, 6) k_pt2_emit(ProblemDev P,
         const double py = psi[det];
         int64_t run = offs ? offs[det] : det * (int64_t)nexc;
         if (B == 1) {
+            const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                           o4 = o3 + (uint32_t)P.dBB;
+            EnumPos q;
+            q.cls = -1;
             for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
                 const uint32_t e = r0 + lane;
                 const bool take = e < nexc;
                 const unsigned m = __ballot_sync(FULL_MASK, take);
                 if (take) {
                     Exc ex;
-                    decode_exc(P, T, *ctx, x.x, x.y, e, ex);
+                    step_exc(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, ex);
                     const int64_t pos = run + __popc(m & lt);
                     keys[pos] = key_make<K>(ex.a2, ex.b2, norb);
                     vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
