@@ -118,15 +118,20 @@ __global__ void __launch_bounds__(CONN_THREADS) k_conn_fill(ProblemDev P, HashS 
     const unsigned lt = lanemask_lt();
     const uint32_t nexc = (uint32_t)P.nexc;
     const uint32_t nwords = (nexc + 31) / 32;
+    // the diagonal of every row, one thread per configuration (each a sequential FP64 sum; one
+    // lane per warp doing it would hold the FP64 pipe for a whole warp per operation)
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < nS;
+         d += (int64_t)gridDim.x * blockDim.x) {
+        const ulonglong2 x = S[d];
+        const int64_t b = row_ptr[d];
+        col[b] = (int32_t)d;
+        val[b] = diag_element_impl(P, x.x, x.y);
+    }
     for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * CONN_WARPS) {
         ulonglong2 x = S[det];
         fill_ctx(P, x.x, x.y, ctx, lane);
         const int64_t base = row_ptr[det];
-        if (lane == 0) {
-            col[base] = (int32_t)det;
-            val[base] = diag_element_impl(P, x.x, x.y);
-        }
         int64_t run = base + 1;
         if (bits) {
             // The hits of the stored ballot words are appended, in canonical order, to a per-warp

@@ -372,7 +372,8 @@ __device__ __forceinline__ double exc_element(const ProblemDev& P, const DetCtx&
     } else {
         v = eri_at(P, x.i, x.a, x.j, x.b);
     }
-    return x.sign < 0 ? -v : v;
+    // the sign as a flip of the sign bit (the same value as -v, without an FP64 instruction)
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(x.sign < 0) << 63));
 }
 
 // H_xx: sum_{occ} h_ii + sum_{i<j same spin} [J_ij - K_ij] + sum_{i alpha, j beta} J_ij, in the
