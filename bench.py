@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-outer", action="store_true",
                     help="skip the outer-loop measurement (heat-bath set, amplitudes on T, Top-K)")
     ap.add_argument("--buckets", type=int, default=0,
-                    help="PT2 hash buckets (0: enough to keep each bucket under 2^30 emissions)")
+                    help="PT2 hash buckets (0: the library's choice, from the free device memory)")
     ap.add_argument("--no-pt2", action="store_true",
                     help="step without PT2 (for shapes whose PT2 takes minutes); labelled in config")
     ap.add_argument("--no-e2e", action="store_true")
@@ -158,18 +158,21 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 # roofline bookkeeping: algorithmic work per launch of each instrumented kernel family
 # ------------------------------------------------------------------------------------------
-def algorithmic_work(name, wl, nS, nexc, nnz, n_emit, n_unique, net_flops, buckets=1):
+def algorithmic_work(name, wl, nS, nexc, nnz, n_emit, n_unique, net_flops, buckets=1,
+                     launches=1):
     """(bound, amount per launch, unit) - bytes for HBM-bound kernels, FLOP for GEMMs. With B
-    PT2 buckets each PT2 launch handles one bucket: 1/B of the emitted pairs and unique terms."""
+    PT2 buckets each sort and reduction launch handles one bucket: 1/B of the emitted pairs and
+    unique terms; the emission runs once for all buckets or once per bucket (`launches` per
+    step)."""
     kb = 4.0 if 2 * wl.norb <= 32 else (8.0 if 2 * wl.norb <= 64 else 16.0)  # PT2 key width
+    if name == "pt2_emit":     # write key+value per emission, read S and psi
+        return "hbm", ((kb + 8.0) * n_emit + 24.0 * nS) / max(1, launches), "B"
     n_emit = n_emit / max(1, buckets)
     n_unique = n_unique / max(1, buckets)
     if name == "rs_scatter":   # read key+value, write key+value
         return "hbm", 2.0 * (kb + 8.0) * n_emit, "B"
     if name == "rs_hist":      # read keys
         return "hbm", kb * n_emit, "B"
-    if name == "pt2_emit":     # write key+value per emission, read S and psi
-        return "hbm", (kb + 8.0) * n_emit + 24.0 * nS, "B"
     if name == "seg_reduce":   # read keys + values, write (sum, key) per run, read its run index
         return "hbm", (kb + 8.0) * n_emit + (kb + 12.0) * n_unique, "B"
     if name == "conn_fill":    # write col+val per nonzero, read S
@@ -230,9 +233,7 @@ def run_nqs(args, ws, rank, local):
     o_conn = N.opts(precision=dtype, validate=0)
     o_eg = N.opts(precision=dtype, validate=0)
     nexc_total = nS * synth_nexc(wl)
-    buckets = args.buckets if args.buckets > 0 else max(1, -(-nexc_total // (1 << 30)))
-    if args.eps_pt2 > 0 and args.buckets == 0:
-        buckets = 0  # screened: the library sizes the buckets from the counted emissions
+    buckets = args.buckets if args.buckets > 0 else 0  # 0: the library sizes the buckets
     o_pt = N.opts(precision=dtype, buckets=buckets, validate=0, eps_pt2=args.eps_pt2)
     out = torch.empty(4, dtype=torch.float64, device=dev)
     grad = torch.empty(net.num_params(), dtype=net.grad_dtype(), device=dev)
@@ -259,9 +260,9 @@ def run_nqs(args, ws, rank, local):
             r = dict(n_emitted=0, n_unique=0, ext=float("nan"), int=float("nan"))
         elif args.eps_pt2 > 0:
             # the screening threshold refers to psi normalised over S
-            r = N.pt2(P, dets, psi / torch.linalg.norm(psi), E, o=o_pt)
+            r = N.pt2(P, dets, psi / torch.linalg.norm(psi), E, o=o_pt, hss=csr)
         else:
-            r = N.pt2(P, dets, psi, E, o=o_pt)
+            r = N.pt2(P, dets, psi, E, o=o_pt, hss=csr)
         e3 = mark(record)
         info = dict(n_conn=csr.n_enumerated + r["n_emitted"], n_hss=csr.n_enumerated,
                     buckets=r.get("buckets", 0),
@@ -336,7 +337,8 @@ def run_nqs(args, ws, rank, local):
     def work(k):
         per_launch_flops = total_gemm_flops / max(1, prof[k][1] / args.steps)
         return algorithmic_work(k, wl, nS, nexc, info["nnz"], info["n_emit"], info["n_unique"],
-                                per_launch_flops, max(1, info["buckets"]))
+                                per_launch_flops, max(1, info["buckets"]),
+                                max(1, prof[k][1] / args.steps))
 
     # the roofline is reported for the largest kernel with a byte or FLOP bound; the largest
     # kernel overall is named beside it when it is an issue-bound one
@@ -431,9 +433,10 @@ def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, 
     N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
     E64 = out64[0].item()
     r64 = (dict(ext=float("nan"), int=float("nan")) if args.no_pt2 else
-           N.pt2(P, dets, psi64 / torch.linalg.norm(psi64), E64,
+           N.pt2(P, dets, psi64 / torch.linalg.norm(psi64), E64, hss=csr,
                  o=N.opts(validate=0, buckets=0, eps_pt2=args.eps_pt2)) if args.eps_pt2 > 0 else
-           N.pt2(P, dets, psi64, E64, o=N.opts(validate=0, buckets=o_pt_buckets(args, p))))
+           N.pt2(P, dets, psi64, E64, o=N.opts(validate=0, buckets=o_pt_buckets(args, p)),
+                 hss=csr))
     csr.free()
     gm = grad_mixed.double()
     grel = (torch.linalg.norm(gm - g64) / torch.linalg.norm(g64)).item()
@@ -535,8 +538,7 @@ def run_modes(N, P, net, dets, T, nS, o, timed):
 
 
 def o_pt_buckets(args, p):
-    n = len(p.S) * synth_nexc(p.wl)
-    return args.buckets if args.buckets > 0 else max(1, -(-n // (1 << 30)))
+    return args.buckets if args.buckets > 0 else 0
 
 
 def synth_nexc(wl):
@@ -569,7 +571,7 @@ def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_
         grad_host.copy_(grad, non_blocking=True)
         stream.synchronize()
         r = (dict(n_emitted=0) if args.no_pt2 else
-             N.pt2(P, dets, psi, float(out_host[0]), o=o_pt))
+             N.pt2(P, dets, psi, float(out_host[0]), o=o_pt, hss=csr))
         n = csr.n_enumerated + r["n_emitted"]
         csr.free_async()
         b.record(stream)

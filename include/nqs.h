@@ -238,6 +238,16 @@ int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64
             double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
             nqs_stream_t stream);
 
+/* nqs_pt2 with H_SS at hand: hss is the library CSR of nqs_connections over the same dets (row
+ * r = [diagonal, then its hits]; n_rows must equal nS). With opts->eps_pt2 > 0 the internal
+ * term's off-diagonal (H_SS psi)_x is then one SpMV over hss instead of a second enumeration of
+ * the connected sets of S (which at 42 orbitals costs as much as nqs_connections itself);
+ * otherwise the result is the same as nqs_pt2's. hss is read only; it must stay valid until the
+ * call returns. Errors: those of nqs_pt2, and NQS_ERR_ARG for a missing or mis-sized hss. */
+int nqs_pt2_hss(nqs_problem* problem, const uint64_t* dets, const double* psi, int64_t nS,
+                double E_var, const nqs_csr* hss, const nqs_opts* opts, double* out,
+                double* bucket_partials, nqs_stream_t stream);
+
 /* ---- batched evaluation of many independent problems ------------------------------------ */
 typedef struct nqs_batch nqs_batch; /* opaque */
 

@@ -13,6 +13,8 @@
 // y = H x, one warp per row, FP64. Lanes stride the row with four independent partial sums
 // (the loads of four strides in flight per lane: the gathers x[col] are dependent loads), which
 // are added in a fixed order and then reduced by a shuffle tree: the result is deterministic.
+// OFFDIAG skips each row's first entry (the diagonal, first in every row of H_SS).
+template <bool OFFDIAG>
 __global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rp,
                                               const int32_t* __restrict__ col,
                                               const double* __restrict__ val,
@@ -22,7 +24,7 @@ __global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rp,
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int64_t k1 = rp[r + 1];
-        int64_t k = rp[r] + lane;
+        int64_t k = rp[r] + (OFFDIAG ? 1 : 0) + lane;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         for (; k + 96 < k1; k += 128) {
             const int32_t c0 = __ldg(col + k), c1 = __ldg(col + k + 32), c2 = __ldg(col + k + 64),
@@ -116,8 +118,19 @@ int csr_spmv(const nqs_csr* csr, const double* x, double* y, cudaStream_t s) {
     int64_t n = csr->n_rows;
     {
         ProfScope prof_(PROF_SPMV, s);
-        k_spmv<<<grid_for(n * 32, 256, 148 * 64), 256, 0, s>>>(csr->row_ptr, csr->col, csr->val, x, n,
-                                                               y);
+        k_spmv<false><<<grid_for(n * 32, 256, 148 * 64), 256, 0, s>>>(csr->row_ptr, csr->col,
+                                                                      csr->val, x, n, y);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int csr_spmv_offdiag(const nqs_csr* csr, const double* x, double* y, cudaStream_t s) {
+    int64_t n = csr->n_rows;
+    {
+        ProfScope prof_(PROF_SPMV, s);
+        k_spmv<true><<<grid_for(n * 32, 256, 148 * 64), 256, 0, s>>>(csr->row_ptr, csr->col,
+                                                                     csr->val, x, n, y);
     }
     NQS_CK_LAUNCH();
     return NQS_OK;

@@ -295,6 +295,8 @@ int scan_exclusive_f64(nqs_problem* p, Scratch& sc, const double* in, double* ou
                        double* total, cudaStream_t s);
 // y = H x for a device CSR (one warp per row, fixed summation order)
 int csr_spmv(const nqs_csr* csr, const double* x, double* y, cudaStream_t s);
+// the same without each row's first entry (the diagonal of H_SS): the off-diagonal part
+int csr_spmv_offdiag(const nqs_csr* csr, const double* x, double* y, cudaStream_t s);
 // compensated (Neumaier) sum of n FP64 values into *out (device); deterministic
 int ksum_f64(nqs_problem* p, Scratch& sc, const double* x, int64_t n, double* out,
              cudaStream_t s);

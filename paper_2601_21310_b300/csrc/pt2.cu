@@ -192,6 +192,63 @@ __global__ void __launch_bounds__(PT_THREADS, 6) k_pt2_emit(ProblemDev P,
     }
 }
 
+// All buckets in one pass: excitation e of det goes to bucket b = det_hash(x') mod B, at
+// start[b] + offs[b * nS + det] + (its rank among det's excitations in bucket b, canonical
+// order). Every excitation is decoded once (incrementally); per-warp counters in shared memory
+// carry each bucket's rank across rounds of 32.
+template <class K>
+__global__ void __launch_bounds__(PT_THREADS) k_pt2_emit_all(ProblemDev P,
+                                                              const ulonglong2* __restrict__ S,
+                                                              const double* __restrict__ psi,
+                                                              int64_t nS, uint32_t B,
+                                                              const int64_t* __restrict__ start,
+                                                              const int64_t* __restrict__ offs,
+                                                              K* __restrict__ keys,
+                                                              double* __restrict__ vals) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    uint32_t* ctr = (uint32_t*)(smem + pair_table_bytes(P) + PT_WARPS * sizeof(DetCtx)) +
+                    (threadIdx.x >> 5) * B;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const uint32_t nexc = (uint32_t)P.nexc;
+    const int norb = P.norb;
+    const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                   o4 = o3 + (uint32_t)P.dBB;
+    for (int64_t det = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * PT_WARPS) {
+        const ulonglong2 x = S[det];
+        for (uint32_t k = lane; k < B; k += 32) ctr[k] = 0;
+        fill_ctx(P, x.x, x.y, ctx, lane);  // ends with __syncwarp
+        const double py = psi[det];
+        EnumPos q;
+        q.cls = -1;
+        for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
+            const uint32_t e = r0 + lane;
+            const bool take = e < nexc;
+            Exc ex;
+            uint32_t b = 0xffffffffu;
+            if (take) {
+                step_exc(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, ex);
+                b = (uint32_t)(det_hash(ex.a2, ex.b2) % B);
+            }
+            const unsigned peers = __match_any_sync(FULL_MASK, b);
+            uint32_t base = 0;
+            if (take) {
+                base = ctr[b];
+                const int64_t pos = start[b] + offs[(int64_t)b * nS + det] + base +
+                                    __popc(peers & lt);
+                keys[pos] = key_make<K>(ex.a2, ex.b2, norb);
+                vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
+            }
+            __syncwarp();
+            if (take && lane == __ffs(peers) - 1) ctr[b] = base + __popc(peers);
+            __syncwarp();
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // Run reduction over the sorted (key, value) pairs. The pairs are cut into chunks of SEG_CHUNK;
 // a chunk owns the runs of equal keys whose first element (head) lies in it.
@@ -506,31 +563,14 @@ static double host_ksum(const std::vector<double>& v) {
     return s + c;
 }
 
-// one bucket of the pipeline with key type K; adds the bucket's partial sums on the device
+// sort, deduplicate and reduce one bucket's n emitted pairs (keys, vals; keys2 / vals2 are the
+// sort's second buffers, n long), adding its external sum on the device
 template <class K>
-static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
-                      double E_var, int64_t B, int64_t b, const int64_t* offs, int64_t n,
-                      const HashS& H, double* cS, double* D_dev, double* ext_dev,
-                      unsigned long long* nuniq_dev, size_t smem, double eps, cudaStream_t s) {
+static int pt2_reduce(nqs_problem* p, K* keys, double* vals, K* keys2, double* vals2, int64_t n,
+                      double E_var, const HashS& H, double* cS, double* D_dev, double* ext_dev,
+                      unsigned long long* nuniq_dev, cudaStream_t s) {
     const ProblemDev& P = p->d;
     Scratch bs(p, s);
-    K *keys, *keys2;
-    double *vals, *vals2;
-    NQS_TRY(bs.get(&keys, n));
-    NQS_TRY(bs.get(&vals, n));
-    NQS_TRY(bs.get(&keys2, n));
-    NQS_TRY(bs.get(&vals2, n));
-    if (eps > 0.0) {
-        NQS_TRY(hb_pt2_pass(p, H, dets, psi, nS, eps, (uint64_t)B, (uint64_t)b, nullptr, offs,
-                            keys, vals, s));
-    } else {
-        {
-            ProfScope prof_(PROF_PT2_EMIT, s);
-            k_pt2_emit<K><<<pt_grid(nS), PT_THREADS, smem, s>>>(
-                P, (const ulonglong2*)dets, psi, nS, (uint64_t)B, (uint64_t)b, offs, keys, vals);
-        }
-        NQS_CK_LAUNCH();
-    }
     if (sizeof(K) == 4)
         NQS_TRY(radix_sort_pairs32(p, bs, (uint32_t*&)keys, vals, (uint32_t*&)keys2, vals2, n,
                                    2 * P.norb, s));
@@ -582,13 +622,128 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
     return NQS_OK;
 }
 
+// one bucket of the pipeline with key type K: emit its pairs, then reduce them
+template <class K>
+static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                      double E_var, int64_t B, int64_t b, const int64_t* offs, int64_t n,
+                      const HashS& H, double* cS, double* D_dev, double* ext_dev,
+                      unsigned long long* nuniq_dev, size_t smem, double eps, cudaStream_t s) {
+    const ProblemDev& P = p->d;
+    Scratch bs(p, s);
+    K *keys, *keys2;
+    double *vals, *vals2;
+    NQS_TRY(bs.get(&keys, n));
+    NQS_TRY(bs.get(&vals, n));
+    NQS_TRY(bs.get(&keys2, n));
+    NQS_TRY(bs.get(&vals2, n));
+    if (eps > 0.0) {
+        NQS_TRY(hb_pt2_pass(p, H, dets, psi, nS, eps, (uint64_t)B, (uint64_t)b, nullptr, offs,
+                            keys, vals, s));
+    } else {
+        {
+            ProfScope prof_(PROF_PT2_EMIT, s);
+            k_pt2_emit<K><<<pt_grid(nS), PT_THREADS, smem, s>>>(
+                P, (const ulonglong2*)dets, psi, nS, (uint64_t)B, (uint64_t)b, offs, keys, vals);
+        }
+        NQS_CK_LAUNCH();
+    }
+    return pt2_reduce<K>(p, keys, vals, keys2, vals2, n, E_var, H, cS, D_dev, ext_dev, nuniq_dev,
+                         s);
+}
+
+// The internal term of bucket b: r_x^2 / (D (E - H_xx)) over the dets of S in bucket b, summed
+// into dev_scalars[2 + 2b] (zero without the internal term)
+static int pt2_internal_bucket(nqs_problem* p, const uint64_t* dets, const double* psi,
+                               const double* cS, int64_t nS, double* dev_scalars, double E_var,
+                               int64_t B, int64_t b, double* eint, bool with_int,
+                               cudaStream_t s) {
+    if (!with_int) {
+        NQS_CK(cudaMemsetAsync(dev_scalars + 2 + 2 * b, 0, sizeof(double), s));
+        return NQS_OK;
+    }
+    k_pt2_internal<<<grid_for(nS, 256), 256, 0, s>>>(p->d, (const ulonglong2*)dets, psi, cS, nS,
+                                                     dev_scalars, E_var, (uint64_t)B, (uint64_t)b,
+                                                     eint);
+    NQS_CK_LAUNCH();
+    Scratch sc(p, s);
+    return ksum_f64(p, sc, eint, nS, dev_scalars + 2 + 2 * b, s);
+}
+
+// All buckets resident at once (unscreened, counts of every bucket known): one emission pass
+// writes each pair into its bucket's region (bucket regions start on 16-element boundaries), then
+// the buckets are reduced one after another with one pair of sort buffers of the largest
+// bucket's size. total_emitted receives the number of pairs.
+template <class K>
+static int pt2_resident(nqs_problem* p, Scratch& sc, const uint64_t* dets, const double* psi,
+                        int64_t nS, double E_var, int64_t B, const std::vector<int64_t>& nb, const int64_t* offs_all, const HashS& H,
+                        double* cS, double* dev_scalars, unsigned long long* next_dev, double* eint,
+                        bool with_int, size_t smem, int64_t* total_emitted, cudaStream_t s) {
+    const ProblemDev& P = p->d;
+    std::vector<int64_t> start(B);
+    int64_t at = 0, nmax = 1;
+    for (int64_t b = 0; b < B; ++b) {
+        start[b] = at;
+        at += (nb[b] + 15) & ~(int64_t)15;
+        if (nb[b] > nmax) nmax = nb[b];
+    }
+    Scratch rs(p, s);
+    K *keys, *keys2;
+    double *vals, *vals2;
+    int64_t* start_dev;
+    NQS_TRY(rs.get(&keys, at > 0 ? at : 1));
+    NQS_TRY(rs.get(&vals, at > 0 ? at : 1));
+    NQS_TRY(rs.get(&keys2, nmax));
+    NQS_TRY(rs.get(&vals2, nmax));
+    NQS_TRY(rs.get(&start_dev, B));
+    NQS_CK(cudaMemcpyAsync(start_dev, start.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           s));
+    const size_t smem_all = smem + (size_t)PT_WARPS * B * sizeof(uint32_t);
+    if (smem_all > 48 * 1024)
+        NQS_CK(cudaFuncSetAttribute(k_pt2_emit_all<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_all));
+    {
+        ProfScope prof_(PROF_PT2_EMIT, s);
+        k_pt2_emit_all<K><<<pt_grid(nS), PT_THREADS, smem_all, s>>>(
+            P, (const ulonglong2*)dets, psi, nS, (uint32_t)B, start_dev, offs_all, keys, vals);
+    }
+    NQS_CK_LAUNCH();
+    *total_emitted = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        *total_emitted += nb[b];
+        NQS_TRY(pt2_reduce<K>(p, keys + start[b], vals + start[b], keys2, vals2, nb[b], E_var, H,
+                              cS, dev_scalars, dev_scalars + 1 + 2 * b, next_dev + b, s));
+        NQS_TRY(pt2_internal_bucket(p, dets, psi, cS, nS, dev_scalars, E_var, B, b, eint,
+                                    with_int, s));
+    }
+    return NQS_OK;
+}
+
+static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                    double E_var, const nqs_csr* hss, const nqs_opts* opts, double* out,
+                    double* bucket_partials, cudaStream_t stream);
+
 extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
                        double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
                        nqs_stream_t stream) {
+    return pt2_impl(p, dets, psi, nS, E_var, nullptr, opts, out, bucket_partials,
+                    (cudaStream_t)stream);
+}
+
+extern "C" int nqs_pt2_hss(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                           double E_var, const nqs_csr* hss, const nqs_opts* opts, double* out,
+                           double* bucket_partials, nqs_stream_t stream) {
+    if (!hss || hss->n_rows != nS || !hss->row_ptr || !hss->col || !hss->val) return NQS_ERR_ARG;
+    return pt2_impl(p, dets, psi, nS, E_var, hss, opts, out, bucket_partials,
+                    (cudaStream_t)stream);
+}
+
+static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                    double E_var, const nqs_csr* hss, const nqs_opts* opts, double* out,
+                    double* bucket_partials, cudaStream_t stream) {
     if (!p || !dets || !psi || !out || nS <= 0) return NQS_ERR_ARG;
     if (((uintptr_t)dets) & 15) return NQS_ERR_ARG;
     if (nS >= ((int64_t)1 << 31)) return NQS_ERR_UNSUPPORTED;
-    cudaStream_t s = (cudaStream_t)stream;
+    cudaStream_t s = stream;
     if (opts && opts->buckets <= 0 && bucket_partials) return NQS_ERR_ARG;
     nqs_opts def;
     if (!opts) {
@@ -665,8 +820,12 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     // one counting pass for every bucket when the B x nS count table stays below 2 GiB
     const bool count_all = !screened && B > 1 && B <= PT_HIST_MAX &&
                            (double)nS * (double)B * sizeof(int64_t) <= 2147483648.0;
-    if (screened && opts->internal_pt2) {
-        // the screened emissions leave S out: the internal term takes H_SS psi from S itself
+    if (screened && opts->internal_pt2 && hss) {
+        // the screened emissions leave S out: the internal term takes the off-diagonal part of
+        // H_SS psi from the caller's H_SS
+        NQS_TRY(csr_spmv_offdiag(hss, psi, cS, s));
+    } else if (screened && opts->internal_pt2) {
+        // ... or from the connected sets of S, enumerated again
         if (smem > 48 * 1024)
             NQS_CK(cudaFuncSetAttribute(k_pt2_hss_psi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
@@ -695,7 +854,56 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
     const int64_t cap = opts->chunk > 0 ? opts->chunk : ((int64_t)1 << 32) - 1;
     const int kbits = 2 * P.norb;  // 32-bit, 64-bit or two-word keys
     int64_t total_emitted = 0;
-    for (int64_t b = 0; b < B; ++b) {
+    bool resident = false;
+    if (count_all) {
+        // every bucket's pairs resident at once when they fit: per-bucket offsets, then one
+        // emission pass instead of one decoding pass over all excitations per bucket
+        int64_t* offs_all;
+        int64_t* nb_dev;
+        NQS_TRY(sc.get(&offs_all, (size_t)nS * B));
+        NQS_TRY(sc.get(&nb_dev, B));
+        for (int64_t b = 0; b < B; ++b) {
+            Scratch ts(p, s);
+            NQS_TRY(scan_exclusive_i64(p, ts, cnt + (size_t)b * nS, offs_all + (size_t)b * nS,
+                                       nS, nb_dev + b, s));
+        }
+        std::vector<int64_t> nb(B);
+        NQS_CK(cudaMemcpyAsync(nb.data(), nb_dev, B * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+        double tot = 0.0, nmax = 0.0;
+        bool fits_sort = true;
+        for (int64_t b = 0; b < B; ++b) {
+            tot += (double)nb[b] + 16.0;
+            nmax = fmax(nmax, (double)nb[b]);
+            if (nb[b] > cap) fits_sort = false;
+        }
+        const double kb = kbits <= 32 ? 4.0 : (kbits <= 64 ? 8.0 : 16.0);
+        // pairs of all buckets + one pair of sort buffers + the largest bucket's unique arrays
+        const double need = tot * (kb + 8.0) + nmax * (kb + 8.0) + nmax * (kb + 16.0);
+        size_t fr = 0, totm = 0;
+        NQS_CK(cudaMemGetInfo(&fr, &totm));
+        uint64_t reserved = 0, used = 0;
+        NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+        NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        const double avail = (double)fr + (double)(reserved > used ? reserved - used : 0);
+        if (fits_sort && need <= 0.9 * avail) {
+            resident = true;
+            const bool wi = opts->internal_pt2 != 0;
+            int st = kbits <= 32
+                         ? pt2_resident<uint32_t>(p, sc, dets, psi, nS, E_var, B, nb, offs_all,
+                                                  H, cS, dev_scalars, next_dev, eint, wi, smem,
+                                                  &total_emitted, s)
+                     : kbits <= 64
+                         ? pt2_resident<uint64_t>(p, sc, dets, psi, nS, E_var, B, nb,
+                                                  offs_all, H, cS, dev_scalars, next_dev, eint, wi,
+                                                  smem, &total_emitted, s)
+                         : pt2_resident<Key128>(p, sc, dets, psi, nS, E_var, B, nb, offs_all,
+                                                H, cS, dev_scalars, next_dev, eint, wi, smem,
+                                                &total_emitted, s);
+            NQS_TRY(st);
+        }
+    }
+    for (int64_t b = 0; b < B && !resident; ++b) {
         int64_t n;
         if (B == 1 && !screened) {
             n = nS * P.nexc;
@@ -733,15 +941,8 @@ extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, 
                      : pt2_bucket<Key128>(p, dets, psi, nS, E_var, B, b, o, n, H, cS, dev_scalars,
                                           dev_scalars + 1 + 2 * b, next_dev + b, smem, eps, s);
         NQS_TRY(st);
-        if (opts->internal_pt2) {
-            k_pt2_internal<<<grid_for(nS, 256), 256, 0, s>>>(P, (const ulonglong2*)dets, psi, cS,
-                                                             nS, dev_scalars, E_var, (uint64_t)B,
-                                                             (uint64_t)b, eint);
-            NQS_CK_LAUNCH();
-            NQS_TRY(ksum_f64(p, sc, eint, nS, dev_scalars + 2 + 2 * b, s));
-        } else {
-            NQS_CK(cudaMemsetAsync(dev_scalars + 2 + 2 * b, 0, sizeof(double), s));
-        }
+        NQS_TRY(pt2_internal_bucket(p, dets, psi, cS, nS, dev_scalars, E_var, B, b, eint,
+                                    opts->internal_pt2 != 0, s));
     }
     std::vector<double> hs(1 + 2 * B);
     std::vector<unsigned long long> hn(B);

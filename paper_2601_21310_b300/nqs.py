@@ -73,6 +73,8 @@ EXPORTS = {
                                   C.c_void_p, C.c_void_p]),
     "nqs_pt2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p,
                           C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_pt2_hss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
+                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_hb_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_detset_free": (C.c_int, [C.c_void_p]),
@@ -429,18 +431,24 @@ def lanczos_min(csr: CSR, max_iters: int = 300, tol: float = 1e-13,
 
 
 def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, buckets: int = 1,
-        o: Opts | None = None, stream=None):
-    """Epstein-Nesbet PT2. Returns dict(ext, int, n_unique, n_emitted, partials[B,2])."""
+        o: Opts | None = None, stream=None, hss: "CSR | None" = None):
+    """Epstein-Nesbet PT2. Returns dict(ext, int, n_unique, n_emitted, partials[B,2]). With hss
+    (H_SS of the same dets from connections()) the screened internal term uses it."""
     import numpy as np
     dets = _dets(dets)
     psi = psi.contiguous()
     o = o or opts(buckets=buckets)
     out = np.zeros(5)
     parts = np.zeros(2 * max(o.buckets, 1))
-    _check(lib().nqs_pt2(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0], float(E), C.byref(o),
-                         out.ctypes.data_as(C.c_void_p),
-                         parts.ctypes.data_as(C.c_void_p) if o.buckets > 0 else None,
-                         _stream(stream)), "nqs_pt2")
+    outp = out.ctypes.data_as(C.c_void_p)
+    partp = parts.ctypes.data_as(C.c_void_p) if o.buckets > 0 else None
+    if hss is None:
+        _check(lib().nqs_pt2(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0], float(E),
+                             C.byref(o), outp, partp, _stream(stream)), "nqs_pt2")
+    else:
+        _check(lib().nqs_pt2_hss(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0], float(E),
+                                 C.byref(hss.s), C.byref(o), outp, partp, _stream(stream)),
+               "nqs_pt2_hss")
     return dict(ext=out[0], int=out[1], n_unique=int(out[2]), n_emitted=int(out[3]),
                 buckets=int(out[4]), partials=parts.reshape(-1, 2) if o.buckets > 0 else None)
 

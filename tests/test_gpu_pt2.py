@@ -175,3 +175,57 @@ def test_automatic_bucket_count():
         assert auto["buckets"] == 1 and auto["partials"] is None
         assert auto["n_unique"] == one["n_unique"]
         assert auto["ext"] == one["ext"] and auto["int"] == one["int"]
+
+
+@pytest.mark.parametrize("norb,n,nS,eps", [(10, 5, 1000, 1e-4), (16, 8, 2000, 1e-5),
+                                           (42, 24, 80, 1e-5)])
+def test_screened_pt2_with_hss_matches_oracle(norb, n, nS, eps):
+    """nqs_pt2_hss: the screened internal term from the caller's H_SS (one SpMV without the
+    diagonal) equals the oracle's and nqs_pt2's; the external sum is the same computation."""
+    need_gpu()
+    N = nqs()
+    h, eri, _ = synth.integrals(norb, 2 * norb, norb + 1, 3.0)
+    S = synth.select_S(norb, n, nS)
+    rng = np.random.default_rng(norb + 1)
+    psi = rng.standard_normal(len(S)) * np.exp(-rng.uniform(0, 6, len(S)))
+    psi /= np.linalg.norm(psi)
+    E = -30.0
+    P = N.Problem(norb, n, n, h, eri)
+    d, ps = to_dev(S), torch.from_numpy(psi).cuda()
+    csr = N.connections(P, d)
+    ref = O.pt2(norb, h, eri, S, psi, E, eps=eps)
+    got = N.pt2(P, d, ps, E, o=N.opts(eps_pt2=eps), hss=csr)
+    plain = N.pt2(P, d, ps, E, o=N.opts(eps_pt2=eps))
+    assert got["n_unique"] == ref["n_unique"] == plain["n_unique"]
+    assert got["ext"] == plain["ext"]
+    assert abs(got["ext"] - ref["ext"]) <= 1e-10 * abs(ref["ext"])
+    assert abs(got["int"] - ref["int"]) <= 1e-10 * abs(ref["int"])
+    assert abs(got["int"] - plain["int"]) <= 1e-12 * abs(plain["int"])
+    # unscreened: H_SS is not needed and the result is nqs_pt2's
+    a = N.pt2(P, d, ps, E, hss=csr)
+    b = N.pt2(P, d, ps, E)
+    assert a["ext"] == b["ext"] and a["int"] == b["int"]
+    # a matrix over other configurations is rejected
+    with pytest.raises(N.NQSError):
+        N.pt2(P, d[:-1], ps[:-1], E, o=N.opts(eps_pt2=eps), hss=csr)
+    csr.free()
+
+
+def test_pt2_per_bucket_passes_match_single_pass():
+    """More buckets than one counting pass covers (1030 > 1024): every bucket is counted and
+    emitted by its own pass over S. The unique count and the energies equal those of the
+    single-bucket pipeline and of the all-buckets-resident pipeline (B = 5)."""
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("tiny_n10")
+    P = problem_for(N, p)
+    psi, E = _psi_E(p)
+    d, ps = to_dev(p.S), torch.from_numpy(psi).cuda()
+    one = N.pt2(P, d, ps, E, buckets=1)
+    many = N.pt2(P, d, ps, E, buckets=1030)
+    five = N.pt2(P, d, ps, E, buckets=5)
+    for r in (many, five):
+        assert r["n_unique"] == one["n_unique"]
+        assert r["n_emitted"] == one["n_emitted"]
+        assert abs(r["ext"] - one["ext"]) < 1e-12 and abs(r["int"] - one["int"]) < 1e-12
+    assert abs(many["partials"][:, 0].sum() - many["ext"]) < 1e-12
