@@ -65,7 +65,7 @@ extern "C" int nqs_connections_noalloc(nqs_problem* p, const uint64_t* dets, int
     Scratch sc(arena, NQS_NOALLOC_SCRATCH_BYTES, s);
     if (validate) NQS_TRY(validate_dets(p, sc, dets, nS, true, s));
     HashS H;
-    NQS_TRY(hash_build(p, sc, dets, nS, &H, s));
+    NQS_TRY(hash_build(p, sc, dets, nS, &H, s, 4));  // load factor 1/4 within the static scratch
     size_t smem = conn_smem_bytes(p->d);
     if (smem > 48 * 1024) {
         NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,

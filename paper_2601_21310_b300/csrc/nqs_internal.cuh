@@ -217,8 +217,10 @@ __global__ void k_conn_fill(ProblemDev P, HashS H, const ulonglong2* __restrict_
 size_t conn_smem_bytes(const ProblemDev& P);
 unsigned conn_grid_size(int64_t nS);
 
+// slots_per_det > 0 fixes the capacity to the next power of two >= slots_per_det * nS (the
+// allocation-free path, whose scratch is bounded); 0 takes the default sparse table
 int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, HashS* out,
-               cudaStream_t s);
+               cudaStream_t s, int slots_per_det = 0);
 // screened PT2 emission pass (hb.cu): counts per det when cnt != null, else the (key, H psi)
 // pairs at offs; keys are uint32 / uint64 / Key128 by 2 norb
 int hb_pt2_pass(nqs_problem* p, const HashS& H, const uint64_t* dets, const double* psi,

@@ -355,11 +355,13 @@ __global__ void k_hash_keys(const ulonglong2* S, const int32_t* idx, ulonglong2*
 }
 
 int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, HashS* out,
-               cudaStream_t s) {
+               cudaStream_t s, int slots_per_det) {
     // load factor <= 1/16 up to 2^22 configurations, 1/8 up to 2^26, else 1/4: a warp's probe
     // loop runs as long as its longest probe sequence, so short runs of occupied slots matter
     // more than memory (the 2-byte fingerprints of 2^26 slots take 128 MiB, about the L2 size)
-    const uint64_t load = nS <= ((int64_t)1 << 22) ? 16 : (nS <= ((int64_t)1 << 26) ? 8 : 4);
+    const uint64_t load = slots_per_det > 0 ? (uint64_t)slots_per_det
+                          : nS <= ((int64_t)1 << 22) ? 16
+                          : (nS <= ((int64_t)1 << 26) ? 8 : 4);
     uint64_t cap = 1024;
     while (cap < load * (uint64_t)nS) cap <<= 1;
     ulonglong2* keys;
