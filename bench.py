@@ -159,13 +159,13 @@ class ClockSampler:
 # roofline bookkeeping: algorithmic work per launch of each instrumented kernel family
 # ------------------------------------------------------------------------------------------
 def algorithmic_work(name, wl, nS, nexc, nnz, n_emit, n_unique, net_flops, buckets=1,
-                     launches=1):
+                     launches=1, screened=False):
     """(bound, amount per launch, unit) - bytes for HBM-bound kernels, FLOP for GEMMs. With B
     PT2 buckets each sort and reduction launch handles one bucket: 1/B of the emitted pairs and
     unique terms; the emission runs once for all buckets or once per bucket (`launches` per
     step)."""
     kb = 4.0 if 2 * wl.norb <= 32 else (8.0 if 2 * wl.norb <= 64 else 16.0)  # PT2 key width
-    if name == "pt2_emit":     # write key+value per emission, read S and psi
+    if name == "pt2_emit" and not screened:  # write key+value per emission, read S and psi
         return "hbm", ((kb + 8.0) * n_emit + 24.0 * nS) / max(1, launches), "B"
     n_emit = n_emit / max(1, buckets)
     n_unique = n_unique / max(1, buckets)
@@ -181,7 +181,8 @@ def algorithmic_work(name, wl, nS, nexc, nnz, n_emit, n_unique, net_flops, bucke
         return "hbm", 12.0 * nnz + 8.0 * 3 * nS, "B"
     if name == "gemm":
         return "tensor", net_flops, "FLOP"
-    # enumeration, probing, LU and the H_x'x' loop are issue-bound: no byte or FLOP roofline
+    # enumeration, probing, the screened traversal, LU and the H_x'x' loop are issue-bound: no
+    # byte or FLOP roofline
     return "alu", 0.0, None
 
 
@@ -338,7 +339,7 @@ def run_nqs(args, ws, rank, local):
         per_launch_flops = total_gemm_flops / max(1, prof[k][1] / args.steps)
         return algorithmic_work(k, wl, nS, nexc, info["nnz"], info["n_emit"], info["n_unique"],
                                 per_launch_flops, max(1, info["buckets"]),
-                                max(1, prof[k][1] / args.steps))
+                                max(1, prof[k][1] / args.steps), args.eps_pt2 > 0)
 
     # the roofline is reported for the largest kernel with a byte or FLOP bound; the largest
     # kernel overall is named beside it when it is an issue-bound one
