@@ -380,13 +380,20 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
             const int je = lane < L ? SEG_ITEMS : (lane == L ? jL : 0);  // active: [ja, je)
             const unsigned am = (je >= SEG_ITEMS ? 0xffu : ((1u << je) - 1u)) & ~((1u << ja) - 1u);
             hm &= am;
-            // lane pass: running sums along runs, one FP64 add per element
-            double run = 0.0, tv[SEG_ITEMS];
+            // lane pass: running sums along runs, one FP64 add per element; fsum is the sum of
+            // the lane's first segment (its elements before the lane's first head)
+            double run = 0.0, tv[SEG_ITEMS], fsum = 0.0;
 #pragma unroll
             for (int j = 0; j < SEG_ITEMS; ++j) {
-                if ((am >> j) & 1u) run = ((hm >> j) & 1u) ? v[j] : run + v[j];
+                if ((hm >> j) & 1u) {
+                    if ((hm & ((1u << j) - 1u)) == 0u) fsum = run;
+                    run = v[j];
+                } else if ((am >> j) & 1u) {
+                    run = run + v[j];
+                }
                 tv[j] = run;
             }
+            if (hm == 0u) fsum = run;
             const bool act = am != 0;
             const bool lh = hm != 0;
             const double lsum = act ? run : 0.0;
@@ -436,6 +443,8 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
             if (je < SEG_ITEMS) end_after = true;
             else if (lane < 31) end_after = next_first_ends != 0;
             else end_after = (b + W >= n) || (knext != kk[SEG_ITEMS - 1]);
+            // the first segment's run continues one entering the lane: one add per lane
+            const double first_total = inc + fsum;
 #pragma unroll
             for (int j = 0; j < SEG_ITEMS; ++j) {
                 if ((am >> j) & 1u) {
@@ -443,7 +452,7 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
                     if (tail) {
                         const unsigned upto = hm & ((2u << j) - 1u);  // heads at or before j
                         const uint32_t r = ridx0 + hpre + (uint32_t)__popc(upto) - 1u;
-                        cU[r] = upto ? tv[j] : inc + tv[j];
+                        cU[r] = upto ? tv[j] : first_total;
                         keyU[r] = kk[j];
                     }
                 }
