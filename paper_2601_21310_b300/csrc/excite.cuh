@@ -329,6 +329,85 @@ __device__ __forceinline__ void step_exc(const ProblemDev& P, const PairTables& 
     x.b2 = B ^ (1ull << j) ^ (1ull << b);
 }
 
+// Alpha-beta doubles from per-configuration tables (the emission kernels): the beta single of
+// index lb = xb * mb + yb as its excited string and its ERI column offset j * norb + b with the
+// sign of the beta move in bit 31; the alpha single's string, ERI row offset
+// (i * norb + a) * norb^2 and sign stay in registers while the alpha index stays. Element and
+// key are those of decode_exc / exc_element bit for bit: eri[(((i n + a) n + j) n + b)] with the
+// product of the two single signs.
+struct AbTab {
+    uint64_t* bmask;  // [sB]
+    uint32_t* bco;    // [sB]
+};
+__host__ __device__ __forceinline__ size_t ab_tab_bytes(const ProblemDev& P) {
+    return ((size_t)P.sB * 12 + 15) & ~(size_t)15;
+}
+__device__ __forceinline__ AbTab ab_tab_at(uint8_t* base, const ProblemDev& P) {
+    AbTab t;
+    t.bmask = (uint64_t*)base;
+    t.bco = (uint32_t*)(base + (size_t)P.sB * 8);
+    return t;
+}
+// lane-parallel fill for configuration (., B) with occupation lists c; ends with __syncwarp
+__device__ __forceinline__ void fill_ab_tab(const ProblemDev& P, const DetCtx& c, uint64_t B,
+                                            AbTab t, int lane) {
+    const int n = P.norb;
+    for (int lb = lane; lb < P.sB; lb += 32) {
+        const int xb = lb / P.mb, yb = lb - xb * P.mb;
+        const int j = c.occB[xb], b = c.virB[yb];
+        t.bmask[lb] = B ^ (1ull << j) ^ (1ull << b);
+        t.bco[lb] = (uint32_t)(j * n + b) | (exc_sign(B, j, b) < 0 ? 0x80000000u : 0u);
+    }
+    __syncwarp();
+}
+struct AbState {
+    int on;            // located yet
+    int xa, ya, lb;    // alpha hole / particle positions, beta single index
+    uint64_t a2;       // the alpha string
+    uint32_t ro, sa;   // ERI row offset, alpha sign in bit 31
+};
+__device__ __forceinline__ void ab_load_alpha(const ProblemDev& P, const DetCtx& c, uint64_t A,
+                                              AbState& s) {
+    const int n = P.norb, i = c.occA[s.xa], a = c.virA[s.ya];
+    s.a2 = A ^ (1ull << i) ^ (1ull << a);
+    s.ro = (uint32_t)((i * n + a) * n * n);
+    s.sa = exc_sign(A, i, a) < 0 ? 0x80000000u : 0u;
+}
+// the alpha-beta excitation of canonical offset l = e - o4 (first call) or 32 further on
+__device__ __forceinline__ void ab_fast_step(const ProblemDev& P, const DetCtx& c, uint64_t A,
+                                             uint32_t l, AbState& s) {
+    if (!s.on) {
+        const uint32_t sB = (uint32_t)P.sB;
+        const uint32_t la = l / sB;
+        s.lb = (int)(l - la * sB);
+        s.xa = (int)(la / (uint32_t)P.ma);
+        s.ya = (int)(la - (uint32_t)s.xa * (uint32_t)P.ma);
+        s.on = 1;
+        ab_load_alpha(P, c, A, s);
+        return;
+    }
+    s.lb += 32;
+    if (s.lb >= P.sB) {
+        do {
+            s.lb -= P.sB;
+            if (++s.ya == P.ma) {
+                s.ya = 0;
+                ++s.xa;
+            }
+        } while (s.lb >= P.sB);
+        ab_load_alpha(P, c, A, s);
+    }
+}
+// H_x'x (signed) of the current alpha-beta excitation and its beta string
+__device__ __forceinline__ double ab_fast_element(const ProblemDev& P, const AbTab& t,
+                                                  const AbState& s, uint64_t& b2) {
+    b2 = t.bmask[s.lb];
+    const uint32_t co = t.bco[s.lb];
+    const double v = __ldg(&P.eri[s.ro + (co & 0x7fffffffu)]);
+    return __longlong_as_double(__double_as_longlong(v) ^
+                                ((long long)((s.sa ^ co) >> 31) << 63));
+}
+
 __device__ __forceinline__ double eri_at(const ProblemDev& P, int p, int q, int r, int s) {
     const int n = P.norb;
     return __ldg(&P.eri[(((size_t)p * n + q) * n + r) * n + s]);

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_count_all(ProblemDev P,
 // offs == nullptr: every excitation is emitted at det * nexc + e (B = 1). With B > 1 only the
 // key is decoded first; the full decode and the element are computed for in-bucket ones.
 template <class K>
-__global__ void __launch_bounds__(PT_THREADS, 6) k_pt2_emit(ProblemDev P,
+__global__ void __launch_bounds__(PT_THREADS, 4) k_pt2_emit(ProblemDev P,
                                                           const ulonglong2* __restrict__ S,
                                                           const double* __restrict__ psi,
                                                           int64_t nS, uint64_t B, uint64_t bucket,
@@ -109,6 +109,9 @@ __global__ void __launch_bounds__(PT_THREADS, 6) k_pt2_emit(ProblemDev P,
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    const AbTab abt = ab_tab_at(smem + pair_table_bytes(P) + PT_WARPS * sizeof(DetCtx) +
+                                    (threadIdx.x >> 5) * ab_tab_bytes(P),
+                                P);
     __shared__ uint32_t queue[PT_WARPS * 64];
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -123,21 +126,36 @@ __global__ void __launch_bounds__(PT_THREADS, 6) k_pt2_emit(ProblemDev P,
         if (B == 1) {
             const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
                            o4 = o3 + (uint32_t)P.dBB;
+            fill_ab_tab(P, *ctx, x.y, abt, lane);
             EnumPos q;
             q.cls = -1;
+            AbState ab;
+            ab.on = 0;
             for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
                 const uint32_t e = r0 + lane;
                 const bool take = e < nexc;
                 const unsigned m = __ballot_sync(FULL_MASK, take);
                 if (take) {
-                    Exc ex;
-                    step_exc(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, ex);
+                    uint64_t a2, b2;
+                    double hv;
+                    if (e >= o4) {  // alpha-beta doubles from the tables
+                        ab_fast_step(P, *ctx, x.x, e - o4, ab);
+                        hv = ab_fast_element(P, abt, ab, b2);
+                        a2 = ab.a2;
+                    } else {
+                        Exc ex;
+                        step_exc(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, ex);
+                        a2 = ex.a2;
+                        b2 = ex.b2;
+                        hv = exc_element(P, *ctx, ex);
+                    }
                     const int64_t pos = run + __popc(m & lt);
-                    keys[pos] = key_make<K>(ex.a2, ex.b2, norb);
-                    vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
+                    keys[pos] = key_make<K>(a2, b2, norb);
+                    vals[pos] = __dmul_rn(hv, py);
                 }
                 run += __popc(m);
             }
+            __syncwarp();  // the tables are rewritten for the next configuration
         } else {
             // Only the key is decoded for every excitation. In-bucket indices are appended, in
             // canonical order, to a per-warp queue; each time it holds 32 the whole warp decodes
@@ -208,7 +226,11 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit_all(ProblemDev P,
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
-    uint32_t* ctr = (uint32_t*)(smem + pair_table_bytes(P) + PT_WARPS * sizeof(DetCtx)) +
+    const AbTab abt = ab_tab_at(smem + pair_table_bytes(P) + PT_WARPS * sizeof(DetCtx) +
+                                    (threadIdx.x >> 5) * ab_tab_bytes(P),
+                                P);
+    uint32_t* ctr = (uint32_t*)(smem + pair_table_bytes(P) +
+                                PT_WARPS * (sizeof(DetCtx) + ab_tab_bytes(P))) +
                     (threadIdx.x >> 5) * B;
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
@@ -221,17 +243,31 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit_all(ProblemDev P,
         const ulonglong2 x = S[det];
         for (uint32_t k = lane; k < B; k += 32) ctr[k] = 0;
         fill_ctx(P, x.x, x.y, ctx, lane);  // ends with __syncwarp
+        fill_ab_tab(P, *ctx, x.y, abt, lane);
         const double py = psi[det];
         EnumPos q;
         q.cls = -1;
+        AbState ab;
+        ab.on = 0;
         for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
             const uint32_t e = r0 + lane;
             const bool take = e < nexc;
-            Exc ex;
+            uint64_t a2 = 0, b2 = 0;
+            double hv = 0.0;
             uint32_t b = 0xffffffffu;
             if (take) {
-                step_exc(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, ex);
-                b = (uint32_t)(det_hash(ex.a2, ex.b2) % B);
+                if (e >= o4) {  // alpha-beta doubles from the tables
+                    ab_fast_step(P, *ctx, x.x, e - o4, ab);
+                    hv = ab_fast_element(P, abt, ab, b2);
+                    a2 = ab.a2;
+                } else {
+                    Exc ex;
+                    step_exc(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, ex);
+                    a2 = ex.a2;
+                    b2 = ex.b2;
+                    hv = exc_element(P, *ctx, ex);
+                }
+                b = (uint32_t)(det_hash(a2, b2) % B);
             }
             const unsigned peers = __match_any_sync(FULL_MASK, b);
             uint32_t base = 0;
@@ -239,8 +275,8 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit_all(ProblemDev P,
                 base = ctr[b];
                 const int64_t pos = start[b] + offs[(int64_t)b * nS + det] + base +
                                     __popc(peers & lt);
-                keys[pos] = key_make<K>(ex.a2, ex.b2, norb);
-                vals[pos] = __dmul_rn(exc_element(P, *ctx, ex), py);
+                keys[pos] = key_make<K>(a2, b2, norb);
+                vals[pos] = __dmul_rn(hv, py);
             }
             __syncwarp();
             if (take && lane == __ffs(peers) - 1) ctr[b] = base + __popc(peers);
@@ -551,6 +587,10 @@ __global__ void k_pt2_internal(ProblemDev P, const ulonglong2* __restrict__ S,
     }
 }
 
+// the emission kernels also hold each warp's alpha-beta tables
+static size_t pt_smem_emit(const ProblemDev& P) {
+    return pair_table_bytes(P) + PT_WARPS * (sizeof(DetCtx) + ab_tab_bytes(P));
+}
 static size_t pt_smem(const ProblemDev& P) {
     return pair_table_bytes(P) + PT_WARPS * sizeof(DetCtx);
 }
@@ -651,7 +691,7 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
     } else {
         {
             ProfScope prof_(PROF_PT2_EMIT, s);
-            k_pt2_emit<K><<<pt_grid(nS), PT_THREADS, smem, s>>>(
+            k_pt2_emit<K><<<pt_grid(nS), PT_THREADS, pt_smem_emit(P), s>>>(
                 P, (const ulonglong2*)dets, psi, nS, (uint64_t)B, (uint64_t)b, offs, keys, vals);
         }
         NQS_CK_LAUNCH();
@@ -706,7 +746,8 @@ static int pt2_resident(nqs_problem* p, Scratch& sc, const uint64_t* dets, const
     NQS_TRY(rs.get(&start_dev, B));
     NQS_CK(cudaMemcpyAsync(start_dev, start.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice,
                            s));
-    const size_t smem_all = smem + (size_t)PT_WARPS * B * sizeof(uint32_t);
+    const size_t smem_all = pt_smem_emit(P) + (size_t)PT_WARPS * B * sizeof(uint32_t);
+    (void)smem;
     if (smem_all > 48 * 1024)
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit_all<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem_all));
@@ -769,16 +810,19 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
     NQS_TRY(hash_build(p, sc, dets, nS, &H, s));
     const ProblemDev& P = p->d;
     size_t smem = pt_smem(P);
-    if (smem > 48 * 1024) {
+    if (smem > 48 * 1024)
         NQS_CK(cudaFuncSetAttribute(k_pt2_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
+    const size_t sme = pt_smem_emit(P);
+    if (sme > 48 * 1024) {
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit<uint32_t>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sme));
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit<uint64_t>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sme));
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit<Key128>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sme));
     }
+
     int64_t* pre_offs = nullptr;  // offsets of a screened single-bucket count, when one ran
     int64_t pre_total = 0;
     if (B <= 0) {
