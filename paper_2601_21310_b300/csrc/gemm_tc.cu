@@ -203,6 +203,10 @@ __device__ __forceinline__ void epilogue32_tma(const TcArgs& a, const U& w, int 
     }
     const bool f32 = a.splits > 1 || !a.c_bf16;
     const bool do_c = a.splits > 1 || a.C;
+    // the stores issued from this buffer by the previous chunk must have read it; waiting only
+    // now lets that read overlap this chunk's accumulator load and epilogue arithmetic
+    if (lane == 0) bulk_wait_read0();
+    __syncwarp();
     if (do_c) {
         if (f32) {
             float4* dst = (float4*)(stage + lane * 128);
@@ -239,7 +243,6 @@ __device__ __forceinline__ void epilogue32_tma(const TcArgs& a, const U& w, int 
         else if (a.C) tma_store_2d(mapC, stage, nb, rowbase);
         if (a.CT) tma_store_2d(mapCT, stT, rowbase, nb);
         bulk_commit();
-        bulk_wait_read0();  // the buffer is rewritten by the next chunk
     }
     __syncwarp();
 }
