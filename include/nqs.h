@@ -55,7 +55,7 @@ typedef struct CUstream_st* nqs_stream_t; /* the same object as cudaStream_t */
 #define NQS_ERR_OOM (-5)           /* device allocation failed */
 #define NQS_ERR_CUDA (-6)          /* a CUDA runtime call or a kernel launch failed */
 #define NQS_ERR_TIMEOUT (-7)       /* a bounded device-side wait gave up */
-#define NQS_ERR_UNSUPPORTED (-8)   /* valid request outside what this build implements */
+#define NQS_ERR_UNSUPPORTED (-8)   /* valid request outside what the library implements */
 
 /* ---- precision forms -------------------------------------------------------------------- */
 #define NQS_FP64 0   /* plain form: FP64 parameters, FP64 GEMMs, FP64 LU */
