@@ -294,7 +294,7 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 // order, and the tile is written out digit run by digit run (coalesced). The wait on the
 // mbarrier is bounded; on timeout the error word is set and the tile is left unwritten.
 template <class K>
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__ kin,
+__global__ void __launch_bounds__(RS_THREADS, 3) k_rs_scatter(const K* __restrict__ kin,
                                                             const double* __restrict__ vin,
                                                             K* __restrict__ kout,
                                                             double* __restrict__ vout, int64_t n,
@@ -308,8 +308,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     K* sk = (K*)(sv + RS_TILE);                // [RS_TILE] keys, input order
     uint16_t* perm = (uint16_t*)(sk + RS_TILE);  // [RS_TILE] input index at each sorted slot
     __shared__ uint32_t whist[RS_WARPS][256];
-    __shared__ uint32_t dstart[256];
-    __shared__ uint32_t goff[256];
+    __shared__ uint32_t gdelta[256];  // global position of digit d's run minus its tile start
     __shared__ uint32_t warp_tot[RS_THREADS / 32];
     __shared__ uint32_t total;
     __shared__ __align__(8) uint64_t bar;
@@ -340,7 +339,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
         }
     }
     for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_THREADS) (&whist[0][0])[i] = 0;
-    goff[threadIdx.x] = offs[(int64_t)threadIdx.x * T + blockIdx.x];
+    // this tile's global offset of digit threadIdx.x (read while the tile is in flight)
+    const uint32_t goff = offs[(int64_t)threadIdx.x * T + blockIdx.x];
     if (!bulk) {
         for (int i = threadIdx.x; i < tn; i += RS_THREADS) {
             sk[i] = kin[tbase + i];
@@ -372,46 +372,71 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const K* __restrict__
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wb = warp * (RS_ITEMS * 32);
+    // Ranking. The digits and the match masks of all items are independent of the running
+    // per-warp counts, so they are formed first (independent shared loads and matches in
+    // flight together); only the count update below is a chain, item by item (elements in
+    // ascending index order: warp, item, lane). Digit 256 marks a slot past the tile's end.
+    uint32_t dg[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) {
+        const int li = wb + k * 32 + lane;
+        dg[k] = li < tn ? key_digit(sk[li], shift) : 256u;
+    }
     uint32_t rank[RS_ITEMS];
+#pragma unroll
+    for (int k = 0; k < RS_ITEMS; ++k) rank[k] = __match_any_sync(FULL_MASK, dg[k]);
     const unsigned lt = lanemask_lt();
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-        const int li = wb + k * 32 + lane;
-        const bool v = li < tn;
-        const uint32_t d = v ? key_digit(sk[li], shift) : 256u;
-        const unsigned peers = __match_any_sync(FULL_MASK, d);
-        const uint32_t old = v ? whist[warp][d] : 0u;
+        const unsigned peers = rank[k];
+        const bool v = dg[k] < 256u;
+        const uint32_t old = v ? whist[warp][dg[k]] : 0u;
         __syncwarp();
-        if (v && lane == __ffs(peers) - 1) whist[warp][d] = old + __popc(peers);
+        if (v && lane == __ffs(peers) - 1) whist[warp][dg[k]] = old + __popc(peers);
         __syncwarp();
-        rank[k] = old + __popc(peers & lt);
+        rank[k] = ((old + __popc(peers & lt)) << 9) | dg[k];  // rank in warp, digit
     }
     __syncthreads();
+    // thread d: the tile's count of digit d, the warps' exclusive prefixes over it, the start of
+    // digit d's run in the tile; each warp's slot base for digit d is folded into whist
     uint32_t cnt = 0;
+    uint32_t wpre[RS_WARPS];
 #pragma unroll
     for (int w = 0; w < RS_WARPS; ++w) {
-        const uint32_t c = whist[w][threadIdx.x];
-        whist[w][threadIdx.x] = cnt;
-        cnt += c;
+        wpre[w] = cnt;
+        cnt += whist[w][threadIdx.x];
     }
-    dstart[threadIdx.x] = block_exclusive_scan<uint32_t>(cnt, warp_tot, &total);
+    const uint32_t dstart = block_exclusive_scan<uint32_t>(cnt, warp_tot, &total);
+#pragma unroll
+    for (int w = 0; w < RS_WARPS; ++w) whist[w][threadIdx.x] = dstart + wpre[w];
+    gdelta[threadIdx.x] = goff - dstart;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < RS_ITEMS; ++k) {
-        const int li = wb + k * 32 + lane;
-        if (li < tn) {
-            const uint32_t d = key_digit(sk[li], shift);
-            perm[dstart[d] + whist[warp][d] + rank[k]] = (uint16_t)li;
-        }
+        const uint32_t d = rank[k] & 511u;
+        if (d < 256u) perm[whist[warp][d] + (rank[k] >> 9)] = (uint16_t)(wb + k * 32 + lane);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < tn; i += RS_THREADS) {
-        const int j = perm[i];
-        const K kk = sk[j];
-        const uint32_t d = key_digit(kk, shift);
-        const uint32_t gp = goff[d] + (uint32_t)i - dstart[d];
-        kout[gp] = kk;
-        vout[gp] = sv[j];
+    // write-out in sorted-slot order: consecutive threads store consecutive elements of each
+    // digit run; slot i of digit d goes to gdelta[d] + i (unsigned wrap-around is exact)
+    if (bulk) {
+#pragma unroll
+        for (int k = 0; k < RS_ITEMS; ++k) {
+            const int i = k * RS_THREADS + threadIdx.x;
+            const int j = perm[i];
+            const K kk = sk[j];
+            const uint32_t gp = gdelta[key_digit(kk, shift)] + (uint32_t)i;
+            kout[gp] = kk;
+            vout[gp] = sv[j];
+        }
+    } else {
+        for (int i = threadIdx.x; i < tn; i += RS_THREADS) {
+            const int j = perm[i];
+            const K kk = sk[j];
+            const uint32_t gp = gdelta[key_digit(kk, shift)] + (uint32_t)i;
+            kout[gp] = kk;
+            vout[gp] = sv[j];
+        }
     }
 }
 
