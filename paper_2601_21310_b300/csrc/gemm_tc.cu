@@ -207,14 +207,20 @@ __device__ __forceinline__ void epilogue32_tma(const TcArgs& a, const U& w, int 
     // now lets that read overlap this chunk's accumulator load and epilogue arithmetic
     if (lane == 0) bulk_wait_read0();
     __syncwarp();
+    // The staging rows are written in the layout of the store map's swizzle (128-byte swizzle
+    // for 128-byte FP32 rows, 64-byte swizzle for 64-byte bf16 rows: the 16-byte chunk index is
+    // XORed with address bits 7.. of the row), so the 16-byte stores of the eight lanes of a
+    // quarter-warp fall in eight different bank groups instead of one or two.
     if (do_c) {
         if (f32) {
             float4* dst = (float4*)(stage + lane * 128);
+            const int sw = lane & 7;
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                dst[q ^ sw] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         } else {
             uint4* dst = (uint4*)(stage + lane * 64);
+            const int sw = (lane >> 1) & 3;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 uint4 pk;
@@ -224,7 +230,7 @@ __device__ __forceinline__ void epilogue32_tma(const TcArgs& a, const U& w, int 
                     __nv_bfloat162 h2 = __floats2bfloat162_rn(v[q * 8 + 2 * t], v[q * 8 + 2 * t + 1]);
                     wd[t] = *(uint32_t*)&h2;
                 }
-                dst[q] = pk;
+                dst[q ^ sw] = pk;
             }
         }
     }
@@ -558,11 +564,12 @@ int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64
     return NQS_OK;
 }
 
-// plain (unswizzled) store map with a 32 x 32 box: dims innermost first, strides in bytes of
-// the outer dims; false when the layout cannot take TMA (alignment) — the caller then stores
-// directly
+// store map with a 32 x 32 box and the given swizzle of the shared-memory side: dims innermost
+// first, strides in bytes of the outer dims; false when the layout cannot take TMA (alignment) —
+// the caller then stores directly
 bool make_store_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, int esize, int rank,
-                    const cuuint64_t* dims, const cuuint64_t* strides) {
+                    const cuuint64_t* dims, const cuuint64_t* strides,
+                    CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE) {
     if (get_encoder() != NQS_OK || ((uintptr_t)base & 15)) return false;
     for (int i = 0; i < rank - 1; ++i)
         if (strides[i] % 16) return false;
@@ -570,7 +577,7 @@ bool make_store_map(CUtensorMap* m, const void* base, CUtensorMapDataType dt, in
     cuuint32_t es[3] = {1, 1, 1};
     (void)esize;
     CUresult r = g_encode(m, dt, rank, (void*)base, dims, strides, box, es,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -649,7 +656,8 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
     if (splits > 1) {
         const cuuint64_t dims[3] = {(cuuint64_t)g.N, (cuuint64_t)g.M, (cuuint64_t)splits};
         const cuuint64_t str[2] = {(cuuint64_t)g.N * 4, (cuuint64_t)g.M * g.N * 4};
-        tma = make_store_map(&tp, a.partial, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 3, dims, str);
+        tma = make_store_map(&tp, a.partial, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 3, dims, str,
+                             CU_TENSOR_MAP_SWIZZLE_128B);
     } else {
         if (g.C) {
             const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
@@ -657,7 +665,8 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
             tma = make_store_map(&tc, g.C,
                                  g.c_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                                 g.c_bf16 ? 2 : 4, 2, dims, str);
+                                 g.c_bf16 ? 2 : 4, 2, dims, str,
+                                 g.c_bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
         }
         if (tma && g.CT) {
             tma = g.C == nullptr || g.c_bf16;  // one 4 KB staging buffer: bf16 C + bf16 CT
