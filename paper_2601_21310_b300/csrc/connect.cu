@@ -100,6 +100,221 @@ __global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count(ProblemDev P, Ha
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Pass 1 with an index of S by alpha string (nqs_connections). S is sorted by (a, b), so the
+// configurations of S that share an alpha string a' form one contiguous run S[start, start +
+// cnt). An alpha-beta double (i_a -> a_a, j_b -> b_b) of x = (A, B) leads to x' = (a', b') with
+// a' = A's single (i_a, a_a); x' is in S exactly when a' has a run and b' is among the run's beta
+// strings. For each alpha single the warp therefore looks a' up once in the alpha index and
+//   - skips the whole block of beta singles when a' is not an alpha string of S;
+//   - scans a short run (cnt <= 4 x beta singles): a run member's beta string b_y is a beta
+//     single of B exactly when popcount(B ^ b_y) == 2, and the two differing bits give j_b and
+//     b_b, hence the canonical index;
+//   - otherwise probes the hash of S for each beta single, as the plain pass does.
+// Every index resolves to the same hit or miss as a lookup of x' in S, so the ballot words are
+// bit for bit those of k_conn_count. The singles and same-spin doubles (indices below the
+// alpha-beta block) go through the plain pass unchanged. The alpha-beta ballot words are
+// cleared first and hits are set with atomicOr (order-free).
+// ------------------------------------------------------------------------------------------
+struct AlphaIdx {
+    const uint64_t* key;  // [cap] alpha string, 0 = empty (alpha strings of S are nonzero)
+    const int2* run;      // [cap] {start in S, length}
+    uint64_t mask;        // cap - 1
+};
+
+__device__ __forceinline__ uint64_t alpha_slot(uint64_t a, uint64_t mask) {
+    uint64_t h = a * 0x9E3779B97F4A7C15ull;
+    return (h ^ (h >> 29)) & mask;
+}
+
+// one thread per configuration; the first of each alpha run inserts (a, start, length)
+__global__ void k_alpha_index(const ulonglong2* __restrict__ S, int64_t nS, uint64_t* key,
+                              int2* run, uint64_t mask) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nS;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = S[i].x;
+        if (i > 0 && S[i - 1].x == a) continue;
+        int64_t lo = i + 1, hi = nS;  // first position after the run (S ascending by a)
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (S[mid].x == a) lo = mid + 1;
+            else hi = mid;
+        }
+        uint64_t slot = alpha_slot(a, mask);
+        for (uint64_t it = 0; it <= mask; ++it) {
+            if (atomicCAS((unsigned long long*)&key[slot], 0ull, (unsigned long long)a) == 0ull) {
+                run[slot] = make_int2((int)i, (int)(lo - i));
+                break;
+            }
+            slot = (slot + 1) & mask;
+        }
+    }
+}
+
+__device__ __forceinline__ bool alpha_find(const AlphaIdx& X, uint64_t a, int2& r) {
+    uint64_t slot = alpha_slot(a, X.mask);
+    for (uint64_t it = 0; it <= X.mask; ++it) {
+        const uint64_t k = __ldg(&X.key[slot]);
+        if (k == a) {
+            r = __ldg(&X.run[slot]);
+            return true;
+        }
+        if (k == 0ull) return false;
+        slot = (slot + 1) & X.mask;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count_ab(ProblemDev P, HashS H,
+                                                                 AlphaIdx X,
+                                                                 const ulonglong2* __restrict__ S,
+                                                                 int64_t nS, int64_t* rowcnt,
+                                                                 uint32_t* __restrict__ bits) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const uint32_t nexc = (uint32_t)P.nexc;
+    const uint32_t nwords = (nexc + 31) / 32;
+    const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                   o4 = o3 + (uint32_t)P.dBB;
+    const uint32_t sA = (uint32_t)P.sA, sB = (uint32_t)P.sB;
+    const uint32_t scan_max = 4 * sB;
+    for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * CONN_WARPS) {
+        ulonglong2 x = S[det];
+        fill_ctx(P, x.x, x.y, ctx, lane);
+        uint32_t* wb = bits + det * nwords;
+        int cnt = 0;
+        // singles and same-spin doubles: the plain pass over indices [0, o4)
+        EnumPos q;
+        q.cls = -1;
+        for (uint32_t r0 = 0; r0 < o4; r0 += 64) {
+            const uint32_t e0 = r0 + lane, e1 = e0 + 32;
+            const bool v0 = e0 < o4, v1 = e1 < o4;
+            uint64_t a0 = 0, b0 = 0, a1 = 0, b1 = 0, s0 = 0, s1 = 0;
+            uint16_t f0 = 0, f1 = 0, g0 = 0, g1 = 0;
+            if (v0) {
+                step_key(P, T, *ctx, x.x, x.y, e0, o2, o3, o4, q, a0, b0);
+                const uint64_t hh = s_hash(a0, b0);
+                s0 = hash_slot(hh, H.mask);
+                f0 = hash_fingerprint(hh);
+                g0 = __ldg(&H.fp[s0]);
+            }
+            if (v1) {
+                step_key(P, T, *ctx, x.x, x.y, e1, o2, o3, o4, q, a1, b1);
+                const uint64_t hh = s_hash(a1, b1);
+                s1 = hash_slot(hh, H.mask);
+                f1 = hash_fingerprint(hh);
+                g1 = __ldg(&H.fp[s1]);
+            }
+            bool h0 = false, h1 = false;
+            for (uint64_t it = 0; v0 && g0 != 0 && it <= H.mask; ++it) {
+                if (g0 == f0) {
+                    const ulonglong2 k = __ldg(&H.keys[s0]);
+                    if (k.x == a0 && k.y == b0) {
+                        h0 = true;
+                        break;
+                    }
+                }
+                s0 = (s0 + 1) & H.mask;
+                g0 = __ldg(&H.fp[s0]);
+            }
+            for (uint64_t it = 0; v1 && g1 != 0 && it <= H.mask; ++it) {
+                if (g1 == f1) {
+                    const ulonglong2 k = __ldg(&H.keys[s1]);
+                    if (k.x == a1 && k.y == b1) {
+                        h1 = true;
+                        break;
+                    }
+                }
+                s1 = (s1 + 1) & H.mask;
+                g1 = __ldg(&H.fp[s1]);
+            }
+            const unsigned m0 = __ballot_sync(FULL_MASK, h0);
+            const unsigned m1 = __ballot_sync(FULL_MASK, h1);
+            if (lane == 0) {
+                cnt += __popc(m0) + __popc(m1);
+                wb[r0 / 32] = m0;
+                if (r0 / 32 + 1 < nwords) wb[r0 / 32 + 1] = m1;
+            }
+        }
+        // alpha-beta doubles: clear the words that lie wholly in the block (the word holding
+        // index o4, if o4 is not a multiple of 32, was written above with zeros past o4)
+        for (uint32_t w = (o4 + 31) / 32 + lane; w < nwords; w += 32) wb[w] = 0u;
+        __syncwarp();
+        for (uint32_t sa0 = 0; sa0 < sA; sa0 += 32) {
+            const uint32_t si = sa0 + lane;
+            uint64_t a2 = 0;
+            int2 r = make_int2(0, 0);
+            uint32_t w = 0;
+            bool scan = false;
+            if (si < sA) {
+                const uint32_t xa = si / (uint32_t)P.ma, ya = si - xa * (uint32_t)P.ma;
+                a2 = x.x ^ (1ull << ctx->occA[xa]) ^ (1ull << ctx->virA[ya]);
+                if (alpha_find(X, a2, r)) {
+                    scan = (uint32_t)r.y <= scan_max;
+                    w = scan ? (uint32_t)r.y : sB;
+                }
+            }
+            uint32_t incl = w;  // inclusive prefix of the work over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL_MASK, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
+            const uint32_t excl = incl - w;
+            for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                // owner lane of work item t: the first lane whose inclusive prefix exceeds t
+                int lo = 0, hi = 31;
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (lo + hi) >> 1;
+                    const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
+                    if (v > t) hi = mid;
+                    else lo = mid + 1;
+                }
+                const int own = lo;
+                const uint32_t base = __shfl_sync(FULL_MASK, excl, own);
+                const int start = __shfl_sync(FULL_MASK, r.x, own);
+                const uint64_t ao = __shfl_sync(FULL_MASK, a2, own);
+                const bool so = __shfl_sync(FULL_MASK, (int)scan, own) != 0;
+                bool hit = false;
+                uint32_t lb = 0;
+                if (t < total) {
+                    const uint32_t k = t - base;
+                    if (so) {
+                        const uint64_t by = __ldg(&S[start + k].y);
+                        const uint64_t d = by ^ x.y;
+                        if (__popcll(d) == 2) {
+                            const uint64_t jbit = x.y & d, bbit = by & d;
+                            const uint32_t xb = (uint32_t)__popcll(x.y & (jbit - 1ull));
+                            const uint32_t yb = (uint32_t)__popcll(~x.y & (bbit - 1ull));
+                            lb = xb * (uint32_t)P.mb + yb;
+                            hit = true;
+                        }
+                    } else {
+                        const uint32_t xb = k / (uint32_t)P.mb, yb = k - xb * (uint32_t)P.mb;
+                        const uint64_t b2 =
+                            x.y ^ (1ull << ctx->occB[xb]) ^ (1ull << ctx->virB[yb]);
+                        hit = hash_lookup(H, ao, b2) >= 0;
+                        lb = k;
+                    }
+                }
+                if (hit) {
+                    const uint32_t e = o4 + (sa0 + (uint32_t)own) * sB + lb;
+                    atomicOr(&wb[e / 32], 1u << (e & 31));
+                }
+                cnt += __popc(__ballot_sync(FULL_MASK, hit));
+            }
+        }
+        if (lane == 0) rowcnt[det] = cnt + 1;  // + diagonal
+        __syncwarp();
+    }
+}
+
 // Pass 2: write each row in canonical order: the diagonal, then the hits. With bits the warp
 // walks the stored ballot words (skipping empty ones) and decodes, probes and evaluates only
 // the hits; without bits it re-enumerates every excitation.
@@ -226,8 +441,29 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
     if (smem > 48 * 1024) {
         NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_conn_count_ab, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
         NQS_CK(cudaFuncSetAttribute(k_conn_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
+    }
+    // index of S by alpha string (runs of the sorted S), for the alpha-beta block of pass 1
+    const bool use_ab = p->d.dAB > 0;
+    AlphaIdx X;
+    memset(&X, 0, sizeof X);
+    if (use_ab) {
+        uint64_t cap = 1024;
+        while (cap < 2 * (uint64_t)nS) cap <<= 1;
+        uint64_t* akey;
+        int2* arun;
+        NQS_TRY(sc.get(&akey, cap));
+        NQS_TRY(sc.get(&arun, cap));
+        NQS_CK(cudaMemsetAsync(akey, 0, cap * sizeof(uint64_t), s));
+        k_alpha_index<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, akey, arun,
+                                                        cap - 1);
+        NQS_CK_LAUNCH();
+        X.key = akey;
+        X.run = arun;
+        X.mask = cap - 1;
     }
     int64_t* rowcnt;
     NQS_TRY(sc.get(&rowcnt, nS));
@@ -243,8 +479,12 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
     };
     {
         ProfScope prof_(PROF_CONN_COUNT, s);
-        k_conn_count<<<conn_grid(nS), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)dets, nS,
-                                                               rowcnt, bits);
+        if (use_ab)
+            k_conn_count_ab<<<conn_grid(nS), CONN_THREADS, smem, s>>>(
+                p->d, H, X, (const ulonglong2*)dets, nS, rowcnt, bits);
+        else
+            k_conn_count<<<conn_grid(nS), CONN_THREADS, smem, s>>>(
+                p->d, H, (const ulonglong2*)dets, nS, rowcnt, bits);
     }
     nqs_note_launch();
     if (cudaGetLastError() != cudaSuccess) return fail(NQS_ERR_CUDA);
