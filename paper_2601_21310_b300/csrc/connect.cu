@@ -165,7 +165,86 @@ __device__ __forceinline__ bool alpha_find(const AlphaIdx& X, uint64_t a, int2& 
     return false;
 }
 
-__global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count_ab(ProblemDev P, HashS H,
+// OR a 32-bit ballot whose bit k stands for canonical index base + k into the row's words
+__device__ __forceinline__ void or_ballot(uint32_t* wb, uint32_t base, unsigned m) {
+    if (!m) return;
+    const uint32_t w = base >> 5, sh = base & 31u;
+    atomicOr(&wb[w], m << sh);
+    if (sh) {
+        const unsigned hi = m >> (32u - sh);
+        if (hi) atomicOr(&wb[w + 1], hi);
+    }
+}
+
+// The plain probe pass over the canonical indices [lo, hi) of one class range (singles decode
+// directly; same-spin doubles step incrementally from a fresh position). Returns, in lane 0,
+// the number of hits; ballots are ORed into the row's (cleared) words.
+__device__ __forceinline__ int probe_range(const ProblemDev& P, const PairTables& T,
+                                           const DetCtx& c, const HashS& H, ulonglong2 x,
+                                           uint32_t lo, uint32_t hi, uint32_t o2, uint32_t o3,
+                                           uint32_t o4, uint32_t* wb, int lane) {
+    int cnt = 0;
+    EnumPos q;
+    q.cls = -1;
+    for (uint32_t r0 = lo; r0 < hi; r0 += 64) {
+        const uint32_t e0 = r0 + lane, e1 = e0 + 32;
+        const bool v0 = e0 < hi, v1 = e1 < hi;
+        uint64_t a0 = 0, b0 = 0, a1 = 0, b1 = 0, s0 = 0, s1 = 0;
+        uint16_t f0 = 0, f1 = 0, g0 = 0, g1 = 0;
+        if (v0) {
+            step_key(P, T, c, x.x, x.y, e0, o2, o3, o4, q, a0, b0);
+            const uint64_t hh = s_hash(a0, b0);
+            s0 = hash_slot(hh, H.mask);
+            f0 = hash_fingerprint(hh);
+            g0 = __ldg(&H.fp[s0]);
+        }
+        if (v1) {
+            step_key(P, T, c, x.x, x.y, e1, o2, o3, o4, q, a1, b1);
+            const uint64_t hh = s_hash(a1, b1);
+            s1 = hash_slot(hh, H.mask);
+            f1 = hash_fingerprint(hh);
+            g1 = __ldg(&H.fp[s1]);
+        }
+        bool h0 = false, h1 = false;
+        for (uint64_t it = 0; v0 && g0 != 0 && it <= H.mask; ++it) {
+            if (g0 == f0) {
+                const ulonglong2 k = __ldg(&H.keys[s0]);
+                if (k.x == a0 && k.y == b0) {
+                    h0 = true;
+                    break;
+                }
+            }
+            s0 = (s0 + 1) & H.mask;
+            g0 = __ldg(&H.fp[s0]);
+        }
+        for (uint64_t it = 0; v1 && g1 != 0 && it <= H.mask; ++it) {
+            if (g1 == f1) {
+                const ulonglong2 k = __ldg(&H.keys[s1]);
+                if (k.x == a1 && k.y == b1) {
+                    h1 = true;
+                    break;
+                }
+            }
+            s1 = (s1 + 1) & H.mask;
+            g1 = __ldg(&H.fp[s1]);
+        }
+        const unsigned m0 = __ballot_sync(FULL_MASK, h0);
+        const unsigned m1 = __ballot_sync(FULL_MASK, h1);
+        if (lane == 0) {
+            cnt += __popc(m0) + __popc(m1);
+            or_ballot(wb, r0, m0);
+            or_ballot(wb, r0 + 32, m1);
+        }
+    }
+    return cnt;
+}
+
+// position of the pair (r1 < r2) in the lexicographic list of pairs of n items
+__device__ __forceinline__ uint32_t pair_pos(uint32_t r1, uint32_t r2, uint32_t n) {
+    return r1 * (2 * n - r1 - 1) / 2 + (r2 - r1 - 1);
+}
+
+__global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P, HashS H,
                                                                  AlphaIdx X,
                                                                  const ulonglong2* __restrict__ S,
                                                                  int64_t nS, int64_t* rowcnt,
@@ -176,72 +255,61 @@ __global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count_ab(ProblemDev P,
     const int lane = threadIdx.x & 31;
     const uint32_t nexc = (uint32_t)P.nexc;
     const uint32_t nwords = (nexc + 31) / 32;
-    const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+    const uint32_t o1 = (uint32_t)P.sA, o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
                    o4 = o3 + (uint32_t)P.dBB;
     const uint32_t sA = (uint32_t)P.sA, sB = (uint32_t)P.sB;
     const uint32_t scan_max = 4 * sB;
+    const uint32_t own_scan_max = 4 * (sB + (uint32_t)P.dBB);
+    const uint32_t nb = (uint32_t)P.nb, mb = (uint32_t)P.mb, Qb = (uint32_t)choose2(P.mb);
     for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * CONN_WARPS) {
         ulonglong2 x = S[det];
         fill_ctx(P, x.x, x.y, ctx, lane);
         uint32_t* wb = bits + det * nwords;
-        int cnt = 0;
-        // singles and same-spin doubles: the plain pass over indices [0, o4)
-        EnumPos q;
-        q.cls = -1;
-        for (uint32_t r0 = 0; r0 < o4; r0 += 64) {
-            const uint32_t e0 = r0 + lane, e1 = e0 + 32;
-            const bool v0 = e0 < o4, v1 = e1 < o4;
-            uint64_t a0 = 0, b0 = 0, a1 = 0, b1 = 0, s0 = 0, s1 = 0;
-            uint16_t f0 = 0, f1 = 0, g0 = 0, g1 = 0;
-            if (v0) {
-                step_key(P, T, *ctx, x.x, x.y, e0, o2, o3, o4, q, a0, b0);
-                const uint64_t hh = s_hash(a0, b0);
-                s0 = hash_slot(hh, H.mask);
-                f0 = hash_fingerprint(hh);
-                g0 = __ldg(&H.fp[s0]);
-            }
-            if (v1) {
-                step_key(P, T, *ctx, x.x, x.y, e1, o2, o3, o4, q, a1, b1);
-                const uint64_t hh = s_hash(a1, b1);
-                s1 = hash_slot(hh, H.mask);
-                f1 = hash_fingerprint(hh);
-                g1 = __ldg(&H.fp[s1]);
-            }
-            bool h0 = false, h1 = false;
-            for (uint64_t it = 0; v0 && g0 != 0 && it <= H.mask; ++it) {
-                if (g0 == f0) {
-                    const ulonglong2 k = __ldg(&H.keys[s0]);
-                    if (k.x == a0 && k.y == b0) {
-                        h0 = true;
-                        break;
+        for (uint32_t w = lane; w < nwords; w += 32) wb[w] = 0u;
+        __syncwarp();
+        // alpha singles and alpha-alpha doubles: the plain probe pass
+        int cnt = probe_range(P, T, *ctx, H, x, 0, o1, o2, o3, o4, wb, lane);
+        cnt += probe_range(P, T, *ctx, H, x, o2, o3, o2, o3, o4, wb, lane);
+        // beta singles and beta-beta doubles of x keep its alpha string: they are the members
+        // y of x's own alpha run with popcount(B ^ b_y) = 2 (single) or 4 (double)
+        int2 own = make_int2(0, 0);
+        const bool have_own = alpha_find(X, x.x, own);  // x is in S: always found
+        if (have_own && (uint32_t)own.y <= own_scan_max) {
+            for (uint32_t k0 = 0; k0 < (uint32_t)own.y; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                bool hit = false;
+                uint32_t e = 0;
+                if (k < (uint32_t)own.y) {
+                    const uint64_t by = __ldg(&S[own.x + k].y);
+                    const uint64_t d = by ^ x.y;
+                    const int pc = __popcll(d);
+                    if (pc == 2) {
+                        const uint64_t jbit = x.y & d, bbit = by & d;
+                        const uint32_t xb = (uint32_t)__popcll(x.y & (jbit - 1ull));
+                        const uint32_t yb = (uint32_t)__popcll(~x.y & (bbit - 1ull));
+                        e = o1 + xb * mb + yb;
+                        hit = true;
+                    } else if (pc == 4) {
+                        const uint64_t holes = x.y & d, parts = by & d;
+                        const uint64_t j1 = holes & (~holes + 1ull), j2 = holes ^ j1;
+                        const uint64_t b1 = parts & (~parts + 1ull), b2 = parts ^ b1;
+                        const uint32_t r1 = (uint32_t)__popcll(x.y & (j1 - 1ull)),
+                                       r2 = (uint32_t)__popcll(x.y & (j2 - 1ull));
+                        const uint32_t v1 = (uint32_t)__popcll(~x.y & (b1 - 1ull)),
+                                       v2 = (uint32_t)__popcll(~x.y & (b2 - 1ull));
+                        e = o3 + pair_pos(r1, r2, nb) * Qb + pair_pos(v1, v2, mb);
+                        hit = true;
                     }
                 }
-                s0 = (s0 + 1) & H.mask;
-                g0 = __ldg(&H.fp[s0]);
+                if (hit) atomicOr(&wb[e >> 5], 1u << (e & 31));
+                const unsigned mh = __ballot_sync(FULL_MASK, hit);
+                if (lane == 0) cnt += __popc(mh);
             }
-            for (uint64_t it = 0; v1 && g1 != 0 && it <= H.mask; ++it) {
-                if (g1 == f1) {
-                    const ulonglong2 k = __ldg(&H.keys[s1]);
-                    if (k.x == a1 && k.y == b1) {
-                        h1 = true;
-                        break;
-                    }
-                }
-                s1 = (s1 + 1) & H.mask;
-                g1 = __ldg(&H.fp[s1]);
-            }
-            const unsigned m0 = __ballot_sync(FULL_MASK, h0);
-            const unsigned m1 = __ballot_sync(FULL_MASK, h1);
-            if (lane == 0) {
-                cnt += __popc(m0) + __popc(m1);
-                wb[r0 / 32] = m0;
-                if (r0 / 32 + 1 < nwords) wb[r0 / 32 + 1] = m1;
-            }
+        } else {
+            cnt += probe_range(P, T, *ctx, H, x, o1, o2, o2, o3, o4, wb, lane);
+            cnt += probe_range(P, T, *ctx, H, x, o3, o4, o2, o3, o4, wb, lane);
         }
-        // alpha-beta doubles: clear the words that lie wholly in the block (the word holding
-        // index o4, if o4 is not a multiple of 32, was written above with zeros past o4)
-        for (uint32_t w = (o4 + 31) / 32 + lane; w < nwords; w += 32) wb[w] = 0u;
         __syncwarp();
         for (uint32_t sa0 = 0; sa0 < sA; sa0 += 32) {
             const uint32_t si = sa0 + lane;
@@ -307,7 +375,8 @@ __global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count_ab(ProblemDev P,
                     const uint32_t e = o4 + (sa0 + (uint32_t)own) * sB + lb;
                     atomicOr(&wb[e / 32], 1u << (e & 31));
                 }
-                cnt += __popc(__ballot_sync(FULL_MASK, hit));
+                const unsigned mh = __ballot_sync(FULL_MASK, hit);
+                if (lane == 0) cnt += __popc(mh);
             }
         }
         if (lane == 0) rowcnt[det] = cnt + 1;  // + diagonal
