@@ -165,6 +165,66 @@ __device__ __forceinline__ bool alpha_find(const AlphaIdx& X, uint64_t a, int2& 
     return false;
 }
 
+// Index of S by beta string: the alpha strings of the configurations that share a beta string,
+// grouped in one list (bucket order inside a group is arbitrary: the count pass only tests
+// membership). Built by counting per beta string, an exclusive scan over the table and a fill.
+// Beta strings are nonzero whenever the beta electrons have somewhere to go (nb >= 1, mb >= 1),
+// which is the only case in which it is used.
+struct BetaIdx {
+    const uint64_t* key;    // [cap] beta string, 0 = empty
+    const uint32_t* off;    // [cap] start of the group in alist
+    const uint32_t* cnt;    // [cap] group size
+    const uint64_t* alist;  // [nS] alpha strings, grouped by beta string
+    uint64_t mask;          // cap - 1
+};
+
+__device__ __forceinline__ int64_t beta_slot_insert(uint64_t* key, uint64_t b, uint64_t mask) {
+    uint64_t slot = alpha_slot(b, mask);
+    for (uint64_t it = 0; it <= mask; ++it) {
+        const unsigned long long prev =
+            atomicCAS((unsigned long long*)&key[slot], 0ull, (unsigned long long)b);
+        if (prev == 0ull || prev == b) return (int64_t)slot;
+        slot = (slot + 1) & mask;
+    }
+    return -1;
+}
+
+__global__ void k_beta_count(const ulonglong2* __restrict__ S, int64_t nS, uint64_t* key,
+                             uint32_t* cnt, uint64_t mask) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nS;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = beta_slot_insert(key, S[i].y, mask);
+        if (slot >= 0) atomicAdd(&cnt[slot], 1u);
+    }
+}
+
+__global__ void k_beta_fill(const ulonglong2* __restrict__ S, int64_t nS, uint64_t* key,
+                            const uint32_t* __restrict__ off, uint32_t* fill, uint64_t* alist,
+                            uint64_t mask) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nS;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const ulonglong2 x = S[i];
+        const int64_t slot = beta_slot_insert(key, x.y, mask);  // present: finds its slot
+        if (slot >= 0) alist[off[slot] + atomicAdd(&fill[slot], 1u)] = x.x;
+    }
+}
+
+__device__ __forceinline__ bool beta_find(const BetaIdx& Y, uint64_t b, uint32_t& off,
+                                          uint32_t& n) {
+    uint64_t slot = alpha_slot(b, Y.mask);
+    for (uint64_t it = 0; it <= Y.mask; ++it) {
+        const uint64_t k = __ldg(&Y.key[slot]);
+        if (k == b) {
+            off = __ldg(&Y.off[slot]);
+            n = __ldg(&Y.cnt[slot]);
+            return true;
+        }
+        if (k == 0ull) return false;
+        slot = (slot + 1) & Y.mask;
+    }
+    return false;
+}
+
 // OR a 32-bit ballot whose bit k stands for canonical index base + k into the row's words
 __device__ __forceinline__ void or_ballot(uint32_t* wb, uint32_t base, unsigned m) {
     if (!m) return;
@@ -245,7 +305,7 @@ __device__ __forceinline__ uint32_t pair_pos(uint32_t r1, uint32_t r2, uint32_t 
 }
 
 __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P, HashS H,
-                                                                 AlphaIdx X,
+                                                                 AlphaIdx X, BetaIdx Y,
                                                                  const ulonglong2* __restrict__ S,
                                                                  int64_t nS, int64_t* rowcnt,
                                                                  uint32_t* __restrict__ bits) {
@@ -261,6 +321,8 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
     const uint32_t scan_max = 4 * sB;
     const uint32_t own_scan_max = 4 * (sB + (uint32_t)P.dBB);
     const uint32_t nb = (uint32_t)P.nb, mb = (uint32_t)P.mb, Qb = (uint32_t)choose2(P.mb);
+    const uint32_t na = (uint32_t)P.na, ma = (uint32_t)P.ma, Qa = (uint32_t)choose2(P.ma);
+    const uint32_t own_a_scan_max = 4 * (sA + (uint32_t)P.dAA);
     for (int64_t det = (int64_t)blockIdx.x * CONN_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * CONN_WARPS) {
         ulonglong2 x = S[det];
@@ -268,9 +330,45 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
         uint32_t* wb = bits + det * nwords;
         for (uint32_t w = lane; w < nwords; w += 32) wb[w] = 0u;
         __syncwarp();
-        // alpha singles and alpha-alpha doubles: the plain probe pass
-        int cnt = probe_range(P, T, *ctx, H, x, 0, o1, o2, o3, o4, wb, lane);
-        cnt += probe_range(P, T, *ctx, H, x, o2, o3, o2, o3, o4, wb, lane);
+        // alpha singles and alpha-alpha doubles of x keep its beta string: they are the alpha
+        // strings a_y of x's own beta group with popcount(A ^ a_y) = 2 (single) or 4 (double)
+        int cnt = 0;
+        uint32_t boff = 0, blen = 0;
+        if (Y.key && beta_find(Y, x.y, boff, blen) && blen <= own_a_scan_max) {
+            for (uint32_t k0 = 0; k0 < blen; k0 += 32) {
+                const uint32_t k = k0 + lane;
+                bool hit = false;
+                uint32_t e = 0;
+                if (k < blen) {
+                    const uint64_t ay = __ldg(&Y.alist[boff + k]);
+                    const uint64_t d = ay ^ x.x;
+                    const int pc = __popcll(d);
+                    if (pc == 2) {
+                        const uint64_t ibit = x.x & d, abit = ay & d;
+                        const uint32_t xa = (uint32_t)__popcll(x.x & (ibit - 1ull));
+                        const uint32_t ya = (uint32_t)__popcll(~x.x & (abit - 1ull));
+                        e = xa * ma + ya;
+                        hit = true;
+                    } else if (pc == 4) {
+                        const uint64_t holes = x.x & d, parts = ay & d;
+                        const uint64_t i1 = holes & (~holes + 1ull), i2 = holes ^ i1;
+                        const uint64_t a1 = parts & (~parts + 1ull), a2 = parts ^ a1;
+                        const uint32_t r1 = (uint32_t)__popcll(x.x & (i1 - 1ull)),
+                                       r2 = (uint32_t)__popcll(x.x & (i2 - 1ull));
+                        const uint32_t v1 = (uint32_t)__popcll(~x.x & (a1 - 1ull)),
+                                       v2 = (uint32_t)__popcll(~x.x & (a2 - 1ull));
+                        e = o2 + pair_pos(r1, r2, na) * Qa + pair_pos(v1, v2, ma);
+                        hit = true;
+                    }
+                }
+                if (hit) atomicOr(&wb[e >> 5], 1u << (e & 31));
+                const unsigned mh = __ballot_sync(FULL_MASK, hit);
+                if (lane == 0) cnt += __popc(mh);
+            }
+        } else {
+            cnt += probe_range(P, T, *ctx, H, x, 0, o1, o2, o3, o4, wb, lane);
+            cnt += probe_range(P, T, *ctx, H, x, o2, o3, o2, o3, o4, wb, lane);
+        }
         // beta singles and beta-beta doubles of x keep its alpha string: they are the members
         // y of x's own alpha run with popcount(B ^ b_y) = 2 (single) or 4 (double)
         int2 own = make_int2(0, 0);
@@ -534,6 +632,35 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
         X.run = arun;
         X.mask = cap - 1;
     }
+    // index of S by beta string, for the alpha singles and alpha-alpha doubles of pass 1
+    BetaIdx Y;
+    memset(&Y, 0, sizeof Y);
+    if (use_ab && p->d.nb >= 1 && p->d.mb >= 1) {
+        uint64_t cap = 1024;
+        while (cap < 2 * (uint64_t)nS) cap <<= 1;
+        uint64_t *bkey, *alist;
+        uint32_t *bcnt, *boff, *bfill;
+        NQS_TRY(sc.get(&bkey, cap));
+        NQS_TRY(sc.get(&bcnt, cap));
+        NQS_TRY(sc.get(&boff, cap));
+        NQS_TRY(sc.get(&bfill, cap));
+        NQS_TRY(sc.get(&alist, nS));
+        NQS_CK(cudaMemsetAsync(bkey, 0, cap * sizeof(uint64_t), s));
+        NQS_CK(cudaMemsetAsync(bcnt, 0, cap * sizeof(uint32_t), s));
+        NQS_CK(cudaMemsetAsync(bfill, 0, cap * sizeof(uint32_t), s));
+        k_beta_count<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, bkey, bcnt,
+                                                       cap - 1);
+        NQS_CK_LAUNCH();
+        NQS_TRY(scan_exclusive_u32(p, sc, bcnt, boff, (int64_t)cap, s));
+        k_beta_fill<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, bkey, boff,
+                                                      bfill, alist, cap - 1);
+        NQS_CK_LAUNCH();
+        Y.key = bkey;
+        Y.off = boff;
+        Y.cnt = bcnt;
+        Y.alist = alist;
+        Y.mask = cap - 1;
+    }
     int64_t* rowcnt;
     NQS_TRY(sc.get(&rowcnt, nS));
     uint32_t* bits;
@@ -550,7 +677,7 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
         ProfScope prof_(PROF_CONN_COUNT, s);
         if (use_ab)
             k_conn_count_ab<<<conn_grid(nS), CONN_THREADS, smem, s>>>(
-                p->d, H, X, (const ulonglong2*)dets, nS, rowcnt, bits);
+                p->d, H, X, Y, (const ulonglong2*)dets, nS, rowcnt, bits);
         else
             k_conn_count<<<conn_grid(nS), CONN_THREADS, smem, s>>>(
                 p->d, H, (const ulonglong2*)dets, nS, rowcnt, bits);
