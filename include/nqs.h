@@ -133,12 +133,19 @@ int64_t nqs_net_num_params(const nqs_net* net);
 int nqs_diag(nqs_problem* problem, const uint64_t* dets, int64_t n, double* out,
              nqs_stream_t stream);
 
-/* Enumerate every single and double excitation of every det of S (Eq. connected_set), look
- * each up in S, and build H_SS in CSR (Sec. 3.1: the combinatorial kernel exports H_VV as
- * CSR; Algorithm 1 step 1). dets: device [nS][2], sorted and unique. On success *out holds a
- * library-owned CSR and *n_enumerated (host, may be NULL) the number of (det, excitation)
- * pairs resolved. Synchronises the stream (nnz must be known to allocate). Errors:
- * NQS_ERR_ARG, NQS_ERR_UNSORTED / NQS_ERR_POPCOUNT (with validate), NQS_ERR_OOM, NQS_ERR_CUDA. */
+/* Resolve every single and double excitation of every det of S (Eq. connected_set) as a member
+ * of S or not, and build H_SS in CSR (Sec. 3.1: the combinatorial kernel exports H_VV as CSR;
+ * Algorithm 1 step 1). Membership comes from a hash table of S and, for whole blocks of
+ * excitations at once, from indices of S by alpha string and by beta string (a det's beta
+ * excitations are the members of its own alpha run that differ in 2 or 4 beta bits, and so
+ * on); the result is the same as looking up each excitation. Rows: the diagonal, then the hits
+ * in canonical excitation order. dets: device [nS][2], sorted and unique. On success *out holds
+ * a library-owned CSR and *n_enumerated (host, may be NULL) the number of (det, excitation)
+ * pairs resolved (nS times the excitations per det). Device scratch from the problem's pool:
+ * the hash table (22 B per slot, 16 to 32 slots per det up to 2^22 dets, fewer above), the two
+ * indices (80 to 152 B per det) and the hit ballots (4 B per 32 excitations per det).
+ * Synchronises the stream (nnz must be known to allocate). Errors: NQS_ERR_ARG,
+ * NQS_ERR_UNSORTED / NQS_ERR_POPCOUNT (with validate), NQS_ERR_OOM, NQS_ERR_CUDA. */
 int nqs_connections(nqs_problem* problem, const uint64_t* dets, int64_t nS, const nqs_opts* opts,
                     nqs_csr* out, int64_t* n_enumerated, nqs_stream_t stream);
 /* Release a library-owned CSR (from nqs_connections or nqs_proxy_hamiltonian; its arrays come
