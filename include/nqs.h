@@ -233,8 +233,9 @@ int nqs_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr, cons
  * psi: device [nS] FP64 at any scale. out: host [5] = {external, internal, number of unique
  * x' in C\S, number of emitted pairs, number of buckets used}. opts->buckets = 0 chooses the
  * bucket count: one bucket's pairs use at most half of the free device memory. bucket_partials:
- * host [2*B] (external, internal per bucket) or NULL (required with opts->buckets = 0). Sort keys are 32-bit, 64-bit or two-word by 2*norb. Each bucket's emissions
- * must stay below 2^32 (and fit in memory): use more buckets for larger problems.
+ * host [2*B] (external, internal per bucket) or NULL (required with opts->buckets = 0). Sort
+ * keys are 32-bit, 64-bit or two-word by 2*norb. Each bucket's emissions must stay below 2^32
+ * (and fit in memory): use more buckets for larger problems.
  * With opts->eps_pt2 > 0 (Sec. 3.3: the external sum of Eq. pt2_correction runs over the
  * screened perturbative set P) only the contributions with |H_x'y psi_y| >= eps_pt2 to x' outside
  * S are emitted, found by the sorted-integral walk of nqs_hb_select; c(x') sums those, P is the
