@@ -1,11 +1,12 @@
 // H_SS construction (Sec. 3.1 combinatorial kernel, Eq. connected_set, Algorithm 1 step 1):
-// every single and double excitation of every det of S is enumerated in canonical order,
-// looked up in S through an open-addressing hash table, and the hits become CSR entries.
+// every single and double excitation of every det of S, in canonical order, is resolved as a
+// member of S or not (through an open-addressing hash table of S, and in nqs_connections
+// through indices of S by alpha and by beta string that settle whole blocks at once), and the
+// hits become CSR entries.
 //
-// One warp per det. Pass 1 counts the hits of each row; an exclusive scan gives row_ptr;
-// pass 2 re-enumerates in rounds of 32 canonical indices and compacts the hits with a warp
-// ballot, so each row is written in canonical order without any sort. The matrix element is
-// computed only for hits.
+// One warp per det. Pass 1 counts the hits of each row and records them as ballot words; an
+// exclusive scan gives row_ptr; pass 2 walks the ballot words in canonical order and writes
+// each row without any sort. The matrix element is computed only for hits.
 #include <stdlib.h>
 #include <string.h>
 
@@ -101,20 +102,23 @@ __global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count(ProblemDev P, Ha
 }
 
 // ------------------------------------------------------------------------------------------
-// Pass 1 with an index of S by alpha string (nqs_connections). S is sorted by (a, b), so the
-// configurations of S that share an alpha string a' form one contiguous run S[start, start +
-// cnt). An alpha-beta double (i_a -> a_a, j_b -> b_b) of x = (A, B) leads to x' = (a', b') with
-// a' = A's single (i_a, a_a); x' is in S exactly when a' has a run and b' is among the run's beta
-// strings. For each alpha single the warp therefore looks a' up once in the alpha index and
-//   - skips the whole block of beta singles when a' is not an alpha string of S;
-//   - scans a short run (cnt <= 4 x beta singles): a run member's beta string b_y is a beta
-//     single of B exactly when popcount(B ^ b_y) == 2, and the two differing bits give j_b and
-//     b_b, hence the canonical index;
-//   - otherwise probes the hash of S for each beta single, as the plain pass does.
-// Every index resolves to the same hit or miss as a lookup of x' in S, so the ballot words are
-// bit for bit those of k_conn_count. The singles and same-spin doubles (indices below the
-// alpha-beta block) go through the plain pass unchanged. The alpha-beta ballot words are
-// cleared first and hits are set with atomicOr (order-free).
+// Pass 1 with indices of S (nqs_connections). S is sorted by (a, b), so the configurations of
+// S that share an alpha string form one contiguous run; a second index groups the alpha strings
+// of S by beta string. For x = (A, B) the count pass then resolves
+//   - the alpha-beta doubles per alpha single a' of A (the block of all beta singles that go
+//     with it): one lookup of a' in the alpha index; nothing to do when a' is not an alpha
+//     string of S; a scan of a''s run when it is short (length <= 4 x the beta singles), a
+//     member's beta string b_y being a beta single of B exactly when popcount(B ^ b_y) == 2,
+//     the two differing bits giving j_b and b_b and hence the canonical index; otherwise a
+//     probe of the hash of S for each beta single, as the plain pass does;
+//   - the beta singles and beta-beta doubles (same alpha string A) by one scan of x's own
+//     alpha run: popcount(B ^ b_y) == 2 or 4;
+//   - the alpha singles and alpha-alpha doubles (same beta string B) by one scan of x's own
+//     beta group: popcount(A ^ a_y) == 2 or 4;
+// falling back to the plain probe pass for a class whenever its run or group is long. Every
+// canonical index resolves to the same hit or miss as a lookup of its x' in S, so the ballot
+// words are bit for bit those of k_conn_count. The row's words are cleared first and hits are
+// ORed in (order-free).
 // ------------------------------------------------------------------------------------------
 struct AlphaIdx {
     const uint64_t* key;  // [cap] alpha string, 0 = empty (alpha strings of S are nonzero)
@@ -166,7 +170,7 @@ __device__ __forceinline__ bool alpha_find(const AlphaIdx& X, uint64_t a, int2& 
 }
 
 // Index of S by beta string: the alpha strings of the configurations that share a beta string,
-// grouped in one list (bucket order inside a group is arbitrary: the count pass only tests
+// grouped in one list (the order inside a group is arbitrary: the count pass only tests
 // membership). Built by counting per beta string, an exclusive scan over the table and a fill.
 // Beta strings are nonzero whenever the beta electrons have somewhere to go (nb >= 1, mb >= 1),
 // which is the only case in which it is used.
