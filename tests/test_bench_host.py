@@ -1,0 +1,82 @@
+"""Host-side arithmetic of bench.py on CPU: the connection count per configuration that the
+benchmark's connections/s is built on, the algorithmic bytes of the sort kernels that enter the
+roofline line, and the rule that a committed DRAM-traffic figure is used only while the kernel
+source it was captured from is unchanged."""
+import hashlib
+import os
+
+import pytest
+
+import bench
+from paper_2601_21310_b300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+# singles + same-spin doubles + opposite-spin doubles per configuration of the four workload
+# shapes: n(norb - n) per spin, C(n,2) C(norb-n,2) per spin, (n (norb - n))^2
+@pytest.mark.parametrize("name,per_det", [("tiny_n10", 875), ("small_n16", 5792),
+                                          ("cr2_24e30o", 67284), ("cr2_48e42o", 271944)])
+def test_connections_per_configuration(olib, name, per_det):
+    wl = synth.WORKLOADS[name]
+    assert bench.synth_nexc(wl) == per_det
+    # the oracle's connected set (Eq. connected_set) has the same size
+    assert olib.n_excitations(wl.norb, wl.nalpha, wl.nbeta) == per_det
+
+
+def test_connected_set_size_matches_enumeration(olib):
+    # one configuration of the 16-orbital workload, enumerated by the oracle
+    wl = synth.WORKLOADS["small_n16"]
+    S = synth.select_S(wl.norb, wl.nalpha, 64)
+    for a, b in S[[0, 7, 63]]:
+        assert len(olib.excitations(wl.norb, a, b)) == bench.synth_nexc(wl)
+
+
+def test_sort_bytes_per_pair():
+    # a radix pass reads and writes key + FP64 value; keys are 4 B for 2 norb <= 32, 8 B up to
+    # 64, 16 B above
+    n = 1_000_000
+    for name, key in (("small_n16", 4), ("cr2_24e30o", 8), ("cr2_48e42o", 16)):
+        wl = synth.WORKLOADS[name]
+        bound, b, unit = bench.algorithmic_work("rs_scatter", wl, 1, 1, 0, n, 0, 0)
+        assert (bound, unit) == ("hbm", "B") and b == 2 * (key + 8) * n
+        bound, b, _ = bench.algorithmic_work("rs_hist", wl, 1, 1, 0, n, 0, 0)
+        assert b == key * n
+        # with B buckets a sort launch handles 1/B of the pairs
+        _, b4, _ = bench.algorithmic_work("rs_scatter", wl, 1, 1, 0, n, 0, 0, buckets=4)
+        assert b4 == 2 * (key + 8) * n / 4
+    # issue-bound kernels carry no byte roofline
+    assert bench.algorithmic_work("conn_count", synth.WORKLOADS["small_n16"], 1, 1, 0, 0, 0,
+                                  0)[0] == "alu"
+
+
+def _profile_fields(path):
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+    return vals
+
+
+def test_committed_traffic_tracks_the_kernel_source():
+    path = os.path.join(ROOT, "profiles", "rs_scatter_small_n16.md")
+    vals = _profile_fields(path)
+    with open(os.path.join(ROOT, vals["source_file"]), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    tr = bench.kernel_traffic("rs_scatter", "small_n16")
+    if sha == vals["source_sha256"]:
+        assert tr == float(vals["dram_bytes_per_launch"])
+        # the captured traffic is within 5% of the algorithmic bytes of one pass (24 B per pair
+        # over the 9.49e7 pairs of one step's PT2 sort): no re-reads
+        assert abs(tr / (24.0 * 16384 * 5792) - 1.0) < 0.05
+    else:
+        assert tr is None  # stale figures are never reported
+
+
+def test_peaks_source():
+    peaks, kind = bench.load_peaks()
+    assert kind in ("measured", "fallback")
+    assert peaks["hbm_gbs"] > 1000 and peaks["bf16_tflops"] > 100
+    assert bench.whole_job_rate(1e6, 500.0, 4) == 8e6
