@@ -80,3 +80,13 @@ def test_peaks_source():
     assert kind in ("measured", "fallback")
     assert peaks["hbm_gbs"] > 1000 and peaks["bf16_tflops"] > 100
     assert bench.whole_job_rate(1e6, 500.0, 4) == 8e6
+
+
+def test_pt2_screening_default_by_workload(monkeypatch):
+    # exact PT2 over C minus S up to 30 orbitals, the paper's screened set above
+    for name, eps in (("tiny_n10", 0.0), ("small_n16", 0.0), ("cr2_24e30o", 0.0),
+                      ("cr2_48e42o", 1e-6), ("batched", 0.0)):
+        monkeypatch.setattr("sys.argv", ["bench.py", "--workload", name])
+        assert bench.parse().eps_pt2 == eps
+    monkeypatch.setattr("sys.argv", ["bench.py", "--workload", "cr2_48e42o", "--eps-pt2", "0"])
+    assert bench.parse().eps_pt2 == 0.0  # an explicit value wins
