@@ -48,3 +48,33 @@ def test_status_strings_without_gpu():
     assert L.nqs_status_string(0) == b"ok"
     assert b"sorted" in L.nqs_status_string(-2)
     assert L.nqs_version().startswith(b"nqs-b300")
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of nqs_opts, nqs_csr and nqs_detset have the C layout: offsets and
+    sizes as gcc lays out the header's structs."""
+    import shutil
+
+    from paper_2601_21310_b300 import nqs as N
+    if shutil.which("gcc") is None:
+        import pytest
+        pytest.skip("gcc not available")
+    structs = {"nqs_opts": N.Opts, "nqs_csr": N.CSRStruct, "nqs_detset": N.DetSetStruct}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nqs.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    c_layout = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert c_layout[(cname, "size")] == ctypes.sizeof(py)
+        for fname, _ in py._fields_:
+            assert c_layout[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
