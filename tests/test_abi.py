@@ -78,3 +78,36 @@ def test_binding_structs_match_the_header(tmp_path):
         assert c_layout[(cname, "size")] == ctypes.sizeof(py)
         for fname, _ in py._fields_:
             assert c_layout[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def _prototypes():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(nqs_\w+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
+        params = " ".join(m.group(2).split())
+        protos[m.group(1)] = [] if params in ("", "void") else [p.strip()
+                                                                 for p in params.split(",")]
+    return protos
+
+
+def test_binding_argtypes_match_the_prototypes():
+    """Every bound entry point passes as many arguments as the header declares, each of the
+    declared kind (pointer / stream, 32-bit int, int64_t, double)."""
+    from paper_2601_21310_b300 import nqs as N
+    protos = _prototypes()
+
+    def kind_of_c(p):
+        if "*" in p or p.startswith("nqs_stream_t"):
+            return "ptr"
+        t = p.rsplit(" ", 1)[0] if " " in p else p
+        return {"int": "i32", "int64_t": "i64", "double": "f64"}.get(t.replace("const ", ""), t)
+
+    def kind_of_ctypes(t):
+        return {ctypes.c_void_p: "ptr", ctypes.c_char_p: "ptr", ctypes.c_int: "i32",
+                ctypes.c_int64: "i64", ctypes.c_double: "f64"}[t]
+
+    for name, (_, argtypes) in N.EXPORTS.items():
+        assert name in protos, name
+        c_kinds = [kind_of_c(p) for p in protos[name]]
+        assert c_kinds == [kind_of_ctypes(t) for t in argtypes], name
