@@ -84,10 +84,12 @@ def _prototypes():
     txt = open(HEADER).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     protos = {}
-    for m in re.finditer(r"\b(nqs_\w+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
-        params = " ".join(m.group(2).split())
-        protos[m.group(1)] = [] if params in ("", "void") else [p.strip()
-                                                                 for p in params.split(",")]
+    for m in re.finditer(r"^\s*((?:const\s+)?\w+\s*\**)\s*\b(nqs_\w+)\s*\(([^;{]*?)\)\s*;", txt,
+                         flags=re.S | re.M):
+        params = " ".join(m.group(3).split())
+        protos[m.group(2)] = (" ".join(m.group(1).split()),
+                              [] if params in ("", "void") else [p.strip()
+                                                                 for p in params.split(",")])
     return protos
 
 
@@ -107,7 +109,11 @@ def test_binding_argtypes_match_the_prototypes():
         return {ctypes.c_void_p: "ptr", ctypes.c_char_p: "ptr", ctypes.c_int: "i32",
                 ctypes.c_int64: "i64", ctypes.c_double: "f64"}[t]
 
-    for name, (_, argtypes) in N.EXPORTS.items():
+    ret_kinds = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "const char*": ctypes.c_char_p,
+                 "void": None}
+    for name, (restype, argtypes) in N.EXPORTS.items():
         assert name in protos, name
-        c_kinds = [kind_of_c(p) for p in protos[name]]
+        ret, params = protos[name]
+        assert ret_kinds[ret.replace(" *", "*")] is restype, (name, ret)
+        c_kinds = [kind_of_c(p) for p in params]
         assert c_kinds == [kind_of_ctypes(t) for t in argtypes], name
