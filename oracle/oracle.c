@@ -766,7 +766,7 @@ uint64_t orc_bucket(uint64_t a, uint64_t b, uint64_t nbuckets) {
  * (y ascending), sorting by (key, emission number) and summing each run in order. The
  * external sum runs in ascending key order, the internal in S order, both compensated.
  * bucket >= 0 restricts both terms to configurations x with bucket(x) == bucket.
- * out = [dE_ext, dE_int, n_unique_external, D].
+ * out = [dE_ext, dE_int, n_unique_external, D, number of emitted pairs].
  * ---------------------------------------------------------------------------------------- */
 typedef struct {
     uint64_t a, b;
@@ -804,9 +804,30 @@ static int pt2_keep(const uint64_t* S, int64_t nS, uint64_t xa, uint64_t xb, dou
  * each contribution): c(x') keeps only the terms H_x'y psi_y with |H_x'y psi_y| >= eps, and the
  * external sum runs over the x' outside S that receive at least one such term (the screened
  * perturbative set P). The internal term stays exact. eps = 0 is orc_pt2. */
+static int pt2_core(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
+                    const double* psi, double E, double eps, int64_t nbuckets, int64_t bucket,
+                    double* out, int64_t cap, uint64_t* keys_out, double* c_out);
+
 int orc_pt2_eps(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
                 const double* psi, double E, double eps, int64_t nbuckets, int64_t bucket,
                 double* out) {
+    return pt2_core(norb, h, eri, S, nS, psi, E, eps, nbuckets, bucket, out, 0, NULL, NULL);
+}
+
+/* The unique external set of the same reduction: for every x' in C\S (of bucket `bucket`, or
+ * all when bucket < 0), in ascending key order, the configuration (keys_out[2k], keys_out[2k+1])
+ * and c(x') = sum_{y in S} H_x'y psi_y (c_out[k]), for k < min(n_unique, cap). out as in
+ * orc_pt2_eps; returns ORC_OK. */
+int orc_pt2_unique(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
+                   const double* psi, double E, int64_t nbuckets, int64_t bucket, double* out,
+                   int64_t cap, uint64_t* keys_out, double* c_out) {
+    return pt2_core(norb, h, eri, S, nS, psi, E, 0.0, nbuckets, bucket, out, cap, keys_out,
+                    c_out);
+}
+
+static int pt2_core(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
+                    const double* psi, double E, double eps, int64_t nbuckets, int64_t bucket,
+                    double* out, int64_t cap, uint64_t* keys_out, double* c_out) {
     if (nS <= 0 || nbuckets < 1 || !(eps >= 0.0)) return ORC_ERR_ARG;
     int na = popc(S[0]), nb = popc(S[1]);
     int64_t nexc = orc_n_excitations(norb, na, nb);
@@ -879,6 +900,11 @@ int orc_pt2_eps(int norb, const double* h, const double* eri, const uint64_t* S,
         } else {
             double hxx = orc_diag(norb, h, eri, em[k].a, em[k].b);
             kadd(&ext, (c * c) / (D * (E - hxx)));
+            if (nuniq < cap) {
+                keys_out[2 * nuniq] = em[k].a;
+                keys_out[2 * nuniq + 1] = em[k].b;
+                c_out[nuniq] = c;
+            }
             ++nuniq;
         }
         k = e;
@@ -896,6 +922,7 @@ int orc_pt2_eps(int norb, const double* h, const double* eri, const uint64_t* S,
     out[1] = kval(&in);
     out[2] = (double)nuniq;
     out[3] = D;
+    out[4] = (double)total;
     free(cS);
     free(em);
     free(cnt);

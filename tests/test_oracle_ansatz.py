@@ -208,6 +208,37 @@ def test_pt2_matches_dense_bruteforce(olib):
     assert got["n_unique"] == int(ext_mask.sum())
 
 
+@pytest.mark.parametrize("nbuckets,bucket_id", [(1, -1), (3, 1)])
+def test_pt2_unique_set_matches_dense_bruteforce(olib, nbuckets, bucket_id):
+    """The deduplicated external set of Eq. (pt2_correction): every configuration outside S
+    within two excitations of some member of S (found by counting differing occupation bits,
+    not by enumerating excitations), ascending by (a, b), with c(x') = (H psi)_x' from the
+    dense brute-force H; with buckets, the members of that hash bucket only."""
+    norb, n = 6, 3
+    h, eri, _ = synth.integrals(norb, 12, 22, 3.0)
+    dets, H = BF.dense_hamiltonian(norb, n, n, h, eri)
+    rng = np.random.default_rng(5)
+    pick = np.sort(rng.choice(len(dets), size=40, replace=False))
+    S = dets[pick]
+    psi = rng.normal(size=40)
+    full = np.zeros(len(dets))
+    full[pick] = psi
+    c = H @ full
+    inS = np.zeros(len(dets), bool)
+    inS[pick] = True
+    diff = (np.bitwise_count(dets[:, None, 0] ^ S[None, :, 0]) +
+            np.bitwise_count(dets[:, None, 1] ^ S[None, :, 1]))
+    reach = ((diff > 0) & (diff <= 4)).any(axis=1) & ~inS
+    if bucket_id >= 0:
+        reach &= np.array([olib.bucket(a, b, nbuckets) == bucket_id for a, b in dets])
+    keys, cu, info = olib.pt2_unique(norb, h, eri, S, psi, -1.0, nbuckets, bucket_id)
+    order = np.lexsort((dets[reach, 1], dets[reach, 0]))
+    assert np.array_equal(keys, dets[reach][order])
+    assert np.abs(cu - c[reach][order]).max() < 1e-13
+    assert info["n_unique"] == int(reach.sum())
+    assert info["ext"] == olib.pt2(norb, h, eri, S, psi, -1.0, nbuckets, bucket_id)["ext"]
+
+
 def test_pt2_buckets_partition(olib, tiny):
     p, csr = tiny
     r = olib.energy_grad(olib.Net(p.net), p.S, csr, with_grad=False)
