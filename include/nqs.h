@@ -240,7 +240,12 @@ int nqs_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr, cons
  * screened perturbative set P) only the contributions with |H_x'y psi_y| >= eps_pt2 to x' outside
  * S are emitted, found by the sorted-integral walk of nqs_hb_select; c(x') sums those, P is the
  * x' that receive at least one, and the internal term takes H_SS psi exactly from the connected
- * sets of S. Synchronises the stream. Errors: NQS_ERR_ARG (also eps_pt2 < 0 or NaN),
+ * sets of S. The screened runs are summed exactly in 128-bit fixed point (each term rounded
+ * once to a grid far below FP64 resolution, one rounding to FP64 per x'), so c(x') does not
+ * depend on the order of its terms; with opts->buckets = 0 the screened emissions are then
+ * written in one traversal (appended in timing order; buffers sized from a counted sample of S
+ * and enlarged once if needed) and split into counted buckets only when they do not fit in
+ * memory. Synchronises the stream. Errors: NQS_ERR_ARG (also eps_pt2 < 0 or NaN),
  * NQS_ERR_OOM (a bucket too large), NQS_ERR_CUDA. */
 int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64_t nS,
             double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
@@ -255,6 +260,19 @@ int nqs_pt2(nqs_problem* problem, const uint64_t* dets, const double* psi, int64
 int nqs_pt2_hss(nqs_problem* problem, const uint64_t* dets, const double* psi, int64_t nS,
                 double E_var, const nqs_csr* hss, const nqs_opts* opts, double* out,
                 double* bucket_partials, nqs_stream_t stream);
+
+/* The deduplicated external set of nqs_pt2 (unscreened) for one hash bucket, for inspection
+ * and testing of Eq. pt2_correction's reduction: every x' in C\S with bucket(x') = bucket (of
+ * `buckets`; the bucket function of nqs_pt2), ascending by (a, b), and c(x') = sum over y in S
+ * of H_x'y psi_y. Runs the same emission, sort and run reduction as nqs_pt2 for that bucket.
+ * dets: device [nS][2], sorted and unique; psi: device [nS] FP64. dets_out: device [capacity][2]
+ * (16-byte aligned), c_out: device [capacity]; both may be NULL with capacity 0. *n_unique
+ * (host) receives the size of the set; if it exceeds capacity nothing is written and the call
+ * returns NQS_ERR_ARG, so the caller can size the buffers and call again. Synchronises the
+ * stream. Errors: NQS_ERR_ARG (also bucket outside 0..buckets-1), NQS_ERR_OOM, NQS_ERR_CUDA. */
+int nqs_pt2_unique(nqs_problem* problem, const uint64_t* dets, const double* psi, int64_t nS,
+                   int buckets, int bucket, uint64_t* dets_out, double* c_out, int64_t capacity,
+                   int64_t* n_unique, nqs_stream_t stream);
 
 /* ---- batched evaluation of many independent problems ------------------------------------ */
 typedef struct nqs_batch nqs_batch; /* opaque */
@@ -286,18 +304,22 @@ int nqs_set_autotune(int on);
 int nqs_autotune_entries(int* M, int* N, int* K, int* width, int capacity);
 
 /* H_SS build without any device allocation (the paper has no counterpart: this exists for
- * callers that cannot allocate device memory, such as a host framework that owns every
- * allocation or code that must not call the allocator while work is being recorded).
- * Same result as nqs_connections, written into caller-owned device buffers: row_ptr
- * [nS + 1] int64, col [capacity] int32, val [capacity] FP64. The library's scratch (hash table
- * of S, row counts, scan partials) lives in one static device array of 8 MiB, which limits
- * nS to 65536 (larger nS returns NQS_ERR_ARG with a message in nqs_last_error()). Every GPU
- * that loads the library holds the array until process exit. The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) with that device current; make it
- * before any stream capture. *nnz (host) receives the number of nonzeros; if it exceeds
- * capacity the call returns NQS_ERR_ARG without writing col/val, so the caller can size the
- * buffers and call again. All calls share the static array: calls that overlap on the GPU
- * race and must be serialised. validate as in nqs_opts. Synchronises the stream. */
+ * callers that cannot allocate device memory, such as a host framework that owns every device
+ * allocation and gives the library none of its own, or an embedded solver that runs on a fixed
+ * device budget). Same result as nqs_connections, written into caller-owned device buffers:
+ * row_ptr [nS + 1] int64, col [capacity] int32, val [capacity] FP64. The library's scratch (hash
+ * table of S, row counts, scan partials, validation flags) lives in one static device array of
+ * 8 MiB, which limits nS to 65536 (larger nS returns NQS_ERR_ARG with a message in
+ * nqs_last_error()). Every GPU that loads the library holds the array until process exit. The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current and keeps it for later calls on that device, which assumes the device's
+ * primary context lives until the process exits (no cudaDeviceReset in between); make that
+ * first call before any stream capture. *nnz (host) receives the number of nonzeros; if it
+ * exceeds capacity the call returns NQS_ERR_ARG without writing col/val, so the caller can size
+ * the buffers and call again. All calls share the static array, which keeps the previous
+ * call's contents (what must start at zero is cleared on every call): calls that overlap on
+ * the GPU race and must be serialised. validate as in nqs_opts. Synchronises the stream (the
+ * number of nonzeros is read back to the host before col/val are written). */
 int nqs_connections_noalloc(nqs_problem* problem, const uint64_t* dets, int64_t nS, int validate,
                             int64_t* row_ptr, int32_t* col, double* val, int64_t capacity,
                             int64_t* nnz, int64_t* n_enumerated, nqs_stream_t stream);
@@ -361,6 +383,22 @@ int nqs_select(nqs_problem* problem, const uint64_t* T, const double* logabs, in
  * for strides the tensor-memory-access unit cannot take. */
 int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                   float* C, int64_t ldc, int* err_flag, nqs_stream_t stream);
+
+/* ---- failure detection and memory accounting (not steps of the method) ------------------ */
+/* Check of the timeout path: one device thread waits, with the same bounded mbarrier wait as
+ * the tensor-core GEMM pipeline, on a barrier that nothing completes; the wait gives up after
+ * limit_cycles SM clocks (1 .. 4e9; the pipeline's own limit is 4e9, about 2 s) and reports
+ * through the problem's error word exactly as a timed-out pipeline does. Returns
+ * NQS_ERR_TIMEOUT (the expected result) and clears the word; the CUDA context stays usable.
+ * Synchronises the stream. Errors: NQS_ERR_ARG, NQS_ERR_CUDA. */
+int nqs_wait_probe(nqs_problem* problem, int64_t limit_cycles, nqs_stream_t stream);
+/* Cap on the problem's stream-ordered scratch pool: a scratch request that would take the
+ * pool's bytes in use above `bytes` fails and the call returns NQS_ERR_OOM, with every
+ * scratch block it took returned to the pool. 0 removes the cap. Errors: NQS_ERR_ARG. */
+int nqs_set_scratch_limit(nqs_problem* problem, int64_t bytes);
+/* Bytes of the problem's scratch pool in use (scratch of running calls and library-owned CSRs)
+ * and reserved from the device (kept between calls). Errors: NQS_ERR_ARG, NQS_ERR_CUDA. */
+int nqs_pool_usage(nqs_problem* problem, int64_t* used, int64_t* reserved);
 
 /* Optional per-kernel timing for benchmarks (not part of the method): when enabled, the
  * library brackets its main kernel launches with CUDA events recorded on the launching stream.

@@ -338,8 +338,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// bounded wait that also gives up as soon as another role of the CTA has aborted
-__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort) {
+// bounded wait that also gives up as soon as another role of the CTA has aborted; `limit` SM
+// clocks (about 2 s by default)
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                             long long limit = 4000000000ll) {
     const uint32_t addr = smem_u32(bar);
     const long long t0 = clock64();
     while (true) {
@@ -353,7 +355,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, vol
             : "memory");
         if (done) return true;
         if (*abort) return false;
-        if (clock64() - t0 > 4000000000ll) {
+        if (clock64() - t0 > limit) {
             *abort = 1;
             return false;
         }
@@ -803,4 +805,31 @@ extern "C" int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t 
     g.ldc = ldc;
     g.err = err_flag;
     return gemm_bf16_tcgen05(g, sc, s);
+}
+
+// ------------------------------------------------------------------------------------------
+// Failure-detection check: one thread waits, with the pipeline's bounded mbarrier wait, on a
+// barrier that expects one arrival that never comes. The wait gives up after `limit` clocks
+// and reports through the problem's error word, as a timed-out GEMM pipeline does.
+// ------------------------------------------------------------------------------------------
+__global__ void k_wait_probe(long long limit, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_ab(&bar, 0u, (volatile int*)&abort_flag, limit))
+        atomicExch(err, 1);
+    __syncthreads();
+}
+
+extern "C" int nqs_wait_probe(nqs_problem* p, int64_t limit_cycles, nqs_stream_t stream) {
+    if (!p || limit_cycles < 1 || limit_cycles > 4000000000ll) return NQS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    k_wait_probe<<<1, 32, 0, s>>>((long long)limit_cycles, p->err_word);
+    NQS_CK_LAUNCH();
+    return check_err_word(p, s);
 }

@@ -195,13 +195,20 @@ __device__ __forceinline__ double double_element(const ProblemDev& P, int grp, u
     return exc_sign(wA, i, a) * exc_sign(wB, j, b) < 0 ? -v : v;
 }
 
-// The screened traversal of one x per warp, in four modes:
+// The screened traversal of one x per warp, in six modes:
 //   HB_COUNT / HB_EMIT  heat-bath set: cnt[det] = number of kept pairs, or the pairs
 //                       (key, |H_x'x psi_x|) written from offs[det] on;
 //   PT_COUNT / PT_EMIT  screened PT2 emissions of one hash bucket: the same test plus
-//                       bucket(x') == bucket, emitting the signed H_x'x psi_x.
+//                       bucket(x') == bucket, emitting the signed H_x'x psi_x;
+//   HB_APPEND / PT_APPEND  one traversal without counts: each warp stages its kept pairs in
+//                       shared memory and appends them 32 at a time at a position taken from
+//                       the global cursor (*cursor counts every pair; pairs at or past `cap`
+//                       are not written, so *cursor > cap tells the host to retry with more
+//                       room). The order of the output then depends on timing; everything
+//                       downstream is order independent (a sort, exact run sums, a maximum).
 // examined (may be null) accumulates the number of candidates whose coupling was tested.
-enum { HB_COUNT = 0, HB_EMIT = 1, PT_COUNT = 2, PT_EMIT = 3 };
+enum { HB_COUNT = 0, HB_EMIT = 1, PT_COUNT = 2, PT_EMIT = 3, HB_APPEND = 5, PT_APPEND = 7 };
+#define HB_STAGE 64  // staged pairs per warp (append modes)
 
 template <int MODE, class K>
 __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS H, HbTab T,
@@ -213,22 +220,56 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                                                           const int64_t* __restrict__ offs,
                                                           K* __restrict__ keys,
                                                           double* __restrict__ vals,
-                                                          unsigned long long* examined) {
+                                                          unsigned long long* examined,
+                                                          unsigned long long* __restrict__ cursor,
+                                                          uint64_t cap) {
     constexpr bool EMIT = (MODE & 1) != 0;
-    constexpr bool PTM = MODE >= PT_COUNT;
+    constexpr bool PTM = (MODE & 2) != 0;
+    constexpr bool APPEND = (MODE & 4) != 0;
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables PT = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    // append staging: HB_STAGE keys then HB_STAGE values per warp, after the contexts
+    uint8_t* stage = smem + pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx) +
+                     (threadIdx.x >> 5) * HB_STAGE * (sizeof(K) + sizeof(double));
+    K* sk = (K*)stage;
+    double* sv = (double*)(stage + HB_STAGE * sizeof(K));
     const int lane = threadIdx.x & 31;
     const unsigned lt = lanemask_lt();
     const int n = P.norb;
     const uint32_t nsing = (uint32_t)(P.sA + P.sB);
+    int qn = 0;  // staged pairs of this warp (append modes)
+    // write the first `cnt_` staged pairs at a reserved position and move the rest down
+    auto flush = [&](int cnt_) {
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)cnt_);
+        base = __shfl_sync(FULL_MASK, base, 0);
+        if (lane < cnt_ && base + lane < cap) {
+            keys[base + lane] = sk[lane];
+            vals[base + lane] = sv[lane];
+        }
+        const int rest = qn - cnt_;
+        K k2 = key_zero<K>();
+        double v2 = 0.0;
+        if (lane < rest) {
+            k2 = sk[cnt_ + lane];
+            v2 = sv[cnt_ + lane];
+        }
+        __syncwarp();
+        if (lane < rest) {
+            sk[lane] = k2;
+            sv[lane] = v2;
+        }
+        __syncwarp();
+        qn = rest;
+    };
     for (int64_t det = (int64_t)blockIdx.x * HB_WARPS + (threadIdx.x >> 5); det < nS;
          det += (int64_t)gridDim.x * HB_WARPS) {
         const ulonglong2 x = S[det];
         const double py = psi[det];
         const double ap = fabs(py);
-        int64_t run = EMIT ? offs[det] : 0;
+        int64_t run = (EMIT && !APPEND) ? offs[det] : 0;
         unsigned long long tested = 0;
         // m = |H| |psi| >= eps fails for every coupling when |psi| = 0 < eps, and when psi is
         // not a number: nothing to do for this x
@@ -239,7 +280,15 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
         fill_ctx(P, x.x, x.y, ctx, lane);
         auto keep = [&](bool take, uint64_t a2, uint64_t b2, double m) {
             const unsigned bal = __ballot_sync(FULL_MASK, take);
-            if (EMIT && take) {
+            if (APPEND) {
+                if (take) {
+                    const int slot = qn + __popc(bal & lt);
+                    sk[slot] = key_make<K>(a2, b2, n);
+                    sv[slot] = m;
+                }
+                qn += __popc(bal);
+                if (qn >= 32) flush(32);
+            } else if (EMIT && take) {
                 const int64_t pos = run + __popc(bal & lt);
                 keys[pos] = key_make<K>(a2, b2, n);
                 vals[pos] = m;
@@ -346,6 +395,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
         if (examined && lane == 0) atomicAdd(examined, tested);
         __syncwarp();
     }
+    if (APPEND && qn > 0) flush(qn);
 }
 
 // output: one configuration per run of equal keys, with the maximum coupling of the run
@@ -403,7 +453,7 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
         ProfScope prof_(PROF_HB_SELECT, s);
         k_hb_select<HB_COUNT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
             P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, cnt, nullptr, nullptr, nullptr,
-            examined);
+            examined, nullptr, 0);
     }
     NQS_CK_LAUNCH();
     NQS_TRY(scan_exclusive_i64(p, sc, cnt, offs, nS, total_dev, s));
@@ -429,7 +479,7 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
         ProfScope prof_(PROF_HB_SELECT, s);
         k_hb_select<HB_EMIT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
             P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, nullptr, offs, keys, vals,
-            nullptr);
+            nullptr, nullptr, 0);
     }
     NQS_CK_LAUNCH();
     if (sizeof(K) == 4)
@@ -489,12 +539,12 @@ static int hb_pt2_pass_k(nqs_problem* p, const HbTab& T, const HashS& H, const u
         ProfScope prof_(PROF_PT2_COUNT, s);
         k_hb_select<PT_COUNT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
             P, H, T, (const ulonglong2*)dets, psi, nS, eps, B, bucket, cnt, nullptr, nullptr,
-            nullptr, nullptr);
+            nullptr, nullptr, nullptr, 0);
     } else {
         ProfScope prof_(PROF_PT2_EMIT, s);
         k_hb_select<PT_EMIT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
             P, H, T, (const ulonglong2*)dets, psi, nS, eps, B, bucket, nullptr, offs, (K*)keys,
-            vals, nullptr);
+            vals, nullptr, nullptr, 0);
     }
     NQS_CK_LAUNCH();
     return NQS_OK;
@@ -514,6 +564,46 @@ int hb_pt2_pass(nqs_problem* p, const HashS& H, const uint64_t* dets, const doub
                                        vals, s);
     return hb_pt2_pass_k<Key128>(p, T, H, dets, psi, nS, eps, B, bucket, cnt, offs, keys, vals,
                                  s);
+}
+
+// The screened PT2 emissions of all of C\S in one traversal (PT_APPEND): the pairs go to
+// keys / vals [cap] in an order that depends on timing; *cursor_dev (zeroed here) receives the
+// number of pairs, which exceeds cap when the buffers were too small (then nothing past cap
+// was written and the caller must retry or split into buckets).
+template <class K>
+static int hb_pt2_append_k(nqs_problem* p, const HbTab& T, const HashS& H, const uint64_t* dets,
+                           const double* psi, int64_t nS, double eps, void* keys, double* vals,
+                           int64_t cap, unsigned long long* cursor_dev, cudaStream_t s) {
+    const ProblemDev& P = p->d;
+    const size_t smem = pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx) +
+                        (size_t)HB_WARPS * HB_STAGE * (sizeof(K) + sizeof(double));
+    if (smem > 48 * 1024)
+        NQS_CK(cudaFuncSetAttribute(k_hb_select<PT_APPEND, K>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NQS_CK(cudaMemsetAsync(cursor_dev, 0, sizeof(unsigned long long), s));
+    {
+        ProfScope prof_(PROF_PT2_EMIT, s);
+        k_hb_select<PT_APPEND, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
+            P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, nullptr, nullptr, (K*)keys,
+            vals, nullptr, cursor_dev, (uint64_t)cap);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int hb_pt2_append(nqs_problem* p, const HashS& H, const uint64_t* dets, const double* psi,
+                  int64_t nS, double eps, void* keys, double* vals, int64_t cap,
+                  unsigned long long* cursor_dev, cudaStream_t s) {
+    HbTab T;
+    NQS_TRY(hb_tables(p, &T));
+    const int kbits = 2 * p->d.norb;
+    if (kbits <= 32)
+        return hb_pt2_append_k<uint32_t>(p, T, H, dets, psi, nS, eps, keys, vals, cap, cursor_dev,
+                                         s);
+    if (kbits <= 64)
+        return hb_pt2_append_k<uint64_t>(p, T, H, dets, psi, nS, eps, keys, vals, cap, cursor_dev,
+                                         s);
+    return hb_pt2_append_k<Key128>(p, T, H, dets, psi, nS, eps, keys, vals, cap, cursor_dev, s);
 }
 
 extern "C" int nqs_hb_select(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,

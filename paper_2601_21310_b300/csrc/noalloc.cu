@@ -1,9 +1,9 @@
 // nqs_connections_noalloc: the H_SS build for callers that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc or a stream-ordered allocator at all: code that runs
-// inside a host that owns every allocation (a framework with its own arena, an embedded
-// solver that hands the library a fixed budget), or code that must not touch the allocator
-// while other work is being recorded. For them this entry point does the same work as
+// inside a host that owns every device allocation (a framework with its own arena that gives
+// the library none) or an embedded solver that runs on a fixed device budget. For them this
+// entry point does the same work as
 // nqs_connections with all inputs and outputs passed in and its scratch (the hash table of S,
 // the per-row counts, the scan partials and the validation flags) in one file-scope device
 // array of fixed size, NQS_NOALLOC_SCRATCH_BYTES. Every GPU that loads this library holds that
@@ -11,7 +11,10 @@
 //
 // The host cannot use the array's name as a device address (in host code it names a host-side
 // stand-in), so the first call on each device, with that device current, looks the address up
-// with cudaGetSymbolAddress and caches it; make that first call before any stream capture.
+// with cudaGetSymbolAddress and caches it; make that first call before any stream capture. The
+// cache assumes the device's primary context lives until the process exits (a cudaDeviceReset
+// would leave a stale address behind). The call synchronises its stream: it reads the number
+// of nonzeros back to the host before writing the columns.
 // All calls share the array and it keeps the previous call's contents: everything that must
 // start from zero is cleared on every call, and calls whose work overlaps on the GPU (two
 // streams, two host threads) race on it and must be serialised by the caller.

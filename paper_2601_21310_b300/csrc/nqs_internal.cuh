@@ -66,6 +66,9 @@ struct ProblemDev {
     const long long* Xt;
     const long long* Yt;
     int nbytes;
+    // bound on |<x'|H|y>| over every off-diagonal pair (singles: |h_ia| + sum_j (2 |(ia|jj)| +
+    // |(ij|ja)|); doubles: 2 max |(pq|rs)|): the range of the PT2 fixed-point run sums
+    double hoff_max;
 };
 
 struct nqs_problem {
@@ -79,6 +82,7 @@ struct nqs_problem {
     int* err_word;       // device: set by a kernel whose bounded wait timed out
     double* hb_val;      // heat-bath integral tables (hb.cu), built on first use
     uint16_t* hb_code;
+    size_t scratch_limit;  // 0 = none; else scratch requests beyond it fail with NQS_ERR_OOM
 };
 
 // read and clear the problem's device error word (synchronises the stream)
@@ -226,6 +230,11 @@ int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, Ha
 int hb_pt2_pass(nqs_problem* p, const HashS& H, const uint64_t* dets, const double* psi,
                 int64_t nS, double eps, uint64_t B, uint64_t bucket, int64_t* cnt,
                 const int64_t* offs, void* keys, double* vals, cudaStream_t s);
+// the same emissions for all of C\S in one traversal, appended in timing order to keys / vals
+// [cap]; *cursor_dev receives the number of pairs (> cap: too small, nothing past cap written)
+int hb_pt2_append(nqs_problem* p, const HashS& H, const uint64_t* dets, const double* psi,
+                  int64_t nS, double eps, void* keys, double* vals, int64_t cap,
+                  unsigned long long* cursor_dev, cudaStream_t s);
 int validate_dets(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, bool sorted,
                   cudaStream_t s);
 

@@ -54,6 +54,14 @@ extern "C" void nqs_opts_default(nqs_opts* o) {
 // scratch: a library-owned memory pool, so repeated calls reuse memory without cudaMalloc
 // ------------------------------------------------------------------------------------------
 int nqs_scratch_alloc(nqs_problem* p, void** ptr, size_t bytes, cudaStream_t s) {
+    if (p->scratch_limit) {
+        uint64_t used = 0;
+        NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        if (used + bytes > p->scratch_limit) {
+            nqs_record_message("scratch request beyond the problem's scratch limit");
+            return NQS_ERR_OOM;
+        }
+    }
     cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, p->pool, s);
     if (e != cudaSuccess) {
         nqs_record_error("cudaMallocFromPoolAsync", e, __FILE__, __LINE__);
@@ -230,6 +238,18 @@ extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double*
         d.JKfx = p->fx + n;
         d.Jfx = p->fx + n + n * n;
         d.dscale = ldexp(1.0, -e);
+        double hmax = 0.0, emax = 0.0;
+        for (size_t q = 0; q < (size_t)n * n * n * n; ++q) emax = fmax(emax, fabs(eri[q]));
+        for (int i = 0; i < n; ++i)
+            for (int a = 0; a < n; ++a) {
+                if (a == i) continue;
+                double f = fabs(h[i * n + a]);
+                for (int j = 0; j < n; ++j)
+                    f += 2.0 * fabs(eri[(((size_t)i * n + a) * n + j) * n + j]) +
+                         fabs(eri[(((size_t)i * n + j) * n + j) * n + a]);
+                hmax = fmax(hmax, f);
+            }
+        d.hoff_max = fmax(hmax, 2.0 * emax) * (1.0 + 1e-12);
         // byte tables
         const int nb = (n + 7) / 8;
         const size_t nD = (size_t)nb * 256, nX = (size_t)nb * (nb - 1) / 2 * 65536,
@@ -267,6 +287,22 @@ extern "C" int nqs_problem_destroy(nqs_problem* p) {
     cudaFree(p->hb_code);
     if (p->pool) cudaMemPoolDestroy(p->pool);
     free(p);
+    return NQS_OK;
+}
+
+extern "C" int nqs_set_scratch_limit(nqs_problem* p, int64_t bytes) {
+    if (!p || bytes < 0) return NQS_ERR_ARG;
+    p->scratch_limit = (size_t)bytes;
+    return NQS_OK;
+}
+
+extern "C" int nqs_pool_usage(nqs_problem* p, int64_t* used, int64_t* reserved) {
+    if (!p || !used || !reserved) return NQS_ERR_ARG;
+    uint64_t u = 0, r = 0;
+    NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &u));
+    NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrReservedMemCurrent, &r));
+    *used = (int64_t)u;
+    *reserved = (int64_t)r;
     return NQS_OK;
 }
 

@@ -1,16 +1,19 @@
 // Epstein-Nesbet PT2 over the connected space (Eq. pt2_correction; Algorithm 1 step 4).
 //
 // For each hash bucket b (SplitMix64 finaliser of the det, mod B):
-//   1. emit (key x', H_x'y psi_y) for every excitation x' of every y in S with bucket(x') = b,
-//      in canonical order (y ascending, then canonical excitation index) - with B = 1 the
-//      position of every emission is fixed, otherwise a count pass and a scan give them;
-//   2. stable LSD radix sort by key (2 norb bits), so equal keys stay in emission order;
+//   1. emit (key x', H_x'y psi_y) for every excitation x' of every y in S with bucket(x') = b:
+//      with B = 1 the position of every emission is fixed (y ascending, then canonical
+//      excitation index), otherwise a count pass and a scan give them; the screened form
+//      appends its emissions through per-warp staging in one traversal;
+//   2. stable LSD radix sort by key (2 norb bits), so equal keys keep their emission order;
 //   3. count the run heads per chunk and scan the counts (each chunk's first run index); each
 //      warp then sums the runs that start in its chunk, lane by lane along runs, carrying the
-//      open run across lanes and steps -> c(x') for every unique x'; a per-unique pass sends
-//      members of S to the
-//      internal term (c(x) is the off-diagonal part of (H_SS psi)_x) and turns the others into
-//      c^2 / (D (E - H_x'x')) with H_x'x' from the Slater-Condon diagonal;
+//      open run across lanes and steps -> c(x') for every unique x': in FP64 in emission order
+//      for the unscreened form (fixed positions, so a fixed order), in exact 128-bit fixed
+//      point (fx128.cuh, independent of the order of the run's terms) for the screened form,
+//      whose appended emissions have no fixed order; a per-unique pass sends members of S to
+//      the internal term (c(x) is the off-diagonal part of (H_SS psi)_x) and turns the others
+//      into c^2 / (D (E - H_x'x')) with H_x'x' from the Slater-Condon diagonal;
 //   4. compensated sums of the external terms, and of the internal terms of the dets of S in
 //      bucket b: r_x = H_xx psi_x + c(x) - E psi_x, r_x^2 / (D (E - H_xx)).
 // D = psi.psi, compensated. Keys are the 2 norb-bit number (a << norb) | b: uint32 when
@@ -22,6 +25,7 @@
 #include <vector>
 
 #include "excite.cuh"
+#include "fx128.cuh"
 #include "nqs_internal.cuh"
 #include "prof.cuh"
 
@@ -296,7 +300,9 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit_all(ProblemDev P,
 //                add per element); the open run at each lane's end is passed to the next lane (a
 //                segmented shuffle scan only when some lane holds no head) and, across steps, to
 //                lane 0. The last element of a run writes the run's sum and key at the run index.
-// Sums go in element order within a lane and lane order across lanes: deterministic.
+// Two forms: FP64 sums in element order (emissions at fixed positions), and exact 128-bit
+// fixed-point sums converted to FP64 once per run (emissions appended in timing order), whose
+// c(x') does not depend on the order of the run's terms.
 // ------------------------------------------------------------------------------------------
 #define SEG_CHUNK 2048
 #define SEG_ITEMS 8
@@ -363,6 +369,8 @@ __global__ void __launch_bounds__(256) k_seg_heads(const K* __restrict__ keys, i
     }
 }
 
+// FP64 run sums in element order within a lane and lane order across lanes (the form for
+// emissions at fixed positions, whose order is then fixed too)
 template <class K>
 __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
                                                  const double* __restrict__ vals,
@@ -501,11 +509,177 @@ __global__ void __launch_bounds__(256) k_seg_sum(const K* __restrict__ keys,
     }
 }
 
+// The same reduction with exact 128-bit fixed-point run sums (fx128.cuh): the form for
+// emissions appended in timing order, whose run sums must not depend on the order of their
+// terms. Converting each term costs integer instructions (the kernel is ALU-bound on this part,
+// about twice the FP64 form's time), so the FP64 form is used wherever the order is fixed.
+template <class K>
+__global__ void __launch_bounds__(256) k_seg_sum_fx(const K* __restrict__ keys,
+                                                 const double* __restrict__ vals,
+                                                 const uint32_t* __restrict__ rbase, int64_t n,
+                                                 const unsigned long long* __restrict__ vmax_bits,
+                                                 double hoff_max, double run_max,
+                                                 double* __restrict__ cU, K* __restrict__ keyU) {
+    const int lane = threadIdx.x & 31;
+    constexpr int W = 32 * SEG_ITEMS;  // elements per warp step
+    // the fixed-point grid: every term is |H_x'y psi_y| <= hoff_max * max|psi| and a run has at
+    // most run_max terms
+    const double vmax = __dmul_ru(hoff_max, __longlong_as_double((long long)*vmax_bits));
+    const bool finite = vmax <= 1.7976931348623157e308;
+    const int F = fx_scale(finite ? vmax : 1.0, run_max);
+    const int64_t nchunks = (n + SEG_CHUNK - 1) / SEG_CHUNK;
+    for (int64_t ch = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; ch < nchunks;
+         ch += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t c0 = ch * SEG_CHUNK, c1 = min(n, c0 + SEG_CHUNK);
+        // first head inside [c0, c1)
+        int64_t s0 = -1;
+        for (int64_t b = c0; b < c1 && s0 < 0; b += 32) {
+            const int64_t i = b + lane;
+            const bool h = i < c1 && (i == 0 || keys[i] != keys[i - 1]);
+            const unsigned m = __ballot_sync(FULL_MASK, h);
+            if (m) s0 = b + __ffs(m) - 1;
+        }
+        if (s0 < 0) continue;  // every element continues a run owned by an earlier chunk
+        const int64_t b0 = s0 & ~(int64_t)(SEG_ITEMS - 1);
+        K kbefore = b0 > 0 ? keys[b0 - 1] : key_zero<K>();
+        uint32_t ridx0 = rbase[ch];  // run index of the next head
+        Fx128 carry = fx_zero();     // the open run entering lane 0
+        for (int64_t b = b0; b < n; b += W) {
+            const int64_t i0 = b + (int64_t)SEG_ITEMS * lane;
+            K kk[SEG_ITEMS];
+            double v[SEG_ITEMS];
+            seg_load_keys(keys, i0, n, kk);
+            seg_load_vals(vals, i0, n, v);
+            const K knext = b + W < n ? keys[b + W] : key_zero<K>();
+            const K up = key_shfl_up(kk[SEG_ITEMS - 1], 1);
+            // heads, and the first element that ends the walk (a head at or past c1, or past n)
+            const int ja = (b == b0 && lane == 0) ? (int)(s0 - b0) : 0;
+            unsigned hm = 0;
+            int jstop = SEG_ITEMS;
+            K kp = lane == 0 ? kbefore : up;
+#pragma unroll
+            for (int j = 0; j < SEG_ITEMS; ++j) {
+                const int64_t i = i0 + j;
+                const bool in = i < n;
+                const bool h = in && (i == 0 || kk[j] != kp);
+                if (h) hm |= 1u << j;
+                if ((!in || (h && i >= c1)) && jstop == SEG_ITEMS) jstop = j;
+                kp = kk[j];
+            }
+            const unsigned sm = __ballot_sync(FULL_MASK, jstop < SEG_ITEMS);
+            const int L = sm ? __ffs(sm) - 1 : 32;
+            const int jL = sm ? __shfl_sync(FULL_MASK, jstop, L) : 0;
+            const int je = lane < L ? SEG_ITEMS : (lane == L ? jL : 0);  // active: [ja, je)
+            const unsigned am = (je >= SEG_ITEMS ? 0xffu : ((1u << je) - 1u)) & ~((1u << ja) - 1u);
+            hm &= am;
+            const bool act = am != 0;
+            const bool lh = hm != 0;
+            // run index of each tail: heads before this lane (warp prefix) + heads up to it
+            const uint32_t nh = (uint32_t)__popc(hm);
+            uint32_t hpre = nh;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL_MASK, hpre, o);
+                if (lane >= o) hpre += y;
+            }
+            const uint32_t htot = __shfl_sync(FULL_MASK, hpre, 31);
+            hpre -= nh;
+            // does the run at the lane's last active element end there?
+            const int first_ends = (!act || (hm & 1u)) ? 1 : 0;
+            const int next_first_ends = __shfl_down_sync(FULL_MASK, first_ends, 1);
+            bool end_after;
+            if (je < SEG_ITEMS) end_after = true;
+            else if (lane < 31) end_after = next_first_ends != 0;
+            else end_after = (b + W >= n) || (knext != kk[SEG_ITEMS - 1]);
+            // tails: active elements followed by a head (or by the end of the walk)
+            const unsigned tm = am & ((hm >> 1) | (end_after ? (1u << (je - 1)) : 0u));
+            // lane pass: running sums along runs, one exact integer add per element. A run that
+            // starts in this lane is complete at its tail and written there; the lane's first
+            // segment (its elements before its first head) continues a run entering the lane and
+            // is finished after the scan below. fsum is that first segment's sum.
+            Fx128 run = fx_zero(), fsum = fx_zero();
+            bool tfirst = false;  // the first segment's run ends in this lane, at key kfirst
+            K kfirst = key_zero<K>();
+#pragma unroll
+            for (int j = 0; j < SEG_ITEMS; ++j) {
+                if ((am >> j) & 1u) {
+                    const Fx128 fv = fx_from_double(v[j], F);
+                    const bool head = (hm >> j) & 1u;
+                    if (head && (hm & ((1u << j) - 1u)) == 0u) fsum = run;
+                    run = head ? fv : fx_add(run, fv);
+                    if ((tm >> j) & 1u) {
+                        const unsigned upto = hm & ((2u << j) - 1u);  // heads at or before j
+                        if (upto) {
+                            const uint32_t r = ridx0 + hpre + (uint32_t)__popc(upto) - 1u;
+                            cU[r] = finite ? fx_to_double(run, F) : vmax;
+                            keyU[r] = kk[j];
+                        } else {
+                            tfirst = true;
+                            kfirst = kk[j];
+                        }
+                    }
+                }
+            }
+            if (hm == 0u) fsum = run;
+            const Fx128 lsum = act ? run : fx_zero();
+            // the open run entering this lane: from the previous lane, or a segmented scan when
+            // some active lane holds no head (a run crosses whole lanes)
+            Fx128 inc, nextcarry;
+            if (!__any_sync(FULL_MASK, act && !lh)) {
+                const Fx128 prev = fx_shfl_up(lsum, 1);
+                inc = lane == 0 ? carry : prev;
+                nextcarry = fx_shfl(lsum, 31);
+            } else {
+                Fx128 sv = lsum;
+                int sf = lh ? 1 : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const Fx128 yv = fx_shfl_up(sv, o);
+                    const int yf = __shfl_up_sync(FULL_MASK, sf, o);
+                    if (lane >= o && !sf) sv = fx_add(yv, sv);
+                    if (lane >= o) sf |= yf;
+                }
+                Fx128 ex = fx_shfl_up(sv, 1);
+                int exf = __shfl_up_sync(FULL_MASK, sf, 1);
+                if (lane == 0) {
+                    ex = fx_zero();
+                    exf = 0;
+                }
+                inc = exf ? ex : fx_add(carry, ex);
+                const Fx128 sv31 = fx_shfl(sv, 31);
+                const int sf31 = __shfl_sync(FULL_MASK, sf, 31);
+                nextcarry = sf31 ? sv31 : fx_add(carry, sv31);
+            }
+            if (tfirst) {  // the first segment's run ends in this lane: one add
+                const uint32_t r = ridx0 + hpre - 1u;
+                cU[r] = finite ? fx_to_double(fx_add(inc, fsum), F) : vmax;
+                keyU[r] = kfirst;
+            }
+            ridx0 += htot;
+            carry = nextcarry;
+            kbefore = key_shfl(kk[SEG_ITEMS - 1], 31);
+            if (L < 32) break;
+        }
+    }
+}
+
+// bit pattern of max |psi| (non-negative doubles order like their bit patterns)
+__global__ void k_absmax_bits(const double* __restrict__ x, int64_t n,
+                              unsigned long long* __restrict__ out) {
+    unsigned long long m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(x[i])));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL_MASK, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 template <class K>
 __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU,
                                const double* __restrict__ cU, int64_t nuniq,
                                const double* __restrict__ Dp, double E, double* __restrict__ cS,
-                               double* __restrict__ eterm, unsigned long long* __restrict__ next) {
+                               double* __restrict__ eterm, unsigned long long* __restrict__ next,
+                               uint32_t* __restrict__ ext_flag) {
 
     const double D = *Dp;
     const int norb = P.norb;
@@ -516,6 +690,7 @@ __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU
         key_split(keyU[u], norb, a, b);
         const double c = cU[u];
         const int32_t s = hash_lookup(H, a, b);
+        if (ext_flag) ext_flag[u] = s >= 0 ? 0u : 1u;
         if (s >= 0) {
             cS[s] = c;
             eterm[u] = 0.0;
@@ -527,6 +702,34 @@ __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU
     }
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(FULL_MASK, local, o);
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(next, local);
+}
+
+// every stride-th configuration of S and its amplitude (the sample that sizes the screened
+// single traversal)
+__global__ void k_gather_stride(const ulonglong2* __restrict__ S, const double* __restrict__ psi,
+                                int64_t ns, int64_t stride, ulonglong2* __restrict__ So,
+                                double* __restrict__ po) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        So[i] = S[i * stride];
+        po[i] = psi[i * stride];
+    }
+}
+
+// the external unique set of one bucket, in key order: configuration and c(x')
+template <class K>
+__global__ void k_unique_out(const K* __restrict__ keyU, const double* __restrict__ cU,
+                             const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                             int64_t nuniq, int norb, ulonglong2* __restrict__ dets_out,
+                             double* __restrict__ c_out) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nuniq;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[u]) continue;
+        uint64_t a, b;
+        key_split(keyU[u], norb, a, b);
+        dets_out[pos[u]] = make_ulonglong2(a, b);
+        c_out[pos[u]] = cU[u];
+    }
 }
 
 // cS[x] = sum over the excitations y of x that lie in S of <x|H|y> psi_y (the off-diagonal part
@@ -612,12 +815,29 @@ static double host_ksum(const std::vector<double>& v) {
     return s + c;
 }
 
+// What every bucket's reduction needs besides its pairs.
+struct Pt2Ctx {
+    const HashS* H;
+    double* cS;                      // device [nS]: c(x) of the members of S
+    double* D_dev;                   // device: psi.psi
+    unsigned long long* vmax_bits;   // device: bit pattern of max |psi|
+    double run_max;                  // longest possible run (terms of one c(x'))
+    double E_var;
+    bool exact;                      // fixed-point run sums (screened emissions)
+    // optional: the external unique set of the bucket (nqs_pt2_unique)
+    bool uq_on;
+    uint64_t* uq_dets;  // device [uq_cap][2] (may be null: size only)
+    double* uq_c;       // device [uq_cap]
+    int64_t uq_cap;
+    int64_t uq_n;       // host: size of the set (written by pt2_reduce)
+};
+
 // sort, deduplicate and reduce one bucket's n emitted pairs (keys, vals; keys2 / vals2 are the
 // sort's second buffers, n long), adding its external sum on the device
 template <class K>
 static int pt2_reduce(nqs_problem* p, K* keys, double* vals, K* keys2, double* vals2, int64_t n,
-                      double E_var, const HashS& H, double* cS, double* D_dev, double* ext_dev,
-                      unsigned long long* nuniq_dev, cudaStream_t s) {
+                      Pt2Ctx& cx, double* ext_dev, unsigned long long* nuniq_dev,
+                      cudaStream_t s) {
     const ProblemDev& P = p->d;
     Scratch bs(p, s);
     if (sizeof(K) == 4)
@@ -650,22 +870,47 @@ static int pt2_reduce(nqs_problem* p, K* keys, double* vals, K* keys2, double* v
     }
     double *cU, *eterm;
     K* keyU;
+    uint32_t *flag = nullptr, *pos = nullptr;
     NQS_TRY(bs.get(&cU, nuniq));
     NQS_TRY(bs.get(&keyU, nuniq));
     NQS_TRY(bs.get(&eterm, nuniq));
+    if (cx.uq_on) {
+        NQS_TRY(bs.get(&flag, nuniq));
+        NQS_TRY(bs.get(&pos, nuniq));
+    }
     if (nuniq > 0) {
         {
             ProfScope prof_(PROF_SEG_REDUCE, s);
-            k_seg_sum<K><<<grid_for(nchunks * 32, 256, 148 * 16), 256, 0, s>>>(keys, vals, rbase, n,
-                                                                             cU, keyU);
+            if (cx.exact)
+                k_seg_sum_fx<K><<<grid_for(nchunks * 32, 256, 148 * 16), 256, 0, s>>>(
+                    keys, vals, rbase, n, cx.vmax_bits, P.hoff_max, cx.run_max, cU, keyU);
+            else
+                k_seg_sum<K><<<grid_for(nchunks * 32, 256, 148 * 16), 256, 0, s>>>(
+                    keys, vals, rbase, n, cU, keyU);
         }
         NQS_CK_LAUNCH();
         {
             ProfScope prof_(PROF_UNIQUE, s);
-            k_unique_terms<K><<<grid_for(nuniq, 256), 256, 0, s>>>(P, H, keyU, cU, nuniq, D_dev,
-                                                                     E_var, cS, eterm, nuniq_dev);
+            k_unique_terms<K><<<grid_for(nuniq, 256), 256, 0, s>>>(
+                P, *cx.H, keyU, cU, nuniq, cx.D_dev, cx.E_var, cx.cS, eterm, nuniq_dev, flag);
         }
         NQS_CK_LAUNCH();
+    }
+    if (cx.uq_on) {
+        cx.uq_n = 0;
+        if (nuniq > 0) {
+            NQS_TRY(scan_exclusive_u32(p, bs, flag, pos, nuniq, s));
+            uint32_t lp = 0, lf = 0;
+            NQS_CK(cudaMemcpyAsync(&lp, pos + nuniq - 1, 4, cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaMemcpyAsync(&lf, flag + nuniq - 1, 4, cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaStreamSynchronize(s));
+            cx.uq_n = (int64_t)lp + lf;
+            if (cx.uq_dets && cx.uq_n <= cx.uq_cap) {
+                k_unique_out<K><<<grid_for(nuniq, 256), 256, 0, s>>>(
+                    keyU, cU, flag, pos, nuniq, P.norb, (ulonglong2*)cx.uq_dets, cx.uq_c);
+                NQS_CK_LAUNCH();
+            }
+        }
     }
     NQS_TRY(ksum_f64(p, bs, eterm, nuniq, ext_dev, s));
     return NQS_OK;
@@ -674,9 +919,9 @@ static int pt2_reduce(nqs_problem* p, K* keys, double* vals, K* keys2, double* v
 // one bucket of the pipeline with key type K: emit its pairs, then reduce them
 template <class K>
 static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
-                      double E_var, int64_t B, int64_t b, const int64_t* offs, int64_t n,
-                      const HashS& H, double* cS, double* D_dev, double* ext_dev,
-                      unsigned long long* nuniq_dev, size_t smem, double eps, cudaStream_t s) {
+                      int64_t B, int64_t b, const int64_t* offs, int64_t n, Pt2Ctx& cx,
+                      double* ext_dev, unsigned long long* nuniq_dev, double eps,
+                      cudaStream_t s) {
     const ProblemDev& P = p->d;
     Scratch bs(p, s);
     K *keys, *keys2;
@@ -686,7 +931,7 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
     NQS_TRY(bs.get(&keys2, n));
     NQS_TRY(bs.get(&vals2, n));
     if (eps > 0.0) {
-        NQS_TRY(hb_pt2_pass(p, H, dets, psi, nS, eps, (uint64_t)B, (uint64_t)b, nullptr, offs,
+        NQS_TRY(hb_pt2_pass(p, *cx.H, dets, psi, nS, eps, (uint64_t)B, (uint64_t)b, nullptr, offs,
                             keys, vals, s));
     } else {
         {
@@ -696,8 +941,34 @@ static int pt2_bucket(nqs_problem* p, const uint64_t* dets, const double* psi, i
         }
         NQS_CK_LAUNCH();
     }
-    return pt2_reduce<K>(p, keys, vals, keys2, vals2, n, E_var, H, cS, D_dev, ext_dev, nuniq_dev,
-                         s);
+    return pt2_reduce<K>(p, keys, vals, keys2, vals2, n, cx, ext_dev, nuniq_dev, s);
+}
+
+// The screened emissions of the whole connected space in one traversal, appended into buffers
+// of cap pairs, then reduced as one bucket. *needed receives the number of pairs; when it
+// exceeds cap nothing is reduced (the caller splits into buckets).
+template <class K>
+static int pt2_screened_append(nqs_problem* p, const uint64_t* dets, const double* psi,
+                               int64_t nS, double eps, int64_t cap, Pt2Ctx& cx, double* ext_dev,
+                               unsigned long long* nuniq_dev, int64_t* needed, cudaStream_t s) {
+    Scratch bs(p, s);
+    K* keys;
+    double* vals;
+    unsigned long long* cur;
+    NQS_TRY(bs.get(&keys, cap));
+    NQS_TRY(bs.get(&vals, cap));
+    NQS_TRY(bs.get(&cur, 1));
+    NQS_TRY(hb_pt2_append(p, *cx.H, dets, psi, nS, eps, keys, vals, cap, cur, s));
+    unsigned long long n = 0;
+    NQS_CK(cudaMemcpyAsync(&n, cur, sizeof n, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    *needed = (int64_t)n;
+    if ((int64_t)n > cap) return NQS_OK;
+    K* keys2;
+    double* vals2;
+    NQS_TRY(bs.get(&keys2, n));
+    NQS_TRY(bs.get(&vals2, n));
+    return pt2_reduce<K>(p, keys, vals, keys2, vals2, (int64_t)n, cx, ext_dev, nuniq_dev, s);
 }
 
 // The internal term of bucket b: r_x^2 / (D (E - H_xx)) over the dets of S in bucket b, summed
@@ -723,10 +994,10 @@ static int pt2_internal_bucket(nqs_problem* p, const uint64_t* dets, const doubl
 // the buckets are reduced one after another with one pair of sort buffers of the largest
 // bucket's size. total_emitted receives the number of pairs.
 template <class K>
-static int pt2_resident(nqs_problem* p, Scratch& sc, const uint64_t* dets, const double* psi,
-                        int64_t nS, double E_var, int64_t B, const std::vector<int64_t>& nb, const int64_t* offs_all, const HashS& H,
-                        double* cS, double* dev_scalars, unsigned long long* next_dev, double* eint,
-                        bool with_int, size_t smem, int64_t* total_emitted, cudaStream_t s) {
+static int pt2_resident(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                        int64_t B, const std::vector<int64_t>& nb, const int64_t* offs_all,
+                        Pt2Ctx& cx, double* dev_scalars, unsigned long long* next_dev,
+                        double* eint, bool with_int, int64_t* total_emitted, cudaStream_t s) {
     const ProblemDev& P = p->d;
     std::vector<int64_t> start(B);
     int64_t at = 0, nmax = 1;
@@ -747,7 +1018,6 @@ static int pt2_resident(nqs_problem* p, Scratch& sc, const uint64_t* dets, const
     NQS_CK(cudaMemcpyAsync(start_dev, start.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice,
                            s));
     const size_t smem_all = pt_smem_emit(P) + (size_t)PT_WARPS * B * sizeof(uint32_t);
-    (void)smem;
     if (smem_all > 48 * 1024)
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit_all<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem_all));
@@ -760,23 +1030,32 @@ static int pt2_resident(nqs_problem* p, Scratch& sc, const uint64_t* dets, const
     *total_emitted = 0;
     for (int64_t b = 0; b < B; ++b) {
         *total_emitted += nb[b];
-        NQS_TRY(pt2_reduce<K>(p, keys + start[b], vals + start[b], keys2, vals2, nb[b], E_var, H,
-                              cS, dev_scalars, dev_scalars + 1 + 2 * b, next_dev + b, s));
-        NQS_TRY(pt2_internal_bucket(p, dets, psi, cS, nS, dev_scalars, E_var, B, b, eint,
+        NQS_TRY(pt2_reduce<K>(p, keys + start[b], vals + start[b], keys2, vals2, nb[b], cx,
+                              dev_scalars + 1 + 2 * b, next_dev + b, s));
+        NQS_TRY(pt2_internal_bucket(p, dets, psi, cx.cS, nS, dev_scalars, cx.E_var, B, b, eint,
                                     with_int, s));
     }
     return NQS_OK;
 }
 
+// optional output of nqs_pt2_unique: the external unique set of one bucket
+struct UniqReq {
+    int64_t bucket;
+    uint64_t* dets;
+    double* c;
+    int64_t cap;
+    int64_t n;  // out
+};
+
 static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
                     double E_var, const nqs_csr* hss, const nqs_opts* opts, double* out,
-                    double* bucket_partials, cudaStream_t stream);
+                    double* bucket_partials, cudaStream_t stream, UniqReq* uq);
 
 extern "C" int nqs_pt2(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
                        double E_var, const nqs_opts* opts, double* out, double* bucket_partials,
                        nqs_stream_t stream) {
     return pt2_impl(p, dets, psi, nS, E_var, nullptr, opts, out, bucket_partials,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, nullptr);
 }
 
 extern "C" int nqs_pt2_hss(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
@@ -784,12 +1063,37 @@ extern "C" int nqs_pt2_hss(nqs_problem* p, const uint64_t* dets, const double* p
                            double* bucket_partials, nqs_stream_t stream) {
     if (!hss || hss->n_rows != nS || !hss->row_ptr || !hss->col || !hss->val) return NQS_ERR_ARG;
     return pt2_impl(p, dets, psi, nS, E_var, hss, opts, out, bucket_partials,
-                    (cudaStream_t)stream);
+                    (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int nqs_pt2_unique(nqs_problem* p, const uint64_t* dets, const double* psi,
+                              int64_t nS, int buckets, int bucket, uint64_t* dets_out,
+                              double* c_out, int64_t capacity, int64_t* n_unique,
+                              nqs_stream_t stream) {
+    if (!p || !n_unique || buckets < 1 || bucket < 0 || bucket >= buckets || capacity < 0)
+        return NQS_ERR_ARG;
+    if (capacity > 0 && (!dets_out || !c_out || (((uintptr_t)dets_out) & 15))) return NQS_ERR_ARG;
+    nqs_opts o;
+    nqs_opts_default(&o);
+    o.buckets = buckets;
+    o.validate = 0;
+    UniqReq uq{bucket, dets_out, c_out, capacity, 0};
+    double res[5];
+    const int st = pt2_impl(p, dets, psi, nS, 0.0, nullptr, &o, res, nullptr,
+                            (cudaStream_t)stream, &uq);
+    *n_unique = uq.n;
+    if (st < 0) return st;
+    if (uq.n > capacity) {
+        nqs_record_message("nqs_pt2_unique: capacity smaller than the unique set; *n_unique holds "
+                           "the size needed");
+        return NQS_ERR_ARG;
+    }
+    return NQS_OK;
 }
 
 static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
                     double E_var, const nqs_csr* hss, const nqs_opts* opts, double* out,
-                    double* bucket_partials, cudaStream_t stream) {
+                    double* bucket_partials, cudaStream_t stream, UniqReq* uq) {
     if (!p || !dets || !psi || !out || nS <= 0) return NQS_ERR_ARG;
     if (((uintptr_t)dets) & 15) return NQS_ERR_ARG;
     if (nS >= ((int64_t)1 << 31)) return NQS_ERR_UNSUPPORTED;
@@ -822,57 +1126,54 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
         NQS_CK(cudaFuncSetAttribute(k_pt2_emit<Key128>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sme));
     }
-
-    int64_t* pre_offs = nullptr;  // offsets of a screened single-bucket count, when one ran
-    int64_t pre_total = 0;
-    if (B <= 0) {
-        // automatic: enough buckets that one bucket's pairs (keys and values twice, plus 8 bytes
-        // per pair toward the per-unique arrays) use at most half of the free device memory,
-        // and stay below 2^31
-        const int kbits_ = 2 * P.norb;
-        const double kb = kbits_ <= 32 ? 4.0 : (kbits_ <= 64 ? 8.0 : 16.0);
+    const int kbits = 2 * P.norb;  // 32-bit, 64-bit or two-word keys
+    const double kb = kbits <= 32 ? 4.0 : (kbits <= 64 ? 8.0 : 16.0);
+    // device memory available to this call: free memory plus what the library's pool holds
+    // unused
+    auto avail_bytes = [&](double* av) -> int {
         size_t fr = 0, tot = 0;
         NQS_CK(cudaMemGetInfo(&fr, &tot));
-        // memory the library's pool holds but does not use is available too
         uint64_t reserved = 0, used = 0;
         NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
         NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &used));
-        const double avail = (double)fr + (double)(reserved > used ? reserved - used : 0);
-        double cap = 0.5 * avail / (2.0 * (kb + 8.0) + 8.0);
-        if (cap > 2147483647.0) cap = 2147483647.0;
-        double total = (double)nS * (double)P.nexc;
-        if (screened) {
-            NQS_TRY(sc.get(&pre_offs, nS));
-            int64_t *c1, *t1;
-            NQS_TRY(sc.get(&c1, nS));
-            NQS_TRY(sc.get(&t1, 1));
-            NQS_TRY(hb_pt2_pass(p, H, dets, psi, nS, eps, 1, 0, c1, nullptr, nullptr, nullptr, s));
-            NQS_TRY(scan_exclusive_i64(p, sc, c1, pre_offs, nS, t1, s));
-            NQS_CK(cudaMemcpyAsync(&pre_total, t1, sizeof pre_total, cudaMemcpyDeviceToHost, s));
-            NQS_CK(cudaStreamSynchronize(s));
-            total = (double)pre_total;
-        }
-        B = (int64_t)ceil(total / cap);
+        *av = (double)fr + (double)(reserved > used ? reserved - used : 0);
+        return NQS_OK;
+    };
+
+    if (!screened && B <= 0) {
+        // automatic: enough buckets that one bucket's pairs (keys and values twice, plus 8 bytes
+        // per pair toward the per-unique arrays) use at most half of the free device memory,
+        // and stay below 2^31
+        double av = 0;
+        NQS_TRY(avail_bytes(&av));
+        double capb = 0.5 * av / (2.0 * (kb + 8.0) + 8.0);
+        if (capb > 2147483647.0) capb = 2147483647.0;
+        B = (int64_t)ceil((double)nS * (double)P.nexc / capb);
         if (B < 1) B = 1;
-        if (B > 1) pre_offs = nullptr;  // the counts of one bucket serve only B = 1
     }
+    // per-bucket slots: the bucket count is known here, except for the automatic screened form
+    // (one bucket unless its single traversal overflows; at most 1024 then)
+    const int64_t nslots = B > 1024 ? B : 1024;
     double* dev_scalars;  // [0] = D, then per bucket (ext, int)
-    NQS_TRY(sc.get(&dev_scalars, 1 + 2 * B));
+    NQS_TRY(sc.get(&dev_scalars, 1 + 2 * nslots));
     unsigned long long* next_dev;
-    NQS_TRY(sc.get(&next_dev, B));
-    NQS_CK(cudaMemsetAsync(next_dev, 0, B * sizeof(unsigned long long), s));
+    NQS_TRY(sc.get(&next_dev, nslots));
+    unsigned long long* vmax_bits;
+    NQS_TRY(sc.get(&vmax_bits, 1));
+    NQS_CK(cudaMemsetAsync(next_dev, 0, nslots * sizeof(unsigned long long), s));
+    NQS_CK(cudaMemsetAsync(vmax_bits, 0, sizeof(unsigned long long), s));
     NQS_TRY(kdot2_f64(p, sc, psi, psi, nS, dev_scalars, s));  // dev_scalars[0] = psi.psi
+    k_absmax_bits<<<grid_for(nS, 256, 148 * 4), 256, 0, s>>>(psi, nS, vmax_bits);
+    NQS_CK_LAUNCH();
     double* cS;
     NQS_TRY(sc.get(&cS, nS));
     NQS_CK(cudaMemsetAsync(cS, 0, nS * sizeof(double), s));
     double* eint;
     NQS_TRY(sc.get(&eint, nS));
-    int64_t* cnt = nullptr;
-    int64_t* offs = nullptr;
-    int64_t* total_dev = nullptr;
-    // one counting pass for every bucket when the B x nS count table stays below 2 GiB
-    const bool count_all = !screened && B > 1 && B <= PT_HIST_MAX &&
-                           (double)nS * (double)B * sizeof(int64_t) <= 2147483648.0;
+    Pt2Ctx cx{&H, cS, dev_scalars, vmax_bits,
+              (double)(nS < P.nexc ? nS : P.nexc), E_var, screened, uq != nullptr,
+              uq ? uq->dets : nullptr, uq ? uq->c : nullptr, uq ? uq->cap : 0, 0};
+
     if (screened && opts->internal_pt2 && hss) {
         // the screened emissions leave S out: the internal term takes the off-diagonal part of
         // H_SS psi from the caller's H_SS
@@ -886,7 +1187,83 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
                                                              nS, cS);
         NQS_CK_LAUNCH();
     }
-    if (B > 1 || screened) {
+
+    int64_t total_emitted = 0;
+    bool done = false;
+    if (screened && B <= 0) {
+        // automatic: one traversal appending into buffers sized from a counted sample of S
+        // (every stride-th configuration, x1.5 + 2^16), at most what memory allows (pairs, sort
+        // buffers and per-unique arrays: 3 key widths + 36 bytes per pair, 90% of what is
+        // available). The traversal counts every pair, so one that overflows is repeated with
+        // the exact size when that fits; otherwise the emissions are split into counted buckets.
+        double av = 0;
+        NQS_TRY(avail_bytes(&av));
+        double memcap = 0.9 * av / (3.0 * kb + 36.0);
+        if (memcap > 4294967295.0) memcap = 4294967295.0;
+        const int64_t stride = nS > 4096 ? nS / 4096 : 1;
+        const int64_t ns = (nS + stride - 1) / stride;
+        double est;
+        {
+            Scratch es(p, s);
+            uint64_t* ds;
+            double* ps;
+            int64_t *c1, *o1, *t1;
+            NQS_TRY(es.get(&ds, 2 * ns));
+            NQS_TRY(es.get(&ps, ns));
+            NQS_TRY(es.get(&c1, ns));
+            NQS_TRY(es.get(&o1, ns));
+            NQS_TRY(es.get(&t1, 1));
+            k_gather_stride<<<grid_for(ns, 256), 256, 0, s>>>((const ulonglong2*)dets, psi, ns,
+                                                               stride, (ulonglong2*)ds, ps);
+            NQS_CK_LAUNCH();
+            NQS_TRY(hb_pt2_pass(p, H, ds, ps, ns, eps, 1, 0, c1, nullptr, nullptr, nullptr, s));
+            NQS_TRY(scan_exclusive_i64(p, es, c1, o1, ns, t1, s));
+            int64_t tot = 0;
+            NQS_CK(cudaMemcpyAsync(&tot, t1, sizeof tot, cudaMemcpyDeviceToHost, s));
+            NQS_CK(cudaStreamSynchronize(s));
+            est = (double)tot * ((double)nS / (double)ns);
+        }
+        double capd = fmin(1.5 * est + 65536.0, (double)nS * (double)P.nexc);
+        capd = fmin(capd, memcap);
+        int64_t cap = (int64_t)capd;
+        int64_t needed = 0;
+        for (int attempt = 0; attempt < 2 && !done; ++attempt) {
+            int st = kbits <= 32
+                         ? pt2_screened_append<uint32_t>(p, dets, psi, nS, eps, cap, cx,
+                                                         dev_scalars + 1, next_dev, &needed, s)
+                     : kbits <= 64
+                         ? pt2_screened_append<uint64_t>(p, dets, psi, nS, eps, cap, cx,
+                                                         dev_scalars + 1, next_dev, &needed, s)
+                         : pt2_screened_append<Key128>(p, dets, psi, nS, eps, cap, cx,
+                                                       dev_scalars + 1, next_dev, &needed, s);
+            NQS_TRY(st);
+            if (needed <= cap) {
+                B = 1;
+                total_emitted = needed;
+                NQS_TRY(pt2_internal_bucket(p, dets, psi, cS, nS, dev_scalars, E_var, 1, 0, eint,
+                                            opts->internal_pt2 != 0, s));
+                done = true;
+            } else if ((double)needed <= memcap) {
+                cap = needed;  // the exact size: one more traversal
+            } else {
+                B = (int64_t)ceil((double)needed / memcap);
+                break;
+            }
+        }
+    }
+    if (B > nslots) {
+        nqs_record_message("nqs_pt2: the screened emissions need more than 1024 buckets; raise "
+                           "eps_pt2 or pass opts->buckets");
+        return NQS_ERR_UNSUPPORTED;
+    }
+    if (uq && (uq->bucket >= B)) return NQS_ERR_ARG;
+    int64_t* cnt = nullptr;
+    int64_t* offs = nullptr;
+    int64_t* total_dev = nullptr;
+    // one counting pass for every bucket when the B x nS count table stays below 2 GiB
+    const bool count_all = !done && !screened && B > 1 && B <= PT_HIST_MAX &&
+                           (double)nS * (double)B * sizeof(int64_t) <= 2147483648.0;
+    if (!done && (B > 1 || screened)) {
         NQS_TRY(sc.get(&cnt, count_all ? (size_t)nS * B : (size_t)nS));
         NQS_TRY(sc.get(&offs, nS));
         NQS_TRY(sc.get(&total_dev, 1));
@@ -905,10 +1282,7 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
         NQS_CK_LAUNCH();
     }
     const int64_t cap = opts->chunk > 0 ? opts->chunk : ((int64_t)1 << 32) - 1;
-    const int kbits = 2 * P.norb;  // 32-bit, 64-bit or two-word keys
-    int64_t total_emitted = 0;
-    bool resident = false;
-    if (count_all) {
+    if (count_all && !uq) {
         // every bucket's pairs resident at once when they fit: per-bucket offsets, then one
         // emission pass instead of one decoding pass over all excitations per bucket
         int64_t* offs_all;
@@ -930,38 +1304,35 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
             nmax = fmax(nmax, (double)nb[b]);
             if (nb[b] > cap) fits_sort = false;
         }
-        const double kb = kbits <= 32 ? 4.0 : (kbits <= 64 ? 8.0 : 16.0);
         // pairs of all buckets + one pair of sort buffers + the largest bucket's unique arrays
         const double need = tot * (kb + 8.0) + nmax * (kb + 8.0) + nmax * (kb + 16.0);
-        size_t fr = 0, totm = 0;
-        NQS_CK(cudaMemGetInfo(&fr, &totm));
-        uint64_t reserved = 0, used = 0;
-        NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
-        NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &used));
-        const double avail = (double)fr + (double)(reserved > used ? reserved - used : 0);
-        if (fits_sort && need <= 0.9 * avail) {
-            resident = true;
+        double av = 0;
+        NQS_TRY(avail_bytes(&av));
+        if (fits_sort && need <= 0.9 * av) {
+            done = true;
             const bool wi = opts->internal_pt2 != 0;
             int st = kbits <= 32
-                         ? pt2_resident<uint32_t>(p, sc, dets, psi, nS, E_var, B, nb, offs_all,
-                                                  H, cS, dev_scalars, next_dev, eint, wi, smem,
+                         ? pt2_resident<uint32_t>(p, dets, psi, nS, B, nb, offs_all, cx,
+                                                  dev_scalars, next_dev, eint, wi,
                                                   &total_emitted, s)
                      : kbits <= 64
-                         ? pt2_resident<uint64_t>(p, sc, dets, psi, nS, E_var, B, nb,
-                                                  offs_all, H, cS, dev_scalars, next_dev, eint, wi,
-                                                  smem, &total_emitted, s)
-                         : pt2_resident<Key128>(p, sc, dets, psi, nS, E_var, B, nb, offs_all,
-                                                H, cS, dev_scalars, next_dev, eint, wi, smem,
-                                                &total_emitted, s);
+                         ? pt2_resident<uint64_t>(p, dets, psi, nS, B, nb, offs_all, cx,
+                                                  dev_scalars, next_dev, eint, wi,
+                                                  &total_emitted, s)
+                         : pt2_resident<Key128>(p, dets, psi, nS, B, nb, offs_all, cx,
+                                                dev_scalars, next_dev, eint, wi, &total_emitted,
+                                                s);
             NQS_TRY(st);
         }
     }
-    for (int64_t b = 0; b < B && !resident; ++b) {
+    for (int64_t b = 0; b < B && !done; ++b) {
+        if (uq && b != uq->bucket) {
+            NQS_CK(cudaMemsetAsync(dev_scalars + 1 + 2 * b, 0, 2 * sizeof(double), s));
+            continue;
+        }
         int64_t n;
         if (B == 1 && !screened) {
             n = nS * P.nexc;
-        } else if (pre_offs) {
-            n = pre_total;
         } else {
             Scratch cs(p, s);
             if (screened) {
@@ -982,21 +1353,20 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
         }
         if (n > cap) return NQS_ERR_OOM;  // more buckets needed
         total_emitted += n;
-        const int64_t* o = (B == 1 && !screened) ? nullptr : (pre_offs ? pre_offs : offs);
+        const int64_t* o = (B == 1 && !screened) ? nullptr : offs;
         int st = kbits <= 32
-                     ? pt2_bucket<uint32_t>(p, dets, psi, nS, E_var, B, b, o, n, H, cS,
-                                            dev_scalars, dev_scalars + 1 + 2 * b, next_dev + b,
-                                            smem, eps, s)
+                     ? pt2_bucket<uint32_t>(p, dets, psi, nS, B, b, o, n, cx,
+                                            dev_scalars + 1 + 2 * b, next_dev + b, eps, s)
                  : kbits <= 64
-                     ? pt2_bucket<uint64_t>(p, dets, psi, nS, E_var, B, b, o, n, H, cS,
-                                            dev_scalars, dev_scalars + 1 + 2 * b, next_dev + b,
-                                            smem, eps, s)
-                     : pt2_bucket<Key128>(p, dets, psi, nS, E_var, B, b, o, n, H, cS, dev_scalars,
-                                          dev_scalars + 1 + 2 * b, next_dev + b, smem, eps, s);
+                     ? pt2_bucket<uint64_t>(p, dets, psi, nS, B, b, o, n, cx,
+                                            dev_scalars + 1 + 2 * b, next_dev + b, eps, s)
+                     : pt2_bucket<Key128>(p, dets, psi, nS, B, b, o, n, cx,
+                                          dev_scalars + 1 + 2 * b, next_dev + b, eps, s);
         NQS_TRY(st);
         NQS_TRY(pt2_internal_bucket(p, dets, psi, cS, nS, dev_scalars, E_var, B, b, eint,
                                     opts->internal_pt2 != 0, s));
     }
+    if (uq) uq->n = cx.uq_n;
     std::vector<double> hs(1 + 2 * B);
     std::vector<unsigned long long> hn(B);
     NQS_CK(cudaMemcpyAsync(hs.data(), dev_scalars, hs.size() * sizeof(double),

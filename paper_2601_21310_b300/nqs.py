@@ -17,6 +17,9 @@ LIB_PATH = os.path.join(_HERE, "libnqs.so")
 NQS_FP64 = 0
 NQS_MIXED = 1
 NQS_WARN_SINGULAR = 1
+NQS_ERR_ARG = -1
+NQS_ERR_OOM = -5
+NQS_ERR_TIMEOUT = -7
 
 _lib = None
 
@@ -75,11 +78,17 @@ EXPORTS = {
                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_pt2_hss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_pt2_unique": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
+                                 C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_void_p]),
     "nqs_hb_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_detset_free": (C.c_int, [C.c_void_p]),
     "nqs_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int64,
                              C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "nqs_wait_probe": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "nqs_set_scratch_limit": (C.c_int, [C.c_void_p, C.c_int64]),
+    "nqs_pool_usage": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_profile_enable": (C.c_int, [C.c_int]),
     "nqs_profile_reset": (C.c_int, []),
     "nqs_profile_read": (C.c_int, [C.c_char_p, C.c_void_p, C.c_void_p]),
@@ -453,6 +462,27 @@ def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, bucke
                 buckets=int(out[4]), partials=parts.reshape(-1, 2) if o.buckets > 0 else None)
 
 
+def pt2_unique(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, buckets: int = 1,
+               bucket: int = 0, stream=None):
+    """The deduplicated external set of nqs_pt2 for one hash bucket: (configurations uint64
+    [n, 2] ascending by key, c(x') float64 [n]) on the device. Sizes the output with a first
+    call that reports the set's size."""
+    dets = _dets(dets)
+    psi = psi.contiguous()
+    n = C.c_int64(0)
+    st = lib().nqs_pt2_unique(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0], int(buckets),
+                              int(bucket), None, None, 0, C.byref(n), _stream(stream))
+    if st != NQS_ERR_ARG or n.value == 0:
+        _check(st, "nqs_pt2_unique")
+    cap = max(n.value, 1)
+    out = torch.empty((cap, 2), dtype=torch.int64, device=dets.device)
+    c = torch.empty(cap, dtype=torch.float64, device=dets.device)
+    _check(lib().nqs_pt2_unique(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0],
+                                int(buckets), int(bucket), _ptr(out), _ptr(c), cap, C.byref(n),
+                                _stream(stream)), "nqs_pt2_unique")
+    return out[:n.value].view(torch.uint64), c[:n.value]
+
+
 def hb_select(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, eps: float,
               o: Opts | None = None, stream=None):
     """Heat-bath screened perturbative set (Eq. hb_screen). Returns dict(dets uint64 [n, 2]
@@ -566,6 +596,23 @@ def autotune_entries():
     arrs = [(C.c_int * max(n, 1))() for _ in range(4)]
     lib().nqs_autotune_entries(*arrs, n)
     return [(arrs[0][i], arrs[1][i], arrs[2][i], arrs[3][i]) for i in range(n)]
+
+
+def wait_probe(problem: Problem, limit_cycles: int, stream=None) -> int:
+    """Status of a bounded device wait on a barrier nothing completes (NQS_ERR_TIMEOUT when the
+    timeout path works)."""
+    return lib().nqs_wait_probe(problem.handle, int(limit_cycles), _stream(stream))
+
+
+def set_scratch_limit(problem: Problem, nbytes: int):
+    _check(lib().nqs_set_scratch_limit(problem.handle, int(nbytes)), "nqs_set_scratch_limit")
+
+
+def pool_usage(problem: Problem):
+    """(bytes in use, bytes reserved) of the problem's scratch pool."""
+    u, r = C.c_int64(0), C.c_int64(0)
+    _check(lib().nqs_pool_usage(problem.handle, C.byref(u), C.byref(r)), "nqs_pool_usage")
+    return u.value, r.value
 
 
 def profile_enable(on: bool = True):

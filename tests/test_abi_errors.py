@@ -46,6 +46,7 @@ def test_null_handles_are_rejected(L):
     assert L.nqs_gemm_bf16(None, 8, p, 8, 8, 8, 8, p, 8, None, None) == NQS_ERR_ARG
     assert L.nqs_batch_create(0, p, p, p, p, p, p, p, 1, p) == NQS_ERR_ARG
     assert L.nqs_csr_free(None) == NQS_ERR_ARG
+    assert L.nqs_pt2_unique(None, p, p, 1, 1, 0, None, None, 0, p, None) == NQS_ERR_ARG
 
 
 def test_gemm_rejects_empty_shapes(L):

@@ -1,10 +1,12 @@
 """Batched evaluation of independent problems of uneven shape (concurrent streams, then one
-CUDA graph): every problem's E_S and gradient equal its own nqs_energy_grad result."""
+CUDA graph): every problem's E_S and gradient equal its own nqs_energy_grad result, and members
+of the batch match the oracle's quantisation-matched evaluation."""
 import numpy as np
 import pytest
 import torch
 
 from gpu_common import need_gpu, nqs, to_dev
+from oracle import oracle as O
 from paper_2601_21310_b300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -51,3 +53,32 @@ def test_batch_graph_matches_individual_calls():
         assert torch.equal(it[4], o_ref)
         assert torch.equal(it[5], g_ref)
     assert len(N.autotune_entries()) > 0
+
+
+def test_batch_members_match_quantised_oracle():
+    """Three members of a graph-launched batch (the smallest |S| of the first eight problems),
+    each against the oracle's quantisation-matched E_S and gradient of its own problem: E_S
+    within 1e-6 Ha, gradient within 1e-2 relative L2."""
+    need_gpu()
+    N = nqs()
+    wls = synth.batched_workloads(count=64)[:8]
+    items = [_make(N, wl) for wl in wls]
+    stream = torch.cuda.Stream()
+    b = N.Batch(items, nstreams=4)
+    with torch.cuda.stream(stream):
+        b.run(stream)
+        b.capture(stream)
+        for it in items:
+            it[4].zero_()
+            it[5].zero_()
+        b.launch(stream)
+        stream.synchronize()
+    order = np.argsort([wl.nS for wl in wls])[:3]
+    for i in order:
+        p = synth.make_problem(wls[i])
+        ref = O.energy_grad(O.Net(p.net, quant=True), p.S, O.hss(p.wl.norb, p.h, p.eri, p.S))
+        E = items[i][4][0].item()
+        g = items[i][5].cpu().numpy().astype(np.float64)
+        assert abs(E - ref["E"]) < 1e-6, (wls[i].name, E - ref["E"])
+        rel = np.linalg.norm(g - ref["grad"]) / np.linalg.norm(ref["grad"])
+        assert rel < 1e-2, (wls[i].name, rel)

@@ -52,6 +52,32 @@ def test_full_size_mixed_amplitudes_sampled(cr2):
     assert np.median(d) < 1e-5 and np.quantile(d, 0.99) < 5e-3
 
 
+def test_full_size_mixed_energy_grad_vs_quantised_oracle(cr2):
+    """Mixed form at the full cr2_24e30o size (|S| = 131072): E_S within 1e-6 Ha and the
+    gradient within 1e-2 relative L2 of the oracle's quantisation-matched evaluation (weights and
+    activations rounded to BF16, FP64 arithmetic). The oracle evaluates the network, the
+    determinants, E_S and the adjoint itself; it takes H_SS from the library's CSR copied to the
+    host (its own H_SS would need 8.8e9 host lookups), whose rows equal the oracle's Slater-Condon
+    rows bit for bit on the three row blocks checked here."""
+    N, p, P, dets = cr2
+    csr = N.connections(P, dets)
+    rp, col, val = csr.host()
+    for r0 in (0, 70001, len(p.S) - 32):
+        orp, ocol, oval = O.hss_rows(30, p.h, p.eri, p.S, r0, r0 + 32)
+        a, b = rp[r0], rp[r0 + 32]
+        assert np.array_equal(rp[r0:r0 + 33] - a, orp)
+        assert np.array_equal(col[a:b], ocol) and np.array_equal(val[a:b], oval)
+    net = N.Net(P, N.net_tensors(p.net, N.NQS_MIXED), N.NQS_MIXED)
+    out, grad, _ = N.energy_grad(P, net, csr, dets)
+    E = out[0].item()
+    g = grad.cpu().numpy().astype(np.float64)
+    csr.free()
+    refq = O.energy_grad(O.Net(p.net, quant=True), p.S, O.CSR(rp, col, val, 0))
+    assert abs(E - refq["E"]) < 1e-6, E - refq["E"]
+    rel = np.linalg.norm(g - refq["grad"]) / np.linalg.norm(refq["grad"])
+    assert rel < 1e-2, rel
+
+
 def test_full_size_pt2_independent_of_bucketing(cr2):
     """PT2 over the 8.8e9-connection space: the sums and the unique count do not depend on how
     the connected space is split into hash buckets."""

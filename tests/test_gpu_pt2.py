@@ -1,6 +1,7 @@
 """GPU parity of the Epstein-Nesbet PT2 pipeline (emission, radix sort, dedup, segmented
-reduction) against the oracle, through the C ABI: unique counts bit-exact, energies within
-1e-8 Ha (FP64)."""
+reduction) against the oracle, through the C ABI: the unique set bit-exact key by key, c(x')
+element by element, energies within 1e-8 Ha (FP64); the mixed form's external term within
+1e-6 Ha of the quantisation-matched oracle."""
 import numpy as np
 import pytest
 import torch
@@ -229,3 +230,84 @@ def test_pt2_per_bucket_passes_match_single_pass():
         assert r["n_emitted"] == one["n_emitted"]
         assert abs(r["ext"] - one["ext"]) < 1e-12 and abs(r["int"] - one["int"]) < 1e-12
     assert abs(many["partials"][:, 0].sum() - many["ext"]) < 1e-12
+
+
+def _unique_tol(c_ref):
+    """The oracle adds a run's terms one by one in FP64 in emission order, the library in FP64
+    in the same order but grouped by lanes of eight elements (each sum has error at most
+    k 2^-53 sum|terms|, k the run length); 1e-12 of the largest |c| covers k <= 5792 terms of
+    at most that size with margin."""
+    return 1e-12 * max(1.0, float(np.abs(c_ref).max(initial=0.0)))
+
+
+@pytest.mark.parametrize("name,B,b", [("tiny_n10", 1, 0), ("tiny_n10", 3, 1),
+                                      ("small_n16", 8, 3)])
+def test_pt2_unique_set_matches_oracle(name, B, b):
+    """The deduplicated external set of Eq. (pt2_correction) key by key: every x' of C minus S
+    (of one hash bucket) in ascending order equals the oracle's bit for bit, and c(x') element
+    by element."""
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem(name)
+    P = problem_for(N, p)
+    if name == "tiny_n10":
+        psi, E = _psi_E(p)
+    else:
+        psi = np.random.default_rng(9).normal(size=len(p.S))
+        E = -20.0
+    keys, c = N.pt2_unique(P, to_dev(p.S), torch.from_numpy(psi).cuda(), B, b)
+    rk, rc, info = O.pt2_unique(p.wl.norb, p.h, p.eri, p.S, psi, E, B, b if B > 1 else -1)
+    keys = keys.cpu().numpy()
+    assert keys.shape == rk.shape and len(rk) > 0
+    assert np.array_equal(keys, rk)
+    c = c.cpu().numpy()
+    assert np.abs(c - rc).max() <= _unique_tol(rc), np.abs(c - rc).max()
+    got = N.pt2(P, to_dev(p.S), torch.from_numpy(psi).cuda(), E, buckets=B)
+    assert abs(got["partials"][b, 0] - info["ext"]) <= 1e-11 * max(1.0, abs(info["ext"]))
+
+
+def test_pt2_unique_reports_size_and_rejects_bad_bucket():
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("tiny_n10")
+    P = problem_for(N, p)
+    psi, _ = _psi_E(p)
+    d, ps = to_dev(p.S), torch.from_numpy(psi).cuda()
+    import ctypes as C
+    n = C.c_int64(0)
+    L = N.lib()
+    st = L.nqs_pt2_unique(P.handle, d.data_ptr(), ps.data_ptr(), len(p.S), 1, 0, None, None, 0,
+                          C.byref(n), None)
+    assert st == N.NQS_ERR_ARG and n.value > 0
+    assert L.nqs_pt2_unique(P.handle, d.data_ptr(), ps.data_ptr(), len(p.S), 2, 2, None, None, 0,
+                            C.byref(n), None) == N.NQS_ERR_ARG
+
+
+def test_pt2_mixed_form_vs_quantised_oracle():
+    """The mixed-precision form end to end at small_n16 (BF16 network on the tensor cores, FP32
+    LU, FP64 Hamiltonian side): GPU amplitudes -> E_S -> nqs_pt2, against the oracle's
+    quantisation-matched pipeline (BF16-rounded weights and activations, FP64 arithmetic).
+    E_S and the external term of Eq. (pt2_correction) are gated at 1e-6 Ha. The internal term
+    divides by E - H_xx over S, which for this random network comes within 1.2e-3 Ha of zero:
+    there a 1e-6 change of psi moves the term by ~1e-2 Ha, so no amplitude-level agreement can
+    gate it at 1e-6 Ha. It is compared instead with the oracle evaluated on the GPU's own psi
+    and E_S (one hash bucket of eight), to 1e-9 relative."""
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem("small_n16")
+    P = problem_for(N, p)
+    dets = to_dev(p.S)
+    net = N.Net(P, N.net_tensors(p.net, N.NQS_MIXED), N.NQS_MIXED)
+    csr = N.connections(P, dets)
+    out, _, psi = N.energy_grad(P, net, csr, dets, with_grad=False)
+    E = out[0].item()
+    got = N.pt2(P, dets, psi, E, buckets=8)
+    ref_csr = O.hss(16, p.h, p.eri, p.S)
+    refq = O.energy_grad(O.Net(p.net, quant=True), p.S, ref_csr, with_grad=False)
+    ref = O.pt2(16, p.h, p.eri, p.S, refq["psi"], refq["E"])
+    assert abs(E - refq["E"]) < 1e-6, E - refq["E"]
+    assert abs(got["ext"] - ref["ext"]) < 1e-6, got["ext"] - ref["ext"]
+    psi_g = psi.cpu().numpy()
+    r0 = O.pt2(16, p.h, p.eri, p.S, psi_g, E, 8, 0)
+    assert abs(got["partials"][0, 1] - r0["int"]) <= 1e-9 * abs(r0["int"])
+    assert abs(got["partials"][0, 0] - r0["ext"]) <= 1e-10 * abs(r0["ext"])
