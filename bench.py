@@ -1,15 +1,17 @@
 #!/usr/bin/env python
 """Benchmark of the deterministic-NQS hot path on one B300 (or N independent replicas).
 
-One step = one pass of the whole path over the synthetic 16-orbital workload (8a+8b,
-|S| = 16384, backflow MLP 32-256-256-256 in the mixed BF16 form):
+One step = one pass of the whole path over the synthetic workload of the shape of Cr2
+CAS(48e,42o) (42 orbitals, 24a+24b, |S| = 2^20, backflow MLP 84-1024-1024-2016 in the mixed
+BF16 form; --workload small_n16 / cr2_24e30o / tiny_n10 for the smaller shapes):
   nqs_connections  (enumerate all singles/doubles of S, look up in S, build H_SS CSR)
   nqs_energy_grad  (amplitudes, E_S, adjoint gradient)
-  nqs_pt2          (emit C, radix sort, dedup, segmented reduce, EN-PT2 sums)
+  nqs_pt2          (emit C, radix sort, dedup, segmented reduce, EN-PT2 sums; above 30
+                    orbitals over the screened set of Sec. 3.3 at eps = 1e-6, one traversal)
 Metric: connections resolved per second over the step (H_SS lookups + PT2 emissions), with
 E_S+grad evaluations per second reported beside it.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nqs|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nqs|reference] [--workload W]
 """
 from __future__ import annotations
 
@@ -32,7 +34,7 @@ from paper_2601_21310_b300 import synth  # noqa: E402
 
 METRIC = "connections/s and E_S+grad evals/s at 1 B300; BF16 form vs FP64 at 1e-6 Ha"
 UNIT = "connections/s"
-WORKLOAD = "small_n16"
+WORKLOAD = "cr2_48e42o"
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2
 
 
@@ -59,7 +61,6 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip the plain-FP64 comparison run (e.g. for a launch list of the step)")
-    ap.add_argument("--cpu-sample", type=int, default=4096, help="dets in the CPU-baseline sample")
     args = ap.parse_args()
     if args.eps_pt2 is None:
         args.eps_pt2 = default_eps_pt2(args.workload)
@@ -188,20 +189,18 @@ def algorithmic_work(name, wl, nS, nexc, nnz, n_emit, n_unique, net_flops, bucke
         return "hbm", kb * n_emit, "B"
     if name == "seg_reduce":   # read keys + values, write (sum, key) per run, read its run index
         return "hbm", (kb + 8.0) * n_emit + (kb + 12.0) * n_unique, "B"
-    if name == "conn_fill":    # write col+val per nonzero, read S
-        return "hbm", 12.0 * nnz + 16.0 * nS, "B"
     if name == "spmv":
         return "hbm", 12.0 * nnz + 8.0 * 3 * nS, "B"
     if name == "gemm":
         return "tensor", net_flops, "FLOP"
-    # enumeration, probing, the screened traversal, LU and the H_x'x' loop are issue-bound: no
-    # byte or FLOP roofline
+    # enumeration, probing, the CSR fill (decode + probe per hit), the screened traversal, LU and
+    # the H_x'x' loop are issue-bound: no byte or FLOP roofline
     return "alu", 0.0, None
 
 
-def kernel_traffic(name, wl):
-    """dram read+write bytes per launch from the committed ncu summary, if the kernel source is
-    unchanged since the capture (else None)."""
+def kernel_traffic(name, wl, key="dram_bytes_per_launch"):
+    """A figure of the committed ncu summary of one kernel (dram read+write bytes per launch by
+    default), if the kernel source is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", f"{name}_{wl}.md")
     if not os.path.exists(path):
         return None
@@ -213,7 +212,7 @@ def kernel_traffic(name, wl):
                 vals[k.strip()] = v.strip().split()[0]
     src = vals.get("source_file")
     sha = vals.get("source_sha256")
-    tr = vals.get("dram_bytes_per_launch")
+    tr = vals.get(key)
     if not (src and sha and tr):
         return None
     with open(os.path.join(ROOT, src), "rb") as f:
@@ -270,13 +269,7 @@ def run_nqs(args, ws, rank, local):
         N.energy_grad(P, net, csr, dets, o=o_eg, out=out, grad=grad, psi=psi)
         e2 = mark(record)
         E = out[0].item()
-        if args.no_pt2:
-            r = dict(n_emitted=0, n_unique=0, ext=float("nan"), int=float("nan"))
-        elif args.eps_pt2 > 0:
-            # the screening threshold refers to psi normalised over S
-            r = N.pt2(P, dets, psi / torch.linalg.norm(psi), E, o=o_pt, hss=csr)
-        else:
-            r = N.pt2(P, dets, psi, E, o=o_pt, hss=csr)
+        r = pt2_step(args, N, P, dets, psi, E, o_pt, csr)
         e3 = mark(record)
         info = dict(n_conn=csr.n_enumerated + r["n_emitted"], n_hss=csr.n_enumerated,
                     buckets=r.get("buckets", 0),
@@ -327,7 +320,8 @@ def run_nqs(args, ws, rank, local):
     N.profile_reset()
     N.profile_enable(True)
     prof_times = []
-    for _ in range(args.steps):
+    prof_steps = min(args.steps, 3)
+    for _ in range(prof_steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -349,10 +343,10 @@ def run_nqs(args, ws, rank, local):
     nexc = synth_nexc(wl)
 
     def work(k):
-        per_launch_flops = total_gemm_flops / max(1, prof[k][1] / args.steps)
+        per_launch_flops = total_gemm_flops / max(1, prof[k][1] / prof_steps)
         return algorithmic_work(k, wl, nS, nexc, info["nnz"], info["n_emit"], info["n_unique"],
                                 per_launch_flops, max(1, info["buckets"]),
-                                max(1, prof[k][1] / args.steps), args.eps_pt2 > 0)
+                                max(1, prof[k][1] / prof_steps), args.eps_pt2 > 0)
 
     # the roofline is reported for the largest kernel with a byte or FLOP bound; the largest
     # kernel overall is named beside it when it is an issue-bound one
@@ -375,10 +369,14 @@ def run_nqs(args, ws, rank, local):
                 "unit": r_unit, "frac": round(achieved / peak, 4), "traffic": traffic,
                 "algorithmic_per_launch": amount, "peak_source": peak_kind}
     if top != dom:
-        roofline["largest_kernel"] = {"kernel": top, "bound": "alu",
-                                      "share_of_step": round(shares[top] / sum(shares.values()), 4)}
-    kernels = {k: {"ms_per_step": round(v[0] / args.steps, 4), "launches": v[1],
-                   "share_of_step": round(v[0] / args.steps / ms_step_prof, 4)}
+        # an issue-bound kernel: its roofline is the issue rate (one warp instruction per clock
+        # per scheduler); the fraction of issue slots it used comes from its ncu summary
+        roofline["largest_kernel"] = {
+            "kernel": top, "bound": "alu",
+            "share_of_step": round(shares[top] / sum(shares.values()), 4),
+            "issue_slot_util": kernel_traffic(top, wl.name, "issue_slots_busy_frac")}
+    kernels = {k: {"ms_per_step": round(v[0] / prof_steps, 4), "launches": v[1],
+                   "share_of_step": round(v[0] / prof_steps / ms_step_prof, 4)}
                for k, v in prof.items() if v[1] > 0}
 
     result = {
@@ -418,6 +416,16 @@ def run_nqs(args, ws, rank, local):
     return result, p
 
 
+def pt2_step(args, N, P, dets, psi, E, o_pt, csr):
+    """The PT2 part of a step: over all of C minus S, or (eps_pt2 > 0) over the screened set,
+    whose threshold refers to psi normalised over S."""
+    if args.no_pt2:
+        return dict(n_emitted=0, n_unique=0, ext=float("nan"), int=float("nan"))
+    if args.eps_pt2 > 0:
+        return N.pt2(P, dets, psi / torch.linalg.norm(psi), E, o=o_pt, hss=csr)
+    return N.pt2(P, dets, psi, E, o=o_pt, hss=csr)
+
+
 def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, info_mixed,
                   stream):
     """The same evaluation in the plain FP64 form (FP64 parameters, FP64 GEMMs and LU): its
@@ -431,10 +439,14 @@ def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, 
     out64 = torch.empty(4, dtype=torch.float64, device=dev)
     g64 = torch.empty(net64.num_params(), dtype=torch.float64, device=dev)
     psi64 = torch.empty(len(p.S), dtype=torch.float64, device=dev)
-    for _ in range(max(1, args.warmup)):
-        N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
+    t0 = time.perf_counter()
+    N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    # about 30 s at most for the FP64 form (one evaluation takes ~20 s at 42 orbitals)
+    reps = max(1, min(args.steps, int(30.0 / max(first_s, 1e-3))))
     times = []
-    for _ in range(args.steps):
+    for _ in range(reps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -444,7 +456,6 @@ def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, 
         times.append(a.elapsed_time(b))
     ms = sum(times) / len(times)
     # mixed-form results of the timed steps vs the FP64 form
-    N.energy_grad(P, net64, csr, dets, o=o64, out=out64, grad=g64, psi=psi64)
     E64 = out64[0].item()
     r64 = (dict(ext=float("nan"), int=float("nan")) if args.no_pt2 else
            N.pt2(P, dets, psi64 / torch.linalg.norm(psi64), E64, hss=csr,
@@ -454,7 +465,7 @@ def run_fp64_form(args, N, P, p, dets, dtype, out_mixed, grad_mixed, psi_mixed, 
     csr.free()
     gm = grad_mixed.double()
     grel = (torch.linalg.norm(gm - g64) / torch.linalg.norm(g64)).item()
-    return {"energy_grad_ms": ms, "evals_per_s": 1e3 / ms, "E_S": E64,
+    return {"energy_grad_ms": ms, "evals_per_s": 1e3 / ms, "timed_evals": reps, "E_S": E64,
             "E_S_mixed_minus_fp64": info_mixed["E"] - E64,
             "grad_rel_l2_mixed_vs_fp64": grel,
             "dE_pt2_ext": r64["ext"], "dE_pt2_ext_mixed_minus_fp64": info_mixed["ext"] - r64["ext"],
@@ -484,7 +495,7 @@ def run_outer_loop(args, N, P, net, dets, psi, dtype, stream, eps_hb=1e-6):
             ts.append(a.elapsed_time(b))
         return sorted(ts)[len(ts) // 2], r
 
-    reps = max(3, min(args.steps, 10))
+    reps = 3 if nS >= (1 << 20) else max(3, min(args.steps, 10))
     hb_ms, hb = timed(lambda: N.hb_select(P, dets, psi_n, eps_hb, o=o), reps)
     T = torch.cat([dets.view(torch.int64), hb["dets"].view(torch.int64)]).view(torch.uint64)
     amp_ms, (laT, _, _) = timed(lambda: N.amplitudes(P, net, T, o=o), reps)
@@ -564,14 +575,16 @@ def synth_nexc(wl):
 def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_pt, out, grad,
             psi, stream, ws):
     """Same metric through the public API with host buffers: every step copies S and the
-    parameters host->device and reads E, the gradient and the PT2 result back."""
+    parameters host->device and reads E, the gradient and the PT2 result back (up to 5 timed
+    steps after up to 2 warm-up steps)."""
     grad_host = torch.empty(grad.shape, dtype=grad.dtype).pin_memory()
     out_host = torch.empty(4, dtype=torch.float64).pin_memory()
     h2d = S_host.numel() * 8 + sum(t.numel() * t.element_size() for t in params_host)
     d2h = 4 * 8 + grad.numel() * grad.element_size() + 4 * 8 + 2 * 8 * o_pt.buckets
     times, n_conn = [], 0
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dets.device)
-    for it in range(args.warmup + args.steps):
+    warm, steps = min(args.warmup, 2), min(args.steps, 5)
+    for it in range(warm + steps):
         flush.zero_()  # same L2 hygiene as the device-timed steps (outside the events)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -584,49 +597,74 @@ def run_e2e(args, N, P, net, params, params_host, S_host, dets, o_conn, o_eg, o_
         out_host.copy_(out, non_blocking=True)
         grad_host.copy_(grad, non_blocking=True)
         stream.synchronize()
-        r = (dict(n_emitted=0) if args.no_pt2 else
-             N.pt2(P, dets, psi, float(out_host[0]), o=o_pt, hss=csr))
+        r = pt2_step(args, N, P, dets, psi, float(out_host[0]), o_pt, csr)
         n = csr.n_enumerated + r["n_emitted"]
         csr.free_async()
         b.record(stream)
         b.synchronize()
-        if it >= args.warmup:
+        if it >= warm:
             times.append(a.elapsed_time(b))
             n_conn += n
     total = reduce_max_over_ranks(sum(times), dets.device)
     return {"value": whole_job_rate(n_conn, total, ws), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": total / len(times)}
+            "d2h_bytes_per_step": d2h, "ms_per_step": total / len(times), "steps": steps}
 
 
 # ------------------------------------------------------------------------------------------
 # CPU oracle (the reported baseline, and the reference arm)
 # ------------------------------------------------------------------------------------------
-def oracle_step(O, p, k, quant, with_pt2=True):
-    S = p.S[:k]
+def cpu_slices(nS: int, k: int):
+    """Row blocks [0, k), [nS/2, nS/2 + k) and [nS - k, nS) of S: the bounded sample of the CPU
+    oracle (the whole of S when 3k >= nS)."""
+    if 3 * k >= nS:
+        return [(0, nS)]
+    m = nS // 2
+    return [(0, k), (m, m + k), (nS - k, nS)]
+
+
+def oracle_step(O, p, k, quant, with_pt2=True, eps=0.0, pt2_buckets=(0, 1), nb=64):
+    """The oracle on the bounded sample of one step: H_SS rows of the three row blocks (lookups
+    into all of S), E_S + gradient over the sample's own subspace, and PT2 over the sample's
+    connected space for hash buckets {0, 1} of 64 (screened with eps on the sample's normalised
+    amplitudes when eps > 0, like the GPU step). Returns the connections counted like the GPU
+    step's (H_SS pairs resolved + PT2 pairs emitted) and the sample size."""
     wl = p.wl
-    csr = O.hss(wl.norb, p.h, p.eri, S)
-    r = O.energy_grad(O.Net(p.net, quant=quant), S, csr)
-    n = csr.n_enumerated
+    nexc = O.n_excitations(wl.norb, wl.nalpha, wl.nbeta)
+    rows = cpu_slices(len(p.S), k)
+    n = 0
+    for a, b in rows:
+        O.hss_rows(wl.norb, p.h, p.eri, p.S, a, b)
+        n += (b - a) * nexc
+    sample = np.concatenate([p.S[a:b] for a, b in rows])
+    csr = O.hss(wl.norb, p.h, p.eri, sample)
+    r = O.energy_grad(O.Net(p.net, quant=quant), sample, csr)
     if with_pt2:
-        O.pt2(wl.norb, p.h, p.eri, S, r["psi"], r["E"])
-        n += len(S) * O.n_excitations(wl.norb, wl.nalpha, wl.nbeta)
-    return n
+        psi = r["psi"] / np.linalg.norm(r["psi"]) if eps > 0 else r["psi"]
+        for bk in pt2_buckets:
+            n += O.pt2(wl.norb, p.h, p.eri, sample, psi, r["E"], nb, bk, eps=eps)["n_emitted"]
+    return n, len(sample)
 
 
-def cpu_sample_size(args, p) -> int:
-    """Dets in the CPU-baseline sample: about 5e7 excitations (10-30 s of oracle work)."""
-    return int(max(64, min(args.cpu_sample, len(p.S), 5e7 // synth_nexc(p.wl))))
+def cpu_rows_per_block(p, budget_connections: float) -> int:
+    """Rows per block so that one sample resolves about budget_connections H_SS pairs."""
+    nexc = synth_nexc(p.wl)
+    return int(max(1, min(4096, budget_connections // (3 * nexc))))
 
 
-def cpu_baseline(p, k, with_pt2=True):
+def cpu_baseline(p, eps, with_pt2=True):
+    """The oracle as it stands on ~10-30 s of the step's work (the slices of oracle_step), with
+    the full-step CPU time extrapolated from it by the number of configurations."""
     from oracle import oracle as O
     O.lib()
+    k = cpu_rows_per_block(p, 3e7)
     t = time.perf_counter()
-    n = oracle_step(O, p, k, p.wl.mixed, with_pt2)
+    n, ns = oracle_step(O, p, k, p.wl.mixed, with_pt2, eps)
     dt = time.perf_counter() - t
-    what = "H_SS rows, E_S + gradient" + (", PT2 over their connected space" if with_pt2 else "")
+    what = "H_SS rows, E_S + gradient" + (", PT2 buckets {0, 1} of 64" if with_pt2 else "")
     return {"value": n / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"first {k} of {len(p.S)} dets of S: {what} ({n} connections, {dt:.1f} s)"}
+            "sample": f"row blocks {cpu_slices(len(p.S), k)} of {len(p.S)} dets of S "
+                      f"({ns} dets): {what} ({n} connections, {dt:.1f} s)",
+            "extrapolated_full_step_s": dt * len(p.S) / ns}
 
 
 def run_reference(args, ws, rank):
@@ -636,22 +674,25 @@ def run_reference(args, ws, rank):
     O.lib()
     wl = synth.WORKLOADS[args.workload]
     p = synth.make_problem(wl)
-    k = min(2048, len(p.S))
+    eps = args.eps_pt2
+    # each step a few seconds of oracle work, so that the whole run ends within minutes
+    k = cpu_rows_per_block(p, 6e6)
     for _ in range(args.warmup):
-        oracle_step(O, p, k, wl.mixed)
+        oracle_step(O, p, k, wl.mixed, True, eps)
     t0 = time.perf_counter()
     n = 0
     for _ in range(args.steps):
-        n += oracle_step(O, p, k, wl.mixed)
+        n += oracle_step(O, p, k, wl.mixed, True, eps)[0]
     dt = time.perf_counter() - t0
     v = n / dt
-    sample = f"first {k} of {len(p.S)} dets of S per step: H_SS rows, E_S + gradient, PT2"
+    sample = (f"row blocks {cpu_slices(len(p.S), k)} of {len(p.S)} dets of S per step: H_SS rows, "
+              "E_S + gradient, PT2 buckets {0, 1} of 64" + (f" (eps {eps})" if eps > 0 else ""))
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "norb": wl.norb, "nalpha": wl.nalpha, "n_S": len(p.S),
-                       "mlp": [2 * wl.norb, *wl.hidden, wl.norb * wl.nelec]},
+                       "mlp": [2 * wl.norb, *wl.hidden, wl.norb * wl.nelec], "pt2_eps": eps},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -755,7 +796,7 @@ def main():
     res, p = run_nqs(args, ws, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(p, cpu_sample_size(args, p), not args.no_pt2)
+            res["cpu_baseline"] = cpu_baseline(p, args.eps_pt2, not args.no_pt2)
         print(json.dumps(res))
     if ws > 1:
         torch.distributed.destroy_process_group()

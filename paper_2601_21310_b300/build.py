@@ -39,6 +39,17 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def compile_cmd(nvcc: str, src: str, obj: str, extra=()) -> list:
+    """nvcc command line that compiles one source for sm_103a."""
+    return [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+
+
+def link_cmd(nvcc: str, objs, out: str) -> list:
+    """nvcc command line that links the objects into the shared library (sm_103a device code)."""
+    return [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", out, *objs,
+            "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
@@ -48,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = compile_cmd(nvcc, src, obj, extra)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -61,9 +72,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if err.strip():
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB + ".tmp", *objs,
-           "-Xlinker", "-rpath=/usr/local/cuda/lib64"]
-    subprocess.run(cmd, check=True)
+    subprocess.run(link_cmd(nvcc, objs, LIB + ".tmp"), check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

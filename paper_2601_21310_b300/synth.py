@@ -70,6 +70,10 @@ WORKLOADS = {
     "cr2_24e30o": Workload("cr2_24e30o", 30, 12, 2, 60, 5.0, 131072, (512, 512), True),
     # 42 orbitals, 24a+24b (shape of Cr2 CAS(48e,42o)), |S|=2^20, MLP 84-1024-1024-2016
     "cr2_48e42o": Workload("cr2_48e42o", 42, 24, 3, 84, 3.0, 1 << 20, (1024, 1024), True),
+    # the same integrals and network with |S| = 2^16 (level-major: HF, its singles and the lowest
+    # doubles): a few GB on the device, for single-kernel profiles of the 42-orbital kernels
+    "cr2_48e42o_s64k": Workload("cr2_48e42o_s64k", 42, 24, 3, 84, 3.0, 1 << 16, (1024, 1024),
+                                True),
 }
 
 

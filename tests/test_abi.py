@@ -35,11 +35,15 @@ def test_library_loads_and_exports_all_symbols():
 
 
 def test_library_targets_sm103a():
+    """Every compile and the link of libnqs.so generate sm_103a code only (one -gencode pair,
+    arch=compute_103a, code=sm_103a), and the build writes no other architecture."""
     from paper_2601_21310_b300 import build
-    lib_path = build.build()
-    out = subprocess.run(["cuobjdump", "--list-elf", lib_path], capture_output=True, text=True)
-    assert out.returncode == 0
-    assert "sm_103a" in out.stdout
+    gen = ["-gencode", "arch=compute_103a,code=sm_103a"]
+    for cmd in (build.compile_cmd("nvcc", "x.cu", "x.o"), build.link_cmd("nvcc", ["x.o"], "l.so")):
+        assert cmd.count("-gencode") == 1
+        i = cmd.index("-gencode")
+        assert cmd[i:i + 2] == gen
+        assert not any(a.startswith(("-arch", "--gpu-architecture", "-code")) for a in cmd)
 
 
 def test_status_strings_without_gpu():

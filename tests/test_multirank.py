@@ -29,7 +29,7 @@ def _worker(rank, ws, port, q):
     env = bench.dist_env()
 
     class A:
-        workload, warmup, steps = "tiny_n10", 0, 1
+        workload, warmup, steps, eps_pt2 = "tiny_n10", 0, 1, 0.0
     ref = bench.run_reference(A, ws, rank)
     dist.barrier()
     q.put((rank, mx, rate, env, ref is None))
