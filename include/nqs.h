@@ -278,16 +278,34 @@ int nqs_pt2_unique(nqs_problem* problem, const uint64_t* dets, const double* psi
 typedef struct nqs_batch nqs_batch; /* opaque */
 
 /* A batch of n independent E_S + gradient evaluations (nqs_energy_grad per problem; problems
- * may differ in norb, electron counts, |S| and network width). All arrays have n entries and
- * refer to caller-owned objects that must outlive the batch: problems[i], nets[i] (with
- * nets[i] created on problems[i]), csrs[i] (from nqs_connections on dets[i]), dets[i] (device
- * [nS[i]][2]), outs[i] (device [4]) and grads[i] (device, or NULL for energy only).
- * nstreams side streams run the problems concurrently (largest |S| first). */
+ * may differ in norb, electron counts, |S| and network width), the "many independent
+ * problems" form of the micro-batching of Sec. 3.2. All arrays have n entries and refer to
+ * caller-owned objects that must outlive the batch: problems[i], nets[i] (with nets[i] created
+ * on problems[i]), csrs[i] (from nqs_connections on dets[i]), dets[i] (device [nS[i]][2]),
+ * outs[i] (device [4]) and grads[i] (device, or NULL for energy only). Their device addresses
+ * are fixed for the batch's life (the grouped mode builds its descriptors on them once).
+ * Modes (nqs_batch_set_mode):
+ *   NQS_BATCH_GROUPED  each stage of the pipeline is one launch over all problems: the dense
+ *                      layers as persistent tensor-core GEMMs over a (problem, tile) work list,
+ *                      the LU factorisations one launch per block size, the energy stage and
+ *                      the adjoint one launch each; about twenty launches per step whatever n.
+ *                      Needs every net in NQS_MIXED with hidden widths divisible by 8, every
+ *                      nS[i] <= 2^20, nalpha and nbeta <= 12, and grads all non-NULL or all
+ *                      NULL. The default when the batch qualifies. Holds a workspace of about
+ *                      (7 KB + 4 (nalpha^2 + nbeta^2) B) per configuration at width 128. With
+ *                      autotuning on (nqs_set_autotune), the first run times tile widths
+ *                      64/128/256 per GEMM stage and keeps the fastest.
+ *   NQS_BATCH_STREAMS  nstreams side streams run the problems' own pipelines concurrently
+ *                      (largest |S| first).
+ * Results equal the problems' own nqs_energy_grad calls up to the order of the FP32 sums of
+ * the weight gradients (the grouped GEMMs split K as the single GEMMs do at their default tile
+ * widths). */
 int nqs_batch_create(int n, nqs_problem* const* problems, nqs_net* const* nets,
                      const nqs_csr* csrs, const uint64_t* const* dets, const int64_t* nS,
                      double* const* outs, void* const* grads, int nstreams, nqs_batch** out);
-/* Run the batch eagerly: fork from `stream`, one pipeline per problem on the side streams,
- * join back; stream-ordered, no host sync. */
+/* Run the batch eagerly: the grouped stages on `stream`, or a fork from `stream` to one
+ * pipeline per problem on the side streams and a join back. Stream-ordered; the first grouped
+ * run builds the workspace and descriptors (and tunes the tile widths), synchronising. */
 int nqs_batch_run(nqs_batch* batch, nqs_stream_t stream);
 /* Record nqs_batch_run once into a CUDA graph (stream must not be the legacy NULL stream) and
  * instantiate it; nqs_batch_launch then replays the whole batch with one graph launch. Run
@@ -295,6 +313,13 @@ int nqs_batch_run(nqs_batch* batch, nqs_stream_t stream);
 int nqs_batch_capture(nqs_batch* batch, nqs_stream_t stream);
 int nqs_batch_launch(nqs_batch* batch, nqs_stream_t stream);
 int nqs_batch_destroy(nqs_batch* batch);
+#define NQS_BATCH_STREAMS 0
+#define NQS_BATCH_GROUPED 1
+/* Select the mode; NQS_ERR_UNSUPPORTED when the batch does not qualify for the grouped mode.
+ * A graph recorded in the other mode is dropped (capture again). */
+int nqs_batch_set_mode(nqs_batch* batch, int mode);
+/* the current mode, or NQS_ERR_ARG */
+int nqs_batch_get_mode(const nqs_batch* batch);
 
 /* GEMM tile-width autotuner (project-written): when on, the first tensor-core GEMM of each
  * shape times tile widths 64/128/256 on its stream and keeps the fastest for the process

@@ -368,13 +368,12 @@ __global__ void k_combine(int64_t M, const double* __restrict__ la2, const int* 
 // Same partial pivoting as the warp kernel (largest |a_ik|, lowest row on ties), |det| in FP64
 // as (mantissa, exponent), and the inverse solved column by column from the factors.
 template <class T, int N>
-__global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ dets, int64_t M,
-                                                int norb, int nel, int spin,
-                                                const T* __restrict__ Phi,
-                                                double* __restrict__ la_out,
-                                                int* __restrict__ ex_out,
-                                                int8_t* __restrict__ sg_out, T* __restrict__ Ainv,
-                                                int* singular) {
+__device__ __forceinline__ void lu_reg_rows(const ulonglong2* __restrict__ dets, int64_t M,
+                                            int norb, int nel, int spin,
+                                            const T* __restrict__ Phi,
+                                            double* __restrict__ la_out, int* __restrict__ ex_out,
+                                            int8_t* __restrict__ sg_out, T* __restrict__ Ainv,
+                                            int* singular) {
     const int col0 = spin == 0 ? 0 : nel - N;
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
          m += (int64_t)gridDim.x * blockDim.x) {
@@ -462,6 +461,25 @@ __global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ d
             }
         }
     }
+}
+
+template <class T, int N>
+__global__ void __launch_bounds__(128) k_lu_reg(const ulonglong2* __restrict__ dets, int64_t M,
+                                                int norb, int nel, int spin,
+                                                const T* __restrict__ Phi,
+                                                double* __restrict__ la_out,
+                                                int* __restrict__ ex_out,
+                                                int8_t* __restrict__ sg_out, T* __restrict__ Ainv,
+                                                int* singular) {
+    lu_reg_rows<T, N>(dets, M, norb, nel, spin, Phi, la_out, ex_out, sg_out, Ainv, singular);
+}
+
+// the same over many problems' blocks of one size: blockIdx.y = job
+template <int N>
+__global__ void __launch_bounds__(128) k_g_lu(const GLuJob* __restrict__ jobs) {
+    const GLuJob J = jobs[blockIdx.y];
+    lu_reg_rows<float, N>(J.dets, J.M, J.norb, J.nel, J.spin, J.Phi, J.la, J.ex, J.sg, J.Ainv,
+                          J.singular);
 }
 
 template <class T, int N>
@@ -1323,5 +1341,230 @@ static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, co
     NQS_TRY(rowsum_bf16(sc, dPhiT, nout, M, ldM, gb3, s));
     NQS_TRY(rowsum_bf16(sc, dZ2T, H2, M, ldM, gb2, s));
     NQS_TRY(rowsum_bf16(sc, dZ1T, H1, M, ldM, gb1, s));
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched problems: one launch per stage over all problems (blockIdx.y = problem). The
+// arithmetic of each stage is that of the single-problem kernels above.
+// ------------------------------------------------------------------------------------------
+// X [M][ldX] (bf16 0/1, zero pad columns) and its transpose XT [nin][ldM]; W1p = W1 padded to
+// ldX columns; W2T = W2^T [H1][H2]; W3T = W3^T [H2][ldP] (blockIdx.z: 0 bits, 1 W1p, 2 W2T,
+// 3 W3T)
+__global__ void k_g_bits_prep(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.y];
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const uint16_t one = 0x3F80u;  // bf16 1.0
+    if (blockIdx.z == 0) {
+        const int per = P.ldX / 8;
+        for (int64_t t = t0; t < P.M * per; t += step) {
+            const int64_t m = t / per;
+            const int c0 = (int)(t - m * per) * 8;
+            const ulonglong2 x = P.dets[m];
+            uint32_t w[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = c0 + 2 * k + h;
+                    uint32_t bit = 0;
+                    if (c < P.norb) bit = (uint32_t)(x.x >> c) & 1u;
+                    else if (c < P.nin) bit = (uint32_t)(x.y >> (c - P.norb)) & 1u;
+                    v |= (bit ? (uint32_t)one : 0u) << (16 * h);
+                    if (c < P.nin) ((uint16_t*)P.XT)[(int64_t)c * P.ldM + m] = bit ? one : 0;
+                }
+                w[k] = v;
+            }
+            *(uint4*)(P.X + m * P.ldX + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else if (blockIdx.z == 1) {
+        for (int64_t t = t0; t < (int64_t)P.H1 * P.ldX; t += step) {
+            const int r = (int)(t / P.ldX), c = (int)(t - (int64_t)r * P.ldX);
+            P.W1p[t] = c < P.nin ? P.W1[(int64_t)r * P.nin + c] : __float2bfloat16_rn(0.f);
+        }
+    } else if (blockIdx.z == 2) {
+        for (int64_t t = t0; t < (int64_t)P.H1 * P.H2; t += step) {
+            const int r = (int)(t / P.H2), c = (int)(t - (int64_t)r * P.H2);  // W2T[r][c]
+            P.W2T[t] = P.W2[(int64_t)c * P.H1 + r];
+        }
+    } else {
+        for (int64_t t = t0; t < (int64_t)P.H2 * P.ldP; t += step) {
+            const int r = (int)(t / P.ldP), c = (int)(t - (int64_t)r * P.ldP);  // W3T[r][c]
+            if (c < P.nout) P.W3T[t] = P.W3[(int64_t)c * P.H2 + r];
+        }
+    }
+}
+
+int g_bits_prep(const GProb* P, const GDims& d, cudaStream_t s) {
+    const int64_t work = d.maxMX > (int64_t)d.max_H * d.max_H ? d.maxMX : (int64_t)d.max_H * d.max_H;
+    k_g_bits_prep<<<dim3(grid_for(work, 256, 256), d.np, 4), 256, 0, s>>>(P);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+template <int N>
+static int g_lu_n(const GLuJob* jobs, int njobs, int64_t maxM, cudaStream_t s) {
+    k_g_lu<N><<<dim3(grid_for(maxM, 128, 256), njobs), 128, 0, s>>>(jobs);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int g_lu(const GLuJob* jobs, int njobs, int n, int64_t maxM, cudaStream_t s) {
+    ProfScope prof_(PROF_LU, s);
+    switch (n) {
+#define NQS_GLU(K) \
+    case K: return g_lu_n<K>(jobs, njobs, maxM, s);
+        NQS_GLU(1) NQS_GLU(2) NQS_GLU(3) NQS_GLU(4) NQS_GLU(5) NQS_GLU(6) NQS_GLU(7) NQS_GLU(8)
+        NQS_GLU(9) NQS_GLU(10) NQS_GLU(11) NQS_GLU(12)
+#undef NQS_GLU
+        default: return NQS_ERR_UNSUPPORTED;
+    }
+}
+
+__global__ void k_g_combine(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.y];
+    const int64_t M = P.M;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M;
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const int sg = P.sg2[m] * P.sg2[M + m];
+        P.sign[m] = (int8_t)sg;
+        P.logabs[m] = sg == 0 ? -INFINITY
+                              : log(P.la2[m] * P.la2[M + m]) +
+                                    (double)(P.ex2[m] + P.ex2[M + m]) * M_LN2;
+    }
+}
+
+int g_combine(const GProb* P, const GDims& d, cudaStream_t s) {
+    k_g_combine<<<dim3(grid_for(d.maxM, 256, 256), d.np), 256, 0, s>>>(P);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// dPhi rows: zero, then w_m (A^-1)_kj at [occ_j][col0 + k] of each spin block (as k_adjoint)
+__global__ void __launch_bounds__(256) k_g_adjoint(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.y];
+    __shared__ uint8_t occ_s[8][2][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nel = P.na + P.nb;
+    for (int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; m < P.M;
+         m += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const ulonglong2 x = P.dets[m];
+        __nv_bfloat16* row = P.dPhi + m * P.ldP;
+        for (int c = lane; c < P.ldP; c += 32) row[c] = __float2bfloat16_rn(0.f);
+        for (int p = lane; p < P.norb; p += 32) {
+            const uint64_t below = p == 0 ? 0ull : ((1ull << p) - 1ull);
+            if ((x.x >> p) & 1ull) occ_s[warp][0][__popcll(x.x & below)] = (uint8_t)p;
+            if ((x.y >> p) & 1ull) occ_s[warp][1][__popcll(x.y & below)] = (uint8_t)p;
+        }
+        __syncwarp();
+        const float wm = (float)P.w[m];
+        for (int spin = 0; spin < 2; ++spin) {
+            const int n = spin == 0 ? P.na : P.nb, col0 = spin == 0 ? 0 : P.na;
+            const float* inv = spin == 0 ? P.Ainv_a + m * n * n : P.Ainv_b + m * n * n;
+            for (int r = lane; r < n * n; r += 32) {
+                const int j = r / n, k = r - j * n;
+                const float g = wm * inv[k * n + j];
+                row[(int64_t)occ_s[warp][spin][j] * nel + col0 + k] = __float2bfloat16_rn(g);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+int g_adjoint(const GProb* P, const GDims& d, cudaStream_t s) {
+    k_g_adjoint<<<dim3(grid_for(d.maxM * 32, 256, 512), d.np), 256, 0, s>>>(P);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// dPhiT [nout][ldM] = dPhi^T, 32 x 32 tiles through shared memory (blockIdx.z = problem)
+__global__ void k_g_transpose_dphi(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.z];
+    __shared__ unsigned short tile[32][33];
+    const unsigned short* S = (const unsigned short*)P.dPhi;
+    unsigned short* D = (unsigned short*)P.dPhiT;
+    const int64_t R = P.M, Cn = P.nout;
+    for (int64_t r0 = (int64_t)blockIdx.y * 32; r0 < R; r0 += (int64_t)gridDim.y * 32) {
+        const int64_t c0 = (int64_t)blockIdx.x * 32;
+        if (c0 >= Cn) return;
+        __syncthreads();
+        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+            const int64_t r = r0 + i, c = c0 + threadIdx.x;
+            tile[i][threadIdx.x] = (r < R && c < Cn) ? S[r * P.ldP + c] : (unsigned short)0;
+        }
+        __syncthreads();
+        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+            const int64_t c = c0 + i, r = r0 + threadIdx.x;
+            if (c < Cn && r < R) D[c * P.ldM + r] = tile[threadIdx.x][i];
+        }
+    }
+}
+
+int g_transpose_dphi(const GProb* P, const GDims& d, cudaStream_t s) {
+    const unsigned gy = (unsigned)((d.maxM + 31) / 32 < 1024 ? (d.maxM + 31) / 32 : 1024);
+    k_g_transpose_dphi<<<dim3((unsigned)((d.max_nout + 31) / 32), gy, d.np), dim3(32, 8), 0, s>>>(
+        P);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+// bias gradients: the row sums of dPhiT (db3), dZ2T (db2) and dZ1T (db1) over the first M
+// columns, in the order of k_rowsum_part / k_rowsum_final (chunks of ROWSUM_CHUNK reduced by a
+// fixed tree, the chunk sums added in order). blockIdx.x = row, blockIdx.y = problem,
+// blockIdx.z = which matrix.
+__global__ void __launch_bounds__(256) k_g_bias_grads(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.y];
+    if (!P.grad) return;
+    const int which = blockIdx.z;
+    const int R = which == 0 ? P.nout : (which == 1 ? P.H2 : P.H1);
+    const int r = blockIdx.x;
+    if (r >= R) return;
+    const __nv_bfloat16* X = which == 0 ? P.dPhiT : (which == 1 ? P.dZ2T : P.dZ1T);
+    float* gb1 = P.grad + (size_t)P.H1 * P.nin;
+    float* gb2 = gb1 + P.H1 + (size_t)P.H2 * P.H1;
+    float* gb3 = gb2 + P.H2 + (size_t)P.nout * P.H2;
+    float* out = which == 0 ? gb3 : (which == 1 ? gb2 : gb1);
+    __shared__ float red[8];
+    const __nv_bfloat16* row = X + (int64_t)r * P.ldM;
+    const int64_t M = P.M, ld = P.ldM;
+    float total = 0.f;
+    for (int64_t c0 = 0; c0 < M; c0 += ROWSUM_CHUNK) {
+        const int64_t c1 = c0 + ROWSUM_CHUNK < M ? c0 + ROWSUM_CHUNK : M;
+        float acc = 0.f;
+        if ((ld % 8) == 0) {
+            const int64_t v1 = c0 + ((c1 - c0) & ~(int64_t)7);
+            for (int64_t i = c0 + 8 * threadIdx.x; i < v1; i += 8 * 256) {
+                const uint4 pk = *(const uint4*)(row + i);
+                const __nv_bfloat162* h2 = (const __nv_bfloat162*)&pk;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float2 f = __bfloat1622float2(h2[t]);
+                    acc += f.x + f.y;
+                }
+            }
+            for (int64_t i = v1 + threadIdx.x; i < c1; i += 256) acc += __bfloat162float(row[i]);
+        } else {
+            for (int64_t i = c0 + threadIdx.x; i < c1; i += 256) acc += __bfloat162float(row[i]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int k = 0; k < 8; ++k) t += red[k];
+            total += t;
+        }
+    }
+    if (threadIdx.x == 0) out[r] = total;
+}
+
+int g_bias_grads(const GProb* P, const GDims& d, cudaStream_t s) {
+    const int R = d.max_nout > d.max_H ? d.max_nout : d.max_H;
+    k_g_bias_grads<<<dim3((unsigned)R, d.np, 3), 256, 0, s>>>(P);
+    NQS_CK_LAUNCH();
     return NQS_OK;
 }

@@ -48,6 +48,17 @@ struct TcGemm {
 };
 int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s);
 
+// Grouped form for many independent GEMMs of different shapes (one per batched problem): the
+// descriptors (tensor maps, epilogue arguments, split-K partial buffers) are built once for
+// fixed operand addresses; each launch runs every group's tiles in one persistent kernel with
+// tile width BN (64, 128 or 256), then one grouped split-K reduction.
+struct TcGroupSet;
+int tc_group_set_create(const TcGemm* gs, int n, int BN, TcGroupSet** out);
+int tc_group_set_launch(const TcGroupSet* set, cudaStream_t s);
+int tc_group_set_units(const TcGroupSet* set);
+void tc_group_set_destroy(TcGroupSet* set);
+int tc_autotune_on();  // nqs_set_autotune state
+
 // forward intermediates kept for the backward
 struct Fwd {
     int64_t M;
@@ -74,3 +85,61 @@ int net_forward(nqs_net* net, Scratch& sc, const uint64_t* dets, int64_t M, Fwd&
 // w: device [M] adjoint weights w_x = dE/dpsi~_x * psi~_x; grad: device (double or float)
 int net_backward(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f, const double* w,
                  void* grad, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------------
+// Batched problems, one launch per pipeline stage over all of them (batch.cu drives these).
+// One descriptor per problem in device memory; a grouped kernel takes the problem from
+// blockIdx.y (blockIdx.z for per-problem job lists) and strides over that problem's rows.
+// Mixed form only (BF16 network on the tensor cores, FP32 LU up to 12 x 12 blocks).
+// ------------------------------------------------------------------------------------------
+struct GProb {
+    const ulonglong2* dets;
+    int64_t M;                 // |S|
+    int norb, na, nb, nin, nout, H1, H2, ldX;
+    int64_t ldM, ldP;          // M and nout rounded up to 8
+    const __nv_bfloat16 *W1, *W2, *W3;           // caller's weights
+    const float *b1, *b2, *b3, *phi0;             // caller's biases and Phi0
+    const int64_t* rp;         // H_SS of the problem (library CSR)
+    const int32_t* col;
+    const double* val;
+    double* out;               // caller's [4] = {E, N, D, max log|psi|}
+    float* grad;               // caller's gradient (W1, b1, W2, b2, W3, b3) or null
+    // workspace
+    __nv_bfloat16 *X, *XT, *W1p, *H1a, *H1T, *H2a, *H2T, *W2T, *W3T, *dPhi, *dPhiT, *dZ2, *dZ2T,
+        *dZ1T;
+    float *Phi, *Ainv_a, *Ainv_b;
+    double *la2, *logabs, *psi, *v, *w;
+    int* ex2;
+    int8_t *sg2, *sign;
+    int* singular;
+};
+
+// register-LU job of one spin block of one problem (problems grouped by block size n)
+struct GLuJob {
+    const ulonglong2* dets;
+    int64_t M;
+    int norb, nel, spin;
+    const float* Phi;
+    double* la;
+    int* ex;
+    int8_t* sg;
+    float* Ainv;
+    int* singular;
+};
+
+// launch extents over the problems: the largest of each size
+struct GDims {
+    int np;
+    int64_t maxM, maxMX;  // rows; rows x (ldX / 8)
+    int max_nin, max_nout, max_H;
+};
+
+int g_bits_prep(const GProb* P, const GDims& d, cudaStream_t s);
+int g_lu(const GLuJob* jobs, int njobs, int n, int64_t maxM, cudaStream_t s);
+int g_combine(const GProb* P, const GDims& d, cudaStream_t s);
+int g_adjoint(const GProb* P, const GDims& d, cudaStream_t s);
+int g_transpose_dphi(const GProb* P, const GDims& d, cudaStream_t s);
+int g_bias_grads(const GProb* P, const GDims& d, cudaStream_t s);
+// energy.cu: max log|psi|, scaled psi, SpMV, compensated N and D (part: device
+// [np][2][256] partial sums), E and the adjoint weights
+int g_energy(const GProb* P, const GDims& d, double2* part, cudaStream_t s);

@@ -7,6 +7,7 @@
 
 #include "ansatz.cuh"
 #include "excite.cuh"
+#include "ksum.cuh"
 #include "nqs_internal.cuh"
 #include "prof.cuh"
 
@@ -15,11 +16,11 @@
 // are added in a fixed order and then reduced by a shuffle tree: the result is deterministic.
 // OFFDIAG skips each row's first entry (the diagonal, first in every row of H_SS).
 template <bool OFFDIAG>
-__global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rp,
-                                              const int32_t* __restrict__ col,
-                                              const double* __restrict__ val,
-                                              const double* __restrict__ x, int64_t n,
-                                              double* __restrict__ y) {
+__device__ __forceinline__ void spmv_rows(const int64_t* __restrict__ rp,
+                                          const int32_t* __restrict__ col,
+                                          const double* __restrict__ val,
+                                          const double* __restrict__ x, int64_t n,
+                                          double* __restrict__ y) {
     const int lane = threadIdx.x & 31;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n;
          r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -42,6 +43,15 @@ __global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rp,
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
         if (lane == 0) y[r] = s;
     }
+}
+
+template <bool OFFDIAG>
+__global__ void __launch_bounds__(256) k_spmv(const int64_t* __restrict__ rp,
+                                              const int32_t* __restrict__ col,
+                                              const double* __restrict__ val,
+                                              const double* __restrict__ x, int64_t n,
+                                              double* __restrict__ y) {
+    spmv_rows<OFFDIAG>(rp, col, val, x, n, y);
 }
 
 // psi~ = sign * exp(log|psi| - max log|psi|)
@@ -371,5 +381,99 @@ extern "C" int nqs_asym_energy_grad(nqs_problem* p, nqs_net* net, const nqs_csr*
         NQS_TRY(backward_batched(net, sc, T, nT, mb, f, w, grad, s));
     }
     if (opts && opts->validate) NQS_TRY(check_err_word(p, s));
+    return NQS_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched problems: the energy stage over all problems, one launch per step (blockIdx.y =
+// problem), with the arithmetic of the single-problem path: max log|psi| (over psi != 0),
+// psi~ = sign exp(log|psi| - max), v = H_SS psi~ (spmv_rows), N = psi~.v and D = psi~.psi~ as
+// in kdot2_f64 (KR_BLOCKS partial sums per problem, then one block), E = N / D and the adjoint
+// weights w = (2/D)(v - E psi~) psi~.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_g_maxlog(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.y];
+    __shared__ double sm[256];
+    double m = -INFINITY;
+    for (int64_t i = threadIdx.x; i < P.M; i += 256)
+        if (P.sign[i] != 0) m = fmax(m, P.logabs[i]);
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) P.out[3] = sm[0];
+}
+
+__global__ void k_g_scaled_psi(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.y];
+    const double M = P.out[3];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.M;
+         i += (int64_t)gridDim.x * blockDim.x)
+        P.psi[i] = P.sign[i] == 0 ? 0.0 : (double)P.sign[i] * exp(P.logabs[i] - M);
+}
+
+__global__ void __launch_bounds__(256) k_g_spmv(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.y];
+    spmv_rows<false>(P.rp, P.col, P.val, P.psi, P.M, P.v);
+}
+
+// blockIdx.z = 0: partial sums of v psi~, 1: of psi~ psi~ (KR_BLOCKS blocks per problem)
+__global__ void __launch_bounds__(KR_THREADS) k_g_dot(const GProb* __restrict__ Pv,
+                                                       double2* __restrict__ part) {
+    const GProb& P = Pv[blockIdx.y];
+    const int mode = blockIdx.z;
+    KS k{0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * KR_THREADS + threadIdx.x; i < P.M;
+         i += (int64_t)KR_BLOCKS * KR_THREADS) {
+        const double v = mode == 0 ? __dmul_rn(P.v[i], P.psi[i]) : __dmul_rn(P.psi[i], P.psi[i]);
+        k = ks_add(k, v);
+    }
+    KS r = block_ks(k);
+    if (threadIdx.x == 0)
+        part[((int64_t)blockIdx.y * 2 + mode) * KR_BLOCKS + blockIdx.x] = make_double2(r.s, r.c);
+}
+
+// one block per (problem, mode): N, D; then E = N / D (one thread)
+__global__ void __launch_bounds__(KR_THREADS) k_g_dot_final(const GProb* __restrict__ Pv,
+                                                             const double2* __restrict__ part) {
+    const GProb& P = Pv[blockIdx.x];
+    const int mode = blockIdx.y;
+    const double2* pp = part + ((int64_t)blockIdx.x * 2 + mode) * KR_BLOCKS;
+    KS k{0.0, 0.0};
+    for (int i = threadIdx.x; i < KR_BLOCKS; i += KR_THREADS) k = ks_merge(k, KS{pp[i].x, pp[i].y});
+    KS r = block_ks(k);
+    if (threadIdx.x == 0) P.out[1 + mode] = r.s + r.c;
+}
+
+__global__ void k_g_weights(const GProb* __restrict__ Pv) {
+    const GProb& P = Pv[blockIdx.y];
+    const double N = P.out[1], D = P.out[2];
+    const double E = N / D;
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.out[0] = E;
+    if (!P.grad) return;
+    const double c = __ddiv_rn(2.0, D);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.M;
+         i += (int64_t)gridDim.x * blockDim.x)
+        P.w[i] = __dmul_rn(__dmul_rn(c, __dsub_rn(P.v[i], __dmul_rn(E, P.psi[i]))), P.psi[i]);
+}
+
+int g_energy(const GProb* P, const GDims& d, double2* part, cudaStream_t s) {
+    k_g_maxlog<<<dim3(1, d.np), 256, 0, s>>>(P);
+    NQS_CK_LAUNCH();
+    k_g_scaled_psi<<<dim3(grid_for(d.maxM, 256, 256), d.np), 256, 0, s>>>(P);
+    NQS_CK_LAUNCH();
+    {
+        ProfScope prof_(PROF_SPMV, s);
+        k_g_spmv<<<dim3(grid_for(d.maxM * 32, 256, 1024), d.np), 256, 0, s>>>(P);
+    }
+    NQS_CK_LAUNCH();
+    k_g_dot<<<dim3(KR_BLOCKS, d.np, 2), KR_THREADS, 0, s>>>(P, part);
+    NQS_CK_LAUNCH();
+    k_g_dot_final<<<dim3(d.np, 2), KR_THREADS, 0, s>>>(P, part);
+    NQS_CK_LAUNCH();
+    k_g_weights<<<dim3(grid_for(d.maxM, 256, 256), d.np), 256, 0, s>>>(P);
+    NQS_CK_LAUNCH();
     return NQS_OK;
 }

@@ -429,8 +429,7 @@ __device__ __forceinline__ double exc_element(const ProblemDev& P, const DetCtx&
             int j = c.occA[k];
             if (alpha) {
                 if (j == x.i) continue;
-                double t = __ldg(&P.TJ[base + j]) - __ldg(&P.TK[base + j]);
-                v = v + t;
+                v = v + __ldg(&P.TD[base + j]);
             } else {
                 v = v + __ldg(&P.TJ[base + j]);
             }
@@ -439,8 +438,7 @@ __device__ __forceinline__ double exc_element(const ProblemDev& P, const DetCtx&
             int j = c.occB[k];
             if (!alpha) {
                 if (j == x.i) continue;
-                double t = __ldg(&P.TJ[base + j]) - __ldg(&P.TK[base + j]);
-                v = v + t;
+                v = v + __ldg(&P.TD[base + j]);
             } else {
                 v = v + __ldg(&P.TJ[base + j]);
             }

@@ -24,6 +24,7 @@
 
 #include <map>
 #include <mutex>
+#include <vector>
 
 #include "ansatz.cuh"
 #include "nqs_internal.cuh"
@@ -520,6 +521,209 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                      "r"((uint32_t)(2 * BN)));
 }
 
+// ------------------------------------------------------------------------------------------
+// Grouped form: one persistent launch over the (group, split, row tile, column tile) work list
+// of many independent GEMMs of different shapes (the batched problems of one pipeline stage).
+// Each group's tensor maps and epilogue arguments live in device memory; unit u belongs to the
+// group whose [unit0, unit0 + units) holds it (binary search over the groups). The roles and
+// the pipeline are those of k_gemm_tc; a role that meets a new group first makes the group's
+// tensor maps visible to the tensor-map proxy (they were written by a host copy).
+// ------------------------------------------------------------------------------------------
+struct __align__(128) TcGroupDev {
+    CUtensorMap tmA, tmB, tmC, tmCT, tmP;
+    TcArgs a;
+    int unit0, units;
+};
+
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"((uint64_t)m)
+                 : "memory");
+}
+
+__device__ __forceinline__ int group_of(const TcGroupDev* __restrict__ G, int ng, int u) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (G[mid].unit0 <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc_g(const TcGroupDev* __restrict__ G, int ng, int units) {
+    using L = TcSmem<BN>;
+    constexpr int ST = L::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* epi_stage = smem + ST * L::STAGE;
+    uint64_t* full = (uint64_t*)(smem + ST * L::STAGE + L::EPI);
+    uint64_t* empty = full + ST;
+    uint64_t* tfull = empty + ST;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tslot = (uint32_t*)(tempty + 2);
+    volatile int* abort = (volatile int*)(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], TC_EPI_WARPS);
+        }
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(tslot)),
+            "r"((uint32_t)(2 * BN)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        uint32_t it = 0;
+        int gcur = -1;
+        for (int u = blockIdx.x; u < units && !*abort; u += gridDim.x) {
+            const int g = group_of(G, ng, u);
+            if (g != gcur) {
+                gcur = g;
+                tmap_acquire(&G[g].tmA);
+                tmap_acquire(&G[g].tmB);
+            }
+            const Unit w = unit_of(u - G[g].unit0, G[g].a, BN);
+            for (int i = 0; i < w.nk; ++i, ++it) {
+                const int s = it % ST;
+                const uint32_t ph = (it / ST) & 1u;
+                if (it >= (uint32_t)ST && !mbar_wait_ab(&empty[s], ph ^ 1u, abort)) break;
+                uint8_t* st = smem + s * L::STAGE;
+                mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
+                tma_load_2d(st, &G[g].tmA, &full[s], (w.kb0 + i) * TC_BK, w.m0);
+                tma_load_2d(st + L::A_BYTES, &G[g].tmB, &full[s], (w.kb0 + i) * TC_BK, w.n0);
+            }
+        }
+        // never leave with copies in flight: wait (bounded) for the last load of each stage
+        const uint32_t last = it;
+        for (uint32_t j = last > (uint32_t)ST ? last - ST : 0; j < last; ++j) {
+            volatile int no_abort = 0;
+            mbar_wait_ab(&full[j % ST], (j / ST) & 1u, &no_abort);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_bf16<BN>();
+        uint32_t it = 0, j = 0;
+        for (int u = blockIdx.x; u < units && !*abort; u += gridDim.x, ++j) {
+            const int g = group_of(G, ng, u);
+            const Unit w = unit_of(u - G[g].unit0, G[g].a, BN);
+            const uint32_t b = j & 1u, use = j >> 1;
+            if (use > 0 && !mbar_wait_ab(&tempty[b], (use - 1) & 1u, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + b * BN;
+            bool ok = true;
+            for (int i = 0; i < w.nk; ++i, ++it) {
+                const int s = it % ST;
+                if (!mbar_wait_ab(&full[s], (it / ST) & 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint8_t* st = smem + s * L::STAGE;
+                const uint64_t da = sdesc_sw128(smem_u32(st));
+                const uint64_t db = sdesc_sw128(smem_u32(st + L::A_BYTES));
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk)
+                    umma(acc, da + 2 * kk, db + 2 * kk, idesc, (i | kk) != 0 ? 1u : 0u);
+                umma_commit(&empty[s]);
+            }
+            if (!ok) break;
+            umma_commit(&tfull[b]);
+        }
+    } else if (warp >= 2) {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int c_lo = half * (BN / 2), c_hi = c_lo + BN / 2;
+        uint32_t j = 0;
+        int gcur = -1;
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++j) {
+            const int g = group_of(G, ng, u);
+            const TcArgs& a = G[g].a;  // read in place (L1): fewer live registers
+            if (g != gcur) {
+                // stores of the previous group's buffers have landed before its maps change
+                if (gcur >= 0 && lane == 0) bulk_wait0();
+                gcur = g;
+                if (lane == 0) {
+                    tmap_acquire(&G[g].tmC);
+                    tmap_acquire(&G[g].tmCT);
+                    tmap_acquire(&G[g].tmP);
+                }
+                __syncwarp();
+            }
+            const Unit w = unit_of(u - G[g].unit0, a, BN);
+            const uint32_t b = j & 1u, use = j >> 1;
+            if (!mbar_wait_ab(&tfull[b], use & 1u, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = w.m0 + q * 32 + lane;
+            const bool row_ok = row < a.M;
+#pragma unroll 1
+            for (int c = c_lo; c < c_hi; c += 32) {
+                uint32_t r[32];
+                if (w.nk > 0 && w.n0 + c < a.N) {
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)c, r);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) r[t] = 0u;
+                }
+                if (w.n0 + c >= a.N) continue;  // a column block past this group's N
+                if (a.tma_c)
+                    epilogue32_tma(a, w, row, row_ok, w.n0 + c, w.m0 + q * 32, r,
+                                   epi_stage + (warp - 2) * 4096, &G[g].tmC, &G[g].tmCT,
+                                   &G[g].tmP);
+                else
+                    epilogue32(a, w, row, row_ok, w.n0 + c, r);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+        if (lane == 0) bulk_wait0();  // every store of this warp has landed
+    }
+    if (*abort && G[0].a.err) atomicExch(G[0].a.err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)(2 * BN)));
+}
+
+// split-K sums of many groups: blockIdx.y = job
+struct SplitJob {
+    const float* P;
+    float* C;
+    int64_t ldc;
+    int splits, M, N;
+};
+__global__ void k_splitk_reduce_g(const SplitJob* __restrict__ jobs) {
+    const SplitJob J = jobs[blockIdx.y];
+    const int64_t total = (int64_t)J.M * J.N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int z = 0; z < J.splits; ++z) s += J.P[(size_t)z * total + t];
+        const int64_t m = t / J.N, n = t - m * J.N;
+        J.C[m * J.ldc + n] = s;
+    }
+}
+
 // C[m][n] = sum over splits of P[z][m][n] (fixed order)
 __global__ void k_splitk_reduce(const float* __restrict__ P, int splits, int M, int N,
                                 float* __restrict__ C, int64_t ldc) {
@@ -614,6 +818,9 @@ int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
 
 }  // namespace
 
+// the tile width a shape gets without tuning
+static int heuristic_bn_shape(int N) { return N <= 64 ? 64 : (N <= 128 ? 128 : 256); }
+
 // launch with a given tile width
 static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
     CUtensorMap ta, tb;
@@ -692,6 +899,165 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
 }
 
 // ------------------------------------------------------------------------------------------
+// grouped GEMM sets (batched problems): descriptors built once, one launch per use
+// ------------------------------------------------------------------------------------------
+struct TcGroupSet {
+    TcGroupDev* dev = nullptr;
+    int ng = 0, units = 0, BN = 0;
+    std::vector<float*> partials;
+    SplitJob* jobs = nullptr;
+    int njobs = 0;
+    int64_t max_mn = 0;
+};
+
+void tc_group_set_destroy(TcGroupSet* set) {
+    if (!set) return;
+    cudaFree(set->dev);
+    cudaFree(set->jobs);
+    for (float* q : set->partials) cudaFree(q);
+    delete set;
+}
+
+int tc_group_set_create(const TcGemm* gs, int n, int BN, TcGroupSet** out) {
+    if (!gs || n <= 0 || !out || (BN != 64 && BN != 128 && BN != 256)) return NQS_ERR_ARG;
+    TcGroupSet* set = new TcGroupSet();
+    set->BN = BN;
+    auto fail = [&](int code) {
+        tc_group_set_destroy(set);
+        return code;
+    };
+    std::vector<TcGroupDev> host(n);
+    std::vector<SplitJob> jobs;
+    int unit0 = 0;
+    for (int i = 0; i < n; ++i) {
+        const TcGemm& g = gs[i];
+        if (g.M <= 0 || g.N <= 0 || g.K <= 0) return fail(NQS_ERR_ARG);
+        if ((g.lda * 2) % 16 || (g.ldb * 2) % 16 || ((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15))
+            return fail(NQS_ERR_UNSUPPORTED);
+        TcGroupDev& d = host[i];
+        memset(&d, 0, sizeof d);
+        int st = make_map(&d.tmA, g.A, g.M, g.K, g.lda, 128);
+        if (st == NQS_OK) st = make_map(&d.tmB, g.B, g.N, g.K, g.ldb, BN);
+        if (st != NQS_OK) return fail(st);
+        TcArgs& a = d.a;
+        a.M = g.M;
+        a.N = g.N;
+        a.K = g.K;
+        a.epi = g.epi;
+        a.C = g.C;
+        a.ldc = g.ldc;
+        a.c_bf16 = g.c_bf16;
+        a.CT = g.CT;
+        a.ldct = g.ldct;
+        a.bias = g.bias;
+        a.phi0 = g.phi0;
+        a.aux = g.aux;
+        a.ld_aux = g.ld_aux;
+        a.err = g.err;
+        // K splits as the single GEMM would choose them for this shape (same partial sums)
+        const int bref = heuristic_bn_shape(g.N);
+        const int tiles_ref = ((g.N + bref - 1) / bref) * ((g.M + 127) / 128);
+        const int nkb = (g.K + TC_BK - 1) / TC_BK;
+        int splits = 1;
+        if (g.epi == EPI_STORE && !g.CT && !g.c_bf16)
+            while (tiles_ref * splits < 148 && splits * 2 <= nkb && splits < 64) splits *= 2;
+        if (splits > 1) {
+            const int per = (nkb + splits - 1) / splits;
+            splits = (nkb + per - 1) / per;
+        }
+        a.splits = splits;
+        bool tma = true;
+        if (splits > 1) {
+            float* P = nullptr;
+            if (cudaMalloc(&P, (size_t)splits * g.M * g.N * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(NQS_ERR_OOM);
+            }
+            set->partials.push_back(P);
+            a.partial = P;
+            const cuuint64_t dims[3] = {(cuuint64_t)g.N, (cuuint64_t)g.M, (cuuint64_t)splits};
+            const cuuint64_t str[2] = {(cuuint64_t)g.N * 4, (cuuint64_t)g.M * g.N * 4};
+            tma = make_store_map(&d.tmP, P, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 3, dims, str,
+                                 CU_TENSOR_MAP_SWIZZLE_128B);
+            jobs.push_back(SplitJob{P, (float*)g.C, g.ldc, splits, g.M, g.N});
+            const int64_t mn = (int64_t)g.M * g.N;
+            if (mn > set->max_mn) set->max_mn = mn;
+        } else {
+            if (g.C) {
+                const cuuint64_t dims[2] = {(cuuint64_t)g.N, (cuuint64_t)g.M};
+                const cuuint64_t str[1] = {(cuuint64_t)g.ldc * (g.c_bf16 ? 2 : 4)};
+                tma = make_store_map(&d.tmC, g.C,
+                                     g.c_bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                                     g.c_bf16 ? 2 : 4, 2, dims, str,
+                                     g.c_bf16 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                              : CU_TENSOR_MAP_SWIZZLE_128B);
+            }
+            if (tma && g.CT) {
+                tma = g.C == nullptr || g.c_bf16;
+                const cuuint64_t dims[2] = {(cuuint64_t)g.M, (cuuint64_t)g.N};
+                const cuuint64_t str[1] = {(cuuint64_t)g.ldct * 2};
+                tma = tma && make_store_map(&d.tmCT, g.CT, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, 2,
+                                            dims, str);
+            }
+        }
+        a.tma_c = tma ? 1 : 0;
+        d.unit0 = unit0;
+        d.units = ((g.N + BN - 1) / BN) * ((g.M + 127) / 128) * splits;
+        unit0 += d.units;
+    }
+    set->ng = n;
+    set->units = unit0;
+    if (cudaMalloc(&set->dev, sizeof(TcGroupDev) * n) != cudaSuccess ||
+        cudaMemcpy(set->dev, host.data(), sizeof(TcGroupDev) * n, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return fail(NQS_ERR_OOM);
+    }
+    if (!jobs.empty()) {
+        set->njobs = (int)jobs.size();
+        if (cudaMalloc(&set->jobs, sizeof(SplitJob) * jobs.size()) != cudaSuccess ||
+            cudaMemcpy(set->jobs, jobs.data(), sizeof(SplitJob) * jobs.size(),
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NQS_ERR_OOM);
+        }
+    }
+    *out = set;
+    return NQS_OK;
+}
+
+template <int BN>
+static int launch_tc_g(const TcGroupSet* set, cudaStream_t s) {
+    const int smem = TcSmem<BN>::BYTES;
+    NQS_CK(cudaFuncSetAttribute(k_gemm_tc_g<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem));
+    const int grid = set->units < num_sms() ? set->units : num_sms();
+    {
+        ProfScope prof_(PROF_GEMM, s);
+        k_gemm_tc_g<BN><<<grid, TC_THREADS, smem, s>>>(set->dev, set->ng, set->units);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int tc_group_set_launch(const TcGroupSet* set, cudaStream_t s) {
+    if (!set || set->units <= 0) return NQS_ERR_ARG;
+    const int st = set->BN == 64    ? launch_tc_g<64>(set, s)
+                   : set->BN == 128 ? launch_tc_g<128>(set, s)
+                                    : launch_tc_g<256>(set, s);
+    NQS_TRY(st);
+    if (set->njobs > 0) {
+        k_splitk_reduce_g<<<dim3(grid_for(set->max_mn, 256, 64), set->njobs), 256, 0, s>>>(
+            set->jobs);
+        NQS_CK_LAUNCH();
+    }
+    return NQS_OK;
+}
+
+int tc_group_set_units(const TcGroupSet* set) { return set ? set->units : 0; }
+
+// ------------------------------------------------------------------------------------------
 // tile-width autotuner: when enabled, the first GEMM of each (M, N, K, epilogue, output kind)
 // shape is timed with BN = 64, 128 and 256 (CUDA events on the launching stream, one warm-up
 // and two timed runs each) and the fastest width is remembered for the process. Tuning never
@@ -712,8 +1078,10 @@ std::map<TuneKey, int> g_tuned;
 std::mutex g_tune_mu;
 bool g_autotune = false;
 
-int heuristic_bn(int N) { return N <= 64 ? 64 : (N <= 128 ? 128 : 256); }
+int heuristic_bn(int N) { return heuristic_bn_shape(N); }
 }  // namespace
+
+int tc_autotune_on() { return g_autotune ? 1 : 0; }
 
 extern "C" int nqs_set_autotune(int on) {
     g_autotune = on != 0;

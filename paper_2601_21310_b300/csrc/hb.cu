@@ -178,6 +178,53 @@ __device__ __forceinline__ bool in_bucket_of(uint64_t a, uint64_t b, uint64_t B,
     return B == 1 || (det_hash(a, b) % B) == bucket;
 }
 
+// The screening test fl(v |psi_x|) >= eps for v >= 0 (a table entry or |<x'|H|x>|), without an
+// FP64 multiply per candidate: the rounded product is non-decreasing in v, so it holds exactly
+// when v >= v*, the smallest double that passes, and non-negative doubles order like their bit
+// patterns (an integer compare). v* is found once per x from eps / |psi_x| and its neighbours.
+// Should the search not settle within a few steps (it moves by ulps from the quotient), the
+// test falls back to the product.
+struct HbCut {
+    unsigned long long thr;  // bit pattern of v*
+    double ap, eps;
+    bool exact;              // fall back to fl(v ap) >= eps
+    __device__ __forceinline__ bool pass(double v) const {
+        return exact ? __dmul_rn(v, ap) >= eps
+                     : (unsigned long long)__double_as_longlong(v) >= thr;
+    }
+};
+
+__device__ __forceinline__ HbCut hb_cut(double eps, double ap) {
+    HbCut c;
+    c.ap = ap;
+    c.eps = eps;
+    c.exact = false;
+    c.thr = 0ull;
+    if (!(eps > 0.0)) return c;  // every v >= 0 passes
+    const double t = __ddiv_rn(eps, ap);
+    const unsigned long long inf = 0x7ff0000000000000ull;
+    if (!(t < __longlong_as_double((long long)inf))) {
+        c.thr = inf;  // no finite v passes
+        return c;
+    }
+    unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    int steps = 0;
+    if (__dmul_rn(t, ap) >= eps) {
+        while (b > 0 && steps < 64 && __dmul_rn(__longlong_as_double((long long)(b - 1)), ap) >= eps) {
+            --b;
+            ++steps;
+        }
+    } else {
+        do {
+            ++b;
+            ++steps;
+        } while (b < inf && steps < 64 && __dmul_rn(__longlong_as_double((long long)b), ap) < eps);
+    }
+    c.thr = b;
+    c.exact = steps >= 64;
+    return c;
+}
+
 // signed <x'|H|x> of a double read from its orbitals, with the same terms and signs as
 // exc_element: same spin (grp 0 alpha, 1 beta) holes i<j -> particles a<b, sign of i->a then
 // j->b; opposite spin i->a (alpha), j->b (beta)
@@ -278,6 +325,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             continue;
         }
         fill_ctx(P, x.x, x.y, ctx, lane);
+        const HbCut cut = hb_cut(eps, ap);
         auto keep = [&](bool take, uint64_t a2, uint64_t b2, double m) {
             const unsigned bal = __ballot_sync(FULL_MASK, take);
             if (APPEND) {
@@ -305,13 +353,14 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             if (e < nsing) {
                 decode_exc(P, PT, *ctx, x.x, x.y, e, ex);
                 const double hv = exc_element(P, *ctx, ex);
-                m = __dmul_rn(fabs(hv), ap);
+                const bool ok = cut.pass(fabs(hv));
                 if (PTM) {
-                    take = m >= eps && in_bucket_of(ex.a2, ex.b2, B, bucket) &&
+                    take = ok && in_bucket_of(ex.a2, ex.b2, B, bucket) &&
                            hash_lookup(H, ex.a2, ex.b2) < 0;
-                    m = __dmul_rn(hv, py);
+                    if (EMIT && take) m = __dmul_rn(hv, py);
                 } else {
-                    take = m >= eps && hash_lookup(H, ex.a2, ex.b2) < 0;
+                    take = ok && hash_lookup(H, ex.a2, ex.b2) < 0;
+                    if (EMIT && take) m = __dmul_rn(fabs(hv), ap);
                 }
             }
             keep(take, ex.a2, ex.b2, m);
@@ -342,7 +391,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                         j = ctx->occB[xb];
                         base = T.os_base + (int64_t)(i * n + j) * L;
                     }
-                    head = __dmul_rn(__ldg(&T.val[base]), ap) >= eps;
+                    head = cut.pass(__ldg(&T.val[base]));
                 }
                 unsigned hm = __ballot_sync(FULL_MASK, head);
                 while (hm) {
@@ -357,8 +406,8 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                         uint64_t a2 = 0, b2 = 0;
                         double m = 0.0;
                         if (t < L) {
-                            m = __dmul_rn(__ldg(&T.val[hb + t]), ap);
-                            pass = m >= eps;
+                            const double tv = __ldg(&T.val[hb + t]);
+                            pass = cut.pass(tv);
                             const uint16_t cd = __ldg(&T.code[hb + t]);
                             const int a = cd & 0xff, b = cd >> 8;
                             if (pass) {
@@ -381,6 +430,8 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                                 take = valid && hash_lookup(H, a2, b2) < 0;
                                 if (PTM && EMIT && take)
                                     m = __dmul_rn(double_element(P, grp, wA, wB, hi, hj, a, b), py);
+                                else if (!PTM && EMIT && take)
+                                    m = __dmul_rn(tv, ap);
                             }
                         }
                         keep(take, a2, b2, m);

@@ -51,7 +51,7 @@ struct ProblemDev {
     const double* J;                // J[p][q] = (pp|qq)
     const double* K;                // K[p][q] = (pq|qp)
     const double* TJ;               // TJ[(i*norb+a)*norb+j] = (ia|jj)
-    const double* TK;               // TK[(i*norb+a)*norb+j] = (ij|ja)
+    const double* TD;               // TD[(i*norb+a)*norb+j] = (ia|jj) - (ij|ja), rounded once
     // fixed-point copies for exact integer accumulation of H_xx (value = int * dscale):
     // hfx[p] = h_pp, JKfx[p][q] = J_pq - K_pq (same spin), Jfx[p][q] = J_pq (opposite spin)
     const long long* hfx;
@@ -75,7 +75,7 @@ struct nqs_problem {
     ProblemDev d;
     int device;
     double ecore;
-    double *h, *eri, *J, *K, *TJ, *TK;
+    double *h, *eri, *J, *K, *TJ, *TD;
     long long* fx;  // hfx | JKfx | Jfx
     long long* bt;  // Dt | Xt | Yt
     cudaMemPool_t pool;  // library-owned stream-ordered pool for per-call scratch

@@ -78,13 +78,14 @@ void nqs_scratch_free(nqs_problem* p, void* ptr, cudaStream_t s) {
 // ------------------------------------------------------------------------------------------
 // problem create / destroy
 // ------------------------------------------------------------------------------------------
-__global__ void k_tables(int n, const double* eri, double* J, double* K, double* TJ, double* TK) {
+__global__ void k_tables(int n, const double* eri, double* J, double* K, double* TJ, double* TD) {
     int64_t total = (int64_t)n * n * n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         int j = (int)(t % n), a = (int)((t / n) % n), i = (int)(t / ((int64_t)n * n));
         TJ[t] = eri[(((size_t)i * n + a) * n + j) * n + j];   // (ia|jj)
-        TK[t] = eri[(((size_t)i * n + j) * n + j) * n + a];   // (ij|ja)
+        // (ia|jj) - (ij|ja): the same-spin term of a single's element, rounded once here
+        TD[t] = __dsub_rn(TJ[t], eri[(((size_t)i * n + j) * n + j) * n + a]);
         if (a == 0) {
             J[i * n + j] = eri[(((size_t)i * n + i) * n + j) * n + j];  // (ii|jj)
             K[i * n + j] = eri[(((size_t)i * n + j) * n + j) * n + i];  // (ij|ji)
@@ -157,14 +158,14 @@ extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double*
     };
     if (cudaMalloc(&p->h, n2 * 8) != cudaSuccess || cudaMalloc(&p->eri, n4 * 8) != cudaSuccess ||
         cudaMalloc(&p->J, n2 * 8) != cudaSuccess || cudaMalloc(&p->K, n2 * 8) != cudaSuccess ||
-        cudaMalloc(&p->TJ, n3 * 8) != cudaSuccess || cudaMalloc(&p->TK, n3 * 8) != cudaSuccess) {
+        cudaMalloc(&p->TJ, n3 * 8) != cudaSuccess || cudaMalloc(&p->TD, n3 * 8) != cudaSuccess) {
         cudaGetLastError();
         return fail(NQS_ERR_OOM);
     }
     if (cudaMemcpy(p->h, h, n2 * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->eri, eri, n4 * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(NQS_ERR_CUDA);
-    k_tables<<<grid_for((int64_t)n3, 256), 256>>>(norb, p->eri, p->J, p->K, p->TJ, p->TK);
+    k_tables<<<grid_for((int64_t)n3, 256), 256>>>(norb, p->eri, p->J, p->K, p->TJ, p->TD);
     nqs_note_launch();
     if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
         return fail(NQS_ERR_CUDA);
@@ -203,7 +204,7 @@ extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double*
     d.J = p->J;
     d.K = p->K;
     d.TJ = p->TJ;
-    d.TK = p->TK;
+    d.TD = p->TD;
     if (d.nexc >= ((int64_t)1 << 31)) return fail(NQS_ERR_NORB);
     // Fixed-point tables for the diagonal: every partial sum of H_xx is bounded by
     // bound = sum_p |h_pp| + sum_{p<q} |J_pq - K_pq| * 2 + sum_{p,q} |J_pq|, so with
@@ -279,7 +280,7 @@ extern "C" int nqs_problem_destroy(nqs_problem* p) {
     cudaFree(p->J);
     cudaFree(p->K);
     cudaFree(p->TJ);
-    cudaFree(p->TK);
+    cudaFree(p->TD);
     cudaFree(p->err_word);
     cudaFree(p->fx);
     cudaFree(p->bt);

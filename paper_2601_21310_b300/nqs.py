@@ -99,6 +99,8 @@ EXPORTS = {
     "nqs_batch_capture": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nqs_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "nqs_batch_destroy": (C.c_int, [C.c_void_p]),
+    "nqs_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "nqs_batch_get_mode": (C.c_int, [C.c_void_p]),
     "nqs_set_autotune": (C.c_int, [C.c_int]),
     "nqs_autotune_entries": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "nqs_gemm_bf16": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_int,
@@ -547,11 +549,16 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
     return C_
 
 
-class Batch:
-    """nqs_batch: many independent E_S + gradient evaluations run concurrently, optionally as
-    one CUDA graph. items: list of (problem, net, csr, dets, out[4], grad) tuples."""
+BATCH_STREAMS, BATCH_GROUPED = 0, 1
 
-    def __init__(self, items, nstreams: int = 16):
+
+class Batch:
+    """nqs_batch: many independent E_S + gradient evaluations, either one launch per pipeline
+    stage over all problems (BATCH_GROUPED, the default when the batch qualifies) or the
+    problems' own pipelines on side streams (BATCH_STREAMS), optionally recorded as one CUDA
+    graph. items: list of (problem, net, csr, dets, out[4], grad) tuples."""
+
+    def __init__(self, items, nstreams: int = 16, mode: int | None = None):
         self.items = items  # keeps every referenced object alive
         n = len(items)
         P = (C.c_void_p * n)(*[it[0].handle.value for it in items])
@@ -565,6 +572,15 @@ class Batch:
         _check(lib().nqs_batch_create(n, P, Nt, csrs, D, nS, O, G, nstreams, C.byref(h)),
                "nqs_batch_create")
         self.handle = h
+        if mode is not None:
+            self.set_mode(mode)
+
+    def set_mode(self, mode: int):
+        _check(lib().nqs_batch_set_mode(self.handle, int(mode)), "nqs_batch_set_mode")
+
+    @property
+    def mode(self) -> int:
+        return lib().nqs_batch_get_mode(self.handle)
 
     def run(self, stream=None):
         _check(lib().nqs_batch_run(self.handle, _stream(stream)), "nqs_batch_run")
