@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             }
             keep(take, ex.a2, ex.b2, m);
         }
-        tested += nsing;
+        if (!APPEND) tested += nsing;
         // doubles: three groups of hole pairs; each lane tests the head of one list
         for (int grp = 0; grp < 3; ++grp) {
             const int npairs = grp == 0 ? (int)choose2(P.na)
@@ -400,15 +400,24 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                     const int hi = __shfl_sync(FULL_MASK, i, src);
                     const int hj = __shfl_sync(FULL_MASK, j, src);
                     const int64_t hb = __shfl_sync(FULL_MASK, base, src);
+                    // software-pipelined walk: the next 32 entries are loaded before this
+                    // chunk's candidates are probed, so the two L2 round trips overlap
+                    double tv = lane < L ? __ldg(&T.val[hb + lane]) : 0.0;
+                    uint16_t cd = lane < L ? __ldg(&T.code[hb + lane]) : (uint16_t)0;
                     for (int c0 = 0; c0 < L; c0 += 32) {
                         const int t = c0 + lane;
-                        bool pass = false, take = false;
+                        bool take = false;
                         uint64_t a2 = 0, b2 = 0;
                         double m = 0.0;
-                        if (t < L) {
-                            const double tv = __ldg(&T.val[hb + t]);
-                            pass = cut.pass(tv);
-                            const uint16_t cd = __ldg(&T.code[hb + t]);
+                        const bool pass = t < L && cut.pass(tv);
+                        const unsigned stop = __ballot_sync(FULL_MASK, !pass);
+                        double tvn = 0.0;
+                        uint16_t cdn = 0;
+                        if (!stop && t + 32 < L) {
+                            tvn = __ldg(&T.val[hb + t + 32]);
+                            cdn = __ldg(&T.code[hb + t + 32]);
+                        }
+                        {
                             const int a = cd & 0xff, b = cd >> 8;
                             if (pass) {
                                 bool valid = false;
@@ -435,9 +444,10 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                             }
                         }
                         keep(take, a2, b2, m);
-                        const unsigned stop = __ballot_sync(FULL_MASK, !pass);
-                        tested += stop ? (unsigned)(__ffs(stop) - 1) : 32u;
+                        if (!APPEND) tested += stop ? (unsigned)(__ffs(stop) - 1) : 32u;
                         if (stop) break;  // sorted: every later entry fails too
+                        tv = tvn;
+                        cd = cdn;
                     }
                 }
             }
