@@ -70,7 +70,8 @@ typedef struct nqs_net nqs_net;         /* opaque: refers to caller-owned device
 typedef struct {
     int precision;      /* NQS_FP64 or NQS_MIXED (must match the net's dtype) */
     int buckets;        /* PT2 hash buckets, >= 1 (more buckets = less scratch memory) */
-    int64_t chunk;      /* PT2 cap on emitted (key, value) pairs held at once; 0 = automatic */
+    int64_t chunk;      /* PT2 cap on emitted (key, value) pairs per sorted bucket, and on the
+                           slots of a hashed pass's table; 0 = automatic (from free memory) */
     int validate;       /* 1: check that S is sorted, unique and has the right popcounts */
     int internal_pt2;   /* 1: also compute the internal (x in S) PT2 term */
     double eps_pt2;     /* PT2 screening (Sec. 3.3 criterion per contribution): 0 = the full
@@ -240,7 +241,13 @@ int nqs_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr, cons
  * screened perturbative set P) only the contributions with |H_x'y psi_y| >= eps_pt2 to x' outside
  * S are emitted, found by the sorted-integral walk of nqs_hb_select; c(x') sums those, P is the
  * x' that receive at least one, and the internal term takes H_SS psi exactly from the connected
- * sets of S. The screened runs are summed exactly in 128-bit fixed point (each term rounded
+ * sets of S. Unscreened with opts->buckets = 0, when sorted buckets would traverse the connected
+ * space more than eight times (their pairs do not fit in memory, or opts->chunk caps them), the
+ * work runs in hashed passes instead: a pass takes a range of 256 fine buckets
+ * (det_hash mod 256) sized to memory from the measured ratio of unique to emitted, accumulates
+ * every emission of that range into a hash table of configurations in exact 128-bit fixed point
+ * (one slot per unique x'), then sorts and reduces the unique set; out[4] then counts passes.
+ * The screened runs are summed exactly in 128-bit fixed point (each term rounded
  * once to a grid far below FP64 resolution, one rounding to FP64 per x'), so c(x') does not
  * depend on the order of its terms; with opts->buckets = 0 the screened emissions are then
  * written in one traversal (appended in timing order; buffers sized from a counted sample of S

@@ -110,3 +110,38 @@ __device__ __forceinline__ int fx_scale(double vmax, double run_max) {
     frexp(b, &k);  // b < 2^k
     return 125 - k;
 }
+
+// ------------------------------------------------------------------------------------------
+// Accumulation into a hash table of configurations (PT2 over a connected space too large to
+// sort at once): a slot holds the key (a, b) and an Fx128 sum; keys are claimed with a 128-bit
+// compare-and-swap and sums added with 64-bit atomics (the low word's carry passed to the high
+// word), so every slot ends with the exact sum of its terms in any order of arrival.
+// ------------------------------------------------------------------------------------------
+struct __align__(32) FxSlot {
+    unsigned long long a, b;    // key; a = b = ~0 marks an empty slot
+    unsigned long long lo, hi;  // Fx128 sum
+};
+
+#define FX_EMPTY 0xffffffffffffffffull
+
+// 128-bit compare-and-swap of the slot's key: returns the key found (the empty key when this
+// thread claimed the slot)
+__device__ __forceinline__ void fx_cas_key(FxSlot* s, unsigned long long a, unsigned long long b,
+                                           unsigned long long& oa, unsigned long long& ob) {
+    asm volatile(
+        "{\n\t.reg .b128 cmp, val, old;\n\t"
+        "mov.b128 cmp, {%2, %3};\n\t"
+        "mov.b128 val, {%4, %5};\n\t"
+        "atom.global.cas.b128 old, [%6], cmp, val;\n\t"
+        "mov.b128 {%0, %1}, old;\n\t}"
+        : "=l"(oa), "=l"(ob)
+        : "l"(FX_EMPTY), "l"(FX_EMPTY), "l"(a), "l"(b), "l"(s)
+        : "memory");
+}
+
+__device__ __forceinline__ void fx_atomic_add(FxSlot* s, Fx128 v) {
+    const unsigned long long old = atomicAdd(&s->lo, v.lo);
+    const unsigned long long carry = (old + v.lo < old) ? 1ull : 0ull;
+    const unsigned long long h = v.hi + carry;
+    if (h) atomicAdd(&s->hi, h);
+}

@@ -111,8 +111,11 @@ struct Scratch {
     Scratch(nqs_problem* p_, cudaStream_t s_) : p(p_), s(s_) {}
     Scratch(void* arena_, size_t size_, cudaStream_t s_)
         : p(nullptr), s(s_), arena((uint8_t*)arena_), arena_size(size_) {}
-    ~Scratch() {
+    ~Scratch() { release(); }
+    // return every block taken so far (stream-ordered); the holder can be used again
+    void release() {
         for (int i = n - 1; i >= 0; --i) nqs_scratch_free(p, ptrs[i], s);
+        n = 0;
     }
     template <class T>
     int get(T** out, size_t count) {

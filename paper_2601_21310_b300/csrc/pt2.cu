@@ -790,6 +790,165 @@ __global__ void k_pt2_internal(ProblemDev P, const ulonglong2* __restrict__ S,
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// PT2 over a connected space whose unique set does not fit in device memory (hashed passes).
+// Fine buckets fb(x') = det_hash(x') mod FB; a pass takes a contiguous range of fine buckets and
+// accumulates every emission (x', H_x'y psi_y) of that range into a hash table of
+// configurations in exact 128-bit fixed point (FxSlot: 128-bit CAS for the key, 64-bit atomics
+// for the sum), so the table holds one slot per unique x' instead of one entry per emitted
+// pair and the connected space is traversed once per pass. The table is then compacted, the
+// unique keys sorted, and the sums reduced as any bucket is.
+// ------------------------------------------------------------------------------------------
+#define PT_FB 256
+#define PT_HASHED_MIN_BUCKETS 8  // sorted buckets above which the hashed passes are used
+
+// emitted pairs per fine bucket: per-warp shared-memory histograms over all of the warp's
+// configurations, added to tot[PT_FB] at the end
+__global__ void __launch_bounds__(PT_THREADS) k_pt2_fine_totals(ProblemDev P,
+                                                                 const ulonglong2* __restrict__ S,
+                                                                 int64_t nS,
+                                                                 unsigned long long* __restrict__ tot) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    uint32_t* hist = (uint32_t*)(smem + pair_table_bytes(P) + PT_WARPS * sizeof(DetCtx)) +
+                     (threadIdx.x >> 5) * PT_FB;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nexc = (uint32_t)P.nexc;
+    const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                   o4 = o3 + (uint32_t)P.dBB;
+    for (uint32_t k = lane; k < PT_FB; k += 32) hist[k] = 0;
+    __syncwarp();
+    for (int64_t det = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * PT_WARPS) {
+        ulonglong2 x = S[det];
+        fill_ctx(P, x.x, x.y, ctx, lane);  // ends with __syncwarp
+        EnumPos q;
+        q.cls = -1;
+        for (uint32_t e = lane; e < nexc; e += 32) {
+            uint64_t a2, b2;
+            step_key(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, a2, b2);
+            atomicAdd(&hist[det_hash(a2, b2) % PT_FB], 1u);
+        }
+        __syncwarp();
+    }
+    for (uint32_t k = lane; k < PT_FB; k += 32)
+        if (hist[k]) atomicAdd(&tot[k], (unsigned long long)hist[k]);
+}
+
+__global__ void k_fx_table_clear(FxSlot* __restrict__ t, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        t[i] = FxSlot{FX_EMPTY, FX_EMPTY, 0ull, 0ull};
+}
+
+// The emissions of the fine buckets [lo, hi) into the table (capacity mask + 1): only the key is
+// decoded for every excitation; in-range ones are queued per warp and, 32 at a time, fully
+// decoded, evaluated (H_x'y psi_y in FP64, as the emission kernels do), converted to fixed
+// point on the grid 2^-F and added. A key that finds no slot within FX_PROBES probes sets
+// *overflow (the pass is then repeated on a smaller range).
+#define FX_PROBES 4096
+__global__ void __launch_bounds__(PT_THREADS, 4) k_pt2_insert(ProblemDev P,
+                                                            const ulonglong2* __restrict__ S,
+                                                            const double* __restrict__ psi,
+                                                            int64_t nS, uint32_t lo, uint32_t hi,
+                                                            FxSlot* __restrict__ tab,
+                                                            uint64_t mask, int F,
+                                                            int* __restrict__ overflow) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    PairTables T = setup_pair_tables(P, (uint16_t*)smem);
+    DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
+    __shared__ uint32_t queue[PT_WARPS * 64];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    const uint32_t nexc = (uint32_t)P.nexc;
+    const uint32_t o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
+                   o4 = o3 + (uint32_t)P.dBB;
+    uint32_t* q = queue + (threadIdx.x >> 5) * 64;
+    for (int64_t det = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); det < nS;
+         det += (int64_t)gridDim.x * PT_WARPS) {
+        const ulonglong2 x = S[det];
+        fill_ctx(P, x.x, x.y, ctx, lane);
+        const double py = psi[det];
+        // one batch of up to 32 queued excitations: decode, evaluate, add into the table
+        auto insert_batch = [&](uint32_t nt) {
+            if ((uint32_t)lane < nt) {
+                Exc ex;
+                decode_exc(P, T, *ctx, x.x, x.y, q[lane], ex);
+                const Fx128 v = fx_from_double(__dmul_rn(exc_element(P, *ctx, ex), py), F);
+                uint64_t slot = hash_slot(s_hash(ex.a2, ex.b2), mask);
+                bool done = false;
+                for (int it = 0; it < FX_PROBES && !done; ++it) {
+                    unsigned long long oa, ob;
+                    fx_cas_key(tab + slot, ex.a2, ex.b2, oa, ob);
+                    if ((oa == FX_EMPTY && ob == FX_EMPTY) || (oa == ex.a2 && ob == ex.b2)) {
+                        fx_atomic_add(tab + slot, v);
+                        done = true;
+                    } else {
+                        slot = (slot + 1) & mask;
+                    }
+                }
+                if (!done) atomicOr(overflow, 1);
+            }
+        };
+        uint32_t qn = 0;
+        EnumPos pos;
+        pos.cls = -1;
+        for (uint32_t r0 = 0; r0 < nexc; r0 += 32) {
+            const uint32_t e = r0 + lane;
+            bool take = false;
+            if (e < nexc) {
+                uint64_t a2, b2;
+                step_key(P, T, *ctx, x.x, x.y, e, o2, o3, o4, pos, a2, b2);
+                const uint32_t fb = (uint32_t)(det_hash(a2, b2) % PT_FB);
+                take = fb >= lo && fb < hi;
+            }
+            const unsigned m = __ballot_sync(FULL_MASK, take);
+            if (take) q[qn + __popc(m & lt)] = e;
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                insert_batch(32);
+                const uint32_t rest = qn - 32;
+                const uint32_t moved = (uint32_t)lane < rest ? q[32 + lane] : 0u;
+                __syncwarp();
+                if ((uint32_t)lane < rest) q[lane] = moved;
+                qn = rest;
+                __syncwarp();
+            }
+        }
+        if (qn > 0) insert_batch(qn);
+        __syncwarp();  // the queue and the context are rewritten for the next configuration
+    }
+}
+
+// occupied slots -> (packed key, c(x')) in an order that depends on timing (sorted afterwards)
+template <class K>
+__global__ void k_fx_table_compact(const FxSlot* __restrict__ t, uint64_t n, int F, int norb,
+                                   K* __restrict__ keys, double* __restrict__ vals,
+                                   unsigned long long* __restrict__ cursor, uint64_t cap) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~(uint64_t)31; i0 < n;
+         i0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = i0 + lane;
+        FxSlot sl = FxSlot{FX_EMPTY, FX_EMPTY, 0ull, 0ull};
+        if (i < n) sl = t[i];
+        const bool occ = !(sl.a == FX_EMPTY && sl.b == FX_EMPTY);
+        const unsigned m = __ballot_sync(FULL_MASK, occ);
+        unsigned long long base = 0;
+        if (lane == 0 && m) base = atomicAdd(cursor, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL_MASK, base, 0);
+        if (occ) {
+            const uint64_t p = base + __popc(m & lt);
+            if (p < cap) {
+                keys[p] = key_make<K>(sl.a, sl.b, norb);
+                vals[p] = fx_to_double(Fx128{sl.lo, sl.hi}, F);
+            }
+        }
+    }
+}
+
 // the emission kernels also hold each warp's alpha-beta tables
 static size_t pt_smem_emit(const ProblemDev& P) {
     return pair_table_bytes(P) + PT_WARPS * (sizeof(DetCtx) + ab_tab_bytes(P));
@@ -1038,6 +1197,140 @@ static int pt2_resident(nqs_problem* p, const uint64_t* dets, const double* psi,
     return NQS_OK;
 }
 
+// Hashed passes over the fine buckets (see k_pt2_insert): each pass takes the next range of fine
+// buckets whose estimated unique count fits the table (unique / emitted ratio: 0.3 until a pass
+// has measured it, then the largest seen x 1.15), accumulates its emissions in the table,
+// compacts and sorts the unique keys and reduces them (runs of one: the sums are final), adding
+// the pass's external sum into dev_scalars[1 + 2 pass]. A pass whose table overflows is
+// repeated on half its range. *passes and *total_emitted receive the pass count and the
+// number of emitted pairs.
+template <class K>
+static int pt2_hashed(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                      Pt2Ctx& cx, double* dev_scalars, unsigned long long* next_dev,
+                      int64_t nslots, double avail, int64_t chunk, int* passes,
+                      int64_t* total_emitted, cudaStream_t s) {
+    const ProblemDev& P = p->d;
+    Scratch sc(p, s);
+    // emitted pairs per fine bucket
+    unsigned long long* tot_dev;
+    NQS_TRY(sc.get(&tot_dev, PT_FB));
+    NQS_CK(cudaMemsetAsync(tot_dev, 0, PT_FB * sizeof(unsigned long long), s));
+    const size_t smem_t = pt_smem(P) + (size_t)PT_WARPS * PT_FB * sizeof(uint32_t);
+    if (smem_t > 48 * 1024)
+        NQS_CK(cudaFuncSetAttribute(k_pt2_fine_totals, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_t));
+    {
+        ProfScope prof_(PROF_PT2_COUNT, s);
+        k_pt2_fine_totals<<<pt_grid(nS), PT_THREADS, smem_t, s>>>(P, (const ulonglong2*)dets, nS,
+                                                                  tot_dev);
+    }
+    NQS_CK_LAUNCH();
+    std::vector<unsigned long long> tot(PT_FB);
+    unsigned long long vbits = 0;
+    NQS_CK(cudaMemcpyAsync(tot.data(), tot_dev, PT_FB * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaMemcpyAsync(&vbits, cx.vmax_bits, sizeof vbits, cudaMemcpyDeviceToHost, s));
+    NQS_CK(cudaStreamSynchronize(s));
+    // the fixed-point grid (as k_seg_sum_fx chooses it)
+    double vmax;
+    memcpy(&vmax, &vbits, sizeof vmax);
+    vmax *= P.hoff_max * (1.0 + 1e-15);
+    int F = 100;
+    if (vmax > 0.0 && vmax < 1e300) {
+        int k;
+        frexp(vmax * cx.run_max, &k);
+        F = 125 - k;
+    }
+    // table capacity: the table (32 B per slot) and the compacted keys (key + value per unique,
+    // 0.75 per slot) during compaction; then key and value twice for the sort plus the per-unique
+    // arrays of the reduction (key + 16 B), at most 0.75 of the slots
+    const double kb = (double)sizeof(K);
+    const double per_slot = fmax(32.0 + 0.75 * (kb + 8.0), 0.75 * (3.0 * kb + 32.0));
+    double cmax = 0.8 * avail / per_slot;
+    if (chunk > 0 && (double)chunk < cmax) cmax = (double)chunk;  // the caller's cap
+    uint64_t C = 1024;
+    while ((double)(C * 2) <= cmax) C *= 2;
+    const double ucap = 0.75 * (double)C;
+    const size_t smem_i = pt_smem(P);
+    if (smem_i > 48 * 1024)
+        NQS_CK(cudaFuncSetAttribute(k_pt2_insert, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_i));
+    double ratio = 0.3;
+    int pass = 0;
+    *total_emitted = 0;
+    uint32_t lo = 0;
+    while (lo < PT_FB) {
+        // the next range: fine buckets while the estimated unique count fits
+        uint32_t hi = lo;
+        double pairs = 0.0;
+        while (hi < PT_FB && (hi == lo || (pairs + (double)tot[hi]) * ratio <= ucap)) {
+            pairs += (double)tot[hi];
+            ++hi;
+        }
+        if (pass >= nslots) {
+            nqs_record_message("nqs_pt2: more hashed passes than result slots");
+            return NQS_ERR_UNSUPPORTED;
+        }
+        Scratch ps(p, s);
+        FxSlot* tab;
+        int* ovf;
+        unsigned long long* cur;
+        NQS_TRY(ps.get(&tab, C));
+        NQS_TRY(ps.get(&ovf, 1));
+        NQS_TRY(ps.get(&cur, 1));
+        k_fx_table_clear<<<grid_for((int64_t)C, 256), 256, 0, s>>>(tab, C);
+        NQS_CK_LAUNCH();
+        NQS_CK(cudaMemsetAsync(ovf, 0, sizeof(int), s));
+        NQS_CK(cudaMemsetAsync(cur, 0, sizeof(unsigned long long), s));
+        {
+            ProfScope prof_(PROF_PT2_EMIT, s);
+            k_pt2_insert<<<pt_grid(nS), PT_THREADS, smem_i, s>>>(P, (const ulonglong2*)dets, psi, nS,
+                                                                 lo, hi, tab, C - 1, F, ovf);
+        }
+        NQS_CK_LAUNCH();
+        int ovh = 0;
+        NQS_CK(cudaMemcpyAsync(&ovh, ovf, sizeof ovh, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+        if (ovh) {
+            if (hi - lo == 1) {
+                nqs_record_message("nqs_pt2: one fine bucket's unique set exceeds the table");
+                return NQS_ERR_OOM;
+            }
+            ratio *= 2.0;  // plan again on a smaller range
+            continue;
+        }
+        // compact into arrays of the table's occupancy bound, then free the table
+        const uint64_t ucapn = (uint64_t)ucap + 1024;
+        K *keys, *keys2;
+        double *vals, *vals2;
+        Scratch rs(p, s);
+        NQS_TRY(rs.get(&keys, ucapn));
+        NQS_TRY(rs.get(&vals, ucapn));
+        k_fx_table_compact<K><<<grid_for((int64_t)C, 256), 256, 0, s>>>(tab, C, F, P.norb, keys,
+                                                                          vals, cur, ucapn);
+        NQS_CK_LAUNCH();
+        unsigned long long nu = 0;
+        NQS_CK(cudaMemcpyAsync(&nu, cur, sizeof nu, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+        if (nu > ucapn) {  // fuller than planned: everything is in the table, but not compacted
+            ratio = fmax(ratio * 2.0, (double)nu / fmax(pairs, 1.0) * 1.15);
+            continue;
+        }
+        ps.release();  // the table: its memory serves the sort
+        NQS_TRY(rs.get(&keys2, nu));
+        NQS_TRY(rs.get(&vals2, nu));
+        NQS_TRY(pt2_reduce<K>(p, keys, vals, keys2, vals2, (int64_t)nu, cx,
+                              dev_scalars + 1 + 2 * pass, next_dev + pass, s));
+        NQS_CK(cudaMemsetAsync(dev_scalars + 2 + 2 * pass, 0, sizeof(double), s));
+        *total_emitted += (int64_t)pairs;
+        ratio = fmax(pass == 0 ? 0.0 : ratio / 1.15, (double)nu / fmax(pairs, 1.0)) * 1.15;
+        ++pass;
+        lo = hi;
+    }
+    *passes = pass;
+    return NQS_OK;
+}
+
 // optional output of nqs_pt2_unique: the external unique set of one bucket
 struct UniqReq {
     int64_t bucket;
@@ -1140,6 +1433,7 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
         return NQS_OK;
     };
 
+    bool hashed = false;
     if (!screened && B <= 0) {
         // automatic: enough buckets that one bucket's pairs (keys and values twice, plus 8 bytes
         // per pair toward the per-unique arrays) use at most half of the free device memory,
@@ -1148,8 +1442,13 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
         NQS_TRY(avail_bytes(&av));
         double capb = 0.5 * av / (2.0 * (kb + 8.0) + 8.0);
         if (capb > 2147483647.0) capb = 2147483647.0;
+        if (opts->chunk > 0 && (double)opts->chunk < capb) capb = (double)opts->chunk;
         B = (int64_t)ceil((double)nS * (double)P.nexc / capb);
         if (B < 1) B = 1;
+        // when the sorted buckets would traverse the connected space many times, accumulate
+        // into hash tables of unique configurations instead (one traversal per pass, memory per
+        // unique x' rather than per emitted pair)
+        hashed = B > PT_HASHED_MIN_BUCKETS && !uq;
     }
     // per-bucket slots: the bucket count is known here, except for the automatic screened form
     // (one bucket unless its single traversal overflows; at most 1024 then)
@@ -1190,6 +1489,23 @@ static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int
 
     int64_t total_emitted = 0;
     bool done = false;
+    if (hashed) {
+        double av = 0;
+        NQS_TRY(avail_bytes(&av));
+        int passes = 0;
+        int st = kbits <= 32 ? pt2_hashed<uint32_t>(p, dets, psi, nS, cx, dev_scalars, next_dev,
+                                                    nslots, av, opts->chunk, &passes, &total_emitted, s)
+               : kbits <= 64 ? pt2_hashed<uint64_t>(p, dets, psi, nS, cx, dev_scalars, next_dev,
+                                                    nslots, av, opts->chunk, &passes, &total_emitted, s)
+                             : pt2_hashed<Key128>(p, dets, psi, nS, cx, dev_scalars, next_dev,
+                                                  nslots, av, opts->chunk, &passes, &total_emitted, s);
+        NQS_TRY(st);
+        B = passes;
+        // the internal term over all of S once every pass has filled its c(x) of S
+        NQS_TRY(pt2_internal_bucket(p, dets, psi, cS, nS, dev_scalars, E_var, 1, 0, eint,
+                                    opts->internal_pt2 != 0, s));
+        done = true;
+    }
     if (screened && B <= 0) {
         // automatic: one traversal appending into buffers sized from a counted sample of S
         // (every stride-th configuration, x1.5 + 2^16), at most what memory allows (pairs, sort

@@ -311,3 +311,36 @@ def test_pt2_mixed_form_vs_quantised_oracle():
     r0 = O.pt2(16, p.h, p.eri, p.S, psi_g, E, 8, 0)
     assert abs(got["partials"][0, 1] - r0["int"]) <= 1e-9 * abs(r0["int"])
     assert abs(got["partials"][0, 0] - r0["ext"]) <= 1e-10 * abs(r0["ext"])
+
+
+@pytest.mark.parametrize("name,chunk", [("tiny_n10", 8192), ("small_n16", 4_000_000)])
+def test_pt2_hashed_passes_match(name, chunk):
+    """PT2 over all of C minus S in hashed passes: with opts.buckets = 0 and a pair cap small
+    enough that sorted buckets would traverse the connected space more than eight times, each
+    pass accumulates the emissions of a range of fine buckets into a hash table of
+    configurations in exact fixed point (several passes here). The unique count, the emitted
+    count and both terms equal the single-bucket pipeline's, and the oracle's on tiny_n10."""
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem(name)
+    P = problem_for(N, p)
+    if name == "tiny_n10":
+        psi, E = _psi_E(p)
+    else:
+        psi = np.random.default_rng(11).normal(size=len(p.S))
+        E = -20.0
+    d, ps = to_dev(p.S), torch.from_numpy(psi).cuda()
+    one = N.pt2(P, d, ps, E, buckets=1)
+    hashed = N.pt2(P, d, ps, E, o=N.opts(buckets=0, chunk=chunk))
+    assert hashed["buckets"] > 1 and hashed["partials"] is None
+    assert hashed["n_unique"] == one["n_unique"]
+    assert hashed["n_emitted"] == one["n_emitted"] == len(p.S) * O.n_excitations(
+        p.wl.norb, p.wl.nalpha, p.wl.nbeta)
+    assert abs(hashed["ext"] - one["ext"]) <= 1e-12 * max(1.0, abs(one["ext"]))
+    assert abs(hashed["int"] - one["int"]) <= 1e-12 * max(1.0, abs(one["int"]))
+    if name == "tiny_n10":
+        ref = O.pt2(10, p.h, p.eri, p.S, psi, E)
+        assert hashed["n_unique"] == ref["n_unique"]
+        assert abs(hashed["ext"] - ref["ext"]) < 1e-12 and abs(hashed["int"] - ref["int"]) < 1e-12
+    again = N.pt2(P, d, ps, E, o=N.opts(buckets=0, chunk=chunk))
+    assert again["ext"] == hashed["ext"] and again["int"] == hashed["int"]  # deterministic
