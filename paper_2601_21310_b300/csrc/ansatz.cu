@@ -1479,33 +1479,39 @@ int g_adjoint(const GProb* P, const GDims& d, cudaStream_t s) {
     return NQS_OK;
 }
 
-// dPhiT [nout][ldM] = dPhi^T, 32 x 32 tiles through shared memory (blockIdx.z = problem)
-__global__ void k_g_transpose_dphi(const GProb* __restrict__ Pv) {
-    const GProb& P = Pv[blockIdx.z];
+// dPhiT [nout][ldM] = dPhi^T, 32 x 32 tiles through shared memory, one block per tile over the
+// work list of every problem's tiles (tile_off: prefix of ceil(M/32) ceil(nout/32) per problem)
+__global__ void k_g_transpose_dphi(const GProb* __restrict__ Pv, const int64_t* __restrict__ tile_off,
+                                   int np) {
     __shared__ unsigned short tile[32][33];
+    const int64_t t = blockIdx.x;
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_off[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const GProb& P = Pv[lo];
+    const int64_t local = t - tile_off[lo];
+    const int64_t tc = (P.nout + 31) / 32;
+    const int64_t r0 = (local / tc) * 32, c0 = (local % tc) * 32;
     const unsigned short* S = (const unsigned short*)P.dPhi;
     unsigned short* D = (unsigned short*)P.dPhiT;
     const int64_t R = P.M, Cn = P.nout;
-    for (int64_t r0 = (int64_t)blockIdx.y * 32; r0 < R; r0 += (int64_t)gridDim.y * 32) {
-        const int64_t c0 = (int64_t)blockIdx.x * 32;
-        if (c0 >= Cn) return;
-        __syncthreads();
-        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-            const int64_t r = r0 + i, c = c0 + threadIdx.x;
-            tile[i][threadIdx.x] = (r < R && c < Cn) ? S[r * P.ldP + c] : (unsigned short)0;
-        }
-        __syncthreads();
-        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-            const int64_t c = c0 + i, r = r0 + threadIdx.x;
-            if (c < Cn && r < R) D[c * P.ldM + r] = tile[threadIdx.x][i];
-        }
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < R && c < Cn) ? S[r * P.ldP + c] : (unsigned short)0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (c < Cn && r < R) D[c * P.ldM + r] = tile[threadIdx.x][i];
     }
 }
 
-int g_transpose_dphi(const GProb* P, const GDims& d, cudaStream_t s) {
-    const unsigned gy = (unsigned)((d.maxM + 31) / 32 < 1024 ? (d.maxM + 31) / 32 : 1024);
-    k_g_transpose_dphi<<<dim3((unsigned)((d.max_nout + 31) / 32), gy, d.np), dim3(32, 8), 0, s>>>(
-        P);
+int g_transpose_dphi(const GProb* P, const GDims& d, const int64_t* tile_off, int64_t tiles,
+                     cudaStream_t s) {
+    k_g_transpose_dphi<<<(unsigned)tiles, dim3(32, 8), 0, s>>>(P, tile_off, d.np);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }

@@ -138,7 +138,9 @@ int g_bits_prep(const GProb* P, const GDims& d, cudaStream_t s);
 int g_lu(const GLuJob* jobs, int njobs, int n, int64_t maxM, cudaStream_t s);
 int g_combine(const GProb* P, const GDims& d, cudaStream_t s);
 int g_adjoint(const GProb* P, const GDims& d, cudaStream_t s);
-int g_transpose_dphi(const GProb* P, const GDims& d, cudaStream_t s);
+// tile_off: device [np + 1] prefix of each problem's 32 x 32 tiles of dPhi (tiles in all)
+int g_transpose_dphi(const GProb* P, const GDims& d, const int64_t* tile_off, int64_t tiles,
+                     cudaStream_t s);
 int g_bias_grads(const GProb* P, const GDims& d, cudaStream_t s);
 // energy.cu: max log|psi|, scaled psi, SpMV, compensated N and D (part: device
 // [np][2][256] partial sums), E and the adjoint weights

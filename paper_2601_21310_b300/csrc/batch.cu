@@ -31,6 +31,8 @@ struct GroupedState {
     std::vector<GProb> hP;
     GDims dims;
     double2* kpart = nullptr;
+    int64_t* tile_off = nullptr;  // prefix of the problems' dPhi transpose tiles
+    int64_t tiles = 0;
     bool with_grad = false;
     std::vector<int> lu_n;
     std::vector<GLuJob*> lu_jobs;
@@ -41,6 +43,7 @@ struct GroupedState {
         cudaFree(ws);
         cudaFree(dP);
         cudaFree(kpart);
+        cudaFree(tile_off);
         for (auto j : lu_jobs) cudaFree(j);
         for (auto t : sets) tc_group_set_destroy(t);
     }
@@ -352,6 +355,19 @@ static int grouped_prepare(nqs_batch* b, cudaStream_t s) {
     }
     if (cudaMemcpy(G->dP, G->hP.data(), sizeof(GProb) * n, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(NQS_ERR_CUDA);
+    {
+        std::vector<int64_t> toff(n + 1, 0);
+        for (int i = 0; i < n; ++i)
+            toff[i + 1] = toff[i] + ((G->hP[i].M + 31) / 32) * ((G->hP[i].nout + 31) / 32);
+        G->tiles = toff[n];
+        if (cudaMalloc(&G->tile_off, sizeof(int64_t) * (n + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NQS_ERR_OOM);
+        }
+        if (cudaMemcpy(G->tile_off, toff.data(), sizeof(int64_t) * (n + 1),
+                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(NQS_ERR_CUDA);
+    }
     // LU jobs by block size (both spins)
     std::map<int, std::vector<GLuJob>> byn;
     for (int i = 0; i < n; ++i) {
@@ -463,7 +479,7 @@ static int grouped_run(nqs_batch* b, cudaStream_t s) {
     NQS_TRY(g_energy(G->dP, d, G->kpart, s));
     if (!G->with_grad) return NQS_OK;
     NQS_TRY(g_adjoint(G->dP, d, s));
-    NQS_TRY(g_transpose_dphi(G->dP, d, s));
+    NQS_TRY(g_transpose_dphi(G->dP, d, G->tile_off, G->tiles, s));
     for (int k = 3; k < 6; ++k) NQS_TRY(tc_group_set_launch(G->sets[k], s));
     NQS_TRY(g_bias_grads(G->dP, d, s));
     return NQS_OK;
