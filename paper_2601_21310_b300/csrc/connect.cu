@@ -308,10 +308,14 @@ __device__ __forceinline__ uint32_t pair_pos(uint32_t r1, uint32_t r2, uint32_t 
     return r1 * (2 * n - r1 - 1) / 2 + (r2 - r1 - 1);
 }
 
+// S: the rows to resolve; R: the sorted set they are resolved against (the array the alpha
+// index's runs point into; R = S for H_SS, the sorted target set for the proxy Hamiltonian)
 __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P, HashS H,
                                                                  AlphaIdx X, BetaIdx Y,
                                                                  const ulonglong2* __restrict__ S,
-                                                                 int64_t nS, int64_t* rowcnt,
+                                                                 int64_t nS,
+                                                                 const ulonglong2* __restrict__ R,
+                                                                 int64_t* rowcnt,
                                                                  uint32_t* __restrict__ bits) {
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
                 bool hit = false;
                 uint32_t e = 0;
                 if (k < (uint32_t)own.y) {
-                    const uint64_t by = __ldg(&S[own.x + k].y);
+                    const uint64_t by = __ldg(&R[own.x + k].y);
                     const uint64_t d = by ^ x.y;
                     const int pc = __popcll(d);
                     if (pc == 2) {
@@ -456,7 +460,7 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
                 if (t < total) {
                     const uint32_t k = t - base;
                     if (so) {
-                        const uint64_t by = __ldg(&S[start + k].y);
+                        const uint64_t by = __ldg(&R[start + k].y);
                         const uint64_t d = by ^ x.y;
                         if (__popcll(d) == 2) {
                             const uint64_t jbit = x.y & d, bbit = by & d;
@@ -591,6 +595,142 @@ static unsigned conn_grid(int64_t nS) {
 size_t conn_smem_bytes(const ProblemDev& P) { return conn_smem(P); }
 unsigned conn_grid_size(int64_t nS) { return conn_grid(nS); }
 
+template <class K>
+__global__ void k_cfg_keys(const ulonglong2* __restrict__ in, int64_t n, int norb,
+                           K* __restrict__ keys, double* __restrict__ pad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const ulonglong2 x = in[i];
+        keys[i] = key_make<K>(x.x, x.y, norb);
+        pad[i] = 0.0;
+    }
+}
+
+template <class K>
+__global__ void k_cfg_unkeys(const K* __restrict__ keys, int64_t n, int norb,
+                             ulonglong2* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t a, b;
+        key_split(keys[i], norb, a, b);
+        out[i] = make_ulonglong2(a, b);
+    }
+}
+
+template <class K>
+static int sort_configs_k(nqs_problem* p, Scratch& sc, const uint64_t* in, int64_t n,
+                          uint64_t* out, cudaStream_t s) {
+    const int norb = p->d.norb;
+    K *keys, *keys2;
+    double *pad, *pad2;
+    NQS_TRY(sc.get(&keys, n));
+    NQS_TRY(sc.get(&keys2, n));
+    NQS_TRY(sc.get(&pad, n));
+    NQS_TRY(sc.get(&pad2, n));
+    k_cfg_keys<K><<<grid_for(n, 256), 256, 0, s>>>((const ulonglong2*)in, n, norb, keys, pad);
+    NQS_CK_LAUNCH();
+    int st;
+    if (sizeof(K) == 4)
+        st = radix_sort_pairs32(p, sc, (uint32_t*&)keys, pad, (uint32_t*&)keys2, pad2, n,
+                                2 * norb, s);
+    else if (sizeof(K) == 8)
+        st = radix_sort_pairs(p, sc, (uint64_t*&)keys, pad, (uint64_t*&)keys2, pad2, n,
+                              2 * norb, s);
+    else
+        st = radix_sort_pairs128(p, sc, (Key128*&)keys, pad, (Key128*&)keys2, pad2, n,
+                                 2 * norb, s);
+    if (st < 0) return st;
+    k_cfg_unkeys<K><<<grid_for(n, 256), 256, 0, s>>>(keys, n, norb, (ulonglong2*)out);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
+int sort_configs(nqs_problem* p, Scratch& sc, const uint64_t* in, int64_t n, uint64_t* out,
+                 cudaStream_t s) {
+    if (n <= 0) return NQS_OK;
+    const int norb = p->d.norb;
+    if (2 * norb <= 32) return sort_configs_k<uint32_t>(p, sc, in, n, out, s);
+    if (2 * norb <= 64) return sort_configs_k<uint64_t>(p, sc, in, n, out, s);
+    return sort_configs_k<Key128>(p, sc, in, n, out, s);
+}
+
+// The count pass over `rows` (nrows configurations) against the sorted, unique set R (nR
+// configurations, hashed in H; every row must be a member of R): the indices of R by alpha
+// string and by beta string, then k_conn_count_ab (k_conn_count when there are no alpha-beta
+// doubles). rowcnt [nrows] receives the row lengths (diagonal included) and bits
+// [nrows][ceil(nexc / 32)] the hit ballots.
+int conn_count_indexed(nqs_problem* p, Scratch& sc, const HashS& H, const uint64_t* rows,
+                       int64_t nrows, const uint64_t* Rset, int64_t nR, int64_t* rowcnt,
+                       uint32_t* bits, cudaStream_t s) {
+    const size_t smem = conn_smem(p->d);
+    if (smem > 48 * 1024) {
+        NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_conn_count_ab, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    }
+    // index of R by alpha string (runs of the sorted R), for the alpha-beta block of pass 1
+    const bool use_ab = p->d.dAB > 0;
+    AlphaIdx X;
+    memset(&X, 0, sizeof X);
+    if (use_ab) {
+        uint64_t cap = 1024;
+        while (cap < 2 * (uint64_t)nR) cap <<= 1;
+        uint64_t* akey;
+        int2* arun;
+        NQS_TRY(sc.get(&akey, cap));
+        NQS_TRY(sc.get(&arun, cap));
+        NQS_CK(cudaMemsetAsync(akey, 0, cap * sizeof(uint64_t), s));
+        k_alpha_index<<<grid_for(nR, 256), 256, 0, s>>>((const ulonglong2*)Rset, nR, akey, arun,
+                                                        cap - 1);
+        NQS_CK_LAUNCH();
+        X.key = akey;
+        X.run = arun;
+        X.mask = cap - 1;
+    }
+    // index of R by beta string, for the alpha singles and alpha-alpha doubles of pass 1
+    BetaIdx Y;
+    memset(&Y, 0, sizeof Y);
+    if (use_ab && p->d.nb >= 1 && p->d.mb >= 1) {
+        uint64_t cap = 1024;
+        while (cap < 2 * (uint64_t)nR) cap <<= 1;
+        uint64_t *bkey, *alist;
+        uint32_t *bcnt, *boff, *bfill;
+        NQS_TRY(sc.get(&bkey, cap));
+        NQS_TRY(sc.get(&bcnt, cap));
+        NQS_TRY(sc.get(&boff, cap));
+        NQS_TRY(sc.get(&bfill, cap));
+        NQS_TRY(sc.get(&alist, nR));
+        NQS_CK(cudaMemsetAsync(bkey, 0, cap * sizeof(uint64_t), s));
+        NQS_CK(cudaMemsetAsync(bcnt, 0, cap * sizeof(uint32_t), s));
+        NQS_CK(cudaMemsetAsync(bfill, 0, cap * sizeof(uint32_t), s));
+        k_beta_count<<<grid_for(nR, 256), 256, 0, s>>>((const ulonglong2*)Rset, nR, bkey, bcnt,
+                                                       cap - 1);
+        NQS_CK_LAUNCH();
+        NQS_TRY(scan_exclusive_u32(p, sc, bcnt, boff, (int64_t)cap, s));
+        k_beta_fill<<<grid_for(nR, 256), 256, 0, s>>>((const ulonglong2*)Rset, nR, bkey, boff,
+                                                      bfill, alist, cap - 1);
+        NQS_CK_LAUNCH();
+        Y.key = bkey;
+        Y.off = boff;
+        Y.cnt = bcnt;
+        Y.alist = alist;
+        Y.mask = cap - 1;
+    }
+    {
+        ProfScope prof_(PROF_CONN_COUNT, s);
+        if (use_ab)
+            k_conn_count_ab<<<conn_grid(nrows), CONN_THREADS, smem, s>>>(
+                p->d, H, X, Y, (const ulonglong2*)rows, nrows, (const ulonglong2*)Rset, rowcnt,
+                bits);
+        else
+            k_conn_count<<<conn_grid(nrows), CONN_THREADS, smem, s>>>(
+                p->d, H, (const ulonglong2*)rows, nrows, rowcnt, bits);
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
 extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
                                const nqs_opts* opts, nqs_csr* out, int64_t* n_enumerated,
                                nqs_stream_t stream) {
@@ -609,62 +749,9 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
     HashS H;
     NQS_TRY(hash_build(p, sc, dets, nS, &H, s));
     size_t smem = conn_smem(p->d);
-    if (smem > 48 * 1024) {
-        NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-        NQS_CK(cudaFuncSetAttribute(k_conn_count_ab, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+    if (smem > 48 * 1024)
         NQS_CK(cudaFuncSetAttribute(k_conn_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-    }
-    // index of S by alpha string (runs of the sorted S), for the alpha-beta block of pass 1
-    const bool use_ab = p->d.dAB > 0;
-    AlphaIdx X;
-    memset(&X, 0, sizeof X);
-    if (use_ab) {
-        uint64_t cap = 1024;
-        while (cap < 2 * (uint64_t)nS) cap <<= 1;
-        uint64_t* akey;
-        int2* arun;
-        NQS_TRY(sc.get(&akey, cap));
-        NQS_TRY(sc.get(&arun, cap));
-        NQS_CK(cudaMemsetAsync(akey, 0, cap * sizeof(uint64_t), s));
-        k_alpha_index<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, akey, arun,
-                                                        cap - 1);
-        NQS_CK_LAUNCH();
-        X.key = akey;
-        X.run = arun;
-        X.mask = cap - 1;
-    }
-    // index of S by beta string, for the alpha singles and alpha-alpha doubles of pass 1
-    BetaIdx Y;
-    memset(&Y, 0, sizeof Y);
-    if (use_ab && p->d.nb >= 1 && p->d.mb >= 1) {
-        uint64_t cap = 1024;
-        while (cap < 2 * (uint64_t)nS) cap <<= 1;
-        uint64_t *bkey, *alist;
-        uint32_t *bcnt, *boff, *bfill;
-        NQS_TRY(sc.get(&bkey, cap));
-        NQS_TRY(sc.get(&bcnt, cap));
-        NQS_TRY(sc.get(&boff, cap));
-        NQS_TRY(sc.get(&bfill, cap));
-        NQS_TRY(sc.get(&alist, nS));
-        NQS_CK(cudaMemsetAsync(bkey, 0, cap * sizeof(uint64_t), s));
-        NQS_CK(cudaMemsetAsync(bcnt, 0, cap * sizeof(uint32_t), s));
-        NQS_CK(cudaMemsetAsync(bfill, 0, cap * sizeof(uint32_t), s));
-        k_beta_count<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, bkey, bcnt,
-                                                       cap - 1);
-        NQS_CK_LAUNCH();
-        NQS_TRY(scan_exclusive_u32(p, sc, bcnt, boff, (int64_t)cap, s));
-        k_beta_fill<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, bkey, boff,
-                                                      bfill, alist, cap - 1);
-        NQS_CK_LAUNCH();
-        Y.key = bkey;
-        Y.off = boff;
-        Y.cnt = bcnt;
-        Y.alist = alist;
-        Y.mask = cap - 1;
-    }
     int64_t* rowcnt;
     NQS_TRY(sc.get(&rowcnt, nS));
     uint32_t* bits;
@@ -677,18 +764,9 @@ extern "C" int nqs_connections(nqs_problem* p, const uint64_t* dets, int64_t nS,
         nqs_scratch_free(p, row_ptr, s);
         return code;
     };
-    {
-        ProfScope prof_(PROF_CONN_COUNT, s);
-        if (use_ab)
-            k_conn_count_ab<<<conn_grid(nS), CONN_THREADS, smem, s>>>(
-                p->d, H, X, Y, (const ulonglong2*)dets, nS, rowcnt, bits);
-        else
-            k_conn_count<<<conn_grid(nS), CONN_THREADS, smem, s>>>(
-                p->d, H, (const ulonglong2*)dets, nS, rowcnt, bits);
-    }
-    nqs_note_launch();
-    if (cudaGetLastError() != cudaSuccess) return fail(NQS_ERR_CUDA);
-    int st = scan_exclusive_i64(p, sc, rowcnt, row_ptr, nS, row_ptr + nS, s);
+    int st = conn_count_indexed(p, sc, H, dets, nS, dets, nS, rowcnt, bits, s);
+    if (st < 0) return fail(st);
+    st = scan_exclusive_i64(p, sc, rowcnt, row_ptr, nS, row_ptr + nS, s);
     if (st < 0) return fail(st);
     int64_t nnz = 0;
     if (cudaMemcpyAsync(&nnz, row_ptr + nS, sizeof nnz, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -453,6 +453,37 @@ __device__ __forceinline__ double exc_element(const ProblemDev& P, const DetCtx&
     return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(x.sign < 0) << 63));
 }
 
+// The element of a single (x.cls <= 1) in fixed point, without its sign: the integer sum of the
+// same terms as exc_element, each table entry rounded once to the grid 2^-P.sfx_e, so it is
+// exact and differs from exc_element's FP64 sum by at most 49 half-units of the grid plus that
+// sum's own rounding (at most 48 ulps of hoff_max).
+__device__ __forceinline__ long long single_element_fx(const ProblemDev& P, const DetCtx& c,
+                                                       const Exc& x) {
+    const int n = P.norb;
+    const size_t base = ((size_t)x.i * n + x.a) * n;
+    long long v = __ldg(&P.hfx_off[x.i * n + x.a]);
+    const bool alpha = x.cls == 0;
+    for (int k = 0; k < P.na; ++k) {
+        const int j = c.occA[k];
+        if (alpha) {
+            if (j == x.i) continue;
+            v += __ldg(&P.TDfx[base + j]);
+        } else {
+            v += __ldg(&P.TJfx[base + j]);
+        }
+    }
+    for (int k = 0; k < P.nb; ++k) {
+        const int j = c.occB[k];
+        if (!alpha) {
+            if (j == x.i) continue;
+            v += __ldg(&P.TDfx[base + j]);
+        } else {
+            v += __ldg(&P.TJfx[base + j]);
+        }
+    }
+    return v;
+}
+
 // H_xx: sum_{occ} h_ii + sum_{i<j same spin} [J_ij - K_ij] + sum_{i alpha, j beta} J_ij, in the
 // order alpha h, beta h, alpha pairs, beta pairs, alpha-beta pairs (one running sum).
 __device__ __forceinline__ double diag_element_impl(const ProblemDev& P, uint64_t a, uint64_t b) {

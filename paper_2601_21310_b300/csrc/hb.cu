@@ -181,24 +181,63 @@ __device__ __forceinline__ bool in_bucket_of(uint64_t a, uint64_t b, uint64_t B,
 // The screening test fl(v |psi_x|) >= eps for v >= 0 (a table entry or |<x'|H|x>|), without an
 // FP64 multiply per candidate: the rounded product is non-decreasing in v, so it holds exactly
 // when v >= v*, the smallest double that passes, and non-negative doubles order like their bit
-// patterns (an integer compare). v* is found once per x from eps / |psi_x| and its neighbours.
-// Should the search not settle within a few steps (it moves by ulps from the quotient), the
-// test falls back to the product.
+// patterns (an integer compare). v* is found once per x: a few ulp steps from eps / |psi_x|,
+// else a bisection over the bit patterns of [0, inf] (exact, at most 63 products).
 struct HbCut {
     unsigned long long thr;  // bit pattern of v*
-    double ap, eps;
-    bool exact;              // fall back to fl(v ap) >= eps
     __device__ __forceinline__ bool pass(double v) const {
-        return exact ? __dmul_rn(v, ap) >= eps
-                     : (unsigned long long)__double_as_longlong(v) >= thr;
+        return (unsigned long long)__double_as_longlong(v) >= thr;
     }
 };
 
+// the FP64 element of a single near the cut (rare): out of line, so that the traversal keeps
+// its registers for the common path
+__device__ __noinline__ double single_element_near_cut(const ProblemDev& P, const DetCtx& c,
+                                                       const Exc& x) {
+    return exc_element(P, c, x);
+}
+
+// The same cut for a single's element from its fixed-point value F (units 2^-e): |F| at or above
+// hi passes and at or below lo fails whatever FP64 rounding the exact element has (the margin
+// covers the table roundings and the FP64 sum's own error); in between the FP64 element is
+// formed exactly and tested.
+struct HbCutFx {
+    long long lo, hi;  // fail surely when |F| <= lo (lo = -1: never), pass surely when |F| >= hi
+    bool all;          // eps = 0: every single passes
+};
+
+__device__ __forceinline__ HbCutFx hb_cut_fx(const HbCut& c, const ProblemDev& P) {
+    const long long never_pass = 0x7fffffffffffffffll;
+    HbCutFx r;
+    r.all = c.thr == 0ull;
+    r.lo = -1;
+    r.hi = never_pass;
+    if (r.all) return r;
+    // margin in grid units: 49 roundings of table entries (half a unit each), the FP64 sum's
+    // error (48 ulps of at most hoff_max, i.e. 48 * 2^-53 hoff_max 2^e <= 48 * 2^9 units), and
+    // 2048 for the rounding of t +- margin in FP64 (spacing at most 2^10 below 2^62)
+    const double margin = 24.5 + 48.0 * 512.0 + 2048.0;
+    const double t = ldexp(__longlong_as_double((long long)c.thr), P.sfx_e);
+    const double two62 = 4611686018427387904.0;
+    if (t + margin < two62) r.hi = (long long)ceil(t + margin);
+    if (t - margin >= two62) r.lo = never_pass;  // no element reaches the cut
+    else if (t - margin > 0.0) r.lo = (long long)floor(t - margin);
+    return r;
+}
+
+__device__ __noinline__ unsigned long long hb_cut_bisect(double eps, double ap) {
+    unsigned long long lo = 0ull, hi = 0x7ff0000000000000ull;  // fails at lo, passes at hi
+    while (hi - lo > 1ull) {
+        const unsigned long long mid = lo + ((hi - lo) >> 1);
+        if (__dmul_rn(__longlong_as_double((long long)mid), ap) >= eps) hi = mid;
+        else lo = mid;
+    }
+    return hi;
+}
+
+// requires eps > 0 or returns the pass-all cut; ap > 0 and finite
 __device__ __forceinline__ HbCut hb_cut(double eps, double ap) {
     HbCut c;
-    c.ap = ap;
-    c.eps = eps;
-    c.exact = false;
     c.thr = 0ull;
     if (!(eps > 0.0)) return c;  // every v >= 0 passes
     const double t = __ddiv_rn(eps, ap);
@@ -210,7 +249,7 @@ __device__ __forceinline__ HbCut hb_cut(double eps, double ap) {
     unsigned long long b = (unsigned long long)__double_as_longlong(t);
     int steps = 0;
     if (__dmul_rn(t, ap) >= eps) {
-        while (b > 0 && steps < 64 && __dmul_rn(__longlong_as_double((long long)(b - 1)), ap) >= eps) {
+        while (b > 0 && steps < 8 && __dmul_rn(__longlong_as_double((long long)(b - 1)), ap) >= eps) {
             --b;
             ++steps;
         }
@@ -218,10 +257,9 @@ __device__ __forceinline__ HbCut hb_cut(double eps, double ap) {
         do {
             ++b;
             ++steps;
-        } while (b < inf && steps < 64 && __dmul_rn(__longlong_as_double((long long)b), ap) < eps);
+        } while (b < inf && steps < 8 && __dmul_rn(__longlong_as_double((long long)b), ap) < eps);
     }
-    c.thr = b;
-    c.exact = steps >= 64;
+    c.thr = steps >= 8 ? hb_cut_bisect(eps, ap) : b;
     return c;
 }
 
@@ -344,6 +382,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             run += __popc(bal);
         };
         // singles: every one, with its exact element
+        const HbCutFx cutfx = hb_cut_fx(cut, P);
         for (uint32_t r0 = 0; r0 < nsing; r0 += 32) {
             const uint32_t e = r0 + lane;
             bool take = false;
@@ -352,20 +391,41 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             double m = 0.0;
             if (e < nsing) {
                 decode_exc(P, PT, *ctx, x.x, x.y, e, ex);
-                const double hv = exc_element(P, *ctx, ex);
-                const bool ok = cut.pass(fabs(hv));
                 if (PTM) {
+                    // the element in exact fixed point; the FP64 element only near the cut
+                    const long long F = single_element_fx(P, *ctx, ex);
+                    const long long aF = F < 0 ? -F : F;
+                    bool ok;
+                    double hv = 0.0;
+                    bool have_hv = false;
+                    if (cutfx.all || aF >= cutfx.hi) {
+                        ok = true;
+                    } else if (aF <= cutfx.lo) {
+                        ok = false;
+                    } else {
+                        hv = single_element_near_cut(P, *ctx, ex);
+                        have_hv = true;
+                        ok = cut.pass(fabs(hv));
+                    }
                     take = ok && in_bucket_of(ex.a2, ex.b2, B, bucket) &&
                            hash_lookup(H, ex.a2, ex.b2) < 0;
-                    if (EMIT && take) m = __dmul_rn(hv, py);
+                    if (EMIT && take) {
+                        if (!have_hv) {  // the fixed-point element with the excitation's sign
+                            const double f = ldexp(__ll2double_rn(F), -P.sfx_e);
+                            hv = ex.sign < 0 ? -f : f;
+                        }
+                        m = __dmul_rn(hv, py);
+                    }
                 } else {
+                    const double hv = exc_element(P, *ctx, ex);
+                    const bool ok = cut.pass(fabs(hv));
                     take = ok && hash_lookup(H, ex.a2, ex.b2) < 0;
                     if (EMIT && take) m = __dmul_rn(fabs(hv), ap);
                 }
             }
             keep(take, ex.a2, ex.b2, m);
         }
-        if (!APPEND) tested += nsing;
+        if (!(APPEND && PTM)) tested += nsing;
         // doubles: three groups of hole pairs; each lane tests the head of one list
         for (int grp = 0; grp < 3; ++grp) {
             const int npairs = grp == 0 ? (int)choose2(P.na)
@@ -444,7 +504,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                             }
                         }
                         keep(take, a2, b2, m);
-                        if (!APPEND) tested += stop ? (unsigned)(__ffs(stop) - 1) : 32u;
+                        if (!(APPEND && PTM)) tested += stop ? (unsigned)(__ffs(stop) - 1) : 32u;
                         if (stop) break;  // sorted: every later entry fails too
                         tv = tvn;
                         cd = cdn;
@@ -491,6 +551,18 @@ static unsigned hb_grid(int64_t nS) {
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// every stride-th configuration of S and its amplitude (the sample that sizes the buffers of
+// the one-traversal emission)
+__global__ void k_hb_gather_stride(const ulonglong2* __restrict__ S, const double* __restrict__ psi,
+                                   int64_t ns, int64_t stride, ulonglong2* __restrict__ So,
+                                   double* __restrict__ po) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        So[i] = S[i * stride];
+        po[i] = psi[i * stride];
+    }
+}
+
 template <class K>
 static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
                   const uint64_t* dets, const double* psi, int64_t nS, double eps,
@@ -503,46 +575,87 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
         NQS_CK(cudaFuncSetAttribute(k_hb_select<HB_EMIT, K>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    int64_t *cnt, *offs, *total_dev;
-    unsigned long long* examined;
-    NQS_TRY(sc.get(&cnt, nS));
-    NQS_TRY(sc.get(&offs, nS));
-    NQS_TRY(sc.get(&total_dev, 1));
+    // One traversal appending the kept pairs (their order is then timing-dependent; the
+    // reduction below, a sort and a maximum per run, is not), into buffers sized from a counted
+    // sample of S (every stride-th configuration, x1.5) and enlarged once if they overflow.
+    const size_t smem_a = smem + (size_t)HB_WARPS * HB_STAGE * (sizeof(K) + sizeof(double));
+    if (smem_a > 48 * 1024)
+        NQS_CK(cudaFuncSetAttribute(k_hb_select<HB_APPEND, K>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
+    unsigned long long *examined, *cursor;
     NQS_TRY(sc.get(&examined, 1));
-    NQS_CK(cudaMemsetAsync(examined, 0, sizeof(unsigned long long), s));
+    NQS_TRY(sc.get(&cursor, 1));
+    double est;
     {
-        ProfScope prof_(PROF_HB_SELECT, s);
-        k_hb_select<HB_COUNT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
-            P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, cnt, nullptr, nullptr, nullptr,
-            examined, nullptr, 0);
+        const int64_t stride = nS > 4096 ? nS / 4096 : 1;
+        const int64_t ns = (nS + stride - 1) / stride;
+        Scratch es(p, s);
+        ulonglong2* ds;
+        double* ps;
+        int64_t *c1, *o1, *t1;
+        NQS_TRY(es.get(&ds, ns));
+        NQS_TRY(es.get(&ps, ns));
+        NQS_TRY(es.get(&c1, ns));
+        NQS_TRY(es.get(&o1, ns));
+        NQS_TRY(es.get(&t1, 1));
+        k_hb_gather_stride<<<grid_for(ns, 256), 256, 0, s>>>((const ulonglong2*)dets, psi, ns,
+                                                              stride, ds, ps);
+        NQS_CK_LAUNCH();
+        {
+            ProfScope prof_(PROF_HB_SELECT, s);
+            k_hb_select<HB_COUNT, K><<<hb_grid(ns), HB_THREADS, smem, s>>>(
+                P, H, T, ds, ps, ns, eps, 1, 0, c1, nullptr, nullptr, nullptr, nullptr, nullptr,
+                0);
+        }
+        NQS_CK_LAUNCH();
+        NQS_TRY(scan_exclusive_i64(p, es, c1, o1, ns, t1, s));
+        int64_t tot = 0;
+        NQS_CK(cudaMemcpyAsync(&tot, t1, sizeof tot, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+        est = (double)tot * ((double)nS / (double)ns);
     }
-    NQS_CK_LAUNCH();
-    NQS_TRY(scan_exclusive_i64(p, sc, cnt, offs, nS, total_dev, s));
+    size_t fr = 0, totm = 0;
+    NQS_CK(cudaMemGetInfo(&fr, &totm));
+    uint64_t reserved = 0, used = 0;
+    NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+    NQS_CK(cudaMemPoolGetAttribute(p->pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    const double avail = (double)fr + (double)(reserved > used ? reserved - used : 0);
+    // pairs, sort buffers and the output: 2 (key + 8) + 12 bytes per pair, 90% of what is free
+    const double memcap = fmin(0.9 * avail / (2.0 * (sizeof(K) + 8.0) + 12.0), 4294967295.0);
+    int64_t cap = (int64_t)fmin(fmin(1.5 * est + 65536.0, (double)nS * (double)P.nexc), memcap);
     int64_t n = 0;
-    unsigned long long nexam = 0;
-    NQS_CK(cudaMemcpyAsync(&n, total_dev, sizeof n, cudaMemcpyDeviceToHost, s));
-    NQS_CK(cudaMemcpyAsync(&nexam, examined, sizeof nexam, cudaMemcpyDeviceToHost, s));
-    NQS_CK(cudaStreamSynchronize(s));
-    out->n_emitted = n;
-    out->n_examined = (int64_t)nexam;
-    if (n == 0) return NQS_OK;
-    if (n >= ((int64_t)1 << 32)) {
-        nqs_record_message("nqs_hb_select: more than 2^32 kept pairs; raise eps_hb");
-        return NQS_ERR_UNSUPPORTED;
+    K *keys = nullptr, *keys2;
+    double *vals = nullptr, *vals2;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        NQS_TRY(sc.get(&keys, cap));
+        NQS_TRY(sc.get(&vals, cap));
+        NQS_CK(cudaMemsetAsync(examined, 0, sizeof(unsigned long long), s));
+        NQS_CK(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s));
+        {
+            ProfScope prof_(PROF_HB_SELECT, s);
+            k_hb_select<HB_APPEND, K><<<hb_grid(nS), HB_THREADS, smem_a, s>>>(
+                P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, nullptr, nullptr, keys,
+                vals, examined, cursor, (uint64_t)cap);
+        }
+        NQS_CK_LAUNCH();
+        unsigned long long nc = 0, nexam = 0;
+        NQS_CK(cudaMemcpyAsync(&nc, cursor, sizeof nc, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaMemcpyAsync(&nexam, examined, sizeof nexam, cudaMemcpyDeviceToHost, s));
+        NQS_CK(cudaStreamSynchronize(s));
+        n = (int64_t)nc;
+        out->n_emitted = n;
+        out->n_examined = (int64_t)nexam;
+        if (n <= cap) break;
+        if ((double)n > memcap || n >= ((int64_t)1 << 32)) {
+            nqs_record_message("nqs_hb_select: the kept pairs do not fit in device memory (or "
+                               "exceed 2^32); raise eps_hb");
+            return NQS_ERR_UNSUPPORTED;
+        }
+        cap = n;  // the exact size: one more traversal
     }
-    K *keys, *keys2;
-    double *vals, *vals2;
-    NQS_TRY(sc.get(&keys, n));
-    NQS_TRY(sc.get(&vals, n));
+    if (n == 0) return NQS_OK;
     NQS_TRY(sc.get(&keys2, n));
     NQS_TRY(sc.get(&vals2, n));
-    {
-        ProfScope prof_(PROF_HB_SELECT, s);
-        k_hb_select<HB_EMIT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
-            P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, nullptr, offs, keys, vals,
-            nullptr, nullptr, 0);
-    }
-    NQS_CK_LAUNCH();
     if (sizeof(K) == 4)
         NQS_TRY(radix_sort_pairs32(p, sc, (uint32_t*&)keys, vals, (uint32_t*&)keys2, vals2, n,
                                    2 * P.norb, s));

@@ -69,6 +69,13 @@ struct ProblemDev {
     // bound on |<x'|H|y>| over every off-diagonal pair (singles: |h_ia| + sum_j (2 |(ia|jj)| +
     // |(ij|ja)|); doubles: 2 max |(pq|rs)|): the range of the PT2 fixed-point run sums
     double hoff_max;
+    // single-excitation elements in exact fixed point (value = int * 2^-sfx_e): the same terms
+    // as TJ / TD / h rounded once each, for the screened PT2 emission (hb.cu); every partial sum
+    // of one element stays below 2^62 (sfx_e from hoff_max)
+    const long long* TJfx;
+    const long long* TDfx;
+    const long long* hfx_off;  // h_pq
+    int sfx_e;
 };
 
 struct nqs_problem {
@@ -78,6 +85,7 @@ struct nqs_problem {
     double *h, *eri, *J, *K, *TJ, *TD;
     long long* fx;  // hfx | JKfx | Jfx
     long long* bt;  // Dt | Xt | Yt
+    long long* sfx; // TJfx | TDfx | hfx_off
     cudaMemPool_t pool;  // library-owned stream-ordered pool for per-call scratch
     int* err_word;       // device: set by a kernel whose bounded wait timed out
     double* hb_val;      // heat-bath integral tables (hb.cu), built on first use
@@ -222,6 +230,14 @@ __global__ void k_conn_fill(ProblemDev P, HashS H, const ulonglong2* __restrict_
                             const int64_t* __restrict__ row_ptr, int32_t* __restrict__ col,
                             double* __restrict__ val, const uint32_t* __restrict__ bits);
 size_t conn_smem_bytes(const ProblemDev& P);
+// the H_SS count pass over `rows` against the sorted unique set Rset (hashed in H): indices of
+// Rset by alpha and beta string, then the indexed count kernel (connect.cu)
+int conn_count_indexed(nqs_problem* p, Scratch& sc, const HashS& H, const uint64_t* rows,
+                       int64_t nrows, const uint64_t* Rset, int64_t nR, int64_t* rowcnt,
+                       uint32_t* bits, cudaStream_t s);
+// a sorted copy of n configurations (ascending by (a, b)) into out [n][2]
+int sort_configs(nqs_problem* p, Scratch& sc, const uint64_t* in, int64_t n, uint64_t* out,
+                 cudaStream_t s);
 unsigned conn_grid_size(int64_t nS);
 
 // slots_per_det > 0 fixes the capacity to the next power of two >= slots_per_det * nS (the

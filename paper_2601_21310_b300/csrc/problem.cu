@@ -78,6 +78,16 @@ void nqs_scratch_free(nqs_problem* p, void* ptr, cudaStream_t s) {
 // ------------------------------------------------------------------------------------------
 // problem create / destroy
 // ------------------------------------------------------------------------------------------
+// the single-excitation tables in fixed point: v * 2^e rounded to the nearest integer
+__global__ void k_fx_tables(int64_t n3, int n, const double* TJ, const double* TD, const double* h,
+                            int e, long long* out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 2 * n3 + (int64_t)n * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const double v = t < n3 ? TJ[t] : (t < 2 * n3 ? TD[t - n3] : h[t - 2 * n3]);
+        out[t] = __double2ll_rn(ldexp(v, e));
+    }
+}
+
 __global__ void k_tables(int n, const double* eri, double* J, double* K, double* TJ, double* TD) {
     int64_t total = (int64_t)n * n * n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -251,6 +261,21 @@ extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double*
                 hmax = fmax(hmax, f);
             }
         d.hoff_max = fmax(hmax, 2.0 * emax) * (1.0 + 1e-12);
+        // fixed-point single tables: every partial sum of an element is bounded by hoff_max
+        d.sfx_e = 62 - (int)ceil(log2(d.hoff_max > 0.0 ? d.hoff_max : 1.0));
+        const int64_t n3 = (int64_t)n * n * n;
+        if (cudaMalloc(&p->sfx, (2 * n3 + (int64_t)n * n) * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NQS_ERR_OOM);
+        }
+        k_fx_tables<<<grid_for(2 * n3 + (int64_t)n * n, 256), 256>>>(n3, n, p->TJ, p->TD, p->h,
+                                                                   d.sfx_e, p->sfx);
+        nqs_note_launch();
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+            return fail(NQS_ERR_CUDA);
+        d.TJfx = p->sfx;
+        d.TDfx = p->sfx + n3;
+        d.hfx_off = p->sfx + 2 * n3;
         // byte tables
         const int nb = (n + 7) / 8;
         const size_t nD = (size_t)nb * 256, nX = (size_t)nb * (nb - 1) / 2 * 65536,
@@ -284,6 +309,7 @@ extern "C" int nqs_problem_destroy(nqs_problem* p) {
     cudaFree(p->err_word);
     cudaFree(p->fx);
     cudaFree(p->bt);
+    cudaFree(p->sfx);
     cudaFree(p->hb_val);
     cudaFree(p->hb_code);
     if (p->pool) cudaMemPoolDestroy(p->pool);

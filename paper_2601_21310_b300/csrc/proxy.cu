@@ -140,24 +140,20 @@ extern "C" int nqs_proxy_hamiltonian(nqs_problem* p, const uint64_t* T, int64_t 
         }
     }
     const size_t smem = conn_smem_bytes(p->d);
-    if (smem > 48 * 1024) {
-        NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+    if (smem > 48 * 1024)
         NQS_CK(cudaFuncSetAttribute(k_conn_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-    }
-    // rows of V: every connection inside T
+    // rows of V: every connection inside T, counted against the indices of a sorted copy of T
+    // (V and P are each sorted, their union is not)
+    uint64_t* Tsort;
+    NQS_TRY(sc.get(&Tsort, 2 * (size_t)nT));
+    NQS_TRY(sort_configs(p, sc, T, nT, Tsort, s));
     int64_t *rowcnt, *rpV;
     uint32_t* bits;
     NQS_TRY(sc.get(&rowcnt, nV));
     NQS_TRY(sc.get(&rpV, nV + 1));
     NQS_TRY(sc.get(&bits, (size_t)nV * ((p->d.nexc + 31) / 32)));
-    {
-        ProfScope prof_(PROF_CONN_COUNT, s);
-        k_conn_count<<<conn_grid_size(nV), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)T,
-                                                                     nV, rowcnt, bits);
-    }
-    NQS_CK_LAUNCH();
+    NQS_TRY(conn_count_indexed(p, sc, H, T, nV, Tsort, nT, rowcnt, bits, s));
     NQS_TRY(scan_exclusive_i64(p, sc, rowcnt, rpV, nV, rpV + nV, s));
     int64_t nnzV = 0;
     NQS_CK(cudaMemcpyAsync(&nnzV, rpV + nV, sizeof nnzV, cudaMemcpyDeviceToHost, s));
