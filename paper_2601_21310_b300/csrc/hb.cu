@@ -294,6 +294,16 @@ __device__ __forceinline__ double double_element(const ProblemDev& P, int grp, u
 // examined (may be null) accumulates the number of candidates whose coupling was tested.
 enum { HB_COUNT = 0, HB_EMIT = 1, PT_COUNT = 2, PT_EMIT = 3, HB_APPEND = 5, PT_APPEND = 7 };
 #define HB_STAGE 64  // staged pairs per warp (append modes)
+#define HB_CQ 64     // queued double-excitation candidates per warp
+#define HB_CQ_BYTES (HB_CQ * (sizeof(uint32_t) + sizeof(double)))
+
+// shared memory of k_hb_select: pair tables, per-warp contexts and candidate queues, and in
+// the append modes the per-warp staging of kept pairs
+template <class K>
+static size_t hb_smem(const ProblemDev& P, bool append) {
+    return pair_table_bytes(P) + HB_WARPS * (sizeof(DetCtx) + HB_CQ_BYTES) +
+           (append ? (size_t)HB_WARPS * HB_STAGE * (sizeof(K) + sizeof(double)) : 0);
+}
 
 template <int MODE, class K>
 __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS H, HbTab T,
@@ -314,8 +324,13 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
     extern __shared__ __align__(16) uint8_t smem[];
     PairTables PT = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
-    // append staging: HB_STAGE keys then HB_STAGE values per warp, after the contexts
-    uint8_t* stage = smem + pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx) +
+    // candidate queue of this warp (HB_CQ codes, then HB_CQ table values), after the contexts
+    uint8_t* cqb = smem + pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx) +
+                   (threadIdx.x >> 5) * HB_CQ_BYTES;
+    uint32_t* cq = (uint32_t*)cqb;
+    double* cqv = (double*)(cqb + HB_CQ * sizeof(uint32_t));
+    // append staging: HB_STAGE keys then HB_STAGE values per warp, after the queues
+    uint8_t* stage = smem + pair_table_bytes(P) + HB_WARPS * (sizeof(DetCtx) + HB_CQ_BYTES) +
                      (threadIdx.x >> 5) * HB_STAGE * (sizeof(K) + sizeof(double));
     K* sk = (K*)stage;
     double* sv = (double*)(stage + HB_STAGE * sizeof(K));
@@ -426,13 +441,65 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             keep(take, ex.a2, ex.b2, m);
         }
         if (!(APPEND && PTM)) tested += nsing;
-        // doubles: three groups of hole pairs; each lane tests the head of one list
+        // doubles: three groups of hole pairs; each lane tests the head of one list. A list is
+        // walked 32 entries at a time; the entries that pass the cut and whose particles are
+        // empty in x are queued (hole and particle orbitals and group in one word, with the
+        // table value), and the queue is resolved 32 at a time: the configuration, the bucket
+        // test, the probe into S and the element, each at full warp width
+        const uint64_t wA = x.x, wB = x.y;
+        int cn = 0;  // queued candidates of this warp
+        auto drain = [&](int cnt_) {
+            __syncwarp();
+            bool take = false;
+            uint64_t a2 = 0, b2 = 0;
+            double m = 0.0;
+            uint32_t code = 0;
+            double tq = 0.0;
+            if (lane < cnt_) {
+                code = cq[lane];
+                tq = cqv[lane];
+            }
+            const int rest = cn - cnt_;
+            uint32_t c2 = 0;
+            double t2 = 0.0;
+            if (lane < rest) {
+                c2 = cq[cnt_ + lane];
+                t2 = cqv[cnt_ + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+                cq[lane] = c2;
+                cqv[lane] = t2;
+            }
+            cn = rest;
+            if (lane < cnt_) {
+                const int hi = code & 63, hj = (code >> 6) & 63, a = (code >> 12) & 63,
+                          b = (code >> 18) & 63, grp = (int)(code >> 24);
+                if (grp < 2) {
+                    const uint64_t w = grp == 0 ? wA : wB;
+                    const uint64_t w2 =
+                        w ^ (1ull << hi) ^ (1ull << hj) ^ (1ull << a) ^ (1ull << b);
+                    a2 = grp == 0 ? w2 : wA;
+                    b2 = grp == 0 ? wB : w2;
+                } else {
+                    a2 = wA ^ (1ull << hi) ^ (1ull << a);
+                    b2 = wB ^ (1ull << hj) ^ (1ull << b);
+                }
+                const bool inb = PTM ? in_bucket_of(a2, b2, B, bucket) : true;
+                take = inb && hash_lookup(H, a2, b2) < 0;
+                if (PTM && EMIT && take)
+                    m = __dmul_rn(double_element(P, grp, wA, wB, hi, hj, a, b), py);
+                else if (!PTM && EMIT && take)
+                    m = __dmul_rn(tq, ap);
+            }
+            keep(take, a2, b2, m);
+            __syncwarp();
+        };
         for (int grp = 0; grp < 3; ++grp) {
             const int npairs = grp == 0 ? (int)choose2(P.na)
                              : grp == 1 ? (int)choose2(P.nb) : P.na * P.nb;
             const int L = grp < 2 ? T.Lss : T.Los;
             if (L == 0) continue;
-            const uint64_t wA = x.x, wB = x.y;
             for (int p0 = 0; p0 < npairs; p0 += 32) {
                 const int pi = p0 + lane;
                 int i = 0, j = 0;
@@ -460,15 +527,16 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                     const int hi = __shfl_sync(FULL_MASK, i, src);
                     const int hj = __shfl_sync(FULL_MASK, j, src);
                     const int64_t hb = __shfl_sync(FULL_MASK, base, src);
+                    // particles must be empty in x: in the alpha (grp 0) or beta (grp 1)
+                    // string for same-spin pairs, a in alpha and b in beta for grp 2
+                    const uint64_t wa = grp == 1 ? wB : wA, wb = grp == 0 ? wA : wB;
+                    const uint32_t hcode = (uint32_t)hi | ((uint32_t)hj << 6) | ((uint32_t)grp << 24);
                     // software-pipelined walk: the next 32 entries are loaded before this
-                    // chunk's candidates are probed, so the two L2 round trips overlap
+                    // chunk's candidates are tested, so the two L2 round trips overlap
                     double tv = lane < L ? __ldg(&T.val[hb + lane]) : 0.0;
                     uint16_t cd = lane < L ? __ldg(&T.code[hb + lane]) : (uint16_t)0;
                     for (int c0 = 0; c0 < L; c0 += 32) {
                         const int t = c0 + lane;
-                        bool take = false;
-                        uint64_t a2 = 0, b2 = 0;
-                        double m = 0.0;
                         const bool pass = t < L && cut.pass(tv);
                         const unsigned stop = __ballot_sync(FULL_MASK, !pass);
                         double tvn = 0.0;
@@ -477,33 +545,16 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                             tvn = __ldg(&T.val[hb + t + 32]);
                             cdn = __ldg(&T.code[hb + t + 32]);
                         }
-                        {
-                            const int a = cd & 0xff, b = cd >> 8;
-                            if (pass) {
-                                bool valid = false;
-                                if (grp < 2) {
-                                    const uint64_t w = grp == 0 ? wA : wB;
-                                    if (!((w >> a) & 1ull) && !((w >> b) & 1ull)) {
-                                        const uint64_t w2 =
-                                            w ^ (1ull << hi) ^ (1ull << hj) ^ (1ull << a) ^ (1ull << b);
-                                        a2 = grp == 0 ? w2 : wA;
-                                        b2 = grp == 0 ? wB : w2;
-                                        valid = true;
-                                    }
-                                } else if (!((wA >> a) & 1ull) && !((wB >> b) & 1ull)) {
-                                    a2 = wA ^ (1ull << hi) ^ (1ull << a);
-                                    b2 = wB ^ (1ull << hj) ^ (1ull << b);
-                                    valid = true;
-                                }
-                                if (PTM) valid = valid && in_bucket_of(a2, b2, B, bucket);
-                                take = valid && hash_lookup(H, a2, b2) < 0;
-                                if (PTM && EMIT && take)
-                                    m = __dmul_rn(double_element(P, grp, wA, wB, hi, hj, a, b), py);
-                                else if (!PTM && EMIT && take)
-                                    m = __dmul_rn(tv, ap);
-                            }
+                        const int a = cd & 0xff, b = cd >> 8;
+                        const bool valid = pass && !((wa >> a) & 1ull) && !((wb >> b) & 1ull);
+                        const unsigned vb = __ballot_sync(FULL_MASK, valid);
+                        if (valid) {
+                            const int slot = cn + __popc(vb & lt);
+                            cq[slot] = hcode | ((uint32_t)a << 12) | ((uint32_t)b << 18);
+                            if (!PTM) cqv[slot] = tv;
                         }
-                        keep(take, a2, b2, m);
+                        cn += __popc(vb);
+                        if (cn >= 32) drain(32);
                         if (!(APPEND && PTM)) tested += stop ? (unsigned)(__ffs(stop) - 1) : 32u;
                         if (stop) break;  // sorted: every later entry fails too
                         tv = tvn;
@@ -512,6 +563,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                 }
             }
         }
+        if (cn > 0) drain(cn);
         if (!EMIT && lane == 0) cnt[det] = run;
         if (examined && lane == 0) atomicAdd(examined, tested);
         __syncwarp();
@@ -568,7 +620,7 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
                   const uint64_t* dets, const double* psi, int64_t nS, double eps,
                   nqs_detset* out, cudaStream_t s) {
     const ProblemDev& P = p->d;
-    const size_t smem = pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx);
+    const size_t smem = hb_smem<K>(P, false);
     if (smem > 48 * 1024) {
         NQS_CK(cudaFuncSetAttribute(k_hb_select<HB_COUNT, K>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -578,7 +630,7 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
     // One traversal appending the kept pairs (their order is then timing-dependent; the
     // reduction below, a sort and a maximum per run, is not), into buffers sized from a counted
     // sample of S (every stride-th configuration, x1.5) and enlarged once if they overflow.
-    const size_t smem_a = smem + (size_t)HB_WARPS * HB_STAGE * (sizeof(K) + sizeof(double));
+    const size_t smem_a = hb_smem<K>(P, true);
     if (smem_a > 48 * 1024)
         NQS_CK(cudaFuncSetAttribute(k_hb_select<HB_APPEND, K>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a));
@@ -702,7 +754,7 @@ static int hb_pt2_pass_k(nqs_problem* p, const HbTab& T, const HashS& H, const u
                          int64_t* cnt, const int64_t* offs, void* keys, double* vals,
                          cudaStream_t s) {
     const ProblemDev& P = p->d;
-    const size_t smem = pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx);
+    const size_t smem = hb_smem<K>(P, false);
     if (smem > 48 * 1024) {
         NQS_CK(cudaFuncSetAttribute(k_hb_select<PT_COUNT, K>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -749,8 +801,7 @@ static int hb_pt2_append_k(nqs_problem* p, const HbTab& T, const HashS& H, const
                            const double* psi, int64_t nS, double eps, void* keys, double* vals,
                            int64_t cap, unsigned long long* cursor_dev, cudaStream_t s) {
     const ProblemDev& P = p->d;
-    const size_t smem = pair_table_bytes(P) + HB_WARPS * sizeof(DetCtx) +
-                        (size_t)HB_WARPS * HB_STAGE * (sizeof(K) + sizeof(double));
+    const size_t smem = hb_smem<K>(P, true);
     if (smem > 48 * 1024)
         NQS_CK(cudaFuncSetAttribute(k_hb_select<PT_APPEND, K>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
