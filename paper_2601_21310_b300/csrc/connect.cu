@@ -595,65 +595,6 @@ static unsigned conn_grid(int64_t nS) {
 size_t conn_smem_bytes(const ProblemDev& P) { return conn_smem(P); }
 unsigned conn_grid_size(int64_t nS) { return conn_grid(nS); }
 
-template <class K>
-__global__ void k_cfg_keys(const ulonglong2* __restrict__ in, int64_t n, int norb,
-                           K* __restrict__ keys, double* __restrict__ pad) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const ulonglong2 x = in[i];
-        keys[i] = key_make<K>(x.x, x.y, norb);
-        pad[i] = 0.0;
-    }
-}
-
-template <class K>
-__global__ void k_cfg_unkeys(const K* __restrict__ keys, int64_t n, int norb,
-                             ulonglong2* __restrict__ out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t a, b;
-        key_split(keys[i], norb, a, b);
-        out[i] = make_ulonglong2(a, b);
-    }
-}
-
-template <class K>
-static int sort_configs_k(nqs_problem* p, Scratch& sc, const uint64_t* in, int64_t n,
-                          uint64_t* out, cudaStream_t s) {
-    const int norb = p->d.norb;
-    K *keys, *keys2;
-    double *pad, *pad2;
-    NQS_TRY(sc.get(&keys, n));
-    NQS_TRY(sc.get(&keys2, n));
-    NQS_TRY(sc.get(&pad, n));
-    NQS_TRY(sc.get(&pad2, n));
-    k_cfg_keys<K><<<grid_for(n, 256), 256, 0, s>>>((const ulonglong2*)in, n, norb, keys, pad);
-    NQS_CK_LAUNCH();
-    int st;
-    if (sizeof(K) == 4)
-        st = radix_sort_pairs32(p, sc, (uint32_t*&)keys, pad, (uint32_t*&)keys2, pad2, n,
-                                2 * norb, s);
-    else if (sizeof(K) == 8)
-        st = radix_sort_pairs(p, sc, (uint64_t*&)keys, pad, (uint64_t*&)keys2, pad2, n,
-                              2 * norb, s);
-    else
-        st = radix_sort_pairs128(p, sc, (Key128*&)keys, pad, (Key128*&)keys2, pad2, n,
-                                 2 * norb, s);
-    if (st < 0) return st;
-    k_cfg_unkeys<K><<<grid_for(n, 256), 256, 0, s>>>(keys, n, norb, (ulonglong2*)out);
-    NQS_CK_LAUNCH();
-    return NQS_OK;
-}
-
-int sort_configs(nqs_problem* p, Scratch& sc, const uint64_t* in, int64_t n, uint64_t* out,
-                 cudaStream_t s) {
-    if (n <= 0) return NQS_OK;
-    const int norb = p->d.norb;
-    if (2 * norb <= 32) return sort_configs_k<uint32_t>(p, sc, in, n, out, s);
-    if (2 * norb <= 64) return sort_configs_k<uint64_t>(p, sc, in, n, out, s);
-    return sort_configs_k<Key128>(p, sc, in, n, out, s);
-}
-
 // The count pass over `rows` (nrows configurations) against the sorted, unique set R (nR
 // configurations, hashed in H; every row must be a member of R): the indices of R by alpha
 // string and by beta string, then k_conn_count_ab (k_conn_count when there are no alpha-beta

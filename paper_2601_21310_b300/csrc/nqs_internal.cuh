@@ -235,9 +235,6 @@ size_t conn_smem_bytes(const ProblemDev& P);
 int conn_count_indexed(nqs_problem* p, Scratch& sc, const HashS& H, const uint64_t* rows,
                        int64_t nrows, const uint64_t* Rset, int64_t nR, int64_t* rowcnt,
                        uint32_t* bits, cudaStream_t s);
-// a sorted copy of n configurations (ascending by (a, b)) into out [n][2]
-int sort_configs(nqs_problem* p, Scratch& sc, const uint64_t* in, int64_t n, uint64_t* out,
-                 cudaStream_t s);
 unsigned conn_grid_size(int64_t nS);
 
 // slots_per_det > 0 fixes the capacity to the next power of two >= slots_per_det * nS (the

@@ -140,20 +140,26 @@ extern "C" int nqs_proxy_hamiltonian(nqs_problem* p, const uint64_t* T, int64_t 
         }
     }
     const size_t smem = conn_smem_bytes(p->d);
-    if (smem > 48 * 1024)
+    if (smem > 48 * 1024) {
+        NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
         NQS_CK(cudaFuncSetAttribute(k_conn_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-    // rows of V: every connection inside T, counted against the indices of a sorted copy of T
-    // (V and P are each sorted, their union is not)
-    uint64_t* Tsort;
-    NQS_TRY(sc.get(&Tsort, 2 * (size_t)nT));
-    NQS_TRY(sort_configs(p, sc, T, nT, Tsort, s));
+    }
+    // rows of V: every connection inside T, one probe of the hash of T per excitation. The
+    // indexed pass of nqs_connections (scans of alpha and beta runs) is slower here: T is much
+    // larger than V, so the runs it would scan are long (measured at 16 and 30 orbitals)
     int64_t *rowcnt, *rpV;
     uint32_t* bits;
     NQS_TRY(sc.get(&rowcnt, nV));
     NQS_TRY(sc.get(&rpV, nV + 1));
     NQS_TRY(sc.get(&bits, (size_t)nV * ((p->d.nexc + 31) / 32)));
-    NQS_TRY(conn_count_indexed(p, sc, H, T, nV, Tsort, nT, rowcnt, bits, s));
+    {
+        ProfScope prof_(PROF_CONN_COUNT, s);
+        k_conn_count<<<conn_grid_size(nV), CONN_THREADS, smem, s>>>(p->d, H, (const ulonglong2*)T,
+                                                                     nV, rowcnt, bits);
+    }
+    NQS_CK_LAUNCH();
     NQS_TRY(scan_exclusive_i64(p, sc, rowcnt, rpV, nV, rpV + nV, s));
     int64_t nnzV = 0;
     NQS_CK(cudaMemcpyAsync(&nnzV, rpV + nV, sizeof nnzV, cudaMemcpyDeviceToHost, s));
