@@ -310,7 +310,16 @@ __device__ __forceinline__ uint32_t pair_pos(uint32_t r1, uint32_t r2, uint32_t 
 
 // S: the rows to resolve; R: the sorted set they are resolved against (the array the alpha
 // index's runs point into; R = S for H_SS, the sorted target set for the proxy Hamiltonian)
-__global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P, HashS H,
+// the alpha-beta work of one lane of k_conn_count_ab: its first item in the warp's item range,
+// the start of the alpha run it scans in R (-1: probe the beta singles instead) and the alpha
+// string of its single
+struct __align__(16) OwnerRec {
+    uint32_t first;
+    int32_t start;
+    uint64_t a2;
+};
+
+__global__ void __launch_bounds__(CONN_THREADS, 7) k_conn_count_ab(ProblemDev P, HashS H,
                                                                  AlphaIdx X, BetaIdx Y,
                                                                  const ulonglong2* __restrict__ S,
                                                                  int64_t nS,
@@ -318,9 +327,16 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
                                                                  int64_t* rowcnt,
                                                                  uint32_t* __restrict__ bits) {
     extern __shared__ __align__(16) uint8_t smem[];
+    // per warp, for the alpha-beta block: each lane's work record and the lane of each rank
+    // among the lanes that have work
+    __shared__ OwnerRec orec[CONN_WARPS][32];
+    __shared__ uint8_t orank[CONN_WARPS][32];
     PairTables T = setup_pair_tables(P, (uint16_t*)smem);
     DetCtx* ctx = (DetCtx*)(smem + pair_table_bytes(P)) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    const unsigned lt = lanemask_lt();
+    OwnerRec* rec = orec[threadIdx.x >> 5];
+    uint8_t* rank_lane = orank[threadIdx.x >> 5];
     const uint32_t nexc = (uint32_t)P.nexc;
     const uint32_t nwords = (nexc + 31) / 32;
     const uint32_t o1 = (uint32_t)P.sA, o2 = (uint32_t)(P.sA + P.sB), o3 = o2 + (uint32_t)P.dAA,
@@ -439,28 +455,36 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
             }
             const uint32_t total = __shfl_sync(FULL_MASK, incl, 31);
             const uint32_t excl = incl - w;
+            // work item t belongs to the last lane with work whose first item is at or before t
+            // (those first items are strictly increasing over such lanes). Per chunk of 32
+            // items: the lanes with work starting at or before the chunk, plus a mask of the
+            // starts inside it, give each item the rank of its owner; the owner's record comes
+            // from shared memory.
+            const unsigned has = __ballot_sync(FULL_MASK, w > 0u);
+            if (w > 0u) {
+                OwnerRec o;
+                o.first = excl;
+                o.start = scan ? r.x : -1;
+                o.a2 = a2;
+                rec[lane] = o;
+                rank_lane[__popc(has & lt)] = (uint8_t)lane;
+            }
+            __syncwarp();
             for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+                const int dj = (int)(excl - t0);  // excl, t0 < 2^31
+                const unsigned before = __ballot_sync(FULL_MASK, w > 0u && dj <= 0);
+                const unsigned inside = __reduce_or_sync(
+                    FULL_MASK, (w > 0u && dj > 0 && dj < 32) ? (1u << dj) : 0u);
+                const int c = __popc(before) + __popc(inside & ((2u << lane) - 1u));
+                const int own = rank_lane[c - 1];
+                const OwnerRec o = rec[own];
                 const uint32_t t = t0 + lane;
-                // owner lane of work item t: the first lane whose inclusive prefix exceeds t
-                int lo = 0, hi = 31;
-#pragma unroll
-                for (int step = 0; step < 5; ++step) {
-                    const int mid = (lo + hi) >> 1;
-                    const uint32_t v = __shfl_sync(FULL_MASK, incl, mid);
-                    if (v > t) hi = mid;
-                    else lo = mid + 1;
-                }
-                const int own = lo;
-                const uint32_t base = __shfl_sync(FULL_MASK, excl, own);
-                const int start = __shfl_sync(FULL_MASK, r.x, own);
-                const uint64_t ao = __shfl_sync(FULL_MASK, a2, own);
-                const bool so = __shfl_sync(FULL_MASK, (int)scan, own) != 0;
                 bool hit = false;
                 uint32_t lb = 0;
                 if (t < total) {
-                    const uint32_t k = t - base;
-                    if (so) {
-                        const uint64_t by = __ldg(&R[start + k].y);
+                    const uint32_t k = t - o.first;
+                    if (o.start >= 0) {
+                        const uint64_t by = __ldg(&R[o.start + k].y);
                         const uint64_t d = by ^ x.y;
                         if (__popcll(d) == 2) {
                             const uint64_t jbit = x.y & d, bbit = by & d;
@@ -473,7 +497,7 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
                         const uint32_t xb = k / (uint32_t)P.mb, yb = k - xb * (uint32_t)P.mb;
                         const uint64_t b2 =
                             x.y ^ (1ull << ctx->occB[xb]) ^ (1ull << ctx->virB[yb]);
-                        hit = hash_lookup(H, ao, b2) >= 0;
+                        hit = hash_lookup(H, o.a2, b2) >= 0;
                         lb = k;
                     }
                 }
@@ -484,6 +508,7 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
                 const unsigned mh = __ballot_sync(FULL_MASK, hit);
                 if (lane == 0) cnt += __popc(mh);
             }
+            __syncwarp();  // the records are rewritten by the next round of alpha singles
         }
         if (lane == 0) rowcnt[det] = cnt + 1;  // + diagonal
         __syncwarp();
@@ -493,7 +518,7 @@ __global__ void __launch_bounds__(CONN_THREADS, 4) k_conn_count_ab(ProblemDev P,
 // Pass 2: write each row in canonical order: the diagonal, then the hits. With bits the warp
 // walks the stored ballot words (skipping empty ones) and decodes, probes and evaluates only
 // the hits; without bits it re-enumerates every excitation.
-__global__ void __launch_bounds__(CONN_THREADS) k_conn_fill(ProblemDev P, HashS H,
+__global__ void __launch_bounds__(CONN_THREADS, 6) k_conn_fill(ProblemDev P, HashS H,
                                                              const ulonglong2* __restrict__ S,
                                                              int64_t nS,
                                                              const int64_t* __restrict__ row_ptr,
@@ -546,8 +571,12 @@ __global__ void __launch_bounds__(CONN_THREADS) k_conn_fill(ProblemDev P, HashS 
                 qn = rest;
                 __syncwarp();
             };
+            // the next 32 ballot words are loaded before this chunk's hits are queued and
+            // resolved, so the load's latency overlaps the work
+            uint32_t nxt = lane < nwords ? __ldcs(&wb[lane]) : 0u;
             for (uint32_t w0 = 0; w0 < nwords; w0 += 32) {
-                const uint32_t my = (w0 + lane < nwords) ? wb[w0 + lane] : 0u;
+                const uint32_t my = nxt;
+                nxt = (w0 + 32 + lane < nwords) ? __ldcs(&wb[w0 + 32 + lane]) : 0u;
                 unsigned nz = __ballot_sync(FULL_MASK, my != 0u);
                 while (nz) {
                     const int src = __ffs(nz) - 1;
