@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count(ProblemDev P, Ha
             bool h0 = false, h1 = false;
             for (uint64_t it = 0; v0 && g0 != 0 && it <= H.mask; ++it) {
                 if (g0 == f0) {
-                    const ulonglong2 k = __ldg(&H.keys[s0]);
+                    const ulonglong2 k = __ldg(&H.set[__ldg(&H.idx[s0])]);
                     if (k.x == a0 && k.y == b0) {
                         h0 = true;
                         break;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(CONN_THREADS, 5) k_conn_count(ProblemDev P, Ha
             }
             for (uint64_t it = 0; v1 && g1 != 0 && it <= H.mask; ++it) {
                 if (g1 == f1) {
-                    const ulonglong2 k = __ldg(&H.keys[s1]);
+                    const ulonglong2 k = __ldg(&H.set[__ldg(&H.idx[s1])]);
                     if (k.x == a1 && k.y == b1) {
                         h1 = true;
                         break;
@@ -272,7 +272,7 @@ __device__ __forceinline__ int probe_range(const ProblemDev& P, const PairTables
         bool h0 = false, h1 = false;
         for (uint64_t it = 0; v0 && g0 != 0 && it <= H.mask; ++it) {
             if (g0 == f0) {
-                const ulonglong2 k = __ldg(&H.keys[s0]);
+                const ulonglong2 k = __ldg(&H.set[__ldg(&H.idx[s0])]);
                 if (k.x == a0 && k.y == b0) {
                     h0 = true;
                     break;
@@ -283,7 +283,7 @@ __device__ __forceinline__ int probe_range(const ProblemDev& P, const PairTables
         }
         for (uint64_t it = 0; v1 && g1 != 0 && it <= H.mask; ++it) {
             if (g1 == f1) {
-                const ulonglong2 k = __ldg(&H.keys[s1]);
+                const ulonglong2 k = __ldg(&H.set[__ldg(&H.idx[s1])]);
                 if (k.x == a1 && k.y == b1) {
                     h1 = true;
                     break;

@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                                                           double* __restrict__ vals,
                                                           unsigned long long* examined,
                                                           unsigned long long* __restrict__ cursor,
-                                                          uint64_t cap) {
+                                                          uint64_t cap, int nparts) {
     constexpr bool EMIT = (MODE & 1) != 0;
     constexpr bool PTM = (MODE & 2) != 0;
     constexpr bool APPEND = (MODE & 4) != 0;
@@ -364,8 +364,17 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
         __syncwarp();
         qn = rest;
     };
-    for (int64_t det = (int64_t)blockIdx.x * HB_WARPS + (threadIdx.x >> 5); det < nS;
-         det += (int64_t)gridDim.x * HB_WARPS) {
+    // work items: (x, part) with part < nparts; part p takes the singles (p = 0) and the p-th of
+    // every nparts chunks of 32 hole pairs, so the lists of one x with much work are walked by
+    // several warps at once (count and append modes; the emit modes write each x's pairs in
+    // order from offs[x] and take nparts = 1). Counts of several parts are added atomically
+    // into cnt, which the caller zeroes.
+    if (EMIT) nparts = 1;  // emit and append modes: one warp per x, without the split's cost
+    const int64_t nitems = nS * (int64_t)nparts;
+    for (int64_t item = (int64_t)blockIdx.x * HB_WARPS + (threadIdx.x >> 5); item < nitems;
+         item += (int64_t)gridDim.x * HB_WARPS) {
+        const int64_t det = nparts == 1 ? item : item / nparts;
+        const int part = nparts == 1 ? 0 : (int)(item - det * nparts);
         const ulonglong2 x = S[det];
         const double py = psi[det];
         const double ap = fabs(py);
@@ -374,7 +383,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
         // m = |H| |psi| >= eps fails for every coupling when |psi| = 0 < eps, and when psi is
         // not a number: nothing to do for this x
         if (!(ap >= 0.0) || (ap == 0.0 && eps > 0.0)) {
-            if (!EMIT && lane == 0) cnt[det] = 0;
+            if (!EMIT && lane == 0 && nparts == 1) cnt[det] = 0;
             continue;
         }
         fill_ctx(P, x.x, x.y, ctx, lane);
@@ -398,7 +407,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
         };
         // singles: every one, with its exact element
         const HbCutFx cutfx = hb_cut_fx(cut, P);
-        for (uint32_t r0 = 0; r0 < nsing; r0 += 32) {
+        for (uint32_t r0 = 0; part == 0 && r0 < nsing; r0 += 32) {
             const uint32_t e = r0 + lane;
             bool take = false;
             Exc ex;
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             }
             keep(take, ex.a2, ex.b2, m);
         }
-        if (!(APPEND && PTM)) tested += nsing;
+        if (!(APPEND && PTM) && part == 0) tested += nsing;
         // doubles: three groups of hole pairs; each lane tests the head of one list. A list is
         // walked 32 entries at a time; the entries that pass the cut and whose particles are
         // empty in x are queued (hole and particle orbitals and group in one word, with the
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                              : grp == 1 ? (int)choose2(P.nb) : P.na * P.nb;
             const int L = grp < 2 ? T.Lss : T.Los;
             if (L == 0) continue;
-            for (int p0 = 0; p0 < npairs; p0 += 32) {
+            for (int p0 = 32 * part; p0 < npairs; p0 += 32 * nparts) {
                 const int pi = p0 + lane;
                 int i = 0, j = 0;
                 int64_t base = 0;
@@ -564,7 +573,10 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
             }
         }
         if (cn > 0) drain(cn);
-        if (!EMIT && lane == 0) cnt[det] = run;
+        if (!EMIT && lane == 0) {
+            if (nparts == 1) cnt[det] = run;
+            else atomicAdd((unsigned long long*)&cnt[det], (unsigned long long)run);
+        }
         if (examined && lane == 0) atomicAdd(examined, tested);
         __syncwarp();
     }
@@ -596,6 +608,11 @@ __global__ void k_hb_heads(const K* __restrict__ keys, int64_t n, uint32_t* __re
          i += (int64_t)gridDim.x * blockDim.x)
         f[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
 }
+
+// parts per configuration for the count passes: with few configurations (the strided samples
+// that size the one-traversal buffers) the warps that walk the heaviest ones set the duration,
+// so their lists are split over 8 warps; with many, one warp per configuration
+static int hb_count_parts(int64_t n) { return n <= 32768 ? 8 : 1; }
 
 static unsigned hb_grid(int64_t nS) {
     int64_t g = (nS + HB_WARPS - 1) / HB_WARPS;
@@ -653,11 +670,13 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
         k_hb_gather_stride<<<grid_for(ns, 256), 256, 0, s>>>((const ulonglong2*)dets, psi, ns,
                                                               stride, ds, ps);
         NQS_CK_LAUNCH();
+        const int np = hb_count_parts(ns);
+        if (np > 1) NQS_CK(cudaMemsetAsync(c1, 0, ns * sizeof(int64_t), s));
         {
             ProfScope prof_(PROF_HB_SELECT, s);
-            k_hb_select<HB_COUNT, K><<<hb_grid(ns), HB_THREADS, smem, s>>>(
+            k_hb_select<HB_COUNT, K><<<hb_grid(ns * np), HB_THREADS, smem, s>>>(
                 P, H, T, ds, ps, ns, eps, 1, 0, c1, nullptr, nullptr, nullptr, nullptr, nullptr,
-                0);
+                0, np);
         }
         NQS_CK_LAUNCH();
         NQS_TRY(scan_exclusive_i64(p, es, c1, o1, ns, t1, s));
@@ -687,7 +706,7 @@ static int hb_run(nqs_problem* p, Scratch& sc, const HashS& H, const HbTab& T,
             ProfScope prof_(PROF_HB_SELECT, s);
             k_hb_select<HB_APPEND, K><<<hb_grid(nS), HB_THREADS, smem_a, s>>>(
                 P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, nullptr, nullptr, keys,
-                vals, examined, cursor, (uint64_t)cap);
+                vals, examined, cursor, (uint64_t)cap, 1);
         }
         NQS_CK_LAUNCH();
         unsigned long long nc = 0, nexam = 0;
@@ -762,15 +781,17 @@ static int hb_pt2_pass_k(nqs_problem* p, const HbTab& T, const HashS& H, const u
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     if (cnt) {
+        const int np = hb_count_parts(nS);
+        if (np > 1) NQS_CK(cudaMemsetAsync(cnt, 0, nS * sizeof(int64_t), s));
         ProfScope prof_(PROF_PT2_COUNT, s);
-        k_hb_select<PT_COUNT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
+        k_hb_select<PT_COUNT, K><<<hb_grid(nS * np), HB_THREADS, smem, s>>>(
             P, H, T, (const ulonglong2*)dets, psi, nS, eps, B, bucket, cnt, nullptr, nullptr,
-            nullptr, nullptr, nullptr, 0);
+            nullptr, nullptr, nullptr, 0, np);
     } else {
         ProfScope prof_(PROF_PT2_EMIT, s);
         k_hb_select<PT_EMIT, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
             P, H, T, (const ulonglong2*)dets, psi, nS, eps, B, bucket, nullptr, offs, (K*)keys,
-            vals, nullptr, nullptr, 0);
+            vals, nullptr, nullptr, 0, 1);
     }
     NQS_CK_LAUNCH();
     return NQS_OK;
@@ -810,7 +831,7 @@ static int hb_pt2_append_k(nqs_problem* p, const HbTab& T, const HashS& H, const
         ProfScope prof_(PROF_PT2_EMIT, s);
         k_hb_select<PT_APPEND, K><<<hb_grid(nS), HB_THREADS, smem, s>>>(
             P, H, T, (const ulonglong2*)dets, psi, nS, eps, 1, 0, nullptr, nullptr, (K*)keys,
-            vals, nullptr, cursor_dev, (uint64_t)cap);
+            vals, nullptr, cursor_dev, (uint64_t)cap, 1);
     }
     NQS_CK_LAUNCH();
     return NQS_OK;

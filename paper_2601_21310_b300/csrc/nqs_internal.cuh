@@ -179,10 +179,10 @@ __host__ __device__ __forceinline__ uint64_t det_hash(uint64_t a, uint64_t b) {
 // ------------------------------------------------------------------------------------------
 #define NQS_EMPTY_WORD 0xffffffffffffffffull
 struct HashS {
-    const ulonglong2* keys;  // [cap] {a, b}
-    const int32_t* idx;      // [cap] position in S
-    const uint16_t* fp;      // [cap] fingerprint, 0 = empty slot
-    uint64_t mask;           // cap - 1
+    const ulonglong2* set;  // the hashed configurations {a, b}, in their own order
+    const int32_t* idx;     // [cap] position in set of the slot's configuration
+    const uint16_t* fp;     // [cap] fingerprint, 0 = empty slot
+    uint64_t mask;          // cap - 1
 };
 
 // Hash of a configuration for this table (independent of the bucket hash det_hash, which is
@@ -208,9 +208,11 @@ __device__ __forceinline__ int32_t hash_lookup_h(const HashS& H, uint64_t a, uin
     for (uint64_t it = 0; it <= H.mask; ++it) {
         const uint16_t v = __ldg(&H.fp[slot]);
         if (v == 0) return -1;
-        if (v == f) {
-            const ulonglong2 k = __ldg(&H.keys[slot]);
-            if (k.x == a && k.y == b) return __ldg(&H.idx[slot]);
+        if (v == f) {  // the key is compared in the set itself (L2-resident, unlike a copy
+                       // of the keys per slot)
+            const int32_t j = __ldg(&H.idx[slot]);
+            const ulonglong2 k = __ldg(&H.set[j]);
+            if (k.x == a && k.y == b) return j;
         }
         slot = (slot + 1) & H.mask;
     }

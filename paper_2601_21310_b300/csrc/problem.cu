@@ -383,10 +383,9 @@ int validate_dets(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS,
 // ------------------------------------------------------------------------------------------
 // hash table of S
 // ------------------------------------------------------------------------------------------
-__global__ void k_hash_clear(ulonglong2* keys, int32_t* idx, uint16_t* fp, uint64_t cap) {
+__global__ void k_hash_clear(int32_t* idx, uint16_t* fp, uint64_t cap) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        keys[i] = make_ulonglong2(NQS_EMPTY_WORD, NQS_EMPTY_WORD);
         idx[i] = -1;
         fp[i] = 0;
     }
@@ -404,14 +403,12 @@ __global__ void k_hash_insert(const ulonglong2* S, int64_t n, int32_t* idx, uint
     }
 }
 
-__global__ void k_hash_keys(const ulonglong2* S, const int32_t* idx, ulonglong2* keys,
-                            uint16_t* fp, uint64_t cap) {
+__global__ void k_hash_fp(const ulonglong2* S, const int32_t* idx, uint16_t* fp, uint64_t cap) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < cap;
          i += (uint64_t)gridDim.x * blockDim.x) {
         int32_t k = idx[i];
         if (k >= 0) {
             const ulonglong2 x = S[k];
-            keys[i] = x;
             fp[i] = hash_fingerprint(s_hash(x.x, x.y));
         }
     }
@@ -427,19 +424,17 @@ int hash_build(nqs_problem* p, Scratch& sc, const uint64_t* dets, int64_t nS, Ha
                           : (nS <= ((int64_t)1 << 26) ? 8 : 4);
     uint64_t cap = 1024;
     while (cap < load * (uint64_t)nS) cap <<= 1;
-    ulonglong2* keys;
     int32_t* idx;
     uint16_t* fp;
-    NQS_TRY(sc.get(&keys, cap));
     NQS_TRY(sc.get(&idx, cap));
     NQS_TRY(sc.get(&fp, cap));
-    k_hash_clear<<<grid_for(cap, 256), 256, 0, s>>>(keys, idx, fp, cap);
+    k_hash_clear<<<grid_for(cap, 256), 256, 0, s>>>(idx, fp, cap);
     NQS_CK_LAUNCH();
     k_hash_insert<<<grid_for(nS, 256), 256, 0, s>>>((const ulonglong2*)dets, nS, idx, cap - 1);
     NQS_CK_LAUNCH();
-    k_hash_keys<<<grid_for(cap, 256), 256, 0, s>>>((const ulonglong2*)dets, idx, keys, fp, cap);
+    k_hash_fp<<<grid_for(cap, 256), 256, 0, s>>>((const ulonglong2*)dets, idx, fp, cap);
     NQS_CK_LAUNCH();
-    out->keys = keys;
+    out->set = (const ulonglong2*)dets;
     out->idx = idx;
     out->fp = fp;
     out->mask = cap - 1;
