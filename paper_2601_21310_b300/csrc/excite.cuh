@@ -456,30 +456,22 @@ __device__ __forceinline__ double exc_element(const ProblemDev& P, const DetCtx&
 // The element of a single (x.cls <= 1) in fixed point, without its sign: the integer sum of the
 // same terms as exc_element, each table entry rounded once to the grid 2^-P.sfx_e, so it is
 // exact and differs from exc_element's FP64 sum by at most 49 half-units of the grid plus that
-// sum's own rounding (at most 48 ulps of hoff_max).
-__device__ __forceinline__ long long single_element_fx(const ProblemDev& P, const DetCtx& c,
-                                                       const Exc& x) {
-    const int n = P.norb;
-    const size_t base = ((size_t)x.i * n + x.a) * n;
-    long long v = __ldg(&P.hfx_off[x.i * n + x.a]);
+// sum's own rounding (at most 48 ulps of hoff_max). The sums over the occupied orbitals j of the
+// configuration (wA, wB) come from the byte tables, one entry per byte of each string; the
+// same-spin sum there includes j = i, whose term is subtracted (integer sums: exact in any
+// grouping).
+__device__ __forceinline__ long long single_element_fx(const ProblemDev& P, uint64_t wA,
+                                                       uint64_t wB, const Exc& x) {
+    const int n = P.norb, nb = P.nbytes;
+    const size_t ia = (size_t)x.i * n + x.a;
     const bool alpha = x.cls == 0;
-    for (int k = 0; k < P.na; ++k) {
-        const int j = c.occA[k];
-        if (alpha) {
-            if (j == x.i) continue;
-            v += __ldg(&P.TDfx[base + j]);
-        } else {
-            v += __ldg(&P.TJfx[base + j]);
-        }
-    }
-    for (int k = 0; k < P.nb; ++k) {
-        const int j = c.occB[k];
-        if (!alpha) {
-            if (j == x.i) continue;
-            v += __ldg(&P.TDfx[base + j]);
-        } else {
-            v += __ldg(&P.TJfx[base + j]);
-        }
+    const uint64_t ws = alpha ? wA : wB, wo = alpha ? wB : wA;  // same spin, other spin
+    const long long* same = P.SDt + ia * nb * 256;
+    const long long* other = P.SJt + ia * nb * 256;
+    long long v = __ldg(&P.hfx_off[ia]) - __ldg(&P.TDfx[ia * n + x.i]);
+    for (int k = 0; k < nb; ++k) {
+        v += __ldg(&same[k * 256 + (int)((ws >> (8 * k)) & 255ull)]);
+        v += __ldg(&other[k * 256 + (int)((wo >> (8 * k)) & 255ull)]);
     }
     return v;
 }

@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(HB_THREADS, 4) k_hb_select(ProblemDev P, HashS
                 decode_exc(P, PT, *ctx, x.x, x.y, e, ex);
                 if (PTM) {
                     // the element in exact fixed point; the FP64 element only near the cut
-                    const long long F = single_element_fx(P, *ctx, ex);
+                    const long long F = single_element_fx(P, x.x, x.y, ex);
                     const long long aF = F < 0 ? -F : F;
                     bool ok;
                     double hv = 0.0;

@@ -76,6 +76,11 @@ struct ProblemDev {
     const long long* TDfx;
     const long long* hfx_off;  // h_pq
     int sfx_e;
+    // byte tables of those terms per single: SDt[i][a][k][u] = sum of TDfx[i][a][j] over the
+    // orbitals j = 8k + bit of the set bits of byte value u (j < norb), SJt the same of TJfx;
+    // an element's sum over an occupied set is then one entry per byte of its string
+    const long long* SDt;
+    const long long* SJt;
 };
 
 struct nqs_problem {
@@ -86,6 +91,7 @@ struct nqs_problem {
     long long* fx;  // hfx | JKfx | Jfx
     long long* bt;  // Dt | Xt | Yt
     long long* sfx; // TJfx | TDfx | hfx_off
+    long long* sbt; // SDt | SJt
     cudaMemPool_t pool;  // library-owned stream-ordered pool for per-call scratch
     int* err_word;       // device: set by a kernel whose bounded wait timed out
     double* hb_val;      // heat-bath integral tables (hb.cu), built on first use

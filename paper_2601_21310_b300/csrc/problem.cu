@@ -88,6 +88,25 @@ __global__ void k_fx_tables(int64_t n3, int n, const double* TJ, const double* T
     }
 }
 
+// entry t of SDt | SJt: the sum of the fixed-point single terms over the orbitals of one byte
+__global__ void k_single_byte_tables(int n, int nb, const long long* TDfx, const long long* TJfx,
+                                     long long* out) {
+    const int64_t per = (int64_t)n * n * nb * 256;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 2 * per;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const long long* X = t < per ? TDfx : TJfx;
+        const int64_t r = t < per ? t : t - per;
+        const int u = (int)(r % 256), k = (int)((r / 256) % nb);
+        const int64_t ia = r / (256 * (int64_t)nb);  // i * n + a
+        long long v = 0;
+        for (int bit = 0; bit < 8; ++bit) {
+            const int j = 8 * k + bit;
+            if (((u >> bit) & 1) && j < n) v += X[ia * n + j];
+        }
+        out[t] = v;
+    }
+}
+
 __global__ void k_tables(int n, const double* eri, double* J, double* K, double* TJ, double* TD) {
     int64_t total = (int64_t)n * n * n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -278,6 +297,17 @@ extern "C" int nqs_problem_create(int norb, int nalpha, int nbeta, const double*
         d.hfx_off = p->sfx + 2 * n3;
         // byte tables
         const int nb = (n + 7) / 8;
+        const int64_t nsb = (int64_t)n * n * nb * 256;
+        if (cudaMalloc(&p->sbt, 2 * nsb * sizeof(long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NQS_ERR_OOM);
+        }
+        k_single_byte_tables<<<grid_for(2 * nsb, 256), 256>>>(n, nb, d.TDfx, d.TJfx, p->sbt);
+        nqs_note_launch();
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+            return fail(NQS_ERR_CUDA);
+        d.SDt = p->sbt;
+        d.SJt = p->sbt + nsb;
         const size_t nD = (size_t)nb * 256, nX = (size_t)nb * (nb - 1) / 2 * 65536,
                      nY = (size_t)nb * nb * 65536;
         if (cudaMalloc(&p->bt, (nD + nX + nY) * sizeof(long long)) != cudaSuccess) {
@@ -310,6 +340,7 @@ extern "C" int nqs_problem_destroy(nqs_problem* p) {
     cudaFree(p->fx);
     cudaFree(p->bt);
     cudaFree(p->sfx);
+    cudaFree(p->sbt);
     cudaFree(p->hb_val);
     cudaFree(p->hb_code);
     if (p->pool) cudaMemPoolDestroy(p->pool);
