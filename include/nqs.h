@@ -345,8 +345,7 @@ int nqs_autotune_entries(int* M, int* N, int* K, int* width, int capacity);
  * nqs_last_error()). Every GPU that loads the library holds the array until process exit. The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current and keeps it for later calls on that device, which assumes the device's
- * primary context lives until the process exits (no cudaDeviceReset in between); make that
- * first call before any stream capture. *nnz (host) receives the number of nonzeros; if it
+ * primary context lives until the process exits (no cudaDeviceReset in between). *nnz (host) receives the number of nonzeros; if it
  * exceeds capacity the call returns NQS_ERR_ARG without writing col/val, so the caller can size
  * the buffers and call again. All calls share the static array, which keeps the previous
  * call's contents (what must start at zero is cleared on every call): calls that overlap on

@@ -11,9 +11,8 @@
 //
 // The host cannot use the array's name as a device address (in host code it names a host-side
 // stand-in), so the first call on each device, with that device current, looks the address up
-// with cudaGetSymbolAddress and caches it; make that first call before any stream capture. The
-// cache assumes the device's primary context lives until the process exits (a cudaDeviceReset
-// would leave a stale address behind). The call synchronises its stream: it reads the number
+// with cudaGetSymbolAddress and caches it. The cache assumes the device's primary context
+// lives until the process exits (a cudaDeviceReset would leave a stale address behind). The call synchronises its stream: it reads the number
 // of nonzeros back to the host before writing the columns.
 // All calls share the array and it keeps the previous call's contents: everything that must
 // start from zero is cleared on every call, and calls whose work overlaps on the GPU (two
