@@ -177,13 +177,13 @@ __host__ __device__ __forceinline__ uint64_t det_hash(uint64_t a, uint64_t b) {
 
 // ------------------------------------------------------------------------------------------
 // hash table of S: open addressing, linear probing, capacity a power of two >= 16|S| (8|S|
-// above 2^22 configurations, 4|S| above 2^26). Next to the 16-byte keys each slot has a 2-byte
-// fingerprint (16 bits of the hash, low bit forced to 1; 0 = empty): a probe reads the
-// fingerprints (32 slots per 64 bytes; 32 MB for 16 M slots, so they stay in L2 while the keys
-// may not) and touches a key only when its fingerprint matches. Most probes of the method miss,
-// and a miss then never reads a key; at these load factors most misses end at the first slot.
+// above 2^22 configurations, 4|S| above 2^26). Each slot holds the configuration's position in
+// S and a 2-byte fingerprint (16 bits of the hash, low bit forced to 1; 0 = empty): a probe
+// reads the fingerprints (32 slots per 64 bytes; 32 MB for 16 M slots, so they stay in L2) and
+// only on a match reads the position and compares the key in S itself. Most probes of the method
+// miss, and a miss then never reads a key; at these load factors most misses end at the first
+// slot.
 // ------------------------------------------------------------------------------------------
-#define NQS_EMPTY_WORD 0xffffffffffffffffull
 struct HashS {
     const ulonglong2* set;  // the hashed configurations {a, b}, in their own order
     const int32_t* idx;     // [cap] position in set of the slot's configuration
