@@ -1023,28 +1023,68 @@ int net_backward(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f, 
 // transposed ([H][ldM], ldM = |S| rounded up to 8 for 16-byte TMA strides).
 // ------------------------------------------------------------------------------------------
 // dst[c][r] = src[r][c] for a bf16 matrix, 32x32 tiles through shared memory
-__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ src, int64_t R, int64_t Cn,
-                                 int64_t lds, __nv_bfloat16* __restrict__ dst, int64_t ldd) {
-    __shared__ unsigned short tile[32][33];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+// dst[c][r] = src[r][c] for r < R, c < Cn: 64 x 64 tiles through shared memory. Each thread
+// moves 8 consecutive elements (16 bytes) on the global side when the row is whole and aligned
+// (vec), else element by element; the shared tile's row stride of 66 elements (33 words) keeps
+// the column reads of the write-out to 2-way bank conflicts.
+#define TR_T 64
+#define TR_LD 66
+__global__ void __launch_bounds__(256) k_transpose_bf16(const __nv_bfloat16* __restrict__ src,
+                                                        int64_t R, int64_t Cn, int64_t lds,
+                                                        __nv_bfloat16* __restrict__ dst,
+                                                        int64_t ldd, int vec) {
+    __shared__ __align__(16) unsigned short tile[TR_T][TR_LD];
+    const int64_t r0 = (int64_t)blockIdx.y * TR_T, c0 = (int64_t)blockIdx.x * TR_T;
     const unsigned short* S = (const unsigned short*)src;
     unsigned short* D = (unsigned short*)dst;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        int64_t r = r0 + i, c = c0 + threadIdx.x;
-        tile[i][threadIdx.x] = (r < R && c < Cn) ? S[r * lds + c] : (unsigned short)0;
+    for (int t = threadIdx.x; t < TR_T * 8; t += 256) {
+        const int rr = t >> 3, c8 = (t & 7) * 8;
+        const int64_t r = r0 + rr, c = c0 + c8;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (r < R) {
+            if (vec && c + 8 <= Cn) {
+                const uint4 v = __ldcs((const uint4*)(S + r * lds + c));
+                w[0] = v.x;
+                w[1] = v.y;
+                w[2] = v.z;
+                w[3] = v.w;
+            } else {
+                for (int j = 0; j < 8; ++j)
+                    if (c + j < Cn) w[j >> 1] |= (uint32_t)S[r * lds + c + j] << (16 * (j & 1));
+            }
+        }
+        uint32_t* row = (uint32_t*)&tile[rr][c8];  // 4-byte aligned: TR_LD and c8 are even
+        row[0] = w[0];
+        row[1] = w[1];
+        row[2] = w[2];
+        row[3] = w[3];
     }
     __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        int64_t c = c0 + i, r = r0 + threadIdx.x;
-        if (c < Cn && r < R) D[c * ldd + r] = tile[threadIdx.x][i];
+    for (int t = threadIdx.x; t < TR_T * 8; t += 256) {
+        const int cc = t >> 3, r8 = (t & 7) * 8;
+        const int64_t c = c0 + cc, r = r0 + r8;
+        if (c >= Cn) continue;
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            w[k] = (uint32_t)tile[r8 + 2 * k][cc] | ((uint32_t)tile[r8 + 2 * k + 1][cc] << 16);
+        if (vec && r + 8 <= R) {
+            *(uint4*)(D + c * ldd + r) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            for (int j = 0; j < 8; ++j)
+                if (r + j < R) D[c * ldd + r + j] = (unsigned short)(w[j >> 1] >> (16 * (j & 1)));
+        }
     }
 }
 
 static int transpose_bf16(const void* src, int64_t R, int64_t Cn, int64_t lds, void* dst,
                           int64_t ldd, cudaStream_t s) {
-    dim3 grid((unsigned)((Cn + 31) / 32), (unsigned)((R + 31) / 32));
-    k_transpose_bf16<<<grid, dim3(32, 8), 0, s>>>((const __nv_bfloat16*)src, R, Cn, lds,
-                                                  (__nv_bfloat16*)dst, ldd);
+    dim3 grid((unsigned)((Cn + TR_T - 1) / TR_T), (unsigned)((R + TR_T - 1) / TR_T));
+    // 16-byte global accesses when both matrices' rows start on 16-byte boundaries
+    const int vec = (((uintptr_t)src | (uintptr_t)dst) & 15) == 0 && (lds & 7) == 0 &&
+                    (ldd & 7) == 0;
+    k_transpose_bf16<<<grid, 256, 0, s>>>((const __nv_bfloat16*)src, R, Cn, lds,
+                                          (__nv_bfloat16*)dst, ldd, vec);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }
