@@ -821,6 +821,19 @@ int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
 // the tile width a shape gets without tuning
 static int heuristic_bn_shape(int N) { return N <= 64 ? 64 : (N <= 128 ? 128 : 256); }
 
+// K splits of a plain FP32-output GEMM: enough units to fill the GPU, and no unit longer than
+// TC_MAX_UNIT_KB k-blocks. The CTAs that work on one split read the same K window of A and B and
+// share it in L2 only while they stay close in K; over long ranges they drift apart and the
+// operands come from DRAM again (the weight gradients over 2^20 configurations ran at a third of
+// the rate their 2^16 counterparts reach per FLOP).
+#define TC_MAX_UNIT_KB 512
+static int tc_split_count(int tiles, int nkb) {
+    int splits = 1;
+    while (tiles * splits < 148 && splits * 2 <= nkb && splits < 64) splits *= 2;
+    while (nkb / splits > TC_MAX_UNIT_KB && splits * 2 <= nkb && splits < 64) splits *= 2;
+    return splits;
+}
+
 // launch with a given tile width
 static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
     CUtensorMap ta, tb;
@@ -846,9 +859,7 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
     const int tiles = ((g.N + BN - 1) / BN) * ((g.M + 127) / 128);
     const int nkb = (g.K + TC_BK - 1) / TC_BK;
     int splits = 1;
-    if (g.epi == EPI_STORE && !g.CT && !g.c_bf16) {
-        while (tiles * splits < 148 && splits * 2 <= nkb && splits < 64) splits *= 2;
-    }
+    if (g.epi == EPI_STORE && !g.CT && !g.c_bf16) splits = tc_split_count(tiles, nkb);
     if (splits > 1) {
         NQS_TRY(sc.get(&a.partial, (size_t)splits * g.M * g.N));
         // ceil split so that no split is empty
@@ -959,8 +970,7 @@ int tc_group_set_create(const TcGemm* gs, int n, int BN, TcGroupSet** out) {
         const int tiles_ref = ((g.N + bref - 1) / bref) * ((g.M + 127) / 128);
         const int nkb = (g.K + TC_BK - 1) / TC_BK;
         int splits = 1;
-        if (g.epi == EPI_STORE && !g.CT && !g.c_bf16)
-            while (tiles_ref * splits < 148 && splits * 2 <= nkb && splits < 64) splits *= 2;
+        if (g.epi == EPI_STORE && !g.CT && !g.c_bf16) splits = tc_split_count(tiles_ref, nkb);
         if (splits > 1) {
             const int per = (nkb + splits - 1) / splits;
             splits = (nkb + per - 1) / per;
