@@ -824,9 +824,12 @@ static int heuristic_bn_shape(int N) { return N <= 64 ? 64 : (N <= 128 ? 128 : 2
 // K splits of a plain FP32-output GEMM: enough units to fill the GPU, and no unit longer than
 // TC_MAX_UNIT_KB k-blocks. The CTAs that work on one split read the same K window of A and B and
 // share it in L2 only while they stay close in K; over long ranges they drift apart and the
-// operands come from DRAM again (the weight gradients over 2^20 configurations ran at a third of
-// the rate their 2^16 counterparts reach per FLOP).
+// operands come from DRAM again (the weight gradients over 2^20 configurations: the step's
+// GEMMs took 28.4 ms with units of 4096 k-blocks, 26.5 ms with at most 512; one wave of
+// longer units, 148 / tiles splits, measured 28.4 ms on three boxes and 24.5 ms on one).
 #define TC_MAX_UNIT_KB 512
+static int single_bn_for(const TcGemm& g);  // the tile width the single GEMM runs g with
+
 static int tc_split_count(int tiles, int nkb) {
     int splits = 1;
     while (tiles * splits < 148 && splits * 2 <= nkb && splits < 64) splits *= 2;
@@ -965,8 +968,9 @@ int tc_group_set_create(const TcGemm* gs, int n, int BN, TcGroupSet** out) {
         a.aux = g.aux;
         a.ld_aux = g.ld_aux;
         a.err = g.err;
-        // K splits as the single GEMM would choose them for this shape (same partial sums)
-        const int bref = heuristic_bn_shape(g.N);
+        // K splits as the single GEMM chooses them for this shape, with the tile width it uses
+        // (tuned or not), so both give the same partial sums
+        const int bref = single_bn_for(g);
         const int tiles_ref = ((g.N + bref - 1) / bref) * ((g.M + 127) / 128);
         const int nkb = (g.K + TC_BK - 1) / TC_BK;
         int splits = 1;
@@ -1090,6 +1094,13 @@ bool g_autotune = false;
 
 int heuristic_bn(int N) { return heuristic_bn_shape(N); }
 }  // namespace
+
+static int single_bn_for(const TcGemm& g) {
+    const TuneKey key{g.M, g.N, g.K, g.epi, (g.c_bf16 ? 1 : 0) | (g.CT ? 2 : 0)};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    return it != g_tuned.end() ? it->second : heuristic_bn_shape(g.N);
+}
 
 int tc_autotune_on() { return g_autotune ? 1 : 0; }
 
