@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(CONN_THREADS, 6) k_conn_fill(ProblemDev P, Has
                 if ((uint32_t)lane < nt) {
                     Exc ex;
                     decode_exc(P, T, *ctx, x.x, x.y, qu[lane], ex);
-                    col[run + lane] = hash_lookup(H, ex.a2, ex.b2);
+                    col[run + lane] = hash_lookup_member(H, ex.a2, ex.b2);  // a hit: in S
                     val[run + lane] = exc_element(P, *ctx, ex);
                 }
                 run += nt;

@@ -229,6 +229,28 @@ __device__ __forceinline__ int32_t hash_lookup(const HashS& H, uint64_t a, uint6
     return hash_lookup_h(H, a, b, s_hash(a, b));
 }
 
+// position of (a, b) when the caller knows it is in the set (a hit of the count pass): the probe
+// sequence up to the first empty slot holds its slot, so a single fingerprint match there is
+// that slot and no key needs to be read; several matches fall back to comparing keys
+__device__ __forceinline__ int32_t hash_lookup_member(const HashS& H, uint64_t a, uint64_t b) {
+    const uint64_t h = s_hash(a, b);
+    uint64_t slot = hash_slot(h, H.mask);
+    const uint16_t f = hash_fingerprint(h);
+    uint64_t first = 0;
+    int matches = 0;
+    for (uint64_t it = 0; it <= H.mask; ++it) {
+        const uint16_t v = __ldg(&H.fp[slot]);
+        if (v == 0) break;
+        if (v == f) {
+            if (matches == 0) first = slot;
+            ++matches;
+        }
+        slot = (slot + 1) & H.mask;
+    }
+    if (matches == 1) return __ldg(&H.idx[first]);
+    return hash_lookup_h(H, a, b, h);
+}
+
 // the H_SS enumeration kernels (connect.cu) and their launch shape
 #define CONN_THREADS 256
 #define CONN_WARPS (CONN_THREADS / 32)
