@@ -189,3 +189,54 @@ def test_amplitudes_beyond_one_micro_batch():
     rla, rsg = O.amplitudes(O.Net(net), T[rows])
     assert np.array_equal(sg[rows], rsg)
     assert np.abs(la[rows] - rla).max() < 1e-9
+
+
+def test_cr2_48e42o_full_size_pt2_unique_sampled(cr2_48):
+    """42 orbitals, |S| = 2^20: one hash bucket of 4096 of the deduplicated external set of Eq.
+    (pt2_correction) at full size, checked on samples the oracle computes one by one: for sampled
+    x' of the GPU's set, x' is outside S, in the bucket, and c(x') = sum over the members y of S
+    connected to x' of H_x'y psi_y (oracle elements); and sampled excitations x' of members of S
+    that are outside S and in the bucket appear in the GPU's set."""
+    N, p, P, dets = cr2_48
+    S = p.S
+    rng = np.random.default_rng(21)
+    psi = rng.normal(size=len(S))
+    B, b = 4096, 0
+    keys, c = N.pt2_unique(P, dets, torch.from_numpy(psi).cuda(), B, b)
+    keys, c = keys.cpu().numpy(), c.cpu().numpy()
+    assert len(keys) > 1000
+    # ascending by (a, b), unique
+    assert np.all((keys[1:, 0] > keys[:-1, 0]) |
+                  ((keys[1:, 0] == keys[:-1, 0]) & (keys[1:, 1] > keys[:-1, 1])))
+    sh = 42
+    index = {int(a) << sh | int(bb): i for i, (a, bb) in enumerate(S.tolist())}
+
+    def in_set(ya, yb):  # keys ascending by (a, b)
+        lo = np.searchsorted(keys[:, 0], np.uint64(ya), "left")
+        hi = np.searchsorted(keys[:, 0], np.uint64(ya), "right")
+        return bool(np.any(keys[lo:hi, 1] == np.uint64(yb)))
+
+    for k in rng.choice(len(keys), 24, replace=False):
+        xa, xb = int(keys[k, 0]), int(keys[k, 1])
+        assert (xa << sh | xb) not in index
+        assert O.bucket(xa, xb, B) == b
+        ref, scale = 0.0, 0.0
+        for ya, yb in O.excitations(42, xa, xb).tolist():
+            j = index.get(int(ya) << sh | int(yb))
+            if j is None:
+                continue
+            v, _ = O.element(42, p.h, p.eri, (ya, yb), (xa, xb))
+            ref += v * psi[j]
+            scale += abs(v * psi[j])
+        assert abs(c[k] - ref) <= 1e-12 * scale + 1e-300, (k, c[k], ref)
+    # completeness: outside-S excitations of sampled members of S, in the bucket, are present
+    found = 0
+    for r in rng.choice(len(S), 64, replace=False):
+        ex = O.excitations(42, int(S[r, 0]), int(S[r, 1]))
+        for ya, yb in ex[rng.choice(len(ex), 2000, replace=False)].tolist():
+            key = int(ya) << sh | int(yb)
+            if key in index or O.bucket(ya, yb, B) != b:
+                continue
+            assert in_set(ya, yb), (ya, yb)
+            found += 1
+    assert found > 0
