@@ -281,6 +281,16 @@ int nqs_pt2_unique(nqs_problem* problem, const uint64_t* dets, const double* psi
                    int buckets, int bucket, uint64_t* dets_out, double* c_out, int64_t capacity,
                    int64_t* n_unique, nqs_stream_t stream);
 
+/* The same set for the screened form of nqs_pt2 (opts->eps_pt2 = eps_pt2 > 0, Sec. 3.3): the x'
+ * reached by at least one contribution with |H_x'y psi_y| >= eps_pt2 (psi as passed), and c(x')
+ * the sum of those contributions only. Emission by the sorted-integral walk of nqs_pt2 for the
+ * one bucket. Arguments, output and errors as nqs_pt2_unique; eps_pt2 <= 0 or not finite:
+ * NQS_ERR_ARG. */
+int nqs_pt2_unique_screened(nqs_problem* problem, const uint64_t* dets, const double* psi,
+                            int64_t nS, double eps_pt2, int buckets, int bucket, uint64_t* dets_out,
+                            double* c_out, int64_t capacity, int64_t* n_unique,
+                            nqs_stream_t stream);
+
 /* ---- batched evaluation of many independent problems ------------------------------------ */
 typedef struct nqs_batch nqs_batch; /* opaque */
 

@@ -825,6 +825,16 @@ int orc_pt2_unique(int norb, const double* h, const double* eri, const uint64_t*
                     c_out);
 }
 
+/* the same set for the screened sum (contributions with |H_x'y| |psi_y| >= eps kept, Sec. 3.3):
+ * x' reached by at least one kept contribution, c(x') the sum of those */
+int orc_pt2_unique_eps(int norb, const double* h, const double* eri, const uint64_t* S,
+                       int64_t nS, const double* psi, double E, double eps, int64_t nbuckets,
+                       int64_t bucket, double* out, int64_t cap, uint64_t* keys_out,
+                       double* c_out) {
+    return pt2_core(norb, h, eri, S, nS, psi, E, eps, nbuckets, bucket, out, cap, keys_out,
+                    c_out);
+}
+
 static int pt2_core(int norb, const double* h, const double* eri, const uint64_t* S, int64_t nS,
                     const double* psi, double E, double eps, int64_t nbuckets, int64_t bucket,
                     double* out, int64_t cap, uint64_t* keys_out, double* c_out) {

@@ -60,6 +60,9 @@ def lib():
         L.orc_pt2_unique.restype = C.c_int
         L.orc_pt2_unique.argtypes = [C.c_int, dp, dp, dp, i64, dp, C.c_double, i64, i64, dp,
                                      i64, dp, dp]
+        L.orc_pt2_unique_eps.restype = C.c_int
+        L.orc_pt2_unique_eps.argtypes = [C.c_int, dp, dp, dp, i64, dp, C.c_double, C.c_double,
+                                         i64, i64, dp, i64, dp, dp]
         L.orc_proxy_csr.restype = C.c_int
         L.orc_proxy_csr.argtypes = [C.c_int, dp, dp, dp, i64, i64, C.c_int, dp, dp, dp]
         L.orc_asym_energy_grad.restype = C.c_int
@@ -264,21 +267,29 @@ def pt2(norb, h, eri, S, psi, E, nbuckets: int = 1, bucket_id: int = -1, eps: fl
     return dict(ext=out[0], int=out[1], n_unique=int(out[2]), D=out[3], n_emitted=int(out[4]))
 
 
-def pt2_unique(norb, h, eri, S, psi, E, nbuckets: int = 1, bucket_id: int = -1):
+def pt2_unique(norb, h, eri, S, psi, E, nbuckets: int = 1, bucket_id: int = -1,
+               eps: float = 0.0):
     """The deduplicated external set of pt2 (Eq. pt2_correction): (keys uint64 [n, 2] ascending
     by (a, b), c [n] with c(x') = sum_{y in S} H_x'y psi_y) over C minus S, restricted to one
-    hash bucket when bucket_id >= 0, plus pt2's result dict."""
+    hash bucket when bucket_id >= 0, plus pt2's result dict. eps > 0: the screened set, x' with
+    at least one contribution |H_x'y psi_y| >= eps and c(x') the sum of those (Sec. 3.3)."""
     h, eri, S, psi = _f64(h), _f64(eri), _u64(S), _f64(psi)
     out = np.zeros(5)
     L = lib()
-    args = (norb, _p(h), _p(eri), _p(S), S.shape[0], _p(psi), float(E), int(nbuckets),
-            int(bucket_id), _p(out))
-    st = L.orc_pt2_unique(*args, 0, None, None)
+    args = (norb, _p(h), _p(eri), _p(S), S.shape[0], _p(psi), float(E))
+    tail = (int(nbuckets), int(bucket_id), _p(out))
+
+    def call(n, keys, c):
+        if eps > 0.0:
+            return L.orc_pt2_unique_eps(*args, float(eps), *tail, n, keys, c)
+        return L.orc_pt2_unique(*args, *tail, n, keys, c)
+
+    st = call(0, None, None)
     assert st == 0, st
     n = int(out[2])
     keys = np.zeros((max(n, 1), 2), np.uint64)
     c = np.zeros(max(n, 1))
-    st = L.orc_pt2_unique(*args, n, _p(keys), _p(c))
+    st = call(n, _p(keys), _p(c))
     assert st == 0, st
     return keys[:n], c[:n], dict(ext=out[0], int=out[1], n_unique=n, D=out[3])
 

@@ -1359,10 +1359,10 @@ extern "C" int nqs_pt2_hss(nqs_problem* p, const uint64_t* dets, const double* p
                     (cudaStream_t)stream, nullptr);
 }
 
-extern "C" int nqs_pt2_unique(nqs_problem* p, const uint64_t* dets, const double* psi,
-                              int64_t nS, int buckets, int bucket, uint64_t* dets_out,
-                              double* c_out, int64_t capacity, int64_t* n_unique,
-                              nqs_stream_t stream) {
+static int pt2_unique_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,
+                           double eps, int buckets, int bucket, uint64_t* dets_out,
+                           double* c_out, int64_t capacity, int64_t* n_unique,
+                           nqs_stream_t stream) {
     if (!p || !n_unique || buckets < 1 || bucket < 0 || bucket >= buckets || capacity < 0)
         return NQS_ERR_ARG;
     if (capacity > 0 && (!dets_out || !c_out || (((uintptr_t)dets_out) & 15))) return NQS_ERR_ARG;
@@ -1370,6 +1370,7 @@ extern "C" int nqs_pt2_unique(nqs_problem* p, const uint64_t* dets, const double
     nqs_opts_default(&o);
     o.buckets = buckets;
     o.validate = 0;
+    o.eps_pt2 = eps;
     UniqReq uq{bucket, dets_out, c_out, capacity, 0};
     double res[5];
     const int st = pt2_impl(p, dets, psi, nS, 0.0, nullptr, &o, res, nullptr,
@@ -1382,6 +1383,23 @@ extern "C" int nqs_pt2_unique(nqs_problem* p, const uint64_t* dets, const double
         return NQS_ERR_ARG;
     }
     return NQS_OK;
+}
+
+extern "C" int nqs_pt2_unique(nqs_problem* p, const uint64_t* dets, const double* psi,
+                              int64_t nS, int buckets, int bucket, uint64_t* dets_out,
+                              double* c_out, int64_t capacity, int64_t* n_unique,
+                              nqs_stream_t stream) {
+    return pt2_unique_impl(p, dets, psi, nS, 0.0, buckets, bucket, dets_out, c_out, capacity,
+                           n_unique, stream);
+}
+
+extern "C" int nqs_pt2_unique_screened(nqs_problem* p, const uint64_t* dets, const double* psi,
+                                       int64_t nS, double eps_pt2, int buckets, int bucket,
+                                       uint64_t* dets_out, double* c_out, int64_t capacity,
+                                       int64_t* n_unique, nqs_stream_t stream) {
+    if (!(eps_pt2 > 0.0) || !(eps_pt2 < INFINITY)) return NQS_ERR_ARG;
+    return pt2_unique_impl(p, dets, psi, nS, eps_pt2, buckets, bucket, dets_out, c_out, capacity,
+                           n_unique, stream);
 }
 
 static int pt2_impl(nqs_problem* p, const uint64_t* dets, const double* psi, int64_t nS,

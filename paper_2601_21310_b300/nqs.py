@@ -81,6 +81,9 @@ EXPORTS = {
     "nqs_pt2_unique": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
                                  C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                  C.c_void_p]),
+    "nqs_pt2_unique_screened": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                          C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                          C.c_int64, C.c_void_p, C.c_void_p]),
     "nqs_hb_select": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_double,
                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "nqs_detset_free": (C.c_int, [C.c_void_p]),
@@ -465,23 +468,31 @@ def pt2(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, E: float, bucke
 
 
 def pt2_unique(problem: Problem, dets: torch.Tensor, psi: torch.Tensor, buckets: int = 1,
-               bucket: int = 0, stream=None):
+               bucket: int = 0, eps: float = 0.0, stream=None):
     """The deduplicated external set of nqs_pt2 for one hash bucket: (configurations uint64
-    [n, 2] ascending by key, c(x') float64 [n]) on the device. Sizes the output with a first
-    call that reports the set's size."""
+    [n, 2] ascending by key, c(x') float64 [n]) on the device; with eps > 0 the screened set
+    (nqs_pt2_unique_screened). Sizes the output with a first call that reports the set's size."""
     dets = _dets(dets)
     psi = psi.contiguous()
     n = C.c_int64(0)
-    st = lib().nqs_pt2_unique(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0], int(buckets),
-                              int(bucket), None, None, 0, C.byref(n), _stream(stream))
+    L = lib()
+
+    def call(out, c, cap):
+        if eps > 0.0:
+            return L.nqs_pt2_unique_screened(problem.handle, _ptr(dets), _ptr(psi),
+                                             dets.shape[0], float(eps), int(buckets), int(bucket),
+                                             out, c, cap, C.byref(n), _stream(stream))
+        return L.nqs_pt2_unique(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0],
+                                int(buckets), int(bucket), out, c, cap, C.byref(n),
+                                _stream(stream))
+
+    st = call(None, None, 0)
     if st != NQS_ERR_ARG or n.value == 0:
         _check(st, "nqs_pt2_unique")
     cap = max(n.value, 1)
     out = torch.empty((cap, 2), dtype=torch.int64, device=dets.device)
     c = torch.empty(cap, dtype=torch.float64, device=dets.device)
-    _check(lib().nqs_pt2_unique(problem.handle, _ptr(dets), _ptr(psi), dets.shape[0],
-                                int(buckets), int(bucket), _ptr(out), _ptr(c), cap, C.byref(n),
-                                _stream(stream)), "nqs_pt2_unique")
+    _check(call(_ptr(out), _ptr(c), cap), "nqs_pt2_unique")
     return out[:n.value].view(torch.uint64), c[:n.value]
 
 

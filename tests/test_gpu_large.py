@@ -240,3 +240,56 @@ def test_cr2_48e42o_full_size_pt2_unique_sampled(cr2_48):
             assert in_set(ya, yb), (ya, yb)
             found += 1
     assert found > 0
+
+
+def test_cr2_48e42o_full_size_screened_pt2_unique_sampled(cr2_48):
+    """The screened form at 42 orbitals, |S| = 2^20, eps = 1e-6 on normalised amplitudes: one
+    hash bucket of 4096, checked on samples. For sampled x' of the GPU's set: outside S, in the
+    bucket, and c(x') = the sum over members y of S connected to x' of the contributions
+    H_x'y psi_y with |H_x'y| |psi_y| >= eps (oracle elements), at least one of them kept; and
+    kept contributions to sampled excitations of members of S land on x' in the set."""
+    N, p, P, dets = cr2_48
+    S = p.S
+    rng = np.random.default_rng(23)
+    psi = rng.normal(size=len(S))
+    psi /= np.linalg.norm(psi)
+    eps, B, b = 1e-6, 4096, 0
+    keys, c = N.pt2_unique(P, dets, torch.from_numpy(psi).cuda(), B, b, eps=eps)
+    keys, c = keys.cpu().numpy(), c.cpu().numpy()
+    assert len(keys) > 100
+    sh = 42
+    index = {int(a) << sh | int(bb): i for i, (a, bb) in enumerate(S.tolist())}
+
+    def in_set(ya, yb):  # keys ascending by (a, b)
+        lo = np.searchsorted(keys[:, 0], np.uint64(ya), "left")
+        hi = np.searchsorted(keys[:, 0], np.uint64(ya), "right")
+        return bool(np.any(keys[lo:hi, 1] == np.uint64(yb)))
+
+    for k in rng.choice(len(keys), 24, replace=False):
+        xa, xb = int(keys[k, 0]), int(keys[k, 1])
+        assert (xa << sh | xb) not in index
+        assert O.bucket(xa, xb, B) == b
+        ref, scale, kept = 0.0, 0.0, 0
+        for ya, yb in O.excitations(42, xa, xb).tolist():
+            j = index.get(int(ya) << sh | int(yb))
+            if j is None:
+                continue
+            v, _ = O.element(42, p.h, p.eri, (ya, yb), (xa, xb))
+            if abs(v) * abs(psi[j]) >= eps:
+                ref += v * psi[j]
+                scale += abs(v * psi[j])
+                kept += 1
+        assert kept > 0
+        assert abs(c[k] - ref) <= 1e-12 * scale, (k, c[k], ref)
+    found = 0
+    for r in rng.choice(len(S), 256, replace=False):
+        ya, yb = int(S[r, 0]), int(S[r, 1])
+        ex = O.excitations(42, ya, yb)
+        for xa, xb in ex[rng.choice(len(ex), 2000, replace=False)].tolist():
+            if (int(xa) << sh | int(xb)) in index or O.bucket(xa, xb, B) != b:
+                continue
+            v, _ = O.element(42, p.h, p.eri, (ya, yb), (xa, xb))
+            if abs(v) * abs(psi[r]) >= eps:
+                assert in_set(xa, xb), (xa, xb)
+                found += 1
+    assert found > 0

@@ -266,6 +266,29 @@ def test_pt2_unique_set_matches_oracle(name, B, b):
     assert abs(got["partials"][b, 0] - info["ext"]) <= 1e-11 * max(1.0, abs(info["ext"]))
 
 
+@pytest.mark.parametrize("name,B,b,eps", [("tiny_n10", 1, 0, 1e-3), ("tiny_n10", 3, 1, 1e-4),
+                                          ("small_n16", 8, 3, 1e-5)])
+def test_pt2_unique_screened_set_matches_oracle(name, B, b, eps):
+    """The screened external set (Sec. 3.3) key by key: the x' of C minus S (of one hash bucket)
+    reached by at least one contribution |H_x'y psi_y| >= eps equal the oracle's bit for bit, and
+    c(x'), the sum of the kept contributions, element by element."""
+    need_gpu()
+    N = nqs()
+    p = synth.make_problem(name)
+    P = problem_for(N, p)
+    psi = np.random.default_rng(13).normal(size=len(p.S))
+    psi /= np.linalg.norm(psi)
+    keys, c = N.pt2_unique(P, to_dev(p.S), torch.from_numpy(psi).cuda(), B, b, eps=eps)
+    rk, rc, _ = O.pt2_unique(p.wl.norb, p.h, p.eri, p.S, psi, -20.0, B, b if B > 1 else -1,
+                             eps=eps)
+    full, _, _ = O.pt2_unique(p.wl.norb, p.h, p.eri, p.S, psi, -20.0, B, b if B > 1 else -1)
+    assert 0 < len(rk) < len(full)  # the cut removes some x' entirely
+    keys = keys.cpu().numpy()
+    assert np.array_equal(keys, rk)
+    c = c.cpu().numpy()
+    assert np.abs(c - rc).max() <= _unique_tol(rc), np.abs(c - rc).max()
+
+
 def test_pt2_unique_reports_size_and_rejects_bad_bucket():
     need_gpu()
     N = nqs()

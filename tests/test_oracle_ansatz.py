@@ -293,3 +293,35 @@ def test_screened_pt2_matches_dense_bruteforce(olib, eps):
     z = olib.pt2(norb, h, eri, S, psi, E, eps=0.0)
     u = olib.pt2(norb, h, eri, S, psi, E)
     assert z == u
+
+
+def test_pt2_unique_screened_matches_dense_bruteforce(olib):
+    """The screened external set of Sec. 3.3: the configurations outside S with at least one
+    contribution |H_x'y psi_y| >= eps, ascending by (a, b), and c(x') the sum of the kept
+    contributions, from the dense brute-force H (eps placed away from every contribution, so
+    the last-bit difference between the two forms of H decides nothing)."""
+    norb, n = 6, 3
+    h, eri, _ = synth.integrals(norb, 12, 22, 3.0)
+    dets, H = BF.dense_hamiltonian(norb, n, n, h, eri)
+    rng = np.random.default_rng(7)
+    pick = np.sort(rng.choice(len(dets), size=40, replace=False))
+    S = dets[pick]
+    psi = rng.normal(size=40)
+    inS = np.zeros(len(dets), bool)
+    inS[pick] = True
+    contrib = H[:, pick] * psi[None, :]
+    mags = np.sort(np.abs(contrib[~inS][np.abs(contrib[~inS]) > 0]))
+    k = (9 * len(mags)) // 10  # a cut that drops most contributions and some x' entirely
+    while mags[k + 1] <= mags[k] * (1 + 1e-6):  # a gap between two neighbouring magnitudes
+        k += 1
+    eps = float(np.sqrt(mags[k] * mags[k + 1]))
+    assert mags[k] < eps * (1 - 1e-9) and mags[k + 1] > eps * (1 + 1e-9)
+    kept = np.abs(contrib) >= eps
+    reach = kept.any(axis=1) & ~inS
+    c = np.where(kept, contrib, 0.0).sum(axis=1)
+    keys, cu, info = olib.pt2_unique(norb, h, eri, S, psi, -1.0, eps=eps)
+    order = np.lexsort((dets[reach, 1], dets[reach, 0]))
+    assert 0 < len(keys) < int((np.abs(contrib[~inS]) > 0).any(axis=1).sum())
+    assert np.array_equal(keys, dets[reach][order])
+    assert np.abs(cu - c[reach][order]).max() < 1e-13
+    assert info["ext"] == olib.pt2(norb, h, eri, S, psi, -1.0, eps=eps)["ext"]
