@@ -679,8 +679,9 @@ __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU
                                const double* __restrict__ cU, int64_t nuniq,
                                const double* __restrict__ Dp, double E, double* __restrict__ cS,
                                double* __restrict__ eterm, unsigned long long* __restrict__ next,
-                               uint32_t* __restrict__ ext_flag) {
-
+                               uint32_t* __restrict__ ext_flag, int outside) {
+    // outside != 0: every key is known to lie outside S (the screened emission leaves S out),
+    // so no probe is needed
     const double D = *Dp;
     const int norb = P.norb;
     unsigned long long local = 0;
@@ -689,7 +690,7 @@ __global__ void k_unique_terms(ProblemDev P, HashS H, const K* __restrict__ keyU
         uint64_t a, b;
         key_split(keyU[u], norb, a, b);
         const double c = cU[u];
-        const int32_t s = hash_lookup(H, a, b);
+        const int32_t s = outside ? -1 : hash_lookup(H, a, b);
         if (ext_flag) ext_flag[u] = s >= 0 ? 0u : 1u;
         if (s >= 0) {
             cS[s] = c;
@@ -1051,7 +1052,8 @@ static int pt2_reduce(nqs_problem* p, K* keys, double* vals, K* keys2, double* v
         {
             ProfScope prof_(PROF_UNIQUE, s);
             k_unique_terms<K><<<grid_for(nuniq, 256), 256, 0, s>>>(
-                P, *cx.H, keyU, cU, nuniq, cx.D_dev, cx.E_var, cx.cS, eterm, nuniq_dev, flag);
+                P, *cx.H, keyU, cU, nuniq, cx.D_dev, cx.E_var, cx.cS, eterm, nuniq_dev, flag,
+                cx.exact ? 1 : 0);
         }
         NQS_CK_LAUNCH();
     }
