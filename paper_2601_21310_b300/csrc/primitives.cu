@@ -40,15 +40,37 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T* warp_tot, T* total) {
     return r;
 }
 
+// a thread's SC_ITEMS consecutive elements: 16-byte loads when the whole run is in range and
+// the array is 16-byte aligned (vec), else element by element
+template <class T>
+__device__ __forceinline__ void sc_load(const T* in, int64_t base, int64_t n, bool vec,
+                                        T (&v)[SC_ITEMS]) {
+    if (vec && base + SC_ITEMS <= n) {
+        const uint4* q = (const uint4*)(in + base);
+#pragma unroll
+        for (int k = 0; k < (int)(SC_ITEMS * sizeof(T) / 16); ++k) {
+            const uint4 w = q[k];
+            T* d = (T*)&w;
+#pragma unroll
+            for (int j = 0; j < (int)(16 / sizeof(T)); ++j) v[k * (16 / sizeof(T)) + j] = d[j];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SC_ITEMS; ++k) v[k] = (base + k < n) ? in[base + k] : T(0);
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(SC_THREADS) k_tile_sum(const T* in, int64_t n, T* sums) {
     __shared__ T warp_tot[SC_THREADS / 32];
     __shared__ T total;
     int64_t base = (int64_t)blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+    const bool vec = (((uintptr_t)in) & 15) == 0;
+    T v[SC_ITEMS];
+    sc_load<T>(in, base, n, vec, v);
     T s = 0;
 #pragma unroll
-    for (int k = 0; k < SC_ITEMS; ++k)
-        if (base + k < n) s += in[base + k];
+    for (int k = 0; k < SC_ITEMS; ++k) s += v[k];
     block_exclusive_scan<T>(s, warp_tot, &total);
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
@@ -59,20 +81,29 @@ __global__ void __launch_bounds__(SC_THREADS) k_tile_scan(const T* in, T* out, i
     __shared__ T warp_tot[SC_THREADS / 32];
     __shared__ T total;
     int64_t base = (int64_t)blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+    const bool vec = ((((uintptr_t)in) | ((uintptr_t)out)) & 15) == 0;
     T v[SC_ITEMS];
+    sc_load<T>(in, base, n, vec, v);
     T s = 0;
 #pragma unroll
-    for (int k = 0; k < SC_ITEMS; ++k) {
-        v[k] = (base + k < n) ? in[base + k] : T(0);
-        s += v[k];
-    }
+    for (int k = 0; k < SC_ITEMS; ++k) s += v[k];
     T ex = block_exclusive_scan<T>(s, warp_tot, &total);
     T off = offs ? offs[blockIdx.x] : T(0);
     T run = off + ex;
+    __align__(16) T o[SC_ITEMS];
 #pragma unroll
     for (int k = 0; k < SC_ITEMS; ++k) {
-        if (base + k < n) out[base + k] = run;
+        o[k] = run;
         run += v[k];
+    }
+    if (vec && base + SC_ITEMS <= n) {
+        uint4* q = (uint4*)(out + base);
+#pragma unroll
+        for (int k = 0; k < (int)(SC_ITEMS * sizeof(T) / 16); ++k) q[k] = ((const uint4*)o)[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < SC_ITEMS; ++k)
+            if (base + k < n) out[base + k] = o[k];
     }
     if (grand && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *grand = off + total;
 }
