@@ -230,7 +230,8 @@ int nqs_energy_grad(nqs_problem* problem, nqs_net* net, const nqs_csr* csr, cons
  * C\S is generated on the device: every excitation of every y in S is emitted as
  * (key x', H_x'y psi_y) in canonical order, radix-sorted by key (stable), deduplicated, and
  * each run summed in emission order; members of S feed the internal term. The work is split
- * into hash buckets (SplitMix64 finaliser: bucket = mix(mix(a) ^ b) mod B).
+ * into hash buckets (SplitMix64 finaliser: h = mix(mix(a) ^ b), bucket = the high 32 bits of h
+ * times B, shifted right by 32; B < 2^32).
  * psi: device [nS] FP64 at any scale. out: host [5] = {external, internal, number of unique
  * x' in C\S, number of emitted pairs, number of buckets used}. opts->buckets = 0 chooses the
  * bucket count: one bucket's pairs use at most half of the free device memory. bucket_partials:

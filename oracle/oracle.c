@@ -747,7 +747,8 @@ int orc_asym_energy_grad(const orc_net* n, const uint64_t* T, int64_t nT, int64_
 /* ------------------------------------------------------------------------------------------
  * Bucket function for hash-partitioned PT2: SplitMix64's output finaliser (Steele, Lea and
  * Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014), applied as
- * bucket(a, b) = mix(mix(a) ^ b) mod B. Part of the interface, restated on each side.
+ * h = mix(mix(a) ^ b), and bucket(a, b) = floor(floor(h / 2^32) * B / 2^32) for B < 2^32 (the
+ * high 32 bits of h scaled to [0, B)). Part of the interface, restated on each side.
  * ---------------------------------------------------------------------------------------- */
 static inline uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
@@ -755,7 +756,8 @@ static inline uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 uint64_t orc_bucket(uint64_t a, uint64_t b, uint64_t nbuckets) {
-    return mix64(mix64(a) ^ b) % nbuckets;
+    const uint64_t h = mix64(mix64(a) ^ b);
+    return ((h >> 32) * nbuckets) >> 32;
 }
 
 /* ------------------------------------------------------------------------------------------

@@ -175,7 +175,7 @@ static int hb_tables(nqs_problem* p, HbTab* out) {
 }
 
 __device__ __forceinline__ bool in_bucket_of(uint64_t a, uint64_t b, uint64_t B, uint64_t bucket) {
-    return B == 1 || (det_hash(a, b) % B) == bucket;
+    return B == 1 || det_bucket(a, b, B) == bucket;
 }
 
 // The screening test fl(v |psi_x|) >= eps for v >= 0 (a table entry or |<x'|H|x>|), without an

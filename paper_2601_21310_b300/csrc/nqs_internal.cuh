@@ -174,6 +174,12 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 __host__ __device__ __forceinline__ uint64_t det_hash(uint64_t a, uint64_t b) {
     return mix64(mix64(a) ^ b);
 }
+// PT2 bucket of a configuration among B < 2^32: the high 32 bits of det_hash scaled to [0, B)
+// (one multiply; a 64-bit remainder by a variable B costs a long instruction sequence per
+// excitation)
+__host__ __device__ __forceinline__ uint32_t det_bucket(uint64_t a, uint64_t b, uint64_t B) {
+    return (uint32_t)(((det_hash(a, b) >> 32) * B) >> 32);
+}
 
 // ------------------------------------------------------------------------------------------
 // hash table of S: open addressing, linear probing, capacity a power of two >= 16|S| (8|S|

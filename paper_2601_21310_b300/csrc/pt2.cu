@@ -1,6 +1,6 @@
 // Epstein-Nesbet PT2 over the connected space (Eq. pt2_correction; Algorithm 1 step 4).
 //
-// For each hash bucket b (SplitMix64 finaliser of the det, mod B):
+// For each hash bucket b (the high 32 bits of a SplitMix64 hash of the det, scaled to [0, B)):
 //   1. emit (key x', H_x'y psi_y) for every excitation x' of every y in S with bucket(x') = b:
 //      with B = 1 the position of every emission is fixed (y ascending, then canonical
 //      excitation index), otherwise a count pass and a scan give them; the screened form
@@ -33,7 +33,7 @@
 #define PT_WARPS (PT_THREADS / 32)
 
 __device__ __forceinline__ bool in_bucket(uint64_t a, uint64_t b, uint64_t B, uint64_t bucket) {
-    return B == 1 || (det_hash(a, b) % B) == bucket;
+    return B == 1 || det_bucket(a, b, B) == bucket;
 }
 
 __global__ void __launch_bounds__(PT_THREADS) k_pt2_count(ProblemDev P,
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_count_all(ProblemDev P,
         for (uint32_t e = lane; e < nexc; e += 32) {
             uint64_t a2, b2;
             step_key(P, T, *ctx, x.x, x.y, e, o2, o3, o4, q, a2, b2);
-            atomicAdd(&hist[det_hash(a2, b2) % B], 1u);
+            atomicAdd(&hist[det_bucket(a2, b2, B)], 1u);
         }
         __syncwarp();
         for (uint32_t k = lane; k < B; k += 32) cnt[(int64_t)k * nS + det] = hist[k];
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(PT_THREADS, 4) k_pt2_emit(ProblemDev P,
     }
 }
 
-// All buckets in one pass: excitation e of det goes to bucket b = det_hash(x') mod B, at
+// All buckets in one pass: excitation e of det goes to bucket b = det_bucket(x', B), at
 // start[b] + offs[b * nS + det] + (its rank among det's excitations in bucket b, canonical
 // order). Every excitation is decoded once (incrementally); per-warp counters in shared memory
 // carry each bucket's rank across rounds of 32.
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(PT_THREADS) k_pt2_emit_all(ProblemDev P,
                     b2 = ex.b2;
                     hv = exc_element(P, *ctx, ex);
                 }
-                b = (uint32_t)(det_hash(a2, b2) % B);
+                b = det_bucket(a2, b2, B);
             }
             const unsigned peers = __match_any_sync(FULL_MASK, b);
             uint32_t base = 0;
