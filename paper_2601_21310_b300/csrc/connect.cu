@@ -319,7 +319,14 @@ struct __align__(16) OwnerRec {
     uint64_t a2;
 };
 
-__global__ void __launch_bounds__(CONN_THREADS, 7) k_conn_count_ab(ProblemDev P, HashS H,
+// PART 0: the row's words cleared, then the singles and same-spin doubles (scans of x's own
+// beta group and alpha run); PART 1, launched after it: the alpha-beta block, adding to the
+// row's count. Two kernels, so that each keeps fewer values live than the whole pass would.
+#define CONN_AB_BLOCKS0 7  // blocks per SM of each part (a sweep: 5, 6 and 8 no faster)
+#define CONN_AB_BLOCKS1 7
+template <int PART>
+__global__ void __launch_bounds__(CONN_THREADS, PART == 0 ? CONN_AB_BLOCKS0 : CONN_AB_BLOCKS1)
+    k_conn_count_ab(ProblemDev P, HashS H,
                                                                  AlphaIdx X, BetaIdx Y,
                                                                  const ulonglong2* __restrict__ S,
                                                                  int64_t nS,
@@ -352,11 +359,12 @@ __global__ void __launch_bounds__(CONN_THREADS, 7) k_conn_count_ab(ProblemDev P,
         ulonglong2 x = S[det];
         fill_ctx(P, x.x, x.y, ctx, lane);
         uint32_t* wb = bits + det * nwords;
+        int cnt = 0;
+        if (PART == 0) {
         for (uint32_t w = lane; w < nwords; w += 32) wb[w] = 0u;
         __syncwarp();
         // alpha singles and alpha-alpha doubles of x keep its beta string: they are the alpha
         // strings a_y of x's own beta group with popcount(A ^ a_y) = 2 (single) or 4 (double)
-        int cnt = 0;
         uint32_t boff = 0, blen = 0;
         if (Y.key && beta_find(Y, x.y, boff, blen) && blen <= own_a_scan_max) {
             for (uint32_t k0 = 0; k0 < blen; k0 += 32) {
@@ -432,8 +440,9 @@ __global__ void __launch_bounds__(CONN_THREADS, 7) k_conn_count_ab(ProblemDev P,
             cnt += probe_range(P, T, *ctx, H, x, o1, o2, o2, o3, o4, wb, lane);
             cnt += probe_range(P, T, *ctx, H, x, o3, o4, o2, o3, o4, wb, lane);
         }
+        }  // PART 0
         __syncwarp();
-        for (uint32_t sa0 = 0; sa0 < sA; sa0 += 32) {
+        for (uint32_t sa0 = 0; PART == 1 && sa0 < sA; sa0 += 32) {
             const uint32_t si = sa0 + lane;
             uint64_t a2 = 0;
             int2 r = make_int2(0, 0);
@@ -510,7 +519,10 @@ __global__ void __launch_bounds__(CONN_THREADS, 7) k_conn_count_ab(ProblemDev P,
             }
             __syncwarp();  // the records are rewritten by the next round of alpha singles
         }
-        if (lane == 0) rowcnt[det] = cnt + 1;  // + diagonal
+        if (lane == 0) {
+            if (PART == 0) rowcnt[det] = cnt + 1;  // + diagonal
+            else rowcnt[det] += cnt;
+        }
         __syncwarp();
     }
 }
@@ -636,8 +648,10 @@ int conn_count_indexed(nqs_problem* p, Scratch& sc, const HashS& H, const uint64
     if (smem > 48 * 1024) {
         NQS_CK(cudaFuncSetAttribute(k_conn_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));
-        NQS_CK(cudaFuncSetAttribute(k_conn_count_ab, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_conn_count_ab<0>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        NQS_CK(cudaFuncSetAttribute(k_conn_count_ab<1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     // index of R by alpha string (runs of the sorted R), for the alpha-beta block of pass 1
     const bool use_ab = p->d.dAB > 0;
@@ -689,11 +703,14 @@ int conn_count_indexed(nqs_problem* p, Scratch& sc, const HashS& H, const uint64
     }
     {
         ProfScope prof_(PROF_CONN_COUNT, s);
-        if (use_ab)
-            k_conn_count_ab<<<conn_grid(nrows), CONN_THREADS, smem, s>>>(
+        if (use_ab) {
+            k_conn_count_ab<0><<<conn_grid(nrows), CONN_THREADS, smem, s>>>(
                 p->d, H, X, Y, (const ulonglong2*)rows, nrows, (const ulonglong2*)Rset, rowcnt,
                 bits);
-        else
+            k_conn_count_ab<1><<<conn_grid(nrows), CONN_THREADS, smem, s>>>(
+                p->d, H, X, Y, (const ulonglong2*)rows, nrows, (const ulonglong2*)Rset, rowcnt,
+                bits);
+        } else
             k_conn_count<<<conn_grid(nrows), CONN_THREADS, smem, s>>>(
                 p->d, H, (const ulonglong2*)rows, nrows, rowcnt, bits);
     }
