@@ -243,7 +243,7 @@ __device__ __forceinline__ void or_ballot(uint32_t* wb, uint32_t base, unsigned 
 // The plain probe pass over the canonical indices [lo, hi) of one class range (singles decode
 // directly; same-spin doubles step incrementally from a fresh position). Returns, in lane 0,
 // the number of hits; ballots are ORed into the row's (cleared) words.
-__device__ __forceinline__ int probe_range(const ProblemDev& P, const PairTables& T,
+__device__ __noinline__ int probe_range(const ProblemDev& P, const PairTables& T,
                                            const DetCtx& c, const HashS& H, ulonglong2 x,
                                            uint32_t lo, uint32_t hi, uint32_t o2, uint32_t o3,
                                            uint32_t o4, uint32_t* wb, int lane) {
