@@ -514,30 +514,53 @@ def run_outer_loop(args, N, P, net, dets, psi, dtype, stream, eps_hb=1e-6):
 
 
 def run_tensor_probe(N, stream, M=1 << 20, Nn=2016, K=1024, reps=10):
-    """The library's tcgen05 GEMM (nqs_gemm_bf16: bf16 in, FP32 out) on the output-layer shape
-    of the 42-orbital network (|S| = 2^20 rows, 2016 outputs, width 1024), timed with CUDA events
-    on the launching stream after warm-up, against the measured bf16 peaks."""
+    """The library's tcgen05 GEMM (nqs_gemm_bf16: bf16 in, FP32 out; 256-column tiles in the
+    paired two-SM form) on the output-layer shape of the 42-orbital network (|S| = 2^20 rows,
+    2016 outputs, width 1024), timed with CUDA events on the launching stream after warm-up.
+    `achieved` is the best of `reps` single launches, each timed alone (the method of the
+    measured burst peak: best of 10 timed launches), against that burst peak; `back_to_back`
+    is the mean over `reps` launches in a row, which runs into the power cap, against the
+    measured sustained peak."""
     A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
     B = torch.randn(Nn, K, device="cuda").to(torch.bfloat16)
     for _ in range(3):
         N.gemm_bf16(A, B)
     torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
+    flops = 2.0 * M * Nn * K
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    singles = []
+    for a, b in ev:
+        torch.cuda.synchronize()
+        time.sleep(0.02)
+        a.record(stream)
+        N.gemm_bf16(A, B)
+        b.record(stream)
+        b.synchronize()
+        singles.append(a.elapsed_time(b))
+    a, b = ev[0]
     a.record(stream)
     for _ in range(reps):
         N.gemm_bf16(A, B)
     b.record(stream)
     b.synchronize()
-    ms = a.elapsed_time(b) / reps
-    tf = 2.0 * M * Nn * K / (ms * 1e-3) / 1e12
+    ms_b2b = a.elapsed_time(b) / reps
+    ms = min(singles)
+    tf = flops / (ms * 1e-3) / 1e12
+    tf_b2b = flops / (ms_b2b * 1e-3) / 1e12
     peaks, kind = load_peaks()
     peak = peaks.get("bf16_tflops", 1800.0)
+    peak_sus = peaks.get("bf16_tflops_sustained", 1400.0)
     del A, B
     torch.cuda.empty_cache()
-    return {"kernel": "k_gemm_tc", "shape": [M, Nn, K], "bound": "tensor", "ms": ms,
+    return {"kernel": "k_gemm_tc_pair", "shape": [M, Nn, K], "bound": "tensor", "ms": ms,
+            "ms_median_single": float(np.median(singles)),
             "achieved": round(tf, 1), "peak": peak, "unit": "TFLOP/s",
-            "frac": round(tf / peak, 4), "peak_source": kind + " bf16 burst"}
+            "frac": round(tf / peak, 4), "peak_source": kind + " bf16 burst",
+            "timing": f"best of {reps} single launches",
+            "back_to_back": {"ms": ms_b2b, "achieved": round(tf_b2b, 1), "peak": peak_sus,
+                             "frac": round(tf_b2b / peak_sus, 4),
+                             "peak_source": kind + " bf16 sustained"}}
 
 
 MODES_MAX_T = 4 << 20

@@ -345,6 +345,11 @@ int nqs_batch_get_mode(const nqs_batch* batch);
  * (M, N, K, chosen width) and returns how many there are. */
 int nqs_set_autotune(int on);
 int nqs_autotune_entries(int* M, int* N, int* K, int* width, int capacity);
+/* Paired tensor-core GEMM (on by default): GEMMs with 256-column tiles run on clusters of two
+ * SMs that share one M = 256 tcgen05.mma stream (cta_group::2), each SM staging its own 128 rows
+ * of A and half of B. Off: every tile runs on one SM (M = 128). Process-wide; affects the
+ * network's GEMMs and nqs_gemm_bf16, not the grouped batch GEMMs. */
+int nqs_set_gemm_pairing(int on);
 
 /* H_SS build without any device allocation (the paper has no counterpart: this exists for
  * callers that cannot allocate device memory, such as a host framework that owns every device

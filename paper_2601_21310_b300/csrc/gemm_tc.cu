@@ -522,6 +522,296 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------------------
+// Paired form (tcgen05 cta_group::2): a cluster of two CTAs on two SMs computes a 256 x BN
+// output tile with one MMA stream of M = 256 issued by the even CTA. Each CTA stages its own
+// 128 rows of A and one half (BN/2 rows) of B, so an SM moves A + B/2 per k-block instead of
+// A + B, and its tensor memory receives the accumulator rows of its own A rows (all BN
+// columns), which its epilogue warps drain exactly as in k_gemm_tc.
+// Barriers: the even CTA's full[s] counts the transaction bytes of both CTAs' copies (the odd
+// CTA's copies signal it through the .cta_group::2 form of the load); the MMA's commits
+// arrive on empty[s] and tfull[b] of both CTAs (multicast); the epilogue warps of both CTAs
+// arrive on the even CTA's tempty[b]. A timeout in either CTA raises the abort flag of both.
+// ------------------------------------------------------------------------------------------
+template <int BN>
+struct TcSmem2 {
+    static constexpr int A_BYTES = 128 * TC_BK * 2;
+    static constexpr int B_BYTES = (BN / 2) * TC_BK * 2;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    // one 4 KB staging buffer per epilogue warp: a second one would cost a pipeline stage at
+    // BN = 256, and the deeper operand pipeline is worth more (1354 against 1193 TFLOP/s on
+    // 2^20 x 2016 x 1024 with 6 stages and one buffer, against 5 stages and two)
+    static constexpr int EPI = TC_EPI_WARPS * 4096;
+    static constexpr int ROOM = 232448 - 1024 /*align*/ - 256 /*barriers*/ - EPI;
+    static constexpr int STAGES = ROOM / STAGE < 8 ? ROOM / STAGE : 8;
+    static constexpr int BYTES = STAGES * STAGE + EPI + 1024 + 256;
+};
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_idx() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// address of the same shared-memory variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t smem_in_cta(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+                 : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cluster_addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cluster_addr), "r"(v) : "memory");
+}
+
+// bounded wait as mbar_wait_ab; acquire at cluster scope (arrivals from the other CTA), and a
+// timeout also raises the other CTA's abort flag
+__device__ __forceinline__ bool mbar_wait_pair(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                               uint32_t peer_abort) {
+    const uint32_t addr = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > 4000000000ll) {
+            *abort = 1;
+            st_cluster_u32(peer_abort, 1u);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
+        : "memory");
+}
+
+template <int BN>
+__device__ __forceinline__ uint32_t idesc_bf16_m256() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(256 >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+// commit of the MMAs issued so far, arriving on the barrier at this offset in the CTAs of mask
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+// one work unit of the paired form: (split z, 256-row tile, BN-column tile)
+__device__ __forceinline__ Unit unit_of_pair(int u, const TcArgs& a, int BN) {
+    const int ntn = (a.N + BN - 1) / BN, ntm = (a.M + 255) / 256;
+    const int tiles = ntn * ntm;
+    const int z = u / tiles, t = u - z * tiles;
+    const int nkb = (a.K + TC_BK - 1) / TC_BK;
+    const int per = (nkb + a.splits - 1) / a.splits;
+    Unit r;
+    r.z = z;
+    r.m0 = (t / ntn) * 256;
+    r.n0 = (t % ntn) * BN;
+    r.kb0 = z * per;
+    r.nk = max(0, min(nkb, r.kb0 + per) - r.kb0);
+    return r;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC,
+                   const __grid_constant__ CUtensorMap tmCT,
+                   const __grid_constant__ CUtensorMap tmP, TcArgs a) {
+    using L = TcSmem2<BN>;
+    constexpr int ST = L::STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* epi_stage = smem + ST * L::STAGE;
+    uint64_t* full = (uint64_t*)(smem + ST * L::STAGE + L::EPI);
+    uint64_t* empty = full + ST;
+    uint64_t* tfull = empty + ST;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tslot = (uint32_t*)(drain + 1);
+    volatile int* abort = (volatile int*)(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const int cid = (int)cluster_idx(), ncl = (int)cluster_count();
+    const int units = ((a.N + BN - 1) / BN) * ((a.M + 255) / 256) * a.splits;
+    const uint32_t peer_abort = smem_in_cta((const void*)abort, rank ^ 1u);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 2 * TC_EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(tslot)),
+            "r"((uint32_t)(2 * BN)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // both CTAs' barriers are initialised before any copy or arrival may reach them
+    cluster_sync_all();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer (both CTAs) ----------------
+        uint32_t it = 0;
+        for (int u = cid; u < units && !*abort; u += ncl) {
+            const Unit w = unit_of_pair(u, a, BN);
+            for (int i = 0; i < w.nk; ++i, ++it) {
+                const int s = it % ST;
+                const uint32_t ph = (it / ST) & 1u;
+                if (it >= (uint32_t)ST && !mbar_wait_pair(&empty[s], ph ^ 1u, abort, peer_abort))
+                    break;
+                uint8_t* st = smem + s * L::STAGE;
+                if (rank == 0) mbar_expect_tx(&full[s], 2u * (uint32_t)L::STAGE);
+                const uint32_t fb = smem_in_cta(&full[s], 0u);
+                tma_load_2d_pair(st, &tmA, fb, (w.kb0 + i) * TC_BK, w.m0 + (int)rank * 128);
+                tma_load_2d_pair(st + L::A_BYTES, &tmB, fb, (w.kb0 + i) * TC_BK,
+                                 w.n0 + (int)rank * (BN / 2));
+            }
+        }
+        // the even CTA's full barriers count both CTAs' copies: waiting (bounded) for the last
+        // load of each stage there covers the copies in flight of the pair
+        if (rank == 0) {
+            const uint32_t last = it;
+            for (uint32_t j = last > (uint32_t)ST ? last - ST : 0; j < last; ++j) {
+                volatile int no_abort = 0;
+                mbar_wait_ab(&full[j % ST], (j / ST) & 1u, &no_abort);
+            }
+        }
+    } else if (warp == 1 && lane == 0 && rank == 0) {
+        // ---------------- MMA issuer (even CTA) ----------------
+        const uint32_t idesc = idesc_bf16_m256<BN>();
+        uint32_t it = 0, j = 0;
+        for (int u = cid; u < units && !*abort; u += ncl, ++j) {
+            const Unit w = unit_of_pair(u, a, BN);
+            const uint32_t b = j & 1u, use = j >> 1;
+            if (use > 0 && !mbar_wait_pair(&tempty[b], (use - 1) & 1u, abort, peer_abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t acc = tmem + b * BN;
+            bool ok = true;
+            for (int i = 0; i < w.nk; ++i, ++it) {
+                const int s = it % ST;
+                if (!mbar_wait_pair(&full[s], (it / ST) & 1u, abort, peer_abort)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint8_t* st = smem + s * L::STAGE;
+                const uint64_t da = sdesc_sw128(smem_u32(st));
+                const uint64_t db = sdesc_sw128(smem_u32(st + L::A_BYTES));
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk)
+                    umma_pair(acc, da + 2 * kk, db + 2 * kk, idesc, (i | kk) != 0 ? 1u : 0u);
+                umma_commit_pair(&empty[s], (uint16_t)3);
+            }
+            if (!ok) break;
+            umma_commit_pair(&tfull[b], (uint16_t)3);
+        }
+        // every MMA issued has completed (it reads the other CTA's shared memory) before the
+        // pair may leave
+        umma_commit_pair(drain, (uint16_t)1);
+        volatile int no_abort = 0;
+        mbar_wait_ab(drain, 0u, &no_abort);
+    } else if (warp >= 2) {
+        // ---------------- epilogue (both CTAs, own accumulator rows) ----------------
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int c_lo = half * (BN / 2), c_hi = c_lo + BN / 2;
+        const uint32_t tempty0 = smem_in_cta(&tempty[0], 0u);
+        uint32_t j = 0;
+        for (int u = cid; u < units; u += ncl, ++j) {
+            Unit w = unit_of_pair(u, a, BN);
+            w.m0 += (int)rank * 128;
+            const uint32_t b = j & 1u, use = j >> 1;
+            if (!mbar_wait_pair(&tfull[b], use & 1u, abort, peer_abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = w.m0 + q * 32 + lane;
+            const bool row_ok = row < a.M;
+#pragma unroll 1
+            for (int c = c_lo; c < c_hi; c += 32) {
+                uint32_t r[32];
+                if (w.nk > 0) {
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)c, r);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) r[t] = 0u;
+                }
+                if (a.tma_c)
+                    epilogue32_tma(a, w, row, row_ok, w.n0 + c, w.m0 + q * 32, r,
+                                   epi_stage + (warp - 2) * 4096, &tmC, &tmCT, &tmP);
+                else
+                    epilogue32(a, w, row, row_ok, w.n0 + c, r);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(tempty0 + b * 8u);
+        }
+        if (a.tma_c && lane == 0) bulk_wait0();
+    }
+    if (*abort && a.err) atomicExch(a.err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    // no CTA of the pair leaves (or releases tensor memory) while the other may still touch its
+    // shared memory or the pair's accumulators
+    cluster_sync_all();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)(2 * BN)));
+    cluster_sync_all();
+}
+
+// ------------------------------------------------------------------------------------------
 // Grouped form: one persistent launch over the (group, split, row tile, column tile) work list
 // of many independent GEMMs of different shapes (the batched problems of one pipeline stage).
 // Each group's tensor maps and epilogue arguments live in device memory; unit u belongs to the
@@ -816,6 +1106,46 @@ int launch_tc(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
     return NQS_OK;
 }
 
+// The paired form: clusters of two CTAs, as many clusters as can be resident at once (the SMs
+// of a GPC pair up; an odd SM left over in a GPC stays idle), at most one per 256 x BN unit.
+template <int BN>
+int launch_tc_pair(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
+                   const CUtensorMap& tct, const CUtensorMap& tp, const TcArgs& a,
+                   cudaStream_t s) {
+    const int smem = TcSmem2<BN>::BYTES;
+    NQS_CK(cudaFuncSetAttribute(k_gemm_tc_pair<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem));
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters = 0;  // per tile width (one template instance each)
+    if (max_clusters == 0) {
+        cfg.gridDim = dim3(2 * (num_sms() / 2), 1, 1);
+        int n = 0;
+        NQS_CK(cudaOccupancyMaxActiveClusters(&n, k_gemm_tc_pair<BN>, &cfg));
+        if (n <= 0) return NQS_ERR_UNSUPPORTED;
+        max_clusters = n;
+    }
+    const int units = ((a.N + BN - 1) / BN) * ((a.M + 255) / 256) * a.splits;
+    const int clusters = units < max_clusters ? units : max_clusters;
+    cfg.gridDim = dim3(2 * clusters, 1, 1);
+    {
+        ProfScope prof_(PROF_GEMM, s);
+        NQS_CK(cudaLaunchKernelEx(&cfg, k_gemm_tc_pair<BN>, ta, tb, tc, tct, tp, a));
+    }
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
 }  // namespace
 
 // the tile width a shape gets without tuning
@@ -838,10 +1168,14 @@ static int tc_split_count(int tiles, int nkb) {
 }
 
 // launch with a given tile width
+static bool g_pair = true;  // nqs_set_gemm_pairing
+
 static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
+    // 256-column tiles run in the paired (two-SM) form
+    const bool pair = g_pair && BN == 256;
     CUtensorMap ta, tb;
     NQS_TRY(make_map(&ta, g.A, g.M, g.K, g.lda, 128));
-    NQS_TRY(make_map(&tb, g.B, g.N, g.K, g.ldb, BN));
+    NQS_TRY(make_map(&tb, g.B, g.N, g.K, g.ldb, pair ? BN / 2 : BN));
     TcArgs a;
     memset(&a, 0, sizeof a);
     a.M = g.M;
@@ -900,9 +1234,10 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
         }
     }
     a.tma_c = tma ? 1 : 0;
-    int st = BN == 64 ? launch_tc<64>(ta, tb, tc, tct, tp, a, s)
-                      : (BN == 128 ? launch_tc<128>(ta, tb, tc, tct, tp, a, s)
-                                   : launch_tc<256>(ta, tb, tc, tct, tp, a, s));
+    int st = pair ? launch_tc_pair<256>(ta, tb, tc, tct, tp, a, s)
+                  : (BN == 64 ? launch_tc<64>(ta, tb, tc, tct, tp, a, s)
+                              : (BN == 128 ? launch_tc<128>(ta, tb, tc, tct, tp, a, s)
+                                           : launch_tc<256>(ta, tb, tc, tct, tp, a, s)));
     NQS_TRY(st);
     if (splits > 1) {
         k_splitk_reduce<<<grid_for((int64_t)g.M * g.N, 256), 256, 0, s>>>(
@@ -1103,6 +1438,11 @@ static int single_bn_for(const TcGemm& g) {
 }
 
 int tc_autotune_on() { return g_autotune ? 1 : 0; }
+
+extern "C" int nqs_set_gemm_pairing(int on) {
+    g_pair = on != 0;
+    return NQS_OK;
+}
 
 extern "C" int nqs_set_autotune(int on) {
     g_autotune = on != 0;

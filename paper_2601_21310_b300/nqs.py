@@ -105,6 +105,7 @@ EXPORTS = {
     "nqs_batch_set_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "nqs_batch_get_mode": (C.c_int, [C.c_void_p]),
     "nqs_set_autotune": (C.c_int, [C.c_int]),
+    "nqs_set_gemm_pairing": (C.c_int, [C.c_int]),
     "nqs_autotune_entries": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "nqs_gemm_bf16": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_int,
                                 C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -616,6 +617,11 @@ class Batch:
 
 def set_autotune(on: bool):
     lib().nqs_set_autotune(1 if on else 0)
+
+
+def set_gemm_pairing(on: bool):
+    """Paired (two-SM, cta_group::2) tensor-core GEMMs for 256-column tiles on or off."""
+    lib().nqs_set_gemm_pairing(1 if on else 0)
 
 
 def autotune_entries():

@@ -9,10 +9,20 @@ from gpu_common import need_gpu, nqs
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(params=[True, False], ids=["paired", "single"])
+def pairing(request):
+    """Both forms of the 256-column tiles: paired (two SMs, cta_group::2) and single-SM."""
+    need_gpu()
+    N_ = nqs()
+    N_.set_gemm_pairing(request.param)
+    yield request.param
+    N_.set_gemm_pairing(True)
+
+
 @pytest.mark.parametrize("M,N,K", [(128, 64, 64), (64, 32, 64), (300, 100, 200), (1000, 256, 256),
                                    (16384, 256, 256), (256, 256, 16384), (720, 512, 4104),
-                                   (130, 250, 72)])
-def test_gemm_bf16_matches_torch(M, N, K):
+                                   (130, 250, 72), (200, 2016, 136), (4096 + 77, 1000, 1024)])
+def test_gemm_bf16_matches_torch(M, N, K, pairing):
     need_gpu()
     N_ = nqs()
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N * 3 + K)
@@ -23,6 +33,27 @@ def test_gemm_bf16_matches_torch(M, N, K):
     bound = (A.double().abs() @ B.double().abs().T) * 2e-6 + 1e-6
     err = (C.double() - ref).abs()
     assert bool((err <= bound).all()), float((err / bound).max())
+
+
+def test_gemm_paired_and_single_agree():
+    """The paired (M = 256 over two SMs) and single-SM forms give the same FP32 results on a
+    shape with ragged rows and columns, a multi-wave one and a split-K one, up to the bound of
+    the FP32 accumulation (the two forms sum each output over k in the same order)."""
+    need_gpu()
+    N_ = nqs()
+    try:
+        for (M, N, K) in [(1000, 300, 200), (40000, 1024, 256), (512, 512, 65536)]:
+            g = torch.Generator(device="cuda").manual_seed(M + N + K)
+            A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+            B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+            N_.set_gemm_pairing(True)
+            Cp = N_.gemm_bf16(A, B)
+            N_.set_gemm_pairing(False)
+            Cs = N_.gemm_bf16(A, B)
+            bound = (A.float().abs() @ B.float().abs().T) * 2e-6 + 1e-6
+            assert bool(((Cp - Cs).abs() <= bound).all())
+    finally:
+        N_.set_gemm_pairing(True)
 
 
 def test_gemm_rejects_unaligned_stride():
