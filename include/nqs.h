@@ -430,6 +430,13 @@ int nqs_select(nqs_problem* problem, const uint64_t* T, const double* logabs, in
  * for strides the tensor-memory-access unit cannot take. */
 int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K,
                   float* C, int64_t ldc, int* err_flag, nqs_stream_t stream);
+/* The same GEMM with either operand stored MN-major (the layout the weight gradients of the
+ * network read: row-major activations, no transposed copy): a_mn = 1 means A[m][k] is at
+ * A[k * lda + m] (A is [K][lda], m contiguous, lda >= M); b_mn = 1 means B[n][k] is at
+ * B[k * ldb + n]. a_mn = b_mn = 0 is nqs_gemm_bf16. Alignment rules and errors as above. */
+int nqs_gemm_bf16_ex(const void* A, int64_t lda, int a_mn, const void* B, int64_t ldb, int b_mn,
+                     int M, int N, int K, float* C, int64_t ldc, int* err_flag,
+                     nqs_stream_t stream);
 
 /* ---- failure detection and memory accounting (not steps of the method) ------------------ */
 /* Check of the timeout path: one device thread waits, with the same bounded mbarrier wait as

@@ -1018,11 +1018,10 @@ int net_backward(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f, 
 }
 
 // ------------------------------------------------------------------------------------------
-// mixed form on tensor cores (tcgen05): every GEMM operand is K-major, so the activations
-// that later act as the reduction operand of a weight gradient (K = |S|) are also kept
-// transposed ([H][ldM], ldM = |S| rounded up to 8 for 16-byte TMA strides).
+// mixed form on tensor cores (tcgen05): the layer GEMMs take K-major operands; the weight
+// gradients (K = |S|) read the row-major activations and adjoints as MN-major operands, so no
+// transposed copy of an [|S|][H] matrix is made. The transposes below are of the weights.
 // ------------------------------------------------------------------------------------------
-// dst[c][r] = src[r][c] for a bf16 matrix, 32x32 tiles through shared memory
 // dst[c][r] = src[r][c] for r < R, c < Cn: 64 x 64 tiles through shared memory. Each thread
 // moves 8 consecutive elements (16 bytes) on the global side when the row is whole and aligned
 // (vec), else element by element; the shared tile's row stride of 66 elements (33 words) keeps
@@ -1127,63 +1126,70 @@ __global__ void k_pad_cols_bf16(const __nv_bfloat16* __restrict__ W, int R, int 
     }
 }
 
-// out[r] = sum over the first M entries of row r of X [R][ld] (bf16), FP32, fixed order: each
-// block sums one chunk of ROWSUM_CHUNK entries of one row (16-byte loads, a fixed tree), then
-// one thread per row adds the chunk partials in order
+// chunk length of the bias-gradient row sums of the batched problems (k_g_bias_grads)
 #define ROWSUM_CHUNK 16384
-__global__ void __launch_bounds__(256) k_rowsum_part(const __nv_bfloat16* __restrict__ X, int64_t M,
-                                                     int64_t ld, float* __restrict__ part,
-                                                     int nchunks) {
-    __shared__ float red[8];
-    const int r = blockIdx.y, c = blockIdx.x;
-    const __nv_bfloat16* row = X + (int64_t)r * ld;
-    const int64_t c0 = (int64_t)c * ROWSUM_CHUNK;
-    const int64_t c1 = c0 + ROWSUM_CHUNK < M ? c0 + ROWSUM_CHUNK : M;
-    float acc = 0.f;
-    if ((ld % 8) == 0) {
-        const int64_t v1 = c0 + ((c1 - c0) & ~(int64_t)7);
-        for (int64_t i = c0 + 8 * threadIdx.x; i < v1; i += 8 * 256) {
-            const uint4 pk = *(const uint4*)(row + i);
+
+// out[n] = sum over the M rows of X [M][ld] (bf16) of column n, FP32 with compensated
+// (Kahan) additions, fixed order: each block sums COLSUM_ROWS rows in row order (thread t:
+// columns 8t .. 8t + 7 by one 16-byte load per row), then one thread per column adds the
+// blocks' partial sums in order. The compensation keeps the error near one rounding of the
+// result whatever |S|, so the order of the terms does not show at the level of FP32.
+#define COLSUM_ROWS 2048
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+__global__ void __launch_bounds__(256) k_colsum_part(const __nv_bfloat16* __restrict__ X, int64_t M,
+                                                     int N, int64_t ld, float2* __restrict__ part) {
+    const int64_t r0 = (int64_t)blockIdx.x * COLSUM_ROWS;
+    const int64_t r1 = r0 + COLSUM_ROWS < M ? r0 + COLSUM_ROWS : M;
+    for (int c8 = 8 * threadIdx.x; c8 < N; c8 += 8 * 256) {
+        float acc[8], cmp[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = 0.f;
+        for (int64_t r = r0; r < r1; ++r) {
+            const uint4 pk = *(const uint4*)(X + r * ld + c8);
             const __nv_bfloat162* h2 = (const __nv_bfloat162*)&pk;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const float2 f = __bfloat1622float2(h2[t]);
-                acc += f.x + f.y;
+                kahan_add(acc[2 * t], cmp[2 * t], f.x);
+                kahan_add(acc[2 * t + 1], cmp[2 * t + 1], f.y);
             }
         }
-        for (int64_t i = v1 + threadIdx.x; i < c1; i += 256) acc += __bfloat162float(row[i]);
-    } else {
-        for (int64_t i = c0 + threadIdx.x; i < c1; i += 256) acc += __bfloat162float(row[i]);
-    }
+        float2* out = part + (int64_t)blockIdx.x * N;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL_MASK, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.f;
-        for (int k = 0; k < 8; ++k) t += red[k];
-        part[(int64_t)r * nchunks + c] = t;
+        for (int t = 0; t < 8; ++t)
+            if (c8 + t < N) out[c8 + t] = make_float2(acc[t], cmp[t]);
     }
 }
 
-__global__ void k_rowsum_final(const float* __restrict__ part, int R, int nchunks,
+__global__ void k_colsum_final(const float2* __restrict__ part, int N, int nblocks,
                                float* __restrict__ out) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    float t = 0.f;
-    for (int c = 0; c < nchunks; ++c) t += part[(int64_t)r * nchunks + c];
-    out[r] = t;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float t = 0.f, c = 0.f;
+    for (int b = 0; b < nblocks; ++b) {
+        const float2 p = part[(int64_t)b * N + n];
+        kahan_add(t, c, p.x);
+        kahan_add(t, c, -p.y);  // the block's own compensation (its sum's missing part, negated)
+    }
+    out[n] = t;
 }
 
-static int rowsum_bf16(Scratch& sc, const void* X, int R, int64_t M, int64_t ld, float* out,
+// ld: a multiple of 8 with room for N rounded up to 8 (the padding columns are read, not used)
+static int colsum_bf16(Scratch& sc, const void* X, int64_t M, int N, int64_t ld, float* out,
                        cudaStream_t s) {
-    const int nchunks = (int)((M + ROWSUM_CHUNK - 1) / ROWSUM_CHUNK);
-    float* part;
-    NQS_TRY(sc.get(&part, (size_t)R * nchunks));
-    k_rowsum_part<<<dim3((unsigned)nchunks, (unsigned)R), 256, 0, s>>>(
-        (const __nv_bfloat16*)X, M, ld, part, nchunks);
+    if (ld % 8 || ld < ((N + 7) & ~7) || ((uintptr_t)X & 15)) return NQS_ERR_ARG;
+    const int nblocks = (int)((M + COLSUM_ROWS - 1) / COLSUM_ROWS);
+    float2* part;
+    NQS_TRY(sc.get(&part, (size_t)nblocks * N));
+    k_colsum_part<<<(unsigned)nblocks, 256, 0, s>>>((const __nv_bfloat16*)X, M, N, ld, part);
     NQS_CK_LAUNCH();
-    k_rowsum_final<<<(R + 255) / 256, 256, 0, s>>>(part, R, nchunks, out);
+    k_colsum_final<<<(N + 255) / 256, 256, 0, s>>>(part, N, nblocks, out);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }
@@ -1195,7 +1201,6 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
     memset(&f, 0, sizeof f);
     f.M = M;
     f.tc = true;
-    f.ldM = (M + 7) & ~(int64_t)7;
     f.logabs = logabs;
     f.sign = sign;
     f.err = net->prob->err_word;
@@ -1203,9 +1208,6 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
     NQS_TRY(sc.get((__nv_bfloat16**)&f.H2, M * H2));
     NQS_TRY(sc.get((float**)&f.Phi, M * nout));
     if (keep) {
-        NQS_TRY(sc.get((__nv_bfloat16**)&f.H1T, (size_t)H1 * f.ldM));
-        NQS_TRY(sc.get((__nv_bfloat16**)&f.H2T, (size_t)H2 * f.ldM));
-        NQS_TRY(sc.get((__nv_bfloat16**)&f.XT, (size_t)nin * f.ldM));
         NQS_TRY(sc.get((float**)&f.Ainv_a, M * P.na * P.na));
         NQS_TRY(sc.get((float**)&f.Ainv_b, M * P.nb * P.nb));
     }
@@ -1226,7 +1228,8 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
     k_pad_cols_bf16<<<grid_for((int64_t)H1 * ldX, 256), 256, 0, s>>>(
         (const __nv_bfloat16*)net->p[0], H1, nin, ldX, W1p);
     NQS_CK_LAUNCH();
-    if (keep) NQS_TRY(transpose_bf16(X, M, nin, ldX, f.XT, f.ldM, s));
+    f.X = X;
+    f.ldX = ldX;
     TcGemm g;
     memset(&g, 0, sizeof g);
     g.err = f.err;
@@ -1242,12 +1245,10 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
     g.C = f.H1;
     g.ldc = H1;
     g.c_bf16 = 1;
-    g.CT = keep ? (__nv_bfloat16*)f.H1T : nullptr;
-    g.ldct = f.ldM;
     NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
     memset(&g, 0, sizeof g);
     g.err = f.err;
-    // layer 2: H2 = tanh(H1 W2^T + b2), with the transposed copy for dW3
+    // layer 2: H2 = tanh(H1 W2^T + b2)
     g.A = (const __nv_bfloat16*)f.H1;
     g.lda = H1;
     g.B = (const __nv_bfloat16*)net->p[2];
@@ -1260,8 +1261,6 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
     g.C = f.H2;
     g.ldc = H2;
     g.c_bf16 = 1;
-    g.CT = keep ? (__nv_bfloat16*)f.H2T : nullptr;
-    g.ldct = f.ldM;
     NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
     // layer 3: Phi = Phi0 + (H2 W3^T + b3)
     memset(&g, 0, sizeof g);
@@ -1295,7 +1294,7 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
 static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f,
                              const double* w, void* grad, cudaStream_t s) {
     const ProblemDev& P = net->prob->d;
-    const int64_t M = f.M, ldM = f.ldM;
+    const int64_t M = f.M;
     const int H1 = net->H1, H2 = net->H2, nin = net->nin, nout = net->nout;
     const int64_t ldP = (nout + 7) & ~7;
     float* G = (float*)grad;
@@ -1305,24 +1304,21 @@ static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, co
     float* gb2 = gW2 + (size_t)H2 * H1;
     float* gW3 = gb2 + H2;
     float* gb3 = gW3 + (size_t)nout * H2;
-    __nv_bfloat16 *dPhi, *dPhiT, *W3T, *W2T, *dZ2, *dZ2T, *dZ1T;
+    __nv_bfloat16 *dPhi, *W3T, *W2T, *dZ2, *dZ1;
     NQS_TRY(sc.get(&dPhi, M * ldP));
-    NQS_TRY(sc.get(&dPhiT, (size_t)nout * ldM));
     NQS_TRY(sc.get(&W3T, (size_t)H2 * ldP));
     NQS_TRY(sc.get(&W2T, (size_t)H1 * H2));
     NQS_TRY(sc.get(&dZ2, M * H2));
-    NQS_TRY(sc.get(&dZ2T, (size_t)H2 * ldM));
-    NQS_TRY(sc.get(&dZ1T, (size_t)H1 * ldM));
+    NQS_TRY(sc.get(&dZ1, M * H1));
     NQS_CK(cudaMemsetAsync(dPhi, 0, M * ldP * 2, s));
     k_adjoint<float, __nv_bfloat16><<<grid_for(M * 32, 256, 148 * 64), 256, 0, s>>>(
         (const ulonglong2*)dets, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a,
         (const float*)f.Ainv_b, dPhi, ldP);
     NQS_CK_LAUNCH();
-    NQS_TRY(transpose_bf16(dPhi, M, nout, ldP, dPhiT, ldM, s));  // [M][nout] -> [nout][ldM]
     NQS_TRY(transpose_bf16(net->p[4], nout, H2, H2, W3T, ldP, s));  // W3 [nout][H2] -> [H2][nout]
     NQS_TRY(transpose_bf16(net->p[2], H2, H1, H1, W2T, H2, s));     // W2 [H2][H1] -> [H1][H2]
     TcGemm g;
-    // dZ2 = (dPhi W3) * (1 - H2^2), row-major and transposed
+    // dZ2 = (dPhi W3) * (1 - H2^2)
     memset(&g, 0, sizeof g);
     g.err = f.err;
     g.A = dPhi;
@@ -1338,10 +1334,8 @@ static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, co
     g.C = dZ2;
     g.ldc = H2;
     g.c_bf16 = 1;
-    g.CT = dZ2T;
-    g.ldct = ldM;
     NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
-    // dZ1^T = ((dZ2 W2) * (1 - H1^2))^T
+    // dZ1 = (dZ2 W2) * (1 - H1^2)
     memset(&g, 0, sizeof g);
     g.err = f.err;
     g.A = dZ2;
@@ -1354,19 +1348,23 @@ static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, co
     g.epi = EPI_TANH_BWD;
     g.aux = (const __nv_bfloat16*)f.H1;
     g.ld_aux = H1;
-    g.CT = dZ1T;
-    g.ldct = ldM;
+    g.C = dZ1;
+    g.ldc = H1;
+    g.c_bf16 = 1;
     NQS_TRY(gemm_bf16_tcgen05(g, sc, s));
-    // weight gradients: reductions over |S| (K = M), split across CTAs
-    auto wgrad = [&](const __nv_bfloat16* At, int rows, const __nv_bfloat16* Bt, int cols,
-                     float* out) -> int {
+    // weight gradients dW = dZ^T H: reductions over |S| (K = M) with both operands read
+    // row-major ([M][ld], MN-major), split across CTAs
+    auto wgrad = [&](const __nv_bfloat16* dZ, int64_t ldz, int rows, const __nv_bfloat16* Hm,
+                     int64_t ldh, int cols, float* out) -> int {
         TcGemm q;
         memset(&q, 0, sizeof q);
         q.err = f.err;
-        q.A = At;
-        q.lda = ldM;
-        q.B = Bt;
-        q.ldb = ldM;
+        q.A = dZ;
+        q.lda = ldz;
+        q.a_mn = 1;
+        q.B = Hm;
+        q.ldb = ldh;
+        q.b_mn = 1;
         q.M = rows;
         q.N = cols;
         q.K = (int)M;
@@ -1375,12 +1373,12 @@ static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, co
         q.ldc = cols;
         return gemm_bf16_tcgen05(q, sc, s);
     };
-    NQS_TRY(wgrad(dPhiT, nout, (const __nv_bfloat16*)f.H2T, H2, gW3));
-    NQS_TRY(wgrad(dZ2T, H2, (const __nv_bfloat16*)f.H1T, H1, gW2));
-    NQS_TRY(wgrad(dZ1T, H1, (const __nv_bfloat16*)f.XT, nin, gW1));
-    NQS_TRY(rowsum_bf16(sc, dPhiT, nout, M, ldM, gb3, s));
-    NQS_TRY(rowsum_bf16(sc, dZ2T, H2, M, ldM, gb2, s));
-    NQS_TRY(rowsum_bf16(sc, dZ1T, H1, M, ldM, gb1, s));
+    NQS_TRY(wgrad(dPhi, ldP, nout, (const __nv_bfloat16*)f.H2, H2, H2, gW3));
+    NQS_TRY(wgrad(dZ2, H2, H2, (const __nv_bfloat16*)f.H1, H1, H1, gW2));
+    NQS_TRY(wgrad(dZ1, H1, H1, (const __nv_bfloat16*)f.X, f.ldX, nin, gW1));
+    NQS_TRY(colsum_bf16(sc, dPhi, M, nout, ldP, gb3, s));
+    NQS_TRY(colsum_bf16(sc, dZ2, M, H2, H2, gb2, s));
+    NQS_TRY(colsum_bf16(sc, dZ1, M, H1, H1, gb1, s));
     return NQS_OK;
 }
 
@@ -1557,9 +1555,8 @@ int g_transpose_dphi(const GProb* P, const GDims& d, const int64_t* tile_off, in
 }
 
 // bias gradients: the row sums of dPhiT (db3), dZ2T (db2) and dZ1T (db1) over the first M
-// columns, in the order of k_rowsum_part / k_rowsum_final (chunks of ROWSUM_CHUNK reduced by a
-// fixed tree, the chunk sums added in order). blockIdx.x = row, blockIdx.y = problem,
-// blockIdx.z = which matrix.
+// columns, FP32 in a fixed order (chunks of ROWSUM_CHUNK entries reduced by a fixed tree, the
+// chunk sums added in order). blockIdx.x = row, blockIdx.y = problem, blockIdx.z = which matrix.
 __global__ void __launch_bounds__(256) k_g_bias_grads(const GProb* __restrict__ Pv) {
     const GProb& P = Pv[blockIdx.y];
     if (!P.grad) return;

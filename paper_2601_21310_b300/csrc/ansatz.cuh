@@ -26,8 +26,10 @@ int gemm_f64(const GemmArgs& g, cudaStream_t s);
 int gemm_bf16_simt(const GemmArgs& g, bool out_bf16, cudaStream_t s);
 
 // tcgen05 path (gemm_tc.cu): C[m][n] = epi(sum_k A[m][k] B[n][k]), A [M][lda] and B [N][ldb]
-// bfloat16 with k contiguous (lda, ldb multiples of 8). Optional row-major C (bf16 or float)
-// and transposed bf16 copy CT[n][m]. EPI_STORE with float C may split K across CTAs.
+// bfloat16 with k contiguous (lda, ldb multiples of 8); with a_mn (b_mn) set, A (B) is stored
+// with m (n) contiguous instead, A[m][k] at A[k * lda + m] (the row-major activations of a
+// weight gradient, read without a transposed copy). Optional row-major C (bf16 or float) and
+// transposed bf16 copy CT[n][m]. EPI_STORE with float C may split K across CTAs.
 struct TcGemm {
     const __nv_bfloat16* A;
     int64_t lda;
@@ -45,6 +47,7 @@ struct TcGemm {
     const __nv_bfloat16* aux;
     int64_t ld_aux;
     int* err;
+    int a_mn, b_mn;
 };
 int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s);
 
@@ -71,12 +74,10 @@ struct Fwd {
     double* logabs; // [M]
     int8_t* sign;   // [M]
     int* singular;  // device flag
-    // mixed form on tensor cores: transposed copies ([H][ldM], ldM = M rounded up to 8)
+    // mixed form on tensor cores: X is [M][ldX] bf16 (nin padded to 8 with zero columns);
+    // the weight gradients read X, H1 and H2 row-major as MN-major GEMM operands
     bool tc;
-    int64_t ldM;
-    void* H1T;
-    void* H2T;
-    void* XT;       // [nin][ldM]
+    int64_t ldX;
     int* err;       // tensor-core pipeline error word
 };
 

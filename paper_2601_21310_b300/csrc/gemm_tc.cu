@@ -70,7 +70,21 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both operands K-major
+// shared-memory matrix descriptor: MN-major operand, 128-byte swizzle; the tile is a row of
+// 64-element (128-byte) MN atoms 8 KB apart (leading byte offset), each 64 k-rows of 128 bytes
+// with 8-row groups 1024 B apart (stride byte offset)
+__device__ __forceinline__ uint64_t sdesc_sw128_mn(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(8192u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both operands K-major (bits 15 / 16
+// select MN-major A / B)
 template <int BN>
 __device__ __forceinline__ uint32_t idesc_bf16() {
     return (1u << 4)            // D format: F32
@@ -126,7 +140,44 @@ struct TcArgs {
     int splits;
     int tma_c, tma_ct, tma_p;  // stores go through the tensor maps below (else direct)
     int* err;
+    int a_mn, b_mn;          // MN-major operands (TcGemm)
 };
+
+// The operand copies of k-block kb into one stage: K-major, one box of 64 k x rows; MN-major,
+// boxes of 64 (m or n) x 64 k-rows, 8 KB apart. `bar` is a shared::cluster address; pair
+// selects the .cta_group::2 form (the barrier may sit in the other CTA of the pair).
+__device__ __forceinline__ void tma_load_any(bool pair, void* dst, const CUtensorMap* map,
+                                             uint32_t bar, int x, int y) {
+    if (pair)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::"
+            "bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+            "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+            : "memory");
+    else
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+            "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+            : "memory");
+}
+__device__ __forceinline__ void load_operand(bool pair, bool mn, uint8_t* dst,
+                                             const CUtensorMap* map, uint32_t bar, int kb,
+                                             int row0, int rows) {
+    if (!mn) {
+        tma_load_any(pair, dst, map, bar, kb * TC_BK, row0);
+    } else {
+        for (int j = 0; j < rows / 64; ++j)
+            tma_load_any(pair, dst + j * 8192, map, bar, row0 + 64 * j, kb * TC_BK);
+    }
+}
+// descriptor of the operand at saddr and its advance per K = 16 step
+__device__ __forceinline__ uint64_t operand_desc(bool mn, uint32_t saddr) {
+    return mn ? sdesc_sw128_mn(saddr) : sdesc_sw128(saddr);
+}
+__device__ __forceinline__ uint64_t operand_step(bool mn) {
+    return mn ? (uint64_t)(2048u >> 4) : (uint64_t)2;  // 16 k-rows of 128 B, or 32 B in the row
+}
 
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
     asm volatile(
@@ -441,8 +492,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (it >= (uint32_t)ST && !mbar_wait_ab(&empty[s], ph ^ 1u, abort)) break;
                 uint8_t* st = smem + s * L::STAGE;
                 mbar_expect_tx(&full[s], (uint32_t)L::STAGE);
-                tma_load_2d(st, &tmA, &full[s], (w.kb0 + i) * TC_BK, w.m0);
-                tma_load_2d(st + L::A_BYTES, &tmB, &full[s], (w.kb0 + i) * TC_BK, w.n0);
+                const uint32_t fb = smem_u32(&full[s]);
+                load_operand(false, a.a_mn, st, &tmA, fb, w.kb0 + i, w.m0, 128);
+                load_operand(false, a.b_mn, st + L::A_BYTES, &tmB, fb, w.kb0 + i, w.n0, BN);
             }
         }
         // never leave with copies in flight: wait (bounded) for the last load of each stage
@@ -453,7 +505,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t idesc = idesc_bf16<BN>();
+        const uint32_t idesc =
+            idesc_bf16<BN>() | ((uint32_t)a.a_mn << 15) | ((uint32_t)a.b_mn << 16);
+        const uint64_t sa = operand_step(a.a_mn), sb = operand_step(a.b_mn);
         uint32_t it = 0, j = 0;
         for (int u = blockIdx.x; u < units && !*abort; u += gridDim.x, ++j) {
             const Unit w = unit_of(u, a, BN);
@@ -470,11 +524,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint8_t* st = smem + s * L::STAGE;
-                const uint64_t da = sdesc_sw128(smem_u32(st));
-                const uint64_t db = sdesc_sw128(smem_u32(st + L::A_BYTES));
+                const uint64_t da = operand_desc(a.a_mn, smem_u32(st));
+                const uint64_t db = operand_desc(a.b_mn, smem_u32(st + L::A_BYTES));
 #pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk)  // +32 bytes per K=16 step in the atom
-                    umma(acc, da + 2 * kk, db + 2 * kk, idesc, (i | kk) != 0 ? 1u : 0u);
+                for (int kk = 0; kk < TC_BK / 16; ++kk)
+                    umma(acc, da + sa * kk, db + sb * kk, idesc, (i | kk) != 0 ? 1u : 0u);
                 umma_commit(&empty[s]);
             }
             if (!ok) break;
@@ -603,15 +657,6 @@ __device__ __forceinline__ bool mbar_wait_pair(uint64_t* bar, uint32_t parity, v
     }
 }
 
-__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map,
-                                                 uint32_t bar_cluster, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(bar_cluster), "r"(x), "r"(y)
-        : "memory");
-}
-
 template <int BN>
 __device__ __forceinline__ uint32_t idesc_bf16_m256() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -715,9 +760,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 uint8_t* st = smem + s * L::STAGE;
                 if (rank == 0) mbar_expect_tx(&full[s], 2u * (uint32_t)L::STAGE);
                 const uint32_t fb = smem_in_cta(&full[s], 0u);
-                tma_load_2d_pair(st, &tmA, fb, (w.kb0 + i) * TC_BK, w.m0 + (int)rank * 128);
-                tma_load_2d_pair(st + L::A_BYTES, &tmB, fb, (w.kb0 + i) * TC_BK,
-                                 w.n0 + (int)rank * (BN / 2));
+                load_operand(true, a.a_mn, st, &tmA, fb, w.kb0 + i, w.m0 + (int)rank * 128, 128);
+                load_operand(true, a.b_mn, st + L::A_BYTES, &tmB, fb, w.kb0 + i,
+                             w.n0 + (int)rank * (BN / 2), BN / 2);
             }
         }
         // the even CTA's full barriers count both CTAs' copies: waiting (bounded) for the last
@@ -731,7 +776,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else if (warp == 1 && lane == 0 && rank == 0) {
         // ---------------- MMA issuer (even CTA) ----------------
-        const uint32_t idesc = idesc_bf16_m256<BN>();
+        const uint32_t idesc =
+            idesc_bf16_m256<BN>() | ((uint32_t)a.a_mn << 15) | ((uint32_t)a.b_mn << 16);
+        const uint64_t sa = operand_step(a.a_mn), sb = operand_step(a.b_mn);
         uint32_t it = 0, j = 0;
         for (int u = cid; u < units && !*abort; u += ncl, ++j) {
             const Unit w = unit_of_pair(u, a, BN);
@@ -748,11 +795,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint8_t* st = smem + s * L::STAGE;
-                const uint64_t da = sdesc_sw128(smem_u32(st));
-                const uint64_t db = sdesc_sw128(smem_u32(st + L::A_BYTES));
+                const uint64_t da = operand_desc(a.a_mn, smem_u32(st));
+                const uint64_t db = operand_desc(a.b_mn, smem_u32(st + L::A_BYTES));
 #pragma unroll
                 for (int kk = 0; kk < TC_BK / 16; ++kk)
-                    umma_pair(acc, da + 2 * kk, db + 2 * kk, idesc, (i | kk) != 0 ? 1u : 0u);
+                    umma_pair(acc, da + sa * kk, db + sb * kk, idesc, (i | kk) != 0 ? 1u : 0u);
                 umma_commit_pair(&empty[s], (uint16_t)3);
             }
             if (!ok) break;
@@ -1174,8 +1221,11 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
     // 256-column tiles run in the paired (two-SM) form
     const bool pair = g_pair && BN == 256;
     CUtensorMap ta, tb;
-    NQS_TRY(make_map(&ta, g.A, g.M, g.K, g.lda, 128));
-    NQS_TRY(make_map(&tb, g.B, g.N, g.K, g.ldb, pair ? BN / 2 : BN));
+    // K-major: boxes of 64 k x (128 or the B tile's) rows; MN-major: boxes of 64 x 64 k-rows
+    if (g.a_mn) NQS_TRY(make_map(&ta, g.A, g.K, g.M, g.lda, 64));
+    else NQS_TRY(make_map(&ta, g.A, g.M, g.K, g.lda, 128));
+    if (g.b_mn) NQS_TRY(make_map(&tb, g.B, g.K, g.N, g.ldb, 64));
+    else NQS_TRY(make_map(&tb, g.B, g.N, g.K, g.ldb, pair ? BN / 2 : BN));
     TcArgs a;
     memset(&a, 0, sizeof a);
     a.M = g.M;
@@ -1192,6 +1242,8 @@ static int gemm_tc_run(const TcGemm& g, Scratch& sc, cudaStream_t s, int BN) {
     a.aux = g.aux;
     a.ld_aux = g.ld_aux;
     a.err = g.err;
+    a.a_mn = g.a_mn ? 1 : 0;
+    a.b_mn = g.b_mn ? 1 : 0;
     // split K when the output has too few tiles to fill the GPU
     const int tiles = ((g.N + BN - 1) / BN) * ((g.M + 127) / 128);
     const int nkb = (g.K + TC_BK - 1) / TC_BK;
@@ -1281,6 +1333,7 @@ int tc_group_set_create(const TcGemm* gs, int n, int BN, TcGroupSet** out) {
     for (int i = 0; i < n; ++i) {
         const TcGemm& g = gs[i];
         if (g.M <= 0 || g.N <= 0 || g.K <= 0) return fail(NQS_ERR_ARG);
+        if (g.a_mn || g.b_mn) return fail(NQS_ERR_UNSUPPORTED);  // K-major operands only
         if ((g.lda * 2) % 16 || (g.ldb * 2) % 16 || ((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15))
             return fail(NQS_ERR_UNSUPPORTED);
         TcGroupDev& d = host[i];
@@ -1431,7 +1484,8 @@ int heuristic_bn(int N) { return heuristic_bn_shape(N); }
 }  // namespace
 
 static int single_bn_for(const TcGemm& g) {
-    const TuneKey key{g.M, g.N, g.K, g.epi, (g.c_bf16 ? 1 : 0) | (g.CT ? 2 : 0)};
+    const TuneKey key{g.M, g.N, g.K, g.epi,
+                      (g.c_bf16 ? 1 : 0) | (g.CT ? 2 : 0) | (g.a_mn ? 4 : 0) | (g.b_mn ? 8 : 0)};
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
     return it != g_tuned.end() ? it->second : heuristic_bn_shape(g.N);
@@ -1468,7 +1522,8 @@ int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return NQS_ERR_ARG;
     if ((g.lda * 2) % 16 || (g.ldb * 2) % 16 || ((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15))
         return NQS_ERR_UNSUPPORTED;
-    const TuneKey key{g.M, g.N, g.K, g.epi, (g.c_bf16 ? 1 : 0) | (g.CT ? 2 : 0)};
+    const TuneKey key{g.M, g.N, g.K, g.epi,
+                      (g.c_bf16 ? 1 : 0) | (g.CT ? 2 : 0) | (g.a_mn ? 4 : 0) | (g.b_mn ? 8 : 0)};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
@@ -1512,7 +1567,15 @@ int gemm_bf16_tcgen05(const TcGemm& g, Scratch& sc, cudaStream_t s) {
 // ------------------------------------------------------------------------------------------
 extern "C" int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N,
                              int K, float* C, int64_t ldc, int* err_flag, nqs_stream_t stream) {
+    return nqs_gemm_bf16_ex(A, lda, 0, B, ldb, 0, M, N, K, C, ldc, err_flag, stream);
+}
+
+extern "C" int nqs_gemm_bf16_ex(const void* A, int64_t lda, int a_mn, const void* B, int64_t ldb,
+                                int b_mn, int M, int N, int K, float* C, int64_t ldc,
+                                int* err_flag, nqs_stream_t stream) {
     if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0) return NQS_ERR_ARG;
+    if ((a_mn && lda < M) || (!a_mn && lda < K) || (b_mn && ldb < N) || (!b_mn && ldb < K))
+        return NQS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     nqs_problem host;
     memset(&host, 0, sizeof host);
@@ -1533,6 +1596,8 @@ extern "C" int nqs_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t 
     g.C = C;
     g.ldc = ldc;
     g.err = err_flag;
+    g.a_mn = a_mn ? 1 : 0;
+    g.b_mn = b_mn ? 1 : 0;
     return gemm_bf16_tcgen05(g, sc, s);
 }
 

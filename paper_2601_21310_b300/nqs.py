@@ -109,6 +109,9 @@ EXPORTS = {
     "nqs_autotune_entries": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "nqs_gemm_bf16": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int, C.c_int,
                                 C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "nqs_gemm_bf16_ex": (C.c_int, [C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_int64,
+                                   C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64,
+                                   C.c_void_p, C.c_void_p]),
     "nqs_connections_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                           C.c_void_p, C.c_void_p]),
@@ -558,6 +561,27 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor, stream=None) -> torch.Tensor:
                                _stream(stream)), "nqs_gemm_bf16")
     if int(err.item()) != 0:
         raise NQSError("nqs_gemm_bf16: a pipeline wait timed out")
+    return C_
+
+
+def gemm_bf16_ex(A: torch.Tensor, a_mn: bool, B: torch.Tensor, b_mn: bool, M=None, N=None,
+                 stream=None) -> torch.Tensor:
+    """C = A' B'^T with A' = A^T if a_mn else A (A [K][lda] or [M][K]) and B' = B^T if b_mn
+    else B (B [K][ldb] or [N][K]), bfloat16 in, float out (nqs_gemm_bf16_ex). M (N) may be
+    given below the row length of an MN-major A (B): the trailing columns are not read."""
+    A, B = A.contiguous(), B.contiguous()
+    K = A.shape[0] if a_mn else A.shape[1]
+    if M is None:
+        M = A.shape[1] if a_mn else A.shape[0]
+    if N is None:
+        N = B.shape[1] if b_mn else B.shape[0]
+    C_ = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib().nqs_gemm_bf16_ex(_ptr(A), A.shape[1], 1 if a_mn else 0, _ptr(B), B.shape[1],
+                                  1 if b_mn else 0, M, N, K, _ptr(C_), N, _ptr(err),
+                                  _stream(stream)), "nqs_gemm_bf16_ex")
+    if int(err.item()) != 0:
+        raise NQSError("nqs_gemm_bf16_ex: a pipeline wait timed out")
     return C_
 
 

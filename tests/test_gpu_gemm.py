@@ -63,3 +63,26 @@ def test_gemm_rejects_unaligned_stride():
     B = torch.randn(64, 100, device="cuda").to(torch.bfloat16)
     with pytest.raises(N_.NQSError, match="unsupported"):
         N_.gemm_bf16(A, B)
+
+
+@pytest.mark.parametrize("M,N,K,ldb", [(1000, 296, 200, 296), (304, 84, 5000, 88),
+                                       (2016, 1024, 16384, 1024), (136, 250, 72, 256),
+                                       (1024, 256, 4104, 256)])
+@pytest.mark.parametrize("a_mn,b_mn", [(1, 1), (1, 0), (0, 1)])
+def test_gemm_bf16_mn_major_operands(M, N, K, ldb, a_mn, b_mn, pairing):
+    """MN-major operands (A stored [K][M], B stored [K][ldb] with N <= ldb: the row-major
+    activations a weight gradient reads) against the PyTorch reference of the same product,
+    for ragged M / N / K, a row pitch wider than N, and split-K."""
+    need_gpu()
+    N_ = nqs()
+    g = torch.Generator(device="cuda").manual_seed(M * 5 + N * 3 + K + a_mn + 2 * b_mn)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    Bfull = torch.randn(ldb, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = Bfull[:N]
+    Aop = A.T.contiguous() if a_mn else A
+    Bop = Bfull.T.contiguous() if b_mn else B.contiguous()
+    C = N_.gemm_bf16_ex(Aop, bool(a_mn), Bop, bool(b_mn), M=M, N=N)
+    ref = A.double() @ B.double().T
+    bound = (A.double().abs() @ B.double().abs().T) * 2e-6 + 1e-6
+    err = (C.double() - ref).abs()
+    assert bool((err <= bound).all()), float((err / bound).max())
