@@ -51,6 +51,12 @@ def parse():
                          "to 30 orbitals, 1e-6 above (see default_eps_pt2)")
     ap.add_argument("--no-tensor-probe", action="store_true",
                     help="skip the tensor-core GEMM probe on the 42-orbital output-layer shape")
+    ap.add_argument("--tensor-probe-only", default=None, metavar="M,N,K",
+                    help="run only the tensor-core GEMM probe on this shape and print its line "
+                         "(for profiling one GEMM form on a small case)")
+    ap.add_argument("--probe-mn", action="store_true",
+                    help="with --tensor-probe-only: both operands MN-major (the weight-gradient "
+                         "layout: row-major [K][M] and [K][N])")
     ap.add_argument("--no-outer", action="store_true",
                     help="skip the outer-loop measurement (heat-bath set, amplitudes on T, Top-K)")
     ap.add_argument("--buckets", type=int, default=0,
@@ -513,18 +519,25 @@ def run_outer_loop(args, N, P, net, dets, psi, dtype, stream, eps_hb=1e-6):
             "modes": modes}
 
 
-def run_tensor_probe(N, stream, M=1 << 20, Nn=2016, K=1024, reps=10):
+def run_tensor_probe(N, stream, M=1 << 20, Nn=2016, K=1024, reps=10, mn=False):
     """The library's tcgen05 GEMM (nqs_gemm_bf16: bf16 in, FP32 out; 256-column tiles in the
     paired two-SM form) on the output-layer shape of the 42-orbital network (|S| = 2^20 rows,
     2016 outputs, width 1024), timed with CUDA events on the launching stream after warm-up.
     `achieved` is the best of `reps` single launches, each timed alone (the method of the
     measured burst peak: best of 10 timed launches), against that burst peak; `back_to_back`
     is the mean over `reps` launches in a row, which runs into the power cap, against the
-    measured sustained peak."""
-    A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
-    B = torch.randn(Nn, K, device="cuda").to(torch.bfloat16)
+    measured sustained peak. mn: both operands MN-major ([K][M] and [K][N], row-major
+    activations as the weight gradients read them)."""
+    if mn:
+        A = torch.randn(K, M, device="cuda").to(torch.bfloat16)
+        B = torch.randn(K, Nn, device="cuda").to(torch.bfloat16)
+        gemm = lambda: N.gemm_bf16_ex(A, True, B, True)  # noqa: E731
+    else:
+        A = torch.randn(M, K, device="cuda").to(torch.bfloat16)
+        B = torch.randn(Nn, K, device="cuda").to(torch.bfloat16)
+        gemm = lambda: N.gemm_bf16(A, B)  # noqa: E731
     for _ in range(3):
-        N.gemm_bf16(A, B)
+        gemm()
     torch.cuda.synchronize()
     flops = 2.0 * M * Nn * K
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -534,14 +547,14 @@ def run_tensor_probe(N, stream, M=1 << 20, Nn=2016, K=1024, reps=10):
         torch.cuda.synchronize()
         time.sleep(0.02)
         a.record(stream)
-        N.gemm_bf16(A, B)
+        gemm()
         b.record(stream)
         b.synchronize()
         singles.append(a.elapsed_time(b))
     a, b = ev[0]
     a.record(stream)
     for _ in range(reps):
-        N.gemm_bf16(A, B)
+        gemm()
     b.record(stream)
     b.synchronize()
     ms_b2b = a.elapsed_time(b) / reps
@@ -553,7 +566,8 @@ def run_tensor_probe(N, stream, M=1 << 20, Nn=2016, K=1024, reps=10):
     peak_sus = peaks.get("bf16_tflops_sustained", 1400.0)
     del A, B
     torch.cuda.empty_cache()
-    return {"kernel": "k_gemm_tc_pair", "shape": [M, Nn, K], "bound": "tensor", "ms": ms,
+    return {"kernel": "k_gemm_tc_pair", "shape": [M, Nn, K],
+            "operands": "MN-major" if mn else "K-major", "bound": "tensor", "ms": ms,
             "ms_median_single": float(np.median(singles)),
             "achieved": round(tf, 1), "peak": peak, "unit": "TFLOP/s",
             "frac": round(tf / peak, 4), "peak_source": kind + " bf16 burst",
@@ -825,6 +839,14 @@ def main():
         res = run_reference(args, ws, rank)
         if res is not None:
             print(json.dumps(res))
+        return
+    if args.tensor_probe_only:
+        M, Nn, K = (int(v) for v in args.tensor_probe_only.split(","))
+        import paper_2601_21310_b300.nqs as N
+        from paper_2601_21310_b300 import build as B
+        B.build()
+        print(json.dumps(run_tensor_probe(N, torch.cuda.current_stream(), M=M, Nn=Nn, K=K,
+                                          mn=args.probe_mn)))
         return
     if ws > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
