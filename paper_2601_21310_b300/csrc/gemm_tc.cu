@@ -124,6 +124,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// the same load without the wait: the registers are valid only after tmem_wait_ld(r), whose
+// read-write operands keep every use of r behind the wait
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]),
+                   "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]),
+                   "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 struct TcArgs {
     int M, N, K;
     int epi;                 // EPI_* (ansatz.cuh)
@@ -824,24 +851,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = w.m0 + q * 32 + lane;
             const bool row_ok = row < a.M;
-#pragma unroll 1
-            for (int c = c_lo; c < c_hi; c += 32) {
-                uint32_t r[32];
-                if (w.nk > 0) {
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)c, r);
-                } else {
-#pragma unroll
-                    for (int t = 0; t < 32; ++t) r[t] = 0u;
-                }
+            uint8_t* stage = epi_stage + (warp - 2) * 4096;
+            auto drain = [&](int c, const uint32_t (&r)[32]) {
                 if (a.tma_c)
-                    epilogue32_tma(a, w, row, row_ok, w.n0 + c, w.m0 + q * 32, r,
-                                   epi_stage + (warp - 2) * 4096, &tmC, &tmCT, &tmP);
+                    epilogue32_tma(a, w, row, row_ok, w.n0 + c, w.m0 + q * 32, r, stage, &tmC,
+                                   &tmCT, &tmP);
                 else
                     epilogue32(a, w, row, row_ok, w.n0 + c, r);
+            };
+            auto release = [&]() {  // every accumulator load of this warp has completed
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(tempty0 + b * 8u);
+            };
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + b * BN;
+            if (w.nk > 0) {
+                // the load of the next 32 columns is in flight while this block is staged and
+                // stored; the accumulator is released as soon as its last load has completed
+                uint32_t ra[32], rb[32];
+                tmem_ld32_async(tbase + (uint32_t)c_lo, ra);
+#pragma unroll 1
+                for (int c = c_lo; c < c_hi; c += 64) {
+                    tmem_wait_ld(ra);
+                    if (c + 32 < c_hi) tmem_ld32_async(tbase + (uint32_t)(c + 32), rb);
+                    else release();
+                    drain(c, ra);
+                    if (c + 32 < c_hi) {
+                        tmem_wait_ld(rb);
+                        if (c + 64 < c_hi) tmem_ld32_async(tbase + (uint32_t)(c + 64), ra);
+                        else release();
+                        drain(c + 32, rb);
+                    }
+                }
+            } else {
+                uint32_t r[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) r[t] = 0u;
+                release();
+#pragma unroll 1
+                for (int c = c_lo; c < c_hi; c += 32) drain(c, r);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(tempty0 + b * 8u);
         }
         if (a.tma_c && lane == 0) bulk_wait0();
     }
