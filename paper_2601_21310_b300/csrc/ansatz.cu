@@ -512,7 +512,7 @@ static int launch_lu_reg(const uint64_t* dets, int64_t M, int norb, int nel, int
     }
 }
 
-// Mixed-form blocks of 13..32 rows: one warp per (configuration, spin block), lane i holds row i
+// Mixed-form blocks of 25..32 rows: one warp per (configuration, spin block), lane i holds row i
 // of the block in registers (N is a template parameter, so every register index is static).
 // Partial pivoting as in the other kernels (largest |a_ik|; on ties the row that would sit
 // lowest after the row exchanges so far, tracked per lane as its current position): a warp
@@ -673,6 +673,259 @@ __global__ void __launch_bounds__(LU_LANE_WARPS * 32) k_lu_lane(
     }
 }
 
+// Mixed-form blocks of 13..24 rows, four blocks per warp: the eight lanes of group g (lanes
+// 8g .. 8g + 7) factor the block of configuration 4w + g, lane l holding rows l, l + 8, l + 16
+// of it in registers. The pivot rule, the row-exchange sign and the arithmetic (the multiplier
+// a_ik * (1 / a_kk) rounded, then one FMA per entry) are those of k_lu_lane. The pivot search
+// reduces one 64-bit key per lane over the group (|a_ik| bits, then the complement of the row's
+// position, so that ties go to the lowest position); the pivot row reaches the group through
+// shared memory (16-byte stores by its owner, 16-byte broadcast loads by every lane), so each
+// shared-memory access serves four blocks where k_lu_lane spends one shuffle per entry and
+// block, and no lane idles (k_lu_lane leaves 32 - n lanes without a row). Inverse: each lane
+// solves the columns of its own rows, the solves sharing every factor load.
+#define LU_GRP_WARPS 4
+template <int N>
+__global__ void __launch_bounds__(LU_GRP_WARPS * 32) k_lu_grp(
+    const ulonglong2* __restrict__ dets, int64_t M, int norb, int nel, int spin,
+    const float* __restrict__ Phi, double* __restrict__ la_out, int* __restrict__ ex_out,
+    int8_t* __restrict__ sg_out, float* __restrict__ Ainv, int* singular) {
+    constexpr int R = (N + 7) / 8;     // rows per lane
+    constexpr int LD = (N + 3) & ~3;  // factor rows padded to 16 bytes
+    __shared__ __align__(16) float fac_s[LU_GRP_WARPS][4][N][LD];
+    __shared__ __align__(16) float prow_s[LU_GRP_WARPS][4][LD];
+    __shared__ float dinv_s[LU_GRP_WARPS][4][N];
+    __shared__ uint8_t occ_s[LU_GRP_WARPS][4][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 3, l = lane & 7;
+    const int col0 = spin == 0 ? 0 : nel - N;
+    const bool vec = ((nel | col0) & 3) == 0 && (N & 3) == 0;
+    float(*F)[LD] = fac_s[warp][g];
+    float* prow = prow_s[warp][g];
+    float* dinv = dinv_s[warp][g];
+    uint8_t* occ = occ_s[warp][g];
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t mw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; mw * 4 < M;
+         mw += wstride) {
+        const int64_t m = mw * 4 + g;
+        const bool mv = m < M;
+        uint64_t wb = 0;
+        if (mv) {
+            const ulonglong2 x = dets[m];
+            wb = spin == 0 ? x.x : x.y;
+        }
+        for (int p = l; p < norb; p += 8) {
+            const uint64_t below = p == 0 ? 0ull : ((1ull << p) - 1ull);
+            if ((wb >> p) & 1ull) occ[__popcll(wb & below)] = (uint8_t)p;
+        }
+        __syncwarp();
+        float r[R][N];
+        bool used[R];
+        int pos[R], step[R];
+        float piv_own[R], dinv_own[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int i = l + 8 * t;
+            const bool live = mv && i < N;
+            used[t] = !live;  // rows past the block (and groups past M) never pivot
+            pos[t] = i;
+            step[t] = 0;
+            piv_own[t] = 1.f;
+            dinv_own[t] = 1.f;
+            if (live) {
+                const float* row =
+                    Phi + m * (int64_t)norb * nel + (int64_t)occ[i] * nel + col0;
+                if (vec) {
+#pragma unroll
+                    for (int c = 0; c < N; c += 4) {
+                        const float4 v = *(const float4*)(row + c);
+                        r[t][c] = v.x;
+                        r[t][c + 1] = v.y;
+                        r[t][c + 2] = v.z;
+                        r[t][c + 3] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < N; ++c) r[t][c] = row[c];
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < N; ++c) r[t][c] = 0.f;
+            }
+        }
+        int sgn = 1;
+        bool ok = mv;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            unsigned long long best = 0ull;
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (!used[t]) {
+                    const unsigned long long key =
+                        ((unsigned long long)__float_as_uint(fabsf(r[t][k])) << 32) |
+                        (unsigned long long)(~(unsigned)pos[t]);
+                    best = key > best ? key : best;
+                }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(FULL_MASK, best, o, 8);
+                best = other > best ? other : best;
+            }
+            if ((best >> 32) == 0ull) ok = false;  // no nonzero pivot left: singular block
+            const int pmin = (int)(~(unsigned)best);
+            int tstar = -1;
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (ok && !used[t] && pos[t] == pmin) tstar = t;
+            __syncwarp();  // the previous step's reads of prow are done
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (t == tstar) {
+#pragma unroll
+                    for (int c = k & ~3; c < LD; c += 4)
+                        *(float4*)&prow[c] =
+                            make_float4(c < N ? r[t][c] : 0.f, c + 1 < N ? r[t][c + 1] : 0.f,
+                                        c + 2 < N ? r[t][c + 2] : 0.f,
+                                        c + 3 < N ? r[t][c + 3] : 0.f);
+                }
+            __syncwarp();
+            if (ok) {
+                const float piv = prow[k];
+                if (pmin != k) {  // the equivalent row exchange of positions k and pmin
+                    sgn = -sgn;
+#pragma unroll
+                    for (int t = 0; t < R; ++t)
+                        if (pos[t] == k) pos[t] = pmin;
+                }
+                if (piv < 0.f) sgn = -sgn;
+                const float rp = 1.0f / piv;
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+                    if (t == tstar) {
+                        used[t] = true;
+                        pos[t] = k;
+                        step[t] = k;
+                        piv_own[t] = fabsf(piv);
+                        dinv_own[t] = rp;
+                    }
+#pragma unroll
+                for (int t = 0; t < R; ++t) {
+                    if (used[t]) continue;
+                    const float f = r[t][k] * rp;
+#pragma unroll
+                    for (int c = (k + 1) & ~3; c < N; c += 4) {
+                        const float4 u4 = *(const float4*)&prow[c];
+                        if (c > k) r[t][c] = fmaf(-f, u4.x, r[t][c]);
+                        if (c + 1 > k && c + 1 < N) r[t][c + 1] = fmaf(-f, u4.y, r[t][c + 1]);
+                        if (c + 2 > k && c + 2 < N) r[t][c + 2] = fmaf(-f, u4.z, r[t][c + 2]);
+                        if (c + 3 > k && c + 3 < N) r[t][c + 3] = fmaf(-f, u4.w, r[t][c + 3]);
+                    }
+                    r[t][k] = f;
+                }
+            }
+        }
+        // |det| over the group: mantissa in [0.5, 1) and exponent of each pivot, a product tree
+        double mt = 1.0;
+        int et = 0;
+#pragma unroll
+        for (int t = 0; t < R; ++t)
+            if (ok && l + 8 * t < N) {
+                int e = 0;
+                mt *= (double)frexpf(piv_own[t], &e);
+                et += e;
+            }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+            mt *= __shfl_xor_sync(FULL_MASK, mt, o, 8);
+            et += __shfl_xor_sync(FULL_MASK, et, o, 8);
+        }
+        if (l == 0 && mv) {
+            la_out[m] = ok ? mt : 0.0;
+            ex_out[m] = ok ? et : 0;
+            sg_out[m] = (int8_t)(ok ? sgn : 0);
+            if (!ok && singular) atomicOr(singular, 1);
+        }
+        if (Ainv) {
+            float* out = Ainv + m * (int64_t)N * N;
+            if (ok) {
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+                    if (l + 8 * t < N) {
+#pragma unroll
+                        for (int c = 0; c < LD; c += 4)
+                            *(float4*)&F[step[t]][c] = make_float4(
+                                r[t][c], c + 1 < N ? r[t][c + 1] : 0.f,
+                                c + 2 < N ? r[t][c + 2] : 0.f, c + 3 < N ? r[t][c + 3] : 0.f);
+                        dinv[step[t]] = dinv_own[t];
+                    }
+            } else if (mv) {
+                for (int q = l; q < N * N; q += 8) out[q] = 0.f;
+            }
+            __syncwarp();
+            if (ok) {
+                // lane l, row t: y = L^{-1} e_step, then x = U^{-1} y: column l + 8t of the
+                // inverse (the unit vector of that row's pivot step)
+                float y[R][N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    float v[R];
+#pragma unroll
+                    for (int t = 0; t < R; ++t) v[t] = i == step[t] ? 1.f : 0.f;
+#pragma unroll
+                    for (int c = 0; c < ((i + 3) & ~3); c += 4) {
+                        const float4 l4 = *(const float4*)&F[i][c];
+#pragma unroll
+                        for (int t = 0; t < R; ++t) {
+                            if (c < i) v[t] = fmaf(-l4.x, y[t][c], v[t]);
+                            if (c + 1 < i) v[t] = fmaf(-l4.y, y[t][c + 1], v[t]);
+                            if (c + 2 < i) v[t] = fmaf(-l4.z, y[t][c + 2], v[t]);
+                            if (c + 3 < i) v[t] = fmaf(-l4.w, y[t][c + 3], v[t]);
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < R; ++t) y[t][i] = v[t];
+                }
+#pragma unroll
+                for (int i = N - 1; i >= 0; --i) {
+                    float v[R];
+#pragma unroll
+                    for (int t = 0; t < R; ++t) v[t] = y[t][i];
+#pragma unroll
+                    for (int c = (i + 1) & ~3; c < N; c += 4) {
+                        const float4 u4 = *(const float4*)&F[i][c];
+#pragma unroll
+                        for (int t = 0; t < R; ++t) {
+                            if (c > i) v[t] = fmaf(-u4.x, y[t][c], v[t]);
+                            if (c + 1 > i && c + 1 < N) v[t] = fmaf(-u4.y, y[t][c + 1], v[t]);
+                            if (c + 2 > i && c + 2 < N) v[t] = fmaf(-u4.z, y[t][c + 2], v[t]);
+                            if (c + 3 > i && c + 3 < N) v[t] = fmaf(-u4.w, y[t][c + 3], v[t]);
+                        }
+                    }
+                    const float di = dinv[i];
+#pragma unroll
+                    for (int t = 0; t < R; ++t) y[t][i] = v[t] * di;
+                }
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+                    if (l + 8 * t < N) {
+#pragma unroll
+                        for (int i = 0; i < N; ++i) out[i * N + l + 8 * t] = y[t][i];
+                    }
+            }
+        }
+        __syncwarp();  // occ, F and dinv are rewritten by the next configuration
+    }
+}
+
+template <int N>
+static int launch_lu_grp_n(const uint64_t* dets, int64_t M, int norb, int nel, int spin,
+                           const float* Phi, double* la, int* ex, int8_t* sg, float* Ainv,
+                           int* singular, cudaStream_t s) {
+    const int64_t warps = (M + 3) / 4;
+    k_lu_grp<N><<<grid_for(warps * 32, LU_GRP_WARPS * 32, 148 * 32), LU_GRP_WARPS * 32, 0, s>>>(
+        (const ulonglong2*)dets, M, norb, nel, spin, Phi, la, ex, sg, Ainv, singular);
+    NQS_CK_LAUNCH();
+    return NQS_OK;
+}
+
 template <int N>
 static int launch_lu_lane_n(const uint64_t* dets, int64_t M, int norb, int nel, int spin,
                             const float* Phi, double* la, int* ex, int8_t* sg, float* Ainv,
@@ -687,15 +940,19 @@ static int launch_lu_lane(const uint64_t* dets, int64_t M, int norb, int nel, in
                           const float* Phi, double* la, int* ex, int8_t* sg, float* Ainv,
                           int* singular, cudaStream_t s) {
     switch (n) {
+#define NQS_GRP_CASE(K)                                                                       \
+    case K:                                                                                   \
+        return launch_lu_grp_n<K>(dets, M, norb, nel, spin, Phi, la, ex, sg, Ainv, singular, s);
 #define NQS_LANE_CASE(K)                                                                      \
     case K:                                                                                   \
         return launch_lu_lane_n<K>(dets, M, norb, nel, spin, Phi, la, ex, sg, Ainv, singular, s);
-        NQS_LANE_CASE(13) NQS_LANE_CASE(14) NQS_LANE_CASE(15) NQS_LANE_CASE(16)
-        NQS_LANE_CASE(17) NQS_LANE_CASE(18) NQS_LANE_CASE(19) NQS_LANE_CASE(20)
-        NQS_LANE_CASE(21) NQS_LANE_CASE(22) NQS_LANE_CASE(23) NQS_LANE_CASE(24)
+        NQS_GRP_CASE(13) NQS_GRP_CASE(14) NQS_GRP_CASE(15) NQS_GRP_CASE(16)
+        NQS_GRP_CASE(17) NQS_GRP_CASE(18) NQS_GRP_CASE(19) NQS_GRP_CASE(20)
+        NQS_GRP_CASE(21) NQS_GRP_CASE(22) NQS_GRP_CASE(23) NQS_GRP_CASE(24)
         NQS_LANE_CASE(25) NQS_LANE_CASE(26) NQS_LANE_CASE(27) NQS_LANE_CASE(28)
         NQS_LANE_CASE(29) NQS_LANE_CASE(30) NQS_LANE_CASE(31) NQS_LANE_CASE(32)
 #undef NQS_LANE_CASE
+#undef NQS_GRP_CASE
         default: return NQS_ERR_UNSUPPORTED;
     }
 }

@@ -179,11 +179,12 @@ def test_micro_batched_gradient_recomputation(mixed):
     assert rel < (1e-5 if mixed else 1e-12), rel
 
 
-@pytest.mark.parametrize("norb,n", [(18, 13), (20, 16), (26, 24)])
+@pytest.mark.parametrize("norb,n", [(18, 13), (20, 16), (22, 20), (26, 24), (31, 28)])
 def test_mixed_blocks_of_13_to_32_rows_vs_quantised_oracle(norb, n):
-    """Spin blocks of 13..32 rows in the mixed form (the FP32 LU with one lane per row, scalar
-    loads at 13 rows, 16-byte loads at 16 and 24): amplitudes, E_S and the gradient, which goes
-    through the block inverses, against the quantisation-matched oracle."""
+    """Spin blocks of 13..32 rows in the mixed form: the FP32 LU with four blocks per warp and
+    up to three rows per lane at 13..24 rows (scalar loads at 13, a partial third row at 20,
+    16-byte loads at 16, 20 and 24), one lane per row at 28. Amplitudes, E_S and the gradient,
+    which goes through the block inverses, against the quantisation-matched oracle."""
     need_gpu()
     N = nqs()
     p, _ = small_problem(norb, n, 400, 70 + norb, hidden=(64, 64))
