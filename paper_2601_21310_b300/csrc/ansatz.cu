@@ -1387,11 +1387,14 @@ __global__ void k_pad_cols_bf16(const __nv_bfloat16* __restrict__ W, int R, int 
 #define ROWSUM_CHUNK 16384
 
 // out[n] = sum over the M rows of X [M][ld] (bf16) of column n, FP32 with compensated
-// (Kahan) additions, fixed order: each block sums COLSUM_ROWS rows in row order (thread t:
-// columns 8t .. 8t + 7 by one 16-byte load per row), then one thread per column adds the
-// blocks' partial sums in order. The compensation keeps the error near one rounding of the
+// (Kahan) additions, fixed order: a row is covered by tpr = ceil(N / 8) threads rounded up to
+// a warp (thread t: columns 8t .. 8t + 7, one 16-byte load per row), a 256-thread block holds
+// 256 / tpr such groups, and group q of block b sums rows [(b G + q) R, (b G + q + 1) R) in row
+// order (R = COLSUM_ROWS, G groups a block); then one warp per column adds the groups'
+// partial sums: lane l of the column's warp the partials l, l + 32, ... in order, then the 32
+// lane sums by a fixed shuffle tree. The compensation keeps the error near one rounding of the
 // result whatever |S|, so the order of the terms does not show at the level of FP32.
-#define COLSUM_ROWS 2048
+#define COLSUM_ROWS 1024
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
     const float y = x - comp;
     const float t = sum + y;
@@ -1400,13 +1403,19 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
 }
 
 __global__ void __launch_bounds__(256) k_colsum_part(const __nv_bfloat16* __restrict__ X, int64_t M,
-                                                     int N, int64_t ld, float2* __restrict__ part) {
-    const int64_t r0 = (int64_t)blockIdx.x * COLSUM_ROWS;
+                                                     int N, int64_t ld, int tpr,
+                                                     float2* __restrict__ part) {
+    const int groups = 256 / tpr;
+    const int q = threadIdx.x / tpr, tt = threadIdx.x - q * tpr;
+    if (q >= groups) return;
+    const int64_t pidx = (int64_t)blockIdx.x * groups + q;
+    const int64_t r0 = pidx * COLSUM_ROWS;
     const int64_t r1 = r0 + COLSUM_ROWS < M ? r0 + COLSUM_ROWS : M;
-    for (int c8 = 8 * threadIdx.x; c8 < N; c8 += 8 * 256) {
+    for (int c8 = 8 * tt; c8 < N; c8 += 8 * tpr) {
         float acc[8], cmp[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) acc[t] = cmp[t] = 0.f;
+#pragma unroll 4
         for (int64_t r = r0; r < r1; ++r) {
             const uint4 pk = *(const uint4*)(X + r * ld + c8);
             const __nv_bfloat162* h2 = (const __nv_bfloat162*)&pk;
@@ -1417,36 +1426,47 @@ __global__ void __launch_bounds__(256) k_colsum_part(const __nv_bfloat16* __rest
                 kahan_add(acc[2 * t + 1], cmp[2 * t + 1], f.y);
             }
         }
-        float2* out = part + (int64_t)blockIdx.x * N;
+        float2* out = part + pidx * N;
 #pragma unroll
         for (int t = 0; t < 8; ++t)
             if (c8 + t < N) out[c8 + t] = make_float2(acc[t], cmp[t]);
     }
 }
 
-__global__ void k_colsum_final(const float2* __restrict__ part, int N, int nblocks,
+__global__ void k_colsum_final(const float2* __restrict__ part, int N, int64_t nparts,
                                float* __restrict__ out) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+    const int n = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (n >= N) return;  // warp-uniform
     float t = 0.f, c = 0.f;
-    for (int b = 0; b < nblocks; ++b) {
-        const float2 p = part[(int64_t)b * N + n];
+    for (int64_t b = lane; b < nparts; b += 32) {
+        const float2 p = part[b * N + n];
         kahan_add(t, c, p.x);
-        kahan_add(t, c, -p.y);  // the block's own compensation (its sum's missing part, negated)
+        kahan_add(t, c, -p.y);  // the group's own compensation (its sum's missing part, negated)
     }
-    out[n] = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ot = __shfl_xor_sync(FULL_MASK, t, o), oc = __shfl_xor_sync(FULL_MASK, c, o);
+        kahan_add(t, c, ot);
+        kahan_add(t, c, -oc);
+    }
+    if (lane == 0) out[n] = t;
 }
 
 // ld: a multiple of 8 with room for N rounded up to 8 (the padding columns are read, not used)
 static int colsum_bf16(Scratch& sc, const void* X, int64_t M, int N, int64_t ld, float* out,
                        cudaStream_t s) {
-    if (ld % 8 || ld < ((N + 7) & ~7) || ((uintptr_t)X & 15)) return NQS_ERR_ARG;
-    const int nblocks = (int)((M + COLSUM_ROWS - 1) / COLSUM_ROWS);
+    if (ld % 8 || ld < ((N + 7) & ~7) || ((uintptr_t)X & 15) || N <= 0) return NQS_ERR_ARG;
+    int tpr = ((N + 7) / 8 + 31) & ~31;
+    if (tpr > 256) tpr = 256;
+    const int groups = 256 / tpr;
+    const int64_t nparts = (M + COLSUM_ROWS - 1) / COLSUM_ROWS;
+    const int64_t nblocks = (nparts + groups - 1) / groups;
     float2* part;
-    NQS_TRY(sc.get(&part, (size_t)nblocks * N));
-    k_colsum_part<<<(unsigned)nblocks, 256, 0, s>>>((const __nv_bfloat16*)X, M, N, ld, part);
+    NQS_TRY(sc.get(&part, (size_t)nblocks * groups * N));
+    k_colsum_part<<<(unsigned)nblocks, 256, 0, s>>>((const __nv_bfloat16*)X, M, N, ld, tpr, part);
     NQS_CK_LAUNCH();
-    k_colsum_final<<<(N + 255) / 256, 256, 0, s>>>(part, N, nblocks, out);
+    k_colsum_final<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(part, N, nparts, out);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }

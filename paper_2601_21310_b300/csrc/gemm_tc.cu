@@ -22,6 +22,7 @@
 #include <cudaTypedefs.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <vector>
@@ -1223,13 +1224,20 @@ int launch_tc_pair(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorM
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    static int max_clusters = 0;  // per tile width (one template instance each)
+    // resident clusters, per device and tile width (one template instance each); concurrent
+    // first calls may both query, and store the same value
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    NQS_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return NQS_ERR_UNSUPPORTED;
+    int max_clusters = cache[dev].load(std::memory_order_relaxed);
     if (max_clusters == 0) {
         cfg.gridDim = dim3(2 * (num_sms() / 2), 1, 1);
         int n = 0;
         NQS_CK(cudaOccupancyMaxActiveClusters(&n, k_gemm_tc_pair<BN>, &cfg));
         if (n <= 0) return NQS_ERR_UNSUPPORTED;
         max_clusters = n;
+        cache[dev].store(n, std::memory_order_relaxed);
     }
     const int units = ((a.N + BN - 1) / BN) * ((a.M + 255) / 256) * a.splits;
     const int clusters = units < max_clusters ? units : max_clusters;
