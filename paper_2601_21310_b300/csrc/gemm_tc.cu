@@ -1,6 +1,11 @@
 // BF16 tensor-core GEMM for the dense backflow layers on sm_103a (5th-generation tensor cores):
-//   C[m][n] = epilogue( sum_k A[m][k] * B[n][k] ),  A, B bfloat16, K-major (k contiguous),
-//   FP32 accumulation in tensor memory.
+//   C[m][n] = epilogue( sum_k A[m][k] * B[n][k] ),  A, B bfloat16, each operand K-major
+//   (k contiguous) or MN-major (m or n contiguous: the row-major activations a weight gradient
+//   reduces over), FP32 accumulation in tensor memory.
+//
+// Two kernels. k_gemm_tc (below) runs 64- and 128-column tiles on single SMs; k_gemm_tc_pair
+// runs 256-column tiles on clusters of two SMs sharing one M = 256 MMA stream (cta_group::2),
+// each SM staging its own rows of A and half of B; its roles are those described here.
 //
 // Persistent kernel, one CTA per SM, work units (128 x BN output tiles, times the K splits)
 // dealt round-robin; ten warps:
