@@ -1402,9 +1402,9 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
     sum = t;
 }
 
-__global__ void __launch_bounds__(256) k_colsum_part(const __nv_bfloat16* __restrict__ X, int64_t M,
-                                                     int N, int64_t ld, int tpr,
-                                                     float2* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_colsum_bf16_part(const __nv_bfloat16* __restrict__ X,
+                                                          int64_t M, int N, int64_t ld, int tpr,
+                                                          float2* __restrict__ part) {
     const int groups = 256 / tpr;
     const int q = threadIdx.x / tpr, tt = threadIdx.x - q * tpr;
     if (q >= groups) return;
@@ -1433,8 +1433,8 @@ __global__ void __launch_bounds__(256) k_colsum_part(const __nv_bfloat16* __rest
     }
 }
 
-__global__ void k_colsum_final(const float2* __restrict__ part, int N, int64_t nparts,
-                               float* __restrict__ out) {
+__global__ void k_colsum_bf16_final(const float2* __restrict__ part, int N, int64_t nparts,
+                                    float* __restrict__ out) {
     const int n = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (n >= N) return;  // warp-uniform
@@ -1464,9 +1464,10 @@ static int colsum_bf16(Scratch& sc, const void* X, int64_t M, int N, int64_t ld,
     const int64_t nblocks = (nparts + groups - 1) / groups;
     float2* part;
     NQS_TRY(sc.get(&part, (size_t)nblocks * groups * N));
-    k_colsum_part<<<(unsigned)nblocks, 256, 0, s>>>((const __nv_bfloat16*)X, M, N, ld, tpr, part);
+    k_colsum_bf16_part<<<(unsigned)nblocks, 256, 0, s>>>((const __nv_bfloat16*)X, M, N, ld, tpr,
+                                                         part);
     NQS_CK_LAUNCH();
-    k_colsum_final<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(part, N, nparts, out);
+    k_colsum_bf16_final<<<(unsigned)((N + 7) / 8), 256, 0, s>>>(part, N, nparts, out);
     NQS_CK_LAUNCH();
     return NQS_OK;
 }
@@ -1568,6 +1569,51 @@ static int forward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, int
     return NQS_OK;
 }
 
+// dPhi of the mixed form written whole rows at a time: each warp clears a shared-memory copy
+// of its configuration's row ([norb][nel] bf16, ldp entries), places w_m (A^-1)_kj at
+// [occ_j][col0 + k] of each spin block (the values of k_adjoint), and writes the row out with
+// 16-byte stores. No separate clearing pass; the global stores are whole rows.
+__global__ void __launch_bounds__(256) k_adjoint_rows(const ulonglong2* __restrict__ dets,
+                                                      int64_t M, int norb, int na, int nb,
+                                                      const double* __restrict__ w,
+                                                      const float* __restrict__ Ainv_a,
+                                                      const float* __restrict__ Ainv_b,
+                                                      __nv_bfloat16* __restrict__ dPhi,
+                                                      int64_t ldp) {
+    extern __shared__ __align__(16) uint8_t adj_smem[];
+    __shared__ uint8_t occ_s[8][2][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nel = na + nb;
+    const int nvec = (int)(ldp / 8);  // 16-byte pieces of a row (ldp is a multiple of 8)
+    uint4* rowv = (uint4*)adj_smem + (int64_t)warp * nvec;
+    __nv_bfloat16* row = (__nv_bfloat16*)rowv;
+    for (int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; m < M;
+         m += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const ulonglong2 x = dets[m];
+        for (int v = lane; v < nvec; v += 32) rowv[v] = make_uint4(0u, 0u, 0u, 0u);
+        for (int p = lane; p < norb; p += 32) {
+            const uint64_t below = p == 0 ? 0ull : ((1ull << p) - 1ull);
+            if ((x.x >> p) & 1ull) occ_s[warp][0][__popcll(x.x & below)] = (uint8_t)p;
+            if ((x.y >> p) & 1ull) occ_s[warp][1][__popcll(x.y & below)] = (uint8_t)p;
+        }
+        __syncwarp();
+        const float wm = (float)w[m];
+        for (int spin = 0; spin < 2; ++spin) {
+            const int n = spin == 0 ? na : nb, col0 = spin == 0 ? 0 : na;
+            const float* inv = spin == 0 ? Ainv_a + m * na * na : Ainv_b + m * nb * nb;
+            for (int r = lane; r < n * n; r += 32) {
+                const int j = r / n, k = r - j * n;
+                const float g = wm * inv[k * n + j];
+                row[occ_s[warp][spin][j] * nel + col0 + k] = __float2bfloat16_rn(g);
+            }
+        }
+        __syncwarp();
+        uint4* out = (uint4*)(dPhi + m * ldp);
+        for (int v = lane; v < nvec; v += 32) out[v] = rowv[v];
+        __syncwarp();
+    }
+}
+
 static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, const Fwd& f,
                              const double* w, void* grad, cudaStream_t s) {
     const ProblemDev& P = net->prob->d;
@@ -1587,10 +1633,17 @@ static int backward_mixed_tc(nqs_net* net, Scratch& sc, const uint64_t* dets, co
     NQS_TRY(sc.get(&W2T, (size_t)H1 * H2));
     NQS_TRY(sc.get(&dZ2, M * H2));
     NQS_TRY(sc.get(&dZ1, M * H1));
-    NQS_CK(cudaMemsetAsync(dPhi, 0, M * ldP * 2, s));
-    k_adjoint<float, __nv_bfloat16><<<grid_for(M * 32, 256, 148 * 64), 256, 0, s>>>(
-        (const ulonglong2*)dets, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a,
-        (const float*)f.Ainv_b, dPhi, ldP);
+    const size_t adj_smem = (size_t)8 * ldP * 2;  // one dPhi row per warp
+    if (adj_smem <= 48 * 1024) {
+        k_adjoint_rows<<<grid_for(M * 32, 256, 148 * 64), 256, adj_smem, s>>>(
+            (const ulonglong2*)dets, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a,
+            (const float*)f.Ainv_b, dPhi, ldP);
+    } else {
+        NQS_CK(cudaMemsetAsync(dPhi, 0, M * ldP * 2, s));
+        k_adjoint<float, __nv_bfloat16><<<grid_for(M * 32, 256, 148 * 64), 256, 0, s>>>(
+            (const ulonglong2*)dets, M, P.norb, P.na, P.nb, w, (const float*)f.Ainv_a,
+            (const float*)f.Ainv_b, dPhi, ldP);
+    }
     NQS_CK_LAUNCH();
     NQS_TRY(transpose_bf16(net->p[4], nout, H2, H2, W3T, ldP, s));  // W3 [nout][H2] -> [H2][nout]
     NQS_TRY(transpose_bf16(net->p[2], H2, H1, H1, W2T, H2, s));     // W2 [H2][H1] -> [H1][H2]
