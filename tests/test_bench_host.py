@@ -90,3 +90,30 @@ def test_pt2_screening_default_by_workload(monkeypatch):
         assert bench.parse().eps_pt2 == eps
     monkeypatch.setattr("sys.argv", ["bench.py", "--workload", "cr2_48e42o", "--eps-pt2", "0"])
     assert bench.parse().eps_pt2 == 0.0  # an explicit value wins
+
+
+def test_largest_kernel_issue_figure_tracks_the_kernel_source():
+    """The issue-slot fraction of the screened traversal (the bench line's largest kernel) is
+    read from its committed ncu summary only while hb.cu is the source it was captured from."""
+    path = os.path.join(ROOT, "profiles", "pt2_emit_cr2_48e42o.md")
+    vals = _profile_fields(path)
+    with open(os.path.join(ROOT, vals["source_file"]), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    u = bench.kernel_traffic("pt2_emit", "cr2_48e42o", "issue_slots_busy_frac")
+    if sha == vals["source_sha256"]:
+        assert u == float(vals["issue_slots_busy_frac"]) and 0.0 < u <= 1.0
+    else:
+        assert u is None
+
+
+def test_tensor_probe_only_option(monkeypatch):
+    """--tensor-probe-only M,N,K (and --probe-mn) select the one-GEMM profiling run."""
+    monkeypatch.setattr("sys.argv", ["bench.py", "--tensor-probe-only", "262144,2016,1024"])
+    a = bench.parse()
+    assert a.tensor_probe_only == "262144,2016,1024" and not a.probe_mn
+    assert tuple(int(v) for v in a.tensor_probe_only.split(",")) == (262144, 2016, 1024)
+    monkeypatch.setattr("sys.argv", ["bench.py", "--tensor-probe-only", "1024,1024,262144",
+                                     "--probe-mn"])
+    assert bench.parse().probe_mn
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    assert bench.parse().tensor_probe_only is None
