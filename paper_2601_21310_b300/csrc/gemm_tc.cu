@@ -419,6 +419,13 @@ struct TcSmem {
     static constexpr int BYTES = STAGES * STAGE + EPI + 1024 /*align*/ + 256 /*barriers*/;
 };
 
+// shared memory of one CTA (227 KB opt-in limit); barriers: full and empty per stage, two
+// accumulator-full and two accumulator-empty, then the TMEM address slot and the abort flag
+static_assert(TcSmem<64>::BYTES <= 232448 && TcSmem<128>::BYTES <= 232448 &&
+                  TcSmem<256>::BYTES <= 232448,
+              "single-SM GEMM shared memory");
+static_assert((2 * TcSmem<64>::STAGES + 4) * 8 + 8 <= 256, "single-SM GEMM barrier block");
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -632,6 +639,10 @@ struct TcSmem2 {
     static constexpr int STAGES = ROOM / STAGE < 8 ? ROOM / STAGE : 8;
     static constexpr int BYTES = STAGES * STAGE + EPI + 1024 + 256;
 };
+
+// as TcSmem, plus the drain barrier of the MMA issuer
+static_assert(TcSmem2<256>::BYTES <= 232448, "paired GEMM shared memory");
+static_assert((2 * TcSmem2<256>::STAGES + 5) * 8 + 8 <= 256, "paired GEMM barrier block");
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {
     uint32_t r;
