@@ -60,3 +60,28 @@ def test_every_status_has_a_message(L):
     for code in range(-8, 2):
         msg = L.nqs_status_string(code)
         assert isinstance(msg, bytes) and len(msg) > 0
+
+
+def test_gemm_ex_rejects_bad_arguments(L):
+    """nqs_gemm_bf16_ex: null operands, empty shapes, and leading dimensions shorter than the
+    contiguous extent of each operand layout (K for K-major, M or N for MN-major)."""
+    buf = np.zeros(64, np.float32)
+    p = buf.ctypes.data_as(C.c_void_p)
+    ex = L.nqs_gemm_bf16_ex
+    assert ex(None, 8, 0, p, 8, 0, 8, 8, 8, p, 8, None, None) == NQS_ERR_ARG
+    assert ex(p, 8, 0, None, 8, 0, 8, 8, 8, p, 8, None, None) == NQS_ERR_ARG
+    assert ex(p, 8, 0, p, 8, 0, 8, 8, 8, None, 8, None, None) == NQS_ERR_ARG
+    for M, Nn, K in ((0, 8, 8), (8, 0, 8), (8, 8, 0)):
+        assert ex(p, 8, 1, p, 8, 1, M, Nn, K, p, 8, None, None) == NQS_ERR_ARG
+    # K-major needs lda, ldb >= K; MN-major needs lda >= M, ldb >= N
+    assert ex(p, 8, 0, p, 16, 0, 8, 8, 16, p, 8, None, None) == NQS_ERR_ARG
+    assert ex(p, 16, 0, p, 8, 0, 8, 8, 16, p, 8, None, None) == NQS_ERR_ARG
+    assert ex(p, 8, 1, p, 16, 1, 16, 16, 8, p, 16, None, None) == NQS_ERR_ARG
+    assert ex(p, 16, 1, p, 8, 1, 16, 16, 8, p, 16, None, None) == NQS_ERR_ARG
+
+
+def test_gemm_pairing_switch(L):
+    """nqs_set_gemm_pairing takes any int (non-zero: on) and leaves the library paired."""
+    assert L.nqs_set_gemm_pairing(0) == 0
+    assert L.nqs_set_gemm_pairing(7) == 0
+    assert L.nqs_set_gemm_pairing(1) == 0
